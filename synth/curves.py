@@ -1,0 +1,124 @@
+"""Closed-curve samplers for the Nystrom discretisation (Sec. 3.1).
+
+A curve is sampled at N equispaced parameters theta_j = 2*pi*j/N, j = 0..N-1.
+For a counter-clockwise parametrisation gamma(theta) the sampler returns
+
+* x_j, y_j           the node gamma(theta_j)
+* nx_j, ny_j         the unit normal (gamma_2', -gamma_1')/|gamma'|, which points
+                     out of the bounded region Omega_1 (into Omega_0, Sec. 2)
+* w_j                the trapezoidal weight |gamma'(theta_j)| * 2*pi/N (Sec. 3.1)
+* kappa_j            the signed curvature, positive on a convex curve
+
+Every curve here is a "Fourier star" r(theta) = 1 + sum_m a_m cos(m*theta + phi_m)
+in polar form; the unit disk is the case with no modes.  The samples are
+computed in float64 from the closed-form derivatives of r(theta).
+"""
+
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Dict, List, Sequence, Tuple
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class Curve:
+    """Sampled closed curve (structure of arrays, float64, length N)."""
+
+    x: np.ndarray
+    y: np.ndarray
+    nx: np.ndarray
+    ny: np.ndarray
+    w: np.ndarray
+    kappa: np.ndarray
+    name: str = "curve"
+
+    @property
+    def n(self) -> int:
+        return int(self.x.shape[0])
+
+    def arrays(self) -> Tuple[np.ndarray, ...]:
+        return (self.x, self.y, self.nx, self.ny, self.w, self.kappa)
+
+
+def fourier_star(n: int, modes: Sequence[Tuple[int, float, float]] = (), name: str = "star") -> Curve:
+    """Sample r(theta) = 1 + sum a*cos(m*theta + phi) over (m, a, phi) in ``modes``."""
+    if n <= 0:
+        raise ValueError("n must be positive")
+    theta = 2.0 * np.pi * np.arange(n, dtype=np.float64) / n
+    r = np.ones(n)
+    dr = np.zeros(n)
+    ddr = np.zeros(n)
+    for m, a, phi in modes:
+        arg = m * theta + phi
+        r += a * np.cos(arg)
+        dr -= a * m * np.sin(arg)
+        ddr -= a * m * m * np.cos(arg)
+    c, s = np.cos(theta), np.sin(theta)
+    x, y = r * c, r * s
+    dx = dr * c - r * s
+    dy = dr * s + r * c
+    ddx = ddr * c - 2.0 * dr * s - r * c
+    ddy = ddr * s + 2.0 * dr * c - r * s
+    speed = np.sqrt(dx * dx + dy * dy)
+    nx, ny = dy / speed, -dx / speed
+    w = speed * (2.0 * np.pi / n)
+    kappa = (dx * ddy - dy * ddx) / speed**3
+    return Curve(x, y, nx, ny, w, kappa, name)
+
+
+def disk(n: int) -> Curve:
+    """Unit circle: nodes (cos, sin), normals equal to the nodes, w = 2*pi/N, kappa = 1."""
+    return fourier_star(n, (), name="disk")
+
+
+def star(n: int, amp: float = 0.3, m: int = 5) -> Curve:
+    """Star r(theta) = 1 + amp*cos(m*theta)."""
+    return fourier_star(n, ((m, amp, 0.0),), name=f"star{m}")
+
+
+def random_star_batch(count: int, seed: int, n_min: int = 2048, n_max: int = 32768,
+                      k_range: Tuple[float, float] = (5.0, 40.0),
+                      ratio_range: Tuple[float, float] = (1.2, 2.0),
+                      leaf: int = 128) -> List[Dict]:
+    """Random scatterers r = 1 + sum_{m=2..8} a_m cos(m*theta + phi_m), a_m ~ U(0, 0.05).
+
+    Node counts are drawn log-uniformly in [n_min, n_max] and rounded to a
+    multiple of ``leaf``; k_ext ~ U(k_range), k_int = k_ext * U(ratio_range).
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        a = rng.uniform(0.0, 0.05, size=7)
+        phi = rng.uniform(0.0, 2.0 * np.pi, size=7)
+        n = int(round(math.exp(rng.uniform(math.log(n_min), math.log(n_max)))))
+        n = max(leaf, leaf * int(round(n / leaf)))
+        k0 = float(rng.uniform(*k_range))
+        k1 = k0 * float(rng.uniform(*ratio_range))
+        modes = tuple((m, float(a[m - 2]), float(phi[m - 2])) for m in range(2, 9))
+        out.append({"curve": fourier_star(n, modes, name=f"rstar{i}"), "k0": k0, "k1": k1})
+    return out
+
+
+# Named workloads.  eps0 = 1 and eps1 = (k1/k0)^2 follow k_i = omega*sqrt(eps_i) (Sec. 2)
+# with eps0 = 1 as in Sec. 6.
+WORKLOADS: Dict[str, Dict] = {
+    "disk512": dict(curve=("disk", 512), k0=5.0, k1=8.0, leaf=64, nproxy=32, tol=1e-10),
+    "star16k": dict(curve=("star", 16384), k0=20.0, k1=30.0, leaf=128, nproxy=64, tol=1e-10),
+    "star64k": dict(curve=("star", 65536), k0=40.0, k1=60.0, leaf=128, nproxy=64, tol=1e-10),
+    "star262k": dict(curve=("star", 262144), k0=100.0, k1=150.0, leaf=128, nproxy=64, tol=1e-8),
+}
+
+
+def workload(name: str, n: int | None = None) -> Dict:
+    """Return the named workload with its sampled curve; ``n`` overrides the node count."""
+    spec = dict(WORKLOADS[name])
+    kind, n0 = spec.pop("curve")
+    n = n0 if n is None else n
+    spec["curve"] = disk(n) if kind == "disk" else star(n)
+    spec["eps0"] = 1.0
+    spec["eps1"] = (spec["k1"] / spec["k0"]) ** 2
+    spec["name"] = name
+    return spec
