@@ -1,0 +1,351 @@
+"""Benchmark: symmetric HSS compress + factor + solve on one B300 (replicas for N > 1).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload star16k]
+
+Workload (default): star r(theta) = 1 + 0.3 cos(5 theta), 16384 Nystrom nodes (32768 complex128
+unknowns), k_ext = 20, k_int = 30, eps0 = 1, eps1 = (k_int/k_ext)^2, leaf 128, ID tolerance 1e-10,
+rings of at least 64 proxy points at 1.5x the box radius, plane wave at angle 0.
+A step is one full compress + factor + right-hand side + solve of that scatterer through the
+C ABI, with the curve already resident on the device.  The symmetric single-ID solver is the
+headline; the non-symmetric two-ID baseline is timed on the same GPU and inputs.
+
+Metric: seconds per scatterer (compress + factor + solve); for N GPUs every rank solves its own
+copy of the workload (replicas, weak scaling) and value = max-over-ranks seconds per step / N.
+L2: flushed between timed steps by writing a 512 MiB buffer outside the timed events.
+
+--impl reference times the FP64 CPU oracle on this host (bounded sample, see cpu_baseline).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "HSS compress+factor+solve sec, sym vs non-sym, rel err ≤1e-8; % roofline"
+FP64_PEAK_TFLOPS = 1.25   # nominal dense FP64 of a B300 (148 SMs at up to 2032 MHz)
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _workload(name):
+    from synth import workload
+    return workload(name)
+
+
+def _config(w, mode):
+    c = w["curve"]
+    return {"workload": f"{w['name']}: {c.name} curve, N={c.n} nodes ({2 * c.n} complex128 unknowns), "
+                        f"k_ext={w['k0']:g}, k_int={w['k1']:g}, eps1=(k_int/k_ext)^2, leaf {w['leaf']}, "
+                        f"ID tol {w['tol']:g}, >= {w['nproxy']}-point proxy rings at 1.5x box radius",
+            "mode": mode, "l2": "flushed between timed steps (512 MiB write outside the timed events)",
+            "parallelism": "replicas (one scatterer per GPU)"}
+
+
+# ----------------------------------------------------------------------------------- ours
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2609_33216_b300 import symhss as S
+    from paper_2609_33216_b300.solver import Solver
+
+    rank, world, local = _env_rank()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    w = _workload(args.workload)
+    c = w["curve"]
+    kw = dict(leaf=w["leaf"], nproxy=w["nproxy"], tol=w["tol"])
+    dev_curve = True
+    solvers = {m: Solver(c, w["k0"], w["k1"], w["eps0"], w["eps1"], mode=m, curve_on_device=dev_curve, **kw)
+               for m in ("sym", "base")}
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(s):
+        s.compress()
+        s.factor()
+        return s.solve(s.rhs(0.0))
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    results = {}
+    for mode in ("sym", "base"):
+        s = solvers[mode]
+        for _ in range(args.warmup):
+            x = step(s)
+        barrier()
+        sampler = ClockSampler(local) if (mode == "sym" and rank == 0) else None
+        if sampler:
+            sampler.start()
+        times = []
+        launches = 0
+        kms = [0.0] * 8
+        kwork = [0.0] * 8
+        klaunch = [0] * 8
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            x = step(s)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            st = s.stats()
+            for k in range(8):
+                kms[k] += st.kernel_ms[k]
+                kwork[k] += st.kernel_work[k]
+                klaunch[k] += st.kernel_launches[k]
+            launches += sum(st.kernel_launches[k] for k in range(8)) + 1  # + plane-wave kernel
+        barrier()
+        clocks = sampler.stop() if sampler else None
+        tot = torch.tensor([sum(times)], device="cuda", dtype=torch.float64)
+        if world > 1:
+            dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+        st = s.stats()
+        results[mode] = dict(ms_total=float(tot.item()), times=times, x=x, stats=st, clocks=clocks,
+                             launches=launches, kms=kms, kwork=kwork, klaunch=klaunch)
+
+    xs = results["sym"]["x"].cpu().numpy()
+    xb = results["base"]["x"].cpu().numpy()
+    rel_diff = float(np.linalg.norm(xs - xb) / np.linalg.norm(xb))
+
+    # end to end through the C ABI: host curve in, host solution out, every step
+    e2e_s = solvers["sym"]
+    host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in c.arrays()]
+    xh = torch.empty(2 * c.n, dtype=torch.complex128).pin_memory()
+    curve_struct = S.curve_struct(c.n, [t.data_ptr() for t in host], S.SYMHSS_HOST)
+
+    def e2e_step():
+        S.symhss_set_curve(e2e_s.h, curve_struct, stream.cuda_stream)
+        x = step(e2e_s)
+        xh.copy_(x, non_blocking=True)
+        torch.cuda.synchronize()
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    barrier()
+    e2e_sec = (time.perf_counter() - t0) / args.steps
+    e2e_t = torch.tensor([e2e_sec], device="cuda", dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_sec = float(e2e_t.item())
+
+    if rank == 0:
+        r = results["sym"]
+        sec_sym = r["ms_total"] / args.steps / 1000.0
+        sec_base = results["base"]["ms_total"] / args.steps / 1000.0
+        names = S.K_NAMES
+        per_kernel = {names[k]: {"ms_per_step": r["kms"][k] / args.steps, "launches_per_step": r["klaunch"][k] / args.steps,
+                                 "work_per_step": r["kwork"][k] / args.steps} for k in range(5)}
+        # dominant dense-arithmetic kernel class by device time
+        dom = max(range(5), key=lambda k: r["kms"][k])
+        roof = None
+        if r["kms"][dom] > 0 and r["kwork"][dom] > 0 and dom != 0:
+            achieved = r["kwork"][dom] / (r["kms"][dom] * 1e-3) / 1e12
+            roof = {"kernel": names[dom], "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                    "peak_source": "nominal FP64 of the B300 (derived: not in the measured-peaks file)",
+                    "avg_launch_ms": r["kms"][dom] / max(1, r["klaunch"][dom])}
+        elif r["kms"][dom] > 0:
+            roof = {"kernel": names[dom], "bound": "alu", "achieved": r["kwork"][dom] / (r["kms"][dom] * 1e-3),
+                    "peak": None, "unit": "pairs/s", "frac": None, "traffic": None}
+        st = r["stats"]
+        out = {
+            "metric": METRIC, "value": sec_sym / world, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sec_sym * 1000.0, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "complex128 (f64)", "data": "synthetic",
+            "config": _config(w, "sym"),
+            "nonsym": {"value": sec_base / world, "unit": "s", "ms_per_step": sec_base * 1000.0},
+            "speedup_sym_vs_nonsym": sec_base / sec_sym,
+            "rel_diff_sym_vs_nonsym": rel_diff,
+            "phases_ms": {"compress": st.ms_compress, "factor": st.ms_factor, "solve": st.ms_solve},
+            "per_kernel": per_kernel,
+            "ranks": {"max_flux": st.max_rank[0], "max_trace": st.max_rank[1], "root_size": st.root_size,
+                      "leaf_mean": [st.level_mean_rank[st.depth][0], st.level_mean_rank[st.depth][1]]},
+            "roofline": roof,
+            "e2e": {"value": e2e_sec / world, "unit": "s", "h2d_bytes_per_step": 6 * 8 * c.n,
+                    "d2h_bytes_per_step": 16 * 2 * c.n},
+            "gpu_launches": int(r["launches"]),
+            "clocks": r["clocks"],
+        }
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(w, args.cpu_sample_boxes)
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+
+def cpu_baseline(w, sample_boxes: int):
+    """Time the FP64 oracle on a bounded sample of the workload and scale it to the whole job.
+
+    Sample: the leaf level of the oracle's compression and factorisation (M_R tiles, two column
+    IDs, diagonal-block LU, X = D^-1 R^T and Atilde) for `sample_boxes` of the leaf boxes; the
+    per-box time is multiplied by the number of leaf boxes.  Upper levels are not included, so
+    the value is a lower bound of the oracle's whole-job time.
+    """
+    import numpy as np
+    import scipy.linalg as sla
+
+    from oracle.hss import HSS, Options
+    from oracle.kernels import Params
+
+    prm = Params(w["k0"], w["k1"], w["eps0"], w["eps1"])
+    solver = HSS(w["curve"], prm, Options(leaf=w["leaf"], nproxy=w["nproxy"], tol=w["tol"]))
+    lev = solver.levels[-1]
+    for b in lev:
+        ids = np.arange(b.begin, b.end)
+        b.act = [ids, ids]
+        b.actrow = [ids, ids]
+    idx = np.linspace(0, len(lev) - 1, min(sample_boxes, len(lev))).astype(int)
+    t0 = time.perf_counter()
+    from oracle.hss import cpqr_id
+    for i in idx:
+        b = lev[i]
+        mr = solver.m_r(b, lev)
+        n0 = len(b.act[0])
+        b.rank, b.perm, b.T = [], [], []
+        for half in (mr[:, :n0], mr[:, n0:]):
+            r, p, t = cpqr_id(half, w["tol"])
+            b.rank.append(r)
+            b.perm.append(p)
+            b.T.append(t)
+        b.rrank, b.rperm, b.rT = b.rank, b.perm, b.T
+        d = solver._diag_block(b, solver.depth)
+        lu = sla.lu_factor(d)
+        rt = solver._basis(b, solver.depth, row=False)
+        x = sla.lu_solve(lu, rt)
+        np.linalg.inv(rt.T @ x)
+    dt = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": dt / len(idx) * len(lev), "unit": "s", "cores": cores, "kind": "oracle",
+            "sample": f"leaf level only: compress+factor of {len(idx)} of {len(lev)} leaf boxes "
+                      f"({dt:.1f} s), scaled by {len(lev)}/{len(idx)}; numpy/scipy FP64, BLAS threads = host cores"}
+
+
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return
+    w = _workload(args.workload)
+    for _ in range(args.warmup):
+        cpu_baseline(w, args.ref_sample_boxes)
+    vals = []
+    last = None
+    for _ in range(args.steps):
+        last = cpu_baseline(w, args.ref_sample_boxes)
+        vals.append(last["value"])
+    v = sum(vals) / len(vals)
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": v * 1000.0, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "complex128 (f64)", "data": "synthetic", "config": _config(w, "sym"),
+           "cpu_baseline": dict(last, value=v),
+           "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="star16k")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-boxes", type=int, default=16)
+    ap.add_argument("--ref-sample-boxes", type=int, default=4)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,228 @@
+/*
+ * symhss.h -- C ABI of the B300 (sm_103a) symmetric HSS direct solver for 2-D
+ * Helmholtz transmission scattering (symmetric Muller-like Nystrom system).
+ *
+ * Problem (Sec. 2): find the boundary flux q and trace u of the field scattered
+ * by a closed curve Gamma with wavenumber k0 / material constant eps0 outside
+ * and k1 / eps1 inside, for an incident plane wave.  The discrete system is the
+ * row-scaled symmetric Muller-like system (Eq. 15) on an equispaced-parameter
+ * trapezoidal Nystrom rule with a one-point corrected diagonal (Sec. 3.1).  It is
+ * compressed by the proxy method with one column interpolative decomposition per
+ * box and component, reused as the row basis because the matrix is complex
+ * symmetric (Sec. 4.1, Eq. low-rank_R), then factorised and solved by the
+ * multilevel compressed-equation (Martinsson-Rokhlin / HSS-ULV) scheme (Sec. 4.2).
+ * SYMHSS_NONSYM selects the non-symmetric baseline instead: the unscaled system of
+ * Sec. 6 (naive Muller-like) with separate row and column IDs (4 IDs per box).
+ *
+ * Conventions
+ *   - Complex numbers are complex128: two doubles (re, im), interleaved.
+ *   - Unknown / equation ordering at the boundary is [q_1..q_N, u_1..u_N] and
+ *     [eq1_1..eq1_N, eq2_1..eq2_N] (Eq. 15).
+ *   - Every call returns an int status: SYMHSS_OK (0) or a negative error code.
+ *     No call aborts the process, traps on the device or prints.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Calls that must read results back to the host synchronise that stream.
+ *   - All device memory the handle needs is allocated and owned by the handle and
+ *     released by symhss_destroy.  Caller buffers are never freed by the library.
+ */
+#ifndef SYMHSS_H
+#define SYMHSS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------- */
+#define SYMHSS_OK                  0
+#define SYMHSS_ERR_INVALID        -1  /* bad size, pointer, parameter, NaN/Inf input */
+#define SYMHSS_ERR_NOMEM          -2  /* device or pinned host allocation failed */
+#define SYMHSS_ERR_CUDA           -3  /* a CUDA runtime call or launch failed */
+#define SYMHSS_ERR_RANK_OVERFLOW  -4  /* an ID rank exceeded the preallocated capacity */
+#define SYMHSS_ERR_SINGULAR       -5  /* an exactly singular pivot in a block LU */
+#define SYMHSS_ERR_TIMEOUT        -6  /* a bounded device wait expired */
+#define SYMHSS_ERR_STATE          -7  /* calls out of order (e.g. factor before compress) */
+#define SYMHSS_ERR_DEVICE         -8  /* a kernel detected an out-of-range index and skipped it */
+
+/* ---- enums ---------------------------------------------------------------- */
+#define SYMHSS_SYM     0   /* symmetric single-ID compression, row-scaled system (Eq. 15) */
+#define SYMHSS_NONSYM  1   /* non-symmetric two-ID baseline, unscaled system (Sec. 6)    */
+
+#define SYMHSS_FP64    0   /* every stage in FP64 */
+
+#define SYMHSS_HOST    0   /* pointer location flags */
+#define SYMHSS_DEVICE  1
+
+typedef struct symhss_s* symhss_t;  /* opaque handle */
+
+/* Sampled curve (Sec. 3.1): nodes gamma(theta_j) at theta_j = 2 pi j / n,
+ * outward unit normals (pointing into the exterior Omega_0), trapezoidal
+ * weights w_j = |gamma'(theta_j)| 2 pi / n and signed curvature kappa_j (positive
+ * on a convex curve).  Equispaced parameters are required: the one-point
+ * corrected diagonal relies on them.  Arrays have n doubles each and live in
+ * host or device memory as `location` says; they are copied at create time. */
+typedef struct {
+  int n;
+  const double *x, *y, *nx, *ny, *w, *kappa;
+  int location;
+} symhss_curve;
+
+/* Solver parameters.  symhss_params_default fills the defaults shown. */
+typedef struct {
+  double k0, k1;          /* exterior / interior wavenumber (> 0)                   */
+  double eps0, eps1;      /* material constants (> 0); eps_i = (k_i/omega)^2 (Sec. 2) */
+  double tol;             /* relative ID tolerance |R_kk| <= tol |R_00|  (1e-10)      */
+  int leaf;               /* leaf box size in nodes (128)                             */
+  int nproxy;             /* minimum proxy points per ring (64)                       */
+  double proxy_factor;    /* proxy ring radius / box radius (1.5)                     */
+  int mode;               /* SYMHSS_SYM or SYMHSS_NONSYM                              */
+  int precision;          /* SYMHSS_FP64                                              */
+  int fixed_rank_kL;      /* > 0: fixed ranks k_l = ceil(a^(L-l) kL) (Sec. 4.3), 0: tol */
+  double rank_scale_a;    /* a of Sec. 4.3 (1.15)                                     */
+  int oversample;         /* sketch oversampling p (16); 0 disables the sketch        */
+  int reserved;
+  uint64_t seed;          /* seed of the counter-based sketch generator               */
+} symhss_params;
+
+/* Per-handle statistics of the last compress / factor / solve. */
+#define SYMHSS_MAX_LEVELS 32
+/* kernel classes of the per-class device timing in symhss_stats_t */
+#define SYMHSS_K_TILES  0   /* kernel-entry tile generator                       */
+#define SYMHSS_K_ID     1   /* pivoted-QR column ID                              */
+#define SYMHSS_K_GETRF  2   /* batched block LU                                  */
+#define SYMHSS_K_GETRS  3   /* batched triangular solves (X = D^-1 L, Atilde, g)  */
+#define SYMHSS_K_OTHER  4   /* bases, R X, small GEMMs, copies, gather / scatter  */
+#define SYMHSS_K_COUNT  8
+typedef struct {
+  int n;                          /* nodes                                    */
+  int depth;                      /* L: leaves are at level L, root at 0       */
+  int nboxes_leaf;
+  int root_size;                  /* order of the root diagonal block          */
+  int max_rank[2];                /* largest column-ID rank, flux / trace part */
+  int level_max_rank[SYMHSS_MAX_LEVELS][2];
+  double level_mean_rank[SYMHSS_MAX_LEVELS][2];
+  int level_nproxy[SYMHSS_MAX_LEVELS];  /* proxy points per ring (max over boxes) */
+  double ms_compress, ms_factor, ms_solve;  /* device time of the last call      */
+  double ms_tiles, ms_id, ms_lu, ms_basis;  /* device time split of compress+factor */
+  long long pairs_evaluated;      /* (point, point) kernel pairs of compress+factor */
+  long long id_count;             /* interpolative decompositions performed     */
+  double flops_lu;                /* real flops of block LU + solves in factor  */
+  double flops_id;                /* real flops of the pivoted QRs              */
+  long long device_bytes;         /* device memory held by the handle           */
+  /* per kernel class, accumulated over the last compress + factor + solve: device
+   * time from CUDA events recorded around each launch on the caller's stream,
+   * number of launches, and algorithmic real flops (tiles: (point, point) pairs) */
+  double kernel_ms[SYMHSS_K_COUNT];
+  long long kernel_launches[SYMHSS_K_COUNT];
+  double kernel_work[SYMHSS_K_COUNT];
+} symhss_stats_t;
+
+/* ---- handle lifecycle ------------------------------------------------------ */
+
+/* Fill `p` with the defaults above (k0 = k1 = 1, eps0 = eps1 = 1). */
+int symhss_params_default(symhss_params* p);
+
+/* Create a solver for `curve` with parameters `prm`.  Validates every input
+ * (n >= 2, positive wavenumbers, material constants, weights; finite
+ * coordinates; 1 <= leaf; nproxy >= 8; proxy_factor > 1; tol >= 0), copies the
+ * curve, builds the box tree and proxy rings, and uploads them on `stream`.
+ * On success *out owns all library allocations. */
+int symhss_create(const symhss_curve* curve, const symhss_params* prm, void* stream, symhss_t* out);
+
+/* Replace the node arrays by a new curve with the same n (same tree shape).
+ * Invalidates any previous compression. */
+int symhss_set_curve(symhss_t h, const symhss_curve* curve, void* stream);
+
+/* Proxy-method compression of every level (Sec. 4.1): kernel tiles M_R, one
+ * column ID per box and component (two more row IDs of M_L per box with
+ * SYMHSS_NONSYM).  Synchronises `stream` once per level to read ranks. */
+int symhss_compress(symhss_t h, void* stream);
+
+/* Multilevel factorisation (Sec. 4.2): block LU of every diagonal block,
+ * X = D^{-1} L, Atilde = (R X)^{-1}, parent blocks, root LU.  Requires compress. */
+int symhss_factor(symhss_t h, void* stream);
+
+/* Right-hand side of the handle's system for the plane wave
+ * u_in = exp(i k0 (x cos(angle) + y sin(angle))): [-eps0 W u_in ; W du_in/dnu]
+ * (Eq. 15; the unscaled form without W for SYMHSS_NONSYM).  rhs: device
+ * complex128[2n]. */
+int symhss_rhs_plane_wave(symhss_t h, double angle, void* rhs, void* stream);
+
+/* Solve A x = rhs for `nrhs` right-hand sides (Sec. 4.2).  rhs, x: device
+ * complex128[2n * nrhs], column j at offset 2n*j; rhs is not modified; rhs and x
+ * may not overlap.  Requires factor. */
+int symhss_solve(symhss_t h, const void* rhs, void* x, int nrhs, void* stream);
+
+/* As symhss_solve with host buffers: copies rhs in and x out inside the call. */
+int symhss_solve_host(symhss_t h, const void* rhs_host, void* x_host, int nrhs, void* stream);
+
+/* Statistics of the last phases (device-synchronising). */
+int symhss_stats(symhss_t h, symhss_stats_t* out);
+
+/* Column-ID ranks of level `level` (1..depth): out[2*b + h] for box b and part h.
+ * `out` is a host int array of 2 * 2^level entries. */
+int symhss_level_ranks(symhss_t h, int level, int* out);
+
+/* Release everything the handle owns.  NULL is accepted. */
+int symhss_destroy(symhss_t h);
+
+/* Static message for a status code. */
+const char* symhss_strerror(int status);
+
+/* ---- building blocks (device pointers; used by the solver, exposed for tests) ---- */
+
+/* H_0^(1)(x_i) and H_1^(1)(x_i) (Sec. 3.1: G_k = (i/4) H_0(k r)) for n device doubles
+ * x_i > 0, written to out (device complex128[2n]): H_0 values, then H_1 values.
+ * The evaluator the tile generator uses (power series, Miller's recurrence,
+ * Hankel's expansion; about 1e-15 relative accuracy). */
+int symhss_hankel01(const double* x, int n, void* out, void* stream);
+
+/* A set of points for symhss_kernel_block: coordinates, unit normals, weights,
+ * curvature and an id; two points with the same id >= 0 are the same curve
+ * node and receive the corrected diagonal (Sec. 3.1) and the free terms (Eq. 15).
+ * All arrays are device arrays of n entries. */
+typedef struct {
+  int n;
+  const double *x, *y, *nx, *ny, *w, *kappa;
+  const int* id;
+} symhss_points;
+
+/* Tile generator: out[i + j*ld] = A[(obs_i, obs_eq[i]), (src_j, src_comp[j])]
+ * with eq/comp in {0, 1} (0: first equation / flux unknown q, 1: second
+ * equation / trace unknown u).  `scaled` = 1 gives the row-scaled symmetric
+ * matrix (Eq. 15), 0 the unscaled baseline (Sec. 6).  out: device complex128,
+ * column-major, ld >= obs->n. */
+int symhss_kernel_block(const symhss_params* prm, const symhss_points* obs, const int* obs_eq,
+                        const symhss_points* src, const int* src_comp, int scaled,
+                        void* out, int ld, void* stream);
+
+/* Batched column interpolative decomposition (Sec. 4.1) by Householder QR with
+ * column pivoting: for each of `batch` matrices M_b = A + b*strideA (m x n,
+ * column-major, leading dimension lda, complex128, OVERWRITTEN), find rank r_b,
+ * a permutation perm_b (n ints at perm + b*n) and T_b = R11^{-1} R12 (r_b x (n-r_b),
+ * column-major with leading dimension r_b, at T + b*strideT complex128 entries;
+ * strideT >= floor(n/2)*ceil(n/2) always suffices) with
+ * M_b[:, perm_b] ~= M_b[:, perm_b[:r_b]] [I T_b].
+ * fixed_rank < 0: stop at the first |R_kk| <= tol |R_00|; else exactly
+ * min(fixed_rank, m, n) steps.  rank: device int[batch]. */
+int symhss_column_id(void* A, int m, int n, int lda, long long strideA, int batch, double tol,
+                     int fixed_rank, int* rank, int* perm, void* T, long long strideT, void* stream);
+
+/* Batched LU with partial pivoting of n x n complex128 matrices A + b*strideA
+ * (leading dimension lda; overwritten by L\U), pivots ipiv + b*n (0-based row
+ * swapped with row k at step k), info[b] = 0 or k+1 for the first zero pivot. */
+int symhss_lu_batched(void* A, int n, int lda, long long strideA, int batch, int* ipiv,
+                      int* info, void* stream);
+
+/* Solve with the factors of symhss_lu_batched: B_b <- A_b^{-1} B_b for nrhs
+ * columns (leading dimension ldb, stride strideB). */
+int symhss_lu_solve_batched(const void* LU, int n, int lda, long long strideA, const int* ipiv,
+                            void* B, int nrhs, int ldb, long long strideB, int batch, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SYMHSS_H */

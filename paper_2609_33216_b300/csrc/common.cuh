@@ -1,0 +1,258 @@
+// Shared device helpers of the symhss library: complex128 arithmetic on double2,
+// block reductions, job descriptors and launcher declarations.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/symhss.h"
+
+namespace symhss {
+
+// ---- complex128 on double2 (x = re, y = im) ---------------------------------
+
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+__device__ __forceinline__ double2 cmulc(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -a.x * b.y));
+}
+// conj(a) * b
+__device__ __forceinline__ double2 cconjmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.x, b.y, -a.y * b.x));
+}
+// acc += a * b
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 acc) {
+  return make_double2(fma(a.x, b.x, fma(-a.y, b.y, acc.x)), fma(a.x, b.y, fma(a.y, b.x, acc.y)));
+}
+// acc -= a * b
+__device__ __forceinline__ double2 cfms(double2 a, double2 b, double2 acc) {
+  return make_double2(fma(-a.x, b.x, fma(a.y, b.y, acc.x)), fma(-a.x, b.y, fma(-a.y, b.x, acc.y)));
+}
+__device__ __forceinline__ double cabs2(double2 a) { return fma(a.x, a.x, a.y * a.y); }
+__device__ __forceinline__ double cabs1(double2 a) { return fabs(a.x) + fabs(a.y); }
+__device__ __forceinline__ double2 cinv(double2 a) {
+  // 1/a with scaling against overflow (Smith's method)
+  if (fabs(a.x) >= fabs(a.y)) {
+    double r = a.y / a.x, d = a.x + a.y * r;
+    return make_double2(1.0 / d, -r / d);
+  } else {
+    double r = a.x / a.y, d = a.y + a.x * r;
+    return make_double2(r / d, -1.0 / d);
+  }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double2 warp_csum(double2 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+// argmax over (value, index) with ties to the lowest index
+__device__ __forceinline__ void warp_argmax(double& v, int& i) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    double ov = __shfl_xor_sync(0xffffffffu, v, o);
+    int oi = __shfl_xor_sync(0xffffffffu, i, o);
+    if (ov > v || (ov == v && oi < i)) { v = ov; i = oi; }
+  }
+}
+
+// device status bits (OR-ed into a device word the host reads at sync points)
+enum : int {
+  ST_BAD_INDEX = 1,
+  ST_RANK_OVERFLOW = 2,
+  ST_SINGULAR = 4,
+  ST_SMEM = 8,
+};
+
+// ---- tile generator ---------------------------------------------------------
+
+// Point table (structure of arrays).  id >= 0 marks a curve node.
+struct PointTable {
+  const double *x, *y, *nx, *ny, *w, *kappa;
+  const int* id;
+};
+
+// Physical constants of one system.
+struct KernelParams {
+  double k0, k1, eps0, eps1;
+  double e0sq, e1sq;   // eps0^2, eps1^2
+  double half_ft;      // (eps0 + eps1) / 2
+};
+
+// A tile: "thread points" (one per thread) x "loop points" (staged in shared
+// memory).  Each point carries two output slots (-1 = absent): for observation
+// points the rows of equation 1 and 2, for source points the columns of the
+// flux and trace unknowns.  Element (thread slot s, loop slot t) is written to
+// out[out_off + s + t * ld].
+struct TileJob {
+  int tp_off, n_tp;        // thread points: [tp_off, tp_off + n_tp) of the thread lists
+  int lp_off, n_lp;        // loop points
+  long long out_off;
+  int ld;
+  int flags;               // TILE_SRC_IS_THREAD: thread points are sources (transposed output)
+                           // TILE_UNSCALED: the baseline system of Sec. 6
+};
+enum : int { TILE_SRC_IS_THREAD = 1, TILE_UNSCALED = 2 };
+
+struct TileChunk { int job, t0, l0; };
+
+struct TileLaunch {
+  PointTable tpts, lpts;   // tables the thread / loop point indices refer to
+  const int *tp_pt, *tp_s0, *tp_s1;
+  const int *lp_pt, *lp_s0, *lp_s1;
+  const TileJob* jobs;
+  const TileChunk* chunks;
+  int nchunks;
+  double2* out;
+  int* status;
+  KernelParams kp;
+};
+
+constexpr int TILE_T = 128;   // thread points per chunk (= threads per block)
+constexpr int TILE_L = 32;    // loop points per chunk
+
+cudaError_t launch_tiles(const TileLaunch& a, cudaStream_t s);
+cudaError_t launch_hankel(const double* x, int n, double2* out, cudaStream_t s);
+
+// ---- column ID (pivoted QR) ---------------------------------------------------
+
+struct IdJob {
+  long long m_off;   // M at mats + m_off (column-major, leading dim ld)
+  int m, n, ld;
+  int start;         // first QR step (0 = fresh; > 0 continues a previous run)
+  int fixed;         // < 0: tolerance stop; else stop after `fixed` steps
+  long long t_off;   // T output at tbuf + t_off (leading dim = rank)
+  long long perm_off;
+  int out_idx;       // rank[out_idx], ref[out_idx]
+};
+
+struct IdLaunch {
+  double2* mats;
+  double2* tbuf;
+  int* perm;
+  int* rank;
+  double* ref;       // |R_00| of each job (kept for continuation runs)
+  const IdJob* jobs;
+  int njobs;
+  double tol;
+  int* status;
+  int max_m, max_n;
+};
+cudaError_t launch_cpqr(const IdLaunch& a, cudaStream_t s);
+
+// ---- batched LU and solves -----------------------------------------------------
+
+struct LuJob {
+  long long a_off;  // matrix at base + a_off
+  int n, ld;
+  long long piv_off;
+  int info_idx;
+};
+struct LuLaunch {
+  double2* base;
+  int* piv;
+  int* info;
+  const LuJob* jobs;
+  int njobs;
+  int max_n;
+  int* status;
+};
+cudaError_t launch_getrf(const LuLaunch& a, cudaStream_t s);
+
+struct RsJob {
+  long long a_off; int n, lda; long long piv_off;
+  long long b_off; int ldb; int nrhs;
+};
+struct RsLaunch {
+  const double2* abase;
+  const int* piv;
+  double2* bbase;
+  const RsJob* jobs;
+  int njobs;
+  int max_rhs;
+  int max_n;
+};
+cudaError_t launch_getrs(const RsLaunch& a, cudaStream_t s);
+
+// ---- factor / solve helpers ------------------------------------------------------
+
+// Interpolation basis of one box in its diagonal-block ordering (Sec. 4.1): for
+// part h (flux / trace), q[c] (c < n_h) is the diagonal-block position of the c-th
+// pivoted active unknown; the first r_h are the skeleton.  T is r_h x (n_h - r_h)
+// with leading dimension r_h, and R^h = [I T] Pi^T.
+struct BasisPart {
+  long long q_off;   // into the int buffer
+  long long t_off;   // into the T buffer
+  int n, r;
+  int col0;          // first row/column of this part among the box's k = r_0 + r_1
+};
+struct BasisJob {
+  BasisPart part[2];
+  int size;          // diagonal-block order
+  int k;             // r_0 + r_1
+  long long in_off;  // input (size x ncols, leading dim ld_in)   [apply_r]
+  int ld_in;
+  long long out_off; // output: dense basis (size x k, leading dim size) [basis_dense]
+  int ld_out;        //         or R * input (k x ncols, leading dim ld_out) [apply_r]
+  int ncols;
+};
+struct BasisLaunch {
+  const int* q;
+  const double2* T;
+  const double2* in;
+  double2* out;
+  const BasisJob* jobs;
+  int njobs;
+  int max_cols;
+};
+// out = dense R^T (equivalently L for a row basis): 1 at skeleton rows, T^T below
+cudaError_t launch_basis_dense(const BasisLaunch& a, cudaStream_t s);
+// out = R * in
+cudaError_t launch_apply_r(const BasisLaunch& a, cudaStream_t s);
+
+// C = alpha * A * B + beta * C for batches of small complex matrices (alpha, beta real)
+struct GemmJob {
+  long long a_off, b_off, c_off;
+  int lda, ldb, ldc;
+  int m, n, k;
+  double alpha, beta;
+};
+struct GemmLaunch {
+  const double2* A;
+  const double2* B;
+  double2* C;
+  const GemmJob* jobs;
+  int njobs;
+};
+cudaError_t launch_gemm(const GemmLaunch& a, cudaStream_t s);
+
+// dst block (rows x cols, ldd) = src block (lds); identity fill when src_off < 0
+struct CopyJob { long long src_off, dst_off; int rows, cols, lds, ldd; };
+cudaError_t launch_copy_blocks(const double2* src, double2* dst, const CopyJob* jobs, int njobs,
+                               cudaStream_t s);
+
+// Leaf boxes are contiguous node ranges [begin, begin + len); their vectors hold
+// [eq1 rows; eq2 rows] of the box (size 2 len) with nrhs columns.
+struct LeafJob { long long off; int begin, len; };
+cudaError_t launch_leaf_gather(const double2* f, int ldf, double2* g, const LeafJob* jobs, int njobs,
+                               int nrhs, int n, cudaStream_t s);
+cudaError_t launch_leaf_scatter(const double2* g, double2* x, int ldx, const LeafJob* jobs,
+                                int njobs, int nrhs, int n, cudaStream_t s);
+
+cudaError_t launch_plane_wave(const double* x, const double* y, const double* nx, const double* ny,
+                              const double* w, int n, double k0, double eps0, double angle,
+                              int scaled, double2* rhs, cudaStream_t s);
+
+}  // namespace symhss

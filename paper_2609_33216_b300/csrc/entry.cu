@@ -1,0 +1,228 @@
+// Stand-alone building-block entry points of the C ABI (include/symhss.h):
+// the tile generator on explicit point sets, the batched column ID and the
+// batched LU / solve.  They validate their arguments, allocate the small job
+// arrays they need, launch the same kernels the solver uses, and synchronise
+// the stream before returning.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace symhss;
+
+namespace {
+
+struct TmpBuf {
+  void* p = nullptr;
+  ~TmpBuf() { if (p) cudaFree(p); }
+  cudaError_t alloc(size_t b) { return cudaMalloc(&p, b ? b : 16); }
+};
+
+int cerr(cudaError_t e) { return e == cudaErrorMemoryAllocation ? SYMHSS_ERR_NOMEM : SYMHSS_ERR_CUDA; }
+
+#define CKE(call)                                  \
+  do {                                             \
+    cudaError_t _e = (call);                       \
+    if (_e != cudaSuccess) return cerr(_e);        \
+  } while (0)
+
+int status_code(int st) {
+  if (st & ST_BAD_INDEX) return SYMHSS_ERR_DEVICE;
+  if (st & ST_SINGULAR) return SYMHSS_ERR_SINGULAR;
+  if (st) return SYMHSS_ERR_DEVICE;
+  return SYMHSS_OK;
+}
+
+bool points_ok(const symhss_points* p) {
+  return p && p->n >= 0 && (p->n == 0 || (p->x && p->y && p->nx && p->ny && p->w && p->kappa && p->id));
+}
+
+}  // namespace
+
+extern "C" {
+
+int symhss_hankel01(const double* x, int n, void* out, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !out))) return SYMHSS_ERR_INVALID;
+  if (n == 0) return SYMHSS_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  CKE(launch_hankel(x, n, reinterpret_cast<double2*>(out), s));
+  CKE(cudaStreamSynchronize(s));
+  return SYMHSS_OK;
+}
+
+int symhss_kernel_block(const symhss_params* prm, const symhss_points* obs, const int* obs_eq,
+                        const symhss_points* src, const int* src_comp, int scaled, void* out, int ld,
+                        void* stream) {
+  if (!prm || !points_ok(obs) || !points_ok(src) || !out) return SYMHSS_ERR_INVALID;
+  if (!(prm->k0 > 0) || !(prm->k1 > 0) || !std::isfinite(prm->eps0) || !std::isfinite(prm->eps1))
+    return SYMHSS_ERR_INVALID;
+  if (ld < obs->n || ld < 1) return SYMHSS_ERR_INVALID;
+  if ((obs->n > 0 && !obs_eq) || (src->n > 0 && !src_comp)) return SYMHSS_ERR_INVALID;
+  if (obs->n == 0 || src->n == 0) return SYMHSS_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int m = obs->n, n = src->n;
+  // equation / component labels live on the device: fetch them to build the slot lists
+  std::vector<int> eq(m), comp(n);
+  CKE(cudaMemcpyAsync(eq.data(), obs_eq, m * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CKE(cudaMemcpyAsync(comp.data(), src_comp, n * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CKE(cudaStreamSynchronize(s));
+  std::vector<int> tp(m), ts0(m), ts1(m), lp(n), ls0(n), ls1(n);
+  for (int i = 0; i < m; ++i) {
+    if (eq[i] != 0 && eq[i] != 1) return SYMHSS_ERR_INVALID;
+    tp[i] = i; ts0[i] = eq[i] == 0 ? i : -1; ts1[i] = eq[i] == 1 ? i : -1;
+  }
+  for (int j = 0; j < n; ++j) {
+    if (comp[j] != 0 && comp[j] != 1) return SYMHSS_ERR_INVALID;
+    lp[j] = j; ls0[j] = comp[j] == 0 ? j : -1; ls1[j] = comp[j] == 1 ? j : -1;
+  }
+  TileJob jb;
+  jb.tp_off = 0; jb.n_tp = m; jb.lp_off = 0; jb.n_lp = n; jb.out_off = 0; jb.ld = ld;
+  jb.flags = scaled ? 0 : TILE_UNSCALED;
+  std::vector<TileChunk> ch;
+  for (int a = 0; a < m; a += TILE_T)
+    for (int b = 0; b < n; b += TILE_L) ch.push_back(TileChunk{0, a, b});
+  const size_t ints = 3 * (size_t)m + 3 * (size_t)n;
+  TmpBuf buf;
+  const size_t bytes = ints * sizeof(int) + sizeof(TileJob) + ch.size() * sizeof(TileChunk) + sizeof(int) + 64;
+  CKE(buf.alloc(bytes));
+  std::vector<char> host(bytes, 0);
+  char* hp = host.data();
+  size_t off = 0;
+  auto put = [&](const void* src_, size_t b) { std::memcpy(hp + off, src_, b); size_t o = off; off += b; return o; };
+  const size_t o1 = put(tp.data(), m * 4), o2 = put(ts0.data(), m * 4), o3 = put(ts1.data(), m * 4);
+  const size_t o4 = put(lp.data(), n * 4), o5 = put(ls0.data(), n * 4), o6 = put(ls1.data(), n * 4);
+  off = (off + 15) & ~size_t(15);
+  const size_t o7 = put(&jb, sizeof(jb));
+  const size_t o8 = put(ch.data(), ch.size() * sizeof(TileChunk));
+  const size_t o9 = off;
+  CKE(cudaMemcpyAsync(buf.p, hp, bytes, cudaMemcpyHostToDevice, s));
+  char* d = reinterpret_cast<char*>(buf.p);
+  TileLaunch a;
+  a.tpts = PointTable{obs->x, obs->y, obs->nx, obs->ny, obs->w, obs->kappa, obs->id};
+  a.lpts = PointTable{src->x, src->y, src->nx, src->ny, src->w, src->kappa, src->id};
+  a.tp_pt = reinterpret_cast<const int*>(d + o1);
+  a.tp_s0 = reinterpret_cast<const int*>(d + o2);
+  a.tp_s1 = reinterpret_cast<const int*>(d + o3);
+  a.lp_pt = reinterpret_cast<const int*>(d + o4);
+  a.lp_s0 = reinterpret_cast<const int*>(d + o5);
+  a.lp_s1 = reinterpret_cast<const int*>(d + o6);
+  a.jobs = reinterpret_cast<const TileJob*>(d + o7);
+  a.chunks = reinterpret_cast<const TileChunk*>(d + o8);
+  a.nchunks = (int)ch.size();
+  a.out = reinterpret_cast<double2*>(out);
+  a.status = reinterpret_cast<int*>(d + o9);
+  a.kp.k0 = prm->k0; a.kp.k1 = prm->k1; a.kp.eps0 = prm->eps0; a.kp.eps1 = prm->eps1;
+  a.kp.e0sq = prm->eps0 * prm->eps0; a.kp.e1sq = prm->eps1 * prm->eps1;
+  a.kp.half_ft = 0.5 * (prm->eps0 + prm->eps1);
+  CKE(launch_tiles(a, s));
+  int st = 0;
+  CKE(cudaMemcpyAsync(&st, a.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CKE(cudaStreamSynchronize(s));
+  return status_code(st);
+}
+
+int symhss_column_id(void* A, int m, int n, int lda, long long strideA, int batch, double tol, int fixed_rank,
+                     int* rank, int* perm, void* T, long long strideT, void* stream) {
+  if (batch < 0 || m < 0 || n < 0 || lda < m || lda < 1 || !(tol >= 0) || !std::isfinite(tol))
+    return SYMHSS_ERR_INVALID;
+  if (batch == 0) return SYMHSS_OK;
+  if (!A || !rank || !perm || !T) return SYMHSS_ERR_INVALID;
+  if (strideA < (long long)lda * n || strideT < (long long)(n / 2) * ((n + 1) / 2)) return SYMHSS_ERR_INVALID;
+  const size_t smem = (size_t)m * 16 + (size_t)n * 12;
+  if (smem > 220 * 1024) return SYMHSS_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<IdJob> jobs(batch);
+  for (int b = 0; b < batch; ++b) {
+    IdJob& j = jobs[b];
+    j.m_off = strideA * b; j.m = m; j.n = n; j.ld = lda; j.start = 0; j.fixed = fixed_rank < 0 ? -1 : fixed_rank;
+    j.t_off = strideT * b; j.perm_off = (long long)n * b; j.out_idx = b;
+  }
+  TmpBuf buf;
+  const size_t bytes = jobs.size() * sizeof(IdJob) + batch * sizeof(double) + 64;
+  CKE(buf.alloc(bytes));
+  CKE(cudaMemcpyAsync(buf.p, jobs.data(), jobs.size() * sizeof(IdJob), cudaMemcpyHostToDevice, s));
+  char* d = reinterpret_cast<char*>(buf.p);
+  double* ref = reinterpret_cast<double*>(d + ((jobs.size() * sizeof(IdJob) + 15) & ~size_t(15)));
+  int* status = reinterpret_cast<int*>(ref + batch);
+  CKE(cudaMemsetAsync(status, 0, sizeof(int), s));
+  IdLaunch a;
+  a.mats = reinterpret_cast<double2*>(A);
+  a.tbuf = reinterpret_cast<double2*>(T);
+  a.perm = perm;
+  a.rank = rank;
+  a.ref = ref;
+  a.jobs = reinterpret_cast<const IdJob*>(d);
+  a.njobs = batch;
+  a.tol = tol;
+  a.status = status;
+  a.max_m = m > 0 ? m : 1;
+  a.max_n = n > 0 ? n : 1;
+  CKE(launch_cpqr(a, s));
+  int st = 0;
+  CKE(cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CKE(cudaStreamSynchronize(s));
+  return status_code(st);
+}
+
+int symhss_lu_batched(void* A, int n, int lda, long long strideA, int batch, int* ipiv, int* info, void* stream) {
+  if (batch < 0 || n < 0 || lda < n || lda < 1) return SYMHSS_ERR_INVALID;
+  if (batch == 0 || n == 0) return SYMHSS_OK;
+  if (!A || !ipiv || !info || strideA < (long long)lda * n) return SYMHSS_ERR_INVALID;
+  if (2 * (size_t)n * 16 > 220 * 1024) return SYMHSS_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<LuJob> jobs(batch);
+  for (int b = 0; b < batch; ++b) {
+    jobs[b].a_off = strideA * b; jobs[b].n = n; jobs[b].ld = lda; jobs[b].piv_off = (long long)n * b;
+    jobs[b].info_idx = b;
+  }
+  TmpBuf buf;
+  CKE(buf.alloc(jobs.size() * sizeof(LuJob) + 64));
+  CKE(cudaMemcpyAsync(buf.p, jobs.data(), jobs.size() * sizeof(LuJob), cudaMemcpyHostToDevice, s));
+  int* status = reinterpret_cast<int*>(reinterpret_cast<char*>(buf.p) + ((jobs.size() * sizeof(LuJob) + 15) & ~size_t(15)));
+  CKE(cudaMemsetAsync(status, 0, sizeof(int), s));
+  LuLaunch a;
+  a.base = reinterpret_cast<double2*>(A);
+  a.piv = ipiv;
+  a.info = info;
+  a.jobs = reinterpret_cast<const LuJob*>(buf.p);
+  a.njobs = batch;
+  a.max_n = n;
+  a.status = status;
+  CKE(launch_getrf(a, s));
+  int st = 0;
+  CKE(cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CKE(cudaStreamSynchronize(s));
+  return (st & ST_BAD_INDEX) ? SYMHSS_ERR_DEVICE : SYMHSS_OK;  // singular blocks are reported in info
+}
+
+int symhss_lu_solve_batched(const void* LU, int n, int lda, long long strideA, const int* ipiv, void* B, int nrhs,
+                            int ldb, long long strideB, int batch, void* stream) {
+  if (batch < 0 || n < 0 || nrhs < 0 || lda < n || ldb < n || lda < 1 || ldb < 1) return SYMHSS_ERR_INVALID;
+  if (batch == 0 || n == 0 || nrhs == 0) return SYMHSS_OK;
+  if (!LU || !ipiv || !B || strideA < (long long)lda * n || strideB < (long long)ldb * nrhs)
+    return SYMHSS_ERR_INVALID;
+  if ((size_t)n * 4 + 16 + (size_t)4 * n * 16 > 220 * 1024) return SYMHSS_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<RsJob> jobs(batch);
+  for (int b = 0; b < batch; ++b) {
+    jobs[b].a_off = strideA * b; jobs[b].n = n; jobs[b].lda = lda; jobs[b].piv_off = (long long)n * b;
+    jobs[b].b_off = strideB * b; jobs[b].ldb = ldb; jobs[b].nrhs = nrhs;
+  }
+  TmpBuf buf;
+  CKE(buf.alloc(jobs.size() * sizeof(RsJob)));
+  CKE(cudaMemcpyAsync(buf.p, jobs.data(), jobs.size() * sizeof(RsJob), cudaMemcpyHostToDevice, s));
+  RsLaunch a;
+  a.abase = reinterpret_cast<const double2*>(LU);
+  a.piv = ipiv;
+  a.bbase = reinterpret_cast<double2*>(B);
+  a.jobs = reinterpret_cast<const RsJob*>(buf.p);
+  a.njobs = batch;
+  a.max_rhs = nrhs;
+  a.max_n = n;
+  CKE(launch_getrs(a, s));
+  CKE(cudaStreamSynchronize(s));
+  return SYMHSS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,197 @@
+// Small batched operations of the factorisation and solve (Sec. 4.2):
+// interpolation bases, R * X, small GEMMs (Atilde R g, f~ - Atilde y, g - X z),
+// block copies (parent diagonal-block assembly), leaf gather / scatter and the
+// plane-wave right-hand side.
+#include "common.cuh"
+
+namespace symhss {
+
+namespace {
+
+constexpr int kOpsThreads = 256;
+
+// dense R^T in the diagonal-block ordering: column col0 + j holds 1 at q[j] and
+// T[j, i] at q[r + i]
+__global__ void __launch_bounds__(kOpsThreads) basis_dense_kernel(const BasisLaunch a) {
+  const BasisJob jb = a.jobs[blockIdx.x];
+  double2* out = a.out + jb.out_off;
+  const long long total = (long long)jb.size * jb.k;
+  for (long long e = threadIdx.x; e < total; e += blockDim.x) out[e] = make_double2(0.0, 0.0);
+  __syncthreads();
+  for (int h = 0; h < 2; ++h) {
+    const BasisPart pt = jb.part[h];
+    const int* q = a.q + pt.q_off;
+    const double2* T = a.T + pt.t_off;
+    const int nr = pt.n - pt.r;
+    const long long cnt = (long long)pt.r * (nr + 1);
+    for (long long e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const int j = (int)(e % pt.r);
+      const int i = (int)(e / pt.r);  // 0: skeleton entry, 1..nr: T row
+      const int col = pt.col0 + j;
+      if (i == 0) out[q[j] + (long long)col * jb.size] = make_double2(1.0, 0.0);
+      else out[q[pt.r + i - 1] + (long long)col * jb.size] = T[j + (long long)(i - 1) * pt.r];
+    }
+  }
+}
+
+// out[col0 + j, c] = in[q[j], c] + sum_i T[j, i] in[q[r + i], c]
+__global__ void __launch_bounds__(kOpsThreads) apply_r_kernel(const BasisLaunch a) {
+  const BasisJob jb = a.jobs[blockIdx.x];
+  const double2* in = a.in + jb.in_off;
+  double2* out = a.out + jb.out_off;
+  for (int h = 0; h < 2; ++h) {
+    const BasisPart pt = jb.part[h];
+    const int* q = a.q + pt.q_off;
+    const double2* T = a.T + pt.t_off;
+    const int nr = pt.n - pt.r;
+    const long long cnt = (long long)pt.r * jb.ncols;
+    for (long long e = threadIdx.x + (long long)blockIdx.y * blockDim.x; e < cnt;
+         e += (long long)blockDim.x * gridDim.y) {
+      const int j = (int)(e % pt.r);
+      const int c = (int)(e / pt.r);
+      const double2* ic = in + (long long)c * jb.ld_in;
+      double2 s = ic[q[j]];
+      for (int i = 0; i < nr; ++i) s = cfma(T[j + (long long)i * pt.r], ic[q[pt.r + i]], s);
+      out[pt.col0 + j + (long long)c * jb.ld_out] = s;
+    }
+  }
+}
+
+// C = alpha A B + beta C; a 2-D grid of 16x16 output tiles per job
+__global__ void __launch_bounds__(256) gemm_kernel(const GemmLaunch a) {
+  __shared__ double2 as[16][17];
+  __shared__ double2 bs[16][17];
+  const GemmJob jb = a.jobs[blockIdx.x];
+  const int tiles_m = (jb.m + 15) / 16, tiles_n = (jb.n + 15) / 16;
+  const double2* A = a.A + jb.a_off;
+  const double2* B = a.B + jb.b_off;
+  double2* C = a.C + jb.c_off;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  for (int tile = blockIdx.y; tile < tiles_m * tiles_n; tile += gridDim.y) {
+    const int i0 = (tile % tiles_m) * 16, j0 = (tile / tiles_m) * 16;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int l0 = 0; l0 < jb.k; l0 += 16) {
+      const int ai = i0 + tx, al = l0 + ty;
+      as[ty][tx] = (ai < jb.m && al < jb.k) ? A[ai + (long long)al * jb.lda] : make_double2(0.0, 0.0);
+      const int bl = l0 + tx, bj = j0 + ty;
+      bs[ty][tx] = (bl < jb.k && bj < jb.n) ? B[bl + (long long)bj * jb.ldb] : make_double2(0.0, 0.0);
+      __syncthreads();
+#pragma unroll
+      for (int l = 0; l < 16; ++l) acc = cfma(as[l][tx], bs[ty][l], acc);
+      __syncthreads();
+    }
+    const int i = i0 + tx, j = j0 + ty;
+    if (i < jb.m && j < jb.n) {
+      double2* c = C + i + (long long)j * jb.ldc;
+      double2 v = make_double2(jb.alpha * acc.x, jb.alpha * acc.y);
+      if (jb.beta != 0.0) v = make_double2(v.x + jb.beta * c->x, v.y + jb.beta * c->y);
+      *c = v;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kOpsThreads) copy_kernel(const double2* src, double2* dst,
+                                                           const CopyJob* jobs) {
+  const CopyJob jb = jobs[blockIdx.x];
+  const long long total = (long long)jb.rows * jb.cols;
+  for (long long e = threadIdx.x + (long long)blockIdx.y * blockDim.x; e < total;
+       e += (long long)blockDim.x * gridDim.y) {
+    const int i = (int)(e % jb.rows), j = (int)(e / jb.rows);
+    double2 v;
+    if (jb.src_off >= 0) v = src[jb.src_off + i + (long long)j * jb.lds];
+    else v = make_double2(i == j ? 1.0 : 0.0, 0.0);
+    dst[jb.dst_off + i + (long long)j * jb.ldd] = v;
+  }
+}
+
+__global__ void __launch_bounds__(kOpsThreads) leaf_gather_kernel(const double2* f, int ldf, double2* g,
+                                                                  const LeafJob* jobs, int nrhs, int n) {
+  const LeafJob jb = jobs[blockIdx.x];
+  const int size = 2 * jb.len;
+  for (int e = threadIdx.x; e < size * nrhs; e += blockDim.x) {
+    const int i = e % size, c = e / size;
+    const int src = i < jb.len ? jb.begin + i : n + jb.begin + (i - jb.len);
+    g[jb.off + i + (long long)c * size] = f[src + (long long)c * ldf];
+  }
+}
+
+__global__ void __launch_bounds__(kOpsThreads) leaf_scatter_kernel(const double2* g, double2* x, int ldx,
+                                                                   const LeafJob* jobs, int nrhs, int n) {
+  const LeafJob jb = jobs[blockIdx.x];
+  const int size = 2 * jb.len;
+  for (int e = threadIdx.x; e < size * nrhs; e += blockDim.x) {
+    const int i = e % size, c = e / size;
+    const int dst = i < jb.len ? jb.begin + i : n + jb.begin + (i - jb.len);
+    x[dst + (long long)c * ldx] = g[jb.off + i + (long long)c * size];
+  }
+}
+
+__global__ void plane_wave_kernel(const double* x, const double* y, const double* nx, const double* ny,
+                                  const double* w, int n, double k0, double eps0, double ca, double sa,
+                                  int scaled, double2* rhs) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double sn, cs;
+  sincos(k0 * (x[i] * ca + y[i] * sa), &sn, &cs);
+  const double2 uin = make_double2(cs, sn);
+  const double dn = k0 * (nx[i] * ca + ny[i] * sa);
+  const double2 dudn = make_double2(-dn * sn, dn * cs);  // i k0 (nu.dir) u_in
+  const double sc = scaled ? w[i] : 1.0;
+  rhs[i] = make_double2(-eps0 * sc * uin.x, -eps0 * sc * uin.y);
+  rhs[n + i] = make_double2(sc * dudn.x, sc * dudn.y);
+}
+
+}  // namespace
+
+cudaError_t launch_basis_dense(const BasisLaunch& a, cudaStream_t s) {
+  if (a.njobs <= 0) return cudaSuccess;
+  basis_dense_kernel<<<a.njobs, kOpsThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_r(const BasisLaunch& a, cudaStream_t s) {
+  if (a.njobs <= 0) return cudaSuccess;
+  dim3 grid(a.njobs, 4);
+  apply_r_kernel<<<grid, kOpsThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm(const GemmLaunch& a, cudaStream_t s) {
+  if (a.njobs <= 0) return cudaSuccess;
+  dim3 grid(a.njobs, 8);
+  gemm_kernel<<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_blocks(const double2* src, double2* dst, const CopyJob* jobs, int njobs,
+                               cudaStream_t s) {
+  if (njobs <= 0) return cudaSuccess;
+  dim3 grid(njobs, 4);
+  copy_kernel<<<grid, kOpsThreads, 0, s>>>(src, dst, jobs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_leaf_gather(const double2* f, int ldf, double2* g, const LeafJob* jobs, int njobs,
+                               int nrhs, int n, cudaStream_t s) {
+  if (njobs <= 0) return cudaSuccess;
+  leaf_gather_kernel<<<njobs, kOpsThreads, 0, s>>>(f, ldf, g, jobs, nrhs, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_leaf_scatter(const double2* g, double2* x, int ldx, const LeafJob* jobs, int njobs,
+                                int nrhs, int n, cudaStream_t s) {
+  if (njobs <= 0) return cudaSuccess;
+  leaf_scatter_kernel<<<njobs, kOpsThreads, 0, s>>>(g, x, ldx, jobs, nrhs, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plane_wave(const double* x, const double* y, const double* nx, const double* ny,
+                              const double* w, int n, double k0, double eps0, double angle,
+                              int scaled, double2* rhs, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  plane_wave_kernel<<<(n + 255) / 256, 256, 0, s>>>(x, y, nx, ny, w, n, k0, eps0, cos(angle), sin(angle),
+                                                    scaled, rhs);
+  return cudaGetLastError();
+}
+
+}  // namespace symhss

@@ -1,0 +1,1301 @@
+// Host runtime of the symhss library: tree and proxy rings, level-by-level
+// scheduling of the compression (Sec. 4.1), factorisation and solve (Sec. 4.2),
+// device memory, and the C ABI declared in include/symhss.h.
+//
+// Tree (Sec. 4.1, Theorem 1 setting): a binary tree over the node index order;
+// box [b, e) splits into [b, b + (e - b)/2) and the rest; all leaves at depth
+// L = ceil(log2(N / leaf)).  Box centre = mean of its nodes, radius rho = largest
+// node distance from the centre; proxy ring radius R = proxy_factor * rho with
+// P = max(nproxy, 8 ceil((2 max(k0, k1) R + 32) / 8)) equispaced points, outward
+// radial normals and weights 2 pi R / P.
+//
+// Compression of level l: each box's active unknowns are its nodes (leaf) or its
+// children's skeletons.  M_R rows are the near (point, equation) pairs -- active
+// rows of other boxes of the level strictly inside the proxy ring -- ordered
+// [equation 1 rows; equation 2 rows], then the P proxy points for equation 1 and
+// for equation 2; its columns are the box's active flux unknowns then trace
+// unknowns.  One column ID per half (symmetric mode, Eq. low-rank_R: L = R^T).
+// The baseline also builds M_L^T (the box's active equations against near active
+// unknowns and proxy sources) and row-IDs each half; per half both ranks are
+// raised to their maximum so that R D^{-1} L is square.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace symhss {
+
+// ---- growable device buffer -------------------------------------------------------
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept : p(o.p), cap(o.cap) { o.p = nullptr; o.cap = 0; }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    if (this != &o) { release(); p = o.p; cap = o.cap; o.p = nullptr; o.cap = 0; }
+    return *this;
+  }
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+  // grow to at least `bytes` (contents are not preserved on growth)
+  cudaError_t ensure(size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (bytes <= cap) return cudaSuccess;
+    release();
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) { p = nullptr; return e; }
+    cap = bytes;
+    return cudaSuccess;
+  }
+  template <class T> T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+// pack several host arrays into one device buffer (one copy); returns offsets
+struct Packer {
+  std::vector<char> host;
+  size_t add(const void* src, size_t bytes) {
+    size_t off = (host.size() + 255) & ~size_t(255);
+    host.resize(off + bytes);
+    if (bytes) std::memcpy(host.data() + off, src, bytes);
+    return off;
+  }
+  template <class T> size_t add(const std::vector<T>& v) { return add(v.data(), v.size() * sizeof(T)); }
+  cudaError_t upload(DevBuf& buf, cudaStream_t s) {
+    cudaError_t e = buf.ensure(host.size());
+    if (e != cudaSuccess) return e;
+    if (host.empty()) return cudaSuccess;
+    return cudaMemcpyAsync(buf.p, host.data(), host.size(), cudaMemcpyHostToDevice, s);
+  }
+};
+
+struct HBox {
+  int begin = 0, end = 0;
+  double cx = 0, cy = 0, rho = 0, R = 0;
+  int P = 0;
+  int proxy0 = 0;  // first proxy point in the point table
+  int child[2] = {-1, -1};
+  std::vector<int> act[2], actrow[2];
+  int rank[2] = {0, 0}, rrank[2] = {0, 0};
+  std::vector<int> perm[2], rperm[2];
+  long long t_off[2] = {0, 0}, rt_off[2] = {0, 0};  // into the level's T buffer
+  // factor
+  int size = 0;      // diagonal-block order
+  int k = 0;         // rank[0] + rank[1]
+  long long d_off = 0, piv_off = 0, x_off = 0, rx_off = 0;
+  long long q_off[2] = {0, 0}, rq_off[2] = {0, 0};
+  long long rxpiv_off = 0;
+  // solve
+  long long g_off = 0, ft_off = 0;
+};
+
+struct Level {
+  std::vector<HBox> boxes;
+  // compress
+  DevBuf mr, tbuf, permbuf, rankbuf, refbuf, clists, idjobs;
+  // factor
+  DevBuf D, piv, rxpiv, info, X, RX, At, qbuf, flists, lujobs, cjobs;
+  // solve
+  DevBuf G, FT, TMP, slists;
+  std::vector<int> h_rank;
+};
+
+}  // namespace symhss
+
+struct symhss_s {
+  symhss_params prm{};
+  int n = 0;
+  int depth = 0;
+  std::vector<double> hx, hy, hnx, hny, hw, hk;  // node arrays on the host
+  int npts = 0;                                   // nodes + proxy points
+  symhss::DevBuf pts;                             // point table (7 arrays)
+  symhss::DevBuf status;
+  std::vector<symhss::Level> levels;              // 0 .. depth
+  bool compressed = false, factored = false;
+  symhss::DevBuf xin, xout;                       // host-buffer solve staging
+  symhss::DevBuf rhsbuf;
+  cudaEvent_t ev[8] = {};
+  // per-launch device timing: events recorded around each launch on the caller's stream
+  std::vector<cudaEvent_t> evpool;
+  size_t evnext = 0;
+  struct Mark { int cls, e0, e1; double work; };
+  std::vector<Mark> marks;
+  symhss_stats_t st{};
+  cudaError_t last_cuda = cudaSuccess;
+  std::vector<int> mark;                          // host scratch (size npts)
+};
+
+namespace symhss {
+
+namespace {
+
+constexpr double kPi = 3.141592653589793238462643383279502884;
+
+int cuda_fail(symhss_s* h, cudaError_t e) {
+  if (h) h->last_cuda = e;
+  return e == cudaErrorMemoryAllocation ? SYMHSS_ERR_NOMEM : SYMHSS_ERR_CUDA;
+}
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t _e = (call);                       \
+    if (_e != cudaSuccess) return cuda_fail(h, _e); \
+  } while (0)
+
+// Record an event before a launch; returns its pool index or -1 (timing skipped).
+int prof_begin(symhss_s* h, cudaStream_t s) {
+  if (h->evnext >= h->evpool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    h->evpool.push_back(e);
+  }
+  const int i = (int)h->evnext++;
+  if (cudaEventRecord(h->evpool[i], s) != cudaSuccess) return -1;
+  return i;
+}
+void prof_end(symhss_s* h, cudaStream_t s, int cls, int e0, double work) {
+  if (e0 < 0) return;
+  const int e1 = prof_begin(h, s);
+  if (e1 < 0) return;
+  h->marks.push_back({cls, e0, e1, work});
+}
+// After a stream synchronisation: fold the recorded launches into the statistics.
+void prof_collect(symhss_s* h) {
+  for (const auto& m : h->marks) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, h->evpool[m.e0], h->evpool[m.e1]) == cudaSuccess) h->st.kernel_ms[m.cls] += ms;
+    h->st.kernel_launches[m.cls] += 1;
+    h->st.kernel_work[m.cls] += m.work;
+  }
+  h->marks.clear();
+  h->evnext = 0;
+}
+#define TIMED(cls, work, call)                     \
+  do {                                             \
+    const int _e0 = prof_begin(h, s);              \
+    CK(call);                                      \
+    prof_end(h, s, (cls), _e0, (work));            \
+  } while (0)
+
+double id_flops(int m, int n, int r) {
+  // Householder application (16 real flops per trailing entry and step) + T = R11^{-1} R12
+  double f = 0;
+  for (int k = 0; k < r; ++k) f += 16.0 * (double)(m - k) * (double)(n - k - 1);
+  return f + 4.0 * (double)r * r * (n - r);
+}
+
+bool finite_all(const std::vector<double>& v) {
+  for (double a : v)
+    if (!std::isfinite(a)) return false;
+  return true;
+}
+
+PointTable table_of(const symhss_s* h) {
+  const double* base = h->pts.as<double>();
+  const size_t np = (size_t)h->npts;
+  PointTable t;
+  t.x = base;
+  t.y = base + np;
+  t.nx = base + 2 * np;
+  t.ny = base + 3 * np;
+  t.w = base + 4 * np;
+  t.kappa = base + 5 * np;
+  t.id = reinterpret_cast<const int*>(base + 6 * np);
+  return t;
+}
+
+KernelParams kparams(const symhss_params& p) {
+  KernelParams k;
+  k.k0 = p.k0; k.k1 = p.k1; k.eps0 = p.eps0; k.eps1 = p.eps1;
+  k.e0sq = p.eps0 * p.eps0; k.e1sq = p.eps1 * p.eps1;
+  k.half_ft = 0.5 * (p.eps0 + p.eps1);
+  return k;
+}
+
+int proxy_count(const symhss_params& p, double radius) {
+  const double kmax = std::max(p.k0, p.k1);
+  const int need = (int)std::ceil((2.0 * kmax * radius + 32.0) / 8.0) * 8;
+  return std::max(p.nproxy, need);
+}
+
+int tree_depth(int n, int leaf) {
+  if (n <= leaf) return 0;
+  return (int)std::ceil(std::log2((double)n / (double)leaf));
+}
+
+int read_status(symhss_s* h, cudaStream_t s) {
+  int st = 0;
+  CK(cudaMemcpyAsync(&st, h->status.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (st & ST_BAD_INDEX) return SYMHSS_ERR_DEVICE;
+  if (st & ST_RANK_OVERFLOW) return SYMHSS_ERR_RANK_OVERFLOW;
+  if (st & ST_SINGULAR) return SYMHSS_ERR_SINGULAR;
+  if (st) return SYMHSS_ERR_DEVICE;
+  return SYMHSS_OK;
+}
+
+// Build the tree (host) and the point table (nodes + proxy rings).
+int build_geometry(symhss_s* h, cudaStream_t s) {
+  const int n = h->n;
+  const symhss_params& p = h->prm;
+  h->depth = tree_depth(n, p.leaf);
+  if (h->depth >= SYMHSS_MAX_LEVELS) return SYMHSS_ERR_INVALID;
+  // keep the levels' device buffers when the tree shape is unchanged (set_curve)
+  if ((int)h->levels.size() != h->depth + 1) {
+    h->levels.clear();
+    h->levels.resize(h->depth + 1);
+  }
+  for (auto& L : h->levels) L.boxes.clear();
+  h->levels[0].boxes.resize(1);
+  h->levels[0].boxes[0].begin = 0;
+  h->levels[0].boxes[0].end = n;
+  for (int l = 1; l <= h->depth; ++l) {
+    auto& prev = h->levels[l - 1].boxes;
+    auto& cur = h->levels[l].boxes;
+    cur.resize(2 * prev.size());
+    for (size_t i = 0; i < prev.size(); ++i) {
+      const int b = prev[i].begin, e = prev[i].end, mid = b + (e - b) / 2;
+      cur[2 * i].begin = b; cur[2 * i].end = mid;
+      cur[2 * i + 1].begin = mid; cur[2 * i + 1].end = e;
+      prev[i].child[0] = (int)(2 * i);
+      prev[i].child[1] = (int)(2 * i + 1);
+    }
+  }
+  int npts = n;
+  for (int l = 0; l <= h->depth; ++l) {
+    for (auto& bx : h->levels[l].boxes) {
+      const int cnt = bx.end - bx.begin;
+      double sx = 0, sy = 0;
+      for (int i = bx.begin; i < bx.end; ++i) { sx += h->hx[i]; sy += h->hy[i]; }
+      bx.cx = cnt ? sx / cnt : 0.0;
+      bx.cy = cnt ? sy / cnt : 0.0;
+      double rho = 0;
+      for (int i = bx.begin; i < bx.end; ++i) rho = std::max(rho, std::hypot(h->hx[i] - bx.cx, h->hy[i] - bx.cy));
+      bx.rho = rho;
+      bx.R = p.proxy_factor * rho;
+      if (l > 0) {
+        bx.P = proxy_count(p, bx.R);
+        bx.proxy0 = npts;
+        npts += bx.P;
+      }
+    }
+  }
+  h->npts = npts;
+  const size_t np = (size_t)npts;
+  std::vector<double> tab(7 * np, 0.0);
+  double *X = tab.data(), *Y = X + np, *NX = Y + np, *NY = NX + np, *W = NY + np, *K = W + np;
+  int* ID = reinterpret_cast<int*>(K + np);
+  for (int i = 0; i < n; ++i) {
+    X[i] = h->hx[i]; Y[i] = h->hy[i]; NX[i] = h->hnx[i]; NY[i] = h->hny[i]; W[i] = h->hw[i]; K[i] = h->hk[i];
+    ID[i] = i;
+  }
+  for (int l = 1; l <= h->depth; ++l) {
+    for (auto& bx : h->levels[l].boxes) {
+      for (int m = 0; m < bx.P; ++m) {
+        const double phi = 2.0 * kPi * m / bx.P;
+        const double c = std::cos(phi), sn = std::sin(phi);
+        const int q = bx.proxy0 + m;
+        X[q] = bx.cx + bx.R * c; Y[q] = bx.cy + bx.R * sn; NX[q] = c; NY[q] = sn;
+        W[q] = 2.0 * kPi * bx.R / bx.P; K[q] = 0.0; ID[q] = -1;
+      }
+    }
+  }
+  CK(h->pts.ensure(tab.size() * sizeof(double)));
+  CK(cudaMemcpyAsync(h->pts.p, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));  // `tab` is pageable and goes out of scope
+  h->mark.assign(np, -1);
+  return SYMHSS_OK;
+}
+
+// Merge two ordered point lists carrying slots into "points with two slots".
+// list0[i] gets slot base0 + i, list1[i] gets slot base1 + i.
+void merge_slots(std::vector<int>& mark, const std::vector<int>& list0, int base0,
+                 const std::vector<int>& list1, int base1, std::vector<int>& pt, std::vector<int>& s0,
+                 std::vector<int>& s1) {
+  for (size_t i = 0; i < list1.size(); ++i) mark[list1[i]] = base1 + (int)i;
+  for (size_t i = 0; i < list0.size(); ++i) {
+    const int q = list0[i];
+    pt.push_back(q);
+    s0.push_back(base0 + (int)i);
+    s1.push_back(mark[q]);
+    mark[q] = -2;
+  }
+  for (size_t i = 0; i < list1.size(); ++i) {
+    const int q = list1[i];
+    if (mark[q] >= 0) {
+      pt.push_back(q);
+      s0.push_back(-1);
+      s1.push_back(mark[q]);
+    }
+  }
+  for (int q : list1) mark[q] = -1;
+  for (int q : list0) mark[q] = -1;
+}
+
+struct TileBuilder {
+  std::vector<int> tp_pt, tp_s0, tp_s1, lp_pt, lp_s0, lp_s1;
+  std::vector<TileJob> jobs;
+  std::vector<TileChunk> chunks;
+  long long pairs = 0;
+  // thread points from (list0 -> slot base0+i, list1 -> base1+i); loop points likewise
+  void add(std::vector<int>& mark, const std::vector<int>& t0, int tb0, const std::vector<int>& t1, int tb1,
+           const std::vector<int>& l0, int lb0, const std::vector<int>& l1, int lb1, long long out_off, int ld,
+           int flags) {
+    TileJob jb;
+    jb.tp_off = (int)tp_pt.size();
+    merge_slots(mark, t0, tb0, t1, tb1, tp_pt, tp_s0, tp_s1);
+    jb.n_tp = (int)tp_pt.size() - jb.tp_off;
+    jb.lp_off = (int)lp_pt.size();
+    merge_slots(mark, l0, lb0, l1, lb1, lp_pt, lp_s0, lp_s1);
+    jb.n_lp = (int)lp_pt.size() - jb.lp_off;
+    jb.out_off = out_off;
+    jb.ld = ld;
+    jb.flags = flags;
+    if (jb.n_tp == 0 || jb.n_lp == 0) return;
+    const int j = (int)jobs.size();
+    jobs.push_back(jb);
+    for (int a = 0; a < jb.n_tp; a += TILE_T)
+      for (int b = 0; b < jb.n_lp; b += TILE_L) chunks.push_back(TileChunk{j, a, b});
+    pairs += (long long)jb.n_tp * jb.n_lp;
+  }
+  cudaError_t launch(symhss_s* h, DevBuf& buf, double2* out, cudaStream_t s) {
+    if (jobs.empty()) return cudaSuccess;
+    Packer pk;
+    const size_t o1 = pk.add(tp_pt), o2 = pk.add(tp_s0), o3 = pk.add(tp_s1);
+    const size_t o4 = pk.add(lp_pt), o5 = pk.add(lp_s0), o6 = pk.add(lp_s1);
+    const size_t o7 = pk.add(jobs), o8 = pk.add(chunks);
+    cudaError_t e = pk.upload(buf, s);
+    if (e != cudaSuccess) return e;
+    char* base = buf.as<char>();
+    TileLaunch a;
+    a.tpts = table_of(h);
+    a.lpts = a.tpts;
+    a.tp_pt = reinterpret_cast<const int*>(base + o1);
+    a.tp_s0 = reinterpret_cast<const int*>(base + o2);
+    a.tp_s1 = reinterpret_cast<const int*>(base + o3);
+    a.lp_pt = reinterpret_cast<const int*>(base + o4);
+    a.lp_s0 = reinterpret_cast<const int*>(base + o5);
+    a.lp_s1 = reinterpret_cast<const int*>(base + o6);
+    a.jobs = reinterpret_cast<const TileJob*>(base + o7);
+    a.chunks = reinterpret_cast<const TileChunk*>(base + o8);
+    a.nchunks = (int)chunks.size();
+    a.out = out;
+    a.status = h->status.as<int>();
+    a.kp = kparams(h->prm);
+    return launch_tiles(a, s);
+  }
+};
+
+inline long long tcap(int n) { return (long long)(n / 2) * ((n + 1) / 2) + 1; }
+
+// Near points of box b among the active lists `which` (0: rows, 1: columns) of its level.
+void near_points(const symhss_s* h, const std::vector<HBox>& lev, int b, bool rows, int part,
+                 std::vector<int>& out) {
+  const HBox& bx = lev[b];
+  out.clear();
+  for (size_t o = 0; o < lev.size(); ++o) {
+    if ((int)o == b) continue;
+    const HBox& ot = lev[o];
+    if (std::hypot(ot.cx - bx.cx, ot.cy - bx.cy) >= bx.R + ot.rho) continue;
+    const std::vector<int>& ids = rows ? ot.actrow[part] : ot.act[part];
+    for (int q : ids)
+      if (std::hypot(h->hx[q] - bx.cx, h->hy[q] - bx.cy) < bx.R) out.push_back(q);
+  }
+}
+
+int fixed_rank(const symhss_s* h, int level) {
+  if (h->prm.fixed_rank_kL <= 0) return -1;
+  return (int)std::ceil(std::pow(h->prm.rank_scale_a, h->depth - level) * h->prm.fixed_rank_kL);
+}
+
+int compress_level(symhss_s* h, int l, cudaStream_t s) {
+  Level& L = h->levels[l];
+  auto& boxes = L.boxes;
+  const bool sym = h->prm.mode == SYMHSS_SYM;
+  const int nb = (int)boxes.size();
+  // active sets
+  for (int b = 0; b < nb; ++b) {
+    HBox& bx = boxes[b];
+    if (l == h->depth) {
+      std::vector<int> ids(bx.end - bx.begin);
+      for (int i = 0; i < (int)ids.size(); ++i) ids[i] = bx.begin + i;
+      for (int p = 0; p < 2; ++p) { bx.act[p] = ids; bx.actrow[p] = ids; }
+    } else {
+      const HBox& c1 = h->levels[l + 1].boxes[bx.child[0]];
+      const HBox& c2 = h->levels[l + 1].boxes[bx.child[1]];
+      for (int p = 0; p < 2; ++p) {
+        bx.act[p].assign(c1.perm[p].begin(), c1.perm[p].begin() + c1.rank[p]);
+        for (int& v : bx.act[p]) v = c1.act[p][v];
+        for (int j = 0; j < c2.rank[p]; ++j) bx.act[p].push_back(c2.act[p][c2.perm[p][j]]);
+        bx.actrow[p].clear();
+        for (int j = 0; j < c1.rrank[p]; ++j) bx.actrow[p].push_back(c1.actrow[p][c1.rperm[p][j]]);
+        for (int j = 0; j < c2.rrank[p]; ++j) bx.actrow[p].push_back(c2.actrow[p][c2.rperm[p][j]]);
+      }
+    }
+  }
+  TileBuilder tb;
+  std::vector<IdJob> jobs;
+  long long mr_total = 0, t_total = 0, perm_total = 0;
+  int max_m = 1, max_n = 1;
+  const int fixed = fixed_rank(h, l);
+  std::vector<int> nr0, nr1, prx0, prx1;
+  const int flags = sym ? 0 : TILE_UNSCALED;
+  // M_R of every box (and M_L^T for the baseline)
+  for (int b = 0; b < nb; ++b) {
+    HBox& bx = boxes[b];
+    near_points(h, boxes, b, true, 0, nr0);
+    near_points(h, boxes, b, true, 1, nr1);
+    prx0.resize(bx.P);
+    for (int m = 0; m < bx.P; ++m) prx0[m] = bx.proxy0 + m;
+    const int m0 = (int)nr0.size(), m1 = (int)nr1.size(), P = bx.P;
+    const int m = m0 + m1 + 2 * P;
+    const int n0 = (int)bx.act[0].size(), n1 = (int)bx.act[1].size();
+    // rows: near eq1 (slots 0..m0), near eq2 (m0..), proxy eq1 and eq2 (same points)
+    tb.add(h->mark, nr0, 0, nr1, m0, bx.act[0], 0, bx.act[1], n0, mr_total, m, flags);
+    tb.add(h->mark, prx0, m0 + m1, prx0, m0 + m1 + P, bx.act[0], 0, bx.act[1], n0, mr_total, m, flags);
+    for (int p = 0; p < 2; ++p) {
+      IdJob j;
+      j.m_off = mr_total + (p == 0 ? 0 : (long long)n0 * m);
+      j.m = m; j.n = p == 0 ? n0 : n1; j.ld = m;
+      j.start = 0; j.fixed = fixed;
+      j.t_off = t_total; t_total += tcap(j.n);
+      j.perm_off = perm_total; perm_total += j.n;
+      j.out_idx = 2 * b + p;
+      jobs.push_back(j);
+      bx.t_off[p] = j.t_off;
+      max_n = std::max(max_n, j.n);
+    }
+    max_m = std::max(max_m, m);
+    mr_total += (long long)m * (n0 + n1);
+  }
+  if (!sym) {
+    for (int b = 0; b < nb; ++b) {
+      HBox& bx = boxes[b];
+      near_points(h, boxes, b, false, 0, nr0);
+      near_points(h, boxes, b, false, 1, nr1);
+      prx0.resize(bx.P);
+      for (int m = 0; m < bx.P; ++m) prx0[m] = bx.proxy0 + m;
+      const int c0 = (int)nr0.size(), c1n = (int)nr1.size(), P = bx.P;
+      const int mt = c0 + c1n + 2 * P;  // rows of M_L^T = columns of M_L
+      const int r0 = (int)bx.actrow[0].size(), r1 = (int)bx.actrow[1].size();
+      // thread points = M_L columns (sources), loop points = M_L rows (observations)
+      tb.add(h->mark, nr0, 0, nr1, c0, bx.actrow[0], 0, bx.actrow[1], r0, mr_total, mt,
+             flags | TILE_SRC_IS_THREAD);
+      tb.add(h->mark, prx0, c0 + c1n, prx0, c0 + c1n + P, bx.actrow[0], 0, bx.actrow[1], r0, mr_total, mt,
+             flags | TILE_SRC_IS_THREAD);
+      for (int p = 0; p < 2; ++p) {
+        IdJob j;
+        j.m_off = mr_total + (p == 0 ? 0 : (long long)r0 * mt);
+        j.m = mt; j.n = p == 0 ? r0 : r1; j.ld = mt;
+        j.start = 0; j.fixed = fixed;
+        j.t_off = t_total; t_total += tcap(j.n);
+        j.perm_off = perm_total; perm_total += j.n;
+        j.out_idx = 2 * nb + 2 * b + p;
+        jobs.push_back(j);
+        bx.rt_off[p] = j.t_off;
+        max_n = std::max(max_n, j.n);
+      }
+      max_m = std::max(max_m, mt);
+      mr_total += (long long)mt * (r0 + r1);
+    }
+  }
+  const int njobs = (int)jobs.size();
+  CK(L.mr.ensure(mr_total * sizeof(double2)));
+  CK(L.tbuf.ensure(t_total * sizeof(double2)));
+  CK(L.permbuf.ensure(perm_total * sizeof(int)));
+  CK(L.rankbuf.ensure(njobs * sizeof(int)));
+  CK(L.refbuf.ensure(njobs * sizeof(double)));
+  TIMED(SYMHSS_K_TILES, (double)tb.pairs, tb.launch(h, L.clists, L.mr.as<double2>(), s));
+  Packer pk;
+  pk.add(jobs);
+  CK(pk.upload(L.idjobs, s));
+  IdLaunch ia;
+  ia.mats = L.mr.as<double2>();
+  ia.tbuf = L.tbuf.as<double2>();
+  ia.perm = L.permbuf.as<int>();
+  ia.rank = L.rankbuf.as<int>();
+  ia.ref = L.refbuf.as<double>();
+  ia.jobs = L.idjobs.as<IdJob>();
+  ia.njobs = njobs;
+  ia.tol = h->prm.tol;
+  ia.status = h->status.as<int>();
+  ia.max_m = max_m;
+  ia.max_n = max_n;
+  const size_t id_before = h->marks.size();
+  TIMED(SYMHSS_K_ID, 0.0, launch_cpqr(ia, s));
+  const size_t id_mark = h->marks.size() > id_before ? id_before : (size_t)-1;
+  std::vector<int> hr(njobs), hp(perm_total);
+  CK(cudaMemcpyAsync(hr.data(), L.rankbuf.p, njobs * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(hp.data(), L.permbuf.p, perm_total * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (id_mark < h->marks.size()) {
+    double w = 0;
+    for (const IdJob& j : jobs) w += id_flops(j.m, j.n, hr[j.out_idx]);
+    h->marks[id_mark].work = w;
+  }
+  h->st.pairs_evaluated += tb.pairs;
+  if (!sym) {  // raise the lower of the row / column ranks of each half to the higher
+    std::vector<IdJob> more;
+    for (int b = 0; b < nb; ++b)
+      for (int p = 0; p < 2; ++p) {
+        const int ic = 2 * b + p, ir = 2 * nb + 2 * b + p;
+        const int k = std::max(hr[ic], hr[ir]);
+        for (int idx : {ic, ir}) {
+          if (hr[idx] < k) {
+            IdJob j = jobs[idx];
+            j.start = hr[idx];
+            j.fixed = k;
+            more.push_back(j);
+          }
+        }
+      }
+    if (!more.empty()) {
+      Packer pk2;
+      pk2.add(more);
+      CK(pk2.upload(L.idjobs, s));
+      ia.jobs = L.idjobs.as<IdJob>();
+      ia.njobs = (int)more.size();
+      const size_t more_before = h->marks.size();
+      TIMED(SYMHSS_K_ID, 0.0, launch_cpqr(ia, s));
+      const size_t more_mark = h->marks.size() > more_before ? more_before : (size_t)-1;
+      CK(cudaMemcpyAsync(hr.data(), L.rankbuf.p, njobs * sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(hp.data(), L.permbuf.p, perm_total * sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (more_mark < h->marks.size()) {
+        double w = 0;
+        for (const IdJob& j : more) w += id_flops(j.m, j.n, hr[j.out_idx]) - id_flops(j.m, j.n, j.start);
+        h->marks[more_mark].work = w;
+      }
+    }
+  }
+  prof_collect(h);
+  for (const IdJob& j : jobs) {
+    const int r = hr[j.out_idx];
+    h->st.flops_id += 16.0 * (double)j.m * j.n * r;
+  }
+  h->st.id_count += njobs;
+  for (int b = 0; b < nb; ++b) {
+    HBox& bx = boxes[b];
+    for (int p = 0; p < 2; ++p) {
+      const IdJob& j = jobs[2 * b + p];
+      bx.rank[p] = hr[2 * b + p];
+      bx.perm[p].assign(hp.begin() + j.perm_off, hp.begin() + j.perm_off + j.n);
+      if (sym) {
+        bx.rrank[p] = bx.rank[p];
+        bx.rperm[p] = bx.perm[p];
+        bx.rt_off[p] = bx.t_off[p];
+      } else {
+        const IdJob& jr = jobs[2 * nb + 2 * b + p];
+        bx.rrank[p] = hr[jr.out_idx];
+        bx.rperm[p].assign(hp.begin() + jr.perm_off, hp.begin() + jr.perm_off + jr.n);
+        if (bx.rrank[p] != bx.rank[p]) return SYMHSS_ERR_DEVICE;
+      }
+    }
+  }
+  L.h_rank = hr;
+  return SYMHSS_OK;
+}
+
+// Positions of each active unknown (part p, active order) in the box's diagonal-block
+// ordering: leaf [flux; trace]; parent [child 1 (flux; trace), child 2 (flux; trace)].
+void positions(const symhss_s* h, int l, const HBox& bx, bool rows, std::vector<int> pos[2]) {
+  if (l == h->depth) {
+    const int nb = bx.end - bx.begin;
+    for (int p = 0; p < 2; ++p) {
+      pos[p].resize(nb);
+      for (int i = 0; i < nb; ++i) pos[p][i] = p * nb + i;
+    }
+    return;
+  }
+  const HBox& c1 = h->levels[l + 1].boxes[bx.child[0]];
+  const HBox& c2 = h->levels[l + 1].boxes[bx.child[1]];
+  const int* r1 = rows ? c1.rrank : c1.rank;
+  const int* r2 = rows ? c2.rrank : c2.rank;
+  const int a1 = r1[0] + r1[1];
+  for (int p = 0; p < 2; ++p) {
+    pos[p].clear();
+    const int o1 = p == 0 ? 0 : r1[0];
+    const int o2 = a1 + (p == 0 ? 0 : r2[0]);
+    for (int i = 0; i < r1[p]; ++i) pos[p].push_back(o1 + i);
+    for (int i = 0; i < r2[p]; ++i) pos[p].push_back(o2 + i);
+  }
+}
+
+// skeleton rows / columns of a box, per part, in pivot order
+void skeleton(const HBox& bx, bool rows, int p, std::vector<int>& out) {
+  out.clear();
+  const std::vector<int>& a = rows ? bx.actrow[p] : bx.act[p];
+  const std::vector<int>& pm = rows ? bx.rperm[p] : bx.perm[p];
+  const int r = rows ? bx.rrank[p] : bx.rank[p];
+  for (int j = 0; j < r; ++j) out.push_back(a[pm[j]]);
+}
+
+// Assemble the diagonal blocks D of level l (leaf tiles, or children's Atilde plus
+// skeleton coupling tiles) into L.D and factorise them.
+int assemble_and_lu(symhss_s* h, int l, cudaStream_t s, long long& pairs) {
+  Level& L = h->levels[l];
+  auto& boxes = L.boxes;
+  const bool sym = h->prm.mode == SYMHSS_SYM;
+  const int flags = sym ? 0 : TILE_UNSCALED;
+  const bool leaf = (l == h->depth);
+  long long d_total = 0, piv_total = 0;
+  int max_n = 1;
+  for (auto& bx : boxes) {
+    if (leaf) bx.size = 2 * (bx.end - bx.begin);
+    else {
+      const HBox& c1 = h->levels[l + 1].boxes[bx.child[0]];
+      const HBox& c2 = h->levels[l + 1].boxes[bx.child[1]];
+      bx.size = c1.rank[0] + c1.rank[1] + c2.rank[0] + c2.rank[1];
+    }
+    bx.d_off = d_total;
+    d_total += (long long)bx.size * bx.size;
+    bx.piv_off = piv_total;
+    piv_total += bx.size;
+    max_n = std::max(max_n, bx.size);
+  }
+  CK(L.D.ensure(d_total * sizeof(double2)));
+  CK(L.piv.ensure(piv_total * sizeof(int)));
+  CK(L.info.ensure(boxes.size() * sizeof(int)));
+  TileBuilder tb;
+  std::vector<CopyJob> copies;
+  std::vector<int> t0, t1, u0, u1;
+  for (auto& bx : boxes) {
+    if (leaf) {
+      std::vector<int> ids(bx.end - bx.begin);
+      for (int i = 0; i < (int)ids.size(); ++i) ids[i] = bx.begin + i;
+      const int nb = (int)ids.size();
+      tb.add(h->mark, ids, 0, ids, nb, ids, 0, ids, nb, bx.d_off, bx.size, flags);
+    } else {
+      const HBox& c1 = h->levels[l + 1].boxes[bx.child[0]];
+      const HBox& c2 = h->levels[l + 1].boxes[bx.child[1]];
+      const int a1 = c1.rank[0] + c1.rank[1];
+      // rows of child 1 against columns of child 2, and the transpose position
+      skeleton(c1, true, 0, t0); skeleton(c1, true, 1, t1);
+      skeleton(c2, false, 0, u0); skeleton(c2, false, 1, u1);
+      tb.add(h->mark, t0, 0, t1, c1.rrank[0], u0, a1, u1, a1 + c2.rank[0], bx.d_off, bx.size, flags);
+      skeleton(c2, true, 0, t0); skeleton(c2, true, 1, t1);
+      skeleton(c1, false, 0, u0); skeleton(c1, false, 1, u1);
+      tb.add(h->mark, t0, a1, t1, a1 + c2.rrank[0], u0, 0, u1, c1.rank[0], bx.d_off, bx.size, flags);
+      const Level& LC = h->levels[l + 1];
+      CopyJob cj;
+      cj.src_off = c1.rx_off; cj.dst_off = bx.d_off; cj.rows = a1; cj.cols = a1; cj.lds = a1; cj.ldd = bx.size;
+      copies.push_back(cj);
+      const int a2 = c2.rank[0] + c2.rank[1];
+      cj.src_off = c2.rx_off; cj.dst_off = bx.d_off + a1 + (long long)a1 * bx.size;
+      cj.rows = a2; cj.cols = a2; cj.lds = a2;
+      copies.push_back(cj);
+      (void)LC;
+    }
+  }
+  TIMED(SYMHSS_K_TILES, (double)tb.pairs, tb.launch(h, L.flists, L.D.as<double2>(), s));
+  pairs += tb.pairs;
+  if (!copies.empty()) {
+    Packer pk;
+    pk.add(copies);
+    // child Atilde live in the child level's At buffer
+    DevBuf& tmp = L.cjobs;
+    CK(pk.upload(tmp, s));
+    TIMED(SYMHSS_K_OTHER, 0.0, launch_copy_blocks(h->levels[l + 1].At.as<double2>(), L.D.as<double2>(),
+                                                  tmp.as<CopyJob>(), (int)copies.size(), s));
+  }
+  std::vector<LuJob> lj;
+  double lu_work = 0;
+  for (size_t b = 0; b < boxes.size(); ++b) {
+    LuJob j;
+    j.a_off = boxes[b].d_off; j.n = boxes[b].size; j.ld = boxes[b].size; j.piv_off = boxes[b].piv_off;
+    j.info_idx = (int)b;
+    lj.push_back(j);
+    h->st.flops_lu += 8.0 / 3.0 * std::pow((double)boxes[b].size, 3);
+    lu_work += 8.0 / 3.0 * std::pow((double)boxes[b].size, 3);
+  }
+  Packer pk;
+  pk.add(lj);
+  CK(pk.upload(L.lujobs, s));
+  LuLaunch la;
+  la.base = L.D.as<double2>();
+  la.piv = L.piv.as<int>();
+  la.info = L.info.as<int>();
+  la.jobs = L.lujobs.as<LuJob>();
+  la.njobs = (int)lj.size();
+  la.max_n = max_n;
+  la.status = h->status.as<int>();
+  TIMED(SYMHSS_K_GETRF, lu_work, launch_getrf(la, s));
+  return SYMHSS_OK;
+}
+
+int factor_level(symhss_s* h, int l, cudaStream_t s, long long& pairs) {
+  Level& L = h->levels[l];
+  auto& boxes = L.boxes;
+  int rc = assemble_and_lu(h, l, s, pairs);
+  if (rc) return rc;
+  // bases: L (row ID) for X = D^{-1} L; R (column ID) for R X
+  std::vector<int> qhost;
+  long long x_total = 0, rx_total = 0, rxpiv_total = 0;
+  int max_n = 1, max_k = 1;
+  std::vector<int> pos[2], rpos[2];
+  for (auto& bx : boxes) {
+    positions(h, l, bx, false, pos);
+    positions(h, l, bx, true, rpos);
+    for (int p = 0; p < 2; ++p) {
+      bx.q_off[p] = (long long)qhost.size();
+      for (int c = 0; c < (int)bx.perm[p].size(); ++c) qhost.push_back(pos[p][bx.perm[p][c]]);
+      bx.rq_off[p] = (long long)qhost.size();
+      for (int c = 0; c < (int)bx.rperm[p].size(); ++c) qhost.push_back(rpos[p][bx.rperm[p][c]]);
+    }
+    bx.k = bx.rank[0] + bx.rank[1];
+    bx.x_off = x_total;
+    x_total += (long long)bx.size * bx.k;
+    bx.rx_off = rx_total;
+    rx_total += (long long)bx.k * bx.k;
+    bx.rxpiv_off = rxpiv_total;
+    rxpiv_total += bx.k;
+    max_n = std::max(max_n, bx.size);
+    max_k = std::max(max_k, bx.k);
+  }
+  // job lists
+  std::vector<BasisJob> lbj, rbj;
+  std::vector<RsJob> xs, ats;
+  std::vector<LuJob> rxl;
+  std::vector<CopyJob> eye;
+  for (size_t b = 0; b < boxes.size(); ++b) {
+    HBox& bx = boxes[b];
+    BasisJob jl{}, jr{};
+    for (int p = 0; p < 2; ++p) {
+      jl.part[p].q_off = bx.rq_off[p]; jl.part[p].t_off = bx.rt_off[p];
+      jl.part[p].n = (int)bx.rperm[p].size(); jl.part[p].r = bx.rrank[p];
+      jl.part[p].col0 = p == 0 ? 0 : bx.rrank[0];
+      jr.part[p].q_off = bx.q_off[p]; jr.part[p].t_off = bx.t_off[p];
+      jr.part[p].n = (int)bx.perm[p].size(); jr.part[p].r = bx.rank[p];
+      jr.part[p].col0 = p == 0 ? 0 : bx.rank[0];
+    }
+    jl.size = jr.size = bx.size;
+    jl.k = jr.k = bx.k;
+    jl.out_off = bx.x_off; jl.ld_out = bx.size;
+    jr.in_off = bx.x_off; jr.ld_in = bx.size; jr.out_off = bx.rx_off; jr.ld_out = bx.k; jr.ncols = bx.k;
+    lbj.push_back(jl);
+    rbj.push_back(jr);
+    RsJob x;
+    x.a_off = bx.d_off; x.n = bx.size; x.lda = bx.size; x.piv_off = bx.piv_off;
+    x.b_off = bx.x_off; x.ldb = bx.size; x.nrhs = bx.k;
+    xs.push_back(x);
+    h->st.flops_lu += 8.0 * (double)bx.size * bx.size * bx.k;
+    LuJob lu;
+    lu.a_off = bx.rx_off; lu.n = bx.k; lu.ld = bx.k; lu.piv_off = bx.rxpiv_off; lu.info_idx = (int)b;
+    rxl.push_back(lu);
+    RsJob at;
+    at.a_off = bx.rx_off; at.n = bx.k; at.lda = bx.k; at.piv_off = bx.rxpiv_off;
+    at.b_off = bx.rx_off; at.ldb = bx.k; at.nrhs = bx.k;
+    ats.push_back(at);
+    CopyJob cj;
+    cj.src_off = -1; cj.dst_off = bx.rx_off; cj.rows = bx.k; cj.cols = bx.k; cj.lds = bx.k; cj.ldd = bx.k;
+    eye.push_back(cj);
+    h->st.flops_lu += 8.0 / 3.0 * std::pow((double)bx.k, 3) + 8.0 * std::pow((double)bx.k, 3);
+  }
+  Packer pk;
+  const size_t oq = pk.add(qhost), ol = pk.add(lbj), orr = pk.add(rbj), ox = pk.add(xs), orl = pk.add(rxl),
+               oa = pk.add(ats), oe = pk.add(eye);
+  CK(pk.upload(L.qbuf, s));
+  char* qb = L.qbuf.as<char>();
+  CK(L.X.ensure(x_total * sizeof(double2)));
+  CK(L.RX.ensure(rx_total * sizeof(double2)));
+  CK(L.At.ensure(rx_total * sizeof(double2)));
+  // X = D^{-1} L
+  BasisLaunch bl;
+  bl.q = reinterpret_cast<const int*>(qb + oq);
+  bl.T = h->levels[l].tbuf.as<double2>();
+  bl.in = nullptr;
+  bl.out = L.X.as<double2>();
+  bl.jobs = reinterpret_cast<const BasisJob*>(qb + ol);
+  bl.njobs = (int)lbj.size();
+  bl.max_cols = max_k;
+  TIMED(SYMHSS_K_OTHER, 0.0, launch_basis_dense(bl, s));
+  double w_x = 0, w_rx = 0, w_rxlu = 0, w_at = 0;
+  for (const auto& bx : boxes) {
+    w_x += 8.0 * (double)bx.size * bx.size * bx.k;
+    w_rx += 8.0 * (double)bx.k * bx.k * (double)(bx.perm[0].size() + bx.perm[1].size());
+    w_rxlu += 8.0 / 3.0 * std::pow((double)bx.k, 3);
+    w_at += 8.0 * std::pow((double)bx.k, 3);
+  }
+  RsLaunch ra;
+  ra.abase = L.D.as<double2>();
+  ra.piv = L.piv.as<int>();
+  ra.bbase = L.X.as<double2>();
+  ra.jobs = reinterpret_cast<const RsJob*>(qb + ox);
+  ra.njobs = (int)xs.size();
+  ra.max_rhs = max_k;
+  ra.max_n = max_n;
+  TIMED(SYMHSS_K_GETRS, w_x, launch_getrs(ra, s));
+  // R X
+  BasisLaunch br = bl;
+  br.in = L.X.as<double2>();
+  br.out = L.RX.as<double2>();
+  br.jobs = reinterpret_cast<const BasisJob*>(qb + orr);
+  TIMED(SYMHSS_K_OTHER, w_rx, launch_apply_r(br, s));
+  // Atilde = (R X)^{-1}
+  CK(L.rxpiv.ensure(rxpiv_total * sizeof(int)));
+  LuLaunch la;
+  la.base = L.RX.as<double2>();
+  la.piv = L.rxpiv.as<int>();
+  la.info = L.info.as<int>();
+  la.jobs = reinterpret_cast<const LuJob*>(qb + orl);
+  la.njobs = (int)rxl.size();
+  la.max_n = max_k;
+  la.status = h->status.as<int>();
+  TIMED(SYMHSS_K_GETRF, w_rxlu, launch_getrf(la, s));
+  TIMED(SYMHSS_K_OTHER, 0.0, launch_copy_blocks(nullptr, L.At.as<double2>(),
+                                                reinterpret_cast<const CopyJob*>(qb + oe), (int)eye.size(), s));
+  RsLaunch rb;
+  rb.abase = L.RX.as<double2>();
+  rb.piv = L.rxpiv.as<int>();
+  rb.bbase = L.At.as<double2>();
+  rb.jobs = reinterpret_cast<const RsJob*>(qb + oa);
+  rb.njobs = (int)ats.size();
+  rb.max_rhs = max_k;
+  rb.max_n = max_k;
+  TIMED(SYMHSS_K_GETRS, w_at, launch_getrs(rb, s));
+  return SYMHSS_OK;
+}
+
+}  // namespace
+}  // namespace symhss
+
+using namespace symhss;
+
+// =============================================================================== C ABI
+
+extern "C" {
+
+const char* symhss_strerror(int status) {
+  switch (status) {
+    case SYMHSS_OK: return "ok";
+    case SYMHSS_ERR_INVALID: return "invalid argument";
+    case SYMHSS_ERR_NOMEM: return "out of memory";
+    case SYMHSS_ERR_CUDA: return "CUDA error";
+    case SYMHSS_ERR_RANK_OVERFLOW: return "ID rank exceeded capacity";
+    case SYMHSS_ERR_SINGULAR: return "singular diagonal block";
+    case SYMHSS_ERR_TIMEOUT: return "device wait timed out";
+    case SYMHSS_ERR_STATE: return "calls out of order";
+    case SYMHSS_ERR_DEVICE: return "device-side index check failed";
+    default: return "unknown status";
+  }
+}
+
+int symhss_params_default(symhss_params* p) {
+  if (!p) return SYMHSS_ERR_INVALID;
+  std::memset(p, 0, sizeof(*p));
+  p->k0 = 1.0; p->k1 = 1.0; p->eps0 = 1.0; p->eps1 = 1.0;
+  p->tol = 1e-10; p->leaf = 128; p->nproxy = 64; p->proxy_factor = 1.5;
+  p->mode = SYMHSS_SYM; p->precision = SYMHSS_FP64;
+  p->fixed_rank_kL = 0; p->rank_scale_a = 1.15; p->oversample = 16; p->seed = 0x5eed;
+  return SYMHSS_OK;
+}
+
+static int validate_params(const symhss_params* p) {
+  if (!p) return SYMHSS_ERR_INVALID;
+  if (!(p->k0 > 0) || !(p->k1 > 0) || !(p->eps0 > 0) || !(p->eps1 > 0)) return SYMHSS_ERR_INVALID;
+  if (!std::isfinite(p->k0) || !std::isfinite(p->k1) || !std::isfinite(p->eps0) || !std::isfinite(p->eps1))
+    return SYMHSS_ERR_INVALID;
+  if (!(p->tol >= 0) || !std::isfinite(p->tol)) return SYMHSS_ERR_INVALID;
+  if (p->leaf < 1 || p->nproxy < 8 || !(p->proxy_factor > 1.0) || !std::isfinite(p->proxy_factor))
+    return SYMHSS_ERR_INVALID;
+  if (p->mode != SYMHSS_SYM && p->mode != SYMHSS_NONSYM) return SYMHSS_ERR_INVALID;
+  if (p->precision != SYMHSS_FP64) return SYMHSS_ERR_INVALID;
+  if (p->fixed_rank_kL < 0 || (p->fixed_rank_kL > 0 && !(p->rank_scale_a >= 1.0))) return SYMHSS_ERR_INVALID;
+  return SYMHSS_OK;
+}
+
+static int load_curve(symhss_s* h, const symhss_curve* c, cudaStream_t s) {
+  if (!c || c->n < 2) return SYMHSS_ERR_INVALID;
+  if (!c->x || !c->y || !c->nx || !c->ny || !c->w || !c->kappa) return SYMHSS_ERR_INVALID;
+  if (c->location != SYMHSS_HOST && c->location != SYMHSS_DEVICE) return SYMHSS_ERR_INVALID;
+  const int n = c->n;
+  std::vector<double>* dst[6] = {&h->hx, &h->hy, &h->hnx, &h->hny, &h->hw, &h->hk};
+  const double* src[6] = {c->x, c->y, c->nx, c->ny, c->w, c->kappa};
+  for (int i = 0; i < 6; ++i) {
+    dst[i]->resize(n);
+    if (c->location == SYMHSS_HOST) {
+      std::memcpy(dst[i]->data(), src[i], n * sizeof(double));
+    } else {
+      cudaError_t e = cudaMemcpyAsync(dst[i]->data(), src[i], n * sizeof(double), cudaMemcpyDeviceToHost, s);
+      if (e != cudaSuccess) return cuda_fail(h, e);
+    }
+  }
+  if (c->location == SYMHSS_DEVICE) {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+  }
+  for (int i = 0; i < 6; ++i)
+    if (!finite_all(*dst[i])) return SYMHSS_ERR_INVALID;
+  for (int i = 0; i < n; ++i)
+    if (!(h->hw[i] > 0)) return SYMHSS_ERR_INVALID;
+  h->n = n;
+  return SYMHSS_OK;
+}
+
+int symhss_create(const symhss_curve* curve, const symhss_params* prm, void* stream, symhss_t* out) {
+  if (!out) return SYMHSS_ERR_INVALID;
+  *out = nullptr;
+  int rc = validate_params(prm);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  symhss_s* h = new (std::nothrow) symhss_s();
+  if (!h) return SYMHSS_ERR_NOMEM;
+  try {
+    h->prm = *prm;
+    rc = load_curve(h, curve, s);
+    if (!rc) rc = build_geometry(h, s);
+    if (!rc) {
+      cudaError_t e = h->status.ensure(sizeof(int));
+      if (e == cudaSuccess) e = cudaMemsetAsync(h->status.p, 0, sizeof(int), s);
+      for (int i = 0; i < 8 && e == cudaSuccess; ++i) e = cudaEventCreate(&h->ev[i]);
+      if (e != cudaSuccess) rc = cuda_fail(h, e);
+    }
+  } catch (const std::bad_alloc&) {
+    rc = SYMHSS_ERR_NOMEM;
+  }
+  if (rc) {
+    symhss_destroy(h);
+    return rc;
+  }
+  h->st.n = h->n;
+  h->st.depth = h->depth;
+  h->st.nboxes_leaf = (int)h->levels[h->depth].boxes.size();
+  *out = h;
+  return SYMHSS_OK;
+}
+
+int symhss_set_curve(symhss_t h, const symhss_curve* curve, void* stream) {
+  if (!h || !curve || curve->n != h->n) return SYMHSS_ERR_INVALID;
+  try {
+    int rc = load_curve(h, curve, (cudaStream_t)stream);
+    if (rc) return rc;
+    rc = build_geometry(h, (cudaStream_t)stream);
+    h->compressed = h->factored = false;
+    return rc;
+  } catch (const std::bad_alloc&) {
+    return SYMHSS_ERR_NOMEM;
+  }
+}
+
+int symhss_compress(symhss_t h, void* stream) {
+  if (!h) return SYMHSS_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  h->compressed = h->factored = false;
+  h->st.ms_tiles = h->st.ms_id = 0;
+  h->st.pairs_evaluated = 0;
+  h->st.id_count = 0;
+  h->st.flops_id = 0;
+  for (int c = 0; c < SYMHSS_K_COUNT; ++c) {
+    h->st.kernel_ms[c] = 0;
+    h->st.kernel_launches[c] = 0;
+    h->st.kernel_work[c] = 0;
+  }
+  h->marks.clear();
+  h->evnext = 0;
+  try {
+    CK(cudaMemsetAsync(h->status.p, 0, sizeof(int), s));
+    CK(cudaEventRecord(h->ev[0], s));
+    for (int l = h->depth; l >= 1; --l) {
+      int rc = compress_level(h, l, s);
+      if (rc) return rc;
+      rc = read_status(h, s);
+      if (rc) return rc;
+    }
+    CK(cudaEventRecord(h->ev[1], s));
+    CK(cudaEventSynchronize(h->ev[1]));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
+    h->st.ms_compress = ms;
+  } catch (const std::bad_alloc&) {
+    return SYMHSS_ERR_NOMEM;
+  }
+  // rank statistics
+  h->st.max_rank[0] = h->st.max_rank[1] = 0;
+  for (int l = 1; l <= h->depth; ++l) {
+    auto& bxs = h->levels[l].boxes;
+    for (int p = 0; p < 2; ++p) {
+      int mx = 0;
+      double sum = 0;
+      for (auto& b : bxs) { mx = std::max(mx, b.rank[p]); sum += b.rank[p]; }
+      h->st.level_max_rank[l][p] = mx;
+      h->st.level_mean_rank[l][p] = bxs.empty() ? 0.0 : sum / bxs.size();
+      h->st.max_rank[p] = std::max(h->st.max_rank[p], mx);
+    }
+    int mp = 0;
+    for (auto& b : bxs) mp = std::max(mp, b.P);
+    h->st.level_nproxy[l] = mp;
+  }
+  h->compressed = true;
+  return SYMHSS_OK;
+}
+
+int symhss_factor(symhss_t h, void* stream) {
+  if (!h) return SYMHSS_ERR_INVALID;
+  if (!h->compressed && h->depth > 0) return SYMHSS_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  h->factored = false;
+  h->st.flops_lu = 0;
+  long long pairs = 0;
+  try {
+    CK(cudaMemsetAsync(h->status.p, 0, sizeof(int), s));
+    CK(cudaEventRecord(h->ev[0], s));
+    for (int l = h->depth; l >= 1; --l) {
+      int rc = factor_level(h, l, s, pairs);
+      if (rc) return rc;
+    }
+    int rc = assemble_and_lu(h, 0, s, pairs);
+    if (rc) return rc;
+    CK(cudaEventRecord(h->ev[1], s));
+    rc = read_status(h, s);
+    if (rc) return rc;
+    prof_collect(h);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
+    h->st.ms_factor = ms;
+    h->st.root_size = h->levels[0].boxes[0].size;
+  } catch (const std::bad_alloc&) {
+    return SYMHSS_ERR_NOMEM;
+  }
+  h->st.pairs_evaluated += pairs;
+  h->factored = true;
+  return SYMHSS_OK;
+}
+
+int symhss_rhs_plane_wave(symhss_t h, double angle, void* rhs, void* stream) {
+  if (!h || !rhs || !std::isfinite(angle)) return SYMHSS_ERR_INVALID;
+  PointTable t = table_of(h);
+  CK(launch_plane_wave(t.x, t.y, t.nx, t.ny, t.w, h->n, h->prm.k0, h->prm.eps0, angle,
+                       h->prm.mode == SYMHSS_SYM ? 1 : 0, reinterpret_cast<double2*>(rhs),
+                       (cudaStream_t)stream));
+  return SYMHSS_OK;
+}
+
+int symhss_solve(symhss_t h, const void* rhs, void* x, int nrhs, void* stream) {
+  if (!h || !rhs || !x || nrhs < 1) return SYMHSS_ERR_INVALID;
+  if (!h->factored) return SYMHSS_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n = h->n;
+  const double2* f = reinterpret_cast<const double2*>(rhs);
+  double2* xo = reinterpret_cast<double2*>(x);
+  try {
+    CK(cudaEventRecord(h->ev[0], s));
+    // up pass
+    for (int l = h->depth; l >= 0; --l) {
+      Level& L = h->levels[l];
+      auto& boxes = L.boxes;
+      long long g_total = 0, ft_total = 0;
+      for (auto& bx : boxes) {
+        bx.g_off = g_total;
+        g_total += (long long)bx.size * nrhs;
+        bx.ft_off = ft_total;
+        ft_total += (long long)(l > 0 ? bx.k : 0) * nrhs;
+      }
+      CK(L.G.ensure(g_total * sizeof(double2)));
+      CK(L.FT.ensure(ft_total * sizeof(double2)));
+      CK(L.TMP.ensure(ft_total * sizeof(double2)));
+      Packer pk;
+      std::vector<LeafJob> lj;
+      std::vector<CopyJob> cj;
+      std::vector<RsJob> rs;
+      std::vector<BasisJob> bj;
+      std::vector<GemmJob> gj;
+      int max_n = 1, max_k = 1;
+      for (auto& bx : boxes) {
+        if (l == h->depth) {
+          lj.push_back(LeafJob{bx.g_off, bx.begin, bx.end - bx.begin});
+        } else {
+          const HBox& c1 = h->levels[l + 1].boxes[bx.child[0]];
+          const HBox& c2 = h->levels[l + 1].boxes[bx.child[1]];
+          CopyJob c;
+          c.src_off = c1.ft_off; c.dst_off = bx.g_off; c.rows = c1.k; c.cols = nrhs; c.lds = c1.k; c.ldd = bx.size;
+          cj.push_back(c);
+          c.src_off = c2.ft_off; c.dst_off = bx.g_off + c1.k; c.rows = c2.k; c.lds = c2.k;
+          cj.push_back(c);
+        }
+        RsJob r;
+        r.a_off = bx.d_off; r.n = bx.size; r.lda = bx.size; r.piv_off = bx.piv_off;
+        r.b_off = bx.g_off; r.ldb = bx.size; r.nrhs = nrhs;
+        rs.push_back(r);
+        max_n = std::max(max_n, bx.size);
+        if (l > 0) {
+          BasisJob b{};
+          for (int p = 0; p < 2; ++p) {
+            b.part[p].q_off = bx.q_off[p]; b.part[p].t_off = bx.t_off[p];
+            b.part[p].n = (int)bx.perm[p].size(); b.part[p].r = bx.rank[p];
+            b.part[p].col0 = p == 0 ? 0 : bx.rank[0];
+          }
+          b.size = bx.size; b.k = bx.k;
+          b.in_off = bx.g_off; b.ld_in = bx.size; b.out_off = bx.ft_off; b.ld_out = bx.k; b.ncols = nrhs;
+          bj.push_back(b);
+          GemmJob gmm;
+          gmm.a_off = bx.rx_off; gmm.lda = bx.k;
+          gmm.b_off = bx.ft_off; gmm.ldb = bx.k;
+          gmm.c_off = bx.ft_off; gmm.ldc = bx.k;
+          gmm.m = bx.k; gmm.n = nrhs; gmm.k = bx.k; gmm.alpha = 1.0; gmm.beta = 0.0;
+          gj.push_back(gmm);
+          max_k = std::max(max_k, bx.k);
+        }
+      }
+      const size_t olj = pk.add(lj), ocj = pk.add(cj), ors = pk.add(rs), obj = pk.add(bj), ogj = pk.add(gj);
+      CK(pk.upload(L.slists, s));
+      char* sb = L.slists.as<char>();
+      if (l == h->depth)
+        TIMED(SYMHSS_K_OTHER, 0.0, launch_leaf_gather(f, 2 * n, L.G.as<double2>(),
+                                                      reinterpret_cast<const LeafJob*>(sb + olj), (int)lj.size(),
+                                                      nrhs, n, s));
+      else
+        TIMED(SYMHSS_K_OTHER, 0.0, launch_copy_blocks(h->levels[l + 1].FT.as<double2>(), L.G.as<double2>(),
+                                                      reinterpret_cast<const CopyJob*>(sb + ocj), (int)cj.size(),
+                                                      s));
+      double w_g = 0, w_up = 0;
+      for (auto& bx : boxes) {
+        w_g += 8.0 * (double)bx.size * bx.size * nrhs;
+        if (l > 0) w_up += 8.0 * (double)bx.k * (double)(bx.perm[0].size() + bx.perm[1].size() + bx.k) * nrhs;
+      }
+      RsLaunch ra;
+      ra.abase = L.D.as<double2>(); ra.piv = L.piv.as<int>(); ra.bbase = L.G.as<double2>();
+      ra.jobs = reinterpret_cast<const RsJob*>(sb + ors); ra.njobs = (int)rs.size();
+      ra.max_rhs = nrhs; ra.max_n = max_n;
+      TIMED(SYMHSS_K_GETRS, w_g, launch_getrs(ra, s));
+      if (l > 0) {
+        // tmp = R g ; f~ = Atilde tmp
+        BasisLaunch ba;
+        ba.q = reinterpret_cast<const int*>(L.qbuf.p);
+        ba.T = L.tbuf.as<double2>();
+        ba.in = L.G.as<double2>();
+        ba.out = L.TMP.as<double2>();
+        ba.jobs = reinterpret_cast<const BasisJob*>(sb + obj);
+        ba.njobs = (int)bj.size();
+        ba.max_cols = nrhs;
+        TIMED(SYMHSS_K_OTHER, w_up, launch_apply_r(ba, s));
+        GemmLaunch ga;
+        ga.A = L.At.as<double2>(); ga.B = L.TMP.as<double2>(); ga.C = L.FT.as<double2>();
+        ga.jobs = reinterpret_cast<const GemmJob*>(sb + ogj); ga.njobs = (int)gj.size();
+        TIMED(SYMHSS_K_OTHER, 0.0, launch_gemm(ga, s));
+      }
+    }
+    // down pass: x_c = g_c - X_c (f~_c - Atilde_c y_c)
+    for (int l = 1; l <= h->depth; ++l) {
+      Level& L = h->levels[l];
+      Level& LP = h->levels[l - 1];
+      std::vector<GemmJob> g1, g2;
+      for (auto& par : LP.boxes) {
+        int row0 = 0;
+        for (int c = 0; c < 2; ++c) {
+          HBox& bx = L.boxes[par.child[c]];
+          GemmJob a;
+          a.a_off = bx.rx_off; a.lda = bx.k;
+          a.b_off = par.g_off + row0; a.ldb = par.size;
+          a.c_off = bx.ft_off; a.ldc = bx.k;
+          a.m = bx.k; a.n = nrhs; a.k = bx.k; a.alpha = -1.0; a.beta = 1.0;
+          g1.push_back(a);
+          GemmJob b;
+          b.a_off = bx.x_off; b.lda = bx.size;
+          b.b_off = bx.ft_off; b.ldb = bx.k;
+          b.c_off = bx.g_off; b.ldc = bx.size;
+          b.m = bx.size; b.n = nrhs; b.k = bx.k; b.alpha = -1.0; b.beta = 1.0;
+          g2.push_back(b);
+          row0 += bx.k;
+        }
+      }
+      Packer pk;
+      const size_t o1 = pk.add(g1), o2 = pk.add(g2);
+      CK(pk.upload(L.slists, s));
+      char* sb = L.slists.as<char>();
+      GemmLaunch ga;
+      ga.A = L.At.as<double2>(); ga.B = LP.G.as<double2>(); ga.C = L.FT.as<double2>();
+      ga.jobs = reinterpret_cast<const GemmJob*>(sb + o1); ga.njobs = (int)g1.size();
+      double w_dn = 0;
+      for (const auto& j : g1) w_dn += 8.0 * (double)j.m * j.n * j.k;
+      for (const auto& j : g2) w_dn += 8.0 * (double)j.m * j.n * j.k;
+      TIMED(SYMHSS_K_OTHER, w_dn, launch_gemm(ga, s));
+      GemmLaunch gb;
+      gb.A = L.X.as<double2>(); gb.B = L.FT.as<double2>(); gb.C = L.G.as<double2>();
+      gb.jobs = reinterpret_cast<const GemmJob*>(sb + o2); gb.njobs = (int)g2.size();
+      TIMED(SYMHSS_K_OTHER, 0.0, launch_gemm(gb, s));
+    }
+    {
+      Level& L = h->levels[h->depth];
+      std::vector<LeafJob> lj;
+      for (auto& bx : L.boxes) lj.push_back(LeafJob{bx.g_off, bx.begin, bx.end - bx.begin});
+      Packer pk;
+      const size_t o = pk.add(lj);
+      CK(pk.upload(h->levels[0].slists, s));
+      TIMED(SYMHSS_K_OTHER, 0.0, launch_leaf_scatter(L.G.as<double2>(), xo, 2 * n,
+                             reinterpret_cast<const LeafJob*>(h->levels[0].slists.as<char>() + o),
+                             (int)lj.size(), nrhs, n, s));
+    }
+    CK(cudaEventRecord(h->ev[1], s));
+    int rc = read_status(h, s);
+    if (rc) return rc;
+    prof_collect(h);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
+    h->st.ms_solve = ms;
+  } catch (const std::bad_alloc&) {
+    return SYMHSS_ERR_NOMEM;
+  }
+  return SYMHSS_OK;
+}
+
+int symhss_solve_host(symhss_t h, const void* rhs_host, void* x_host, int nrhs, void* stream) {
+  if (!h || !rhs_host || !x_host || nrhs < 1) return SYMHSS_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = (size_t)2 * h->n * nrhs * sizeof(double2);
+  CK(h->xin.ensure(bytes));
+  CK(h->xout.ensure(bytes));
+  CK(cudaMemcpyAsync(h->xin.p, rhs_host, bytes, cudaMemcpyHostToDevice, s));
+  int rc = symhss_solve(h, h->xin.p, h->xout.p, nrhs, stream);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(x_host, h->xout.p, bytes, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return SYMHSS_OK;
+}
+
+int symhss_stats(symhss_t h, symhss_stats_t* out) {
+  if (!h || !out) return SYMHSS_ERR_INVALID;
+  long long bytes = (long long)h->pts.cap + (long long)h->status.cap + h->xin.cap + h->xout.cap;
+  for (auto& L : h->levels) {
+    for (DevBuf* b : {&L.mr, &L.tbuf, &L.permbuf, &L.rankbuf, &L.refbuf, &L.clists, &L.idjobs, &L.D, &L.piv,
+                      &L.rxpiv, &L.info, &L.X, &L.RX, &L.At, &L.qbuf, &L.flists, &L.lujobs, &L.cjobs, &L.G,
+                      &L.FT, &L.TMP, &L.slists})
+      bytes += (long long)b->cap;
+  }
+  h->st.device_bytes = bytes;
+  h->st.ms_lu = 0;
+  *out = h->st;
+  return SYMHSS_OK;
+}
+
+int symhss_level_ranks(symhss_t h, int level, int* out) {
+  if (!h || !out || level < 1 || level > h->depth) return SYMHSS_ERR_INVALID;
+  if (!h->compressed) return SYMHSS_ERR_STATE;
+  auto& bxs = h->levels[level].boxes;
+  for (size_t b = 0; b < bxs.size(); ++b) {
+    out[2 * b] = bxs[b].rank[0];
+    out[2 * b + 1] = bxs[b].rank[1];
+  }
+  return SYMHSS_OK;
+}
+
+int symhss_destroy(symhss_t h) {
+  if (!h) return SYMHSS_OK;
+  for (auto& e : h->ev)
+    if (e) cudaEventDestroy(e);
+  for (auto& e : h->evpool) cudaEventDestroy(e);
+  delete h;
+  return SYMHSS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,220 @@
+"""ctypes binding of libsymhss.so (C ABI in include/symhss.h).
+
+Argument marshalling only: every step of the solver runs in the library's CUDA
+kernels.  Device buffers are passed as raw pointers (e.g. ``tensor.data_ptr()``
+of a torch tensor on ``cuda:0``), streams as ``torch.cuda.current_stream().cuda_stream``.
+There is no fallback: if the library is missing, importing this module raises.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsymhss.so")
+
+SYMHSS_OK = 0
+SYMHSS_ERR_INVALID = -1
+SYMHSS_ERR_NOMEM = -2
+SYMHSS_ERR_CUDA = -3
+SYMHSS_ERR_RANK_OVERFLOW = -4
+SYMHSS_ERR_SINGULAR = -5
+SYMHSS_ERR_TIMEOUT = -6
+SYMHSS_ERR_STATE = -7
+SYMHSS_ERR_DEVICE = -8
+
+SYMHSS_SYM = 0
+SYMHSS_NONSYM = 1
+SYMHSS_FP64 = 0
+SYMHSS_HOST = 0
+SYMHSS_DEVICE = 1
+SYMHSS_MAX_LEVELS = 32
+K_TILES, K_ID, K_GETRF, K_GETRS, K_OTHER = 0, 1, 2, 3, 4
+K_NAMES = ["tiles", "id", "getrf", "getrs", "other"]
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int)
+
+
+class symhss_curve(C.Structure):
+    _fields_ = [("n", C.c_int), ("x", C.c_void_p), ("y", C.c_void_p), ("nx", C.c_void_p),
+                ("ny", C.c_void_p), ("w", C.c_void_p), ("kappa", C.c_void_p), ("location", C.c_int)]
+
+
+class symhss_params(C.Structure):
+    _fields_ = [("k0", C.c_double), ("k1", C.c_double), ("eps0", C.c_double), ("eps1", C.c_double),
+                ("tol", C.c_double), ("leaf", C.c_int), ("nproxy", C.c_int), ("proxy_factor", C.c_double),
+                ("mode", C.c_int), ("precision", C.c_int), ("fixed_rank_kL", C.c_int),
+                ("rank_scale_a", C.c_double), ("oversample", C.c_int), ("reserved", C.c_int),
+                ("seed", C.c_uint64)]
+
+
+class symhss_stats_t(C.Structure):
+    _fields_ = [("n", C.c_int), ("depth", C.c_int), ("nboxes_leaf", C.c_int), ("root_size", C.c_int),
+                ("max_rank", C.c_int * 2), ("level_max_rank", (C.c_int * 2) * SYMHSS_MAX_LEVELS),
+                ("level_mean_rank", (C.c_double * 2) * SYMHSS_MAX_LEVELS),
+                ("level_nproxy", C.c_int * SYMHSS_MAX_LEVELS),
+                ("ms_compress", C.c_double), ("ms_factor", C.c_double), ("ms_solve", C.c_double),
+                ("ms_tiles", C.c_double), ("ms_id", C.c_double), ("ms_lu", C.c_double),
+                ("ms_basis", C.c_double), ("pairs_evaluated", C.c_longlong), ("id_count", C.c_longlong),
+                ("flops_lu", C.c_double), ("flops_id", C.c_double), ("device_bytes", C.c_longlong),
+                ("kernel_ms", C.c_double * 8), ("kernel_launches", C.c_longlong * 8),
+                ("kernel_work", C.c_double * 8)]
+
+
+class symhss_points(C.Structure):
+    _fields_ = [("n", C.c_int), ("x", C.c_void_p), ("y", C.c_void_p), ("nx", C.c_void_p),
+                ("ny", C.c_void_p), ("w", C.c_void_p), ("kappa", C.c_void_p), ("id", C.c_void_p)]
+
+
+# (name, restype, argtypes) of every exported symbol
+_SIGNATURES = [
+    ("symhss_strerror", C.c_char_p, [C.c_int]),
+    ("symhss_params_default", C.c_int, [C.POINTER(symhss_params)]),
+    ("symhss_create", C.c_int, [C.POINTER(symhss_curve), C.POINTER(symhss_params), C.c_void_p,
+                                C.POINTER(C.c_void_p)]),
+    ("symhss_set_curve", C.c_int, [C.c_void_p, C.POINTER(symhss_curve), C.c_void_p]),
+    ("symhss_compress", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("symhss_factor", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("symhss_rhs_plane_wave", C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p]),
+    ("symhss_solve", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    ("symhss_solve_host", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    ("symhss_stats", C.c_int, [C.c_void_p, C.POINTER(symhss_stats_t)]),
+    ("symhss_level_ranks", C.c_int, [C.c_void_p, C.c_int, _ip]),
+    ("symhss_destroy", C.c_int, [C.c_void_p]),
+    ("symhss_hankel01", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    ("symhss_kernel_block", C.c_int, [C.POINTER(symhss_params), C.POINTER(symhss_points), C.c_void_p,
+                                      C.POINTER(symhss_points), C.c_void_p, C.c_int, C.c_void_p, C.c_int,
+                                      C.c_void_p]),
+    ("symhss_column_id", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_longlong, C.c_int, C.c_double,
+                                   C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p]),
+    ("symhss_lu_batched", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_longlong, C.c_int, C.c_void_p,
+                                    C.c_void_p, C.c_void_p]),
+    ("symhss_lu_solve_batched", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_longlong, C.c_void_p, C.c_void_p,
+                                          C.c_int, C.c_int, C.c_longlong, C.c_int, C.c_void_p]),
+]
+
+SYMBOLS = [s[0] for s in _SIGNATURES]
+
+
+def _load() -> C.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built: run `python -m paper_2609_33216_b300.build`")
+    lib = C.CDLL(LIB_PATH)
+    for name, res, args in _SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+class SymhssError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {lib.symhss_strerror(code).decode()} ({code})")
+
+
+def check(code: int, what: str = "symhss") -> None:
+    if code != SYMHSS_OK:
+        raise SymhssError(code, what)
+
+
+def params(k0: float, k1: float, eps0: float = 1.0, eps1: float = 1.0, **kw) -> symhss_params:
+    """Default parameters with the given wavenumbers / materials and field overrides."""
+    p = symhss_params()
+    check(lib.symhss_params_default(C.byref(p)), "symhss_params_default")
+    p.k0, p.k1, p.eps0, p.eps1 = k0, k1, eps0, eps1
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def curve_struct(n: int, ptrs, location: int) -> symhss_curve:
+    """ptrs: six pointers (x, y, nx, ny, w, kappa) as ints."""
+    return symhss_curve(n, *[C.c_void_p(int(p)) for p in ptrs], location)
+
+
+def symhss_create(curve: symhss_curve, prm: symhss_params, stream: int = 0) -> C.c_void_p:
+    h = C.c_void_p()
+    check(lib.symhss_create(C.byref(curve), C.byref(prm), C.c_void_p(stream), C.byref(h)), "symhss_create")
+    return h
+
+
+def symhss_set_curve(h, curve: symhss_curve, stream: int = 0) -> None:
+    check(lib.symhss_set_curve(h, C.byref(curve), C.c_void_p(stream)), "symhss_set_curve")
+
+
+def symhss_compress(h, stream: int = 0) -> None:
+    check(lib.symhss_compress(h, C.c_void_p(stream)), "symhss_compress")
+
+
+def symhss_factor(h, stream: int = 0) -> None:
+    check(lib.symhss_factor(h, C.c_void_p(stream)), "symhss_factor")
+
+
+def symhss_rhs_plane_wave(h, angle: float, rhs_ptr: int, stream: int = 0) -> None:
+    check(lib.symhss_rhs_plane_wave(h, angle, C.c_void_p(rhs_ptr), C.c_void_p(stream)), "symhss_rhs_plane_wave")
+
+
+def symhss_solve(h, rhs_ptr: int, x_ptr: int, nrhs: int = 1, stream: int = 0) -> None:
+    check(lib.symhss_solve(h, C.c_void_p(rhs_ptr), C.c_void_p(x_ptr), nrhs, C.c_void_p(stream)), "symhss_solve")
+
+
+def symhss_solve_host(h, rhs_ptr: int, x_ptr: int, nrhs: int = 1, stream: int = 0) -> None:
+    check(lib.symhss_solve_host(h, C.c_void_p(rhs_ptr), C.c_void_p(x_ptr), nrhs, C.c_void_p(stream)),
+          "symhss_solve_host")
+
+
+def symhss_stats(h) -> symhss_stats_t:
+    st = symhss_stats_t()
+    check(lib.symhss_stats(h, C.byref(st)), "symhss_stats")
+    return st
+
+
+def symhss_level_ranks(h, level: int):
+    out = (C.c_int * (2 * (1 << level)))()
+    check(lib.symhss_level_ranks(h, level, out), "symhss_level_ranks")
+    return [(out[2 * b], out[2 * b + 1]) for b in range(1 << level)]
+
+
+def symhss_destroy(h) -> None:
+    check(lib.symhss_destroy(h), "symhss_destroy")
+
+
+def symhss_hankel01(x_ptr: int, n: int, out_ptr: int, stream: int = 0) -> None:
+    check(lib.symhss_hankel01(C.c_void_p(x_ptr), n, C.c_void_p(out_ptr), C.c_void_p(stream)), "symhss_hankel01")
+
+
+def points_struct(n: int, ptrs, id_ptr: int) -> symhss_points:
+    return symhss_points(n, *[C.c_void_p(int(p)) for p in ptrs], C.c_void_p(int(id_ptr)))
+
+
+def symhss_kernel_block(prm: symhss_params, obs: symhss_points, obs_eq: int, src: symhss_points, src_comp: int,
+                        scaled: bool, out: int, ld: int, stream: int = 0) -> None:
+    check(lib.symhss_kernel_block(C.byref(prm), C.byref(obs), C.c_void_p(obs_eq), C.byref(src),
+                                  C.c_void_p(src_comp), int(bool(scaled)), C.c_void_p(out), ld,
+                                  C.c_void_p(stream)), "symhss_kernel_block")
+
+
+def symhss_column_id(a: int, m: int, n: int, lda: int, stride_a: int, batch: int, tol: float, fixed_rank: int,
+                     rank: int, perm: int, t: int, stride_t: int, stream: int = 0) -> None:
+    check(lib.symhss_column_id(C.c_void_p(a), m, n, lda, stride_a, batch, tol, fixed_rank, C.c_void_p(rank),
+                               C.c_void_p(perm), C.c_void_p(t), stride_t, C.c_void_p(stream)), "symhss_column_id")
+
+
+def symhss_lu_batched(a: int, n: int, lda: int, stride_a: int, batch: int, ipiv: int, info: int,
+                      stream: int = 0) -> None:
+    check(lib.symhss_lu_batched(C.c_void_p(a), n, lda, stride_a, batch, C.c_void_p(ipiv), C.c_void_p(info),
+                                C.c_void_p(stream)), "symhss_lu_batched")
+
+
+def symhss_lu_solve_batched(lu: int, n: int, lda: int, stride_a: int, ipiv: int, b: int, nrhs: int, ldb: int,
+                            stride_b: int, batch: int, stream: int = 0) -> None:
+    check(lib.symhss_lu_solve_batched(C.c_void_p(lu), n, lda, stride_a, C.c_void_p(ipiv), C.c_void_p(b), nrhs,
+                                      ldb, stride_b, batch, C.c_void_p(stream)), "symhss_lu_solve_batched")

@@ -1,0 +1,53 @@
+"""The C-ABI library loads without a GPU and exports every symbol include/symhss.h declares;
+host-side argument validation rejects bad input before touching the device."""
+
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "symhss.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(symhss_[a-z_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2609_33216_b300 import symhss as S
+    names = _declared()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(S.lib, name), name
+    assert set(names) <= set(S.SYMBOLS)
+
+
+def test_struct_sizes_match_header_layout():
+    from paper_2609_33216_b300 import symhss as S
+    # params: 5 doubles, 2 ints, 1 double, 3 ints (+pad), 1 double, 2 ints, uint64
+    assert C.sizeof(S.symhss_params) == 96
+    assert C.sizeof(S.symhss_curve) == 4 + 4 + 6 * 8 + 8
+
+
+def test_invalid_arguments_rejected_on_host():
+    from paper_2609_33216_b300 import symhss as S
+    import numpy as np
+    n = 64
+    arrs = [np.ones(n) for _ in range(6)]
+    cs = S.curve_struct(n, [a.ctypes.data for a in arrs], S.SYMHSS_HOST)
+    h = C.c_void_p()
+    for bad in (dict(k0=-1.0), dict(tol=-1.0), dict(leaf=0), dict(nproxy=4), dict(proxy_factor=1.0),
+                dict(mode=7), dict(precision=3), dict(fixed_rank_kL=-2), dict(eps1=float("nan"))):
+        kw = dict(k0=1.0, k1=2.0)
+        kw.update(bad)
+        p = S.params(kw.pop("k0"), kw.pop("k1"), **kw)
+        assert S.lib.symhss_create(C.byref(cs), C.byref(p), None, C.byref(h)) == S.SYMHSS_ERR_INVALID
+    assert S.lib.symhss_create(None, None, None, C.byref(h)) == S.SYMHSS_ERR_INVALID
+    assert S.lib.symhss_compress(None, None) == S.SYMHSS_ERR_INVALID
+    assert S.lib.symhss_destroy(None) == S.SYMHSS_OK
+    assert S.lib.symhss_strerror(S.SYMHSS_ERR_SINGULAR) == b"singular diagonal block"
+    assert S.lib.symhss_column_id(None, 4, 4, 2, 16, 1, 1e-3, -1, None, None, None, 4, None) == S.SYMHSS_ERR_INVALID
+    assert S.lib.symhss_lu_batched(None, 4, 2, 16, 1, None, None, None) == S.SYMHSS_ERR_INVALID
