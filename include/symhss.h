@@ -210,6 +210,23 @@ int symhss_kernel_block(const symhss_params* prm, const symhss_points* obs, cons
 int symhss_column_id(void* A, int m, int n, int lda, long long strideA, int batch, double tol,
                      int fixed_rank, int* rank, int* perm, void* T, long long strideT, void* stream);
 
+/* symhss_column_id for callers that cannot allocate device memory: same
+ * arguments, results and errors, but no cudaMalloc / cudaFree (or any other
+ * allocating call) is made.  Such callers are, e.g., code running under a fixed
+ * device-memory budget or inside an allocator it does not own, and latency-
+ * critical loops that cannot afford the implicit device-wide synchronisation of
+ * cudaMalloc / cudaFree.  The scratch it needs (job descriptors, reference norms,
+ * a status word) lives in one library-owned __device__ array sized for at most
+ * 4096 matrices per call, which every GPU that loads the library keeps until the
+ * process exits; batch > 4096 returns SYMHSS_ERR_INVALID.  The first call on a
+ * device looks up that array's device address with the device current, so make
+ * it before any stream capture begins.  Every call reuses the same array: calls
+ * whose GPU work overlaps (unordered streams or host threads) race and must not
+ * be issued.  This entry point is an engineering addition with no counterpart in
+ * the paper. */
+int symhss_column_id_noalloc(void* A, int m, int n, int lda, long long strideA, int batch, double tol,
+                             int fixed_rank, int* rank, int* perm, void* T, long long strideT, void* stream);
+
 /* Batched LU with partial pivoting of n x n complex128 matrices A + b*strideA
  * (leading dimension lda; overwritten by L\U), pivots ipiv + b*n (0-based row
  * swapped with row k at step k), info[b] = 0 or k+1 for the first zero pivot. */

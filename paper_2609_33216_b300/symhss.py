@@ -89,6 +89,9 @@ _SIGNATURES = [
                                       C.c_void_p]),
     ("symhss_column_id", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_longlong, C.c_int, C.c_double,
                                    C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p]),
+    ("symhss_column_id_noalloc", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_longlong, C.c_int,
+                                           C.c_double, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_longlong,
+                                           C.c_void_p]),
     ("symhss_lu_batched", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_longlong, C.c_int, C.c_void_p,
                                     C.c_void_p, C.c_void_p]),
     ("symhss_lu_solve_batched", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_longlong, C.c_void_p, C.c_void_p,
@@ -206,6 +209,13 @@ def symhss_column_id(a: int, m: int, n: int, lda: int, stride_a: int, batch: int
                      rank: int, perm: int, t: int, stride_t: int, stream: int = 0) -> None:
     check(lib.symhss_column_id(C.c_void_p(a), m, n, lda, stride_a, batch, tol, fixed_rank, C.c_void_p(rank),
                                C.c_void_p(perm), C.c_void_p(t), stride_t, C.c_void_p(stream)), "symhss_column_id")
+
+
+def symhss_column_id_noalloc(a: int, m: int, n: int, lda: int, stride_a: int, batch: int, tol: float,
+                             fixed_rank: int, rank: int, perm: int, t: int, stride_t: int, stream: int = 0) -> None:
+    check(lib.symhss_column_id_noalloc(C.c_void_p(a), m, n, lda, stride_a, batch, tol, fixed_rank, C.c_void_p(rank),
+                                       C.c_void_p(perm), C.c_void_p(t), stride_t, C.c_void_p(stream)),
+          "symhss_column_id_noalloc")
 
 
 def symhss_lu_batched(a: int, n: int, lda: int, stride_a: int, batch: int, ipiv: int, info: int,
