@@ -157,25 +157,23 @@ __global__ void __launch_bounds__(kThreads) cpqr_kernel(const IdLaunch a) {
     a.ref[jb.out_idx] = ref < 0.0 ? 0.0 : ref;
   }
   for (int j = tid; j < n; j += kThreads) perm_out[j] = sperm[j];
-  // T = R11^{-1} R12 (r x (n - r), leading dimension r)
-  if (r > 0 && r < n) {
-    double2* inv = vbuf;  // r <= min(m, n) <= max_m
-    for (int i = tid; i < r; i += kThreads) inv[i] = cinv(M[i + (long long)i * ld]);
-    __syncthreads();
-    double2* T = a.tbuf + jb.t_off;
-    for (int j = r + warp; j < n; j += kWarps) {
-      double2* t = T + (long long)(j - r) * r;
-      const double2* col = M + (long long)j * ld;
-      for (int i = lane; i < r; i += 32) t[i] = col[i];
+  // T = R11^{-1} R12 (r x (n - r), leading dimension r); barriers stay unconditional
+  double2* inv = vbuf;  // r <= min(m, n) <= max_m
+  for (int i = tid; i < r; i += kThreads) inv[i] = cinv(M[i + (long long)i * ld]);
+  __syncthreads();
+  double2* T = a.tbuf + jb.t_off;
+  for (int j = r + warp; r > 0 && j < n; j += kWarps) {
+    double2* t = T + (long long)(j - r) * r;
+    const double2* col = M + (long long)j * ld;
+    for (int i = lane; i < r; i += 32) t[i] = col[i];
+    __syncwarp();
+    for (int i = r - 1; i >= 0; --i) {
+      const double2 ti = cmul(t[i], inv[i]);
       __syncwarp();
-      for (int i = r - 1; i >= 0; --i) {
-        const double2 ti = cmul(t[i], inv[i]);
-        __syncwarp();
-        if (lane == 0) t[i] = ti;
-        const double2* ri = M + (long long)i * ld;
-        for (int l = lane; l < i; l += 32) t[l] = cfms(ri[l], ti, t[l]);
-        __syncwarp();
-      }
+      if (lane == 0) t[i] = ti;
+      const double2* ri = M + (long long)i * ld;
+      for (int l = lane; l < i; l += 32) t[l] = cfms(ri[l], ti, t[l]);
+      __syncwarp();
     }
   }
 }

@@ -1,0 +1,199 @@
+// Batched blocked LU with partial pivoting (the diagonal-block factorisations of
+// Sec. 4.2), right-looking with panel width kNb.  All matrices of a batch advance
+// panel by panel in lock step; every panel step is three launches whose work
+// spreads over many thread blocks even when the batch holds a single matrix (the
+// root block):
+//   1. panel: one block per matrix factors columns [j, j + w) of rows [j, n) with
+//      partial pivoting (swaps applied inside the panel only);
+//   2. swaps + TRSM: one thread per column outside the panel applies the panel's
+//      row interchanges and, right of the panel, solves L11 U12 = A12;
+//   3. trailing update: A22 -= L21 U12 in 32 x 32 tiles, one block per tile.
+// The pivots follow the LAPACK convention (row ipiv[k] was swapped with row k at
+// step k), so the result is interchangeable with the unblocked factorisation.
+#include "common.cuh"
+
+namespace symhss {
+
+namespace {
+
+constexpr int kNb = 16;          // panel width
+constexpr int kPanelThreads = 256;
+constexpr int kPanelWarps = kPanelThreads / 32;
+constexpr int kTs = 32;          // trailing-update tile
+constexpr int kSwapThreads = 128;
+
+__global__ void __launch_bounds__(kPanelThreads) panel_kernel(const LuLaunch a, int j) {
+  __shared__ double red[kPanelWarps];
+  __shared__ int redi[kPanelWarps];
+  __shared__ int s_piv;
+  __shared__ double s_pv;
+  __shared__ double2 s_row[kNb];
+  const LuJob jb = a.jobs[blockIdx.x];
+  const int n = jb.n, ld = jb.ld;
+  if (j >= n) return;
+  const int w = min(kNb, n - j);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double2* A = a.base + jb.a_off;
+  int* piv = a.piv + jb.piv_off;
+  for (int c = 0; c < w; ++c) {
+    const int jc = j + c;
+    const double2* col = A + (long long)jc * ld;
+    double bv = -1.0;
+    int bi = n;
+    for (int i = jc + tid; i < n; i += kPanelThreads) {
+      const double v = cabs1(col[i]);
+      if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
+    }
+    warp_argmax(bv, bi);
+    if (lane == 0) { red[warp] = bv; redi[warp] = bi; }
+    __syncthreads();
+    if (warp == 0) {
+      bv = lane < kPanelWarps ? red[lane] : -1.0;
+      bi = lane < kPanelWarps ? redi[lane] : n;
+      warp_argmax(bv, bi);
+      if (lane == 0) { s_piv = bi; s_pv = bv; }
+    }
+    __syncthreads();
+    const int p = s_piv;
+    if (tid == 0) {
+      piv[jc] = p;
+      if (s_pv == 0.0) {
+        if (a.info[jb.info_idx] == 0) a.info[jb.info_idx] = jc + 1;
+        atomicOr(a.status, ST_SINGULAR);
+      }
+    }
+    // an exactly zero pivot column skips the step; every barrier stays unconditional
+    const bool zero = (s_pv == 0.0);
+    if (!zero && tid < w && p != jc) {
+      double2* cc = A + (long long)(j + tid) * ld;
+      const double2 t = cc[jc];
+      cc[jc] = cc[p];
+      cc[p] = t;
+    }
+    __syncthreads();
+    if (tid < w) s_row[tid] = A[jc + (long long)(j + tid) * ld];
+    __syncthreads();
+    const double2 inv = zero ? make_double2(0.0, 0.0) : cinv(s_row[c]);
+    for (int i = jc + 1 + tid; !zero && i < n; i += kPanelThreads) {
+      const double2 l = cmul(A[i + (long long)jc * ld], inv);
+      A[i + (long long)jc * ld] = l;
+      for (int q = c + 1; q < w; ++q) {
+        double2* cq = A + (long long)(j + q) * ld;
+        cq[i] = cfms(l, s_row[q], cq[i]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kSwapThreads) swap_trsm_kernel(const LuLaunch a, int j) {
+  __shared__ double2 l11[kNb][kNb];
+  __shared__ int sp[kNb];
+  const LuJob jb = a.jobs[blockIdx.x];
+  const int n = jb.n, ld = jb.ld;
+  if (j >= n) return;
+  const int w = min(kNb, n - j);
+  double2* A = a.base + jb.a_off;
+  const int* piv = a.piv + jb.piv_off;
+  for (int e = threadIdx.x; e < w * w; e += kSwapThreads) {
+    const int r = e % w, c = e / w;
+    l11[r][c] = A[j + r + (long long)(j + c) * ld];
+  }
+  if (threadIdx.x < w) sp[threadIdx.x] = piv[j + threadIdx.x];
+  __syncthreads();
+  const int col = blockIdx.y * kSwapThreads + threadIdx.x;
+  if (col >= n || (col >= j && col < j + w)) return;
+  double2* cc = A + (long long)col * ld;
+  for (int c = 0; c < w; ++c) {
+    const int p = sp[c];
+    if (p != j + c) {
+      const double2 t = cc[j + c];
+      cc[j + c] = cc[p];
+      cc[p] = t;
+    }
+  }
+  if (col < j + w) return;
+  double2 x[kNb];
+#pragma unroll
+  for (int r = 0; r < kNb; ++r) x[r] = r < w ? cc[j + r] : make_double2(0.0, 0.0);
+#pragma unroll
+  for (int c = 0; c < kNb; ++c) {
+#pragma unroll
+    for (int r = c + 1; r < kNb; ++r) x[r] = cfms(l11[r][c], x[c], x[r]);
+  }
+#pragma unroll
+  for (int r = 0; r < kNb; ++r)
+    if (r < w) cc[j + r] = x[r];
+}
+
+// A22 -= L21 U12 for the tile (blockIdx.y, blockIdx.z) of every matrix
+__global__ void __launch_bounds__(256) update_kernel(const LuLaunch a, int j) {
+  __shared__ double2 at[kNb][kTs];      // L21 tile, transposed: at[c][r]
+  __shared__ double2 bt[kNb][kTs];      // U12 tile: bt[c][col]
+  const LuJob jb = a.jobs[blockIdx.x];
+  const int n = jb.n, ld = jb.ld;
+  const int w = min(kNb, n - j);
+  const int s = j + w;                   // first trailing row / column
+  const int r0 = s + blockIdx.y * kTs, c0 = s + blockIdx.z * kTs;
+  if (j >= n || r0 >= n || c0 >= n) return;
+  double2* A = a.base + jb.a_off;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < kNb * kTs; e += 256) {
+    const int r = e % kTs, c = e / kTs;
+    at[c][r] = (r0 + r < n && c < w) ? A[r0 + r + (long long)(j + c) * ld] : make_double2(0.0, 0.0);
+    const int cc = e % kNb, col = e / kNb;
+    bt[cc][col] = (c0 + col < n && cc < w) ? A[j + cc + (long long)(c0 + col) * ld] : make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  const int tx = tid & 31, ty = tid >> 5;  // row tx, columns ty + 8q
+  const int row = r0 + tx;
+  double2 acc[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int col = c0 + ty + 8 * q;
+    acc[q] = (row < n && col < n) ? A[row + (long long)col * ld] : make_double2(0.0, 0.0);
+  }
+#pragma unroll
+  for (int c = 0; c < kNb; ++c) {
+    const double2 l = at[c][tx];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] = cfms(l, bt[c][ty + 8 * q], acc[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int col = c0 + ty + 8 * q;
+    if (row < n && col < n) A[row + (long long)col * ld] = acc[q];
+  }
+}
+
+__global__ void zero_info_kernel(int* info, const LuJob* jobs, int njobs) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < njobs) info[jobs[b].info_idx] = 0;
+}
+
+}  // namespace
+
+cudaError_t launch_getrf(const LuLaunch& a, cudaStream_t s) {
+  if (a.njobs <= 0 || a.max_n <= 0) return cudaSuccess;
+  zero_info_kernel<<<(a.njobs + 127) / 128, 128, 0, s>>>(a.info, a.jobs, a.njobs);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int ncolblk = (a.max_n + kSwapThreads - 1) / kSwapThreads;
+  for (int j = 0; j < a.max_n; j += kNb) {
+    panel_kernel<<<a.njobs, kPanelThreads, 0, s>>>(a, j);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int rest = a.max_n - j - kNb;
+    if (rest <= 0) continue;
+    swap_trsm_kernel<<<dim3(a.njobs, ncolblk), kSwapThreads, 0, s>>>(a, j);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int tiles = (rest + kTs - 1) / kTs;
+    update_kernel<<<dim3(a.njobs, tiles, tiles), 256, 0, s>>>(a, j);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  // the last panel's interchanges still have to reach the columns left of it
+  const int jlast = ((a.max_n - 1) / kNb) * kNb;
+  swap_trsm_kernel<<<dim3(a.njobs, ncolblk), kSwapThreads, 0, s>>>(a, jlast);
+  return cudaGetLastError();
+}
+
+}  // namespace symhss
