@@ -1,21 +1,30 @@
 // Batched column interpolative decomposition by Householder QR with column
 // pivoting (Sec. 4.1: the ID of each half of the proxy matrix M_R).
 //
-// One thread block per matrix (8 warps).  The matrix stays in global memory
-// (it is L2-resident at these sizes); the Householder vector of the current step
-// is staged in shared memory.  Step k:
-//   1. pivot = column of largest remaining norm (ties to the lowest index);
-//   2. stop if that norm <= tol * (first pivot norm) (tolerance mode) or after
-//      `fixed` steps (fixed-rank mode);
-//   3. swap it to position k, build the reflector H = I - tau v v^H with
-//      H x = alpha e_1, |alpha| = |x|;
-//   4. apply H to every trailing column (one warp per column) and, in the same
-//      pass, recompute that column's remaining norm exactly.
+// Each matrix is factored by one thread-block cluster of C blocks (C = 1, 2, 4,
+// 8 or 16, chosen per launch so that few large IDs still occupy many SMs).  Block
+// `rank` of the cluster owns the columns j with j % C == rank; the matrix stays in
+// global memory (L2-resident) and columns are never moved: the pivot order is
+// kept in order[], and R(k, j) ends up at M(k, j).  Step k:
+//   1. every block proposes its owned, not yet chosen column of largest remaining
+//      norm; after a cluster barrier each block reads all proposals through
+//      distributed shared memory and takes the largest (ties to the lowest index);
+//   2. stop at the first pivot norm <= tol * (first pivot norm), or after `fixed`
+//      steps;
+//   3. the owner of the pivot column builds the reflector H = I - tau v v^H with
+//      H x = alpha e_1 in its shared memory; after a second cluster barrier the
+//      other blocks copy v and tau from it;
+//   4. every block applies H to its remaining columns (one warp per column) and,
+//      in the same pass, recomputes their remaining norms exactly.
 // Afterwards T = R11^{-1} R12 is obtained by back substitution, one warp per
-// column of R12.  The permutation and rank are written out; the matrix is left
-// holding R in its upper triangle, so a later launch can continue the
-// factorisation from step `start` (used to raise a rank to a prescribed value).
+// redundant column.  perm = [chosen columns in pivot order, remaining columns in
+// increasing index]; T's columns follow perm[r:].  A launch with start > 0 resumes
+// a factorisation left by an earlier launch (used to raise a rank).
+#include <cooperative_groups.h>
+
 #include "common.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace symhss {
 
@@ -23,6 +32,8 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
+
+struct Cand { double v; int i; };
 
 __device__ __forceinline__ double block_sum(double v, double* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -36,46 +47,62 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return s;
 }
 
-__global__ void __launch_bounds__(kThreads) cpqr_kernel(const IdLaunch a) {
+__global__ void __launch_bounds__(kThreads) cpqr_cluster_kernel(const IdLaunch a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const IdJob jb = a.jobs[blockIdx.x];
-  double2* vbuf = reinterpret_cast<double2*>(smem_raw);                 // max_m
-  double* norms = reinterpret_cast<double*>(vbuf + a.max_m);            // max_n
-  int* sperm = reinterpret_cast<int*>(norms + a.max_n);                 // max_n
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  const int job = blockIdx.x / C;
+  const IdJob jb = a.jobs[job];
+  double2* vbuf = reinterpret_cast<double2*>(smem_raw);           // max_m
+  double* norms = reinterpret_cast<double*>(vbuf + a.max_m);      // max_n (owned entries)
+  int* order = reinterpret_cast<int*>(norms + a.max_n);           // max_n
+  int* done = order + a.max_n;                                     // max_n: 1 = chosen
   __shared__ double red[kWarps];
   __shared__ int redi[kWarps];
-  __shared__ int s_piv;
-  __shared__ double s_pv, s_tau;
+  __shared__ Cand cand[2];
+  __shared__ double s_tau;
   __shared__ double2 s_alpha;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int m = jb.m, n = jb.n, ld = jb.ld;
-  if (m > a.max_m || n > a.max_n || m < 0 || n < 0) {
-    if (tid == 0) { atomicOr(a.status, ST_BAD_INDEX); a.rank[jb.out_idx] = 0; }
+  const bool bad = (m > a.max_m || n > a.max_n || m < 0 || n < 0 || jb.start < 0);
+  if (bad) {  // uniform over the cluster: every block of the job returns here
+    if (tid == 0 && rank == 0) { atomicOr(a.status, ST_BAD_INDEX); a.rank[jb.out_idx] = 0; }
     return;
   }
   double2* M = a.mats + jb.m_off;
   int* perm_out = a.perm + jb.perm_off;
-  for (int j = tid; j < n; j += kThreads) sperm[j] = (jb.start == 0) ? j : perm_out[j];
+  const int start = min(jb.start, min(m, n));
+  for (int j = tid; j < n; j += kThreads) done[j] = 0;
+  __syncthreads();
+  for (int i = tid; i < start; i += kThreads) {
+    const int q = perm_out[i];
+    order[i] = q;
+    if (q >= 0 && q < n) done[q] = 1;
+  }
+  __syncthreads();
   int kmax = min(m, n);
   if (jb.fixed >= 0) kmax = min(kmax, jb.fixed);
-  int k = jb.start;
-  // remaining norms of columns j >= k over rows k..m-1
-  for (int j = k + warp; j < n; j += kWarps) {
+  int k = start;
+  // remaining norms of owned columns over rows k..m-1
+  for (int j = rank + C * warp; j < n; j += C * kWarps) {
     const double2* col = M + (long long)j * ld;
     double s = 0.0;
     for (int i = k + lane; i < m; i += 32) s += cabs2(col[i]);
     s = warp_sum(s);
     if (lane == 0) norms[j] = sqrt(s);
   }
-  double ref = (jb.start == 0) ? -1.0 : a.ref[jb.out_idx];
+  double ref = (start == 0) ? -1.0 : a.ref[jb.out_idx];
   __syncthreads();
 
-  while (k < kmax) {
-    // 1. pivot
+  int par = 0;
+  while (true) {
+    // 1. local proposal
     double bv = -1.0;
     int bi = n;
-    for (int j = k + tid; j < n; j += kThreads) {
+    for (int j = rank + C * tid; j < n; j += C * kThreads) {
+      if (done[j]) continue;
       const double v = norms[j];
       if (v > bv || (v == bv && j < bi)) { bv = v; bi = j; }
     }
@@ -86,40 +113,33 @@ __global__ void __launch_bounds__(kThreads) cpqr_kernel(const IdLaunch a) {
       bv = lane < kWarps ? red[lane] : -1.0;
       bi = lane < kWarps ? redi[lane] : n;
       warp_argmax(bv, bi);
-      if (lane == 0) { s_piv = bi; s_pv = bv; }
+      if (lane == 0) cand[par] = Cand{bv, bi};
     }
-    __syncthreads();
-    const int p = s_piv;
-    const double pv = s_pv;
+    cl.sync();
+    double pv = -1.0;
+    int p = n;
+    for (int r = 0; r < C; ++r) {
+      const Cand c = *cl.map_shared_rank(&cand[par], r);
+      if (c.v > pv || (c.v == pv && c.i < p)) { pv = c.v; p = c.i; }
+    }
+    par ^= 1;
     if (ref < 0.0) ref = pv;
-    // 2. stop
-    if (pv == 0.0) break;
-    if (jb.fixed < 0 && pv <= a.tol * ref) break;
-    // 3. swap columns k and p
-    if (p != k) {
-      double2* ck = M + (long long)k * ld;
-      double2* cp = M + (long long)p * ld;
-      for (int i = tid; i < m; i += kThreads) {
-        const double2 t = ck[i];
-        ck[i] = cp[i];
-        cp[i] = t;
-      }
-      if (tid == 0) {
-        const double tn = norms[k]; norms[k] = norms[p]; norms[p] = tn;
-        const int tp = sperm[k]; sperm[k] = sperm[p]; sperm[p] = tp;
-      }
-    }
-    __syncthreads();
-    // Householder vector of column k, rows k..m-1
-    const double2* ck = M + (long long)k * ld;
+    // 2. stop (the same decision in every block of the cluster)
+    if (k >= kmax || p >= n || pv <= 0.0 || (jb.fixed < 0 && pv <= a.tol * ref)) break;
+    const int owner = p % C;
+    // 3. reflector, built by the owner (every block takes part in the reduction so
+    //    that no barrier sits in a branch)
     double s = 0.0;
-    for (int i = k + tid; i < m; i += kThreads) {
-      const double2 x = ck[i];
-      vbuf[i - k] = x;
-      s += cabs2(x);
+    if (rank == owner) {
+      const double2* cp = M + (long long)p * ld;
+      for (int i = k + tid; i < m; i += kThreads) {
+        const double2 x = cp[i];
+        vbuf[i - k] = x;
+        s += cabs2(x);
+      }
     }
     const double sigma2 = block_sum(s, red);
-    if (tid == 0) {
+    if (rank == owner && tid == 0) {
       const double sigma = sqrt(sigma2);
       const double2 x0 = vbuf[0];
       const double ax0 = sqrt(cabs2(x0));
@@ -129,10 +149,18 @@ __global__ void __launch_bounds__(kThreads) cpqr_kernel(const IdLaunch a) {
       const double vn2 = 2.0 * sigma * (sigma + ax0);
       s_tau = vn2 > 0.0 ? 2.0 / vn2 : 0.0;
     }
+    cl.sync();
+    if (rank != owner) {
+      const double2* rv = cl.map_shared_rank(vbuf, owner);
+      for (int i = tid; i < m - k; i += kThreads) vbuf[i] = rv[i];
+      if (tid == 0) s_tau = *cl.map_shared_rank(&s_tau, owner);
+    }
+    if (tid == 0) { done[p] = 1; order[k] = p; }
     __syncthreads();
     const double tau = s_tau;
-    // 4. apply to trailing columns, recompute their remaining norms
-    for (int j = k + 1 + warp; j < n; j += kWarps) {
+    // 4. apply to owned remaining columns, recompute their remaining norms
+    for (int j = rank + C * warp; j < n; j += C * kWarps) {
+      if (done[j]) continue;
       double2* col = M + (long long)j * ld;
       double2 w = make_double2(0.0, 0.0);
       for (int i = k + lane; i < m; i += 32) w = cadd(w, cconjmul(vbuf[i - k], col[i]));
@@ -147,23 +175,36 @@ __global__ void __launch_bounds__(kThreads) cpqr_kernel(const IdLaunch a) {
       ns = warp_sum(ns);
       if (lane == 0) norms[j] = sqrt(ns);
     }
-    if (tid == 0) M[k + (long long)k * ld] = s_alpha;
+    if (rank == owner && tid == 0) M[k + (long long)p * ld] = s_alpha;
+    // the owner rewrites vbuf only after the next step's first cluster barrier,
+    // which every reader of this step's v passes after finishing with it
     __syncthreads();
     ++k;
   }
   const int r = k;
-  if (tid == 0) {
+  if (rank == 0 && tid == 0) {
     a.rank[jb.out_idx] = r;
     a.ref[jb.out_idx] = ref < 0.0 ? 0.0 : ref;
   }
-  for (int j = tid; j < n; j += kThreads) perm_out[j] = sperm[j];
-  // T = R11^{-1} R12 (r x (n - r), leading dimension r); barriers stay unconditional
-  double2* inv = vbuf;  // r <= min(m, n) <= max_m
-  for (int i = tid; i < r; i += kThreads) inv[i] = cinv(M[i + (long long)i * ld]);
+  if (rank == 0)
+    for (int i = tid; i < r; i += kThreads) perm_out[i] = order[i];
+  // T = R11^{-1} R12, R11(a, b) = M(a, order[b]); one warp per owned remaining column
+  double2* inv = vbuf;
+  cl.sync();  // every block is done reading other blocks' shared memory
+  for (int i = tid; i < r; i += kThreads) inv[i] = cinv(M[i + (long long)order[i] * ld]);
   __syncthreads();
   double2* T = a.tbuf + jb.t_off;
-  for (int j = r + warp; r > 0 && j < n; j += kWarps) {
-    double2* t = T + (long long)(j - r) * r;
+  for (int j = rank + C * warp; j < n; j += C * kWarps) {
+    if (done[j]) continue;
+    // position of j among the remaining columns (increasing index)
+    int before = 0;
+    for (int i = lane; i < j; i += 32) before += done[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) before += __shfl_xor_sync(0xffffffffu, before, o);
+    const int c = j - before;
+    if (lane == 0) perm_out[r + c] = j;
+    if (r == 0) continue;
+    double2* t = T + (long long)c * r;
     const double2* col = M + (long long)j * ld;
     for (int i = lane; i < r; i += 32) t[i] = col[i];
     __syncwarp();
@@ -171,7 +212,7 @@ __global__ void __launch_bounds__(kThreads) cpqr_kernel(const IdLaunch a) {
       const double2 ti = cmul(t[i], inv[i]);
       __syncwarp();
       if (lane == 0) t[i] = ti;
-      const double2* ri = M + (long long)i * ld;
+      const double2* ri = M + (long long)order[i] * ld;
       for (int l = lane; l < i; l += 32) t[l] = cfms(ri[l], ti, t[l]);
       __syncwarp();
     }
@@ -180,14 +221,45 @@ __global__ void __launch_bounds__(kThreads) cpqr_kernel(const IdLaunch a) {
 
 }  // namespace
 
+// Cluster size for a launch: enough blocks per matrix to spread few large IDs
+// over the SMs, at most 16, and at least 8 columns per block.
+int cpqr_cluster_size(int njobs, int max_n) {
+  int c = 1;
+  while (c < 16 && njobs * c * 2 <= 296 && max_n >= 16 * c) c *= 2;
+  return c;
+}
+
 cudaError_t launch_cpqr(const IdLaunch& a, cudaStream_t s) {
   if (a.njobs <= 0) return cudaSuccess;
-  const size_t smem = (size_t)a.max_m * sizeof(double2) + (size_t)a.max_n * (sizeof(double) + sizeof(int));
-  if (smem > 220 * 1024) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(cpqr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = (size_t)a.max_m * sizeof(double2) + (size_t)a.max_n * (sizeof(double) + 2 * sizeof(int));
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(cpqr_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  cpqr_kernel<<<a.njobs, kThreads, smem, s>>>(a);
-  return cudaGetLastError();
+  int c = cpqr_cluster_size(a.njobs, a.max_n);
+  if (c > 8) {
+    if (cudaFuncSetAttribute(cpqr_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+      cudaGetLastError();
+      c = 8;
+    }
+  }
+  for (;;) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(a.njobs * c, 1, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = c;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, cpqr_cluster_kernel, a);
+    if (e == cudaSuccess || c == 1) return e;
+    cudaGetLastError();  // e.g. the cluster size is not supported: retry smaller
+    c /= 2;
+  }
 }
 
 }  // namespace symhss
