@@ -156,7 +156,7 @@ def run_ours(args):
         if sampler:
             sampler.start()
         times = []
-        launches = 0
+        launches0 = S.lib.symhss_launch_count()
         kms = [0.0] * 8
         kwork = [0.0] * 8
         klaunch = [0] * 8
@@ -174,8 +174,8 @@ def run_ours(args):
                 kms[k] += st.kernel_ms[k]
                 kwork[k] += st.kernel_work[k]
                 klaunch[k] += st.kernel_launches[k]
-            launches += sum(st.kernel_launches[k] for k in range(8)) + 1  # + plane-wave kernel
         barrier()
+        launches = S.lib.symhss_launch_count() - launches0
         clocks = sampler.stop() if sampler else None
         tot = torch.tensor([sum(times)], device="cuda", dtype=torch.float64)
         if world > 1:
@@ -258,6 +258,27 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_profile(args):
+    """One warm-up and one symmetric step of the workload, nothing else (for ncu captures)."""
+    import torch
+
+    from paper_2609_33216_b300.solver import Solver
+
+    torch.cuda.set_device(0)
+    w = _workload(args.workload)
+    s = Solver(w["curve"], w["k0"], w["k1"], w["eps0"], w["eps1"], mode="sym", curve_on_device=True,
+               leaf=w["leaf"], nproxy=w["nproxy"], tol=w["tol"])
+    for _ in range(2):
+        s.compress()
+        s.factor()
+        x = s.solve(s.rhs(0.0))
+    torch.cuda.synchronize()
+    st = s.stats()
+    print(json.dumps({"profile": w["name"], "ms_compress": st.ms_compress, "ms_factor": st.ms_factor,
+                      "ms_solve": st.ms_solve, "x0": [float(x[0].real), float(x[0].imag)]}), flush=True)
+    s.close()
+
+
 # ----------------------------------------------------------------------------- CPU oracle
 
 def cpu_baseline(w, sample_boxes: int):
@@ -338,7 +359,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-boxes", type=int, default=16)
     ap.add_argument("--ref-sample-boxes", type=int, default=4)
+    ap.add_argument("--profile", action="store_true", help="one warm-up + one symmetric step only")
     args = ap.parse_args()
+    if args.profile:
+        run_profile(args)
+        return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":

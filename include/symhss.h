@@ -168,6 +168,10 @@ int symhss_level_ranks(symhss_t h, int level, int* out);
 /* Release everything the handle owns.  NULL is accepted. */
 int symhss_destroy(symhss_t h);
 
+/* Number of CUDA kernels this library has launched in this process so far
+ * (all handles and entry points; for launch accounting in benchmarks). */
+long long symhss_launch_count(void);
+
 /* Static message for a status code. */
 const char* symhss_strerror(int status);
 

@@ -68,6 +68,9 @@ __device__ __forceinline__ void warp_argmax(double& v, int& i) {
   }
 }
 
+// process-wide count of kernels this library has launched (diagnostics)
+void count_launches(long long n);
+
 // device status bits (OR-ed into a device word the host reads at sync points)
 enum : int {
   ST_BAD_INDEX = 1,
@@ -89,6 +92,8 @@ struct KernelParams {
   double k0, k1, eps0, eps1;
   double e0sq, e1sq;   // eps0^2, eps1^2
   double half_ft;      // (eps0 + eps1) / 2
+  double lhk0, lhk1;   // log(k0 / 2), log(k1 / 2)
+  double ik0, ik1;     // 1 / k0, 1 / k1
 };
 
 // A tile: "thread points" (one per thread) x "loop points" (staged in shared
@@ -106,7 +111,7 @@ struct TileJob {
 };
 enum : int { TILE_SRC_IS_THREAD = 1, TILE_UNSCALED = 2 };
 
-struct TileChunk { int job, t0, l0; };
+struct TileChunk { int job, t0, l0, ln; };  // ln: loop points of this chunk (<= TILE_L)
 
 struct TileLaunch {
   PointTable tpts, lpts;   // tables the thread / loop point indices refer to

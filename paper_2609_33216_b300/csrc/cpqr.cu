@@ -256,6 +256,7 @@ cudaError_t launch_cpqr(const IdLaunch& a, cudaStream_t s) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     e = cudaLaunchKernelEx(&cfg, cpqr_cluster_kernel, a);
+    if (e == cudaSuccess) symhss::count_launches(1);
     if (e == cudaSuccess || c == 1) return e;
     cudaGetLastError();  // e.g. the cluster size is not supported: retry smaller
     c /= 2;

@@ -3,6 +3,7 @@
 // batched LU / solve.  They validate their arguments, allocate the small job
 // arrays they need, launch the same kernels the solver uses, and synchronise
 // the stream before returning.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -10,6 +11,12 @@
 #include "common.cuh"
 
 using namespace symhss;
+
+namespace {
+std::atomic<long long> g_launches{0};
+}  // namespace
+
+void symhss::count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 namespace {
 
@@ -41,6 +48,8 @@ bool points_ok(const symhss_points* p) {
 }  // namespace
 
 extern "C" {
+
+long long symhss_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 int symhss_hankel01(const double* x, int n, void* out, void* stream) {
   if (n < 0 || (n > 0 && (!x || !out))) return SYMHSS_ERR_INVALID;
@@ -81,7 +90,7 @@ int symhss_kernel_block(const symhss_params* prm, const symhss_points* obs, cons
   jb.flags = scaled ? 0 : TILE_UNSCALED;
   std::vector<TileChunk> ch;
   for (int a = 0; a < m; a += TILE_T)
-    for (int b = 0; b < n; b += TILE_L) ch.push_back(TileChunk{0, a, b});
+    for (int b = 0; b < n; b += TILE_L) ch.push_back(TileChunk{0, a, b, TILE_L});
   const size_t ints = 3 * (size_t)m + 3 * (size_t)n;
   TmpBuf buf;
   const size_t bytes = ints * sizeof(int) + sizeof(TileJob) + ch.size() * sizeof(TileChunk) + sizeof(int) + 64;
@@ -115,6 +124,10 @@ int symhss_kernel_block(const symhss_params* prm, const symhss_points* obs, cons
   a.kp.k0 = prm->k0; a.kp.k1 = prm->k1; a.kp.eps0 = prm->eps0; a.kp.eps1 = prm->eps1;
   a.kp.e0sq = prm->eps0 * prm->eps0; a.kp.e1sq = prm->eps1 * prm->eps1;
   a.kp.half_ft = 0.5 * (prm->eps0 + prm->eps1);
+  a.kp.lhk0 = std::log(0.5 * prm->k0);
+  a.kp.lhk1 = std::log(0.5 * prm->k1);
+  a.kp.ik0 = 1.0 / prm->k0;
+  a.kp.ik1 = 1.0 / prm->k1;
   CKE(launch_tiles(a, s));
   int st = 0;
   CKE(cudaMemcpyAsync(&st, a.status, sizeof(int), cudaMemcpyDeviceToHost, s));

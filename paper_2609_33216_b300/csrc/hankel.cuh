@@ -91,22 +91,23 @@ __device__ __forceinline__ double horner(const double* c, double t) {
 
 }  // namespace hk
 
-// h0 = H_0^(1)(x), h1 = H_1^(1)(x) for x > 0 (x = re, y = im)
-__device__ __forceinline__ void hankel01(double x, double2& h0, double2& h1) {
+// h0 = H_0^(1)(x), h1 = H_1^(1)(x) for x > 0 (x = re, y = im), given
+// lh = log(x / 2) and ix = 1 / x (callers evaluating several x from one distance
+// share the logarithm and the reciprocal).
+__device__ __forceinline__ void hankel01(double x, double lh, double ix, double2& h0, double2& h1) {
   using namespace hk;
   if (x <= kSeriesMax) {
     const double t = 0.25 * x * x;
     const double j0v = horner<kSeries>(cJ0, t);
     const double j1v = 0.5 * x * horner<kSeries>(cJ1, t);
-    const double L = log(0.5 * x) + kGamma;
+    const double L = lh + kGamma;
     const double y0v = (2.0 / kPi) * fma(L, j0v, horner<kSeries>(cY0, t));
-    const double y1v = (2.0 / kPi) * (L * j1v - 1.0 / x) - (x * (0.5 / kPi)) * horner<kSeries>(cY1, t);
+    const double y1v = (2.0 / kPi) * (L * j1v - ix) - (x * (0.5 / kPi)) * horner<kSeries>(cY1, t);
     h0 = make_double2(j0v, y0v);
     h1 = make_double2(j1v, y1v);
     return;
   }
   if (x >= kAsymMin) {
-    const double ix = 1.0 / x;
     const double ix2 = ix * ix;
     const double p0 = horner<kAsym>(cP0, ix2), q0 = ix * horner<kAsym>(cQ0, ix2);
     const double p1 = horner<kAsym>(cP1, ix2), q1 = ix * horner<kAsym>(cQ1, ix2);
@@ -122,7 +123,7 @@ __device__ __forceinline__ void hankel01(double x, double2& h0, double2& h1) {
   }
   // Miller's backward recurrence
   const int N = 2 * (int)ceil((1.5 * x + 22.0) * 0.5);
-  const double inv2x = 2.0 / x;
+  const double inv2x = 2.0 * ix;
   double jp1 = 0.0, jn = 1.0;  // J_(n+1), J_n (unnormalised), n = N
   double norm = 0.0, s0 = 0.0, s1 = 0.0;
   // running values at n: after the step below jm1 = J_(n-1)
@@ -153,11 +154,15 @@ __device__ __forceinline__ void hankel01(double x, double2& h0, double2& h1) {
   norm += jn;
   const double rn = 1.0 / norm;
   const double j0v = jn * rn, j1v = jp1 * rn;
-  const double L = log(0.5 * x) + kGamma;
+  const double L = lh + kGamma;
   const double y0v = (2.0 / kPi) * (L * j0v - 2.0 * s0 * rn);
   const double y1v = (2.0 / kPi) * (-j0v * (0.5 * inv2x) + L * j1v + s1 * rn);
   h0 = make_double2(j0v, y0v);
   h1 = make_double2(j1v, y1v);
+}
+
+__device__ __forceinline__ void hankel01(double x, double2& h0, double2& h1) {
+  hankel01(x, log(0.5 * x), 1.0 / x, h0, h1);
 }
 
 }  // namespace symhss

@@ -1,24 +1,22 @@
 // Triangular solves with the factors of the batched LU (lu_blocked.cu): the
 // solves of Sec. 4.2 (X = D^{-1} L, Atilde = (R X)^{-1}, g = D^{-1} f, root).
-// One warp per right-hand side; the permuted column is held in shared memory
-// while the unit-lower and upper triangular solves run.
+//
+// Many right-hand sides (factorisation): one warp per right-hand side, up to 8 per
+// block; the permuted column and the inverted diagonal of U live in shared memory.
+// Few right-hand sides (solve phase): one block per right-hand side; the column is
+// processed in 32-row blocks -- one warp solves the 32 x 32 triangle with register
+// shuffles, then every thread of the block updates the rows below (above, for U).
 #include "common.cuh"
 
 namespace symhss {
 
 namespace {
 
-constexpr int kRsWarps = 4;
+constexpr int kRsMaxWarps = 8;
+constexpr int kCtaThreads = 256;
 
-__global__ void __launch_bounds__(kRsWarps * 32) getrs_kernel(const RsLaunch a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const RsJob jb = a.jobs[blockIdx.x];
-  const int n = jb.n;
-  if (n > a.max_n || n < 0) return;
-  int* perm = reinterpret_cast<int*>(smem_raw);
-  double2* cols = reinterpret_cast<double2*>(smem_raw + ((n * sizeof(int) + 15) / 16) * 16);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int* piv = a.piv + jb.piv_off;
+// perm = composition of the recorded row interchanges (thread 0, sequential)
+__device__ __forceinline__ void build_perm(int* perm, const int* piv, int n) {
   if (threadIdx.x == 0) {
     for (int i = 0; i < n; ++i) perm[i] = i;
     for (int k = 0; k < n; ++k) {
@@ -26,13 +24,27 @@ __global__ void __launch_bounds__(kRsWarps * 32) getrs_kernel(const RsLaunch a) 
       if (p != k && p >= 0 && p < n) { const int t = perm[k]; perm[k] = perm[p]; perm[p] = t; }
     }
   }
-  __syncthreads();
-  const int c = blockIdx.y * kRsWarps + warp;
-  if (c >= jb.nrhs) return;
+}
+
+__global__ void getrs_kernel(const RsLaunch a, int warps) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const RsJob jb = a.jobs[blockIdx.x];
+  const int n = jb.n;
+  if (n > a.max_n || n < 0) return;  // uniform per block
+  double2* dinv = reinterpret_cast<double2*>(smem_raw);
+  double2* cols = dinv + a.max_n;
+  int* perm = reinterpret_cast<int*>(cols + (size_t)warps * a.max_n);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int* piv = a.piv + jb.piv_off;
   const double2* A = a.abase + jb.a_off;
   const int lda = jb.lda;
+  build_perm(perm, piv, n);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dinv[i] = cinv(A[i + (long long)i * lda]);
+  __syncthreads();
+  const int c = blockIdx.y * warps + warp;
+  if (c >= jb.nrhs) return;
   double2* b = a.bbase + jb.b_off + (long long)c * jb.ldb;
-  double2* sb = cols + (long long)warp * n;
+  double2* sb = cols + (long long)warp * a.max_n;
   for (int i = lane; i < n; i += 32) sb[i] = b[perm[i]];
   __syncwarp();
   for (int k = 0; k < n; ++k) {  // unit lower
@@ -43,7 +55,7 @@ __global__ void __launch_bounds__(kRsWarps * 32) getrs_kernel(const RsLaunch a) 
   }
   for (int k = n - 1; k >= 0; --k) {  // upper
     const double2* uk = A + (long long)k * lda;
-    const double2 bk = cmul(sb[k], cinv(uk[k]));
+    const double2 bk = cmul(sb[k], dinv[k]);
     __syncwarp();
     if (lane == 0) sb[k] = bk;
     for (int i = lane; i < k; i += 32) sb[i] = cfms(uk[i], bk, sb[i]);
@@ -52,17 +64,91 @@ __global__ void __launch_bounds__(kRsWarps * 32) getrs_kernel(const RsLaunch a) 
   for (int i = lane; i < n; i += 32) b[i] = sb[i];
 }
 
+__global__ void __launch_bounds__(kCtaThreads) getrs_cta_kernel(const RsLaunch a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const RsJob jb = a.jobs[blockIdx.x];
+  const int n = jb.n;
+  const int c = blockIdx.y;
+  if (n > a.max_n || n < 0 || c >= jb.nrhs) return;  // uniform per block
+  double2* x = reinterpret_cast<double2*>(smem_raw);
+  int* perm = reinterpret_cast<int*>(x + a.max_n);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const double2* A = a.abase + jb.a_off;
+  const int lda = jb.lda;
+  double2* b = a.bbase + jb.b_off + (long long)c * jb.ldb;
+  build_perm(perm, a.piv + jb.piv_off, n);
+  __syncthreads();
+  for (int i = tid; i < n; i += kCtaThreads) x[i] = b[perm[i]];
+  __syncthreads();
+  // forward substitution with the unit lower factor, 32 rows at a time
+  for (int kb = 0; kb < n; kb += 32) {
+    const int w = min(32, n - kb);
+    if (warp == 0) {
+      double2 xr = lane < w ? x[kb + lane] : make_double2(0.0, 0.0);
+      for (int q = 0; q < w; ++q) {
+        const double2 xq = make_double2(__shfl_sync(0xffffffffu, xr.x, q), __shfl_sync(0xffffffffu, xr.y, q));
+        if (lane > q && lane < w) xr = cfms(A[kb + lane + (long long)(kb + q) * lda], xq, xr);
+      }
+      if (lane < w) x[kb + lane] = xr;
+    }
+    __syncthreads();
+    for (int i = kb + w + tid; i < n; i += kCtaThreads) {
+      double2 acc = x[i];
+      for (int q = 0; q < w; ++q) acc = cfms(A[i + (long long)(kb + q) * lda], x[kb + q], acc);
+      x[i] = acc;
+    }
+    __syncthreads();
+  }
+  // back substitution with the upper factor, 32 rows at a time from the bottom
+  for (int kb = ((n - 1) / 32) * 32; n > 0 && kb >= 0; kb -= 32) {
+    const int w = min(32, n - kb);
+    if (warp == 0) {
+      double2 xr = lane < w ? x[kb + lane] : make_double2(0.0, 0.0);
+      for (int q = w - 1; q >= 0; --q) {
+        if (lane == q) xr = cmul(xr, cinv(A[kb + q + (long long)(kb + q) * lda]));
+        const double2 xq = make_double2(__shfl_sync(0xffffffffu, xr.x, q), __shfl_sync(0xffffffffu, xr.y, q));
+        if (lane < q) xr = cfms(A[kb + lane + (long long)(kb + q) * lda], xq, xr);
+      }
+      if (lane < w) x[kb + lane] = xr;
+    }
+    __syncthreads();
+    for (int i = tid; i < kb; i += kCtaThreads) {
+      double2 acc = x[i];
+      for (int q = 0; q < w; ++q) acc = cfms(A[i + (long long)(kb + q) * lda], x[kb + q], acc);
+      x[i] = acc;
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < n; i += kCtaThreads) b[i] = x[i];
+}
+
 }  // namespace
 
 cudaError_t launch_getrs(const RsLaunch& a, cudaStream_t s) {
   const int max_n = a.max_n;
   if (a.njobs <= 0 || a.max_rhs <= 0) return cudaSuccess;
-  const size_t smem = ((max_n * sizeof(int) + 15) / 16) * 16 + (size_t)kRsWarps * max_n * sizeof(double2);
-  if (smem > 220 * 1024) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(getrs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e;
+  if (a.max_rhs <= 4) {
+    const size_t smem = (size_t)max_n * (sizeof(double2) + sizeof(int));
+    if (smem > 200 * 1024) return cudaErrorInvalidValue;
+    e = cudaFuncSetAttribute(getrs_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    getrs_cta_kernel<<<dim3(a.njobs, a.max_rhs), kCtaThreads, smem, s>>>(a);
+    symhss::count_launches(1);
+    return cudaGetLastError();
+  }
+  int warps = kRsMaxWarps;
+  size_t smem = 0;
+  for (;; warps /= 2) {
+    smem = (size_t)max_n * sizeof(double2) * (1 + warps) + (size_t)max_n * sizeof(int);
+    if (smem <= 200 * 1024 || warps == 1) break;
+  }
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  e = cudaFuncSetAttribute(getrs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid(a.njobs, (a.max_rhs + kRsWarps - 1) / kRsWarps);
-  getrs_kernel<<<grid, kRsWarps * 32, smem, s>>>(a);
+  dim3 grid(a.njobs, (a.max_rhs + warps - 1) / warps);
+  getrs_kernel<<<grid, warps * 32, smem, s>>>(a, warps);
+  symhss::count_launches(1);
   return cudaGetLastError();
 }
 

@@ -176,23 +176,28 @@ __global__ void zero_info_kernel(int* info, const LuJob* jobs, int njobs) {
 cudaError_t launch_getrf(const LuLaunch& a, cudaStream_t s) {
   if (a.njobs <= 0 || a.max_n <= 0) return cudaSuccess;
   zero_info_kernel<<<(a.njobs + 127) / 128, 128, 0, s>>>(a.info, a.jobs, a.njobs);
+  symhss::count_launches(1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int ncolblk = (a.max_n + kSwapThreads - 1) / kSwapThreads;
   for (int j = 0; j < a.max_n; j += kNb) {
     panel_kernel<<<a.njobs, kPanelThreads, 0, s>>>(a, j);
+    symhss::count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int rest = a.max_n - j - kNb;
     if (rest <= 0) continue;
     swap_trsm_kernel<<<dim3(a.njobs, ncolblk), kSwapThreads, 0, s>>>(a, j);
+    symhss::count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int tiles = (rest + kTs - 1) / kTs;
     update_kernel<<<dim3(a.njobs, tiles, tiles), 256, 0, s>>>(a, j);
+    symhss::count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   // the last panel's interchanges still have to reach the columns left of it
   const int jlast = ((a.max_n - 1) / kNb) * kNb;
   swap_trsm_kernel<<<dim3(a.njobs, ncolblk), kSwapThreads, 0, s>>>(a, jlast);
+  symhss::count_launches(1);
   return cudaGetLastError();
 }
 

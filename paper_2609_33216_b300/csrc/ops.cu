@@ -146,6 +146,7 @@ __global__ void plane_wave_kernel(const double* x, const double* y, const double
 cudaError_t launch_basis_dense(const BasisLaunch& a, cudaStream_t s) {
   if (a.njobs <= 0) return cudaSuccess;
   basis_dense_kernel<<<a.njobs, kOpsThreads, 0, s>>>(a);
+  symhss::count_launches(1);
   return cudaGetLastError();
 }
 
@@ -153,6 +154,7 @@ cudaError_t launch_apply_r(const BasisLaunch& a, cudaStream_t s) {
   if (a.njobs <= 0) return cudaSuccess;
   dim3 grid(a.njobs, 4);
   apply_r_kernel<<<grid, kOpsThreads, 0, s>>>(a);
+  symhss::count_launches(1);
   return cudaGetLastError();
 }
 
@@ -160,6 +162,7 @@ cudaError_t launch_gemm(const GemmLaunch& a, cudaStream_t s) {
   if (a.njobs <= 0) return cudaSuccess;
   dim3 grid(a.njobs, 8);
   gemm_kernel<<<grid, 256, 0, s>>>(a);
+  symhss::count_launches(1);
   return cudaGetLastError();
 }
 
@@ -168,6 +171,7 @@ cudaError_t launch_copy_blocks(const double2* src, double2* dst, const CopyJob* 
   if (njobs <= 0) return cudaSuccess;
   dim3 grid(njobs, 4);
   copy_kernel<<<grid, kOpsThreads, 0, s>>>(src, dst, jobs);
+  symhss::count_launches(1);
   return cudaGetLastError();
 }
 
@@ -175,6 +179,7 @@ cudaError_t launch_leaf_gather(const double2* f, int ldf, double2* g, const Leaf
                                int nrhs, int n, cudaStream_t s) {
   if (njobs <= 0) return cudaSuccess;
   leaf_gather_kernel<<<njobs, kOpsThreads, 0, s>>>(f, ldf, g, jobs, nrhs, n);
+  symhss::count_launches(1);
   return cudaGetLastError();
 }
 
@@ -182,6 +187,7 @@ cudaError_t launch_leaf_scatter(const double2* g, double2* x, int ldx, const Lea
                                 int nrhs, int n, cudaStream_t s) {
   if (njobs <= 0) return cudaSuccess;
   leaf_scatter_kernel<<<njobs, kOpsThreads, 0, s>>>(g, x, ldx, jobs, nrhs, n);
+  symhss::count_launches(1);
   return cudaGetLastError();
 }
 
@@ -191,6 +197,7 @@ cudaError_t launch_plane_wave(const double* x, const double* y, const double* nx
   if (n <= 0) return cudaSuccess;
   plane_wave_kernel<<<(n + 255) / 256, 256, 0, s>>>(x, y, nx, ny, w, n, k0, eps0, cos(angle), sin(angle),
                                                     scaled, rhs);
+  symhss::count_launches(1);
   return cudaGetLastError();
 }
 

@@ -220,6 +220,10 @@ KernelParams kparams(const symhss_params& p) {
   k.k0 = p.k0; k.k1 = p.k1; k.eps0 = p.eps0; k.eps1 = p.eps1;
   k.e0sq = p.eps0 * p.eps0; k.e1sq = p.eps1 * p.eps1;
   k.half_ft = 0.5 * (p.eps0 + p.eps1);
+  k.lhk0 = std::log(0.5 * p.k0);
+  k.lhk1 = std::log(0.5 * p.k1);
+  k.ik0 = 1.0 / p.k0;
+  k.ik1 = 1.0 / p.k1;
   return k;
 }
 
@@ -363,14 +367,24 @@ struct TileBuilder {
     jb.ld = ld;
     jb.flags = flags;
     if (jb.n_tp == 0 || jb.n_lp == 0) return;
-    const int j = (int)jobs.size();
     jobs.push_back(jb);
-    for (int a = 0; a < jb.n_tp; a += TILE_T)
-      for (int b = 0; b < jb.n_lp; b += TILE_L) chunks.push_back(TileChunk{j, a, b});
     pairs += (long long)jb.n_tp * jb.n_lp;
+  }
+  // chunks of TILE_T thread points x ln loop points; a launch that would leave most SMs
+  // idle uses shorter loop chunks (more blocks, each with less work)
+  void make_chunks() {
+    long long base = 0;
+    for (const TileJob& jb : jobs)
+      base += (long long)((jb.n_tp + TILE_T - 1) / TILE_T) * ((jb.n_lp + TILE_L - 1) / TILE_L);
+    const int ln = base >= 4 * 148 ? TILE_L : (base >= 2 * 148 ? TILE_L / 2 : TILE_L / 4);
+    chunks.clear();
+    for (int j = 0; j < (int)jobs.size(); ++j)
+      for (int a = 0; a < jobs[j].n_tp; a += TILE_T)
+        for (int b = 0; b < jobs[j].n_lp; b += ln) chunks.push_back(TileChunk{j, a, b, ln});
   }
   cudaError_t launch(symhss_s* h, DevBuf& buf, double2* out, cudaStream_t s) {
     if (jobs.empty()) return cudaSuccess;
+    make_chunks();
     Packer pk;
     const size_t o1 = pk.add(tp_pt), o2 = pk.add(tp_s0), o3 = pk.add(tp_s1);
     const size_t o4 = pk.add(lp_pt), o5 = pk.add(lp_s0), o6 = pk.add(lp_s1);

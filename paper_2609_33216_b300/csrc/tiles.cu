@@ -37,12 +37,13 @@ constexpr double kEulerGamma = 0.577215664901532860606512090082402431;
 
 struct LayerVals { double2 g, d, ds, n; };
 
-// S, D, D*, N kernels of one wavenumber at a non-coincident pair.
-__device__ __forceinline__ LayerVals layer(double k, double r, double a_r, double b_r,
-                                           double nn_r, double ab_r) {
+// S, D, D*, N kernels of one wavenumber at a non-coincident pair; lr = log(r),
+// inv_r = 1/r, lhk = log(k/2), ik = 1/k.
+__device__ __forceinline__ LayerVals layer(double k, double r, double inv_r, double lr, double lhk, double ik,
+                                           double a_r, double b_r, double nn_r, double ab_r) {
   const double z = __dmul_rn(k, r);
   double2 h0, h1;
-  hankel01(z, h0, h1);
+  hankel01(z, lr + lhk, inv_r * ik, h0, h1);
   const double j0v = h0.x, y0v = h0.y, j1v = h1.x, y1v = h1.y;
   const double kq = 0.25 * k;
   LayerVals v;
@@ -51,7 +52,6 @@ __device__ __forceinline__ LayerVals layer(double k, double r, double a_r, doubl
   v.d = make_double2(__dmul_rn(c1.x, b_r), __dmul_rn(c1.y, b_r));
   v.ds = make_double2(-__dmul_rn(c1.x, a_r), -__dmul_rn(c1.y, a_r));
   // N = c1 * nn/r + i kq (ab/r) (k H0 / r - 2 H1 / r^2)
-  const double inv_r = 1.0 / r;
   const double2 qv = make_double2(k * j0v * inv_r - 2.0 * j1v * inv_r * inv_r,
                                   k * y0v * inv_r - 2.0 * y1v * inv_r * inv_r);
   const double s = kq * ab_r;
@@ -99,10 +99,14 @@ __device__ __forceinline__ void pair_block(const P7& o, const P7& s, const Kerne
   const double a = __fma_rn(dx, o.nx, __dmul_rn(dy, o.ny));
   const double b = __fma_rn(dx, s.nx, __dmul_rn(dy, s.ny));
   const double nn = __fma_rn(o.nx, s.nx, __dmul_rn(o.ny, s.ny));
-  const double a_r = __ddiv_rn(a, r), b_r = __ddiv_rn(b, r);
-  const double nn_r = __ddiv_rn(nn, r), ab_r = __ddiv_rn(__dmul_rn(a, b), r);
-  const LayerVals l0 = layer(kp.k0, r, a_r, b_r, nn_r, ab_r);
-  const LayerVals l1 = layer(kp.k1, r, a_r, b_r, nn_r, ab_r);
+  // one reciprocal and one logarithm per pair; products with inv_r keep the exact
+  // sign symmetry of the quotients under the swap of the two points
+  const double inv_r = __drcp_rn(r);
+  const double lr = log(r);
+  const double a_r = __dmul_rn(a, inv_r), b_r = __dmul_rn(b, inv_r);
+  const double nn_r = __dmul_rn(nn, inv_r), ab_r = __dmul_rn(__dmul_rn(a, b), inv_r);
+  const LayerVals l0 = layer(kp.k0, r, inv_r, lr, kp.lhk0, kp.ik0, a_r, b_r, nn_r, ab_r);
+  const LayerVals l1 = layer(kp.k1, r, inv_r, lr, kp.lhk1, kp.ik1, a_r, b_r, nn_r, ab_r);
   const double2 ks = combo(kp.e0sq, l0.g, kp.e1sq, l1.g);
   const double2 kd = combo(kp.eps0, l0.d, kp.eps1, l1.d);
   const double2 kds = combo(kp.eps0, l0.ds, kp.eps1, l1.ds);
@@ -119,7 +123,7 @@ __global__ void __launch_bounds__(TILE_T) tile_kernel(const TileLaunch a) {
   __shared__ int sid[TILE_L], ss0[TILE_L], ss1[TILE_L];
   const TileChunk ch = a.chunks[blockIdx.x];
   const TileJob jb = a.jobs[ch.job];
-  const int nl = min(TILE_L, jb.n_lp - ch.l0);
+  const int nl = min(min(TILE_L, ch.ln), jb.n_lp - ch.l0);
   const int t = threadIdx.x;
   if (t < nl) {
     const int li = jb.lp_off + ch.l0 + t;
@@ -179,12 +183,14 @@ __global__ void hankel_kernel(const double* x, int n, double2* out) {
 cudaError_t launch_hankel(const double* x, int n, double2* out, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   hankel_kernel<<<(n + 127) / 128, 128, 0, s>>>(x, n, out);
+  symhss::count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_tiles(const TileLaunch& a, cudaStream_t s) {
   if (a.nchunks <= 0) return cudaSuccess;
   tile_kernel<<<a.nchunks, TILE_T, 0, s>>>(a);
+  symhss::count_launches(1);
   return cudaGetLastError();
 }
 

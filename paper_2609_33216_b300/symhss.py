@@ -83,6 +83,7 @@ _SIGNATURES = [
     ("symhss_stats", C.c_int, [C.c_void_p, C.POINTER(symhss_stats_t)]),
     ("symhss_level_ranks", C.c_int, [C.c_void_p, C.c_int, _ip]),
     ("symhss_destroy", C.c_int, [C.c_void_p]),
+    ("symhss_launch_count", C.c_longlong, []),
     ("symhss_hankel01", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     ("symhss_kernel_block", C.c_int, [C.POINTER(symhss_params), C.POINTER(symhss_points), C.c_void_p,
                                       C.POINTER(symhss_points), C.c_void_p, C.c_int, C.c_void_p, C.c_int,
