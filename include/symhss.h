@@ -81,7 +81,9 @@ typedef struct {
   int precision;          /* SYMHSS_FP64                                              */
   int fixed_rank_kL;      /* > 0: fixed ranks k_l = ceil(a^(L-l) kL) (Sec. 4.3), 0: tol */
   double rank_scale_a;    /* a of Sec. 4.3 (1.15)                                     */
-  int oversample;         /* sketch oversampling p (16); 0 disables the sketch        */
+  int oversample;         /* sketch oversampling p (16): an ID is taken of Y = Omega M with
+                           * s = rank estimate + p rows when that is under 0.8 m rows; an ID
+                           * whose rank reaches s - p/2 is redone on M; 0 disables the sketch */
   int reserved;
   uint64_t seed;          /* seed of the counter-based sketch generator               */
 } symhss_params;
@@ -94,6 +96,7 @@ typedef struct {
 #define SYMHSS_K_GETRF  2   /* batched block LU                                  */
 #define SYMHSS_K_GETRS  3   /* batched triangular solves (X = D^-1 L, Atilde, g)  */
 #define SYMHSS_K_OTHER  4   /* bases, R X, small GEMMs, copies, gather / scatter  */
+#define SYMHSS_K_SKETCH 5   /* tensor-core sketch Y = Omega M (slicing + tcgen05 GEMM) */
 #define SYMHSS_K_COUNT  8
 typedef struct {
   int n;                          /* nodes                                    */
@@ -117,6 +120,7 @@ typedef struct {
   double kernel_ms[SYMHSS_K_COUNT];
   long long kernel_launches[SYMHSS_K_COUNT];
   double kernel_work[SYMHSS_K_COUNT];
+  long long sketch_redo;          /* sketched IDs redone on the full matrix (rank near s) */
 } symhss_stats_t;
 
 /* ---- handle lifecycle ------------------------------------------------------ */
@@ -230,6 +234,17 @@ int symhss_column_id(void* A, int m, int n, int lda, long long strideA, int batc
  * the paper. */
 int symhss_column_id_noalloc(void* A, int m, int n, int lda, long long strideA, int batch, double tol,
                              int fixed_rank, int* rank, int* perm, void* T, long long strideT, void* stream);
+
+/* Randomized row sketch Y_b = Omega_b M_b on the tensor cores, to FP64 accuracy
+ * (the sketch of the randomized ID; the ID of Y_b selects the columns of M_b).
+ * M_b = A + b*strideA: m x n complex128, column-major, leading dimension lda (read
+ * only).  Omega_b is the s x m matrix with entries -1 where the top bit of
+ * splitmix64(seed ^ b*0xD1B54A32D192ED03 ^ i*0x8CB92BA72F3D8DD7 ^ k) is set and +1
+ * otherwise (i: row of Y, k: row of M; 64-bit wrapping arithmetic).  Y_b = Y +
+ * b*strideY: s x n complex128, leading dimension ldy.  m <= 65536, s <= 1024.
+ * Returns SYMHSS_ERR_TIMEOUT if a bounded device wait expired. */
+int symhss_sketch(const void* A, int m, int n, int lda, long long strideA, int batch, int s,
+                  unsigned long long seed, void* Y, int ldy, long long strideY, void* stream);
 
 /* Batched LU with partial pivoting of n x n complex128 matrices A + b*strideA
  * (leading dimension lda; overwritten by L\U), pivots ipiv + b*n (0-based row

@@ -77,6 +77,7 @@ enum : int {
   ST_RANK_OVERFLOW = 2,
   ST_SINGULAR = 4,
   ST_SMEM = 8,
+  ST_TIMEOUT = 16,
 };
 
 // ---- tile generator ---------------------------------------------------------
@@ -156,6 +157,40 @@ struct IdLaunch {
   int max_m, max_n;
 };
 cudaError_t launch_cpqr(const IdLaunch& a, cudaStream_t s);
+
+// ---- randomized sketch Y = Omega M on the tensor cores --------------------------------
+
+struct SketchJob {
+  long long m_off;     // M at mats + m_off (m x n complex, leading dim ld)
+  int m, n, ld;
+  int mpad, n2pad;     // m rounded up to 64, 2n rounded up to 32
+  int s;               // rows of Y (<= 128 * number of row tiles)
+  long long y_off;     // Y at y + y_off (s x n complex, leading dim ldy)
+  int ldy;
+  long long slice_off; // bytes into the slice buffer
+  long long exp_off;   // ints into the exponent buffer (2n entries)
+  long long stream_id; // counter-stream index of this job's Omega
+};
+struct SketchColWork { int job, col; };
+struct SketchTile { int job, cb, mtile; };
+struct SketchLaunch {
+  const double2* mats;
+  uint8_t* slices;
+  int* exps;
+  double2* y;
+  const SketchJob* jobs;
+  const SketchColWork* colwork;
+  int ncolwork;
+  const SketchTile* tiles;
+  int ntiles;
+  uint64_t seed;
+  int* status;
+};
+cudaError_t launch_sketch(const SketchLaunch& a, cudaStream_t s);
+size_t sketch_slice_bytes(int mpad, int n2pad);
+int sketch_mpad(int m);
+int sketch_n2pad(int n);
+uint64_t sketch_host_splitmix64(uint64_t x);
 
 // ---- batched LU and solves -----------------------------------------------------
 

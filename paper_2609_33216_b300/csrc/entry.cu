@@ -178,6 +178,63 @@ int symhss_column_id(void* A, int m, int n, int lda, long long strideA, int batc
   return status_code(st);
 }
 
+int symhss_sketch(const void* A, int m, int n, int lda, long long strideA, int batch, int s_rows,
+                  unsigned long long seed, void* Y, int ldy, long long strideY, void* stream) {
+  if (batch < 0 || m < 0 || n < 0 || s_rows < 0 || lda < m || lda < 1 || ldy < s_rows || ldy < 1)
+    return SYMHSS_ERR_INVALID;
+  if (m > 65536 || s_rows > 1024) return SYMHSS_ERR_INVALID;
+  if (batch == 0 || n == 0 || s_rows == 0) return SYMHSS_OK;
+  if (!A || !Y || strideA < (long long)lda * n || strideY < (long long)ldy * n) return SYMHSS_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int mpad = sketch_mpad(m), n2pad = sketch_n2pad(n);
+  const size_t sbytes = sketch_slice_bytes(mpad, n2pad);
+  std::vector<SketchJob> jobs(batch);
+  std::vector<SketchColWork> cw;
+  std::vector<SketchTile> tiles;
+  const int mtiles = (s_rows + 127) / 128;
+  for (int b = 0; b < batch; ++b) {
+    SketchJob& j = jobs[b];
+    j.m_off = strideA * b; j.m = m; j.n = n; j.ld = lda; j.mpad = mpad; j.n2pad = n2pad; j.s = s_rows;
+    j.y_off = strideY * b; j.ldy = ldy; j.slice_off = (long long)sbytes * b; j.exp_off = (long long)2 * n * b;
+    j.stream_id = b;
+    for (int c = 0; c < n; ++c) cw.push_back(SketchColWork{b, c});
+    for (int cb = 0; cb < n2pad / 32; ++cb)
+      for (int mt = 0; mt < mtiles; ++mt) tiles.push_back(SketchTile{b, cb, mt});
+  }
+  TmpBuf slices, meta;
+  CKE(slices.alloc(sbytes * batch));
+  const size_t o_exp = 0, o_jobs = ((size_t)2 * n * batch * sizeof(int) + 255) & ~size_t(255);
+  const size_t o_cw = o_jobs + ((jobs.size() * sizeof(SketchJob) + 255) & ~size_t(255));
+  const size_t o_tiles = o_cw + ((cw.size() * sizeof(SketchColWork) + 255) & ~size_t(255));
+  const size_t o_status = o_tiles + ((tiles.size() * sizeof(SketchTile) + 255) & ~size_t(255));
+  const size_t total = o_status + 256;
+  CKE(meta.alloc(total));
+  std::vector<char> host(total, 0);
+  std::memcpy(host.data() + o_jobs, jobs.data(), jobs.size() * sizeof(SketchJob));
+  std::memcpy(host.data() + o_cw, cw.data(), cw.size() * sizeof(SketchColWork));
+  std::memcpy(host.data() + o_tiles, tiles.data(), tiles.size() * sizeof(SketchTile));
+  CKE(cudaMemcpyAsync(meta.p, host.data(), total, cudaMemcpyHostToDevice, s));
+  char* d = reinterpret_cast<char*>(meta.p);
+  SketchLaunch a;
+  a.mats = reinterpret_cast<const double2*>(A);
+  a.slices = reinterpret_cast<uint8_t*>(slices.p);
+  a.exps = reinterpret_cast<int*>(d + o_exp);
+  a.y = reinterpret_cast<double2*>(Y);
+  a.jobs = reinterpret_cast<const SketchJob*>(d + o_jobs);
+  a.colwork = reinterpret_cast<const SketchColWork*>(d + o_cw);
+  a.ncolwork = (int)cw.size();
+  a.tiles = reinterpret_cast<const SketchTile*>(d + o_tiles);
+  a.ntiles = (int)tiles.size();
+  a.seed = seed;
+  a.status = reinterpret_cast<int*>(d + o_status);
+  CKE(launch_sketch(a, s));
+  int st = 0;
+  CKE(cudaMemcpyAsync(&st, a.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CKE(cudaStreamSynchronize(s));
+  if (st & ST_TIMEOUT) return SYMHSS_ERR_TIMEOUT;
+  return status_code(st);
+}
+
 int symhss_lu_batched(void* A, int n, int lda, long long strideA, int batch, int* ipiv, int* info, void* stream) {
   if (batch < 0 || n < 0 || lda < n || lda < 1) return SYMHSS_ERR_INVALID;
   if (batch == 0 || n == 0) return SYMHSS_OK;

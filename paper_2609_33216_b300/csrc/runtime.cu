@@ -69,7 +69,8 @@ struct Packer {
   size_t add(const void* src, size_t bytes) {
     size_t off = (host.size() + 255) & ~size_t(255);
     host.resize(off + bytes);
-    if (bytes) std::memcpy(host.data() + off, src, bytes);
+    if (bytes && src) std::memcpy(host.data() + off, src, bytes);
+    if (bytes && !src) std::memset(host.data() + off, 0, bytes);
     return off;
   }
   template <class T> size_t add(const std::vector<T>& v) { return add(v.data(), v.size() * sizeof(T)); }
@@ -104,7 +105,7 @@ struct HBox {
 struct Level {
   std::vector<HBox> boxes;
   // compress
-  DevBuf mr, tbuf, permbuf, rankbuf, refbuf, clists, idjobs;
+  DevBuf mr, tbuf, permbuf, rankbuf, refbuf, clists, idjobs, slices, skmeta;
   // factor
   DevBuf D, piv, rxpiv, info, X, RX, At, qbuf, flists, lujobs, cjobs;
   // solve
@@ -135,6 +136,7 @@ struct symhss_s {
   symhss_stats_t st{};
   cudaError_t last_cuda = cudaSuccess;
   std::vector<int> mark;                          // host scratch (size npts)
+  int lvl_max_rank[SYMHSS_MAX_LEVELS][2] = {};    // largest column-ID rank per level and part
 };
 
 namespace symhss {
@@ -525,14 +527,84 @@ int compress_level(symhss_s* h, int l, cudaStream_t s) {
     }
   }
   const int njobs = (int)jobs.size();
-  CK(L.mr.ensure(mr_total * sizeof(double2)));
+  // Randomized sketch (Halko-Martinsson-Tropp): an ID job whose rank estimate plus
+  // oversampling is well below its row count is taken of Y = Omega M instead of M.
+  // Y blocks live after all proxy matrices in the same buffer.  Rank estimate: half
+  // the smaller dimension at the leaves, 1.7x the previous level's largest rank above.
+  const int p_over = h->prm.oversample;
+  const std::vector<IdJob> full = jobs;  // the same IDs on the full proxy matrices
+  std::vector<int> sk_rows(njobs, 0);
+  std::vector<SketchJob> sk;
+  std::vector<SketchColWork> skcw;
+  std::vector<SketchTile> sktiles;
+  long long y_total = 0, slice_total = 0, exp_total = 0;
+  double sketch_work = 0;
+  if (p_over > 0) {
+    for (int i = 0; i < njobs; ++i) {
+      IdJob& j = jobs[i];
+      if (j.n == 0) continue;
+      const int part = j.out_idx & 1;
+      int est;
+      if (fixed >= 0) est = fixed;
+      else if (l == h->depth) est = (std::min(j.m, j.n) + 1) / 2;
+      else est = (int)std::ceil(1.7 * std::max(8, h->lvl_max_rank[l + 1][part]));
+      const int sr = std::max(32, ((est + p_over + 15) / 16) * 16);
+      if (sr > 1024 || 5 * sr >= 4 * j.m) continue;
+      SketchJob sj;
+      sj.m_off = j.m_off; sj.m = j.m; sj.n = j.n; sj.ld = j.ld;
+      sj.mpad = sketch_mpad(j.m); sj.n2pad = sketch_n2pad(j.n); sj.s = sr;
+      sj.y_off = mr_total + y_total; sj.ldy = sr;
+      sj.slice_off = slice_total; sj.exp_off = exp_total;
+      sj.stream_id = ((long long)l << 32) + i;
+      const int sji = (int)sk.size();
+      for (int c = 0; c < j.n; ++c) skcw.push_back(SketchColWork{sji, c});
+      const int mtiles = (sr + 127) / 128;
+      for (int cb = 0; cb < sj.n2pad / 32; ++cb)
+        for (int mt = 0; mt < mtiles; ++mt) sktiles.push_back(SketchTile{sji, cb, mt});
+      sketch_work += 2.0 * 128.0 * mtiles * sj.mpad * 224.0 * (sj.n2pad / 32);
+      y_total += (long long)sr * j.n;
+      slice_total += (long long)sketch_slice_bytes(sj.mpad, sj.n2pad);
+      exp_total += 2LL * j.n;
+      sk.push_back(sj);
+      sk_rows[i] = sr;
+      j.m_off = sj.y_off; j.m = sr; j.ld = sr;
+    }
+  }
+  max_m = 1;
+  for (const IdJob& j : jobs) max_m = std::max(max_m, j.m);
+  CK(L.mr.ensure((mr_total + y_total) * sizeof(double2)));
   CK(L.tbuf.ensure(t_total * sizeof(double2)));
   CK(L.permbuf.ensure(perm_total * sizeof(int)));
   CK(L.rankbuf.ensure(njobs * sizeof(int)));
   CK(L.refbuf.ensure(njobs * sizeof(double)));
   TIMED(SYMHSS_K_TILES, (double)tb.pairs, tb.launch(h, L.clists, L.mr.as<double2>(), s));
+  if (!sk.empty()) {
+    CK(L.slices.ensure((size_t)slice_total));
+    Packer sp;
+    const size_t oj = sp.add(sk), oc = sp.add(skcw), ot = sp.add(sktiles);
+    const size_t oe = sp.add(nullptr, (size_t)exp_total * sizeof(int));
+    CK(sp.upload(L.skmeta, s));
+    char* sb = L.skmeta.as<char>();
+    SketchLaunch sa;
+    sa.mats = L.mr.as<double2>();
+    sa.slices = L.slices.as<uint8_t>();
+    sa.exps = reinterpret_cast<int*>(sb + oe);
+    sa.y = L.mr.as<double2>();
+    sa.jobs = reinterpret_cast<const SketchJob*>(sb + oj);
+    sa.colwork = reinterpret_cast<const SketchColWork*>(sb + oc);
+    sa.ncolwork = (int)skcw.size();
+    sa.tiles = reinterpret_cast<const SketchTile*>(sb + ot);
+    sa.ntiles = (int)sktiles.size();
+    sa.seed = h->prm.seed;
+    sa.status = h->status.as<int>();
+    TIMED(SYMHSS_K_SKETCH, sketch_work, launch_sketch(sa, s));
+  }
+  // IDs of sketches use tol / 4: the sketch compresses the trailing pivot ratios, and at
+  // tol / 4 the interpolation residual on M stays at or below that of the plain ID
+  std::vector<IdJob> plain_jobs, sketch_jobs;
+  for (int i = 0; i < njobs; ++i) (sk_rows[i] > 0 ? sketch_jobs : plain_jobs).push_back(jobs[i]);
   Packer pk;
-  pk.add(jobs);
+  const size_t o_plain = pk.add(plain_jobs), o_sketch = pk.add(sketch_jobs);
   CK(pk.upload(L.idjobs, s));
   IdLaunch ia;
   ia.mats = L.mr.as<double2>();
@@ -540,14 +612,19 @@ int compress_level(symhss_s* h, int l, cudaStream_t s) {
   ia.perm = L.permbuf.as<int>();
   ia.rank = L.rankbuf.as<int>();
   ia.ref = L.refbuf.as<double>();
-  ia.jobs = L.idjobs.as<IdJob>();
-  ia.njobs = njobs;
   ia.tol = h->prm.tol;
   ia.status = h->status.as<int>();
   ia.max_m = max_m;
   ia.max_n = max_n;
   const size_t id_before = h->marks.size();
+  ia.jobs = reinterpret_cast<const IdJob*>(L.idjobs.as<char>() + o_plain);
+  ia.njobs = (int)plain_jobs.size();
   TIMED(SYMHSS_K_ID, 0.0, launch_cpqr(ia, s));
+  ia.jobs = reinterpret_cast<const IdJob*>(L.idjobs.as<char>() + o_sketch);
+  ia.njobs = (int)sketch_jobs.size();
+  ia.tol = 0.25 * h->prm.tol;
+  TIMED(SYMHSS_K_ID, 0.0, launch_cpqr(ia, s));
+  ia.tol = h->prm.tol;
   const size_t id_mark = h->marks.size() > id_before ? id_before : (size_t)-1;
   std::vector<int> hr(njobs), hp(perm_total);
   CK(cudaMemcpyAsync(hr.data(), L.rankbuf.p, njobs * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -558,6 +635,38 @@ int compress_level(symhss_s* h, int l, cudaStream_t s) {
     for (const IdJob& j : jobs) w += id_flops(j.m, j.n, hr[j.out_idx]);
     h->marks[id_mark].work = w;
   }
+  // a sketch too thin for the rank it revealed: redo that ID on the full matrix
+  std::vector<IdJob> cur = jobs;
+  {
+    std::vector<IdJob> redo;
+    for (int i = 0; i < njobs; ++i)
+      if (sk_rows[i] > 0 && fixed < 0 && 2 * hr[i] >= 2 * sk_rows[i] - p_over) {
+        redo.push_back(full[i]);
+        cur[i] = full[i];
+      }
+    h->st.sketch_redo += (long long)redo.size();
+    if (!redo.empty()) {
+      int mm = 1;
+      for (const IdJob& j : redo) mm = std::max(mm, j.m);
+      Packer pr;
+      pr.add(redo);
+      CK(pr.upload(L.idjobs, s));
+      ia.jobs = L.idjobs.as<IdJob>();
+      ia.njobs = (int)redo.size();
+      ia.max_m = mm;
+      const size_t rb = h->marks.size();
+      TIMED(SYMHSS_K_ID, 0.0, launch_cpqr(ia, s));
+      CK(cudaMemcpyAsync(hr.data(), L.rankbuf.p, njobs * sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(hp.data(), L.permbuf.p, perm_total * sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (h->marks.size() > rb) {
+        double w = 0;
+        for (const IdJob& j : redo) w += id_flops(j.m, j.n, hr[j.out_idx]);
+        h->marks[rb].work = w;
+      }
+      ia.max_m = max_m;
+    }
+  }
   h->st.pairs_evaluated += tb.pairs;
   if (!sym) {  // raise the lower of the row / column ranks of each half to the higher
     std::vector<IdJob> more;
@@ -567,8 +676,13 @@ int compress_level(symhss_s* h, int l, cudaStream_t s) {
         const int k = std::max(hr[ic], hr[ir]);
         for (int idx : {ic, ir}) {
           if (hr[idx] < k) {
-            IdJob j = jobs[idx];
-            j.start = hr[idx];
+            IdJob j = cur[idx];
+            if (j.m_off != full[idx].m_off && 2 * k >= 2 * sk_rows[idx] - p_over) {
+              j = full[idx];  // restart on the full matrix with the raised rank
+              j.start = 0;
+            } else {
+              j.start = hr[idx];
+            }
             j.fixed = k;
             more.push_back(j);
           }
@@ -580,6 +694,11 @@ int compress_level(symhss_s* h, int l, cudaStream_t s) {
       CK(pk2.upload(L.idjobs, s));
       ia.jobs = L.idjobs.as<IdJob>();
       ia.njobs = (int)more.size();
+      {
+        int mm = 1;
+        for (const IdJob& j : more) mm = std::max(mm, j.m);
+        ia.max_m = mm;
+      }
       const size_t more_before = h->marks.size();
       TIMED(SYMHSS_K_ID, 0.0, launch_cpqr(ia, s));
       const size_t more_mark = h->marks.size() > more_before ? more_before : (size_t)-1;
@@ -618,6 +737,11 @@ int compress_level(symhss_s* h, int l, cudaStream_t s) {
     }
   }
   L.h_rank = hr;
+  for (int p = 0; p < 2; ++p) {
+    int mx = 0;
+    for (const auto& bx : boxes) mx = std::max(mx, bx.rank[p]);
+    h->lvl_max_rank[l][p] = mx;
+  }
   return SYMHSS_OK;
 }
 
@@ -1010,6 +1134,7 @@ int symhss_compress(symhss_t h, void* stream) {
   h->st.pairs_evaluated = 0;
   h->st.id_count = 0;
   h->st.flops_id = 0;
+  h->st.sketch_redo = 0;
   for (int c = 0; c < SYMHSS_K_COUNT; ++c) {
     h->st.kernel_ms[c] = 0;
     h->st.kernel_launches[c] = 0;
@@ -1281,7 +1406,7 @@ int symhss_stats(symhss_t h, symhss_stats_t* out) {
   if (!h || !out) return SYMHSS_ERR_INVALID;
   long long bytes = (long long)h->pts.cap + (long long)h->status.cap + h->xin.cap + h->xout.cap;
   for (auto& L : h->levels) {
-    for (DevBuf* b : {&L.mr, &L.tbuf, &L.permbuf, &L.rankbuf, &L.refbuf, &L.clists, &L.idjobs, &L.D, &L.piv,
+    for (DevBuf* b : {&L.mr, &L.tbuf, &L.permbuf, &L.rankbuf, &L.refbuf, &L.clists, &L.idjobs, &L.slices, &L.skmeta, &L.D, &L.piv,
                       &L.rxpiv, &L.info, &L.X, &L.RX, &L.At, &L.qbuf, &L.flists, &L.lujobs, &L.cjobs, &L.G,
                       &L.FT, &L.TMP, &L.slists})
       bytes += (long long)b->cap;

@@ -30,8 +30,8 @@ SYMHSS_FP64 = 0
 SYMHSS_HOST = 0
 SYMHSS_DEVICE = 1
 SYMHSS_MAX_LEVELS = 32
-K_TILES, K_ID, K_GETRF, K_GETRS, K_OTHER = 0, 1, 2, 3, 4
-K_NAMES = ["tiles", "id", "getrf", "getrs", "other"]
+K_TILES, K_ID, K_GETRF, K_GETRS, K_OTHER, K_SKETCH = 0, 1, 2, 3, 4, 5
+K_NAMES = ["tiles", "id", "getrf", "getrs", "other", "sketch"]
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int)
@@ -60,7 +60,7 @@ class symhss_stats_t(C.Structure):
                 ("ms_basis", C.c_double), ("pairs_evaluated", C.c_longlong), ("id_count", C.c_longlong),
                 ("flops_lu", C.c_double), ("flops_id", C.c_double), ("device_bytes", C.c_longlong),
                 ("kernel_ms", C.c_double * 8), ("kernel_launches", C.c_longlong * 8),
-                ("kernel_work", C.c_double * 8)]
+                ("kernel_work", C.c_double * 8), ("sketch_redo", C.c_longlong)]
 
 
 class symhss_points(C.Structure):
@@ -93,6 +93,8 @@ _SIGNATURES = [
     ("symhss_column_id_noalloc", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_longlong, C.c_int,
                                            C.c_double, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_longlong,
                                            C.c_void_p]),
+    ("symhss_sketch", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_longlong, C.c_int, C.c_int,
+                                C.c_ulonglong, C.c_void_p, C.c_int, C.c_longlong, C.c_void_p]),
     ("symhss_lu_batched", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_longlong, C.c_int, C.c_void_p,
                                     C.c_void_p, C.c_void_p]),
     ("symhss_lu_solve_batched", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_longlong, C.c_void_p, C.c_void_p,
@@ -217,6 +219,12 @@ def symhss_column_id_noalloc(a: int, m: int, n: int, lda: int, stride_a: int, ba
     check(lib.symhss_column_id_noalloc(C.c_void_p(a), m, n, lda, stride_a, batch, tol, fixed_rank, C.c_void_p(rank),
                                        C.c_void_p(perm), C.c_void_p(t), stride_t, C.c_void_p(stream)),
           "symhss_column_id_noalloc")
+
+
+def symhss_sketch(a: int, m: int, n: int, lda: int, stride_a: int, batch: int, s: int, seed: int, y: int, ldy: int,
+                  stride_y: int, stream: int = 0) -> None:
+    check(lib.symhss_sketch(C.c_void_p(a), m, n, lda, stride_a, batch, s, seed, C.c_void_p(y), ldy, stride_y,
+                            C.c_void_p(stream)), "symhss_sketch")
 
 
 def symhss_lu_batched(a: int, n: int, lda: int, stride_a: int, batch: int, ipiv: int, info: int,

@@ -205,3 +205,41 @@ def test_lu_reports_singular_block(S):
                         torch.cuda.current_stream().cuda_stream)
     torch.cuda.synchronize()
     assert int(info[0]) == 4
+
+
+def _splitmix(x):
+    x = x + np.uint64(0x9E3779B97F4A7C15)
+    x = (x ^ (x >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+    x = (x ^ (x >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    return x ^ (x >> np.uint64(31))
+
+
+def _omega(seed, b, s, m):
+    """Rademacher matrix of the sketch from its published counter-based definition (splitmix64)."""
+    i = np.arange(s, dtype=np.uint64)[:, None]
+    k = np.arange(m, dtype=np.uint64)[None, :]
+    with np.errstate(over="ignore"):
+        h = _splitmix(np.uint64(seed) ^ (np.uint64(b) * np.uint64(0xD1B54A32D192ED03)) ^
+                      (i * np.uint64(0x8CB92BA72F3D8DD7)) ^ k)
+    return np.where((h >> np.uint64(63)) != 0, -1.0, 1.0)
+
+
+@pytest.mark.parametrize("m,n,s,batch", [(64, 16, 8, 1), (384, 128, 64, 3), (830, 265, 170, 2), (1000, 3, 40, 1)])
+def test_tensor_core_sketch_matches_fp64_product(S, m, n, s, batch):
+    """Y = Omega M on the tensor cores (exact 8-bit slices, FP32 accumulation) equals the FP64 product
+    to rounding: column-relative error <= 4e-15 (seven FP64 additions of exact slice products)."""
+    rng = np.random.default_rng(m + n)
+    mats = (rng.normal(size=(batch, m, n)) + 1j * rng.normal(size=(batch, m, n))) * \
+        np.exp(3 * rng.normal(size=(batch, 1, n)))
+    mats[:, :, 0] *= 1e-30
+    da = torch.as_tensor(np.ascontiguousarray(np.transpose(mats, (0, 2, 1)))).to("cuda")
+    y = torch.zeros((batch, n, s), dtype=torch.complex128, device="cuda")
+    seed = 987654321
+    S.symhss_sketch(da.data_ptr(), m, n, m, m * n, batch, s, seed, y.data_ptr(), s, s * n,
+                    torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    yg = np.transpose(y.cpu().numpy(), (0, 2, 1))
+    for b in range(batch):
+        ref = _omega(seed, b, s, m) @ mats[b]
+        err = np.abs(yg[b] - ref).max(axis=0) / np.abs(ref).max(axis=0)
+        assert err.max() <= 4e-15, (b, err.max())

@@ -62,8 +62,12 @@ def test_disk512_matches_dense_and_bessel(solver_mod, mode):
 def test_star2048_matches_dense(solver_mod, mode):
     c = star(2048)
     prm = OK.Params.from_wavenumbers(20.0, 30.0)
-    x, s = _run(solver_mod, c, prm, mode, leaf=128, nproxy=64, tol=1e-10)
     xd = OK.dense_solve(c, prm)
+    x, s = _run(solver_mod, c, prm, mode, leaf=128, nproxy=64, tol=1e-10)
+    assert _rel(x, xd) <= 1e-8
+    s.close()
+    # the plain ID (no sketch) reproduces the oracle's ranks
+    x, s = _run(solver_mod, c, prm, mode, leaf=128, nproxy=64, tol=1e-10, oversample=0)
     assert _rel(x, xd) <= 1e-8
     oracle = OH.HSS(c, prm, OH.Options(leaf=128, nproxy=64, tol=1e-10, symmetric=(mode == "sym"))).compress()
     depth = oracle.depth
@@ -155,3 +159,18 @@ def test_benchmark_workload_matches_oracle_hss(solver_mod):
     s.close()
     xo, _ = OH.hss_solve(c, prm, OH.Options(leaf=w["leaf"], nproxy=w["nproxy"], tol=w["tol"]))
     assert _rel(x, xo) <= 1e-8
+
+
+def test_sketched_and_plain_ids_agree(solver_mod):
+    """The randomized-sketch ID (default) and the ID of the full proxy matrices (oversample 0)
+    give the same solution to the solver tolerance, in both modes."""
+    c = star(2048)
+    prm = OK.Params.from_wavenumbers(20.0, 30.0)
+    xd = OK.dense_solve(c, prm)
+    for mode in ("sym", "base"):
+        xs, s1 = _run(solver_mod, c, prm, mode, leaf=128, nproxy=64, tol=1e-10)
+        xp, s2 = _run(solver_mod, c, prm, mode, leaf=128, nproxy=64, tol=1e-10, oversample=0)
+        assert _rel(xs, xd) <= 1e-8 and _rel(xp, xd) <= 1e-8
+        assert s1.stats().kernel_launches[5] > 0 and s2.stats().kernel_launches[5] == 0
+        s1.close()
+        s2.close()
