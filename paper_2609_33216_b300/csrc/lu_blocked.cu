@@ -4,8 +4,9 @@
 // spreads over many thread blocks even when the batch holds a single matrix (the
 // root block):
 //   1. panel: one block per matrix factors columns [j, j + w) of rows [j, n) with
-//      partial pivoting (swaps applied inside the panel only);
-//   2. swaps + TRSM: one thread per column outside the panel applies the panel's
+//      partial pivoting (swaps applied inside the panel only), the panel held in
+//      shared memory when it fits;
+//   2. swaps + TRSM: one warp per column outside the panel applies the panel's
 //      row interchanges and, right of the panel, solves L11 U12 = A12;
 //   3. trailing update: A22 -= L21 U12 in 32 x 32 tiles, one block per tile.
 // The pivots follow the LAPACK convention (row ipiv[k] was swapped with row k at
@@ -20,7 +21,6 @@ constexpr int kNb = 16;          // panel width
 constexpr int kPanelThreads = 256;
 constexpr int kPanelWarps = kPanelThreads / 32;
 constexpr int kTs = 32;          // trailing-update tile
-constexpr int kSwapThreads = 128;
 
 __global__ void __launch_bounds__(kPanelThreads) panel_kernel(const LuLaunch a, int j) {
   __shared__ double red[kPanelWarps];
@@ -86,44 +86,144 @@ __global__ void __launch_bounds__(kPanelThreads) panel_kernel(const LuLaunch a, 
   }
 }
 
-__global__ void __launch_bounds__(kSwapThreads) swap_trsm_kernel(const LuLaunch a, int j) {
-  __shared__ double2 l11[kNb][kNb];
-  __shared__ int sp[kNb];
+// Panel factorisation with the panel (rows [j, n) x w columns) staged in shared
+// memory; the pivot search of column c + 1 is fused into the update of column c.
+__global__ void __launch_bounds__(kPanelThreads) panel_smem_kernel(const LuLaunch a, int j) {
+  extern __shared__ __align__(16) double2 P[];  // column-major: P[q * rows + i]
+  __shared__ double red[kPanelWarps];
+  __shared__ int redi[kPanelWarps];
+  __shared__ int s_piv;
+  __shared__ double s_pv;
   const LuJob jb = a.jobs[blockIdx.x];
   const int n = jb.n, ld = jb.ld;
-  if (j >= n) return;
+  if (j >= n) return;  // uniform per block
+  const int w = min(kNb, n - j), rows = n - j;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double2* A = a.base + jb.a_off;
+  int* piv = a.piv + jb.piv_off;
+  for (int e = tid; e < rows * w; e += kPanelThreads) {
+    const int i = e % rows, q = e / rows;
+    P[q * rows + i] = A[j + i + (long long)(j + q) * ld];
+  }
+  __syncthreads();
+  double bv = -1.0;
+  int bi = rows;
+  for (int i = tid; i < rows; i += kPanelThreads) {
+    const double v = cabs1(P[i]);
+    if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
+  }
+  for (int c = 0; c < w; ++c) {
+    warp_argmax(bv, bi);
+    if (lane == 0) { red[warp] = bv; redi[warp] = bi; }
+    __syncthreads();
+    if (warp == 0) {
+      bv = lane < kPanelWarps ? red[lane] : -1.0;
+      bi = lane < kPanelWarps ? redi[lane] : rows;
+      warp_argmax(bv, bi);
+      if (lane == 0) { s_piv = bi; s_pv = bv; }
+    }
+    __syncthreads();
+    const int p = s_piv;
+    const bool zero = (s_pv == 0.0);
+    if (tid == 0) {
+      piv[j + c] = j + p;
+      if (zero) {
+        if (a.info[jb.info_idx] == 0) a.info[jb.info_idx] = j + c + 1;
+        atomicOr(a.status, ST_SINGULAR);
+      }
+    }
+    if (!zero && tid < w && p != c) {
+      const double2 t = P[tid * rows + c];
+      P[tid * rows + c] = P[tid * rows + p];
+      P[tid * rows + p] = t;
+    }
+    __syncthreads();
+    const double2 inv = zero ? make_double2(0.0, 0.0) : cinv(P[c * rows + c]);
+    bv = -1.0;
+    bi = rows;
+    for (int i = c + 1 + tid; i < rows; i += kPanelThreads) {
+      if (!zero) {
+        const double2 l = cmul(P[c * rows + i], inv);
+        P[c * rows + i] = l;
+        for (int q = c + 1; q < w; ++q) P[q * rows + i] = cfms(l, P[q * rows + c], P[q * rows + i]);
+      }
+      if (c + 1 < w) {
+        const double v = cabs1(P[(c + 1) * rows + i]);
+        if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < rows * w; e += kPanelThreads) {
+    const int i = e % rows, q = e / rows;
+    A[j + i + (long long)(j + q) * ld] = P[q * rows + i];
+  }
+}
+
+// Row interchanges of a panel and, right of it, L11 U12 = A12: one warp per column.
+// The panel's w interchanges touch at most 2w rows; their composition is a
+// permutation of that row set, built once per block, so each column is permuted by
+// a single gather (lane l ends with the value of row rows[l]); lanes 0..w-1 hold
+// rows j..j+w-1 and then solve the unit-lower 16 x 16 system with shuffles.
+__global__ void __launch_bounds__(256) swap_trsm_warp_kernel(const LuLaunch a, int j) {
+  __shared__ double2 l11[kNb][kNb];
+  __shared__ int rows_s[2 * kNb];   // row set: j..j+w-1, then the outside pivot rows
+  __shared__ int src_s[2 * kNb];    // lane l takes its new value from row src_s[l]
+  __shared__ int nrows_s;
+  const LuJob jb = a.jobs[blockIdx.x];
+  const int n = jb.n, ld = jb.ld;
+  if (j >= n) return;  // uniform per block
   const int w = min(kNb, n - j);
   double2* A = a.base + jb.a_off;
   const int* piv = a.piv + jb.piv_off;
-  for (int e = threadIdx.x; e < w * w; e += kSwapThreads) {
+  for (int e = threadIdx.x; e < w * w; e += 256) {
     const int r = e % w, c = e / w;
     l11[r][c] = A[j + r + (long long)(j + c) * ld];
   }
-  if (threadIdx.x < w) sp[threadIdx.x] = piv[j + threadIdx.x];
+  if (threadIdx.x == 0) {
+    int cnt = w;
+    for (int r = 0; r < w; ++r) rows_s[r] = j + r;
+    for (int c = 0; c < w; ++c) {
+      const int p = piv[j + c];
+      if (p >= j + w) {
+        bool seen = false;
+        for (int q = w; q < cnt; ++q) seen |= (rows_s[q] == p);
+        if (!seen && cnt < 2 * kNb) rows_s[cnt++] = p;
+      }
+    }
+    // content[l] = original row currently stored at rows_s[l]; apply the swaps in order
+    int content[2 * kNb];
+    for (int l = 0; l < cnt; ++l) content[l] = rows_s[l];
+    for (int c = 0; c < w; ++c) {
+      const int p = piv[j + c];
+      if (p == j + c) continue;
+      int lp = -1;
+      for (int q = 0; q < cnt; ++q)
+        if (rows_s[q] == p) lp = q;
+      if (lp < 0) continue;  // cannot happen: every pivot row is in the set
+      const int t = content[c];
+      content[c] = content[lp];
+      content[lp] = t;
+    }
+    for (int l = 0; l < cnt; ++l) src_s[l] = content[l];
+    nrows_s = cnt;
+  }
   __syncthreads();
-  const int col = blockIdx.y * kSwapThreads + threadIdx.x;
-  if (col >= n || (col >= j && col < j + w)) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int col = blockIdx.y * 8 + warp;
+  if (col >= n || (col >= j && col < j + w)) return;  // uniform per warp
   double2* cc = A + (long long)col * ld;
-  for (int c = 0; c < w; ++c) {
-    const int p = sp[c];
-    if (p != j + c) {
-      const double2 t = cc[j + c];
-      cc[j + c] = cc[p];
-      cc[p] = t;
+  const int cnt = nrows_s;
+  double2 x = lane < cnt ? cc[src_s[lane]] : make_double2(0.0, 0.0);
+  __syncwarp();
+  if (lane >= w && lane < cnt) cc[rows_s[lane]] = x;
+  if (col >= j + w) {
+    for (int c = 0; c < w; ++c) {
+      const double2 xc = make_double2(__shfl_sync(0xffffffffu, x.x, c), __shfl_sync(0xffffffffu, x.y, c));
+      if (lane > c && lane < w) x = cfms(l11[lane][c], xc, x);
     }
   }
-  if (col < j + w) return;
-  double2 x[kNb];
-#pragma unroll
-  for (int r = 0; r < kNb; ++r) x[r] = r < w ? cc[j + r] : make_double2(0.0, 0.0);
-#pragma unroll
-  for (int c = 0; c < kNb; ++c) {
-#pragma unroll
-    for (int r = c + 1; r < kNb; ++r) x[r] = cfms(l11[r][c], x[c], x[r]);
-  }
-#pragma unroll
-  for (int r = 0; r < kNb; ++r)
-    if (r < w) cc[j + r] = x[r];
+  if (lane < w) cc[j + lane] = x;
 }
 
 // A22 -= L21 U12 for the tile (blockIdx.y, blockIdx.z) of every matrix
@@ -179,14 +279,22 @@ cudaError_t launch_getrf(const LuLaunch& a, cudaStream_t s) {
   symhss::count_launches(1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int ncolblk = (a.max_n + kSwapThreads - 1) / kSwapThreads;
+  // panels of up to 780 rows fit in shared memory (780 x 16 x 16 B = 195 KB)
+  const size_t panel_smem = (size_t)a.max_n * kNb * sizeof(double2);
+  const bool smem_panel = panel_smem <= 200 * 1024;
+  if (smem_panel) {
+    e = cudaFuncSetAttribute(panel_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem);
+    if (e != cudaSuccess) return e;
+  }
+  const int ncolblk = (a.max_n + 7) / 8;
   for (int j = 0; j < a.max_n; j += kNb) {
-    panel_kernel<<<a.njobs, kPanelThreads, 0, s>>>(a, j);
+    if (smem_panel) panel_smem_kernel<<<a.njobs, kPanelThreads, panel_smem, s>>>(a, j);
+    else panel_kernel<<<a.njobs, kPanelThreads, 0, s>>>(a, j);
     symhss::count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int rest = a.max_n - j - kNb;
     if (rest <= 0) continue;
-    swap_trsm_kernel<<<dim3(a.njobs, ncolblk), kSwapThreads, 0, s>>>(a, j);
+    swap_trsm_warp_kernel<<<dim3(a.njobs, ncolblk), 256, 0, s>>>(a, j);
     symhss::count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int tiles = (rest + kTs - 1) / kTs;
@@ -196,7 +304,7 @@ cudaError_t launch_getrf(const LuLaunch& a, cudaStream_t s) {
   }
   // the last panel's interchanges still have to reach the columns left of it
   const int jlast = ((a.max_n - 1) / kNb) * kNb;
-  swap_trsm_kernel<<<dim3(a.njobs, ncolblk), kSwapThreads, 0, s>>>(a, jlast);
+  swap_trsm_warp_kernel<<<dim3(a.njobs, ncolblk), 256, 0, s>>>(a, jlast);
   symhss::count_launches(1);
   return cudaGetLastError();
 }
