@@ -1,6 +1,6 @@
 """Benchmark: symmetric HSS compress + factor + solve on one B300 (replicas for N > 1).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload star16k]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload star16k|batch64]
 
 Workload (default): star r(theta) = 1 + 0.3 cos(5 theta), 16384 Nystrom nodes (32768 complex128
 unknowns), k_ext = 20, k_int = 30, eps0 = 1, eps1 = (k_int/k_ext)^2, leaf 128, ID tolerance 1e-10,
@@ -8,6 +8,11 @@ rings of at least 64 proxy points at 1.5x the box radius, plane wave at angle 0.
 A step is one full compress + factor + right-hand side + solve of that scatterer through the
 C ABI, with the curve already resident on the device.  The symmetric single-ID solver is the
 headline; the non-symmetric two-ID baseline is timed on the same GPU and inputs.
+
+--workload batch64: 64 independent random star scatterers r = 1 + sum_{m=2..8} a_m cos(m theta + phi_m),
+a_m ~ U(0, 0.05), node counts log-uniform in [2048, 32768] (664375 nodes in total), k_ext ~ U(5, 40),
+k_int / k_ext ~ U(1.2, 2), solved together in one handle (one launch per kernel and tree height);
+a step is the whole batch.
 
 Metric: seconds per scatterer (compress + factor + solve); for N GPUs every rank solves its own
 copy of the workload (replicas, weak scaling) and value = max-over-ranks seconds per step / N.
@@ -106,12 +111,27 @@ def _measured_peaks():
         return {}
 
 
+def _is_batch(name):
+    from synth.curves import BATCH_WORKLOADS
+    return name in BATCH_WORKLOADS
+
+
 def _workload(name):
-    from synth import workload
-    return workload(name)
+    from synth.curves import batch_workload, workload
+    return batch_workload(name) if _is_batch(name) else workload(name)
 
 
 def _config(w, mode):
+    if "problems" in w:
+        P = w["problems"]
+        ns = [p["curve"].n for p in P]
+        k0 = [p["k0"] for p in P]
+        return {"workload": f"{w['name']}: {len(P)} random star scatterers in one batch, N={sum(ns)} nodes in "
+                            f"total ({min(ns)}..{max(ns)} per scatterer), k_ext in [{min(k0):.1f}, {max(k0):.1f}], "
+                            f"k_int/k_ext in [1.2, 2], eps1=(k_int/k_ext)^2, leaf {w['leaf']}, ID tol {w['tol']:g}, "
+                            f">= {w['nproxy']}-point proxy rings at 1.5x box radius",
+                "mode": mode, "l2": "inputs larger than L2 (tens of GB of tiles per step); 512 MiB flush too",
+                "parallelism": "replicas (one batch per GPU)"}
     c = w["curve"]
     return {"workload": f"{w['name']}: {c.name} curve, N={c.n} nodes ({2 * c.n} complex128 unknowns), "
                         f"k_ext={w['k0']:g}, k_int={w['k1']:g}, eps1=(k_int/k_ext)^2, leaf {w['leaf']}, "
@@ -128,18 +148,25 @@ def run_ours(args):
     import torch.distributed as dist
 
     from paper_2609_33216_b300 import symhss as S
-    from paper_2609_33216_b300.solver import Solver
+    from paper_2609_33216_b300.solver import BatchSolver, Solver
 
     rank, world, local = _env_rank()
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl")
     w = _workload(args.workload)
-    c = w["curve"]
+    batch = "problems" in w
+    curves = [p["curve"] for p in w["problems"]] if batch else [w["curve"]]
+    n_total = sum(cv.n for cv in curves)
     kw = dict(leaf=w["leaf"], nproxy=w["nproxy"], tol=w["tol"])
-    dev_curve = True
-    solvers = {m: Solver(c, w["k0"], w["k1"], w["eps0"], w["eps1"], mode=m, curve_on_device=dev_curve, **kw)
-               for m in ("sym", "base")}
+
+    def make(mode):
+        if batch:
+            P = w["problems"]
+            return BatchSolver(curves, [p["k0"] for p in P], [p["k1"] for p in P], [p["eps0"] for p in P],
+                               [p["eps1"] for p in P], mode=mode, **kw)
+        return Solver(w["curve"], w["k0"], w["k1"], w["eps0"], w["eps1"], mode=mode, curve_on_device=True, **kw)
+
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -155,8 +182,10 @@ def run_ours(args):
             torch.cuda.synchronize()
 
     results = {}
-    for mode in ("sym", "base"):
-        s = solvers[mode]
+    solvers = {}
+    for mode in ("base", "sym"):  # the symmetric handle stays alive for the end-to-end leg
+        s = make(mode)
+        solvers[mode] = s
         for _ in range(args.warmup):
             x = step(s)
         barrier()
@@ -189,21 +218,30 @@ def run_ours(args):
         if world > 1:
             dist.all_reduce(tot, op=dist.ReduceOp.MAX)
         st = s.stats()
-        results[mode] = dict(ms_total=float(tot.item()), times=times, x=x, stats=st, clocks=clocks,
+        results[mode] = dict(ms_total=float(tot.item()), times=times, x=x.cpu().numpy(), stats=st, clocks=clocks,
                              launches=launches, kms=kms, kwork=kwork, klaunch=klaunch)
+        del x
+        if mode == "base":
+            s.close()
+            torch.cuda.empty_cache()
 
-    xs = results["sym"]["x"].cpu().numpy()
-    xb = results["base"]["x"].cpu().numpy()
-    rel_diff = float(np.linalg.norm(xs - xb) / np.linalg.norm(xb))
+    xs = results["sym"]["x"]
+    xb = results["base"]["x"]
+    if batch:  # largest per-scatterer relative difference
+        e2e_tmp = solvers["sym"]
+        rel_diff = max(float(np.linalg.norm(xs[r:r + 2 * n] - xb[r:r + 2 * n]) / np.linalg.norm(xb[r:r + 2 * n]))
+                       for r, n in zip(e2e_tmp.row0, e2e_tmp.ns))
+    else:
+        rel_diff = float(np.linalg.norm(xs - xb) / np.linalg.norm(xb))
 
-    # end to end through the C ABI: host curve in, host solution out, every step
+    # end to end through the C ABI: host curves in, host solution out, every step
     e2e_s = solvers["sym"]
-    host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in c.arrays()]
-    xh = torch.empty(2 * c.n, dtype=torch.complex128).pin_memory()
-    curve_struct = S.curve_struct(c.n, [t.data_ptr() for t in host], S.SYMHSS_HOST)
+    host = [[torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in cv.arrays()] for cv in curves]
+    xh = torch.empty(2 * n_total, dtype=torch.complex128).pin_memory()
+    curve_structs = [S.curve_struct(cv.n, [t.data_ptr() for t in hs], S.SYMHSS_HOST) for cv, hs in zip(curves, host)]
 
     def e2e_step():
-        S.symhss_set_curve(e2e_s.h, curve_struct, stream.cuda_stream)
+        S.symhss_set_curves(e2e_s.h, curve_structs, stream.cuda_stream)
         x = step(e2e_s)
         xh.copy_(x, non_blocking=True)
         torch.cuda.synchronize()
@@ -264,14 +302,15 @@ def run_ours(args):
             "ranks": {"max_flux": st.max_rank[0], "max_trace": st.max_rank[1], "root_size": st.root_size,
                       "leaf_mean": [st.level_mean_rank[st.depth][0], st.level_mean_rank[st.depth][1]]},
             "roofline": roof,
-            "e2e": {"value": e2e_sec / world, "unit": "s", "h2d_bytes_per_step": 6 * 8 * c.n,
-                    "d2h_bytes_per_step": 16 * 2 * c.n},
+            "e2e": {"value": e2e_sec / world, "unit": "s", "h2d_bytes_per_step": 6 * 8 * n_total,
+                    "d2h_bytes_per_step": 16 * 2 * n_total},
             "gpu_launches": int(r["launches"]),
             "clocks": r["clocks"],
         }
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(w, args.cpu_sample_boxes)
         print(json.dumps(out), flush=True)
+    solvers["sym"].close()
     if world > 1:
         dist.destroy_process_group()
 
@@ -299,22 +338,17 @@ def run_profile(args):
 
 # ----------------------------------------------------------------------------- CPU oracle
 
-def cpu_baseline(w, sample_boxes: int):
-    """Time the FP64 oracle on a bounded sample of the workload and scale it to the whole job.
-
-    Sample: the leaf level of the oracle's compression and factorisation (M_R tiles, two column
-    IDs, diagonal-block LU, X = D^-1 R^T and Atilde) for `sample_boxes` of the leaf boxes; the
-    per-box time is multiplied by the number of leaf boxes.  Upper levels are not included, so
-    the value is a lower bound of the oracle's whole-job time.
-    """
+def _oracle_leaf_sample(curve, k0, k1, eps0, eps1, w, sample_boxes: int):
+    """Oracle leaf-level compress + factor of `sample_boxes` leaf boxes of one scatterer:
+    (seconds, boxes sampled, leaf boxes of the scatterer)."""
     import numpy as np
     import scipy.linalg as sla
 
-    from oracle.hss import HSS, Options
+    from oracle.hss import HSS, Options, cpqr_id
     from oracle.kernels import Params
 
-    prm = Params(w["k0"], w["k1"], w["eps0"], w["eps1"])
-    solver = HSS(w["curve"], prm, Options(leaf=w["leaf"], nproxy=w["nproxy"], tol=w["tol"]))
+    prm = Params(k0, k1, eps0, eps1)
+    solver = HSS(curve, prm, Options(leaf=w["leaf"], nproxy=w["nproxy"], tol=w["tol"]))
     lev = solver.levels[-1]
     for b in lev:
         ids = np.arange(b.begin, b.end)
@@ -322,7 +356,6 @@ def cpu_baseline(w, sample_boxes: int):
         b.actrow = [ids, ids]
     idx = np.linspace(0, len(lev) - 1, min(sample_boxes, len(lev))).astype(int)
     t0 = time.perf_counter()
-    from oracle.hss import cpqr_id
     for i in idx:
         b = lev[i]
         mr = solver.m_r(b, lev)
@@ -339,11 +372,41 @@ def cpu_baseline(w, sample_boxes: int):
         rt = solver._basis(b, solver.depth, row=False)
         x = sla.lu_solve(lu, rt)
         np.linalg.inv(rt.T @ x)
-    dt = time.perf_counter() - t0
+    return time.perf_counter() - t0, len(idx), len(lev)
+
+
+def cpu_baseline(w, sample_boxes: int):
+    """Time the FP64 oracle on a bounded sample of the workload and scale it to the whole job.
+
+    Sample: the leaf level of the oracle's compression and factorisation (M_R tiles, two column
+    IDs, diagonal-block LU, X = D^-1 R^T and Atilde) for `sample_boxes` of the leaf boxes; the
+    per-box time is multiplied by the number of leaf boxes (of every scatterer of a batch: the
+    sampled boxes are then spread over up to 4 scatterers).  Upper levels are not included, so
+    the value is a lower bound of the oracle's whole-job time.
+    """
+    import math as _m
+
+    if "problems" in w:
+        P = w["problems"]
+        total_leaves = sum(2 ** max(0, _m.ceil(_m.log2(p["curve"].n / w["leaf"]))) if p["curve"].n > w["leaf"] else 1
+                           for p in P)
+        picks = sorted(set(int(round(v)) for v in
+                           [i * (len(P) - 1) / max(1, min(4, len(P)) - 1) for i in range(min(4, len(P)))]))
+        per = max(1, sample_boxes // len(picks))
+        dt, cnt = 0.0, 0
+        for i in picks:
+            p = P[i]
+            d, c, _ = _oracle_leaf_sample(p["curve"], p["k0"], p["k1"], p["eps0"], p["eps1"], w, per)
+            dt += d
+            cnt += c
+        nlev, what = total_leaves, f"{cnt} leaf boxes of {len(picks)} of the {len(P)} scatterers"
+    else:
+        dt, cnt, nlev = _oracle_leaf_sample(w["curve"], w["k0"], w["k1"], w["eps0"], w["eps1"], w, sample_boxes)
+        what = f"{cnt} of {nlev} leaf boxes"
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    return {"value": dt / len(idx) * len(lev), "unit": "s", "cores": cores, "kind": "oracle",
-            "sample": f"leaf level only: compress+factor of {len(idx)} of {len(lev)} leaf boxes "
-                      f"({dt:.1f} s), scaled by {len(lev)}/{len(idx)}; numpy/scipy FP64, BLAS threads = host cores"}
+    return {"value": dt / cnt * nlev, "unit": "s", "cores": cores, "kind": "oracle",
+            "sample": f"leaf level only: compress+factor of {what} ({dt:.1f} s), scaled to all {nlev} leaf boxes; "
+                      f"numpy/scipy FP64, BLAS threads = host cores"}
 
 
 def run_reference(args):

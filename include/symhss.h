@@ -98,6 +98,8 @@ typedef struct {
 #define SYMHSS_K_OTHER  4   /* bases, R X, small GEMMs, copies, gather / scatter  */
 #define SYMHSS_K_SKETCH 5   /* tensor-core sketch Y = Omega M (slicing + tcgen05 GEMM) */
 #define SYMHSS_K_COUNT  8
+/* In a batch: n and nboxes_leaf are totals, depth and root_size maxima, and the
+ * level statistics cover level l of every problem that has it. */
 typedef struct {
   int n;                          /* nodes                                    */
   int depth;                      /* L: leaves are at level L, root at 0       */
@@ -136,8 +138,32 @@ int symhss_params_default(symhss_params* p);
 int symhss_create(const symhss_curve* curve, const symhss_params* prm, void* stream, symhss_t* out);
 
 /* Replace the node arrays by a new curve with the same n (same tree shape).
- * Invalidates any previous compression. */
+ * Invalidates any previous compression.  Single-problem handles only. */
 int symhss_set_curve(symhss_t h, const symhss_curve* curve, void* stream);
+
+/* A batch of `count` independent scatterers in one handle (many obstacles of
+ * uneven size solved together; each is the problem of Sec. 2 on its own curve).
+ * curves[c] and prms[c] describe problem c: wavenumbers and material constants
+ * (k0, k1, eps0, eps1) may differ between problems; every other field of prms[c]
+ * must equal that of prms[0] (else SYMHSS_ERR_INVALID).  Each problem gets its
+ * own tree; compress / factor / solve then process the boxes of every problem at
+ * the same tree height (counted from the leaves) together, one launch per kernel
+ * and height, so the launch count follows the tallest tree, not the batch size.
+ * Batch vectors (rhs, x of symhss_solve) stack the problems' [eq1; eq2] blocks in
+ * problem order: problem c occupies rows [row0_c, row0_c + 2 n_c) with
+ * row0_c = 2 (n_0 + ... + n_(c-1)), and a column has 2 (n_0 + ... + n_(count-1))
+ * entries.  symhss_create is the count = 1 case.  The batch size is bounded by
+ * device memory only (about the sum of the single-problem footprints). */
+int symhss_create_batch(const symhss_curve* curves, const symhss_params* prms, int count, void* stream,
+                        symhss_t* out);
+
+/* Replace every problem's curve (same count and same n per problem). */
+int symhss_set_curves(symhss_t h, const symhss_curve* curves, int count, void* stream);
+
+/* Batch layout: *count problems (if count != NULL); n[c] nodes, depth[c] tree
+ * depth and row0[c] first row of its block in batch vectors, for each array that
+ * is not NULL (each with room for the problem count). */
+int symhss_batch_info(symhss_t h, int* count, int* n, int* depth, long long* row0);
 
 /* Proxy-method compression of every level (Sec. 4.1): kernel tiles M_R, one
  * column ID per box and component (two more row IDs of M_L per box with
@@ -151,7 +177,7 @@ int symhss_factor(symhss_t h, void* stream);
 /* Right-hand side of the handle's system for the plane wave
  * u_in = exp(i k0 (x cos(angle) + y sin(angle))): [-eps0 W u_in ; W du_in/dnu]
  * (Eq. 15; the unscaled form without W for SYMHSS_NONSYM).  rhs: device
- * complex128[2n]. */
+ * complex128[2n] (a batch: every problem's block with its own k0 and eps0). */
 int symhss_rhs_plane_wave(symhss_t h, double angle, void* rhs, void* stream);
 
 /* Solve A x = rhs for `nrhs` right-hand sides (Sec. 4.2).  rhs, x: device
@@ -165,9 +191,12 @@ int symhss_solve_host(symhss_t h, const void* rhs_host, void* x_host, int nrhs, 
 /* Statistics of the last phases (device-synchronising). */
 int symhss_stats(symhss_t h, symhss_stats_t* out);
 
-/* Column-ID ranks of level `level` (1..depth): out[2*b + h] for box b and part h.
- * `out` is a host int array of 2 * 2^level entries. */
+/* Column-ID ranks of level `level` (1..depth) of the first problem: out[2*b + h]
+ * for box b and part h.  `out` is a host int array of 2 * 2^level entries. */
 int symhss_level_ranks(symhss_t h, int level, int* out);
+
+/* As symhss_level_ranks for problem `problem` of a batch (level 1..depth[problem]). */
+int symhss_problem_ranks(symhss_t h, int problem, int level, int* out);
 
 /* Release everything the handle owns.  NULL is accepted. */
 int symhss_destroy(symhss_t h);

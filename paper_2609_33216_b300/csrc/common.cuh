@@ -109,6 +109,8 @@ struct TileJob {
   int ld;
   int flags;               // TILE_SRC_IS_THREAD: thread points are sources (transposed output)
                            // TILE_UNSCALED: the baseline system of Sec. 6
+  int prm;                 // index of this job's physical constants in TileLaunch::kps
+  int pad_;
 };
 enum : int { TILE_SRC_IS_THREAD = 1, TILE_UNSCALED = 2 };
 
@@ -123,7 +125,7 @@ struct TileLaunch {
   int nchunks;
   double2* out;
   int* status;
-  KernelParams kp;
+  const KernelParams* kps;  // device array, one entry per problem
 };
 
 constexpr int TILE_T = 128;   // thread points per chunk (= threads per block)
@@ -283,16 +285,19 @@ struct CopyJob { long long src_off, dst_off; int rows, cols, lds, ldd; };
 cudaError_t launch_copy_blocks(const double2* src, double2* dst, const CopyJob* jobs, int njobs,
                                cudaStream_t s);
 
-// Leaf boxes are contiguous node ranges [begin, begin + len); their vectors hold
-// [eq1 rows; eq2 rows] of the box (size 2 len) with nrhs columns.
-struct LeafJob { long long off; int begin, len; };
-cudaError_t launch_leaf_gather(const double2* f, int ldf, double2* g, const LeafJob* jobs, int njobs,
-                               int nrhs, int n, cudaStream_t s);
-cudaError_t launch_leaf_scatter(const double2* g, double2* x, int ldx, const LeafJob* jobs,
-                                int njobs, int nrhs, int n, cudaStream_t s);
+// Leaf boxes are contiguous node ranges [begin, begin + len) of a problem with n
+// nodes whose [eq1; eq2] block starts at `base` in the global vectors; the box
+// vector holds [eq1 rows; eq2 rows] of the box (size 2 len) with nrhs columns.
+struct LeafJob { long long off; long long base; int begin, len, n, pad_; };
+cudaError_t launch_leaf_gather(const double2* f, long long ldf, double2* g, const LeafJob* jobs, int njobs,
+                               int nrhs, cudaStream_t s);
+cudaError_t launch_leaf_scatter(const double2* g, double2* x, long long ldx, const LeafJob* jobs,
+                                int njobs, int nrhs, cudaStream_t s);
 
-cudaError_t launch_plane_wave(const double* x, const double* y, const double* nx, const double* ny,
-                              const double* w, int n, double k0, double eps0, double angle,
+// Plane-wave right-hand side of problem jobs[j]: nodes [node0, node0 + n) of the
+// point table, rows [vec0, vec0 + 2n) of rhs ([eq1; eq2]).
+struct WaveJob { int node0, n; long long vec0; double k0, eps0; };
+cudaError_t launch_plane_wave(const PointTable& t, const WaveJob* jobs, int njobs, int max_n, double angle,
                               int scaled, double2* rhs, cudaStream_t s);
 
 }  // namespace symhss

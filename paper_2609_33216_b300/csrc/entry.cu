@@ -88,12 +88,15 @@ int symhss_kernel_block(const symhss_params* prm, const symhss_points* obs, cons
   TileJob jb;
   jb.tp_off = 0; jb.n_tp = m; jb.lp_off = 0; jb.n_lp = n; jb.out_off = 0; jb.ld = ld;
   jb.flags = scaled ? 0 : TILE_UNSCALED;
+  jb.prm = 0;
+  jb.pad_ = 0;
   std::vector<TileChunk> ch;
   for (int a = 0; a < m; a += TILE_T)
     for (int b = 0; b < n; b += TILE_L) ch.push_back(TileChunk{0, a, b, TILE_L});
   const size_t ints = 3 * (size_t)m + 3 * (size_t)n;
   TmpBuf buf;
-  const size_t bytes = ints * sizeof(int) + sizeof(TileJob) + ch.size() * sizeof(TileChunk) + sizeof(int) + 64;
+  const size_t bytes = ints * sizeof(int) + sizeof(TileJob) + ch.size() * sizeof(TileChunk) + sizeof(int) +
+                       sizeof(KernelParams) + 128;
   CKE(buf.alloc(bytes));
   std::vector<char> host(bytes, 0);
   char* hp = host.data();
@@ -104,6 +107,16 @@ int symhss_kernel_block(const symhss_params* prm, const symhss_points* obs, cons
   off = (off + 15) & ~size_t(15);
   const size_t o7 = put(&jb, sizeof(jb));
   const size_t o8 = put(ch.data(), ch.size() * sizeof(TileChunk));
+  off = (off + 15) & ~size_t(15);
+  KernelParams kp;
+  kp.k0 = prm->k0; kp.k1 = prm->k1; kp.eps0 = prm->eps0; kp.eps1 = prm->eps1;
+  kp.e0sq = prm->eps0 * prm->eps0; kp.e1sq = prm->eps1 * prm->eps1;
+  kp.half_ft = 0.5 * (prm->eps0 + prm->eps1);
+  kp.lhk0 = std::log(0.5 * prm->k0);
+  kp.lhk1 = std::log(0.5 * prm->k1);
+  kp.ik0 = 1.0 / prm->k0;
+  kp.ik1 = 1.0 / prm->k1;
+  const size_t o10 = put(&kp, sizeof(kp));
   const size_t o9 = off;
   CKE(cudaMemcpyAsync(buf.p, hp, bytes, cudaMemcpyHostToDevice, s));
   char* d = reinterpret_cast<char*>(buf.p);
@@ -121,13 +134,7 @@ int symhss_kernel_block(const symhss_params* prm, const symhss_points* obs, cons
   a.nchunks = (int)ch.size();
   a.out = reinterpret_cast<double2*>(out);
   a.status = reinterpret_cast<int*>(d + o9);
-  a.kp.k0 = prm->k0; a.kp.k1 = prm->k1; a.kp.eps0 = prm->eps0; a.kp.eps1 = prm->eps1;
-  a.kp.e0sq = prm->eps0 * prm->eps0; a.kp.e1sq = prm->eps1 * prm->eps1;
-  a.kp.half_ft = 0.5 * (prm->eps0 + prm->eps1);
-  a.kp.lhk0 = std::log(0.5 * prm->k0);
-  a.kp.lhk1 = std::log(0.5 * prm->k1);
-  a.kp.ik0 = 1.0 / prm->k0;
-  a.kp.ik1 = 1.0 / prm->k1;
+  a.kps = reinterpret_cast<const KernelParams*>(d + o10);
   CKE(launch_tiles(a, s));
   int st = 0;
   CKE(cudaMemcpyAsync(&st, a.status, sizeof(int), cudaMemcpyDeviceToHost, s));

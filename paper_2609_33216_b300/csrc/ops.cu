@@ -104,41 +104,43 @@ __global__ void __launch_bounds__(kOpsThreads) copy_kernel(const double2* src, d
   }
 }
 
-__global__ void __launch_bounds__(kOpsThreads) leaf_gather_kernel(const double2* f, int ldf, double2* g,
-                                                                  const LeafJob* jobs, int nrhs, int n) {
+__global__ void __launch_bounds__(kOpsThreads) leaf_gather_kernel(const double2* f, long long ldf, double2* g,
+                                                                  const LeafJob* jobs, int nrhs) {
   const LeafJob jb = jobs[blockIdx.x];
   const int size = 2 * jb.len;
   for (int e = threadIdx.x; e < size * nrhs; e += blockDim.x) {
     const int i = e % size, c = e / size;
-    const int src = i < jb.len ? jb.begin + i : n + jb.begin + (i - jb.len);
+    const long long src = jb.base + (i < jb.len ? jb.begin + i : jb.n + jb.begin + (i - jb.len));
     g[jb.off + i + (long long)c * size] = f[src + (long long)c * ldf];
   }
 }
 
-__global__ void __launch_bounds__(kOpsThreads) leaf_scatter_kernel(const double2* g, double2* x, int ldx,
-                                                                   const LeafJob* jobs, int nrhs, int n) {
+__global__ void __launch_bounds__(kOpsThreads) leaf_scatter_kernel(const double2* g, double2* x, long long ldx,
+                                                                   const LeafJob* jobs, int nrhs) {
   const LeafJob jb = jobs[blockIdx.x];
   const int size = 2 * jb.len;
   for (int e = threadIdx.x; e < size * nrhs; e += blockDim.x) {
     const int i = e % size, c = e / size;
-    const int dst = i < jb.len ? jb.begin + i : n + jb.begin + (i - jb.len);
+    const long long dst = jb.base + (i < jb.len ? jb.begin + i : jb.n + jb.begin + (i - jb.len));
     x[dst + (long long)c * ldx] = g[jb.off + i + (long long)c * size];
   }
 }
 
-__global__ void plane_wave_kernel(const double* x, const double* y, const double* nx, const double* ny,
-                                  const double* w, int n, double k0, double eps0, double ca, double sa,
-                                  int scaled, double2* rhs) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+__global__ void plane_wave_kernel(const PointTable t, const WaveJob* jobs, double ca, double sa, int scaled,
+                                  double2* rhs) {
+  const WaveJob jb = jobs[blockIdx.y];
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= jb.n) return;
+  const int i = jb.node0 + j;
   double sn, cs;
-  sincos(k0 * (x[i] * ca + y[i] * sa), &sn, &cs);
+  sincos(jb.k0 * (t.x[i] * ca + t.y[i] * sa), &sn, &cs);
   const double2 uin = make_double2(cs, sn);
-  const double dn = k0 * (nx[i] * ca + ny[i] * sa);
+  const double dn = jb.k0 * (t.nx[i] * ca + t.ny[i] * sa);
   const double2 dudn = make_double2(-dn * sn, dn * cs);  // i k0 (nu.dir) u_in
-  const double sc = scaled ? w[i] : 1.0;
-  rhs[i] = make_double2(-eps0 * sc * uin.x, -eps0 * sc * uin.y);
-  rhs[n + i] = make_double2(sc * dudn.x, sc * dudn.y);
+  const double sc = scaled ? t.w[i] : 1.0;
+  double2* r = rhs + jb.vec0;
+  r[j] = make_double2(-jb.eps0 * sc * uin.x, -jb.eps0 * sc * uin.y);
+  r[jb.n + j] = make_double2(sc * dudn.x, sc * dudn.y);
 }
 
 }  // namespace
@@ -175,28 +177,27 @@ cudaError_t launch_copy_blocks(const double2* src, double2* dst, const CopyJob* 
   return cudaGetLastError();
 }
 
-cudaError_t launch_leaf_gather(const double2* f, int ldf, double2* g, const LeafJob* jobs, int njobs,
-                               int nrhs, int n, cudaStream_t s) {
+cudaError_t launch_leaf_gather(const double2* f, long long ldf, double2* g, const LeafJob* jobs, int njobs,
+                               int nrhs, cudaStream_t s) {
   if (njobs <= 0) return cudaSuccess;
-  leaf_gather_kernel<<<njobs, kOpsThreads, 0, s>>>(f, ldf, g, jobs, nrhs, n);
+  leaf_gather_kernel<<<njobs, kOpsThreads, 0, s>>>(f, ldf, g, jobs, nrhs);
   symhss::count_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_leaf_scatter(const double2* g, double2* x, int ldx, const LeafJob* jobs, int njobs,
-                                int nrhs, int n, cudaStream_t s) {
+cudaError_t launch_leaf_scatter(const double2* g, double2* x, long long ldx, const LeafJob* jobs, int njobs,
+                                int nrhs, cudaStream_t s) {
   if (njobs <= 0) return cudaSuccess;
-  leaf_scatter_kernel<<<njobs, kOpsThreads, 0, s>>>(g, x, ldx, jobs, nrhs, n);
+  leaf_scatter_kernel<<<njobs, kOpsThreads, 0, s>>>(g, x, ldx, jobs, nrhs);
   symhss::count_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_plane_wave(const double* x, const double* y, const double* nx, const double* ny,
-                              const double* w, int n, double k0, double eps0, double angle,
+cudaError_t launch_plane_wave(const PointTable& t, const WaveJob* jobs, int njobs, int max_n, double angle,
                               int scaled, double2* rhs, cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  plane_wave_kernel<<<(n + 255) / 256, 256, 0, s>>>(x, y, nx, ny, w, n, k0, eps0, cos(angle), sin(angle),
-                                                    scaled, rhs);
+  if (njobs <= 0 || max_n <= 0) return cudaSuccess;
+  dim3 grid((max_n + 255) / 256, njobs);
+  plane_wave_kernel<<<grid, 256, 0, s>>>(t, jobs, cos(angle), sin(angle), scaled, rhs);
   symhss::count_launches(1);
   return cudaGetLastError();
 }

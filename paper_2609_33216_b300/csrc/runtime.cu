@@ -1,6 +1,12 @@
-// Host runtime of the symhss library: tree and proxy rings, level-by-level
+// Host runtime of the symhss library: trees and proxy rings, height-by-height
 // scheduling of the compression (Sec. 4.1), factorisation and solve (Sec. 4.2),
 // device memory, and the C ABI declared in include/symhss.h.
+//
+// A handle holds one or more independent scatterers ("problems"), each with its
+// own curve, wavenumbers, materials and tree.  Work is scheduled by tree height
+// (counted from the leaves): the boxes of every problem at height t are processed
+// together, one launch per kernel, so a batch of uneven scatterers costs no more
+// launches than its tallest tree.  A problem's root sits at height = its depth.
 //
 // Tree (Sec. 4.1, Theorem 1 setting): a binary tree over the node index order;
 // box [b, e) splits into [b, b + (e - b)/2) and the rest; all leaves at depth
@@ -9,9 +15,9 @@
 // P = max(nproxy, 8 ceil((2 max(k0, k1) R + 32) / 8)) equispaced points, outward
 // radial normals and weights 2 pi R / P.
 //
-// Compression of level l: each box's active unknowns are its nodes (leaf) or its
-// children's skeletons.  M_R rows are the near (point, equation) pairs -- active
-// rows of other boxes of the level strictly inside the proxy ring -- ordered
+// Compression of a box: its active unknowns are its nodes (leaf) or its children's
+// skeletons.  M_R rows are the near (point, equation) pairs -- active rows of other
+// boxes of the same problem and level strictly inside the proxy ring -- ordered
 // [equation 1 rows; equation 2 rows], then the P proxy points for equation 1 and
 // for equation 2; its columns are the box's active flux unknowns then trace
 // unknowns.  One column ID per half (symmetric mode, Eq. low-rank_R: L = R^T).
@@ -83,7 +89,7 @@ struct Packer {
 };
 
 struct HBox {
-  int begin = 0, end = 0;
+  int begin = 0, end = 0;  // node range in the handle's concatenated node order
   double cx = 0, cy = 0, rho = 0, R = 0;
   int P = 0;
   int proxy0 = 0;  // first proxy point in the point table
@@ -91,7 +97,7 @@ struct HBox {
   std::vector<int> act[2], actrow[2];
   int rank[2] = {0, 0}, rrank[2] = {0, 0};
   std::vector<int> perm[2], rperm[2];
-  long long t_off[2] = {0, 0}, rt_off[2] = {0, 0};  // into the level's T buffer
+  long long t_off[2] = {0, 0}, rt_off[2] = {0, 0};  // into the height's T buffer
   // factor
   int size = 0;      // diagonal-block order
   int k = 0;         // rank[0] + rank[1]
@@ -102,8 +108,18 @@ struct HBox {
   long long g_off = 0, ft_off = 0;
 };
 
-struct Level {
-  std::vector<HBox> boxes;
+// One scatterer of the handle.
+struct Problem {
+  symhss_params prm{};
+  int n = 0, depth = 0;
+  int node0 = 0;                           // first node in the concatenated node order
+  long long vec0 = 0;                      // first row of its [eq1; eq2] block in batch vectors
+  std::vector<std::vector<HBox>> levels;   // boxes of levels 0 .. depth
+  int lvl_max_rank[SYMHSS_MAX_LEVELS][2] = {};  // largest column-ID rank per level and part
+};
+
+// Device buffers of all boxes at one tree height (over every problem of the handle).
+struct Height {
   // compress
   DevBuf mr, tbuf, permbuf, rankbuf, refbuf, clists, idjobs, slices, skmeta;
   // factor
@@ -113,20 +129,29 @@ struct Level {
   std::vector<int> h_rank;
 };
 
+// A box at some height: problem p, level l, index b in that level.
+struct BoxRef {
+  int p, l, b;
+  HBox* bx;
+};
+
 }  // namespace symhss
 
 struct symhss_s {
-  symhss_params prm{};
-  int n = 0;
-  int depth = 0;
-  std::vector<double> hx, hy, hnx, hny, hw, hk;  // node arrays on the host
+  symhss_params prm{};                            // shared parameters (problem 0's)
+  std::vector<symhss::Problem> probs;
+  int ntot = 0;                                   // nodes over all problems
+  int maxdepth = 0;
+  std::vector<double> hx, hy, hnx, hny, hw, hk;  // concatenated node arrays on the host
   int npts = 0;                                   // nodes + proxy points
   symhss::DevBuf pts;                             // point table (7 arrays)
+  symhss::DevBuf kps;                             // KernelParams per problem
+  symhss::DevBuf waves;                           // WaveJob per problem
+  int max_n = 0;                                  // largest problem
   symhss::DevBuf status;
-  std::vector<symhss::Level> levels;              // 0 .. depth
+  std::vector<symhss::Height> heights;            // 0 .. maxdepth
   bool compressed = false, factored = false;
   symhss::DevBuf xin, xout;                       // host-buffer solve staging
-  symhss::DevBuf rhsbuf;
   cudaEvent_t ev[8] = {};
   // per-launch device timing: events recorded around each launch on the caller's stream
   std::vector<cudaEvent_t> evpool;
@@ -136,7 +161,6 @@ struct symhss_s {
   symhss_stats_t st{};
   cudaError_t last_cuda = cudaSuccess;
   std::vector<int> mark;                          // host scratch (size npts)
-  int lvl_max_rank[SYMHSS_MAX_LEVELS][2] = {};    // largest column-ID rank per level and part
 };
 
 namespace symhss {
@@ -251,49 +275,75 @@ int read_status(symhss_s* h, cudaStream_t s) {
   return SYMHSS_OK;
 }
 
-// Build the tree (host) and the point table (nodes + proxy rings).
-int build_geometry(symhss_s* h, cudaStream_t s) {
-  const int n = h->n;
-  const symhss_params& p = h->prm;
-  h->depth = tree_depth(n, p.leaf);
-  if (h->depth >= SYMHSS_MAX_LEVELS) return SYMHSS_ERR_INVALID;
-  // keep the levels' device buffers when the tree shape is unchanged (set_curve)
-  if ((int)h->levels.size() != h->depth + 1) {
-    h->levels.clear();
-    h->levels.resize(h->depth + 1);
+// The boxes of every problem at height t (level depth - t), problems in order;
+// roots (height = depth) only if `with_roots`.
+void height_boxes(symhss_s* h, int t, bool with_roots, std::vector<BoxRef>& out) {
+  out.clear();
+  for (int p = 0; p < (int)h->probs.size(); ++p) {
+    Problem& P = h->probs[p];
+    if (P.depth < t || (P.depth == t && !with_roots)) continue;
+    const int l = P.depth - t;
+    auto& bxs = P.levels[l];
+    for (int b = 0; b < (int)bxs.size(); ++b) out.push_back(BoxRef{p, l, b, &bxs[b]});
   }
-  for (auto& L : h->levels) L.boxes.clear();
-  h->levels[0].boxes.resize(1);
-  h->levels[0].boxes[0].begin = 0;
-  h->levels[0].boxes[0].end = n;
-  for (int l = 1; l <= h->depth; ++l) {
-    auto& prev = h->levels[l - 1].boxes;
-    auto& cur = h->levels[l].boxes;
-    cur.resize(2 * prev.size());
-    for (size_t i = 0; i < prev.size(); ++i) {
-      const int b = prev[i].begin, e = prev[i].end, mid = b + (e - b) / 2;
-      cur[2 * i].begin = b; cur[2 * i].end = mid;
-      cur[2 * i + 1].begin = mid; cur[2 * i + 1].end = e;
-      prev[i].child[0] = (int)(2 * i);
-      prev[i].child[1] = (int)(2 * i + 1);
+}
+
+// Build the trees (host) and the point table (nodes of every problem, then the proxy rings).
+int build_geometry(symhss_s* h, cudaStream_t s) {
+  int node0 = 0;
+  h->maxdepth = 0;
+  h->max_n = 0;
+  for (Problem& P : h->probs) {
+    P.depth = tree_depth(P.n, P.prm.leaf);
+    if (P.depth >= SYMHSS_MAX_LEVELS) return SYMHSS_ERR_INVALID;
+    P.node0 = node0;
+    P.vec0 = 2LL * node0;
+    node0 += P.n;
+    h->maxdepth = std::max(h->maxdepth, P.depth);
+    h->max_n = std::max(h->max_n, P.n);
+  }
+  h->ntot = node0;
+  // keep the heights' device buffers when the tallest tree is unchanged (set_curve)
+  if ((int)h->heights.size() != h->maxdepth + 1) {
+    h->heights.clear();
+    h->heights.resize(h->maxdepth + 1);
+  }
+  for (Problem& P : h->probs) {
+    P.levels.assign(P.depth + 1, {});
+    P.levels[0].resize(1);
+    P.levels[0][0].begin = P.node0;
+    P.levels[0][0].end = P.node0 + P.n;
+    for (int l = 1; l <= P.depth; ++l) {
+      auto& prev = P.levels[l - 1];
+      auto& cur = P.levels[l];
+      cur.resize(2 * prev.size());
+      for (size_t i = 0; i < prev.size(); ++i) {
+        const int b = prev[i].begin, e = prev[i].end, mid = b + (e - b) / 2;
+        cur[2 * i].begin = b; cur[2 * i].end = mid;
+        cur[2 * i + 1].begin = mid; cur[2 * i + 1].end = e;
+        prev[i].child[0] = (int)(2 * i);
+        prev[i].child[1] = (int)(2 * i + 1);
+      }
     }
   }
-  int npts = n;
-  for (int l = 0; l <= h->depth; ++l) {
-    for (auto& bx : h->levels[l].boxes) {
-      const int cnt = bx.end - bx.begin;
-      double sx = 0, sy = 0;
-      for (int i = bx.begin; i < bx.end; ++i) { sx += h->hx[i]; sy += h->hy[i]; }
-      bx.cx = cnt ? sx / cnt : 0.0;
-      bx.cy = cnt ? sy / cnt : 0.0;
-      double rho = 0;
-      for (int i = bx.begin; i < bx.end; ++i) rho = std::max(rho, std::hypot(h->hx[i] - bx.cx, h->hy[i] - bx.cy));
-      bx.rho = rho;
-      bx.R = p.proxy_factor * rho;
-      if (l > 0) {
-        bx.P = proxy_count(p, bx.R);
-        bx.proxy0 = npts;
-        npts += bx.P;
+  int npts = h->ntot;
+  for (Problem& P : h->probs) {
+    for (int l = 0; l <= P.depth; ++l) {
+      for (auto& bx : P.levels[l]) {
+        const int cnt = bx.end - bx.begin;
+        double sx = 0, sy = 0;
+        for (int i = bx.begin; i < bx.end; ++i) { sx += h->hx[i]; sy += h->hy[i]; }
+        bx.cx = cnt ? sx / cnt : 0.0;
+        bx.cy = cnt ? sy / cnt : 0.0;
+        double rho = 0;
+        for (int i = bx.begin; i < bx.end; ++i) rho = std::max(rho, std::hypot(h->hx[i] - bx.cx, h->hy[i] - bx.cy));
+        bx.rho = rho;
+        bx.R = P.prm.proxy_factor * rho;
+        if (l > 0) {
+          bx.P = proxy_count(P.prm, bx.R);
+          bx.proxy0 = npts;
+          npts += bx.P;
+        }
       }
     }
   }
@@ -302,24 +352,36 @@ int build_geometry(symhss_s* h, cudaStream_t s) {
   std::vector<double> tab(7 * np, 0.0);
   double *X = tab.data(), *Y = X + np, *NX = Y + np, *NY = NX + np, *W = NY + np, *K = W + np;
   int* ID = reinterpret_cast<int*>(K + np);
-  for (int i = 0; i < n; ++i) {
+  for (int i = 0; i < h->ntot; ++i) {
     X[i] = h->hx[i]; Y[i] = h->hy[i]; NX[i] = h->hnx[i]; NY[i] = h->hny[i]; W[i] = h->hw[i]; K[i] = h->hk[i];
     ID[i] = i;
   }
-  for (int l = 1; l <= h->depth; ++l) {
-    for (auto& bx : h->levels[l].boxes) {
-      for (int m = 0; m < bx.P; ++m) {
-        const double phi = 2.0 * kPi * m / bx.P;
-        const double c = std::cos(phi), sn = std::sin(phi);
-        const int q = bx.proxy0 + m;
-        X[q] = bx.cx + bx.R * c; Y[q] = bx.cy + bx.R * sn; NX[q] = c; NY[q] = sn;
-        W[q] = 2.0 * kPi * bx.R / bx.P; K[q] = 0.0; ID[q] = -1;
+  for (Problem& P : h->probs) {
+    for (int l = 1; l <= P.depth; ++l) {
+      for (auto& bx : P.levels[l]) {
+        for (int m = 0; m < bx.P; ++m) {
+          const double phi = 2.0 * kPi * m / bx.P;
+          const double c = std::cos(phi), sn = std::sin(phi);
+          const int q = bx.proxy0 + m;
+          X[q] = bx.cx + bx.R * c; Y[q] = bx.cy + bx.R * sn; NX[q] = c; NY[q] = sn;
+          W[q] = 2.0 * kPi * bx.R / bx.P; K[q] = 0.0; ID[q] = -1;
+        }
       }
     }
   }
   CK(h->pts.ensure(tab.size() * sizeof(double)));
   CK(cudaMemcpyAsync(h->pts.p, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-  CK(cudaStreamSynchronize(s));  // `tab` is pageable and goes out of scope
+  std::vector<KernelParams> kp;
+  std::vector<WaveJob> wv;
+  for (const Problem& P : h->probs) {
+    kp.push_back(kparams(P.prm));
+    wv.push_back(WaveJob{P.node0, P.n, P.vec0, P.prm.k0, P.prm.eps0});
+  }
+  CK(h->kps.ensure(kp.size() * sizeof(KernelParams)));
+  CK(cudaMemcpyAsync(h->kps.p, kp.data(), kp.size() * sizeof(KernelParams), cudaMemcpyHostToDevice, s));
+  CK(h->waves.ensure(wv.size() * sizeof(WaveJob)));
+  CK(cudaMemcpyAsync(h->waves.p, wv.data(), wv.size() * sizeof(WaveJob), cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));  // the host arrays are pageable and go out of scope
   h->mark.assign(np, -1);
   return SYMHSS_OK;
 }
@@ -354,10 +416,11 @@ struct TileBuilder {
   std::vector<TileJob> jobs;
   std::vector<TileChunk> chunks;
   long long pairs = 0;
-  // thread points from (list0 -> slot base0+i, list1 -> base1+i); loop points likewise
+  // thread points from (list0 -> slot base0+i, list1 -> base1+i); loop points likewise;
+  // `prm`: the problem whose constants the tile uses
   void add(std::vector<int>& mark, const std::vector<int>& t0, int tb0, const std::vector<int>& t1, int tb1,
            const std::vector<int>& l0, int lb0, const std::vector<int>& l1, int lb1, long long out_off, int ld,
-           int flags) {
+           int flags, int prm) {
     TileJob jb;
     jb.tp_off = (int)tp_pt.size();
     merge_slots(mark, t0, tb0, t1, tb1, tp_pt, tp_s0, tp_s1);
@@ -368,6 +431,8 @@ struct TileBuilder {
     jb.out_off = out_off;
     jb.ld = ld;
     jb.flags = flags;
+    jb.prm = prm;
+    jb.pad_ = 0;
     if (jb.n_tp == 0 || jb.n_lp == 0) return;
     jobs.push_back(jb);
     pairs += (long long)jb.n_tp * jb.n_lp;
@@ -408,14 +473,15 @@ struct TileBuilder {
     a.nchunks = (int)chunks.size();
     a.out = out;
     a.status = h->status.as<int>();
-    a.kp = kparams(h->prm);
+    a.kps = h->kps.as<KernelParams>();
     return launch_tiles(a, s);
   }
 };
 
 inline long long tcap(int n) { return (long long)(n / 2) * ((n + 1) / 2) + 1; }
 
-// Near points of box b among the active lists `which` (0: rows, 1: columns) of its level.
+// Near points of box b among the active lists of the other boxes of its level
+// (row lists if `rows`, else column lists), part `part`.
 void near_points(const symhss_s* h, const std::vector<HBox>& lev, int b, bool rows, int part,
                  std::vector<int>& out) {
   const HBox& bx = lev[b];
@@ -430,26 +496,30 @@ void near_points(const symhss_s* h, const std::vector<HBox>& lev, int b, bool ro
   }
 }
 
-int fixed_rank(const symhss_s* h, int level) {
+// Fixed rank of Sec. 4.3 at height t (level L - t): ceil(a^t kL); -1 with tolerance ranks.
+int fixed_rank(const symhss_s* h, int t) {
   if (h->prm.fixed_rank_kL <= 0) return -1;
-  return (int)std::ceil(std::pow(h->prm.rank_scale_a, h->depth - level) * h->prm.fixed_rank_kL);
+  return (int)std::ceil(std::pow(h->prm.rank_scale_a, t) * h->prm.fixed_rank_kL);
 }
 
-int compress_level(symhss_s* h, int l, cudaStream_t s) {
-  Level& L = h->levels[l];
-  auto& boxes = L.boxes;
+int compress_height(symhss_s* h, int t, cudaStream_t s) {
+  Height& H = h->heights[t];
+  std::vector<BoxRef> refs;
+  height_boxes(h, t, false, refs);
+  const int nb = (int)refs.size();
+  if (nb == 0) return SYMHSS_OK;
   const bool sym = h->prm.mode == SYMHSS_SYM;
-  const int nb = (int)boxes.size();
   // active sets
-  for (int b = 0; b < nb; ++b) {
-    HBox& bx = boxes[b];
-    if (l == h->depth) {
+  for (const BoxRef& rf : refs) {
+    HBox& bx = *rf.bx;
+    if (t == 0) {
       std::vector<int> ids(bx.end - bx.begin);
       for (int i = 0; i < (int)ids.size(); ++i) ids[i] = bx.begin + i;
       for (int p = 0; p < 2; ++p) { bx.act[p] = ids; bx.actrow[p] = ids; }
     } else {
-      const HBox& c1 = h->levels[l + 1].boxes[bx.child[0]];
-      const HBox& c2 = h->levels[l + 1].boxes[bx.child[1]];
+      const auto& kids = h->probs[rf.p].levels[rf.l + 1];
+      const HBox& c1 = kids[bx.child[0]];
+      const HBox& c2 = kids[bx.child[1]];
       for (int p = 0; p < 2; ++p) {
         bx.act[p].assign(c1.perm[p].begin(), c1.perm[p].begin() + c1.rank[p]);
         for (int& v : bx.act[p]) v = c1.act[p][v];
@@ -464,22 +534,24 @@ int compress_level(symhss_s* h, int l, cudaStream_t s) {
   std::vector<IdJob> jobs;
   long long mr_total = 0, t_total = 0, perm_total = 0;
   int max_m = 1, max_n = 1;
-  const int fixed = fixed_rank(h, l);
-  std::vector<int> nr0, nr1, prx0, prx1;
+  const int fixed = fixed_rank(h, t);
+  std::vector<int> nr0, nr1, prx0;
   const int flags = sym ? 0 : TILE_UNSCALED;
   // M_R of every box (and M_L^T for the baseline)
-  for (int b = 0; b < nb; ++b) {
-    HBox& bx = boxes[b];
-    near_points(h, boxes, b, true, 0, nr0);
-    near_points(h, boxes, b, true, 1, nr1);
+  for (int i = 0; i < nb; ++i) {
+    const BoxRef& rf = refs[i];
+    HBox& bx = *rf.bx;
+    const auto& lev = h->probs[rf.p].levels[rf.l];
+    near_points(h, lev, rf.b, true, 0, nr0);
+    near_points(h, lev, rf.b, true, 1, nr1);
     prx0.resize(bx.P);
     for (int m = 0; m < bx.P; ++m) prx0[m] = bx.proxy0 + m;
     const int m0 = (int)nr0.size(), m1 = (int)nr1.size(), P = bx.P;
     const int m = m0 + m1 + 2 * P;
     const int n0 = (int)bx.act[0].size(), n1 = (int)bx.act[1].size();
     // rows: near eq1 (slots 0..m0), near eq2 (m0..), proxy eq1 and eq2 (same points)
-    tb.add(h->mark, nr0, 0, nr1, m0, bx.act[0], 0, bx.act[1], n0, mr_total, m, flags);
-    tb.add(h->mark, prx0, m0 + m1, prx0, m0 + m1 + P, bx.act[0], 0, bx.act[1], n0, mr_total, m, flags);
+    tb.add(h->mark, nr0, 0, nr1, m0, bx.act[0], 0, bx.act[1], n0, mr_total, m, flags, rf.p);
+    tb.add(h->mark, prx0, m0 + m1, prx0, m0 + m1 + P, bx.act[0], 0, bx.act[1], n0, mr_total, m, flags, rf.p);
     for (int p = 0; p < 2; ++p) {
       IdJob j;
       j.m_off = mr_total + (p == 0 ? 0 : (long long)n0 * m);
@@ -487,7 +559,7 @@ int compress_level(symhss_s* h, int l, cudaStream_t s) {
       j.start = 0; j.fixed = fixed;
       j.t_off = t_total; t_total += tcap(j.n);
       j.perm_off = perm_total; perm_total += j.n;
-      j.out_idx = 2 * b + p;
+      j.out_idx = 2 * i + p;
       jobs.push_back(j);
       bx.t_off[p] = j.t_off;
       max_n = std::max(max_n, j.n);
@@ -496,10 +568,12 @@ int compress_level(symhss_s* h, int l, cudaStream_t s) {
     mr_total += (long long)m * (n0 + n1);
   }
   if (!sym) {
-    for (int b = 0; b < nb; ++b) {
-      HBox& bx = boxes[b];
-      near_points(h, boxes, b, false, 0, nr0);
-      near_points(h, boxes, b, false, 1, nr1);
+    for (int i = 0; i < nb; ++i) {
+      const BoxRef& rf = refs[i];
+      HBox& bx = *rf.bx;
+      const auto& lev = h->probs[rf.p].levels[rf.l];
+      near_points(h, lev, rf.b, false, 0, nr0);
+      near_points(h, lev, rf.b, false, 1, nr1);
       prx0.resize(bx.P);
       for (int m = 0; m < bx.P; ++m) prx0[m] = bx.proxy0 + m;
       const int c0 = (int)nr0.size(), c1n = (int)nr1.size(), P = bx.P;
@@ -507,9 +581,9 @@ int compress_level(symhss_s* h, int l, cudaStream_t s) {
       const int r0 = (int)bx.actrow[0].size(), r1 = (int)bx.actrow[1].size();
       // thread points = M_L columns (sources), loop points = M_L rows (observations)
       tb.add(h->mark, nr0, 0, nr1, c0, bx.actrow[0], 0, bx.actrow[1], r0, mr_total, mt,
-             flags | TILE_SRC_IS_THREAD);
+             flags | TILE_SRC_IS_THREAD, rf.p);
       tb.add(h->mark, prx0, c0 + c1n, prx0, c0 + c1n + P, bx.actrow[0], 0, bx.actrow[1], r0, mr_total, mt,
-             flags | TILE_SRC_IS_THREAD);
+             flags | TILE_SRC_IS_THREAD, rf.p);
       for (int p = 0; p < 2; ++p) {
         IdJob j;
         j.m_off = mr_total + (p == 0 ? 0 : (long long)r0 * mt);
@@ -517,7 +591,7 @@ int compress_level(symhss_s* h, int l, cudaStream_t s) {
         j.start = 0; j.fixed = fixed;
         j.t_off = t_total; t_total += tcap(j.n);
         j.perm_off = perm_total; perm_total += j.n;
-        j.out_idx = 2 * nb + 2 * b + p;
+        j.out_idx = 2 * nb + 2 * i + p;
         jobs.push_back(j);
         bx.rt_off[p] = j.t_off;
         max_n = std::max(max_n, j.n);
@@ -530,7 +604,8 @@ int compress_level(symhss_s* h, int l, cudaStream_t s) {
   // Randomized sketch (Halko-Martinsson-Tropp): an ID job whose rank estimate plus
   // oversampling is well below its row count is taken of Y = Omega M instead of M.
   // Y blocks live after all proxy matrices in the same buffer.  Rank estimate: half
-  // the smaller dimension at the leaves, 1.7x the previous level's largest rank above.
+  // the smaller dimension at the leaves, 1.7x the problem's largest rank one level
+  // down above.
   const int p_over = h->prm.oversample;
   const std::vector<IdJob> full = jobs;  // the same IDs on the full proxy matrices
   std::vector<int> sk_rows(njobs, 0);
@@ -544,10 +619,11 @@ int compress_level(symhss_s* h, int l, cudaStream_t s) {
       IdJob& j = jobs[i];
       if (j.n == 0) continue;
       const int part = j.out_idx & 1;
+      const BoxRef& rf = refs[(j.out_idx % (2 * nb)) / 2];
       int est;
       if (fixed >= 0) est = fixed;
-      else if (l == h->depth) est = (std::min(j.m, j.n) + 1) / 2;
-      else est = (int)std::ceil(1.7 * std::max(8, h->lvl_max_rank[l + 1][part]));
+      else if (t == 0) est = (std::min(j.m, j.n) + 1) / 2;
+      else est = (int)std::ceil(1.7 * std::max(8, h->probs[rf.p].lvl_max_rank[rf.l + 1][part]));
       const int sr = std::max(32, ((est + p_over + 15) / 16) * 16);
       if (sr > 1024 || 5 * sr >= 4 * j.m) continue;
       SketchJob sj;
@@ -555,7 +631,7 @@ int compress_level(symhss_s* h, int l, cudaStream_t s) {
       sj.mpad = sketch_mpad(j.m); sj.n2pad = sketch_n2pad(j.n); sj.s = sr;
       sj.y_off = mr_total + y_total; sj.ldy = sr;
       sj.slice_off = slice_total; sj.exp_off = exp_total;
-      sj.stream_id = ((long long)l << 32) + i;
+      sj.stream_id = ((long long)t << 32) + i;
       const int sji = (int)sk.size();
       for (int c = 0; c < j.n; ++c) skcw.push_back(SketchColWork{sji, c});
       const int mtiles = (sr + 127) / 128;
@@ -572,24 +648,24 @@ int compress_level(symhss_s* h, int l, cudaStream_t s) {
   }
   max_m = 1;
   for (const IdJob& j : jobs) max_m = std::max(max_m, j.m);
-  CK(L.mr.ensure((mr_total + y_total) * sizeof(double2)));
-  CK(L.tbuf.ensure(t_total * sizeof(double2)));
-  CK(L.permbuf.ensure(perm_total * sizeof(int)));
-  CK(L.rankbuf.ensure(njobs * sizeof(int)));
-  CK(L.refbuf.ensure(njobs * sizeof(double)));
-  TIMED(SYMHSS_K_TILES, (double)tb.pairs, tb.launch(h, L.clists, L.mr.as<double2>(), s));
+  CK(H.mr.ensure((mr_total + y_total) * sizeof(double2)));
+  CK(H.tbuf.ensure(t_total * sizeof(double2)));
+  CK(H.permbuf.ensure(perm_total * sizeof(int)));
+  CK(H.rankbuf.ensure(njobs * sizeof(int)));
+  CK(H.refbuf.ensure(njobs * sizeof(double)));
+  TIMED(SYMHSS_K_TILES, (double)tb.pairs, tb.launch(h, H.clists, H.mr.as<double2>(), s));
   if (!sk.empty()) {
-    CK(L.slices.ensure((size_t)slice_total));
+    CK(H.slices.ensure((size_t)slice_total));
     Packer sp;
     const size_t oj = sp.add(sk), oc = sp.add(skcw), ot = sp.add(sktiles);
     const size_t oe = sp.add(nullptr, (size_t)exp_total * sizeof(int));
-    CK(sp.upload(L.skmeta, s));
-    char* sb = L.skmeta.as<char>();
+    CK(sp.upload(H.skmeta, s));
+    char* sb = H.skmeta.as<char>();
     SketchLaunch sa;
-    sa.mats = L.mr.as<double2>();
-    sa.slices = L.slices.as<uint8_t>();
+    sa.mats = H.mr.as<double2>();
+    sa.slices = H.slices.as<uint8_t>();
     sa.exps = reinterpret_cast<int*>(sb + oe);
-    sa.y = L.mr.as<double2>();
+    sa.y = H.mr.as<double2>();
     sa.jobs = reinterpret_cast<const SketchJob*>(sb + oj);
     sa.colwork = reinterpret_cast<const SketchColWork*>(sb + oc);
     sa.ncolwork = (int)skcw.size();
@@ -605,30 +681,30 @@ int compress_level(symhss_s* h, int l, cudaStream_t s) {
   for (int i = 0; i < njobs; ++i) (sk_rows[i] > 0 ? sketch_jobs : plain_jobs).push_back(jobs[i]);
   Packer pk;
   const size_t o_plain = pk.add(plain_jobs), o_sketch = pk.add(sketch_jobs);
-  CK(pk.upload(L.idjobs, s));
+  CK(pk.upload(H.idjobs, s));
   IdLaunch ia;
-  ia.mats = L.mr.as<double2>();
-  ia.tbuf = L.tbuf.as<double2>();
-  ia.perm = L.permbuf.as<int>();
-  ia.rank = L.rankbuf.as<int>();
-  ia.ref = L.refbuf.as<double>();
+  ia.mats = H.mr.as<double2>();
+  ia.tbuf = H.tbuf.as<double2>();
+  ia.perm = H.permbuf.as<int>();
+  ia.rank = H.rankbuf.as<int>();
+  ia.ref = H.refbuf.as<double>();
   ia.tol = h->prm.tol;
   ia.status = h->status.as<int>();
   ia.max_m = max_m;
   ia.max_n = max_n;
   const size_t id_before = h->marks.size();
-  ia.jobs = reinterpret_cast<const IdJob*>(L.idjobs.as<char>() + o_plain);
+  ia.jobs = reinterpret_cast<const IdJob*>(H.idjobs.as<char>() + o_plain);
   ia.njobs = (int)plain_jobs.size();
   TIMED(SYMHSS_K_ID, 0.0, launch_cpqr(ia, s));
-  ia.jobs = reinterpret_cast<const IdJob*>(L.idjobs.as<char>() + o_sketch);
+  ia.jobs = reinterpret_cast<const IdJob*>(H.idjobs.as<char>() + o_sketch);
   ia.njobs = (int)sketch_jobs.size();
   ia.tol = 0.25 * h->prm.tol;
   TIMED(SYMHSS_K_ID, 0.0, launch_cpqr(ia, s));
   ia.tol = h->prm.tol;
   const size_t id_mark = h->marks.size() > id_before ? id_before : (size_t)-1;
   std::vector<int> hr(njobs), hp(perm_total);
-  CK(cudaMemcpyAsync(hr.data(), L.rankbuf.p, njobs * sizeof(int), cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(hp.data(), L.permbuf.p, perm_total * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(hr.data(), H.rankbuf.p, njobs * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(hp.data(), H.permbuf.p, perm_total * sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (id_mark < h->marks.size()) {
     double w = 0;
@@ -650,14 +726,14 @@ int compress_level(symhss_s* h, int l, cudaStream_t s) {
       for (const IdJob& j : redo) mm = std::max(mm, j.m);
       Packer pr;
       pr.add(redo);
-      CK(pr.upload(L.idjobs, s));
-      ia.jobs = L.idjobs.as<IdJob>();
+      CK(pr.upload(H.idjobs, s));
+      ia.jobs = H.idjobs.as<IdJob>();
       ia.njobs = (int)redo.size();
       ia.max_m = mm;
       const size_t rb = h->marks.size();
       TIMED(SYMHSS_K_ID, 0.0, launch_cpqr(ia, s));
-      CK(cudaMemcpyAsync(hr.data(), L.rankbuf.p, njobs * sizeof(int), cudaMemcpyDeviceToHost, s));
-      CK(cudaMemcpyAsync(hp.data(), L.permbuf.p, perm_total * sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(hr.data(), H.rankbuf.p, njobs * sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(hp.data(), H.permbuf.p, perm_total * sizeof(int), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
       if (h->marks.size() > rb) {
         double w = 0;
@@ -691,8 +767,8 @@ int compress_level(symhss_s* h, int l, cudaStream_t s) {
     if (!more.empty()) {
       Packer pk2;
       pk2.add(more);
-      CK(pk2.upload(L.idjobs, s));
-      ia.jobs = L.idjobs.as<IdJob>();
+      CK(pk2.upload(H.idjobs, s));
+      ia.jobs = H.idjobs.as<IdJob>();
       ia.njobs = (int)more.size();
       {
         int mm = 1;
@@ -702,8 +778,8 @@ int compress_level(symhss_s* h, int l, cudaStream_t s) {
       const size_t more_before = h->marks.size();
       TIMED(SYMHSS_K_ID, 0.0, launch_cpqr(ia, s));
       const size_t more_mark = h->marks.size() > more_before ? more_before : (size_t)-1;
-      CK(cudaMemcpyAsync(hr.data(), L.rankbuf.p, njobs * sizeof(int), cudaMemcpyDeviceToHost, s));
-      CK(cudaMemcpyAsync(hp.data(), L.permbuf.p, perm_total * sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(hr.data(), H.rankbuf.p, njobs * sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(hp.data(), H.permbuf.p, perm_total * sizeof(int), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
       if (more_mark < h->marks.size()) {
         double w = 0;
@@ -718,37 +794,40 @@ int compress_level(symhss_s* h, int l, cudaStream_t s) {
     h->st.flops_id += 16.0 * (double)j.m * j.n * r;
   }
   h->st.id_count += njobs;
-  for (int b = 0; b < nb; ++b) {
-    HBox& bx = boxes[b];
+  for (int i = 0; i < nb; ++i) {
+    HBox& bx = *refs[i].bx;
     for (int p = 0; p < 2; ++p) {
-      const IdJob& j = jobs[2 * b + p];
-      bx.rank[p] = hr[2 * b + p];
+      const IdJob& j = jobs[2 * i + p];
+      bx.rank[p] = hr[2 * i + p];
       bx.perm[p].assign(hp.begin() + j.perm_off, hp.begin() + j.perm_off + j.n);
       if (sym) {
         bx.rrank[p] = bx.rank[p];
         bx.rperm[p] = bx.perm[p];
         bx.rt_off[p] = bx.t_off[p];
       } else {
-        const IdJob& jr = jobs[2 * nb + 2 * b + p];
+        const IdJob& jr = jobs[2 * nb + 2 * i + p];
         bx.rrank[p] = hr[jr.out_idx];
         bx.rperm[p].assign(hp.begin() + jr.perm_off, hp.begin() + jr.perm_off + jr.n);
         if (bx.rrank[p] != bx.rank[p]) return SYMHSS_ERR_DEVICE;
       }
     }
   }
-  L.h_rank = hr;
-  for (int p = 0; p < 2; ++p) {
-    int mx = 0;
-    for (const auto& bx : boxes) mx = std::max(mx, bx.rank[p]);
-    h->lvl_max_rank[l][p] = mx;
-  }
+  H.h_rank = hr;
+  for (Problem& P : h->probs)
+    if (P.depth > t) P.lvl_max_rank[P.depth - t][0] = P.lvl_max_rank[P.depth - t][1] = 0;
+  for (const BoxRef& rf : refs)
+    for (int p = 0; p < 2; ++p) {
+      int& mx = h->probs[rf.p].lvl_max_rank[rf.l][p];
+      mx = std::max(mx, rf.bx->rank[p]);
+    }
   return SYMHSS_OK;
 }
 
 // Positions of each active unknown (part p, active order) in the box's diagonal-block
 // ordering: leaf [flux; trace]; parent [child 1 (flux; trace), child 2 (flux; trace)].
-void positions(const symhss_s* h, int l, const HBox& bx, bool rows, std::vector<int> pos[2]) {
-  if (l == h->depth) {
+void positions(const symhss_s* h, int t, const BoxRef& rf, bool rows, std::vector<int> pos[2]) {
+  const HBox& bx = *rf.bx;
+  if (t == 0) {
     const int nb = bx.end - bx.begin;
     for (int p = 0; p < 2; ++p) {
       pos[p].resize(nb);
@@ -756,8 +835,9 @@ void positions(const symhss_s* h, int l, const HBox& bx, bool rows, std::vector<
     }
     return;
   }
-  const HBox& c1 = h->levels[l + 1].boxes[bx.child[0]];
-  const HBox& c2 = h->levels[l + 1].boxes[bx.child[1]];
+  const auto& kids = h->probs[rf.p].levels[rf.l + 1];
+  const HBox& c1 = kids[bx.child[0]];
+  const HBox& c2 = kids[bx.child[1]];
   const int* r1 = rows ? c1.rrank : c1.rank;
   const int* r2 = rows ? c2.rrank : c2.rank;
   const int a1 = r1[0] + r1[1];
@@ -779,21 +859,25 @@ void skeleton(const HBox& bx, bool rows, int p, std::vector<int>& out) {
   for (int j = 0; j < r; ++j) out.push_back(a[pm[j]]);
 }
 
-// Assemble the diagonal blocks D of level l (leaf tiles, or children's Atilde plus
-// skeleton coupling tiles) into L.D and factorise them.
-int assemble_and_lu(symhss_s* h, int l, cudaStream_t s, long long& pairs) {
-  Level& L = h->levels[l];
-  auto& boxes = L.boxes;
+// Assemble the diagonal blocks D of every box at height t (leaf tiles, or children's
+// Atilde plus skeleton coupling tiles) into H.D and factorise them (roots included).
+int assemble_and_lu(symhss_s* h, int t, cudaStream_t s, long long& pairs) {
+  Height& H = h->heights[t];
+  std::vector<BoxRef> refs;
+  height_boxes(h, t, true, refs);
+  if (refs.empty()) return SYMHSS_OK;
   const bool sym = h->prm.mode == SYMHSS_SYM;
   const int flags = sym ? 0 : TILE_UNSCALED;
-  const bool leaf = (l == h->depth);
+  const bool leaf = (t == 0);
   long long d_total = 0, piv_total = 0;
   int max_n = 1;
-  for (auto& bx : boxes) {
+  for (const BoxRef& rf : refs) {
+    HBox& bx = *rf.bx;
     if (leaf) bx.size = 2 * (bx.end - bx.begin);
     else {
-      const HBox& c1 = h->levels[l + 1].boxes[bx.child[0]];
-      const HBox& c2 = h->levels[l + 1].boxes[bx.child[1]];
+      const auto& kids = h->probs[rf.p].levels[rf.l + 1];
+      const HBox& c1 = kids[bx.child[0]];
+      const HBox& c2 = kids[bx.child[1]];
       bx.size = c1.rank[0] + c1.rank[1] + c2.rank[0] + c2.rank[1];
     }
     bx.d_off = d_total;
@@ -802,30 +886,31 @@ int assemble_and_lu(symhss_s* h, int l, cudaStream_t s, long long& pairs) {
     piv_total += bx.size;
     max_n = std::max(max_n, bx.size);
   }
-  CK(L.D.ensure(d_total * sizeof(double2)));
-  CK(L.piv.ensure(piv_total * sizeof(int)));
-  CK(L.info.ensure(boxes.size() * sizeof(int)));
+  CK(H.D.ensure(d_total * sizeof(double2)));
+  CK(H.piv.ensure(piv_total * sizeof(int)));
+  CK(H.info.ensure(refs.size() * sizeof(int)));
   TileBuilder tb;
   std::vector<CopyJob> copies;
   std::vector<int> t0, t1, u0, u1;
-  for (auto& bx : boxes) {
+  for (const BoxRef& rf : refs) {
+    HBox& bx = *rf.bx;
     if (leaf) {
       std::vector<int> ids(bx.end - bx.begin);
       for (int i = 0; i < (int)ids.size(); ++i) ids[i] = bx.begin + i;
       const int nb = (int)ids.size();
-      tb.add(h->mark, ids, 0, ids, nb, ids, 0, ids, nb, bx.d_off, bx.size, flags);
+      tb.add(h->mark, ids, 0, ids, nb, ids, 0, ids, nb, bx.d_off, bx.size, flags, rf.p);
     } else {
-      const HBox& c1 = h->levels[l + 1].boxes[bx.child[0]];
-      const HBox& c2 = h->levels[l + 1].boxes[bx.child[1]];
+      const auto& kids = h->probs[rf.p].levels[rf.l + 1];
+      const HBox& c1 = kids[bx.child[0]];
+      const HBox& c2 = kids[bx.child[1]];
       const int a1 = c1.rank[0] + c1.rank[1];
       // rows of child 1 against columns of child 2, and the transpose position
       skeleton(c1, true, 0, t0); skeleton(c1, true, 1, t1);
       skeleton(c2, false, 0, u0); skeleton(c2, false, 1, u1);
-      tb.add(h->mark, t0, 0, t1, c1.rrank[0], u0, a1, u1, a1 + c2.rank[0], bx.d_off, bx.size, flags);
+      tb.add(h->mark, t0, 0, t1, c1.rrank[0], u0, a1, u1, a1 + c2.rank[0], bx.d_off, bx.size, flags, rf.p);
       skeleton(c2, true, 0, t0); skeleton(c2, true, 1, t1);
       skeleton(c1, false, 0, u0); skeleton(c1, false, 1, u1);
-      tb.add(h->mark, t0, a1, t1, a1 + c2.rrank[0], u0, 0, u1, c1.rank[0], bx.d_off, bx.size, flags);
-      const Level& LC = h->levels[l + 1];
+      tb.add(h->mark, t0, a1, t1, a1 + c2.rrank[0], u0, 0, u1, c1.rank[0], bx.d_off, bx.size, flags, rf.p);
       CopyJob cj;
       cj.src_off = c1.rx_off; cj.dst_off = bx.d_off; cj.rows = a1; cj.cols = a1; cj.lds = a1; cj.ldd = bx.size;
       copies.push_back(cj);
@@ -833,38 +918,37 @@ int assemble_and_lu(symhss_s* h, int l, cudaStream_t s, long long& pairs) {
       cj.src_off = c2.rx_off; cj.dst_off = bx.d_off + a1 + (long long)a1 * bx.size;
       cj.rows = a2; cj.cols = a2; cj.lds = a2;
       copies.push_back(cj);
-      (void)LC;
     }
   }
-  TIMED(SYMHSS_K_TILES, (double)tb.pairs, tb.launch(h, L.flists, L.D.as<double2>(), s));
+  TIMED(SYMHSS_K_TILES, (double)tb.pairs, tb.launch(h, H.flists, H.D.as<double2>(), s));
   pairs += tb.pairs;
   if (!copies.empty()) {
     Packer pk;
     pk.add(copies);
-    // child Atilde live in the child level's At buffer
-    DevBuf& tmp = L.cjobs;
-    CK(pk.upload(tmp, s));
-    TIMED(SYMHSS_K_OTHER, 0.0, launch_copy_blocks(h->levels[l + 1].At.as<double2>(), L.D.as<double2>(),
-                                                  tmp.as<CopyJob>(), (int)copies.size(), s));
+    CK(pk.upload(H.cjobs, s));
+    // the children's Atilde live in the At buffer one height down
+    TIMED(SYMHSS_K_OTHER, 0.0, launch_copy_blocks(h->heights[t - 1].At.as<double2>(), H.D.as<double2>(),
+                                                  H.cjobs.as<CopyJob>(), (int)copies.size(), s));
   }
   std::vector<LuJob> lj;
   double lu_work = 0;
-  for (size_t b = 0; b < boxes.size(); ++b) {
+  for (size_t b = 0; b < refs.size(); ++b) {
+    const HBox& bx = *refs[b].bx;
     LuJob j;
-    j.a_off = boxes[b].d_off; j.n = boxes[b].size; j.ld = boxes[b].size; j.piv_off = boxes[b].piv_off;
+    j.a_off = bx.d_off; j.n = bx.size; j.ld = bx.size; j.piv_off = bx.piv_off;
     j.info_idx = (int)b;
     lj.push_back(j);
-    h->st.flops_lu += 8.0 / 3.0 * std::pow((double)boxes[b].size, 3);
-    lu_work += 8.0 / 3.0 * std::pow((double)boxes[b].size, 3);
+    h->st.flops_lu += 8.0 / 3.0 * std::pow((double)bx.size, 3);
+    lu_work += 8.0 / 3.0 * std::pow((double)bx.size, 3);
   }
   Packer pk;
   pk.add(lj);
-  CK(pk.upload(L.lujobs, s));
+  CK(pk.upload(H.lujobs, s));
   LuLaunch la;
-  la.base = L.D.as<double2>();
-  la.piv = L.piv.as<int>();
-  la.info = L.info.as<int>();
-  la.jobs = L.lujobs.as<LuJob>();
+  la.base = H.D.as<double2>();
+  la.piv = H.piv.as<int>();
+  la.info = H.info.as<int>();
+  la.jobs = H.lujobs.as<LuJob>();
   la.njobs = (int)lj.size();
   la.max_n = max_n;
   la.status = h->status.as<int>();
@@ -872,19 +956,22 @@ int assemble_and_lu(symhss_s* h, int l, cudaStream_t s, long long& pairs) {
   return SYMHSS_OK;
 }
 
-int factor_level(symhss_s* h, int l, cudaStream_t s, long long& pairs) {
-  Level& L = h->levels[l];
-  auto& boxes = L.boxes;
-  int rc = assemble_and_lu(h, l, s, pairs);
+int factor_height(symhss_s* h, int t, cudaStream_t s, long long& pairs) {
+  Height& H = h->heights[t];
+  int rc = assemble_and_lu(h, t, s, pairs);
   if (rc) return rc;
+  std::vector<BoxRef> refs;
+  height_boxes(h, t, false, refs);
+  if (refs.empty()) return SYMHSS_OK;
   // bases: L (row ID) for X = D^{-1} L; R (column ID) for R X
   std::vector<int> qhost;
   long long x_total = 0, rx_total = 0, rxpiv_total = 0;
   int max_n = 1, max_k = 1;
   std::vector<int> pos[2], rpos[2];
-  for (auto& bx : boxes) {
-    positions(h, l, bx, false, pos);
-    positions(h, l, bx, true, rpos);
+  for (const BoxRef& rf : refs) {
+    HBox& bx = *rf.bx;
+    positions(h, t, rf, false, pos);
+    positions(h, t, rf, true, rpos);
     for (int p = 0; p < 2; ++p) {
       bx.q_off[p] = (long long)qhost.size();
       for (int c = 0; c < (int)bx.perm[p].size(); ++c) qhost.push_back(pos[p][bx.perm[p][c]]);
@@ -906,8 +993,8 @@ int factor_level(symhss_s* h, int l, cudaStream_t s, long long& pairs) {
   std::vector<RsJob> xs, ats;
   std::vector<LuJob> rxl;
   std::vector<CopyJob> eye;
-  for (size_t b = 0; b < boxes.size(); ++b) {
-    HBox& bx = boxes[b];
+  for (size_t b = 0; b < refs.size(); ++b) {
+    HBox& bx = *refs[b].bx;
     BasisJob jl{}, jr{};
     for (int p = 0; p < 2; ++p) {
       jl.part[p].q_off = bx.rq_off[p]; jl.part[p].t_off = bx.rt_off[p];
@@ -943,32 +1030,33 @@ int factor_level(symhss_s* h, int l, cudaStream_t s, long long& pairs) {
   Packer pk;
   const size_t oq = pk.add(qhost), ol = pk.add(lbj), orr = pk.add(rbj), ox = pk.add(xs), orl = pk.add(rxl),
                oa = pk.add(ats), oe = pk.add(eye);
-  CK(pk.upload(L.qbuf, s));
-  char* qb = L.qbuf.as<char>();
-  CK(L.X.ensure(x_total * sizeof(double2)));
-  CK(L.RX.ensure(rx_total * sizeof(double2)));
-  CK(L.At.ensure(rx_total * sizeof(double2)));
+  CK(pk.upload(H.qbuf, s));
+  char* qb = H.qbuf.as<char>();
+  CK(H.X.ensure(x_total * sizeof(double2)));
+  CK(H.RX.ensure(rx_total * sizeof(double2)));
+  CK(H.At.ensure(rx_total * sizeof(double2)));
   // X = D^{-1} L
   BasisLaunch bl;
   bl.q = reinterpret_cast<const int*>(qb + oq);
-  bl.T = h->levels[l].tbuf.as<double2>();
+  bl.T = H.tbuf.as<double2>();
   bl.in = nullptr;
-  bl.out = L.X.as<double2>();
+  bl.out = H.X.as<double2>();
   bl.jobs = reinterpret_cast<const BasisJob*>(qb + ol);
   bl.njobs = (int)lbj.size();
   bl.max_cols = max_k;
   TIMED(SYMHSS_K_OTHER, 0.0, launch_basis_dense(bl, s));
   double w_x = 0, w_rx = 0, w_rxlu = 0, w_at = 0;
-  for (const auto& bx : boxes) {
+  for (const BoxRef& rf : refs) {
+    const HBox& bx = *rf.bx;
     w_x += 8.0 * (double)bx.size * bx.size * bx.k;
     w_rx += 8.0 * (double)bx.k * bx.k * (double)(bx.perm[0].size() + bx.perm[1].size());
     w_rxlu += 8.0 / 3.0 * std::pow((double)bx.k, 3);
     w_at += 8.0 * std::pow((double)bx.k, 3);
   }
   RsLaunch ra;
-  ra.abase = L.D.as<double2>();
-  ra.piv = L.piv.as<int>();
-  ra.bbase = L.X.as<double2>();
+  ra.abase = H.D.as<double2>();
+  ra.piv = H.piv.as<int>();
+  ra.bbase = H.X.as<double2>();
   ra.jobs = reinterpret_cast<const RsJob*>(qb + ox);
   ra.njobs = (int)xs.size();
   ra.max_rhs = max_k;
@@ -976,33 +1064,117 @@ int factor_level(symhss_s* h, int l, cudaStream_t s, long long& pairs) {
   TIMED(SYMHSS_K_GETRS, w_x, launch_getrs(ra, s));
   // R X
   BasisLaunch br = bl;
-  br.in = L.X.as<double2>();
-  br.out = L.RX.as<double2>();
+  br.in = H.X.as<double2>();
+  br.out = H.RX.as<double2>();
   br.jobs = reinterpret_cast<const BasisJob*>(qb + orr);
   TIMED(SYMHSS_K_OTHER, w_rx, launch_apply_r(br, s));
   // Atilde = (R X)^{-1}
-  CK(L.rxpiv.ensure(rxpiv_total * sizeof(int)));
+  CK(H.rxpiv.ensure(rxpiv_total * sizeof(int)));
   LuLaunch la;
-  la.base = L.RX.as<double2>();
-  la.piv = L.rxpiv.as<int>();
-  la.info = L.info.as<int>();
+  la.base = H.RX.as<double2>();
+  la.piv = H.rxpiv.as<int>();
+  la.info = H.info.as<int>();
   la.jobs = reinterpret_cast<const LuJob*>(qb + orl);
   la.njobs = (int)rxl.size();
   la.max_n = max_k;
   la.status = h->status.as<int>();
   TIMED(SYMHSS_K_GETRF, w_rxlu, launch_getrf(la, s));
-  TIMED(SYMHSS_K_OTHER, 0.0, launch_copy_blocks(nullptr, L.At.as<double2>(),
+  TIMED(SYMHSS_K_OTHER, 0.0, launch_copy_blocks(nullptr, H.At.as<double2>(),
                                                 reinterpret_cast<const CopyJob*>(qb + oe), (int)eye.size(), s));
   RsLaunch rb;
-  rb.abase = L.RX.as<double2>();
-  rb.piv = L.rxpiv.as<int>();
-  rb.bbase = L.At.as<double2>();
+  rb.abase = H.RX.as<double2>();
+  rb.piv = H.rxpiv.as<int>();
+  rb.bbase = H.At.as<double2>();
   rb.jobs = reinterpret_cast<const RsJob*>(qb + oa);
   rb.njobs = (int)ats.size();
   rb.max_rhs = max_k;
   rb.max_n = max_k;
   TIMED(SYMHSS_K_GETRS, w_at, launch_getrs(rb, s));
   return SYMHSS_OK;
+}
+
+// leaf gather / scatter jobs of every leaf of every problem
+void leaf_jobs(symhss_s* h, std::vector<LeafJob>& out) {
+  out.clear();
+  std::vector<BoxRef> refs;
+  height_boxes(h, 0, true, refs);
+  for (const BoxRef& rf : refs) {
+    const Problem& P = h->probs[rf.p];
+    const HBox& bx = *rf.bx;
+    out.push_back(LeafJob{bx.g_off, P.vec0, bx.begin - P.node0, bx.end - bx.begin, P.n, 0});
+  }
+}
+
+int validate_params(const symhss_params* p) {
+  if (!p) return SYMHSS_ERR_INVALID;
+  if (!(p->k0 > 0) || !(p->k1 > 0) || !(p->eps0 > 0) || !(p->eps1 > 0)) return SYMHSS_ERR_INVALID;
+  if (!std::isfinite(p->k0) || !std::isfinite(p->k1) || !std::isfinite(p->eps0) || !std::isfinite(p->eps1))
+    return SYMHSS_ERR_INVALID;
+  if (!(p->tol >= 0) || !std::isfinite(p->tol)) return SYMHSS_ERR_INVALID;
+  if (p->leaf < 1 || p->nproxy < 8 || !(p->proxy_factor > 1.0) || !std::isfinite(p->proxy_factor))
+    return SYMHSS_ERR_INVALID;
+  if (p->mode != SYMHSS_SYM && p->mode != SYMHSS_NONSYM) return SYMHSS_ERR_INVALID;
+  if (p->precision != SYMHSS_FP64) return SYMHSS_ERR_INVALID;
+  if (p->fixed_rank_kL < 0 || (p->fixed_rank_kL > 0 && !(p->rank_scale_a >= 1.0))) return SYMHSS_ERR_INVALID;
+  if (p->oversample < 0) return SYMHSS_ERR_INVALID;
+  return SYMHSS_OK;
+}
+
+// the fields every problem of a batch must share
+bool same_shared(const symhss_params& a, const symhss_params& b) {
+  return a.tol == b.tol && a.leaf == b.leaf && a.nproxy == b.nproxy && a.proxy_factor == b.proxy_factor &&
+         a.mode == b.mode && a.precision == b.precision && a.fixed_rank_kL == b.fixed_rank_kL &&
+         a.rank_scale_a == b.rank_scale_a && a.oversample == b.oversample && a.seed == b.seed;
+}
+
+// Copy the curves (host or device arrays) into the concatenated host node arrays.
+int load_curves(symhss_s* h, const symhss_curve* cs, int count, cudaStream_t s) {
+  long long total = 0;
+  for (int c = 0; c < count; ++c) {
+    const symhss_curve* cv = &cs[c];
+    if (cv->n < 2) return SYMHSS_ERR_INVALID;
+    if (!cv->x || !cv->y || !cv->nx || !cv->ny || !cv->w || !cv->kappa) return SYMHSS_ERR_INVALID;
+    if (cv->location != SYMHSS_HOST && cv->location != SYMHSS_DEVICE) return SYMHSS_ERR_INVALID;
+    total += cv->n;
+  }
+  if (total > (1LL << 30)) return SYMHSS_ERR_INVALID;
+  std::vector<double>* dst[6] = {&h->hx, &h->hy, &h->hnx, &h->hny, &h->hw, &h->hk};
+  for (int i = 0; i < 6; ++i) dst[i]->resize((size_t)total);
+  bool any_device = false;
+  long long off = 0;
+  for (int c = 0; c < count; ++c) {
+    const symhss_curve* cv = &cs[c];
+    const double* src[6] = {cv->x, cv->y, cv->nx, cv->ny, cv->w, cv->kappa};
+    for (int i = 0; i < 6; ++i) {
+      double* d = dst[i]->data() + off;
+      if (cv->location == SYMHSS_HOST) {
+        std::memcpy(d, src[i], cv->n * sizeof(double));
+      } else {
+        any_device = true;
+        cudaError_t e = cudaMemcpyAsync(d, src[i], cv->n * sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cuda_fail(h, e);
+      }
+    }
+    off += cv->n;
+  }
+  if (any_device) {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+  }
+  for (int i = 0; i < 6; ++i)
+    if (!finite_all(*dst[i])) return SYMHSS_ERR_INVALID;
+  for (long long i = 0; i < total; ++i)
+    if (!(h->hw[i] > 0)) return SYMHSS_ERR_INVALID;
+  for (int c = 0; c < count; ++c) h->probs[c].n = cs[c].n;
+  return SYMHSS_OK;
+}
+
+void geometry_stats(symhss_s* h) {
+  h->st.n = h->ntot;
+  h->st.depth = h->maxdepth;
+  int leaves = 0;
+  for (const Problem& P : h->probs) leaves += (int)P.levels[P.depth].size();
+  h->st.nboxes_leaf = leaves;
 }
 
 }  // namespace
@@ -1039,59 +1211,25 @@ int symhss_params_default(symhss_params* p) {
   return SYMHSS_OK;
 }
 
-static int validate_params(const symhss_params* p) {
-  if (!p) return SYMHSS_ERR_INVALID;
-  if (!(p->k0 > 0) || !(p->k1 > 0) || !(p->eps0 > 0) || !(p->eps1 > 0)) return SYMHSS_ERR_INVALID;
-  if (!std::isfinite(p->k0) || !std::isfinite(p->k1) || !std::isfinite(p->eps0) || !std::isfinite(p->eps1))
-    return SYMHSS_ERR_INVALID;
-  if (!(p->tol >= 0) || !std::isfinite(p->tol)) return SYMHSS_ERR_INVALID;
-  if (p->leaf < 1 || p->nproxy < 8 || !(p->proxy_factor > 1.0) || !std::isfinite(p->proxy_factor))
-    return SYMHSS_ERR_INVALID;
-  if (p->mode != SYMHSS_SYM && p->mode != SYMHSS_NONSYM) return SYMHSS_ERR_INVALID;
-  if (p->precision != SYMHSS_FP64) return SYMHSS_ERR_INVALID;
-  if (p->fixed_rank_kL < 0 || (p->fixed_rank_kL > 0 && !(p->rank_scale_a >= 1.0))) return SYMHSS_ERR_INVALID;
-  return SYMHSS_OK;
-}
-
-static int load_curve(symhss_s* h, const symhss_curve* c, cudaStream_t s) {
-  if (!c || c->n < 2) return SYMHSS_ERR_INVALID;
-  if (!c->x || !c->y || !c->nx || !c->ny || !c->w || !c->kappa) return SYMHSS_ERR_INVALID;
-  if (c->location != SYMHSS_HOST && c->location != SYMHSS_DEVICE) return SYMHSS_ERR_INVALID;
-  const int n = c->n;
-  std::vector<double>* dst[6] = {&h->hx, &h->hy, &h->hnx, &h->hny, &h->hw, &h->hk};
-  const double* src[6] = {c->x, c->y, c->nx, c->ny, c->w, c->kappa};
-  for (int i = 0; i < 6; ++i) {
-    dst[i]->resize(n);
-    if (c->location == SYMHSS_HOST) {
-      std::memcpy(dst[i]->data(), src[i], n * sizeof(double));
-    } else {
-      cudaError_t e = cudaMemcpyAsync(dst[i]->data(), src[i], n * sizeof(double), cudaMemcpyDeviceToHost, s);
-      if (e != cudaSuccess) return cuda_fail(h, e);
-    }
-  }
-  if (c->location == SYMHSS_DEVICE) {
-    cudaError_t e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_fail(h, e);
-  }
-  for (int i = 0; i < 6; ++i)
-    if (!finite_all(*dst[i])) return SYMHSS_ERR_INVALID;
-  for (int i = 0; i < n; ++i)
-    if (!(h->hw[i] > 0)) return SYMHSS_ERR_INVALID;
-  h->n = n;
-  return SYMHSS_OK;
-}
-
-int symhss_create(const symhss_curve* curve, const symhss_params* prm, void* stream, symhss_t* out) {
+int symhss_create_batch(const symhss_curve* curves, const symhss_params* prms, int count, void* stream,
+                        symhss_t* out) {
   if (!out) return SYMHSS_ERR_INVALID;
   *out = nullptr;
-  int rc = validate_params(prm);
-  if (rc) return rc;
+  if (!curves || !prms || count < 1) return SYMHSS_ERR_INVALID;
+  for (int c = 0; c < count; ++c) {
+    int rc = validate_params(&prms[c]);
+    if (rc) return rc;
+    if (!same_shared(prms[0], prms[c])) return SYMHSS_ERR_INVALID;
+  }
   cudaStream_t s = (cudaStream_t)stream;
   symhss_s* h = new (std::nothrow) symhss_s();
   if (!h) return SYMHSS_ERR_NOMEM;
+  int rc = SYMHSS_OK;
   try {
-    h->prm = *prm;
-    rc = load_curve(h, curve, s);
+    h->prm = prms[0];
+    h->probs.resize(count);
+    for (int c = 0; c < count; ++c) h->probs[c].prm = prms[c];
+    rc = load_curves(h, curves, count, s);
     if (!rc) rc = build_geometry(h, s);
     if (!rc) {
       cudaError_t e = h->status.ensure(sizeof(int));
@@ -1106,24 +1244,49 @@ int symhss_create(const symhss_curve* curve, const symhss_params* prm, void* str
     symhss_destroy(h);
     return rc;
   }
-  h->st.n = h->n;
-  h->st.depth = h->depth;
-  h->st.nboxes_leaf = (int)h->levels[h->depth].boxes.size();
+  geometry_stats(h);
   *out = h;
   return SYMHSS_OK;
 }
 
-int symhss_set_curve(symhss_t h, const symhss_curve* curve, void* stream) {
-  if (!h || !curve || curve->n != h->n) return SYMHSS_ERR_INVALID;
+int symhss_create(const symhss_curve* curve, const symhss_params* prm, void* stream, symhss_t* out) {
+  if (!curve || !prm) {
+    if (out) *out = nullptr;
+    return SYMHSS_ERR_INVALID;
+  }
+  return symhss_create_batch(curve, prm, 1, stream, out);
+}
+
+int symhss_set_curves(symhss_t h, const symhss_curve* curves, int count, void* stream) {
+  if (!h || !curves || count != (int)h->probs.size()) return SYMHSS_ERR_INVALID;
+  for (int c = 0; c < count; ++c)
+    if (curves[c].n != h->probs[c].n) return SYMHSS_ERR_INVALID;
   try {
-    int rc = load_curve(h, curve, (cudaStream_t)stream);
+    h->compressed = h->factored = false;
+    int rc = load_curves(h, curves, count, (cudaStream_t)stream);
     if (rc) return rc;
     rc = build_geometry(h, (cudaStream_t)stream);
-    h->compressed = h->factored = false;
+    if (!rc) geometry_stats(h);
     return rc;
   } catch (const std::bad_alloc&) {
     return SYMHSS_ERR_NOMEM;
   }
+}
+
+int symhss_set_curve(symhss_t h, const symhss_curve* curve, void* stream) {
+  if (!h || (int)h->probs.size() != 1) return SYMHSS_ERR_INVALID;
+  return symhss_set_curves(h, curve, 1, stream);
+}
+
+int symhss_batch_info(symhss_t h, int* count, int* n, int* depth, long long* row0) {
+  if (!h) return SYMHSS_ERR_INVALID;
+  if (count) *count = (int)h->probs.size();
+  for (size_t c = 0; c < h->probs.size(); ++c) {
+    if (n) n[c] = h->probs[c].n;
+    if (depth) depth[c] = h->probs[c].depth;
+    if (row0) row0[c] = h->probs[c].vec0;
+  }
+  return SYMHSS_OK;
 }
 
 int symhss_compress(symhss_t h, void* stream) {
@@ -1145,8 +1308,8 @@ int symhss_compress(symhss_t h, void* stream) {
   try {
     CK(cudaMemsetAsync(h->status.p, 0, sizeof(int), s));
     CK(cudaEventRecord(h->ev[0], s));
-    for (int l = h->depth; l >= 1; --l) {
-      int rc = compress_level(h, l, s);
+    for (int t = 0; t < h->maxdepth; ++t) {
+      int rc = compress_height(h, t, s);
       if (rc) return rc;
       rc = read_status(h, s);
       if (rc) return rc;
@@ -1159,20 +1322,32 @@ int symhss_compress(symhss_t h, void* stream) {
   } catch (const std::bad_alloc&) {
     return SYMHSS_ERR_NOMEM;
   }
-  // rank statistics
+  // rank statistics by level, over every problem that has the level
   h->st.max_rank[0] = h->st.max_rank[1] = 0;
-  for (int l = 1; l <= h->depth; ++l) {
-    auto& bxs = h->levels[l].boxes;
+  for (int l = 0; l < SYMHSS_MAX_LEVELS; ++l) {
+    h->st.level_nproxy[l] = 0;
+    for (int p = 0; p < 2; ++p) {
+      h->st.level_max_rank[l][p] = 0;
+      h->st.level_mean_rank[l][p] = 0.0;
+    }
+  }
+  for (int l = 1; l <= h->maxdepth; ++l) {
     for (int p = 0; p < 2; ++p) {
       int mx = 0;
       double sum = 0;
-      for (auto& b : bxs) { mx = std::max(mx, b.rank[p]); sum += b.rank[p]; }
+      long long cnt = 0;
+      for (const Problem& P : h->probs) {
+        if (P.depth < l) continue;
+        for (const HBox& b : P.levels[l]) { mx = std::max(mx, b.rank[p]); sum += b.rank[p]; ++cnt; }
+      }
       h->st.level_max_rank[l][p] = mx;
-      h->st.level_mean_rank[l][p] = bxs.empty() ? 0.0 : sum / bxs.size();
+      h->st.level_mean_rank[l][p] = cnt ? sum / (double)cnt : 0.0;
       h->st.max_rank[p] = std::max(h->st.max_rank[p], mx);
     }
     int mp = 0;
-    for (auto& b : bxs) mp = std::max(mp, b.P);
+    for (const Problem& P : h->probs)
+      if (P.depth >= l)
+        for (const HBox& b : P.levels[l]) mp = std::max(mp, b.P);
     h->st.level_nproxy[l] = mp;
   }
   h->compressed = true;
@@ -1181,7 +1356,7 @@ int symhss_compress(symhss_t h, void* stream) {
 
 int symhss_factor(symhss_t h, void* stream) {
   if (!h) return SYMHSS_ERR_INVALID;
-  if (!h->compressed && h->depth > 0) return SYMHSS_ERR_STATE;
+  if (!h->compressed && h->maxdepth > 0) return SYMHSS_ERR_STATE;
   cudaStream_t s = (cudaStream_t)stream;
   h->factored = false;
   h->st.flops_lu = 0;
@@ -1189,20 +1364,20 @@ int symhss_factor(symhss_t h, void* stream) {
   try {
     CK(cudaMemsetAsync(h->status.p, 0, sizeof(int), s));
     CK(cudaEventRecord(h->ev[0], s));
-    for (int l = h->depth; l >= 1; --l) {
-      int rc = factor_level(h, l, s, pairs);
+    for (int t = 0; t <= h->maxdepth; ++t) {
+      int rc = factor_height(h, t, s, pairs);
       if (rc) return rc;
     }
-    int rc = assemble_and_lu(h, 0, s, pairs);
-    if (rc) return rc;
     CK(cudaEventRecord(h->ev[1], s));
-    rc = read_status(h, s);
+    int rc = read_status(h, s);
     if (rc) return rc;
     prof_collect(h);
     float ms = 0;
     cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
     h->st.ms_factor = ms;
-    h->st.root_size = h->levels[0].boxes[0].size;
+    int rs = 0;
+    for (const Problem& P : h->probs) rs = std::max(rs, P.levels[0][0].size);
+    h->st.root_size = rs;
   } catch (const std::bad_alloc&) {
     return SYMHSS_ERR_NOMEM;
   }
@@ -1213,10 +1388,8 @@ int symhss_factor(symhss_t h, void* stream) {
 
 int symhss_rhs_plane_wave(symhss_t h, double angle, void* rhs, void* stream) {
   if (!h || !rhs || !std::isfinite(angle)) return SYMHSS_ERR_INVALID;
-  PointTable t = table_of(h);
-  CK(launch_plane_wave(t.x, t.y, t.nx, t.ny, t.w, h->n, h->prm.k0, h->prm.eps0, angle,
-                       h->prm.mode == SYMHSS_SYM ? 1 : 0, reinterpret_cast<double2*>(rhs),
-                       (cudaStream_t)stream));
+  CK(launch_plane_wave(table_of(h), h->waves.as<WaveJob>(), (int)h->probs.size(), h->max_n, angle,
+                       h->prm.mode == SYMHSS_SYM ? 1 : 0, reinterpret_cast<double2*>(rhs), (cudaStream_t)stream));
   return SYMHSS_OK;
 }
 
@@ -1224,38 +1397,43 @@ int symhss_solve(symhss_t h, const void* rhs, void* x, int nrhs, void* stream) {
   if (!h || !rhs || !x || nrhs < 1) return SYMHSS_ERR_INVALID;
   if (!h->factored) return SYMHSS_ERR_STATE;
   cudaStream_t s = (cudaStream_t)stream;
-  const int n = h->n;
+  const long long ldv = 2LL * h->ntot;
   const double2* f = reinterpret_cast<const double2*>(rhs);
   double2* xo = reinterpret_cast<double2*>(x);
   try {
     CK(cudaEventRecord(h->ev[0], s));
-    // up pass
-    for (int l = h->depth; l >= 0; --l) {
-      Level& L = h->levels[l];
-      auto& boxes = L.boxes;
+    std::vector<BoxRef> refs;
+    // up pass: g = D^{-1} f, f~ = Atilde R g, from the leaves to every root
+    for (int t = 0; t <= h->maxdepth; ++t) {
+      Height& H = h->heights[t];
+      height_boxes(h, t, true, refs);
+      if (refs.empty()) continue;
       long long g_total = 0, ft_total = 0;
-      for (auto& bx : boxes) {
+      for (const BoxRef& rf : refs) {
+        HBox& bx = *rf.bx;
+        const bool root = rf.l == 0;
         bx.g_off = g_total;
         g_total += (long long)bx.size * nrhs;
         bx.ft_off = ft_total;
-        ft_total += (long long)(l > 0 ? bx.k : 0) * nrhs;
+        ft_total += (long long)(root ? 0 : bx.k) * nrhs;
       }
-      CK(L.G.ensure(g_total * sizeof(double2)));
-      CK(L.FT.ensure(ft_total * sizeof(double2)));
-      CK(L.TMP.ensure(ft_total * sizeof(double2)));
+      CK(H.G.ensure(g_total * sizeof(double2)));
+      CK(H.FT.ensure(ft_total * sizeof(double2)));
+      CK(H.TMP.ensure(ft_total * sizeof(double2)));
       Packer pk;
       std::vector<LeafJob> lj;
       std::vector<CopyJob> cj;
       std::vector<RsJob> rs;
       std::vector<BasisJob> bj;
       std::vector<GemmJob> gj;
-      int max_n = 1, max_k = 1;
-      for (auto& bx : boxes) {
-        if (l == h->depth) {
-          lj.push_back(LeafJob{bx.g_off, bx.begin, bx.end - bx.begin});
-        } else {
-          const HBox& c1 = h->levels[l + 1].boxes[bx.child[0]];
-          const HBox& c2 = h->levels[l + 1].boxes[bx.child[1]];
+      int max_n = 1;
+      if (t == 0) leaf_jobs(h, lj);
+      for (const BoxRef& rf : refs) {
+        const HBox& bx = *rf.bx;
+        if (t > 0) {
+          const auto& kids = h->probs[rf.p].levels[rf.l + 1];
+          const HBox& c1 = kids[bx.child[0]];
+          const HBox& c2 = kids[bx.child[1]];
           CopyJob c;
           c.src_off = c1.ft_off; c.dst_off = bx.g_off; c.rows = c1.k; c.cols = nrhs; c.lds = c1.k; c.ldd = bx.size;
           cj.push_back(c);
@@ -1267,7 +1445,7 @@ int symhss_solve(symhss_t h, const void* rhs, void* x, int nrhs, void* stream) {
         r.b_off = bx.g_off; r.ldb = bx.size; r.nrhs = nrhs;
         rs.push_back(r);
         max_n = std::max(max_n, bx.size);
-        if (l > 0) {
+        if (rf.l > 0) {
           BasisJob b{};
           for (int p = 0; p < 2; ++p) {
             b.part[p].q_off = bx.q_off[p]; b.part[p].t_off = bx.t_off[p];
@@ -1283,97 +1461,103 @@ int symhss_solve(symhss_t h, const void* rhs, void* x, int nrhs, void* stream) {
           gmm.c_off = bx.ft_off; gmm.ldc = bx.k;
           gmm.m = bx.k; gmm.n = nrhs; gmm.k = bx.k; gmm.alpha = 1.0; gmm.beta = 0.0;
           gj.push_back(gmm);
-          max_k = std::max(max_k, bx.k);
         }
       }
       const size_t olj = pk.add(lj), ocj = pk.add(cj), ors = pk.add(rs), obj = pk.add(bj), ogj = pk.add(gj);
-      CK(pk.upload(L.slists, s));
-      char* sb = L.slists.as<char>();
-      if (l == h->depth)
-        TIMED(SYMHSS_K_OTHER, 0.0, launch_leaf_gather(f, 2 * n, L.G.as<double2>(),
+      CK(pk.upload(H.slists, s));
+      char* sb = H.slists.as<char>();
+      if (t == 0)
+        TIMED(SYMHSS_K_OTHER, 0.0, launch_leaf_gather(f, ldv, H.G.as<double2>(),
                                                       reinterpret_cast<const LeafJob*>(sb + olj), (int)lj.size(),
-                                                      nrhs, n, s));
+                                                      nrhs, s));
       else
-        TIMED(SYMHSS_K_OTHER, 0.0, launch_copy_blocks(h->levels[l + 1].FT.as<double2>(), L.G.as<double2>(),
+        TIMED(SYMHSS_K_OTHER, 0.0, launch_copy_blocks(h->heights[t - 1].FT.as<double2>(), H.G.as<double2>(),
                                                       reinterpret_cast<const CopyJob*>(sb + ocj), (int)cj.size(),
                                                       s));
       double w_g = 0, w_up = 0;
-      for (auto& bx : boxes) {
+      for (const BoxRef& rf : refs) {
+        const HBox& bx = *rf.bx;
         w_g += 8.0 * (double)bx.size * bx.size * nrhs;
-        if (l > 0) w_up += 8.0 * (double)bx.k * (double)(bx.perm[0].size() + bx.perm[1].size() + bx.k) * nrhs;
+        if (rf.l > 0) w_up += 8.0 * (double)bx.k * (double)(bx.perm[0].size() + bx.perm[1].size() + bx.k) * nrhs;
       }
       RsLaunch ra;
-      ra.abase = L.D.as<double2>(); ra.piv = L.piv.as<int>(); ra.bbase = L.G.as<double2>();
+      ra.abase = H.D.as<double2>(); ra.piv = H.piv.as<int>(); ra.bbase = H.G.as<double2>();
       ra.jobs = reinterpret_cast<const RsJob*>(sb + ors); ra.njobs = (int)rs.size();
       ra.max_rhs = nrhs; ra.max_n = max_n;
       TIMED(SYMHSS_K_GETRS, w_g, launch_getrs(ra, s));
-      if (l > 0) {
+      if (!bj.empty()) {
         // tmp = R g ; f~ = Atilde tmp
         BasisLaunch ba;
-        ba.q = reinterpret_cast<const int*>(L.qbuf.p);
-        ba.T = L.tbuf.as<double2>();
-        ba.in = L.G.as<double2>();
-        ba.out = L.TMP.as<double2>();
+        ba.q = reinterpret_cast<const int*>(H.qbuf.p);
+        ba.T = H.tbuf.as<double2>();
+        ba.in = H.G.as<double2>();
+        ba.out = H.TMP.as<double2>();
         ba.jobs = reinterpret_cast<const BasisJob*>(sb + obj);
         ba.njobs = (int)bj.size();
         ba.max_cols = nrhs;
         TIMED(SYMHSS_K_OTHER, w_up, launch_apply_r(ba, s));
         GemmLaunch ga;
-        ga.A = L.At.as<double2>(); ga.B = L.TMP.as<double2>(); ga.C = L.FT.as<double2>();
+        ga.A = H.At.as<double2>(); ga.B = H.TMP.as<double2>(); ga.C = H.FT.as<double2>();
         ga.jobs = reinterpret_cast<const GemmJob*>(sb + ogj); ga.njobs = (int)gj.size();
         TIMED(SYMHSS_K_OTHER, 0.0, launch_gemm(ga, s));
       }
     }
-    // down pass: x_c = g_c - X_c (f~_c - Atilde_c y_c)
-    for (int l = 1; l <= h->depth; ++l) {
-      Level& L = h->levels[l];
-      Level& LP = h->levels[l - 1];
+    // down pass: x_c = g_c - X_c (f~_c - Atilde_c y_c), parents at height t + 1
+    for (int t = h->maxdepth - 1; t >= 0; --t) {
+      Height& H = h->heights[t];
+      Height& HP = h->heights[t + 1];
       std::vector<GemmJob> g1, g2;
-      for (auto& par : LP.boxes) {
-        int row0 = 0;
-        for (int c = 0; c < 2; ++c) {
-          HBox& bx = L.boxes[par.child[c]];
-          GemmJob a;
-          a.a_off = bx.rx_off; a.lda = bx.k;
-          a.b_off = par.g_off + row0; a.ldb = par.size;
-          a.c_off = bx.ft_off; a.ldc = bx.k;
-          a.m = bx.k; a.n = nrhs; a.k = bx.k; a.alpha = -1.0; a.beta = 1.0;
-          g1.push_back(a);
-          GemmJob b;
-          b.a_off = bx.x_off; b.lda = bx.size;
-          b.b_off = bx.ft_off; b.ldb = bx.k;
-          b.c_off = bx.g_off; b.ldc = bx.size;
-          b.m = bx.size; b.n = nrhs; b.k = bx.k; b.alpha = -1.0; b.beta = 1.0;
-          g2.push_back(b);
-          row0 += bx.k;
+      for (Problem& P : h->probs) {
+        if (P.depth <= t) continue;
+        const int l = P.depth - t;
+        for (const HBox& par : P.levels[l - 1]) {
+          int row0 = 0;
+          for (int c = 0; c < 2; ++c) {
+            const HBox& bx = P.levels[l][par.child[c]];
+            GemmJob a;
+            a.a_off = bx.rx_off; a.lda = bx.k;
+            a.b_off = par.g_off + row0; a.ldb = par.size;
+            a.c_off = bx.ft_off; a.ldc = bx.k;
+            a.m = bx.k; a.n = nrhs; a.k = bx.k; a.alpha = -1.0; a.beta = 1.0;
+            g1.push_back(a);
+            GemmJob b;
+            b.a_off = bx.x_off; b.lda = bx.size;
+            b.b_off = bx.ft_off; b.ldb = bx.k;
+            b.c_off = bx.g_off; b.ldc = bx.size;
+            b.m = bx.size; b.n = nrhs; b.k = bx.k; b.alpha = -1.0; b.beta = 1.0;
+            g2.push_back(b);
+            row0 += bx.k;
+          }
         }
       }
+      if (g1.empty()) continue;
       Packer pk;
       const size_t o1 = pk.add(g1), o2 = pk.add(g2);
-      CK(pk.upload(L.slists, s));
-      char* sb = L.slists.as<char>();
+      CK(pk.upload(H.slists, s));
+      char* sb = H.slists.as<char>();
       GemmLaunch ga;
-      ga.A = L.At.as<double2>(); ga.B = LP.G.as<double2>(); ga.C = L.FT.as<double2>();
+      ga.A = H.At.as<double2>(); ga.B = HP.G.as<double2>(); ga.C = H.FT.as<double2>();
       ga.jobs = reinterpret_cast<const GemmJob*>(sb + o1); ga.njobs = (int)g1.size();
       double w_dn = 0;
       for (const auto& j : g1) w_dn += 8.0 * (double)j.m * j.n * j.k;
       for (const auto& j : g2) w_dn += 8.0 * (double)j.m * j.n * j.k;
       TIMED(SYMHSS_K_OTHER, w_dn, launch_gemm(ga, s));
       GemmLaunch gb;
-      gb.A = L.X.as<double2>(); gb.B = L.FT.as<double2>(); gb.C = L.G.as<double2>();
+      gb.A = H.X.as<double2>(); gb.B = H.FT.as<double2>(); gb.C = H.G.as<double2>();
       gb.jobs = reinterpret_cast<const GemmJob*>(sb + o2); gb.njobs = (int)g2.size();
       TIMED(SYMHSS_K_OTHER, 0.0, launch_gemm(gb, s));
     }
     {
-      Level& L = h->levels[h->depth];
+      // the leaf lists of height 0 were overwritten by the down pass: upload them again
       std::vector<LeafJob> lj;
-      for (auto& bx : L.boxes) lj.push_back(LeafJob{bx.g_off, bx.begin, bx.end - bx.begin});
+      leaf_jobs(h, lj);
       Packer pk;
       const size_t o = pk.add(lj);
-      CK(pk.upload(h->levels[0].slists, s));
-      TIMED(SYMHSS_K_OTHER, 0.0, launch_leaf_scatter(L.G.as<double2>(), xo, 2 * n,
-                             reinterpret_cast<const LeafJob*>(h->levels[0].slists.as<char>() + o),
-                             (int)lj.size(), nrhs, n, s));
+      Height& H0 = h->heights[0];
+      DevBuf& lb = h->maxdepth > 0 ? h->heights[h->maxdepth].slists : H0.slists;
+      CK(pk.upload(lb, s));
+      TIMED(SYMHSS_K_OTHER, 0.0, launch_leaf_scatter(H0.G.as<double2>(), xo, ldv,
+                             reinterpret_cast<const LeafJob*>(lb.as<char>() + o), (int)lj.size(), nrhs, s));
     }
     CK(cudaEventRecord(h->ev[1], s));
     int rc = read_status(h, s);
@@ -1391,7 +1575,7 @@ int symhss_solve(symhss_t h, const void* rhs, void* x, int nrhs, void* stream) {
 int symhss_solve_host(symhss_t h, const void* rhs_host, void* x_host, int nrhs, void* stream) {
   if (!h || !rhs_host || !x_host || nrhs < 1) return SYMHSS_ERR_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
-  const size_t bytes = (size_t)2 * h->n * nrhs * sizeof(double2);
+  const size_t bytes = (size_t)2 * h->ntot * nrhs * sizeof(double2);
   CK(h->xin.ensure(bytes));
   CK(h->xout.ensure(bytes));
   CK(cudaMemcpyAsync(h->xin.p, rhs_host, bytes, cudaMemcpyHostToDevice, s));
@@ -1404,11 +1588,12 @@ int symhss_solve_host(symhss_t h, const void* rhs_host, void* x_host, int nrhs, 
 
 int symhss_stats(symhss_t h, symhss_stats_t* out) {
   if (!h || !out) return SYMHSS_ERR_INVALID;
-  long long bytes = (long long)h->pts.cap + (long long)h->status.cap + h->xin.cap + h->xout.cap;
-  for (auto& L : h->levels) {
-    for (DevBuf* b : {&L.mr, &L.tbuf, &L.permbuf, &L.rankbuf, &L.refbuf, &L.clists, &L.idjobs, &L.slices, &L.skmeta, &L.D, &L.piv,
-                      &L.rxpiv, &L.info, &L.X, &L.RX, &L.At, &L.qbuf, &L.flists, &L.lujobs, &L.cjobs, &L.G,
-                      &L.FT, &L.TMP, &L.slists})
+  long long bytes = (long long)h->pts.cap + (long long)h->status.cap + h->xin.cap + h->xout.cap + h->kps.cap +
+                    h->waves.cap;
+  for (auto& H : h->heights) {
+    for (DevBuf* b : {&H.mr, &H.tbuf, &H.permbuf, &H.rankbuf, &H.refbuf, &H.clists, &H.idjobs, &H.slices,
+                      &H.skmeta, &H.D, &H.piv, &H.rxpiv, &H.info, &H.X, &H.RX, &H.At, &H.qbuf, &H.flists,
+                      &H.lujobs, &H.cjobs, &H.G, &H.FT, &H.TMP, &H.slists})
       bytes += (long long)b->cap;
   }
   h->st.device_bytes = bytes;
@@ -1417,16 +1602,20 @@ int symhss_stats(symhss_t h, symhss_stats_t* out) {
   return SYMHSS_OK;
 }
 
-int symhss_level_ranks(symhss_t h, int level, int* out) {
-  if (!h || !out || level < 1 || level > h->depth) return SYMHSS_ERR_INVALID;
+int symhss_problem_ranks(symhss_t h, int problem, int level, int* out) {
+  if (!h || !out || problem < 0 || problem >= (int)h->probs.size()) return SYMHSS_ERR_INVALID;
+  const Problem& P = h->probs[problem];
+  if (level < 1 || level > P.depth) return SYMHSS_ERR_INVALID;
   if (!h->compressed) return SYMHSS_ERR_STATE;
-  auto& bxs = h->levels[level].boxes;
+  const auto& bxs = P.levels[level];
   for (size_t b = 0; b < bxs.size(); ++b) {
     out[2 * b] = bxs[b].rank[0];
     out[2 * b + 1] = bxs[b].rank[1];
   }
   return SYMHSS_OK;
 }
+
+int symhss_level_ranks(symhss_t h, int level, int* out) { return symhss_problem_ranks(h, 0, level, out); }
 
 int symhss_destroy(symhss_t h) {
   if (!h) return SYMHSS_OK;

@@ -143,6 +143,7 @@ __global__ void __launch_bounds__(TILE_T) tile_kernel(const TileLaunch a) {
   const int ts0 = a.tp_s0[tidx], ts1 = a.tp_s1[tidx];
   const bool src_thread = (jb.flags & TILE_SRC_IS_THREAD) != 0;
   const bool unscaled = (jb.flags & TILE_UNSCALED) != 0;
+  const KernelParams kp = a.kps[jb.prm];
   if (ts0 >= jb.ld || ts1 >= jb.ld) { atomicOr(a.status, ST_BAD_INDEX); return; }
   double2* out = a.out + jb.out_off;
   for (int l = 0; l < nl; ++l) {
@@ -152,8 +153,8 @@ __global__ void __launch_bounds__(TILE_T) tile_kernel(const TileLaunch a) {
     const int ls0 = ss0[l], ls1 = ss1[l];
     if ((ts0 < 0 && ts1 < 0) || (ls0 < 0 && ls1 < 0)) continue;
     double2 blk[4];
-    if (src_thread) pair_block(lp, tp, a.kp, unscaled, blk);
-    else pair_block(tp, lp, a.kp, unscaled, blk);
+    if (src_thread) pair_block(lp, tp, kp, unscaled, blk);
+    else pair_block(tp, lp, kp, unscaled, blk);
     // blk[e*2 + c]; thread slots are equations (normal) or unknowns (transposed)
     const int tsl[2] = {ts0, ts1};
     const int lsl[2] = {ls0, ls1};

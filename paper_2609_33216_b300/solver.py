@@ -86,3 +86,73 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+class BatchSolver:
+    """Many independent scatterers in one handle: every tree height of every problem
+    runs in one launch per kernel.  Vectors stack the problems' [eq1; eq2] blocks."""
+
+    def __init__(self, curves, k0s, k1s, eps0s=None, eps1s=None, mode: str = "sym", **params):
+        cnt = len(curves)
+        if eps0s is None:
+            eps0s = [1.0] * cnt
+        if eps1s is None:
+            eps1s = [e0 * (k1 / k0) ** 2 for e0, k0, k1 in zip(eps0s, k0s, k1s)]
+        self.mode = S.SYMHSS_SYM if mode == "sym" else S.SYMHSS_NONSYM
+        self.prms = [S.params(k0, k1, e0, e1, mode=self.mode, **params)
+                     for k0, k1, e0, e1 in zip(k0s, k1s, eps0s, eps1s)]
+        self._keep = []
+        self.h = S.symhss_create_batch(self._curve_structs(curves), self.prms, _stream())
+        self.ns, self.depths, self.row0 = S.symhss_batch_info(self.h)
+        self.rows = 2 * sum(self.ns)
+
+    def _curve_structs(self, curves):
+        keep, out = [], []
+        for c in curves:
+            arrays = [np.ascontiguousarray(a, dtype=np.float64) for a in c.arrays()]
+            keep.append(arrays)
+            out.append(S.curve_struct(int(c.n), [a.ctypes.data for a in arrays], S.SYMHSS_HOST))
+        self._keep = keep
+        return out
+
+    def set_curves(self, curves) -> None:
+        S.symhss_set_curves(self.h, self._curve_structs(curves), _stream())
+
+    def compress(self) -> None:
+        S.symhss_compress(self.h, _stream())
+
+    def factor(self) -> None:
+        S.symhss_factor(self.h, _stream())
+
+    def rhs(self, angle: float = 0.0) -> torch.Tensor:
+        f = torch.empty(self.rows, dtype=torch.complex128, device="cuda")
+        S.symhss_rhs_plane_wave(self.h, angle, f.data_ptr(), _stream())
+        return f
+
+    def solve(self, rhs: torch.Tensor) -> torch.Tensor:
+        rhs = rhs.contiguous()
+        nrhs = 1 if rhs.dim() == 1 else rhs.shape[0]
+        x = torch.empty_like(rhs)
+        S.symhss_solve(self.h, rhs.data_ptr(), x.data_ptr(), nrhs, _stream())
+        return x
+
+    def block(self, v: torch.Tensor, c: int) -> torch.Tensor:
+        """Problem c's [eq1; eq2] block of a batch vector."""
+        return v[..., self.row0[c]:self.row0[c] + 2 * self.ns[c]]
+
+    def stats(self) -> S.symhss_stats_t:
+        return S.symhss_stats(self.h)
+
+    def ranks(self, problem: int, level: int):
+        return S.symhss_problem_ranks(self.h, problem, level)
+
+    def close(self) -> None:
+        if getattr(self, "h", None) is not None:
+            S.symhss_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -75,6 +75,10 @@ _SIGNATURES = [
     ("symhss_create", C.c_int, [C.POINTER(symhss_curve), C.POINTER(symhss_params), C.c_void_p,
                                 C.POINTER(C.c_void_p)]),
     ("symhss_set_curve", C.c_int, [C.c_void_p, C.POINTER(symhss_curve), C.c_void_p]),
+    ("symhss_create_batch", C.c_int, [C.POINTER(symhss_curve), C.POINTER(symhss_params), C.c_int, C.c_void_p,
+                                      C.POINTER(C.c_void_p)]),
+    ("symhss_set_curves", C.c_int, [C.c_void_p, C.POINTER(symhss_curve), C.c_int, C.c_void_p]),
+    ("symhss_batch_info", C.c_int, [C.c_void_p, _ip, _ip, _ip, C.POINTER(C.c_longlong)]),
     ("symhss_compress", C.c_int, [C.c_void_p, C.c_void_p]),
     ("symhss_factor", C.c_int, [C.c_void_p, C.c_void_p]),
     ("symhss_rhs_plane_wave", C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p]),
@@ -82,6 +86,7 @@ _SIGNATURES = [
     ("symhss_solve_host", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     ("symhss_stats", C.c_int, [C.c_void_p, C.POINTER(symhss_stats_t)]),
     ("symhss_level_ranks", C.c_int, [C.c_void_p, C.c_int, _ip]),
+    ("symhss_problem_ranks", C.c_int, [C.c_void_p, C.c_int, C.c_int, _ip]),
     ("symhss_destroy", C.c_int, [C.c_void_p]),
     ("symhss_launch_count", C.c_longlong, []),
     ("symhss_hankel01", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
@@ -150,6 +155,39 @@ def symhss_create(curve: symhss_curve, prm: symhss_params, stream: int = 0) -> C
     h = C.c_void_p()
     check(lib.symhss_create(C.byref(curve), C.byref(prm), C.c_void_p(stream), C.byref(h)), "symhss_create")
     return h
+
+
+def symhss_create_batch(curves, prms, stream: int = 0) -> C.c_void_p:
+    """curves: list of symhss_curve, prms: list of symhss_params (same length)."""
+    cnt = len(curves)
+    ca = (symhss_curve * cnt)(*curves)
+    pa = (symhss_params * cnt)(*prms)
+    h = C.c_void_p()
+    check(lib.symhss_create_batch(ca, pa, cnt, C.c_void_p(stream), C.byref(h)), "symhss_create_batch")
+    return h
+
+
+def symhss_set_curves(h, curves, stream: int = 0) -> None:
+    cnt = len(curves)
+    ca = (symhss_curve * cnt)(*curves)
+    check(lib.symhss_set_curves(h, ca, cnt, C.c_void_p(stream)), "symhss_set_curves")
+
+
+def symhss_batch_info(h):
+    """(n, depth, row0) lists, one entry per problem."""
+    cnt = C.c_int()
+    check(lib.symhss_batch_info(h, C.byref(cnt), None, None, None), "symhss_batch_info")
+    n = (C.c_int * cnt.value)()
+    d = (C.c_int * cnt.value)()
+    r = (C.c_longlong * cnt.value)()
+    check(lib.symhss_batch_info(h, None, n, d, r), "symhss_batch_info")
+    return list(n), list(d), list(r)
+
+
+def symhss_problem_ranks(h, problem: int, level: int):
+    out = (C.c_int * (2 * (1 << level)))()
+    check(lib.symhss_problem_ranks(h, problem, level, out), "symhss_problem_ranks")
+    return [(out[2 * b], out[2 * b + 1]) for b in range(1 << level)]
 
 
 def symhss_set_curve(h, curve: symhss_curve, stream: int = 0) -> None:

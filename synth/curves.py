@@ -81,12 +81,12 @@ def star(n: int, amp: float = 0.3, m: int = 5) -> Curve:
 
 def random_star_batch(count: int, seed: int, n_min: int = 2048, n_max: int = 32768,
                       k_range: Tuple[float, float] = (5.0, 40.0),
-                      ratio_range: Tuple[float, float] = (1.2, 2.0),
-                      leaf: int = 128) -> List[Dict]:
+                      ratio_range: Tuple[float, float] = (1.2, 2.0)) -> List[Dict]:
     """Random scatterers r = 1 + sum_{m=2..8} a_m cos(m*theta + phi_m), a_m ~ U(0, 0.05).
 
-    Node counts are drawn log-uniformly in [n_min, n_max] and rounded to a
-    multiple of ``leaf``; k_ext ~ U(k_range), k_int = k_ext * U(ratio_range).
+    Node counts are drawn log-uniformly in [n_min, n_max] (any integer, so leaf
+    boxes come out uneven); k_ext ~ U(k_range), k_int = k_ext * U(ratio_range),
+    eps0 = 1, eps1 = (k_int / k_ext)^2.
     """
     rng = np.random.default_rng(seed)
     out = []
@@ -94,11 +94,12 @@ def random_star_batch(count: int, seed: int, n_min: int = 2048, n_max: int = 327
         a = rng.uniform(0.0, 0.05, size=7)
         phi = rng.uniform(0.0, 2.0 * np.pi, size=7)
         n = int(round(math.exp(rng.uniform(math.log(n_min), math.log(n_max)))))
-        n = max(leaf, leaf * int(round(n / leaf)))
+        n = min(max(n, n_min), n_max)
         k0 = float(rng.uniform(*k_range))
         k1 = k0 * float(rng.uniform(*ratio_range))
         modes = tuple((m, float(a[m - 2]), float(phi[m - 2])) for m in range(2, 9))
-        out.append({"curve": fourier_star(n, modes, name=f"rstar{i}"), "k0": k0, "k1": k1})
+        out.append({"curve": fourier_star(n, modes, name=f"rstar{i}"), "k0": k0, "k1": k1,
+                    "eps0": 1.0, "eps1": (k1 / k0) ** 2})
     return out
 
 
@@ -110,6 +111,26 @@ WORKLOADS: Dict[str, Dict] = {
     "star64k": dict(curve=("star", 65536), k0=40.0, k1=60.0, leaf=128, nproxy=64, tol=1e-10),
     "star262k": dict(curve=("star", 262144), k0=100.0, k1=150.0, leaf=128, nproxy=64, tol=1e-8),
 }
+
+# Batch of independent random scatterers (random_star_batch), solved in one handle.
+BATCH_WORKLOADS: Dict[str, Dict] = {
+    "batch64": dict(count=64, seed=2024, n_min=2048, n_max=32768, leaf=128, nproxy=64, tol=1e-10),
+}
+
+
+def batch_workload(name: str, count: int | None = None, n_max: int | None = None) -> Dict:
+    """The named batch workload with its sampled scatterers; ``count`` / ``n_max`` shrink it."""
+    spec = dict(BATCH_WORKLOADS[name])
+    cnt = spec.pop("count") if count is None else count
+    spec.pop("count", None)
+    seed = spec.pop("seed")
+    lo, hi = spec.pop("n_min"), spec.pop("n_max")
+    if n_max is not None:
+        hi = n_max
+        lo = min(lo, hi)
+    spec["problems"] = random_star_batch(cnt, seed, lo, hi)
+    spec["name"] = name
+    return spec
 
 
 def workload(name: str, n: int | None = None) -> Dict:

@@ -51,3 +51,27 @@ def test_invalid_arguments_rejected_on_host():
     assert S.lib.symhss_strerror(S.SYMHSS_ERR_SINGULAR) == b"singular diagonal block"
     assert S.lib.symhss_column_id(None, 4, 4, 2, 16, 1, 1e-3, -1, None, None, None, 4, None) == S.SYMHSS_ERR_INVALID
     assert S.lib.symhss_lu_batched(None, 4, 2, 16, 1, None, None, None) == S.SYMHSS_ERR_INVALID
+
+
+def test_batch_create_rejects_mismatched_shared_fields_on_host():
+    from paper_2609_33216_b300 import symhss as S
+    import numpy as np
+    n = 64
+    arrs = [np.ones(n) for _ in range(6)]
+    cs = S.curve_struct(n, [a.ctypes.data for a in arrs], S.SYMHSS_HOST)
+    curves = (S.symhss_curve * 2)(cs, cs)
+    h = C.c_void_p()
+    for field, value in (("tol", 1e-6), ("leaf", 32), ("nproxy", 48), ("mode", S.SYMHSS_NONSYM),
+                         ("oversample", 0), ("seed", 7), ("proxy_factor", 2.0)):
+        p0 = S.params(1.0, 2.0)
+        p1 = S.params(3.0, 4.0, 1.0, 2.0)  # wavenumbers and materials may differ
+        setattr(p1, field, value)
+        prms = (S.symhss_params * 2)(p0, p1)
+        assert S.lib.symhss_create_batch(curves, prms, 2, None, C.byref(h)) == S.SYMHSS_ERR_INVALID, field
+    prms = (S.symhss_params * 2)(S.params(1.0, 2.0), S.params(1.0, -2.0))
+    assert S.lib.symhss_create_batch(curves, prms, 2, None, C.byref(h)) == S.SYMHSS_ERR_INVALID
+    assert S.lib.symhss_create_batch(curves, prms, 0, None, C.byref(h)) == S.SYMHSS_ERR_INVALID
+    assert S.lib.symhss_create_batch(None, prms, 2, None, C.byref(h)) == S.SYMHSS_ERR_INVALID
+    assert S.lib.symhss_set_curves(None, curves, 2, None) == S.SYMHSS_ERR_INVALID
+    assert S.lib.symhss_batch_info(None, None, None, None, None) == S.SYMHSS_ERR_INVALID
+    assert S.lib.symhss_problem_ranks(None, 0, 1, None) == S.SYMHSS_ERR_INVALID
