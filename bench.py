@@ -160,12 +160,25 @@ def run_ours(args):
     n_total = sum(cv.n for cv in curves)
     kw = dict(leaf=w["leaf"], nproxy=w["nproxy"], tol=w["tol"])
 
+    net, prop_info = None, None
+    if args.proposer:  # train the rank proposer first (outside every timed region)
+        from paper_2609_33216_b300.proposer import train_default
+        t_train = time.perf_counter()
+        net = train_default(seed=0, steps=3000)
+        prop_info = {"train_s": time.perf_counter() - t_train, "samples": int(net.data_size), "margin": 1.3,
+                     "training_data": "plain IDs of disk512, star16k, star64k (k 40/60 and 80/120) and 6 random "
+                                      "stars (k 5..60) at tol 1e-10 and 1e-8"}
+
     def make(mode):
         if batch:
             P = w["problems"]
-            return BatchSolver(curves, [p["k0"] for p in P], [p["k1"] for p in P], [p["eps0"] for p in P],
-                               [p["eps1"] for p in P], mode=mode, **kw)
-        return Solver(w["curve"], w["k0"], w["k1"], w["eps0"], w["eps1"], mode=mode, curve_on_device=True, **kw)
+            sv = BatchSolver(curves, [p["k0"] for p in P], [p["k1"] for p in P], [p["eps0"] for p in P],
+                             [p["eps1"] for p in P], mode=mode, **kw)
+        else:
+            sv = Solver(w["curve"], w["k0"], w["k1"], w["eps0"], w["eps1"], mode=mode, curve_on_device=True, **kw)
+        if net is not None:
+            net.attach(sv, margin=1.3)
+        return sv
 
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -296,6 +309,9 @@ def run_ours(args):
             "rel_diff_sym_vs_nonsym": rel_diff,
             "phases_ms": {"compress": st.ms_compress, "factor": st.ms_factor, "solve": st.ms_solve},
             "per_kernel": per_kernel,
+            "proposer": prop_info,
+            "id_checks": {"failed_then_continued": int(st.check_failed), "max_accepted_ratio": st.check_max_ratio,
+                          "proposals": int(st.proposals), "proposal_rank_err": st.proposal_rank_err},
             "sketch": {"redone_ids": int(st.sketch_redo),
                        "tensor_tflops": (r["kwork"][S.K_SKETCH] / (r["kms"][S.K_SKETCH] * 1e-3) / 1e12
                                          if r["kms"][S.K_SKETCH] > 0 else None)},
@@ -441,6 +457,7 @@ def main():
     ap.add_argument("--cpu-sample-boxes", type=int, default=16)
     ap.add_argument("--ref-sample-boxes", type=int, default=4)
     ap.add_argument("--profile", action="store_true", help="one warm-up + one symmetric step only")
+    ap.add_argument("--proposer", action="store_true", help="train the learned rank proposer and attach it")
     args = ap.parse_args()
     if args.profile:
         run_profile(args)

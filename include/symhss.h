@@ -56,6 +56,7 @@ extern "C" {
 #define SYMHSS_DEVICE  1
 
 typedef struct symhss_s* symhss_t;  /* opaque handle */
+typedef struct symhss_mlp_s* symhss_mlp_t;  /* opaque handle of a proposer network */
 
 /* Sampled curve (Sec. 3.1): nodes gamma(theta_j) at theta_j = 2 pi j / n,
  * outward unit normals (pointing into the exterior Omega_0), trapezoidal
@@ -82,8 +83,10 @@ typedef struct {
   int fixed_rank_kL;      /* > 0: fixed ranks k_l = ceil(a^(L-l) kL) (Sec. 4.3), 0: tol */
   double rank_scale_a;    /* a of Sec. 4.3 (1.15)                                     */
   int oversample;         /* sketch oversampling p (16): an ID is taken of Y = Omega M with
-                           * s = rank estimate + p rows when that is under 0.8 m rows; an ID
-                           * whose rank reaches s - p/2 is redone on M; 0 disables the sketch */
+                           * s = rank estimate + p rows (+ 16 held-out rows) when that is
+                           * under 0.8 m rows; an ID whose rank reaches s - p/2, or whose
+                           * residual on the held-out rows exceeds tol, is redone on M;
+                           * 0 disables the sketch */
   int reserved;
   uint64_t seed;          /* seed of the counter-based sketch generator               */
 } symhss_params;
@@ -97,6 +100,8 @@ typedef struct {
 #define SYMHSS_K_GETRS  3   /* batched triangular solves (X = D^-1 L, Atilde, g)  */
 #define SYMHSS_K_OTHER  4   /* bases, R X, small GEMMs, copies, gather / scatter  */
 #define SYMHSS_K_SKETCH 5   /* tensor-core sketch Y = Omega M (slicing + tcgen05 GEMM) */
+#define SYMHSS_K_CHECK  6   /* residual check of sketched IDs on held-out sketch rows  */
+#define SYMHSS_K_MLP    7   /* proposer: box features + MLP forward                     */
 #define SYMHSS_K_COUNT  8
 /* In a batch: n and nboxes_leaf are totals, depth and root_size maxima, and the
  * level statistics cover level l of every problem that has it. */
@@ -122,7 +127,13 @@ typedef struct {
   double kernel_ms[SYMHSS_K_COUNT];
   long long kernel_launches[SYMHSS_K_COUNT];
   double kernel_work[SYMHSS_K_COUNT];
-  long long sketch_redo;          /* sketched IDs redone on the full matrix (rank near s) */
+  long long sketch_redo;          /* sketched IDs redone on the full matrix (rank near s
+                                   * or residual check failed) */
+  long long check_failed;         /* sketched IDs whose residual estimate exceeded tol  */
+  double check_max_ratio;         /* largest accepted residual estimate ratio (<= tol)  */
+  long long proposals;            /* ID ranks proposed by the attached network          */
+  double proposal_rank_err;       /* mean |proposed - ID rank| / max(1, ID rank)        */
+  long long proposal_under;       /* proposals below the ID rank                        */
 } symhss_stats_t;
 
 /* ---- handle lifecycle ------------------------------------------------------ */
@@ -207,6 +218,62 @@ long long symhss_launch_count(void);
 
 /* Static message for a status code. */
 const char* symhss_strerror(int status);
+
+/* ---- learned rank / skeleton proposer (an addition to the paper's method) --------------
+ * A 3-layer MLP (128 inputs, two hidden layers of 128 with ReLU, 128 outputs of which
+ * 66 are used), FP16 weights with FP32 accumulation; FP32 master weights and Adam state
+ * for training.  Parameters are packed float[SYMHSS_MLP_PARAMS]:
+ * [W1 (128 x 128 row-major, out x in), b1, W2, b2, W3, b3].  Inputs are the 128 box
+ * features of symhss_training_data; output 0 / 1 is log2(1 + rank) / 8 of the box's
+ * flux / trace column ID, outputs 2..33 / 34..65 skeleton logits at 32 positions along
+ * the box.  Training loss over B boxes: (1/B) sum (o_h - y_h)^2
+ * + (0.1 / 64B) sum mask * BCE(sigmoid(o), t). */
+#define SYMHSS_MLP_PARAMS 49536
+#define SYMHSS_MLP_WIDTH  128
+
+/* Create a network holding `params` (host float[SYMHSS_MLP_PARAMS]; NULL = zeros) with
+ * scratch for batches of up to max_batch samples (device-synchronising). */
+int symhss_mlp_create(const float* params, int max_batch, symhss_mlp_t* out);
+/* Replace the master weights (host array; NaN/Inf refused) and reset the Adam state. */
+int symhss_mlp_set_params(symhss_mlp_t net, const float* params);
+/* Copy the FP32 master weights (params) and/or their FP16 copy (fp16_params, 2-byte
+ * IEEE halves) to host arrays; either may be NULL. */
+int symhss_mlp_get_params(symhss_mlp_t net, float* params, void* fp16_params);
+/* out[b, :] = network(x[b, :]) for `batch` samples (device float arrays, row-major
+ * batch x 128; any batch size). */
+int symhss_mlp_forward(symhss_mlp_t net, const float* x, int batch, float* out, void* stream);
+/* Loss and its gradient with respect to the FP16 weights for one batch (<= max_batch):
+ * x batch x 128, y_rank batch x 2, y_skel and mask batch x 64 (device float arrays);
+ * loss (host double) and grad (host float[SYMHSS_MLP_PARAMS]) may be NULL. */
+int symhss_mlp_loss_grad(symhss_mlp_t net, const float* x, const float* y_rank, const float* y_skel,
+                         const float* mask, int batch, double* loss, float* grad, void* stream);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8, learning rate lr) on one batch; the FP16
+ * copy is refreshed from the master weights.  loss (host) may be NULL (no sync). */
+int symhss_mlp_train_step(symhss_mlp_t net, const float* x, const float* y_rank, const float* y_skel,
+                          const float* mask, int batch, float lr, double* loss, void* stream);
+int symhss_mlp_destroy(symhss_mlp_t net);
+
+/* Attach a trained network to a solver handle (NULL detaches; the network must outlive
+ * its use).  During symhss_compress the network proposes each box's two ID ranks r~ and
+ * the randomized sketch of that ID gets s = 16 ceil((ceil(margin r~) + 2 + oversample) / 16)
+ * rows for the ID (at least 32) instead of the default estimate.  Every sketched ID --
+ * proposed or not -- also gets 16 held-out sketch rows; it is accepted only if its
+ * interpolation residual on those rows (an a-posteriori estimate of the residual on the
+ * proxy matrix) is at most tol times their largest column norm, and is otherwise redone
+ * as a plain ID of the proxy matrix.  margin >= 1.  Has no effect with oversample = 0 or
+ * fixed ranks. */
+int symhss_set_proposer(symhss_t h, symhss_mlp_t net, double margin);
+
+/* Training data of the last compression: one sample per compressed (non-root) box of
+ * every problem, ordered by tree height, problem, box.  *count: in = capacity of the
+ * arrays (ignored when x is NULL), out = number of boxes (all arrays may be NULL to query
+ * the count).  x: count x 128 features; y_rank: count x 2 (log2(1 + rank) / 8); y_skel,
+ * mask: count x 64 skeleton fractions and position masks; meta: count x 10 ints
+ * (problem, level, height, first node within the problem, node count, active flux and
+ * trace counts, near rows, proxy points, 0); geo: count x 3 (box centre x, y, radius).
+ * Host arrays; requires compress. */
+int symhss_training_data(symhss_t h, int* count, float* x, float* y_rank, float* y_skel, float* mask, int* meta,
+                         double* geo, void* stream);
 
 /* ---- building blocks (device pointers; used by the solver, exposed for tests) ---- */
 

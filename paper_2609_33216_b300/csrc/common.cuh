@@ -160,6 +160,39 @@ struct IdLaunch {
 };
 cudaError_t launch_cpqr(const IdLaunch& a, cudaStream_t s);
 
+// Interpolation residual of an ID on a set of rows (the check that accepts a sketched ID,
+// run on held-out sketch rows): ratio[out] = max over non-skeleton columns c of
+// ||M[:, c] - M[:, J] T[:, c]|| divided by the largest column norm of M (J = perm[0 .. rank),
+// T = R11^{-1} R12 with leading dimension rank).
+struct CheckJob {
+  long long m_off;   // M at mats + m_off (column-major, leading dim ld)
+  int m, n, ld;
+  int rank_idx;      // rank[rank_idx]
+  long long t_off;   // T at tbuf + t_off
+  long long perm_off;
+  int out;           // ratio[out]
+  int pad_;
+};
+cudaError_t launch_id_check(const double2* mats, const double2* tbuf, const int* perm, const int* rank,
+                            const CheckJob* jobs, int njobs, double* ratio, cudaStream_t s);
+
+// ---- learned rank / skeleton proposer --------------------------------------------------
+// A 128-128-128 ReLU MLP with FP16 weights and FP32 accumulation (parameters packed as
+// [W1 (row-major out x in), b1, W2, b2, W3, b3]); input: 128 box features, output 0 / 1:
+// log2(1 + rank) / 8 of the flux / trace half, 2..33 / 34..65: skeleton logits.
+constexpr int kMlpWidth = 128;
+constexpr int kMlpOutUsed = 66;
+constexpr int kMlpLayerParams = kMlpWidth * kMlpWidth + kMlpWidth;
+constexpr int kMlpParams = 3 * kMlpLayerParams;
+
+// Features of one box (see the feature definition in mlp.cu).
+struct FeatJob {
+  double cx, cy, rho, k0, k1, tol;
+  int begin, len, height, n0, n1, m_near, nproxy, pad_;
+};
+cudaError_t launch_box_features(const PointTable& t, const FeatJob* jobs, int njobs, float* out, cudaStream_t s);
+cudaError_t mlp_forward(symhss_mlp_s* net, const float* x, int batch, float* out, cudaStream_t s);
+
 // ---- randomized sketch Y = Omega M on the tensor cores --------------------------------
 
 struct SketchJob {

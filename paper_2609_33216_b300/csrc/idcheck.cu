@@ -1,0 +1,71 @@
+// Interpolation residual of column IDs.  A sketched ID selects its skeleton J and T from
+// rows of Y = Omega M (Sec. 4.1 with a randomized range finder); the runtime points this
+// check at sketch rows the ID did not see, where the residual of column c is
+// Omega_h (m_c - M_J t_c): its norm estimates the residual on M itself (the a-posteriori
+// estimator of Halko, Martinsson and Tropp).  The ID is accepted only if the largest
+// residual is at most the ID tolerance times the largest column norm of the same rows --
+// the bound the plain ID meets by construction -- and is otherwise redone as a plain ID
+// of M.  The kernel itself computes the ratio for whatever rows it is given.
+//
+// One block per ID: warps own columns; a lane walks the rows of its warp's column, so
+// reads of M are coalesced; per-column sums of squares are reduced with shuffles.
+#include "common.cuh"
+
+namespace symhss {
+
+namespace {
+
+constexpr int kCheckThreads = 256;
+
+__global__ void __launch_bounds__(kCheckThreads) id_check_kernel(const double2* mats, const double2* tbuf,
+                                                                 const int* perm, const int* rank,
+                                                                 const CheckJob* jobs, double* ratio) {
+  __shared__ double s_max[2][kCheckThreads / 32];
+  const CheckJob jb = jobs[blockIdx.x];
+  const double2* M = mats + jb.m_off;
+  const double2* T = tbuf + jb.t_off;
+  const int* pm = perm + jb.perm_off;
+  const int r = min(max(rank[jb.rank_idx], 0), jb.n);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kCheckThreads / 32;
+  double ref = 0.0, res = 0.0;
+  // largest column norm of M
+  for (int c = warp; c < jb.n; c += nw) {
+    const double2* col = M + (long long)c * jb.ld;
+    double ss = 0.0;
+    for (int i = lane; i < jb.m; i += 32) ss = fma(col[i].x, col[i].x, fma(col[i].y, col[i].y, ss));
+    ss = warp_sum(ss);
+    ref = fmax(ref, ss);
+  }
+  // residual of every non-skeleton column
+  for (int c = r + warp; c < jb.n; c += nw) {
+    const double2* col = M + (long long)pm[c] * jb.ld;
+    const double2* tc = T + (long long)(c - r) * r;
+    double ss = 0.0;
+    for (int i = lane; i < jb.m; i += 32) {
+      double2 e = col[i];
+      for (int k = 0; k < r; ++k) e = cfms(M[i + (long long)pm[k] * jb.ld], tc[k], e);
+      ss = fma(e.x, e.x, fma(e.y, e.y, ss));
+    }
+    ss = warp_sum(ss);
+    res = fmax(res, ss);
+  }
+  if (lane == 0) { s_max[0][warp] = ref; s_max[1][warp] = res; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < nw; ++w) { a = fmax(a, s_max[0][w]); b = fmax(b, s_max[1][w]); }
+    ratio[jb.out] = a > 0.0 ? sqrt(b / a) : 0.0;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_id_check(const double2* mats, const double2* tbuf, const int* perm, const int* rank,
+                            const CheckJob* jobs, int njobs, double* ratio, cudaStream_t s) {
+  if (njobs <= 0) return cudaSuccess;
+  id_check_kernel<<<njobs, kCheckThreads, 0, s>>>(mats, tbuf, perm, rank, jobs, ratio);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace symhss

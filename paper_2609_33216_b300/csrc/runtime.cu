@@ -93,6 +93,7 @@ struct HBox {
   double cx = 0, cy = 0, rho = 0, R = 0;
   int P = 0;
   int proxy0 = 0;  // first proxy point in the point table
+  int m_near = 0;  // near rows of M_R (both equations)
   int child[2] = {-1, -1};
   std::vector<int> act[2], actrow[2];
   int rank[2] = {0, 0}, rrank[2] = {0, 0};
@@ -161,6 +162,9 @@ struct symhss_s {
   symhss_stats_t st{};
   cudaError_t last_cuda = cudaSuccess;
   std::vector<int> mark;                          // host scratch (size npts)
+  symhss_mlp_s* mlp = nullptr;                    // attached proposer (not owned)
+  double prop_margin = 1.15;
+  symhss::DevBuf featjobs, feats, mlpout, chkjobs, chkratio;
 };
 
 namespace symhss {
@@ -480,6 +484,9 @@ struct TileBuilder {
 
 inline long long tcap(int n) { return (long long)(n / 2) * ((n + 1) / 2) + 1; }
 
+// Sketch rows held out of each sketched ID to estimate its residual on the proxy matrix.
+constexpr int kHoldRows = 16;
+
 // Near points of box b among the active lists of the other boxes of its level
 // (row lists if `rows`, else column lists), part `part`.
 void near_points(const symhss_s* h, const std::vector<HBox>& lev, int b, bool rows, int part,
@@ -549,6 +556,7 @@ int compress_height(symhss_s* h, int t, cudaStream_t s) {
     const int m0 = (int)nr0.size(), m1 = (int)nr1.size(), P = bx.P;
     const int m = m0 + m1 + 2 * P;
     const int n0 = (int)bx.act[0].size(), n1 = (int)bx.act[1].size();
+    bx.m_near = m0 + m1;
     // rows: near eq1 (slots 0..m0), near eq2 (m0..), proxy eq1 and eq2 (same points)
     tb.add(h->mark, nr0, 0, nr1, m0, bx.act[0], 0, bx.act[1], n0, mr_total, m, flags, rf.p);
     tb.add(h->mark, prx0, m0 + m1, prx0, m0 + m1 + P, bx.act[0], 0, bx.act[1], n0, mr_total, m, flags, rf.p);
@@ -601,12 +609,43 @@ int compress_height(symhss_s* h, int t, cudaStream_t s) {
     }
   }
   const int njobs = (int)jobs.size();
+  const int p_over = h->prm.oversample;
+  // Proposed ranks of the attached network (features and forward pass on the device),
+  // read back before the tiles are launched so that the host can size the sketches
+  // while the tiles run.
+  std::vector<float> prop;  // nb x 2 outputs
+  if (h->mlp && p_over > 0 && fixed < 0) {
+    std::vector<FeatJob> fj(nb);
+    for (int i = 0; i < nb; ++i) {
+      const BoxRef& rf = refs[i];
+      const HBox& bx = *rf.bx;
+      const symhss_params& pp = h->probs[rf.p].prm;
+      FeatJob f;
+      f.cx = bx.cx; f.cy = bx.cy; f.rho = bx.rho; f.k0 = pp.k0; f.k1 = pp.k1; f.tol = h->prm.tol;
+      f.begin = bx.begin; f.len = bx.end - bx.begin; f.height = t;
+      f.n0 = (int)bx.act[0].size(); f.n1 = (int)bx.act[1].size(); f.m_near = bx.m_near; f.nproxy = bx.P;
+      f.pad_ = 0;
+      fj[i] = f;
+    }
+    Packer fp;
+    fp.add(fj);
+    CK(fp.upload(h->featjobs, s));
+    CK(h->feats.ensure((size_t)nb * kMlpWidth * sizeof(float)));
+    CK(h->mlpout.ensure((size_t)nb * kMlpWidth * sizeof(float)));
+    const int e0 = prof_begin(h, s);
+    CK(launch_box_features(table_of(h), h->featjobs.as<FeatJob>(), nb, h->feats.as<float>(), s));
+    CK(mlp_forward(h->mlp, h->feats.as<float>(), nb, h->mlpout.as<float>(), s));
+    prof_end(h, s, SYMHSS_K_MLP, e0, 2.0 * 3 * kMlpWidth * kMlpWidth * (double)nb);
+    prop.resize((size_t)nb * 2);
+    CK(cudaMemcpy2DAsync(prop.data(), 2 * sizeof(float), h->mlpout.p, kMlpWidth * sizeof(float),
+                         2 * sizeof(float), nb, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
   // Randomized sketch (Halko-Martinsson-Tropp): an ID job whose rank estimate plus
   // oversampling is well below its row count is taken of Y = Omega M instead of M.
-  // Y blocks live after all proxy matrices in the same buffer.  Rank estimate: half
-  // the smaller dimension at the leaves, 1.7x the problem's largest rank one level
-  // down above.
-  const int p_over = h->prm.oversample;
+  // Y blocks live after all proxy matrices in the same buffer.  Rank estimate: the
+  // network's proposal times the margin when a network is attached; else half the
+  // smaller dimension at the leaves, 1.7x the problem's largest rank one level down above.
   const std::vector<IdJob> full = jobs;  // the same IDs on the full proxy matrices
   std::vector<int> sk_rows(njobs, 0);
   std::vector<SketchJob> sk;
@@ -619,31 +658,36 @@ int compress_height(symhss_s* h, int t, cudaStream_t s) {
       IdJob& j = jobs[i];
       if (j.n == 0) continue;
       const int part = j.out_idx & 1;
-      const BoxRef& rf = refs[(j.out_idx % (2 * nb)) / 2];
+      const int bi = (j.out_idx % (2 * nb)) / 2;
+      const BoxRef& rf = refs[bi];
       int est;
       if (fixed >= 0) est = fixed;
-      else if (t == 0) est = (std::min(j.m, j.n) + 1) / 2;
+      else if (!prop.empty()) {
+        const double r = std::exp2(8.0 * (double)prop[2 * bi + part]) - 1.0;
+        est = (int)std::ceil(h->prop_margin * std::max(0.0, std::min(r, 1e6))) + 2;
+      } else if (t == 0) est = (std::min(j.m, j.n) + 1) / 2;
       else est = (int)std::ceil(1.7 * std::max(8, h->probs[rf.p].lvl_max_rank[rf.l + 1][part]));
       const int sr = std::max(32, ((est + p_over + 15) / 16) * 16);
-      if (sr > 1024 || 5 * sr >= 4 * j.m) continue;
+      const int stot = sr + kHoldRows;  // rows for the ID, then held-out rows for its check
+      if (stot > 1024 || 5 * stot >= 4 * j.m) continue;
       SketchJob sj;
       sj.m_off = j.m_off; sj.m = j.m; sj.n = j.n; sj.ld = j.ld;
-      sj.mpad = sketch_mpad(j.m); sj.n2pad = sketch_n2pad(j.n); sj.s = sr;
-      sj.y_off = mr_total + y_total; sj.ldy = sr;
+      sj.mpad = sketch_mpad(j.m); sj.n2pad = sketch_n2pad(j.n); sj.s = stot;
+      sj.y_off = mr_total + y_total; sj.ldy = stot;
       sj.slice_off = slice_total; sj.exp_off = exp_total;
       sj.stream_id = ((long long)t << 32) + i;
       const int sji = (int)sk.size();
       for (int c = 0; c < j.n; ++c) skcw.push_back(SketchColWork{sji, c});
-      const int mtiles = (sr + 127) / 128;
+      const int mtiles = (stot + 127) / 128;
       for (int cb = 0; cb < sj.n2pad / 32; ++cb)
         for (int mt = 0; mt < mtiles; ++mt) sktiles.push_back(SketchTile{sji, cb, mt});
       sketch_work += 2.0 * 128.0 * mtiles * sj.mpad * 224.0 * (sj.n2pad / 32);
-      y_total += (long long)sr * j.n;
+      y_total += (long long)stot * j.n;
       slice_total += (long long)sketch_slice_bytes(sj.mpad, sj.n2pad);
       exp_total += 2LL * j.n;
       sk.push_back(sj);
       sk_rows[i] = sr;
-      j.m_off = sj.y_off; j.m = sr; j.ld = sr;
+      j.m_off = sj.y_off; j.m = sr; j.ld = stot;
     }
   }
   max_m = 1;
@@ -702,24 +746,130 @@ int compress_height(symhss_s* h, int t, cudaStream_t s) {
   TIMED(SYMHSS_K_ID, 0.0, launch_cpqr(ia, s));
   ia.tol = h->prm.tol;
   const size_t id_mark = h->marks.size() > id_before ? id_before : (size_t)-1;
+  // a-posteriori residual estimate of every sketched ID: its interpolation of the
+  // held-out sketch rows Omega_h M (Halko-Martinsson-Tropp, Sec. 4.3 of their survey:
+  // ||Omega_h e|| / sqrt(q) estimates ||e|| for Rademacher Omega_h with q rows)
+  std::vector<int> chk_of(njobs, -1);
+  std::vector<double> ratio;
+  if (!sketch_jobs.empty()) {
+    std::vector<CheckJob> cj;
+    for (int i = 0; i < njobs; ++i) {
+      if (sk_rows[i] == 0) continue;
+      CheckJob c;
+      c.m_off = jobs[i].m_off + sk_rows[i]; c.m = kHoldRows; c.n = jobs[i].n; c.ld = jobs[i].ld;
+      c.rank_idx = jobs[i].out_idx; c.t_off = jobs[i].t_off; c.perm_off = jobs[i].perm_off;
+      c.out = (int)cj.size(); c.pad_ = 0;
+      chk_of[i] = c.out;
+      cj.push_back(c);
+    }
+    Packer cp;
+    cp.add(cj);
+    CK(cp.upload(h->chkjobs, s));
+    CK(h->chkratio.ensure(cj.size() * sizeof(double)));
+    TIMED(SYMHSS_K_CHECK, 0.0, launch_id_check(H.mr.as<double2>(), H.tbuf.as<double2>(), H.permbuf.as<int>(),
+                                               H.rankbuf.as<int>(), h->chkjobs.as<CheckJob>(), (int)cj.size(),
+                                               h->chkratio.as<double>(), s));
+    ratio.resize(cj.size());
+    CK(cudaMemcpyAsync(ratio.data(), h->chkratio.p, cj.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  }
   std::vector<int> hr(njobs), hp(perm_total);
   CK(cudaMemcpyAsync(hr.data(), H.rankbuf.p, njobs * sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(hp.data(), H.permbuf.p, perm_total * sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  if (!prop.empty()) {
+    for (int i = 0; i < njobs; ++i) {
+      if (jobs[i].n == 0 || jobs[i].out_idx >= 2 * nb) continue;
+      const int bi = jobs[i].out_idx / 2, part = jobs[i].out_idx & 1;
+      const double r = std::exp2(8.0 * (double)prop[2 * bi + part]) - 1.0;
+      const int ri = hr[jobs[i].out_idx];
+      h->st.proposals += 1;
+      h->st.proposal_rank_err += std::fabs(r - ri) / std::max(1, ri);
+      if (r < ri) h->st.proposal_under += 1;
+    }
+  }
   if (id_mark < h->marks.size()) {
     double w = 0;
     for (const IdJob& j : jobs) w += id_flops(j.m, j.n, hr[j.out_idx]);
     h->marks[id_mark].work = w;
   }
-  // a sketch too thin for the rank it revealed: redo that ID on the full matrix
+  // A sketch too thin for the rank it revealed: redo that ID on the full matrix.  An ID
+  // whose held-out residual exceeds tol: continue its pivoted QR on the sketch at tol / 16
+  // (a few more skeleton columns) and check again; redo it on the full matrix only if it
+  // still fails.
   std::vector<IdJob> cur = jobs;
   {
     std::vector<IdJob> redo;
-    for (int i = 0; i < njobs; ++i)
-      if (sk_rows[i] > 0 && fixed < 0 && 2 * hr[i] >= 2 * sk_rows[i] - p_over) {
+    std::vector<int> cont;
+    auto thin = [&](int i) { return fixed < 0 && 2 * hr[i] >= 2 * sk_rows[i] - p_over; };
+    for (int i = 0; i < njobs; ++i) {
+      if (sk_rows[i] == 0) continue;
+      const double rt = chk_of[i] >= 0 ? ratio[chk_of[i]] : 0.0;
+      if (thin(i)) {
         redo.push_back(full[i]);
         cur[i] = full[i];
+      } else if (!(rt <= h->prm.tol)) {
+        h->st.check_failed += 1;
+        cont.push_back(i);
+      } else {
+        h->st.check_max_ratio = std::max(h->st.check_max_ratio, rt);
       }
+    }
+    if (!cont.empty()) {
+      std::vector<IdJob> cjobs;
+      std::vector<CheckJob> chk;
+      int mm = 1;
+      for (int i : cont) {
+        IdJob j = jobs[i];
+        j.start = hr[i];
+        cjobs.push_back(j);
+        mm = std::max(mm, j.m);
+        CheckJob c;
+        c.m_off = jobs[i].m_off + sk_rows[i]; c.m = kHoldRows; c.n = jobs[i].n; c.ld = jobs[i].ld;
+        c.rank_idx = jobs[i].out_idx; c.t_off = jobs[i].t_off; c.perm_off = jobs[i].perm_off;
+        c.out = (int)chk.size(); c.pad_ = 0;
+        chk.push_back(c);
+      }
+      Packer pc;
+      const size_t oj = pc.add(cjobs), oc = pc.add(chk);
+      CK(pc.upload(H.idjobs, s));
+      ia.jobs = reinterpret_cast<const IdJob*>(H.idjobs.as<char>() + oj);
+      ia.njobs = (int)cjobs.size();
+      ia.max_m = mm;
+      ia.tol = h->prm.tol / 16.0;
+      const size_t cb = h->marks.size();
+      TIMED(SYMHSS_K_ID, 0.0, launch_cpqr(ia, s));
+      ia.tol = h->prm.tol;
+      ia.max_m = max_m;
+      CK(h->chkratio.ensure(chk.size() * sizeof(double)));
+      TIMED(SYMHSS_K_CHECK, 0.0, launch_id_check(H.mr.as<double2>(), H.tbuf.as<double2>(), H.permbuf.as<int>(),
+                                                 H.rankbuf.as<int>(),
+                                                 reinterpret_cast<const CheckJob*>(H.idjobs.as<char>() + oc),
+                                                 (int)chk.size(), h->chkratio.as<double>(), s));
+      std::vector<double> r2(chk.size());
+      std::vector<int> before(cont.size());
+      for (size_t k = 0; k < cont.size(); ++k) before[k] = hr[cont[k]];
+      CK(cudaMemcpyAsync(r2.data(), h->chkratio.p, chk.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(hr.data(), H.rankbuf.p, njobs * sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(hp.data(), H.permbuf.p, perm_total * sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (h->marks.size() > cb) {
+        double w = 0;
+        for (size_t k = 0; k < cont.size(); ++k) {
+          const IdJob& j = jobs[cont[k]];
+          w += id_flops(j.m, j.n, hr[j.out_idx]) - id_flops(j.m, j.n, before[k]);
+        }
+        h->marks[cb].work = w;
+      }
+      for (size_t k = 0; k < cont.size(); ++k) {
+        const int i = cont[k];
+        if (thin(i) || !(r2[k] <= h->prm.tol)) {
+          redo.push_back(full[i]);
+          cur[i] = full[i];
+        } else {
+          h->st.check_max_ratio = std::max(h->st.check_max_ratio, r2[k]);
+        }
+      }
+    }
     h->st.sketch_redo += (long long)redo.size();
     if (!redo.empty()) {
       int mm = 1;
@@ -1298,6 +1448,11 @@ int symhss_compress(symhss_t h, void* stream) {
   h->st.id_count = 0;
   h->st.flops_id = 0;
   h->st.sketch_redo = 0;
+  h->st.check_failed = 0;
+  h->st.check_max_ratio = 0;
+  h->st.proposals = 0;
+  h->st.proposal_rank_err = 0;
+  h->st.proposal_under = 0;
   for (int c = 0; c < SYMHSS_K_COUNT; ++c) {
     h->st.kernel_ms[c] = 0;
     h->st.kernel_launches[c] = 0;
@@ -1319,6 +1474,7 @@ int symhss_compress(symhss_t h, void* stream) {
     float ms = 0;
     cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
     h->st.ms_compress = ms;
+    if (h->st.proposals > 0) h->st.proposal_rank_err /= (double)h->st.proposals;
   } catch (const std::bad_alloc&) {
     return SYMHSS_ERR_NOMEM;
   }
@@ -1589,7 +1745,8 @@ int symhss_solve_host(symhss_t h, const void* rhs_host, void* x_host, int nrhs, 
 int symhss_stats(symhss_t h, symhss_stats_t* out) {
   if (!h || !out) return SYMHSS_ERR_INVALID;
   long long bytes = (long long)h->pts.cap + (long long)h->status.cap + h->xin.cap + h->xout.cap + h->kps.cap +
-                    h->waves.cap;
+                    h->waves.cap + h->featjobs.cap + h->feats.cap + h->mlpout.cap + h->chkjobs.cap +
+                    h->chkratio.cap;
   for (auto& H : h->heights) {
     for (DevBuf* b : {&H.mr, &H.tbuf, &H.permbuf, &H.rankbuf, &H.refbuf, &H.clists, &H.idjobs, &H.slices,
                       &H.skmeta, &H.D, &H.piv, &H.rxpiv, &H.info, &H.X, &H.RX, &H.At, &H.qbuf, &H.flists,
@@ -1616,6 +1773,85 @@ int symhss_problem_ranks(symhss_t h, int problem, int level, int* out) {
 }
 
 int symhss_level_ranks(symhss_t h, int level, int* out) { return symhss_problem_ranks(h, 0, level, out); }
+
+int symhss_set_proposer(symhss_t h, symhss_mlp_t net, double margin) {
+  if (!h || !(margin >= 1.0) || !std::isfinite(margin)) return SYMHSS_ERR_INVALID;
+  h->mlp = net;
+  h->prop_margin = margin;
+  return SYMHSS_OK;
+}
+
+int symhss_training_data(symhss_t h, int* count, float* x, float* y_rank, float* y_skel, float* mask, int* meta,
+                         double* geo, void* stream) {
+  if (!h || !count) return SYMHSS_ERR_INVALID;
+  if (!h->compressed) return SYMHSS_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    std::vector<BoxRef> all, refs;
+    for (int t = 0; t < h->maxdepth; ++t) {
+      height_boxes(h, t, false, refs);
+      all.insert(all.end(), refs.begin(), refs.end());
+    }
+    const int total = (int)all.size();
+    const bool want = x || y_rank || y_skel || mask || meta || geo;
+    if (!want) {
+      *count = total;
+      return SYMHSS_OK;
+    }
+    if (*count < total) return SYMHSS_ERR_INVALID;
+    *count = total;
+    if (total == 0) return SYMHSS_OK;
+    std::vector<FeatJob> fj(total);
+    for (int i = 0; i < total; ++i) {
+      const BoxRef& rf = all[i];
+      const HBox& bx = *rf.bx;
+      const Problem& P = h->probs[rf.p];
+      const int t = P.depth - rf.l;
+      FeatJob f;
+      f.cx = bx.cx; f.cy = bx.cy; f.rho = bx.rho; f.k0 = P.prm.k0; f.k1 = P.prm.k1; f.tol = h->prm.tol;
+      f.begin = bx.begin; f.len = bx.end - bx.begin; f.height = t;
+      f.n0 = (int)bx.act[0].size(); f.n1 = (int)bx.act[1].size(); f.m_near = bx.m_near; f.nproxy = bx.P;
+      f.pad_ = 0;
+      fj[i] = f;
+      const int L = bx.end - bx.begin;
+      for (int hh = 0; hh < 2; ++hh) {
+        if (y_rank) y_rank[2 * i + hh] = (float)(std::log2(1.0 + bx.rank[hh]) / 8.0);
+        if (y_skel || mask) {
+          double cnt[32] = {}, hit[32] = {};
+          std::vector<char> sk(L, 0);
+          for (int j = 0; j < bx.rank[hh]; ++j) sk[bx.act[hh][bx.perm[hh][j]] - bx.begin] = 1;
+          for (int q : bx.act[hh]) {
+            const int j = (int)(((long long)(q - bx.begin) * 32) / L);
+            cnt[j] += 1;
+            hit[j] += sk[q - bx.begin];
+          }
+          for (int j = 0; j < 32; ++j) {
+            if (y_skel) y_skel[(size_t)64 * i + 32 * hh + j] = cnt[j] > 0 ? (float)(hit[j] / cnt[j]) : 0.0f;
+            if (mask) mask[(size_t)64 * i + 32 * hh + j] = cnt[j] > 0 ? 1.0f : 0.0f;
+          }
+        }
+      }
+      if (meta) {
+        int* mt = meta + (size_t)10 * i;
+        mt[0] = rf.p; mt[1] = rf.l; mt[2] = t; mt[3] = bx.begin - P.node0; mt[4] = L;
+        mt[5] = f.n0; mt[6] = f.n1; mt[7] = bx.m_near; mt[8] = bx.P; mt[9] = 0;
+      }
+      if (geo) { geo[3 * i] = bx.cx; geo[3 * i + 1] = bx.cy; geo[3 * i + 2] = bx.rho; }
+    }
+    if (x) {
+      Packer fp;
+      fp.add(fj);
+      CK(fp.upload(h->featjobs, s));
+      CK(h->feats.ensure((size_t)total * kMlpWidth * sizeof(float)));
+      CK(launch_box_features(table_of(h), h->featjobs.as<FeatJob>(), total, h->feats.as<float>(), s));
+      CK(cudaMemcpyAsync(x, h->feats.p, (size_t)total * kMlpWidth * sizeof(float), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+    }
+    return SYMHSS_OK;
+  } catch (const std::bad_alloc&) {
+    return SYMHSS_ERR_NOMEM;
+  }
+}
 
 int symhss_destroy(symhss_t h) {
   if (!h) return SYMHSS_OK;

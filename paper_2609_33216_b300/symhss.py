@@ -30,8 +30,10 @@ SYMHSS_FP64 = 0
 SYMHSS_HOST = 0
 SYMHSS_DEVICE = 1
 SYMHSS_MAX_LEVELS = 32
-K_TILES, K_ID, K_GETRF, K_GETRS, K_OTHER, K_SKETCH = 0, 1, 2, 3, 4, 5
-K_NAMES = ["tiles", "id", "getrf", "getrs", "other", "sketch"]
+K_TILES, K_ID, K_GETRF, K_GETRS, K_OTHER, K_SKETCH, K_CHECK, K_MLP = 0, 1, 2, 3, 4, 5, 6, 7
+K_NAMES = ["tiles", "id", "getrf", "getrs", "other", "sketch", "check", "mlp"]
+MLP_PARAMS = 49536
+MLP_WIDTH = 128
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int)
@@ -60,7 +62,9 @@ class symhss_stats_t(C.Structure):
                 ("ms_basis", C.c_double), ("pairs_evaluated", C.c_longlong), ("id_count", C.c_longlong),
                 ("flops_lu", C.c_double), ("flops_id", C.c_double), ("device_bytes", C.c_longlong),
                 ("kernel_ms", C.c_double * 8), ("kernel_launches", C.c_longlong * 8),
-                ("kernel_work", C.c_double * 8), ("sketch_redo", C.c_longlong)]
+                ("kernel_work", C.c_double * 8), ("sketch_redo", C.c_longlong),
+                ("check_failed", C.c_longlong), ("check_max_ratio", C.c_double), ("proposals", C.c_longlong),
+                ("proposal_rank_err", C.c_double), ("proposal_under", C.c_longlong)]
 
 
 class symhss_points(C.Structure):
@@ -88,6 +92,18 @@ _SIGNATURES = [
     ("symhss_level_ranks", C.c_int, [C.c_void_p, C.c_int, _ip]),
     ("symhss_problem_ranks", C.c_int, [C.c_void_p, C.c_int, C.c_int, _ip]),
     ("symhss_destroy", C.c_int, [C.c_void_p]),
+    ("symhss_mlp_create", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),
+    ("symhss_mlp_set_params", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("symhss_mlp_get_params", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("symhss_mlp_forward", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    ("symhss_mlp_loss_grad", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                       C.POINTER(C.c_double), C.c_void_p, C.c_void_p]),
+    ("symhss_mlp_train_step", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                        C.c_float, C.POINTER(C.c_double), C.c_void_p]),
+    ("symhss_mlp_destroy", C.c_int, [C.c_void_p]),
+    ("symhss_set_proposer", C.c_int, [C.c_void_p, C.c_void_p, C.c_double]),
+    ("symhss_training_data", C.c_int, [C.c_void_p, _ip, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.c_void_p, C.c_void_p]),
     ("symhss_launch_count", C.c_longlong, []),
     ("symhss_hankel01", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     ("symhss_kernel_block", C.c_int, [C.POINTER(symhss_params), C.POINTER(symhss_points), C.c_void_p,
@@ -275,3 +291,22 @@ def symhss_lu_solve_batched(lu: int, n: int, lda: int, stride_a: int, ipiv: int,
                             stride_b: int, batch: int, stream: int = 0) -> None:
     check(lib.symhss_lu_solve_batched(C.c_void_p(lu), n, lda, stride_a, C.c_void_p(ipiv), C.c_void_p(b), nrhs,
                                       ldb, stride_b, batch, C.c_void_p(stream)), "symhss_lu_solve_batched")
+
+
+def symhss_training_data(h, stream: int = 0):
+    """(x, y_rank, y_skel, mask, meta, geo) numpy arrays of the handle's last compression."""
+    import numpy as np
+    cnt = C.c_int(0)
+    check(lib.symhss_training_data(h, C.byref(cnt), None, None, None, None, None, None, C.c_void_p(stream)),
+          "symhss_training_data")
+    n = cnt.value
+    x = np.zeros((n, MLP_WIDTH), np.float32)
+    yr = np.zeros((n, 2), np.float32)
+    ys = np.zeros((n, 64), np.float32)
+    mk = np.zeros((n, 64), np.float32)
+    meta = np.zeros((n, 10), np.int32)
+    geo = np.zeros((n, 3), np.float64)
+    if n:
+        check(lib.symhss_training_data(h, C.byref(cnt), x.ctypes.data, yr.ctypes.data, ys.ctypes.data, mk.ctypes.data,
+                                       meta.ctypes.data, geo.ctypes.data, C.c_void_p(stream)), "symhss_training_data")
+    return x, yr, ys, mk, meta, geo
