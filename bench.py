@@ -238,6 +238,30 @@ def run_ours(args):
             s.close()
             torch.cuda.empty_cache()
 
+    # comparator: the symmetric PMCHWT system (first-order accurate) on the same solver
+    comparators = {}
+    if not batch and args.comparators:
+        pm = Solver(w["curve"], w["k0"], w["k1"], w["eps0"], w["eps1"], mode="sym", curve_on_device=True,
+                    formulation="pmchwt", **kw)
+        for _ in range(args.warmup):
+            step(pm)
+        barrier()
+        tms = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(pm)
+            e1.record(stream)
+            e1.synchronize()
+            tms.append(e0.elapsed_time(e1))
+        stp = pm.stats()
+        comparators["pmchwt_sym"] = {"ms_per_step": sum(tms) / len(tms), "max_rank": list(stp.max_rank),
+                                     "root_size": stp.root_size,
+                                     "accuracy": "first order in h (O(h^3) for the Muller-like system)"}
+        pm.close()
+
     xs = results["sym"]["x"]
     xb = results["base"]["x"]
     if batch:  # largest per-scatterer relative difference
@@ -310,6 +334,7 @@ def run_ours(args):
             "phases_ms": {"compress": st.ms_compress, "factor": st.ms_factor, "solve": st.ms_solve},
             "per_kernel": per_kernel,
             "proposer": prop_info,
+            "comparators": comparators or None,
             "id_checks": {"failed_then_continued": int(st.check_failed), "max_accepted_ratio": st.check_max_ratio,
                           "proposals": int(st.proposals), "proposal_rank_err": st.proposal_rank_err},
             "sketch": {"redone_ids": int(st.sketch_redo),
@@ -458,6 +483,7 @@ def main():
     ap.add_argument("--ref-sample-boxes", type=int, default=4)
     ap.add_argument("--profile", action="store_true", help="one warm-up + one symmetric step only")
     ap.add_argument("--proposer", action="store_true", help="train the learned rank proposer and attach it")
+    ap.add_argument("--comparators", type=int, default=1, help="also time the symmetric PMCHWT comparator")
     args = ap.parse_args()
     if args.profile:
         run_profile(args)

@@ -52,6 +52,9 @@ extern "C" {
 
 #define SYMHSS_FP64    0   /* every stage in FP64 */
 
+#define SYMHSS_MULLER  0   /* symmetric Muller-like system (Eq. 15): the method            */
+#define SYMHSS_PMCHWT  1   /* symmetric PMCHWT comparator (Eq. symmetric_pmchwt): first order */
+
 #define SYMHSS_HOST    0   /* pointer location flags */
 #define SYMHSS_DEVICE  1
 
@@ -87,7 +90,11 @@ typedef struct {
                            * under 0.8 m rows; an ID whose rank reaches s - p/2, or whose
                            * residual on the held-out rows exceeds tol, is redone on M;
                            * 0 disables the sketch */
-  int reserved;
+  int formulation;        /* SYMHSS_MULLER (0) or the SYMHSS_PMCHWT comparator: row-scaled
+                           * (SYMHSS_SYM) A = [-(e0 S0 + e1 S1), D0 + D1; D*0 + D*1,
+                           * -(N0/e0 + N1/e1)], rhs [-W u_in; (1/e0) W du_in/dnu]; its
+                           * hypersingular diagonal is one-point corrected (first order).
+                           * SYMHSS_NONSYM gives the unscaled PMCHWT with two IDs.       */
   uint64_t seed;          /* seed of the counter-based sketch generator               */
 } symhss_params;
 
@@ -187,7 +194,8 @@ int symhss_factor(symhss_t h, void* stream);
 
 /* Right-hand side of the handle's system for the plane wave
  * u_in = exp(i k0 (x cos(angle) + y sin(angle))): [-eps0 W u_in ; W du_in/dnu]
- * (Eq. 15; the unscaled form without W for SYMHSS_NONSYM).  rhs: device
+ * (Eq. 15; PMCHWT: [-W u_in ; (1/eps0) W du_in/dnu]; the unscaled forms without W for
+ * SYMHSS_NONSYM).  rhs: device
  * complex128[2n] (a batch: every problem's block with its own k0 and eps0). */
 int symhss_rhs_plane_wave(symhss_t h, double angle, void* rhs, void* stream);
 

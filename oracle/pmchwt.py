@@ -90,3 +90,14 @@ def pmchwt_rhs(curve, prm: Params, angle: float = 0.0, scaled: bool = True) -> n
 def pmchwt_solve(curve, prm: Params, angle: float = 0.0, scaled: bool = True) -> np.ndarray:
     """Dense LU solution [q; u] of the PMCHWT system."""
     return np.linalg.solve(pmchwt_matrix(curve, prm, scaled), pmchwt_rhs(curve, prm, angle, scaled))
+
+
+def pmchwt_entries(obs: Points, obs_eq, src: Points, src_comp, prm: Params, scaled: bool = True) -> np.ndarray:
+    """Dense block A[(p, e), (q, c)] of the PMCHWT system for (point, equation) rows and
+    (point, unknown) columns (e, c in {0, 1} as in kernels.entries)."""
+    obs_eq = np.asarray(obs_eq, dtype=np.int64)
+    src_comp = np.asarray(src_comp, dtype=np.int64)
+    blk = pmchwt_blocks(obs, src, prm, scaled)
+    e = obs_eq[:, None]
+    c = src_comp[None, :]
+    return np.where(e == 0, np.where(c == 0, blk[0], blk[1]), np.where(c == 0, blk[2], blk[3]))

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <cmath>
 #include <stdint.h>
 
 #include "../../include/symhss.h"
@@ -89,13 +90,40 @@ struct PointTable {
 };
 
 // Physical constants of one system.
+// Per-problem constants of the tile generator.  The blocks are combinations of the layer
+// kernels of the two wavenumbers:
+//   A11 = -w (cs0 S_k0 - cs1 S_k1)      A12 = w (cd0 D_k0 - cd1 D_k1) - ft
+//   A21 = w (cd0 D*_k0 - cd1 D*_k1) + ft  A22 = -w (cn0 N_k0 - cn1 N_k1)
+// Muller-like (Eq. 15): cs = (eps0^2, eps1^2), cd = (eps0, eps1), cn = (1, 1), ft = (eps0 + eps1)/2;
+// PMCHWT (Eq. symmetric_pmchwt): cs = (eps0, -eps1), cd = (1, -1), cn = (1/eps0, -1/eps1), ft = 0.
 struct KernelParams {
   double k0, k1, eps0, eps1;
-  double e0sq, e1sq;   // eps0^2, eps1^2
-  double half_ft;      // (eps0 + eps1) / 2
+  double cs0, cs1, cd0, cd1, cn0, cn1;
+  double half_ft;      // free term (eps0 + eps1) / 2, or 0
   double lhk0, lhk1;   // log(k0 / 2), log(k1 / 2)
   double ik0, ik1;     // 1 / k0, 1 / k1
+  int form;            // SYMHSS_MULLER or SYMHSS_PMCHWT
+  int pad_;
 };
+
+inline KernelParams make_kernel_params(const symhss_params& p) {
+  KernelParams k;
+  k.k0 = p.k0; k.k1 = p.k1; k.eps0 = p.eps0; k.eps1 = p.eps1;
+  k.form = p.formulation;
+  k.pad_ = 0;
+  if (p.formulation == SYMHSS_PMCHWT) {
+    k.cs0 = p.eps0; k.cs1 = -p.eps1; k.cd0 = 1.0; k.cd1 = -1.0; k.cn0 = 1.0 / p.eps0; k.cn1 = -1.0 / p.eps1;
+    k.half_ft = 0.0;
+  } else {
+    k.cs0 = p.eps0 * p.eps0; k.cs1 = p.eps1 * p.eps1; k.cd0 = p.eps0; k.cd1 = p.eps1; k.cn0 = 1.0; k.cn1 = 1.0;
+    k.half_ft = 0.5 * (p.eps0 + p.eps1);
+  }
+  k.lhk0 = std::log(0.5 * p.k0);
+  k.lhk1 = std::log(0.5 * p.k1);
+  k.ik0 = 1.0 / p.k0;
+  k.ik1 = 1.0 / p.k1;
+  return k;
+}
 
 // A tile: "thread points" (one per thread) x "loop points" (staged in shared
 // memory).  Each point carries two output slots (-1 = absent): for observation
@@ -329,7 +357,8 @@ cudaError_t launch_leaf_scatter(const double2* g, double2* x, long long ldx, con
 
 // Plane-wave right-hand side of problem jobs[j]: nodes [node0, node0 + n) of the
 // point table, rows [vec0, vec0 + 2n) of rhs ([eq1; eq2]).
-struct WaveJob { int node0, n; long long vec0; double k0, eps0; };
+// rhs rows: [cu W u_in ; cq W du_in/dnu] (W omitted for the unscaled systems)
+struct WaveJob { int node0, n; long long vec0; double k0, cu, cq; };
 cudaError_t launch_plane_wave(const PointTable& t, const WaveJob* jobs, int njobs, int max_n, double angle,
                               int scaled, double2* rhs, cudaStream_t s);
 

@@ -66,6 +66,8 @@ int symhss_kernel_block(const symhss_params* prm, const symhss_points* obs, cons
   if (!prm || !points_ok(obs) || !points_ok(src) || !out) return SYMHSS_ERR_INVALID;
   if (!(prm->k0 > 0) || !(prm->k1 > 0) || !std::isfinite(prm->eps0) || !std::isfinite(prm->eps1))
     return SYMHSS_ERR_INVALID;
+  if (!(prm->eps0 != 0.0) || !(prm->eps1 != 0.0)) return SYMHSS_ERR_INVALID;
+  if (prm->formulation != SYMHSS_MULLER && prm->formulation != SYMHSS_PMCHWT) return SYMHSS_ERR_INVALID;
   if (ld < obs->n || ld < 1) return SYMHSS_ERR_INVALID;
   if ((obs->n > 0 && !obs_eq) || (src->n > 0 && !src_comp)) return SYMHSS_ERR_INVALID;
   if (obs->n == 0 || src->n == 0) return SYMHSS_OK;
@@ -108,14 +110,7 @@ int symhss_kernel_block(const symhss_params* prm, const symhss_points* obs, cons
   const size_t o7 = put(&jb, sizeof(jb));
   const size_t o8 = put(ch.data(), ch.size() * sizeof(TileChunk));
   off = (off + 15) & ~size_t(15);
-  KernelParams kp;
-  kp.k0 = prm->k0; kp.k1 = prm->k1; kp.eps0 = prm->eps0; kp.eps1 = prm->eps1;
-  kp.e0sq = prm->eps0 * prm->eps0; kp.e1sq = prm->eps1 * prm->eps1;
-  kp.half_ft = 0.5 * (prm->eps0 + prm->eps1);
-  kp.lhk0 = std::log(0.5 * prm->k0);
-  kp.lhk1 = std::log(0.5 * prm->k1);
-  kp.ik0 = 1.0 / prm->k0;
-  kp.ik1 = 1.0 / prm->k1;
+  const KernelParams kp = make_kernel_params(*prm);
   const size_t o10 = put(&kp, sizeof(kp));
   const size_t o9 = off;
   CKE(cudaMemcpyAsync(buf.p, hp, bytes, cudaMemcpyHostToDevice, s));

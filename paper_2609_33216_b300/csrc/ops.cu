@@ -139,8 +139,8 @@ __global__ void plane_wave_kernel(const PointTable t, const WaveJob* jobs, doubl
   const double2 dudn = make_double2(-dn * sn, dn * cs);  // i k0 (nu.dir) u_in
   const double sc = scaled ? t.w[i] : 1.0;
   double2* r = rhs + jb.vec0;
-  r[j] = make_double2(-jb.eps0 * sc * uin.x, -jb.eps0 * sc * uin.y);
-  r[jb.n + j] = make_double2(sc * dudn.x, sc * dudn.y);
+  r[j] = make_double2(jb.cu * sc * uin.x, jb.cu * sc * uin.y);
+  r[jb.n + j] = make_double2(jb.cq * sc * dudn.x, jb.cq * sc * dudn.y);
 }
 
 }  // namespace

@@ -245,17 +245,7 @@ PointTable table_of(const symhss_s* h) {
   return t;
 }
 
-KernelParams kparams(const symhss_params& p) {
-  KernelParams k;
-  k.k0 = p.k0; k.k1 = p.k1; k.eps0 = p.eps0; k.eps1 = p.eps1;
-  k.e0sq = p.eps0 * p.eps0; k.e1sq = p.eps1 * p.eps1;
-  k.half_ft = 0.5 * (p.eps0 + p.eps1);
-  k.lhk0 = std::log(0.5 * p.k0);
-  k.lhk1 = std::log(0.5 * p.k1);
-  k.ik0 = 1.0 / p.k0;
-  k.ik1 = 1.0 / p.k1;
-  return k;
-}
+KernelParams kparams(const symhss_params& p) { return make_kernel_params(p); }
 
 int proxy_count(const symhss_params& p, double radius) {
   const double kmax = std::max(p.k0, p.k1);
@@ -379,7 +369,8 @@ int build_geometry(symhss_s* h, cudaStream_t s) {
   std::vector<WaveJob> wv;
   for (const Problem& P : h->probs) {
     kp.push_back(kparams(P.prm));
-    wv.push_back(WaveJob{P.node0, P.n, P.vec0, P.prm.k0, P.prm.eps0});
+    const bool pm = P.prm.formulation == SYMHSS_PMCHWT;
+    wv.push_back(WaveJob{P.node0, P.n, P.vec0, P.prm.k0, pm ? -1.0 : -P.prm.eps0, pm ? 1.0 / P.prm.eps0 : 1.0});
   }
   CK(h->kps.ensure(kp.size() * sizeof(KernelParams)));
   CK(cudaMemcpyAsync(h->kps.p, kp.data(), kp.size() * sizeof(KernelParams), cudaMemcpyHostToDevice, s));
@@ -1267,6 +1258,7 @@ int validate_params(const symhss_params* p) {
   if (p->precision != SYMHSS_FP64) return SYMHSS_ERR_INVALID;
   if (p->fixed_rank_kL < 0 || (p->fixed_rank_kL > 0 && !(p->rank_scale_a >= 1.0))) return SYMHSS_ERR_INVALID;
   if (p->oversample < 0) return SYMHSS_ERR_INVALID;
+  if (p->formulation != SYMHSS_MULLER && p->formulation != SYMHSS_PMCHWT) return SYMHSS_ERR_INVALID;
   return SYMHSS_OK;
 }
 
@@ -1274,7 +1266,8 @@ int validate_params(const symhss_params* p) {
 bool same_shared(const symhss_params& a, const symhss_params& b) {
   return a.tol == b.tol && a.leaf == b.leaf && a.nproxy == b.nproxy && a.proxy_factor == b.proxy_factor &&
          a.mode == b.mode && a.precision == b.precision && a.fixed_rank_kL == b.fixed_rank_kL &&
-         a.rank_scale_a == b.rank_scale_a && a.oversample == b.oversample && a.seed == b.seed;
+         a.rank_scale_a == b.rank_scale_a && a.oversample == b.oversample && a.seed == b.seed &&
+         a.formulation == b.formulation;
 }
 
 // Copy the curves (host or device arrays) into the concatenated host node arrays.

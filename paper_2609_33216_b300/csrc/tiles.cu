@@ -1,5 +1,6 @@
 // Kernel-entry tile generator: blocks of the symmetric Muller-like matrix
-// (Eq. 15; unscaled baseline of Sec. 6) between two point lists.
+// (Eq. 15; unscaled baseline of Sec. 6), or of the PMCHWT comparator (Eq.
+// symmetric_pmchwt), between two point lists.
 //
 // Each thread owns one point of the "thread" list; a chunk of the "loop" list is
 // staged in shared memory.  For every (thread point, loop point) pair the thread
@@ -23,6 +24,9 @@
 //   D~ = D*~ = -kappa / (4 pi)
 //   (N_k0 - N_k1)~ = (i/8)(k0^2 - k1^2) - [k0^2 (log(k0/2) + gamma_E) - k1^2 (log(k1/2) + gamma_E)] / (4 pi)
 //                    + (k0^2 - k1^2) / (8 pi) - (k0^2 - k1^2) log(w / 2 pi) / (4 pi)
+//   PMCHWT: N~_k = -pi / (6 w^2) + kappa^2 / (24 pi) + (the k-dependent terms above for one k):
+//   the zeta-corrected trapezoidal weight of the 1/tau^2 singularity, -2 zeta(2)/h, on the
+//   Laplace part 1/(2 pi |gamma'| tau^2) in the parameter tau, plus its constant on a circle.
 // H_0 and H_1 come from hankel01() (hankel.cuh), accurate to about 1e-15 at every
 // argument.
 #include "common.cuh"
@@ -79,14 +83,28 @@ __device__ __forceinline__ void pair_block(const P7& o, const P7& s, const Kerne
     const double c = 1.0 / (2.0 * kPi);
     const double2 gs0 = make_double2(-c * (kEulerGamma + log(kp.k0 * w / (4.0 * kPi))), 0.25);
     const double2 gs1 = make_double2(-c * (kEulerGamma + log(kp.k1 * w / (4.0 * kPi))), 0.25);
-    const double2 ks = combo(kp.e0sq, gs0, kp.e1sq, gs1);
+    const double2 ks = combo(kp.cs0, gs0, kp.cs1, gs1);
     const double dd = -o.kappa / (4.0 * kPi);
-    const double kd = kp.eps0 * dd - kp.eps1 * dd;
-    const double dk2 = kp.k0 * kp.k0 - kp.k1 * kp.k1;
-    const double nre = -(kp.k0 * kp.k0 * (log(kp.k0 * 0.5) + kEulerGamma) -
-                         kp.k1 * kp.k1 * (log(kp.k1 * 0.5) + kEulerGamma)) / (4.0 * kPi) +
-                       dk2 / (8.0 * kPi) - dk2 / (4.0 * kPi) * log(w / (2.0 * kPi));
-    const double2 kn = make_double2(nre, 0.125 * dk2);
+    const double kd = kp.cd0 * dd - kp.cd1 * dd;
+    // k-dependent part of N~_k: (i/8) k^2 - k^2 (log(k/2) + gamma_E)/(4 pi) + k^2/(8 pi)
+    //                           - k^2 log(w / 2 pi)/(4 pi)
+    const double lw = log(w / (2.0 * kPi));
+    const double k0s = kp.k0 * kp.k0, k1s = kp.k1 * kp.k1;
+    const double f0 = -k0s * (kp.lhk0 + kEulerGamma) / (4.0 * kPi) + k0s / (8.0 * kPi) - k0s / (4.0 * kPi) * lw;
+    const double f1 = -k1s * (kp.lhk1 + kEulerGamma) / (4.0 * kPi) + k1s / (8.0 * kPi) - k1s / (4.0 * kPi) * lw;
+    double2 kn;
+    if (kp.form == SYMHSS_PMCHWT) {
+      // hypersingular part: -pi / (6 w^2) (zeta-corrected 1/tau^2) + kappa^2 / (24 pi)
+      const double hyp = -kPi / (6.0 * w * w) + o.kappa * o.kappa / (24.0 * kPi);
+      kn = make_double2(kp.cn0 * (hyp + f0) - kp.cn1 * (hyp + f1), 0.125 * (kp.cn0 * k0s - kp.cn1 * k1s));
+    } else {
+      // the hypersingular parts cancel in N_k0 - N_k1
+      const double dk2 = k0s - k1s;
+      const double nre = -(k0s * (kp.lhk0 + kEulerGamma) - k1s * (kp.lhk1 + kEulerGamma)) / (4.0 * kPi) +
+                         dk2 / (8.0 * kPi) - dk2 / (4.0 * kPi) * lw;
+      kn = make_double2(nre, 0.125 * dk2);
+      (void)f0; (void)f1;
+    }
     const double ft = kp.half_ft * (unscaled ? 1.0 : w);
     out[0] = make_double2(-wgt * ks.x, -wgt * ks.y);
     out[1] = make_double2(wgt * kd - ft, 0.0);
@@ -107,10 +125,10 @@ __device__ __forceinline__ void pair_block(const P7& o, const P7& s, const Kerne
   const double nn_r = __dmul_rn(nn, inv_r), ab_r = __dmul_rn(__dmul_rn(a, b), inv_r);
   const LayerVals l0 = layer(kp.k0, r, inv_r, lr, kp.lhk0, kp.ik0, a_r, b_r, nn_r, ab_r);
   const LayerVals l1 = layer(kp.k1, r, inv_r, lr, kp.lhk1, kp.ik1, a_r, b_r, nn_r, ab_r);
-  const double2 ks = combo(kp.e0sq, l0.g, kp.e1sq, l1.g);
-  const double2 kd = combo(kp.eps0, l0.d, kp.eps1, l1.d);
-  const double2 kds = combo(kp.eps0, l0.ds, kp.eps1, l1.ds);
-  const double2 kn = make_double2(__dsub_rn(l0.n.x, l1.n.x), __dsub_rn(l0.n.y, l1.n.y));
+  const double2 ks = combo(kp.cs0, l0.g, kp.cs1, l1.g);
+  const double2 kd = combo(kp.cd0, l0.d, kp.cd1, l1.d);
+  const double2 kds = combo(kp.cd0, l0.ds, kp.cd1, l1.ds);
+  const double2 kn = combo(kp.cn0, l0.n, kp.cn1, l1.n);
   const double2 t11 = rscale(wgt, ks), t22 = rscale(wgt, kn);
   out[0] = make_double2(-t11.x, -t11.y);
   out[1] = rscale(wgt, kd);

@@ -22,12 +22,13 @@ class Solver:
     """One scatterer: ``compress()``, ``factor()``, ``solve(rhs)`` on cuda:0."""
 
     def __init__(self, curve, k0: float, k1: float, eps0: float = 1.0, eps1: Optional[float] = None,
-                 mode: str = "sym", curve_on_device: bool = False, **params):
+                 mode: str = "sym", curve_on_device: bool = False, formulation: str = "muller", **params):
         if eps1 is None:
             eps1 = eps0 * (k1 / k0) ** 2
         self.n = int(curve.n)
         self.mode = S.SYMHSS_SYM if mode == "sym" else S.SYMHSS_NONSYM
-        self.prm = S.params(k0, k1, eps0, eps1, mode=self.mode, **params)
+        form = S.SYMHSS_PMCHWT if formulation == "pmchwt" else S.SYMHSS_MULLER
+        self.prm = S.params(k0, k1, eps0, eps1, mode=self.mode, formulation=form, **params)
         self._keep = []
         cs = self._curve_struct(curve, curve_on_device)
         self.h = S.symhss_create(cs, self.prm, _stream())

@@ -27,6 +27,8 @@ SYMHSS_ERR_DEVICE = -8
 SYMHSS_SYM = 0
 SYMHSS_NONSYM = 1
 SYMHSS_FP64 = 0
+SYMHSS_MULLER = 0
+SYMHSS_PMCHWT = 1
 SYMHSS_HOST = 0
 SYMHSS_DEVICE = 1
 SYMHSS_MAX_LEVELS = 32
@@ -48,7 +50,7 @@ class symhss_params(C.Structure):
     _fields_ = [("k0", C.c_double), ("k1", C.c_double), ("eps0", C.c_double), ("eps1", C.c_double),
                 ("tol", C.c_double), ("leaf", C.c_int), ("nproxy", C.c_int), ("proxy_factor", C.c_double),
                 ("mode", C.c_int), ("precision", C.c_int), ("fixed_rank_kL", C.c_int),
-                ("rank_scale_a", C.c_double), ("oversample", C.c_int), ("reserved", C.c_int),
+                ("rank_scale_a", C.c_double), ("oversample", C.c_int), ("formulation", C.c_int),
                 ("seed", C.c_uint64)]
 
 
