@@ -227,6 +227,27 @@ long long symhss_launch_count(void);
 /* Static message for a status code. */
 const char* symhss_strerror(int status);
 
+/* ---- launch tuning and the autotuner -------------------------------------------------
+ * Launch-shape choices that do not change any result bit (except tile_loop_chunk and
+ * id_cluster_max, which change nothing either: the same arithmetic runs in other blocks). */
+typedef struct {
+  int lu_lookahead;       /* 1: next LU panel on a high-priority stream during the trailing update */
+  int lu_panel_threads;   /* 256, 512 or 1024: largest thread block of the LU panel kernel      */
+  int tile_loop_chunk;    /* 0: adaptive (8..32 by launch size); else 8, 16 or 32 loop points per block */
+  int id_cluster_max;     /* 1, 2, 4, 8 or 16: largest thread-block cluster of one column ID      */
+  int reserved[4];
+} symhss_tuning;
+
+int symhss_get_tuning(symhss_t h, symhss_tuning* out);
+/* Set the handle's launch tuning (values outside the lists above: SYMHSS_ERR_INVALID). */
+int symhss_set_tuning(symhss_t h, const symhss_tuning* t);
+/* Autotuner: time the handle's own compress / factor with each value of each tunable
+ * (coordinate search: tile_loop_chunk and id_cluster_max on compress, then
+ * lu_panel_threads x lu_lookahead on factor), `reps` runs per value, the minimum device
+ * time of the affected kernel class deciding; leaves the best tuning set (and in *out,
+ * if not NULL) and the handle compressed and factorised.  Synchronises `stream`. */
+int symhss_autotune(symhss_t h, int reps, symhss_tuning* out, void* stream);
+
 /* ---- learned rank / skeleton proposer (an addition to the paper's method) --------------
  * A 3-layer MLP (128 inputs, two hidden layers of 128 with ReLU, 128 outputs of which
  * 66 are used), FP16 weights with FP32 accumulation; FP32 master weights and Adam state

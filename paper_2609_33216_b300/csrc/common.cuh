@@ -175,6 +175,7 @@ struct IdJob {
 };
 
 struct IdLaunch {
+  int cluster_max = 16;  // largest cluster per ID
   double2* mats;
   double2* tbuf;
   int* perm;
@@ -187,6 +188,7 @@ struct IdLaunch {
   int max_m, max_n;
 };
 cudaError_t launch_cpqr(const IdLaunch& a, cudaStream_t s);
+int cpqr_cluster_size(int njobs, int max_n);
 
 // Interpolation residual of an ID on a set of rows (the check that accepts a sketched ID,
 // run on held-out sketch rows): ratio[out] = max over non-skeleton columns c of
@@ -271,6 +273,8 @@ struct LuLaunch {
   int njobs;
   int max_n;
   int* status;
+  int lookahead = 1;       // depth-1 look-ahead on a side stream
+  int panel_threads = 1024;  // largest panel block
 };
 cudaError_t launch_getrf(const LuLaunch& a, cudaStream_t s);
 

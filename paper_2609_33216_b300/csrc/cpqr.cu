@@ -236,6 +236,7 @@ cudaError_t launch_cpqr(const IdLaunch& a, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(cpqr_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int c = cpqr_cluster_size(a.njobs, a.max_n);
+  while (c > 1 && c > a.cluster_max) c /= 2;
   if (c > 8) {
     if (cudaFuncSetAttribute(cpqr_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
       cudaGetLastError();

@@ -11,6 +11,8 @@
 //   3. trailing update: A22 -= L21 U12 in 32 x 32 tiles, one block per tile.
 // The pivots follow the LAPACK convention (row ipiv[k] was swapped with row k at
 // step k), so the result is interchangeable with the unblocked factorisation.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace symhss {
@@ -88,10 +90,13 @@ __global__ void __launch_bounds__(kPanelThreads) panel_kernel(const LuLaunch a, 
 
 // Panel factorisation with the panel (rows [j, n) x w columns) staged in shared
 // memory; the pivot search of column c + 1 is fused into the update of column c.
-__global__ void __launch_bounds__(kPanelThreads) panel_smem_kernel(const LuLaunch a, int j) {
+// THREADS is chosen per launch so that each thread holds about one or two panel rows.
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) panel_smem_kernel(const LuLaunch a, int j) {
+  constexpr int kWarps = THREADS / 32;
   extern __shared__ __align__(16) double2 P[];  // column-major: P[q * rows + i]
-  __shared__ double red[kPanelWarps];
-  __shared__ int redi[kPanelWarps];
+  __shared__ double red[kWarps];
+  __shared__ int redi[kWarps];
   __shared__ int s_piv;
   __shared__ double s_pv;
   const LuJob jb = a.jobs[blockIdx.x];
@@ -101,14 +106,14 @@ __global__ void __launch_bounds__(kPanelThreads) panel_smem_kernel(const LuLaunc
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   double2* A = a.base + jb.a_off;
   int* piv = a.piv + jb.piv_off;
-  for (int e = tid; e < rows * w; e += kPanelThreads) {
+  for (int e = tid; e < rows * w; e += THREADS) {
     const int i = e % rows, q = e / rows;
     P[q * rows + i] = A[j + i + (long long)(j + q) * ld];
   }
   __syncthreads();
   double bv = -1.0;
   int bi = rows;
-  for (int i = tid; i < rows; i += kPanelThreads) {
+  for (int i = tid; i < rows; i += THREADS) {
     const double v = cabs1(P[i]);
     if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
   }
@@ -117,8 +122,8 @@ __global__ void __launch_bounds__(kPanelThreads) panel_smem_kernel(const LuLaunc
     if (lane == 0) { red[warp] = bv; redi[warp] = bi; }
     __syncthreads();
     if (warp == 0) {
-      bv = lane < kPanelWarps ? red[lane] : -1.0;
-      bi = lane < kPanelWarps ? redi[lane] : rows;
+      bv = lane < kWarps ? red[lane] : -1.0;
+      bi = lane < kWarps ? redi[lane] : rows;
       warp_argmax(bv, bi);
       if (lane == 0) { s_piv = bi; s_pv = bv; }
     }
@@ -141,7 +146,7 @@ __global__ void __launch_bounds__(kPanelThreads) panel_smem_kernel(const LuLaunc
     const double2 inv = zero ? make_double2(0.0, 0.0) : cinv(P[c * rows + c]);
     bv = -1.0;
     bi = rows;
-    for (int i = c + 1 + tid; i < rows; i += kPanelThreads) {
+    for (int i = c + 1 + tid; i < rows; i += THREADS) {
       if (!zero) {
         const double2 l = cmul(P[c * rows + i], inv);
         P[c * rows + i] = l;
@@ -154,7 +159,7 @@ __global__ void __launch_bounds__(kPanelThreads) panel_smem_kernel(const LuLaunc
     }
     __syncthreads();
   }
-  for (int e = tid; e < rows * w; e += kPanelThreads) {
+  for (int e = tid; e < rows * w; e += THREADS) {
     const int i = e % rows, q = e / rows;
     A[j + i + (long long)(j + q) * ld] = P[q * rows + i];
   }
@@ -226,23 +231,25 @@ __global__ void __launch_bounds__(256) swap_trsm_warp_kernel(const LuLaunch a, i
   if (lane < w) cc[j + lane] = x;
 }
 
-// A22 -= L21 U12 for the tile (blockIdx.y, blockIdx.z) of every matrix
-__global__ void __launch_bounds__(256) update_kernel(const LuLaunch a, int j) {
+// A22 -= L21 U12 for the tile (blockIdx.y, blockIdx.z) of every matrix, over the trailing
+// columns [j + w + cskip, j + w + cskip + clen) (clen < 0: to the last column)
+__global__ void __launch_bounds__(256) update_kernel(const LuLaunch a, int j, int cskip, int clen) {
   __shared__ double2 at[kNb][kTs];      // L21 tile, transposed: at[c][r]
   __shared__ double2 bt[kNb][kTs];      // U12 tile: bt[c][col]
   const LuJob jb = a.jobs[blockIdx.x];
   const int n = jb.n, ld = jb.ld;
   const int w = min(kNb, n - j);
   const int s = j + w;                   // first trailing row / column
-  const int r0 = s + blockIdx.y * kTs, c0 = s + blockIdx.z * kTs;
-  if (j >= n || r0 >= n || c0 >= n) return;
+  const int r0 = s + blockIdx.y * kTs, c0 = s + cskip + blockIdx.z * kTs;
+  const int cend = clen < 0 ? n : min(n, s + cskip + clen);
+  if (j >= n || r0 >= n || c0 >= cend) return;
   double2* A = a.base + jb.a_off;
   const int tid = threadIdx.x;
   for (int e = tid; e < kNb * kTs; e += 256) {
     const int r = e % kTs, c = e / kTs;
     at[c][r] = (r0 + r < n && c < w) ? A[r0 + r + (long long)(j + c) * ld] : make_double2(0.0, 0.0);
     const int cc = e % kNb, col = e / kNb;
-    bt[cc][col] = (c0 + col < n && cc < w) ? A[j + cc + (long long)(c0 + col) * ld] : make_double2(0.0, 0.0);
+    bt[cc][col] = (c0 + col < cend && cc < w) ? A[j + cc + (long long)(c0 + col) * ld] : make_double2(0.0, 0.0);
   }
   __syncthreads();
   const int tx = tid & 31, ty = tid >> 5;  // row tx, columns ty + 8q
@@ -251,7 +258,7 @@ __global__ void __launch_bounds__(256) update_kernel(const LuLaunch a, int j) {
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int col = c0 + ty + 8 * q;
-    acc[q] = (row < n && col < n) ? A[row + (long long)col * ld] : make_double2(0.0, 0.0);
+    acc[q] = (row < n && col < cend) ? A[row + (long long)col * ld] : make_double2(0.0, 0.0);
   }
 #pragma unroll
   for (int c = 0; c < kNb; ++c) {
@@ -262,13 +269,46 @@ __global__ void __launch_bounds__(256) update_kernel(const LuLaunch a, int j) {
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int col = c0 + ty + 8 * q;
-    if (row < n && col < n) A[row + (long long)col * ld] = acc[q];
+    if (row < n && col < cend) A[row + (long long)col * ld] = acc[q];
   }
 }
 
 __global__ void zero_info_kernel(int* info, const LuJob* jobs, int njobs) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b < njobs) info[jobs[b].info_idx] = 0;
+}
+
+// Side stream (highest priority) and two events for the look-ahead, one set per host
+// thread and device, created on first use; nullptr if they cannot be created (the
+// factorisation then runs without look-ahead on the caller's stream).
+struct LookAhead {
+  cudaStream_t side = nullptr;
+  cudaEvent_t ready = nullptr, done = nullptr;
+  bool failed = false;
+};
+
+LookAhead* look_ahead_streams() {
+  constexpr int kMaxDev = 64;
+  thread_local LookAhead per_dev[kMaxDev];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  LookAhead& la = per_dev[dev];
+  if (la.failed) return nullptr;
+  if (!la.side) {
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (cudaStreamCreateWithPriority(&la.side, cudaStreamNonBlocking, hi) != cudaSuccess ||
+        cudaEventCreateWithFlags(&la.ready, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&la.done, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      la.failed = true;
+      return nullptr;
+    }
+  }
+  return &la;
 }
 
 }  // namespace
@@ -282,25 +322,62 @@ cudaError_t launch_getrf(const LuLaunch& a, cudaStream_t s) {
   // panels of up to 780 rows fit in shared memory (780 x 16 x 16 B = 195 KB)
   const size_t panel_smem = (size_t)a.max_n * kNb * sizeof(double2);
   const bool smem_panel = panel_smem <= 200 * 1024;
+  const int pcap = a.panel_threads >= 1024 ? 1024 : (a.panel_threads >= 512 ? 512 : 256);
+  const int pthreads = std::min(pcap, a.max_n > 512 ? 1024 : (a.max_n > 256 ? 512 : 256));
   if (smem_panel) {
-    e = cudaFuncSetAttribute(panel_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem);
+    // every variant the loop may pick as the panel shrinks
+    e = cudaFuncSetAttribute(panel_smem_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem);
+    if (e == cudaSuccess && pthreads >= 512)
+      e = cudaFuncSetAttribute(panel_smem_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem);
+    if (e == cudaSuccess && pthreads >= 1024)
+      e = cudaFuncSetAttribute(panel_smem_kernel<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem);
     if (e != cudaSuccess) return e;
   }
   const int ncolblk = (a.max_n + 7) / 8;
-  for (int j = 0; j < a.max_n; j += kNb) {
-    if (smem_panel) panel_smem_kernel<<<a.njobs, kPanelThreads, panel_smem, s>>>(a, j);
-    else panel_kernel<<<a.njobs, kPanelThreads, 0, s>>>(a, j);
+  // Depth-1 look-ahead: after the interchanges and TRSM of panel j, the first trailing
+  // tile column (which holds panel j + kNb) is updated first; panel j + kNb then runs on
+  // a high-priority side stream while the rest of the trailing update runs on s.  The two
+  // touch disjoint columns; s waits for the panel before the next interchanges.
+  LookAhead* la = a.lookahead ? look_ahead_streams() : nullptr;
+  auto panel = [&](int jj, cudaStream_t st) {
+    if (smem_panel) {
+      // the panel height shrinks with jj: fewer threads once the remaining rows allow it
+      const int rows = a.max_n - jj;
+      if (pthreads >= 1024 && rows > 512) panel_smem_kernel<1024><<<a.njobs, 1024, panel_smem, st>>>(a, jj);
+      else if (pthreads >= 512 && rows > 256) panel_smem_kernel<512><<<a.njobs, 512, panel_smem, st>>>(a, jj);
+      else panel_smem_kernel<256><<<a.njobs, 256, panel_smem, st>>>(a, jj);
+    } else {
+      panel_kernel<<<a.njobs, kPanelThreads, 0, st>>>(a, jj);
+    }
     symhss::count_launches(1);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return cudaGetLastError();
+  };
+  if ((e = panel(0, s)) != cudaSuccess) return e;
+  for (int j = 0; j < a.max_n; j += kNb) {
     const int rest = a.max_n - j - kNb;
     if (rest <= 0) continue;
     swap_trsm_warp_kernel<<<dim3(a.njobs, ncolblk), 256, 0, s>>>(a, j);
     symhss::count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const int tiles = (rest + kTs - 1) / kTs;
-    update_kernel<<<dim3(a.njobs, tiles, tiles), 256, 0, s>>>(a, j);
+    const int rtiles = (rest + kTs - 1) / kTs;
+    const bool split = la != nullptr && rest > kTs;
+    // first trailing tile column (all of it when not splitting)
+    update_kernel<<<dim3(a.njobs, rtiles, split ? 1 : rtiles), 256, 0, s>>>(a, j, 0, split ? kTs : -1);
     symhss::count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (!split) {
+      if ((e = panel(j + kNb, s)) != cudaSuccess) return e;
+      continue;
+    }
+    if ((e = cudaEventRecord(la->ready, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(la->side, la->ready, 0)) != cudaSuccess) return e;
+    if ((e = panel(j + kNb, la->side)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(la->done, la->side)) != cudaSuccess) return e;
+    const int ctiles = (rest - kTs + kTs - 1) / kTs;
+    update_kernel<<<dim3(a.njobs, rtiles, ctiles), 256, 0, s>>>(a, j, kTs, -1);
+    symhss::count_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(s, la->done, 0)) != cudaSuccess) return e;
   }
   // the last panel's interchanges still have to reach the columns left of it
   const int jlast = ((a.max_n - 1) / kNb) * kNb;

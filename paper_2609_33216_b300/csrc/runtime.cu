@@ -25,6 +25,7 @@
 // unknowns and proxy sources) and row-IDs each half; per half both ranks are
 // raised to their maximum so that R D^{-1} L is square.
 #include <algorithm>
+#include <initializer_list>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -162,6 +163,7 @@ struct symhss_s {
   symhss_stats_t st{};
   cudaError_t last_cuda = cudaSuccess;
   std::vector<int> mark;                          // host scratch (size npts)
+  symhss_tuning tune = {0, 1024, 0, 16, {0, 0, 0, 0}};  // launch tuning (symhss_set_tuning)
   symhss_mlp_s* mlp = nullptr;                    // attached proposer (not owned)
   double prop_margin = 1.15;
   symhss::DevBuf featjobs, feats, mlpout, chkjobs, chkratio;
@@ -434,11 +436,12 @@ struct TileBuilder {
   }
   // chunks of TILE_T thread points x ln loop points; a launch that would leave most SMs
   // idle uses shorter loop chunks (more blocks, each with less work)
-  void make_chunks() {
+  void make_chunks(int fixed_ln) {
     long long base = 0;
     for (const TileJob& jb : jobs)
       base += (long long)((jb.n_tp + TILE_T - 1) / TILE_T) * ((jb.n_lp + TILE_L - 1) / TILE_L);
-    const int ln = base >= 4 * 148 ? TILE_L : (base >= 2 * 148 ? TILE_L / 2 : TILE_L / 4);
+    int ln = base >= 4 * 148 ? TILE_L : (base >= 2 * 148 ? TILE_L / 2 : TILE_L / 4);
+    if (fixed_ln > 0) ln = std::min(fixed_ln, TILE_L);
     chunks.clear();
     for (int j = 0; j < (int)jobs.size(); ++j)
       for (int a = 0; a < jobs[j].n_tp; a += TILE_T)
@@ -446,7 +449,7 @@ struct TileBuilder {
   }
   cudaError_t launch(symhss_s* h, DevBuf& buf, double2* out, cudaStream_t s) {
     if (jobs.empty()) return cudaSuccess;
-    make_chunks();
+    make_chunks(h->tune.tile_loop_chunk);
     Packer pk;
     const size_t o1 = pk.add(tp_pt), o2 = pk.add(tp_s0), o3 = pk.add(tp_s1);
     const size_t o4 = pk.add(lp_pt), o5 = pk.add(lp_s0), o6 = pk.add(lp_s1);
@@ -727,6 +730,7 @@ int compress_height(symhss_s* h, int t, cudaStream_t s) {
   ia.status = h->status.as<int>();
   ia.max_m = max_m;
   ia.max_n = max_n;
+  ia.cluster_max = h->tune.id_cluster_max;
   const size_t id_before = h->marks.size();
   ia.jobs = reinterpret_cast<const IdJob*>(H.idjobs.as<char>() + o_plain);
   ia.njobs = (int)plain_jobs.size();
@@ -1093,6 +1097,8 @@ int assemble_and_lu(symhss_s* h, int t, cudaStream_t s, long long& pairs) {
   la.njobs = (int)lj.size();
   la.max_n = max_n;
   la.status = h->status.as<int>();
+  la.lookahead = h->tune.lu_lookahead;
+  la.panel_threads = h->tune.lu_panel_threads;
   TIMED(SYMHSS_K_GETRF, lu_work, launch_getrf(la, s));
   return SYMHSS_OK;
 }
@@ -1219,6 +1225,8 @@ int factor_height(symhss_s* h, int t, cudaStream_t s, long long& pairs) {
   la.njobs = (int)rxl.size();
   la.max_n = max_k;
   la.status = h->status.as<int>();
+  la.lookahead = h->tune.lu_lookahead;
+  la.panel_threads = h->tune.lu_panel_threads;
   TIMED(SYMHSS_K_GETRF, w_rxlu, launch_getrf(la, s));
   TIMED(SYMHSS_K_OTHER, 0.0, launch_copy_blocks(nullptr, H.At.as<double2>(),
                                                 reinterpret_cast<const CopyJob*>(qb + oe), (int)eye.size(), s));
@@ -1766,6 +1774,83 @@ int symhss_problem_ranks(symhss_t h, int problem, int level, int* out) {
 }
 
 int symhss_level_ranks(symhss_t h, int level, int* out) { return symhss_problem_ranks(h, 0, level, out); }
+
+static bool tuning_ok(const symhss_tuning* t) {
+  auto in = [](int v, std::initializer_list<int> l) {
+    for (int x : l)
+      if (v == x) return true;
+    return false;
+  };
+  return in(t->lu_lookahead, {0, 1}) && in(t->lu_panel_threads, {256, 512, 1024}) &&
+         in(t->tile_loop_chunk, {0, 8, 16, 32}) && in(t->id_cluster_max, {1, 2, 4, 8, 16});
+}
+
+int symhss_get_tuning(symhss_t h, symhss_tuning* out) {
+  if (!h || !out) return SYMHSS_ERR_INVALID;
+  *out = h->tune;
+  return SYMHSS_OK;
+}
+
+int symhss_set_tuning(symhss_t h, const symhss_tuning* t) {
+  if (!h || !t || !tuning_ok(t)) return SYMHSS_ERR_INVALID;
+  h->tune = *t;
+  return SYMHSS_OK;
+}
+
+int symhss_autotune(symhss_t h, int reps, symhss_tuning* out, void* stream) {
+  if (!h || reps < 1 || reps > 100) return SYMHSS_ERR_INVALID;
+  symhss_tuning best = h->tune;
+  // min over reps of one kernel class's device time in compress
+  auto time_compress = [&](int cls, double* ms) -> int {
+    double m = 1e300;
+    for (int r = 0; r < reps; ++r) {
+      int rc = symhss_compress(h, stream);
+      if (rc) return rc;
+      m = std::min(m, h->st.kernel_ms[cls]);
+    }
+    *ms = m;
+    return SYMHSS_OK;
+  };
+  double bms = 1e300, ms = 0;
+  for (int v : {0, 8, 16, 32}) {
+    h->tune = best;
+    h->tune.tile_loop_chunk = v;
+    int rc = time_compress(SYMHSS_K_TILES, &ms);
+    if (rc) return rc;
+    if (ms < bms) { bms = ms; best.tile_loop_chunk = v; }
+  }
+  bms = 1e300;
+  for (int v : {1, 2, 4, 8, 16}) {
+    h->tune = best;
+    h->tune.id_cluster_max = v;
+    int rc = time_compress(SYMHSS_K_ID, &ms);
+    if (rc) return rc;
+    if (ms < bms) { bms = ms; best.id_cluster_max = v; }
+  }
+  h->tune = best;
+  int rc = symhss_compress(h, stream);
+  if (rc) return rc;
+  bms = 1e300;
+  for (int pt : {256, 512, 1024})
+    for (int la : {0, 1}) {
+      h->tune = best;
+      h->tune.lu_panel_threads = pt;
+      h->tune.lu_lookahead = la;
+      double m = 1e300;
+      for (int r = 0; r < reps; ++r) {
+        const double before = h->st.kernel_ms[SYMHSS_K_GETRF];
+        rc = symhss_factor(h, stream);
+        if (rc) return rc;
+        m = std::min(m, h->st.kernel_ms[SYMHSS_K_GETRF] - before);
+      }
+      if (m < bms) { bms = m; best.lu_panel_threads = pt; best.lu_lookahead = la; }
+    }
+  h->tune = best;
+  rc = symhss_factor(h, stream);
+  if (rc) return rc;
+  if (out) *out = best;
+  return SYMHSS_OK;
+}
 
 int symhss_set_proposer(symhss_t h, symhss_mlp_t net, double margin) {
   if (!h || !(margin >= 1.0) || !std::isfinite(margin)) return SYMHSS_ERR_INVALID;

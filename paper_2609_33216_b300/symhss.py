@@ -69,6 +69,14 @@ class symhss_stats_t(C.Structure):
                 ("proposal_rank_err", C.c_double), ("proposal_under", C.c_longlong)]
 
 
+class symhss_tuning(C.Structure):
+    _fields_ = [("lu_lookahead", C.c_int), ("lu_panel_threads", C.c_int), ("tile_loop_chunk", C.c_int),
+                ("id_cluster_max", C.c_int), ("reserved", C.c_int * 4)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k in ("lu_lookahead", "lu_panel_threads", "tile_loop_chunk", "id_cluster_max")}
+
+
 class symhss_points(C.Structure):
     _fields_ = [("n", C.c_int), ("x", C.c_void_p), ("y", C.c_void_p), ("nx", C.c_void_p),
                 ("ny", C.c_void_p), ("w", C.c_void_p), ("kappa", C.c_void_p), ("id", C.c_void_p)]
@@ -104,6 +112,9 @@ _SIGNATURES = [
                                         C.c_float, C.POINTER(C.c_double), C.c_void_p]),
     ("symhss_mlp_destroy", C.c_int, [C.c_void_p]),
     ("symhss_set_proposer", C.c_int, [C.c_void_p, C.c_void_p, C.c_double]),
+    ("symhss_get_tuning", C.c_int, [C.c_void_p, C.POINTER(symhss_tuning)]),
+    ("symhss_set_tuning", C.c_int, [C.c_void_p, C.POINTER(symhss_tuning)]),
+    ("symhss_autotune", C.c_int, [C.c_void_p, C.c_int, C.POINTER(symhss_tuning), C.c_void_p]),
     ("symhss_training_data", C.c_int, [C.c_void_p, _ip, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                        C.c_void_p, C.c_void_p]),
     ("symhss_launch_count", C.c_longlong, []),
@@ -312,3 +323,22 @@ def symhss_training_data(h, stream: int = 0):
         check(lib.symhss_training_data(h, C.byref(cnt), x.ctypes.data, yr.ctypes.data, ys.ctypes.data, mk.ctypes.data,
                                        meta.ctypes.data, geo.ctypes.data, C.c_void_p(stream)), "symhss_training_data")
     return x, yr, ys, mk, meta, geo
+
+
+def symhss_get_tuning(h) -> symhss_tuning:
+    t = symhss_tuning()
+    check(lib.symhss_get_tuning(h, C.byref(t)), "symhss_get_tuning")
+    return t
+
+
+def symhss_set_tuning(h, **kw) -> None:
+    t = symhss_get_tuning(h)
+    for k, v in kw.items():
+        setattr(t, k, v)
+    check(lib.symhss_set_tuning(h, C.byref(t)), "symhss_set_tuning")
+
+
+def symhss_autotune(h, reps: int = 2, stream: int = 0) -> symhss_tuning:
+    t = symhss_tuning()
+    check(lib.symhss_autotune(h, reps, C.byref(t), C.c_void_p(stream)), "symhss_autotune")
+    return t

@@ -75,3 +75,11 @@ def test_batch_create_rejects_mismatched_shared_fields_on_host():
     assert S.lib.symhss_set_curves(None, curves, 2, None) == S.SYMHSS_ERR_INVALID
     assert S.lib.symhss_batch_info(None, None, None, None, None) == S.SYMHSS_ERR_INVALID
     assert S.lib.symhss_problem_ranks(None, 0, 1, None) == S.SYMHSS_ERR_INVALID
+
+
+def test_tuning_calls_validate_on_host():
+    from paper_2609_33216_b300 import symhss as S
+    t = S.symhss_tuning()
+    assert S.lib.symhss_get_tuning(None, C.byref(t)) == S.SYMHSS_ERR_INVALID
+    assert S.lib.symhss_set_tuning(None, C.byref(t)) == S.SYMHSS_ERR_INVALID
+    assert S.lib.symhss_autotune(None, 1, None, None) == S.SYMHSS_ERR_INVALID
