@@ -175,23 +175,27 @@ def test_column_id_exact_rank_and_fixed_rank(S):
 
 @pytest.mark.parametrize("n", [1, 7, 64, 257])
 def test_lu_batched_solves(S, n):
-    rng = np.random.default_rng(n)
-    batch = 5
+    for nrhs, batch in ((3, 5), (37, 5), (80, 60)):  # per-block CTA path, blocked 8- and 16-column paths
+        _lu_solve_case(S, n, nrhs, batch)
+
+
+def _lu_solve_case(S, n, nrhs, batch):
+    rng = np.random.default_rng(n + nrhs)
     a = rng.normal(size=(batch, n, n)) + 1j * rng.normal(size=(batch, n, n)) + 3 * np.eye(n)
-    b = rng.normal(size=(batch, n, 3)) + 1j * rng.normal(size=(batch, n, 3))
+    b = rng.normal(size=(batch, n, nrhs)) + 1j * rng.normal(size=(batch, n, nrhs))
     da = torch.as_tensor(np.ascontiguousarray(np.transpose(a, (0, 2, 1)))).to("cuda")
     db = torch.as_tensor(np.ascontiguousarray(np.transpose(b, (0, 2, 1)))).to("cuda")
     piv = torch.zeros((batch, n), dtype=torch.int32, device="cuda")
     info = torch.zeros(batch, dtype=torch.int32, device="cuda")
     s = torch.cuda.current_stream().cuda_stream
     S.symhss_lu_batched(da.data_ptr(), n, n, n * n, batch, piv.data_ptr(), info.data_ptr(), s)
-    S.symhss_lu_solve_batched(da.data_ptr(), n, n, n * n, piv.data_ptr(), db.data_ptr(), 3, n, 3 * n, batch, s)
+    S.symhss_lu_solve_batched(da.data_ptr(), n, n, n * n, piv.data_ptr(), db.data_ptr(), nrhs, n, nrhs * n, batch, s)
     torch.cuda.synchronize()
     assert int(info.abs().sum()) == 0
     x = np.transpose(db.cpu().numpy(), (0, 2, 1))
     for i in range(batch):
         ref = np.linalg.solve(a[i], b[i])
-        assert np.linalg.norm(x[i] - ref) <= 1e-12 * np.linalg.cond(a[i]) * np.linalg.norm(ref)
+        assert np.linalg.norm(x[i] - ref) <= 1e-12 * np.linalg.cond(a[i]) * np.linalg.norm(ref), (n, nrhs)
 
 
 def test_lu_reports_singular_block(S):
