@@ -235,7 +235,8 @@ typedef struct {
   int lu_panel_threads;   /* 256, 512 or 1024: largest thread block of the LU panel kernel      */
   int tile_loop_chunk;    /* 0: adaptive (8..32 by launch size); else 8, 16 or 32 loop points per block */
   int id_cluster_max;     /* 1, 2, 4, 8 or 16: largest thread-block cluster of one column ID      */
-  int reserved[4];
+  int lu_panel_cluster;   /* 1, 2, 4, 8 or 16: largest cluster factoring one LU panel (1: one block) */
+  int reserved[3];
 } symhss_tuning;
 
 int symhss_get_tuning(symhss_t h, symhss_tuning* out);
@@ -243,7 +244,7 @@ int symhss_get_tuning(symhss_t h, symhss_tuning* out);
 int symhss_set_tuning(symhss_t h, const symhss_tuning* t);
 /* Autotuner: time the handle's own compress / factor with each value of each tunable
  * (coordinate search: tile_loop_chunk and id_cluster_max on compress, then
- * lu_panel_threads x lu_lookahead on factor), `reps` runs per value, the minimum device
+ * lu_panel_threads x lu_lookahead and lu_panel_cluster on factor), `reps` runs per value, the minimum device
  * time of the affected kernel class deciding; leaves the best tuning set (and in *out,
  * if not NULL) and the handle compressed and factorised.  Synchronises `stream`. */
 int symhss_autotune(symhss_t h, int reps, symhss_tuning* out, void* stream);

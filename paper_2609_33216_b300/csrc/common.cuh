@@ -275,6 +275,7 @@ struct LuLaunch {
   int* status;
   int lookahead = 1;       // depth-1 look-ahead on a side stream
   int panel_threads = 1024;  // largest panel block
+  int panel_cluster = 1;     // largest cluster for the panels of few large matrices (1: one block)
 };
 cudaError_t launch_getrf(const LuLaunch& a, cudaStream_t s);
 

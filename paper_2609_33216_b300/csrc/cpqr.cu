@@ -61,6 +61,7 @@ __global__ void __launch_bounds__(kThreads) cpqr_cluster_kernel(const IdLaunch a
   __shared__ double red[kWarps];
   __shared__ int redi[kWarps];
   __shared__ Cand cand[2];
+  __shared__ Cand s_pick;
   __shared__ double s_tau;
   __shared__ double2 s_alpha;
 
@@ -116,12 +117,21 @@ __global__ void __launch_bounds__(kThreads) cpqr_cluster_kernel(const IdLaunch a
       if (lane == 0) cand[par] = Cand{bv, bi};
     }
     cl.sync();
-    double pv = -1.0;
-    int p = n;
-    for (int r = 0; r < C; ++r) {
-      const Cand c = *cl.map_shared_rank(&cand[par], r);
-      if (c.v > pv || (c.v == pv && c.i < p)) { pv = c.v; p = c.i; }
+    // the C proposals are read in parallel (one lane each) and reduced with shuffles
+    if (warp == 0) {
+      double cv = -1.0;
+      int ci = n;
+      if (lane < C) {
+        const Cand cd = *cl.map_shared_rank(&cand[par], lane);
+        cv = cd.v;
+        ci = cd.i;
+      }
+      warp_argmax(cv, ci);
+      if (lane == 0) s_pick = Cand{cv, ci};
     }
+    __syncthreads();
+    double pv = s_pick.v;
+    int p = s_pick.i;
     par ^= 1;
     if (ref < 0.0) ref = pv;
     // 2. stop (the same decision in every block of the cluster)

@@ -13,7 +13,11 @@
 // step k), so the result is interchangeable with the unblocked factorisation.
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace symhss {
 
@@ -23,6 +27,9 @@ constexpr int kNb = 16;          // panel width
 constexpr int kPanelThreads = 256;
 constexpr int kPanelWarps = kPanelThreads / 32;
 constexpr int kTs = 32;          // trailing-update tile
+constexpr int kClusterPanelThreads = 256;
+
+struct Cand2 { double v; int i; };
 
 __global__ void __launch_bounds__(kPanelThreads) panel_kernel(const LuLaunch a, int j) {
   __shared__ double red[kPanelWarps];
@@ -162,6 +169,124 @@ __global__ void __launch_bounds__(THREADS) panel_smem_kernel(const LuLaunch a, i
   for (int e = tid; e < rows * w; e += THREADS) {
     const int i = e % rows, q = e / rows;
     A[j + i + (long long)(j + q) * ld] = P[q * rows + i];
+  }
+}
+
+
+// Panel factorisation by a thread-block cluster of C blocks (one cluster per matrix), for
+// the few large matrices of the top levels whose panel would otherwise run on one SM.
+// Panel row i (rows [j, n) numbered from 0) lives in block i % C at local index i / C,
+// in shared memory.  Column step c: every block proposes its largest |re| + |im| among its
+// rows >= c; after a cluster barrier every block reads all proposals through distributed
+// shared memory and takes the largest (ties to the lowest row: the pivots of the one-block
+// kernel); every block copies the pivot row and the old row c, a second cluster barrier
+// ends those reads, the owners write the swapped rows, and every block updates its own
+// rows below c (fusing the next column's proposal).  The arithmetic of every row is the
+// one-block kernel's, so the factors are identical.
+__global__ void __launch_bounds__(kClusterPanelThreads) panel_cluster_kernel(const LuLaunch a, int j, int lmax) {
+  extern __shared__ __align__(16) double2 P[];  // P[q * lmax + li]
+  constexpr int kWarps = kClusterPanelThreads / 32;
+  __shared__ double red[kWarps];
+  __shared__ int redi[kWarps];
+  __shared__ Cand2 cand[2];
+  __shared__ Cand2 pick;
+  __shared__ double2 prow[kNb], rowc[kNb];
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  const LuJob jb = a.jobs[blockIdx.x / C];
+  const int n = jb.n, ld = jb.ld;
+  if (j >= n) return;  // uniform over the cluster (one matrix per cluster)
+  const int w = min(kNb, n - j), rows = n - j;
+  const int lrows = rank < rows ? (rows - rank + C - 1) / C : 0;
+  if ((rows + C - 1) / C > lmax) {  // uniform over the cluster (block 0's row count)
+    if (threadIdx.x == 0 && rank == 0) atomicOr(a.status, ST_BAD_INDEX);
+    return;
+  }
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double2* A = a.base + jb.a_off;
+  int* piv = a.piv + jb.piv_off;
+  for (int e = tid; e < lrows * w; e += kClusterPanelThreads) {
+    const int li = e % lrows, q = e / lrows;
+    P[q * lmax + li] = A[j + rank + li * C + (long long)(j + q) * ld];
+  }
+  __syncthreads();
+  double bv = -1.0;
+  int bi = rows;
+  for (int li = tid; li < lrows; li += kClusterPanelThreads) {
+    const double v = cabs1(P[li]);
+    const int i = rank + li * C;
+    if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
+  }
+  int par = 0;
+  for (int c = 0; c < w; ++c) {
+    warp_argmax(bv, bi);
+    if (lane == 0) { red[warp] = bv; redi[warp] = bi; }
+    __syncthreads();
+    if (warp == 0) {
+      bv = lane < kWarps ? red[lane] : -1.0;
+      bi = lane < kWarps ? redi[lane] : rows;
+      warp_argmax(bv, bi);
+      if (lane == 0) cand[par] = Cand2{bv, bi};
+    }
+    cl.sync();
+    // the C proposals are read in parallel (one lane each) and reduced with shuffles
+    if (warp == 0) {
+      double cv = -1.0;
+      int ci = rows;
+      if (lane < C) {
+        const Cand2 cd = *cl.map_shared_rank(&cand[par], lane);
+        cv = cd.v;
+        ci = cd.i;
+      }
+      warp_argmax(cv, ci);
+      if (lane == 0) pick = Cand2{cv, ci};
+    }
+    __syncthreads();
+    double pv = pick.v;
+    int p = pick.i;
+    par ^= 1;
+    const bool zero = !(pv > 0.0) || p >= rows;
+    if (zero) p = c;
+    if (tid < w) {
+      prow[tid] = cl.map_shared_rank(P, p % C)[tid * lmax + p / C];
+      rowc[tid] = cl.map_shared_rank(P, c % C)[tid * lmax + c / C];
+    }
+    if (tid == 0 && rank == 0) {
+      piv[j + c] = j + p;
+      if (zero) {
+        if (a.info[jb.info_idx] == 0) a.info[jb.info_idx] = j + c + 1;
+        atomicOr(a.status, ST_SINGULAR);
+      }
+    }
+    cl.sync();  // every block has read rows p and c
+    if (!zero && p != c && tid < w) {
+      if (c % C == rank) P[tid * lmax + c / C] = prow[tid];
+      if (p % C == rank) P[tid * lmax + p / C] = rowc[tid];
+    }
+    __syncthreads();
+    const double2 inv = zero ? make_double2(0.0, 0.0) : cinv(prow[c]);
+    bv = -1.0;
+    bi = rows;
+    // local rows strictly below c
+    for (int li = tid; li < lrows; li += kClusterPanelThreads) {
+      const int i = rank + li * C;
+      if (i <= c) continue;
+      if (!zero) {
+        const double2 l = cmul(P[c * lmax + li], inv);
+        P[c * lmax + li] = l;
+        for (int q = c + 1; q < w; ++q) P[q * lmax + li] = cfms(l, prow[q], P[q * lmax + li]);
+      }
+      if (c + 1 < w) {
+        const double v = cabs1(P[(c + 1) * lmax + li]);
+        if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < lrows * w; e += kClusterPanelThreads) {
+    const int li = e % lrows, q = e / lrows;
+    A[j + rank + li * C + (long long)(j + q) * ld] = P[q * lmax + li];
   }
 }
 
@@ -339,7 +464,39 @@ cudaError_t launch_getrf(const LuLaunch& a, cudaStream_t s) {
   // a high-priority side stream while the rest of the trailing update runs on s.  The two
   // touch disjoint columns; s waits for the panel before the next interchanges.
   LookAhead* la = a.lookahead ? look_ahead_streams() : nullptr;
+  // cluster panels for few large matrices: C blocks per matrix while the batch still leaves
+  // SMs free and every block keeps at least 32 panel rows
+  int pc = 1;
+  while (pc < 16 && 2 * pc <= a.panel_cluster && a.njobs * 2 * pc <= 148 && a.max_n / (2 * pc) >= 32) pc *= 2;
+  const int lmax = (a.max_n + pc - 1) / pc;
+  if (pc > 1) {
+    e = cudaFuncSetAttribute(panel_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)((size_t)lmax * kNb * sizeof(double2)));
+    if (e == cudaSuccess && pc > 8)
+      e = cudaFuncSetAttribute(panel_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      pc = 1;
+    }
+  }
   auto panel = [&](int jj, cudaStream_t st) {
+    if (pc > 1) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(a.njobs * pc, 1, 1);
+      cfg.blockDim = dim3(kClusterPanelThreads, 1, 1);
+      cfg.dynamicSmemBytes = (size_t)lmax * kNb * sizeof(double2);
+      cfg.stream = st;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = pc;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      cudaError_t le = cudaLaunchKernelEx(&cfg, panel_cluster_kernel, a, jj, lmax);
+      symhss::count_launches(1);
+      return le;
+    }
     if (smem_panel) {
       // the panel height shrinks with jj: fewer threads once the remaining rows allow it
       const int rows = a.max_n - jj;

@@ -163,7 +163,7 @@ struct symhss_s {
   symhss_stats_t st{};
   cudaError_t last_cuda = cudaSuccess;
   std::vector<int> mark;                          // host scratch (size npts)
-  symhss_tuning tune = {0, 256, 0, 16, {0, 0, 0, 0}};  // launch tuning (symhss_set_tuning)
+  symhss_tuning tune = {0, 256, 0, 16, 1, {0, 0, 0}};  // launch tuning (symhss_set_tuning)
   symhss_mlp_s* mlp = nullptr;                    // attached proposer (not owned)
   double prop_margin = 1.15;
   symhss::DevBuf featjobs, feats, mlpout, chkjobs, chkratio;
@@ -1099,6 +1099,7 @@ int assemble_and_lu(symhss_s* h, int t, cudaStream_t s, long long& pairs) {
   la.status = h->status.as<int>();
   la.lookahead = h->tune.lu_lookahead;
   la.panel_threads = h->tune.lu_panel_threads;
+  la.panel_cluster = h->tune.lu_panel_cluster;
   TIMED(SYMHSS_K_GETRF, lu_work, launch_getrf(la, s));
   return SYMHSS_OK;
 }
@@ -1227,6 +1228,7 @@ int factor_height(symhss_s* h, int t, cudaStream_t s, long long& pairs) {
   la.status = h->status.as<int>();
   la.lookahead = h->tune.lu_lookahead;
   la.panel_threads = h->tune.lu_panel_threads;
+  la.panel_cluster = h->tune.lu_panel_cluster;
   TIMED(SYMHSS_K_GETRF, w_rxlu, launch_getrf(la, s));
   TIMED(SYMHSS_K_OTHER, 0.0, launch_copy_blocks(nullptr, H.At.as<double2>(),
                                                 reinterpret_cast<const CopyJob*>(qb + oe), (int)eye.size(), s));
@@ -1782,7 +1784,8 @@ static bool tuning_ok(const symhss_tuning* t) {
     return false;
   };
   return in(t->lu_lookahead, {0, 1}) && in(t->lu_panel_threads, {256, 512, 1024}) &&
-         in(t->tile_loop_chunk, {0, 8, 16, 32}) && in(t->id_cluster_max, {1, 2, 4, 8, 16});
+         in(t->tile_loop_chunk, {0, 8, 16, 32}) && in(t->id_cluster_max, {1, 2, 4, 8, 16}) &&
+         in(t->lu_panel_cluster, {1, 2, 4, 8, 16});
 }
 
 int symhss_get_tuning(symhss_t h, symhss_tuning* out) {
@@ -1845,6 +1848,19 @@ int symhss_autotune(symhss_t h, int reps, symhss_tuning* out, void* stream) {
       }
       if (m < bms) { bms = m; best.lu_panel_threads = pt; best.lu_lookahead = la; }
     }
+  bms = 1e300;
+  for (int pcv : {1, 2, 4, 8, 16}) {
+    h->tune = best;
+    h->tune.lu_panel_cluster = pcv;
+    double m = 1e300;
+    for (int r = 0; r < reps; ++r) {
+      const double before = h->st.kernel_ms[SYMHSS_K_GETRF];
+      rc = symhss_factor(h, stream);
+      if (rc) return rc;
+      m = std::min(m, h->st.kernel_ms[SYMHSS_K_GETRF] - before);
+    }
+    if (m < bms) { bms = m; best.lu_panel_cluster = pcv; }
+  }
   h->tune = best;
   rc = symhss_factor(h, stream);
   if (rc) return rc;
