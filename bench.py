@@ -268,6 +268,28 @@ def run_ours(args):
                                      "root_size": stp.root_size,
                                      "accuracy": "first order in h (O(h^3) for the Muller-like system)"}
         pm.close()
+        bm = Solver(w["curve"], w["k0"], w["k1"], w["eps0"], w["eps1"], mode="base", curve_on_device=True,
+                    formulation="bm", **kw)
+        if "base" in tunings:
+            S.symhss_set_tuning(bm.h, **{k: v for k, v in tunings["base"].items() if k != "seconds"})
+        for _ in range(args.warmup):
+            step(bm)
+        barrier()
+        tms = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(bm)
+            e1.record(stream)
+            e1.synchronize()
+            tms.append(e0.elapsed_time(e1))
+        stb = bm.stats()
+        comparators["burton_miller_nonsym"] = {"ms_per_step": sum(tms) / len(tms), "max_rank": list(stb.max_rank),
+                                               "root_size": stb.root_size,
+                                               "accuracy": "first order in h (hypersingular N_k0)"}
+        bm.close()
 
     xs = results["sym"]["x"]
     xb = results["base"]["x"]

@@ -54,6 +54,8 @@ extern "C" {
 
 #define SYMHSS_MULLER  0   /* symmetric Muller-like system (Eq. 15): the method            */
 #define SYMHSS_PMCHWT  1   /* symmetric PMCHWT comparator (Eq. symmetric_pmchwt): first order */
+#define SYMHSS_BM      2   /* Burton-Miller comparator (Eq. bm): non-symmetric, first order;
+                            * requires SYMHSS_NONSYM */
 
 #define SYMHSS_HOST    0   /* pointer location flags */
 #define SYMHSS_DEVICE  1
@@ -94,7 +96,10 @@ typedef struct {
                            * (SYMHSS_SYM) A = [-(e0 S0 + e1 S1), D0 + D1; D*0 + D*1,
                            * -(N0/e0 + N1/e1)], rhs [-W u_in; (1/e0) W du_in/dnu]; its
                            * hypersingular diagonal is one-point corrected (first order).
-                           * SYMHSS_NONSYM gives the unscaled PMCHWT with two IDs.       */
+                           * SYMHSS_NONSYM gives the unscaled PMCHWT with two IDs.
+                           * SYMHSS_BM (with SYMHSS_NONSYM only): rows [-e0 S0 - a e0 (D*0 + I/2),
+                           * D0 - I/2 + a N0; -e1 S1, D1 + I/2], a = i/k0, rhs
+                           * [-u_in - a du_in/dnu; 0], unscaled, two IDs.                 */
   uint64_t seed;          /* seed of the counter-based sketch generator               */
 } symhss_params;
 
@@ -194,8 +199,8 @@ int symhss_factor(symhss_t h, void* stream);
 
 /* Right-hand side of the handle's system for the plane wave
  * u_in = exp(i k0 (x cos(angle) + y sin(angle))): [-eps0 W u_in ; W du_in/dnu]
- * (Eq. 15; PMCHWT: [-W u_in ; (1/eps0) W du_in/dnu]; the unscaled forms without W for
- * SYMHSS_NONSYM).  rhs: device
+ * (Eq. 15; PMCHWT: [-W u_in ; (1/eps0) W du_in/dnu]; Burton-Miller: [-u_in - (i/k0)
+ * du_in/dnu ; 0]; the unscaled forms without W for SYMHSS_NONSYM).  rhs: device
  * complex128[2n] (a batch: every problem's block with its own k0 and eps0). */
 int symhss_rhs_plane_wave(symhss_t h, double angle, void* rhs, void* stream);
 

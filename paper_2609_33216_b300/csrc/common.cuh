@@ -111,7 +111,10 @@ inline KernelParams make_kernel_params(const symhss_params& p) {
   k.k0 = p.k0; k.k1 = p.k1; k.eps0 = p.eps0; k.eps1 = p.eps1;
   k.form = p.formulation;
   k.pad_ = 0;
-  if (p.formulation == SYMHSS_PMCHWT) {
+  if (p.formulation == SYMHSS_BM) {  // only the layer kernels are combined in the tile kernel's BM branch
+    k.cs0 = p.eps0; k.cs1 = p.eps1; k.cd0 = 1.0; k.cd1 = 1.0; k.cn0 = 1.0 / p.k0; k.cn1 = 0.0;
+    k.half_ft = 0.5;
+  } else if (p.formulation == SYMHSS_PMCHWT) {
     k.cs0 = p.eps0; k.cs1 = -p.eps1; k.cd0 = 1.0; k.cd1 = -1.0; k.cn0 = 1.0 / p.eps0; k.cn1 = -1.0 / p.eps1;
     k.half_ft = 0.0;
   } else {
@@ -362,8 +365,8 @@ cudaError_t launch_leaf_scatter(const double2* g, double2* x, long long ldx, con
 
 // Plane-wave right-hand side of problem jobs[j]: nodes [node0, node0 + n) of the
 // point table, rows [vec0, vec0 + 2n) of rhs ([eq1; eq2]).
-// rhs rows: [cu W u_in ; cq W du_in/dnu] (W omitted for the unscaled systems)
-struct WaveJob { int node0, n; long long vec0; double k0, cu, cq; };
+// rhs rows: [a1 u_in + b1 du_in/dnu ; a2 u_in + b2 du_in/dnu], times W for the row-scaled systems
+struct WaveJob { int node0, n; long long vec0; double k0; double2 a1, b1, a2, b2; };
 cudaError_t launch_plane_wave(const PointTable& t, const WaveJob* jobs, int njobs, int max_n, double angle,
                               int scaled, double2* rhs, cudaStream_t s);
 

@@ -67,7 +67,8 @@ int symhss_kernel_block(const symhss_params* prm, const symhss_points* obs, cons
   if (!(prm->k0 > 0) || !(prm->k1 > 0) || !std::isfinite(prm->eps0) || !std::isfinite(prm->eps1))
     return SYMHSS_ERR_INVALID;
   if (!(prm->eps0 != 0.0) || !(prm->eps1 != 0.0)) return SYMHSS_ERR_INVALID;
-  if (prm->formulation != SYMHSS_MULLER && prm->formulation != SYMHSS_PMCHWT) return SYMHSS_ERR_INVALID;
+  if (prm->formulation != SYMHSS_MULLER && prm->formulation != SYMHSS_PMCHWT && prm->formulation != SYMHSS_BM)
+    return SYMHSS_ERR_INVALID;
   if (ld < obs->n || ld < 1) return SYMHSS_ERR_INVALID;
   if ((obs->n > 0 && !obs_eq) || (src->n > 0 && !src_comp)) return SYMHSS_ERR_INVALID;
   if (obs->n == 0 || src->n == 0) return SYMHSS_OK;

@@ -139,8 +139,10 @@ __global__ void plane_wave_kernel(const PointTable t, const WaveJob* jobs, doubl
   const double2 dudn = make_double2(-dn * sn, dn * cs);  // i k0 (nu.dir) u_in
   const double sc = scaled ? t.w[i] : 1.0;
   double2* r = rhs + jb.vec0;
-  r[j] = make_double2(jb.cu * sc * uin.x, jb.cu * sc * uin.y);
-  r[jb.n + j] = make_double2(jb.cq * sc * dudn.x, jb.cq * sc * dudn.y);
+  const double2 r1 = cadd(cmul(jb.a1, uin), cmul(jb.b1, dudn));
+  const double2 r2 = cadd(cmul(jb.a2, uin), cmul(jb.b2, dudn));
+  r[j] = make_double2(sc * r1.x, sc * r1.y);
+  r[jb.n + j] = make_double2(sc * r2.x, sc * r2.y);
 }
 
 }  // namespace

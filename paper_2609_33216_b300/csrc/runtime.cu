@@ -371,8 +371,17 @@ int build_geometry(symhss_s* h, cudaStream_t s) {
   std::vector<WaveJob> wv;
   for (const Problem& P : h->probs) {
     kp.push_back(kparams(P.prm));
-    const bool pm = P.prm.formulation == SYMHSS_PMCHWT;
-    wv.push_back(WaveJob{P.node0, P.n, P.vec0, P.prm.k0, pm ? -1.0 : -P.prm.eps0, pm ? 1.0 / P.prm.eps0 : 1.0});
+    WaveJob wj;
+    wj.node0 = P.node0; wj.n = P.n; wj.vec0 = P.vec0; wj.k0 = P.prm.k0;
+    const double2 z = make_double2(0.0, 0.0);
+    if (P.prm.formulation == SYMHSS_BM) {  // [-u_in - (i/k0) du_in/dnu ; 0]
+      wj.a1 = make_double2(-1.0, 0.0); wj.b1 = make_double2(0.0, -1.0 / P.prm.k0); wj.a2 = z; wj.b2 = z;
+    } else if (P.prm.formulation == SYMHSS_PMCHWT) {  // [-u_in ; du_in/dnu / eps0]
+      wj.a1 = make_double2(-1.0, 0.0); wj.b1 = z; wj.a2 = z; wj.b2 = make_double2(1.0 / P.prm.eps0, 0.0);
+    } else {  // [-eps0 u_in ; du_in/dnu]
+      wj.a1 = make_double2(-P.prm.eps0, 0.0); wj.b1 = z; wj.a2 = z; wj.b2 = make_double2(1.0, 0.0);
+    }
+    wv.push_back(wj);
   }
   CK(h->kps.ensure(kp.size() * sizeof(KernelParams)));
   CK(cudaMemcpyAsync(h->kps.p, kp.data(), kp.size() * sizeof(KernelParams), cudaMemcpyHostToDevice, s));
@@ -1268,7 +1277,9 @@ int validate_params(const symhss_params* p) {
   if (p->precision != SYMHSS_FP64) return SYMHSS_ERR_INVALID;
   if (p->fixed_rank_kL < 0 || (p->fixed_rank_kL > 0 && !(p->rank_scale_a >= 1.0))) return SYMHSS_ERR_INVALID;
   if (p->oversample < 0) return SYMHSS_ERR_INVALID;
-  if (p->formulation != SYMHSS_MULLER && p->formulation != SYMHSS_PMCHWT) return SYMHSS_ERR_INVALID;
+  if (p->formulation != SYMHSS_MULLER && p->formulation != SYMHSS_PMCHWT && p->formulation != SYMHSS_BM)
+    return SYMHSS_ERR_INVALID;
+  if (p->formulation == SYMHSS_BM && p->mode != SYMHSS_NONSYM) return SYMHSS_ERR_INVALID;
   return SYMHSS_OK;
 }
 

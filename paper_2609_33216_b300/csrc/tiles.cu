@@ -1,6 +1,6 @@
 // Kernel-entry tile generator: blocks of the symmetric Muller-like matrix
-// (Eq. 15; unscaled baseline of Sec. 6), or of the PMCHWT comparator (Eq.
-// symmetric_pmchwt), between two point lists.
+// (Eq. 15; unscaled baseline of Sec. 6), or of the PMCHWT (Eq. symmetric_pmchwt) or
+// Burton-Miller (Eq. bm) comparators, between two point lists.
 //
 // Each thread owns one point of the "thread" list; a chunk of the "loop" list is
 // staged in shared memory.  For every (thread point, loop point) pair the thread
@@ -78,6 +78,29 @@ struct P7 { double x, y, nx, ny, w, kappa; int id; };
 __device__ __forceinline__ void pair_block(const P7& o, const P7& s, const KernelParams& kp,
                                            bool unscaled, double2 out[4]) {
   const double wgt = unscaled ? s.w : __dmul_rn(o.w, s.w);
+  if (o.id >= 0 && o.id == s.id && kp.form == SYMHSS_BM) {
+    // Burton-Miller: [-e0 S0 - a e0 (D*0 + I/2), D0 - I/2 + a N0; -e1 S1, D1 + I/2], a = i/k0
+    const double w = o.w;
+    const double c = 1.0 / (2.0 * kPi);
+    const double2 gs0 = make_double2(-c * (kEulerGamma + log(kp.k0 * w / (4.0 * kPi))), 0.25);
+    const double2 gs1 = make_double2(-c * (kEulerGamma + log(kp.k1 * w / (4.0 * kPi))), 0.25);
+    const double dd = -o.kappa / (4.0 * kPi);
+    const double lw = log(w / (2.0 * kPi));
+    const double k0s = kp.k0 * kp.k0;
+    const double hyp = -kPi / (6.0 * w * w) + o.kappa * o.kappa / (24.0 * kPi);
+    const double2 n0 = make_double2(hyp - k0s * (kp.lhk0 + kEulerGamma) / (4.0 * kPi) + k0s / (8.0 * kPi) -
+                                        k0s / (4.0 * kPi) * lw,
+                                    0.125 * k0s);
+    const double ae = kp.eps0 * kp.ik0;  // |a| eps0
+    const double ft = unscaled ? 1.0 : w;
+    // -e0 S0 - i ae D*0, then - i ae / 2 (free term)
+    out[0] = make_double2(wgt * (-kp.eps0 * gs0.x), wgt * (-kp.eps0 * gs0.y - ae * dd) - 0.5 * ae * ft);
+    // D0 + i (1/k0) N0 - 1/2
+    out[1] = make_double2(wgt * (dd - kp.ik0 * n0.y) - 0.5 * ft, wgt * (kp.ik0 * n0.x));
+    out[2] = make_double2(wgt * (-kp.eps1 * gs1.x), wgt * (-kp.eps1 * gs1.y));
+    out[3] = make_double2(wgt * dd + 0.5 * ft, 0.0);
+    return;
+  }
   if (o.id >= 0 && o.id == s.id) {
     const double w = o.w;
     const double c = 1.0 / (2.0 * kPi);
@@ -125,6 +148,15 @@ __device__ __forceinline__ void pair_block(const P7& o, const P7& s, const Kerne
   const double nn_r = __dmul_rn(nn, inv_r), ab_r = __dmul_rn(__dmul_rn(a, b), inv_r);
   const LayerVals l0 = layer(kp.k0, r, inv_r, lr, kp.lhk0, kp.ik0, a_r, b_r, nn_r, ab_r);
   const LayerVals l1 = layer(kp.k1, r, inv_r, lr, kp.lhk1, kp.ik1, a_r, b_r, nn_r, ab_r);
+  if (kp.form == SYMHSS_BM) {
+    const double ae = kp.eps0 * kp.ik0;
+    // -e0 G0 - i ae D*0 ;  D0 + i (1/k0) N0 ;  -e1 G1 ;  D1
+    out[0] = rscale(wgt, make_double2(-kp.eps0 * l0.g.x + ae * l0.ds.y, -kp.eps0 * l0.g.y - ae * l0.ds.x));
+    out[1] = rscale(wgt, make_double2(l0.d.x - kp.ik0 * l0.n.y, l0.d.y + kp.ik0 * l0.n.x));
+    out[2] = rscale(wgt, make_double2(-kp.eps1 * l1.g.x, -kp.eps1 * l1.g.y));
+    out[3] = rscale(wgt, l1.d);
+    return;
+  }
   const double2 ks = combo(kp.cs0, l0.g, kp.cs1, l1.g);
   const double2 kd = combo(kp.cd0, l0.d, kp.cd1, l1.d);
   const double2 kds = combo(kp.cd0, l0.ds, kp.cd1, l1.ds);

@@ -27,7 +27,7 @@ class Solver:
             eps1 = eps0 * (k1 / k0) ** 2
         self.n = int(curve.n)
         self.mode = S.SYMHSS_SYM if mode == "sym" else S.SYMHSS_NONSYM
-        form = S.SYMHSS_PMCHWT if formulation == "pmchwt" else S.SYMHSS_MULLER
+        form = {"muller": S.SYMHSS_MULLER, "pmchwt": S.SYMHSS_PMCHWT, "bm": S.SYMHSS_BM}[formulation]
         self.prm = S.params(k0, k1, eps0, eps1, mode=self.mode, formulation=form, **params)
         self._keep = []
         cs = self._curve_struct(curve, curve_on_device)

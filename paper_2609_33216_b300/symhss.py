@@ -29,6 +29,7 @@ SYMHSS_NONSYM = 1
 SYMHSS_FP64 = 0
 SYMHSS_MULLER = 0
 SYMHSS_PMCHWT = 1
+SYMHSS_BM = 2
 SYMHSS_HOST = 0
 SYMHSS_DEVICE = 1
 SYMHSS_MAX_LEVELS = 32

@@ -1,12 +1,14 @@
-"""The PMCHWT comparator (Eq. symmetric_pmchwt) on the GPU, against its FP64 oracle
-(oracle/pmchwt.py), through the C ABI:
+"""The PMCHWT (Eq. symmetric_pmchwt) and Burton-Miller (Eq. bm) comparators on the GPU,
+against their FP64 oracles (oracle/pmchwt.py, oracle/bm.py), through the C ABI:
 
 * tile entries (nodes, coincident nodes with the hypersingular corrected diagonal, proxy
   points; row-scaled and unscaled) match the oracle;
 * the GPU's row-scaled PMCHWT matrix is complex symmetric bit for bit (no free terms);
 * the HSS solver with formulation = PMCHWT (symmetric one-ID and non-symmetric two-ID)
   matches the oracle's dense PMCHWT solution to 1e-8 on the disk and on a star, and on the
-  disk its error to the Bessel-series solution is the first-order discretisation error.
+  disk its error to the Bessel-series solution is the first-order discretisation error;
+* Burton-Miller tiles (unscaled and row-scaled) match the oracle, the two-ID solver matches
+  the dense Burton-Miller solution to 1e-8, and the symmetric mode refuses it.
 """
 
 import numpy as np
@@ -18,6 +20,7 @@ torch = pytest.importorskip("torch")
 
 from oracle import hss as OH  # noqa: E402
 from oracle import kernels as OK  # noqa: E402
+from oracle import bm as BM  # noqa: E402
 from oracle import pmchwt as PM  # noqa: E402
 from oracle.exact import disk_solution  # noqa: E402
 from synth import disk, fourier_star, star  # noqa: E402
@@ -34,7 +37,7 @@ def _dev(a, dtype=torch.float64):
     return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
 
 
-def _block(S, prm, obs, obs_eq, src, src_comp, scaled):
+def _block(S, prm, obs, obs_eq, src, src_comp, scaled, form=None):
     keep = []
 
     def pts(p):
@@ -48,7 +51,7 @@ def _block(S, prm, obs, obs_eq, src, src_comp, scaled):
     comp = _dev(np.asarray(src_comp, np.int32), torch.int32)
     m, n = len(obs), len(src)
     out = torch.zeros((n, m), dtype=torch.complex128, device="cuda")
-    p = S.params(prm.k0, prm.k1, prm.eps0, prm.eps1, formulation=S.SYMHSS_PMCHWT)
+    p = S.params(prm.k0, prm.k1, prm.eps0, prm.eps1, formulation=S.SYMHSS_PMCHWT if form is None else form)
     S.symhss_kernel_block(p, ost, eq.data_ptr(), sst, comp.data_ptr(), scaled, out.data_ptr(), m,
                           torch.cuda.current_stream().cuda_stream)
     torch.cuda.synchronize()
@@ -86,9 +89,9 @@ def test_pmchwt_gpu_matrix_symmetric_bit_exact(S):
     assert np.array_equal(a, a.T)
 
 
-def _solve(curve, prm, mode, **kw):
+def _solve(curve, prm, mode, formulation="pmchwt", **kw):
     from paper_2609_33216_b300.solver import Solver
-    s = Solver(curve, prm.k0, prm.k1, prm.eps0, prm.eps1, mode=mode, formulation="pmchwt", **kw)
+    s = Solver(curve, prm.k0, prm.k1, prm.eps0, prm.eps1, mode=mode, formulation=formulation, **kw)
     s.compress()
     s.factor()
     x = s.solve(s.rhs(0.0)).cpu().numpy()
@@ -117,3 +120,35 @@ def test_pmchwt_solver_matches_dense_on_star(S, mode):
     x = _solve(c, prm, mode, leaf=128, nproxy=64, tol=1e-10)
     xd = PM.pmchwt_solve(c, prm)
     assert np.linalg.norm(x - xd) / np.linalg.norm(xd) <= 1e-8
+
+
+@pytest.mark.parametrize("scaled", [True, False], ids=["scaled", "unscaled"])
+def test_bm_tiles_match_oracle(S, scaled):
+    c = fourier_star(300, ((3, 0.2, 0.1), (5, 0.05, 0.7)))
+    prm = OK.Params(9.0, 17.0, 1.3, 3.1)
+    pts = OK.Points.from_curve(c)
+    rng = np.random.default_rng(7)
+    rows = rng.choice(300, 200, replace=False)
+    cols = rng.choice(300, 170, replace=False)
+    cols[:40] = rows[:40]
+    ring = OK.Points.circle(0.2, -0.1, 0.7, 64)
+    obs = OH._stack(pts.take(rows), ring)
+    eq = np.concatenate([rng.integers(0, 2, 200), np.repeat([0, 1], 32)])
+    src = pts.take(cols)
+    comp = rng.integers(0, 2, 170)
+    ref = BM.bm_entries(obs, eq, src, comp, prm, scaled)
+    got = _block(S, prm, obs, eq, src, comp, scaled, form=S.SYMHSS_BM)
+    scale = np.abs(ref).max()
+    err = np.abs(got - ref)
+    assert np.all(err <= 2e-13 * np.abs(ref) + 1e-14 * scale), (err.max(), scale)
+
+
+def test_bm_solver_matches_dense(S):
+    prm = OK.Params.from_wavenumbers(20.0, 30.0, eps0=1.5)
+    c = star(2048)
+    x = _solve(c, prm, "base", formulation="bm", leaf=128, nproxy=64, tol=1e-10)
+    xd = BM.bm_solve(c, prm)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) <= 1e-8
+    from paper_2609_33216_b300.symhss import SymhssError
+    with pytest.raises(SymhssError):
+        _solve(c, prm, "sym", formulation="bm", leaf=128, nproxy=64, tol=1e-10)
