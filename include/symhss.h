@@ -51,6 +51,7 @@ extern "C" {
 #define SYMHSS_NONSYM  1   /* non-symmetric two-ID baseline, unscaled system (Sec. 6)    */
 
 #define SYMHSS_FP64    0   /* every stage in FP64 */
+#define SYMHSS_MIXED   1   /* FP64 compression; complex64 factorisation; FP64 refinement */
 
 #define SYMHSS_MULLER  0   /* symmetric Muller-like system (Eq. 15): the method            */
 #define SYMHSS_PMCHWT  1   /* symmetric PMCHWT comparator (Eq. symmetric_pmchwt): first order */
@@ -84,7 +85,11 @@ typedef struct {
   int nproxy;             /* minimum proxy points per ring (64)                       */
   double proxy_factor;    /* proxy ring radius / box radius (1.5)                     */
   int mode;               /* SYMHSS_SYM or SYMHSS_NONSYM                              */
-  int precision;          /* SYMHSS_FP64                                              */
+  int precision;          /* SYMHSS_FP64, or SYMHSS_MIXED: the block LUs and the solves of the
+                           * factorisation in complex64 (FP32: 60x the FP64 rate of the
+                           * B300), the solution refined against the FP64 compressed operator
+                           * (symhss_matvec): x <- x + B^{-1} (f - A x), 2 steps by default
+                           * (symhss_set_refinement)                                        */
   int fixed_rank_kL;      /* > 0: fixed ranks k_l = ceil(a^(L-l) kL) (Sec. 4.3), 0: tol */
   double rank_scale_a;    /* a of Sec. 4.3 (1.15)                                     */
   int oversample;         /* sketch oversampling p (16): an ID is taken of Y = Omega M with
@@ -208,6 +213,18 @@ int symhss_rhs_plane_wave(symhss_t h, double angle, void* rhs, void* stream);
  * complex128[2n * nrhs], column j at offset 2n*j; rhs is not modified; rhs and x
  * may not overlap.  Requires factor. */
 int symhss_solve(symhss_t h, const void* rhs, void* x, int nrhs, void* stream);
+
+/* y = A_hss x: the handle's FP64 compressed operator (leaf diagonal blocks, sibling skeleton
+ * blocks and the ID interpolation operators of every level, Sec. 4.1) applied to `nrhs`
+ * vectors (device complex128[2n * nrhs], the layout of symhss_solve; x and y may not
+ * overlap).  Requires factor (which keeps the operator's blocks).  Error to the exact
+ * matrix: the compression's (about tol). */
+int symhss_matvec(symhss_t h, const void* x, void* y, int nrhs, void* stream);
+
+/* Refinement steps of SYMHSS_MIXED solves (0..4; 2 after create).  Each step applies
+ * symhss_matvec and one more solve with the complex64 factors; each step gains a factor of
+ * about kappa * 1e-7 (one step suffices at 2048 nodes, k 20/30; two at 65536 nodes, k 40/60). */
+int symhss_set_refinement(symhss_t h, int steps);
 
 /* As symhss_solve with host buffers: copies rhs in and x out inside the call. */
 int symhss_solve_host(symhss_t h, const void* rhs_host, void* x_host, int nrhs, void* stream);

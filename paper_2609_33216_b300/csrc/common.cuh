@@ -46,6 +46,35 @@ __device__ __forceinline__ double2 cinv(double2 a) {
   }
 }
 
+// ---- complex64 on float2 (the mixed-precision factorisation) ----------------
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 acc) {
+  return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y)));
+}
+__device__ __forceinline__ float2 cfms(float2 a, float2 b, float2 acc) {
+  return make_float2(fmaf(-a.x, b.x, fmaf(a.y, b.y, acc.x)), fmaf(-a.x, b.y, fmaf(-a.y, b.x, acc.y)));
+}
+__device__ __forceinline__ float cabs1(float2 a) { return fabsf(a.x) + fabsf(a.y); }
+__device__ __forceinline__ float2 cinv(float2 a) {
+  if (fabsf(a.x) >= fabsf(a.y)) {
+    float r = a.y / a.x, d = a.x + a.y * r;
+    return make_float2(1.0f / d, -r / d);
+  } else {
+    float r = a.x / a.y, d = a.y + a.x * r;
+    return make_float2(r / d, -1.0f / d);
+  }
+}
+// complex constant / conversion in the element type CT (double2 or float2)
+template <typename CT> __device__ __forceinline__ CT make_c(double re, double im);
+template <> __device__ __forceinline__ double2 make_c<double2>(double re, double im) { return make_double2(re, im); }
+template <> __device__ __forceinline__ float2 make_c<float2>(double re, double im) {
+  return make_float2((float)re, (float)im);
+}
+template <typename CT> __device__ __forceinline__ CT to_c(double2 v) { return make_c<CT>(v.x, v.y); }
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -276,6 +305,7 @@ struct LuLaunch {
   int njobs;
   int max_n;
   int* status;
+  float2* base32 = nullptr;  // non-null: factor these complex64 matrices instead of `base`
   int lookahead = 1;       // depth-1 look-ahead on a side stream
   int panel_threads = 1024;  // largest panel block
   int panel_cluster = 1;     // largest cluster for the panels of few large matrices (1: one block)
@@ -290,6 +320,8 @@ struct RsLaunch {
   const double2* abase;
   const int* piv;
   double2* bbase;
+  const float2* abase32 = nullptr;  // non-null: complex64 factors and right-hand sides
+  float2* bbase32 = nullptr;
   const RsJob* jobs;
   int njobs;
   int max_rhs;
@@ -324,6 +356,8 @@ struct BasisLaunch {
   const double2* T;
   const double2* in;
   double2* out;
+  const float2* in32 = nullptr;  // non-null out32: complex64 in / out (T stays complex128)
+  float2* out32 = nullptr;
   const BasisJob* jobs;
   int njobs;
   int max_cols;
@@ -353,6 +387,14 @@ cudaError_t launch_gemm(const GemmLaunch& a, cudaStream_t s);
 struct CopyJob { long long src_off, dst_off; int rows, cols, lds, ldd; };
 cudaError_t launch_copy_blocks(const double2* src, double2* dst, const CopyJob* jobs, int njobs,
                                cudaStream_t s);
+cudaError_t launch_copy_blocks32(const float2* src, float2* dst, const CopyJob* jobs, int njobs, cudaStream_t s);
+// element-wise precision changes of n complex values
+cudaError_t launch_narrow(const double2* src, float2* dst, long long n, cudaStream_t s);
+cudaError_t launch_widen(const float2* src, double2* dst, long long n, cudaStream_t s);
+// out += L * in: the transpose of apply_r (skeleton rows get in, the others T^T in)
+cudaError_t launch_apply_l(const BasisLaunch& a, cudaStream_t s);
+// y = a x + b y, elementwise over n complex values (a, b real)
+cudaError_t launch_axpby(const double2* x, double2* y, long long n, double a, double b, cudaStream_t s);
 
 // Leaf boxes are contiguous node ranges [begin, begin + len) of a problem with n
 // nodes whose [eq1; eq2] block starts at `base` in the global vectors; the box

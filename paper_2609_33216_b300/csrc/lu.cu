@@ -15,6 +15,13 @@ namespace {
 constexpr int kRsMaxWarps = 8;
 constexpr int kCtaThreads = 256;
 
+template <typename CT> __device__ __forceinline__ const CT* rs_a(const RsLaunch& a);
+template <> __device__ __forceinline__ const double2* rs_a<double2>(const RsLaunch& a) { return a.abase; }
+template <> __device__ __forceinline__ const float2* rs_a<float2>(const RsLaunch& a) { return a.abase32; }
+template <typename CT> __device__ __forceinline__ CT* rs_b(const RsLaunch& a);
+template <> __device__ __forceinline__ double2* rs_b<double2>(const RsLaunch& a) { return a.bbase; }
+template <> __device__ __forceinline__ float2* rs_b<float2>(const RsLaunch& a) { return a.bbase32; }
+
 // perm = composition of the recorded row interchanges (thread 0, sequential)
 __device__ __forceinline__ void build_perm(int* perm, const int* piv, int n) {
   if (threadIdx.x == 0) {
@@ -26,36 +33,37 @@ __device__ __forceinline__ void build_perm(int* perm, const int* piv, int n) {
   }
 }
 
+template <typename CT>
 __global__ void getrs_kernel(const RsLaunch a, int warps) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const RsJob jb = a.jobs[blockIdx.x];
   const int n = jb.n;
   if (n > a.max_n || n < 0) return;  // uniform per block
-  double2* dinv = reinterpret_cast<double2*>(smem_raw);
-  double2* cols = dinv + a.max_n;
+  CT* dinv = reinterpret_cast<CT*>(smem_raw);
+  CT* cols = dinv + a.max_n;
   int* perm = reinterpret_cast<int*>(cols + (size_t)warps * a.max_n);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int* piv = a.piv + jb.piv_off;
-  const double2* A = a.abase + jb.a_off;
+  const CT* A = rs_a<CT>(a) + jb.a_off;
   const int lda = jb.lda;
   build_perm(perm, piv, n);
   for (int i = threadIdx.x; i < n; i += blockDim.x) dinv[i] = cinv(A[i + (long long)i * lda]);
   __syncthreads();
   const int c = blockIdx.y * warps + warp;
   if (c >= jb.nrhs) return;
-  double2* b = a.bbase + jb.b_off + (long long)c * jb.ldb;
-  double2* sb = cols + (long long)warp * a.max_n;
+  CT* b = rs_b<CT>(a) + jb.b_off + (long long)c * jb.ldb;
+  CT* sb = cols + (long long)warp * a.max_n;
   for (int i = lane; i < n; i += 32) sb[i] = b[perm[i]];
   __syncwarp();
   for (int k = 0; k < n; ++k) {  // unit lower
-    const double2 bk = sb[k];
-    const double2* lk = A + (long long)k * lda;
+    const CT bk = sb[k];
+    const CT* lk = A + (long long)k * lda;
     for (int i = k + 1 + lane; i < n; i += 32) sb[i] = cfms(lk[i], bk, sb[i]);
     __syncwarp();
   }
   for (int k = n - 1; k >= 0; --k) {  // upper
-    const double2* uk = A + (long long)k * lda;
-    const double2 bk = cmul(sb[k], dinv[k]);
+    const CT* uk = A + (long long)k * lda;
+    const CT bk = cmul(sb[k], dinv[k]);
     __syncwarp();
     if (lane == 0) sb[k] = bk;
     for (int i = lane; i < k; i += 32) sb[i] = cfms(uk[i], bk, sb[i]);
@@ -64,18 +72,19 @@ __global__ void getrs_kernel(const RsLaunch a, int warps) {
   for (int i = lane; i < n; i += 32) b[i] = sb[i];
 }
 
+template <typename CT>
 __global__ void __launch_bounds__(kCtaThreads) getrs_cta_kernel(const RsLaunch a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const RsJob jb = a.jobs[blockIdx.x];
   const int n = jb.n;
   const int c = blockIdx.y;
   if (n > a.max_n || n < 0 || c >= jb.nrhs) return;  // uniform per block
-  double2* x = reinterpret_cast<double2*>(smem_raw);
+  CT* x = reinterpret_cast<CT*>(smem_raw);
   int* perm = reinterpret_cast<int*>(x + a.max_n);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const double2* A = a.abase + jb.a_off;
+  const CT* A = rs_a<CT>(a) + jb.a_off;
   const int lda = jb.lda;
-  double2* b = a.bbase + jb.b_off + (long long)c * jb.ldb;
+  CT* b = rs_b<CT>(a) + jb.b_off + (long long)c * jb.ldb;
   build_perm(perm, a.piv + jb.piv_off, n);
   __syncthreads();
   for (int i = tid; i < n; i += kCtaThreads) x[i] = b[perm[i]];
@@ -84,16 +93,16 @@ __global__ void __launch_bounds__(kCtaThreads) getrs_cta_kernel(const RsLaunch a
   for (int kb = 0; kb < n; kb += 32) {
     const int w = min(32, n - kb);
     if (warp == 0) {
-      double2 xr = lane < w ? x[kb + lane] : make_double2(0.0, 0.0);
+      CT xr = lane < w ? x[kb + lane] : make_c<CT>(0.0, 0.0);
       for (int q = 0; q < w; ++q) {
-        const double2 xq = make_double2(__shfl_sync(0xffffffffu, xr.x, q), __shfl_sync(0xffffffffu, xr.y, q));
+        const CT xq = make_c<CT>(__shfl_sync(0xffffffffu, xr.x, q), __shfl_sync(0xffffffffu, xr.y, q));
         if (lane > q && lane < w) xr = cfms(A[kb + lane + (long long)(kb + q) * lda], xq, xr);
       }
       if (lane < w) x[kb + lane] = xr;
     }
     __syncthreads();
     for (int i = kb + w + tid; i < n; i += kCtaThreads) {
-      double2 acc = x[i];
+      CT acc = x[i];
       for (int q = 0; q < w; ++q) acc = cfms(A[i + (long long)(kb + q) * lda], x[kb + q], acc);
       x[i] = acc;
     }
@@ -103,17 +112,17 @@ __global__ void __launch_bounds__(kCtaThreads) getrs_cta_kernel(const RsLaunch a
   for (int kb = ((n - 1) / 32) * 32; n > 0 && kb >= 0; kb -= 32) {
     const int w = min(32, n - kb);
     if (warp == 0) {
-      double2 xr = lane < w ? x[kb + lane] : make_double2(0.0, 0.0);
+      CT xr = lane < w ? x[kb + lane] : make_c<CT>(0.0, 0.0);
       for (int q = w - 1; q >= 0; --q) {
         if (lane == q) xr = cmul(xr, cinv(A[kb + q + (long long)(kb + q) * lda]));
-        const double2 xq = make_double2(__shfl_sync(0xffffffffu, xr.x, q), __shfl_sync(0xffffffffu, xr.y, q));
+        const CT xq = make_c<CT>(__shfl_sync(0xffffffffu, xr.x, q), __shfl_sync(0xffffffffu, xr.y, q));
         if (lane < q) xr = cfms(A[kb + lane + (long long)(kb + q) * lda], xq, xr);
       }
       if (lane < w) x[kb + lane] = xr;
     }
     __syncthreads();
     for (int i = tid; i < kb; i += kCtaThreads) {
-      double2 acc = x[i];
+      CT acc = x[i];
       for (int q = 0; q < w; ++q) acc = cfms(A[i + (long long)(kb + q) * lda], x[kb + q], acc);
       x[i] = acc;
     }
@@ -124,32 +133,37 @@ __global__ void __launch_bounds__(kCtaThreads) getrs_cta_kernel(const RsLaunch a
 
 }  // namespace
 
-cudaError_t launch_getrs(const RsLaunch& a, cudaStream_t s) {
+template <typename CT>
+cudaError_t getrs_impl(const RsLaunch& a, cudaStream_t s) {
   const int max_n = a.max_n;
   if (a.njobs <= 0 || a.max_rhs <= 0) return cudaSuccess;
   cudaError_t e;
   if (a.max_rhs <= 4) {
-    const size_t smem = (size_t)max_n * (sizeof(double2) + sizeof(int));
+    const size_t smem = (size_t)max_n * (sizeof(CT) + sizeof(int));
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
-    e = cudaFuncSetAttribute(getrs_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(getrs_cta_kernel<CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    getrs_cta_kernel<<<dim3(a.njobs, a.max_rhs), kCtaThreads, smem, s>>>(a);
+    getrs_cta_kernel<CT><<<dim3(a.njobs, a.max_rhs), kCtaThreads, smem, s>>>(a);
     symhss::count_launches(1);
     return cudaGetLastError();
   }
   int warps = kRsMaxWarps;
   size_t smem = 0;
   for (;; warps /= 2) {
-    smem = (size_t)max_n * sizeof(double2) * (1 + warps) + (size_t)max_n * sizeof(int);
+    smem = (size_t)max_n * sizeof(CT) * (1 + warps) + (size_t)max_n * sizeof(int);
     if (smem <= 200 * 1024 || warps == 1) break;
   }
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
-  e = cudaFuncSetAttribute(getrs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = cudaFuncSetAttribute(getrs_kernel<CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid(a.njobs, (a.max_rhs + warps - 1) / warps);
-  getrs_kernel<<<grid, warps * 32, smem, s>>>(a, warps);
+  getrs_kernel<CT><<<grid, warps * 32, smem, s>>>(a, warps);
   symhss::count_launches(1);
   return cudaGetLastError();
+}
+
+cudaError_t launch_getrs(const RsLaunch& a, cudaStream_t s) {
+  return a.abase32 ? getrs_impl<float2>(a, s) : getrs_impl<double2>(a, s);
 }
 
 }  // namespace symhss

@@ -31,22 +31,27 @@ constexpr int kClusterPanelThreads = 256;
 
 struct Cand2 { double v; int i; };
 
+template <typename CT> __device__ __forceinline__ CT* lu_base(const LuLaunch& a);
+template <> __device__ __forceinline__ double2* lu_base<double2>(const LuLaunch& a) { return a.base; }
+template <> __device__ __forceinline__ float2* lu_base<float2>(const LuLaunch& a) { return a.base32; }
+
+template <typename CT>
 __global__ void __launch_bounds__(kPanelThreads) panel_kernel(const LuLaunch a, int j) {
   __shared__ double red[kPanelWarps];
   __shared__ int redi[kPanelWarps];
   __shared__ int s_piv;
   __shared__ double s_pv;
-  __shared__ double2 s_row[kNb];
+  __shared__ CT s_row[kNb];
   const LuJob jb = a.jobs[blockIdx.x];
   const int n = jb.n, ld = jb.ld;
   if (j >= n) return;
   const int w = min(kNb, n - j);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  double2* A = a.base + jb.a_off;
+  CT* A = lu_base<CT>(a) + jb.a_off;
   int* piv = a.piv + jb.piv_off;
   for (int c = 0; c < w; ++c) {
     const int jc = j + c;
-    const double2* col = A + (long long)jc * ld;
+    const CT* col = A + (long long)jc * ld;
     double bv = -1.0;
     int bi = n;
     for (int i = jc + tid; i < n; i += kPanelThreads) {
@@ -74,20 +79,20 @@ __global__ void __launch_bounds__(kPanelThreads) panel_kernel(const LuLaunch a, 
     // an exactly zero pivot column skips the step; every barrier stays unconditional
     const bool zero = (s_pv == 0.0);
     if (!zero && tid < w && p != jc) {
-      double2* cc = A + (long long)(j + tid) * ld;
-      const double2 t = cc[jc];
+      CT* cc = A + (long long)(j + tid) * ld;
+      const CT t = cc[jc];
       cc[jc] = cc[p];
       cc[p] = t;
     }
     __syncthreads();
     if (tid < w) s_row[tid] = A[jc + (long long)(j + tid) * ld];
     __syncthreads();
-    const double2 inv = zero ? make_double2(0.0, 0.0) : cinv(s_row[c]);
+    const CT inv = zero ? make_c<CT>(0.0, 0.0) : cinv(s_row[c]);
     for (int i = jc + 1 + tid; !zero && i < n; i += kPanelThreads) {
-      const double2 l = cmul(A[i + (long long)jc * ld], inv);
+      const CT l = cmul(A[i + (long long)jc * ld], inv);
       A[i + (long long)jc * ld] = l;
       for (int q = c + 1; q < w; ++q) {
-        double2* cq = A + (long long)(j + q) * ld;
+        CT* cq = A + (long long)(j + q) * ld;
         cq[i] = cfms(l, s_row[q], cq[i]);
       }
     }
@@ -98,10 +103,11 @@ __global__ void __launch_bounds__(kPanelThreads) panel_kernel(const LuLaunch a, 
 // Panel factorisation with the panel (rows [j, n) x w columns) staged in shared
 // memory; the pivot search of column c + 1 is fused into the update of column c.
 // THREADS is chosen per launch so that each thread holds about one or two panel rows.
-template <int THREADS>
+template <int THREADS, typename CT>
 __global__ void __launch_bounds__(THREADS) panel_smem_kernel(const LuLaunch a, int j) {
   constexpr int kWarps = THREADS / 32;
-  extern __shared__ __align__(16) double2 P[];  // column-major: P[q * rows + i]
+  extern __shared__ __align__(16) unsigned char p_raw[];
+  CT* P = reinterpret_cast<CT*>(p_raw);  // column-major: P[q * rows + i]
   __shared__ double red[kWarps];
   __shared__ int redi[kWarps];
   __shared__ int s_piv;
@@ -111,7 +117,7 @@ __global__ void __launch_bounds__(THREADS) panel_smem_kernel(const LuLaunch a, i
   if (j >= n) return;  // uniform per block
   const int w = min(kNb, n - j), rows = n - j;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  double2* A = a.base + jb.a_off;
+  CT* A = lu_base<CT>(a) + jb.a_off;
   int* piv = a.piv + jb.piv_off;
   for (int e = tid; e < rows * w; e += THREADS) {
     const int i = e % rows, q = e / rows;
@@ -145,17 +151,17 @@ __global__ void __launch_bounds__(THREADS) panel_smem_kernel(const LuLaunch a, i
       }
     }
     if (!zero && tid < w && p != c) {
-      const double2 t = P[tid * rows + c];
+      const CT t = P[tid * rows + c];
       P[tid * rows + c] = P[tid * rows + p];
       P[tid * rows + p] = t;
     }
     __syncthreads();
-    const double2 inv = zero ? make_double2(0.0, 0.0) : cinv(P[c * rows + c]);
+    const CT inv = zero ? make_c<CT>(0.0, 0.0) : cinv(P[c * rows + c]);
     bv = -1.0;
     bi = rows;
     for (int i = c + 1 + tid; i < rows; i += THREADS) {
       if (!zero) {
-        const double2 l = cmul(P[c * rows + i], inv);
+        const CT l = cmul(P[c * rows + i], inv);
         P[c * rows + i] = l;
         for (int q = c + 1; q < w; ++q) P[q * rows + i] = cfms(l, P[q * rows + c], P[q * rows + i]);
       }
@@ -295,8 +301,9 @@ __global__ void __launch_bounds__(kClusterPanelThreads) panel_cluster_kernel(con
 // permutation of that row set, built once per block, so each column is permuted by
 // a single gather (lane l ends with the value of row rows[l]); lanes 0..w-1 hold
 // rows j..j+w-1 and then solve the unit-lower 16 x 16 system with shuffles.
+template <typename CT>
 __global__ void __launch_bounds__(256) swap_trsm_warp_kernel(const LuLaunch a, int j) {
-  __shared__ double2 l11[kNb][kNb];
+  __shared__ CT l11[kNb][kNb];
   __shared__ int rows_s[2 * kNb];   // row set: j..j+w-1, then the outside pivot rows
   __shared__ int src_s[2 * kNb];    // lane l takes its new value from row src_s[l]
   __shared__ int nrows_s;
@@ -304,7 +311,7 @@ __global__ void __launch_bounds__(256) swap_trsm_warp_kernel(const LuLaunch a, i
   const int n = jb.n, ld = jb.ld;
   if (j >= n) return;  // uniform per block
   const int w = min(kNb, n - j);
-  double2* A = a.base + jb.a_off;
+  CT* A = lu_base<CT>(a) + jb.a_off;
   const int* piv = a.piv + jb.piv_off;
   for (int e = threadIdx.x; e < w * w; e += 256) {
     const int r = e % w, c = e / w;
@@ -342,14 +349,14 @@ __global__ void __launch_bounds__(256) swap_trsm_warp_kernel(const LuLaunch a, i
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int col = blockIdx.y * 8 + warp;
   if (col >= n || (col >= j && col < j + w)) return;  // uniform per warp
-  double2* cc = A + (long long)col * ld;
+  CT* cc = A + (long long)col * ld;
   const int cnt = nrows_s;
-  double2 x = lane < cnt ? cc[src_s[lane]] : make_double2(0.0, 0.0);
+  CT x = lane < cnt ? cc[src_s[lane]] : make_c<CT>(0.0, 0.0);
   __syncwarp();
   if (lane >= w && lane < cnt) cc[rows_s[lane]] = x;
   if (col >= j + w) {
     for (int c = 0; c < w; ++c) {
-      const double2 xc = make_double2(__shfl_sync(0xffffffffu, x.x, c), __shfl_sync(0xffffffffu, x.y, c));
+      const CT xc = make_c<CT>(__shfl_sync(0xffffffffu, x.x, c), __shfl_sync(0xffffffffu, x.y, c));
       if (lane > c && lane < w) x = cfms(l11[lane][c], xc, x);
     }
   }
@@ -358,9 +365,10 @@ __global__ void __launch_bounds__(256) swap_trsm_warp_kernel(const LuLaunch a, i
 
 // A22 -= L21 U12 for the tile (blockIdx.y, blockIdx.z) of every matrix, over the trailing
 // columns [j + w + cskip, j + w + cskip + clen) (clen < 0: to the last column)
+template <typename CT>
 __global__ void __launch_bounds__(256) update_kernel(const LuLaunch a, int j, int cskip, int clen) {
-  __shared__ double2 at[kNb][kTs];      // L21 tile, transposed: at[c][r]
-  __shared__ double2 bt[kNb][kTs];      // U12 tile: bt[c][col]
+  __shared__ CT at[kNb][kTs];      // L21 tile, transposed: at[c][r]
+  __shared__ CT bt[kNb][kTs];      // U12 tile: bt[c][col]
   const LuJob jb = a.jobs[blockIdx.x];
   const int n = jb.n, ld = jb.ld;
   const int w = min(kNb, n - j);
@@ -368,26 +376,26 @@ __global__ void __launch_bounds__(256) update_kernel(const LuLaunch a, int j, in
   const int r0 = s + blockIdx.y * kTs, c0 = s + cskip + blockIdx.z * kTs;
   const int cend = clen < 0 ? n : min(n, s + cskip + clen);
   if (j >= n || r0 >= n || c0 >= cend) return;
-  double2* A = a.base + jb.a_off;
+  CT* A = lu_base<CT>(a) + jb.a_off;
   const int tid = threadIdx.x;
   for (int e = tid; e < kNb * kTs; e += 256) {
     const int r = e % kTs, c = e / kTs;
-    at[c][r] = (r0 + r < n && c < w) ? A[r0 + r + (long long)(j + c) * ld] : make_double2(0.0, 0.0);
+    at[c][r] = (r0 + r < n && c < w) ? A[r0 + r + (long long)(j + c) * ld] : make_c<CT>(0.0, 0.0);
     const int cc = e % kNb, col = e / kNb;
-    bt[cc][col] = (c0 + col < cend && cc < w) ? A[j + cc + (long long)(c0 + col) * ld] : make_double2(0.0, 0.0);
+    bt[cc][col] = (c0 + col < cend && cc < w) ? A[j + cc + (long long)(c0 + col) * ld] : make_c<CT>(0.0, 0.0);
   }
   __syncthreads();
   const int tx = tid & 31, ty = tid >> 5;  // row tx, columns ty + 8q
   const int row = r0 + tx;
-  double2 acc[4];
+  CT acc[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int col = c0 + ty + 8 * q;
-    acc[q] = (row < n && col < cend) ? A[row + (long long)col * ld] : make_double2(0.0, 0.0);
+    acc[q] = (row < n && col < cend) ? A[row + (long long)col * ld] : make_c<CT>(0.0, 0.0);
   }
 #pragma unroll
   for (int c = 0; c < kNb; ++c) {
-    const double2 l = at[c][tx];
+    const CT l = at[c][tx];
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[q] = cfms(l, bt[c][ty + 8 * q], acc[q]);
   }
@@ -438,24 +446,25 @@ LookAhead* look_ahead_streams() {
 
 }  // namespace
 
-cudaError_t launch_getrf(const LuLaunch& a, cudaStream_t s) {
+template <typename CT>
+cudaError_t getrf_impl(const LuLaunch& a, cudaStream_t s) {
   if (a.njobs <= 0 || a.max_n <= 0) return cudaSuccess;
   zero_info_kernel<<<(a.njobs + 127) / 128, 128, 0, s>>>(a.info, a.jobs, a.njobs);
   symhss::count_launches(1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // panels of up to 780 rows fit in shared memory (780 x 16 x 16 B = 195 KB)
-  const size_t panel_smem = (size_t)a.max_n * kNb * sizeof(double2);
+  const size_t panel_smem = (size_t)a.max_n * kNb * sizeof(CT);
   const bool smem_panel = panel_smem <= 200 * 1024;
   const int pcap = a.panel_threads >= 1024 ? 1024 : (a.panel_threads >= 512 ? 512 : 256);
   const int pthreads = std::min(pcap, a.max_n > 512 ? 1024 : (a.max_n > 256 ? 512 : 256));
   if (smem_panel) {
     // every variant the loop may pick as the panel shrinks
-    e = cudaFuncSetAttribute(panel_smem_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem);
+    e = cudaFuncSetAttribute(panel_smem_kernel<256, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem);
     if (e == cudaSuccess && pthreads >= 512)
-      e = cudaFuncSetAttribute(panel_smem_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem);
+      e = cudaFuncSetAttribute(panel_smem_kernel<512, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem);
     if (e == cudaSuccess && pthreads >= 1024)
-      e = cudaFuncSetAttribute(panel_smem_kernel<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem);
+      e = cudaFuncSetAttribute(panel_smem_kernel<1024, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem);
     if (e != cudaSuccess) return e;
   }
   const int ncolblk = (a.max_n + 7) / 8;
@@ -467,7 +476,7 @@ cudaError_t launch_getrf(const LuLaunch& a, cudaStream_t s) {
   // cluster panels for few large matrices: C blocks per matrix while the batch still leaves
   // SMs free and every block keeps at least 32 panel rows
   int pc = 1;
-  while (pc < 16 && 2 * pc <= a.panel_cluster && a.njobs * 2 * pc <= 148 && a.max_n / (2 * pc) >= 32) pc *= 2;
+  while (sizeof(CT) == sizeof(double2) && pc < 16 && 2 * pc <= a.panel_cluster && a.njobs * 2 * pc <= 148 && a.max_n / (2 * pc) >= 32) pc *= 2;
   const int lmax = (a.max_n + pc - 1) / pc;
   if (pc > 1) {
     e = cudaFuncSetAttribute(panel_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -500,11 +509,11 @@ cudaError_t launch_getrf(const LuLaunch& a, cudaStream_t s) {
     if (smem_panel) {
       // the panel height shrinks with jj: fewer threads once the remaining rows allow it
       const int rows = a.max_n - jj;
-      if (pthreads >= 1024 && rows > 512) panel_smem_kernel<1024><<<a.njobs, 1024, panel_smem, st>>>(a, jj);
-      else if (pthreads >= 512 && rows > 256) panel_smem_kernel<512><<<a.njobs, 512, panel_smem, st>>>(a, jj);
-      else panel_smem_kernel<256><<<a.njobs, 256, panel_smem, st>>>(a, jj);
+      if (pthreads >= 1024 && rows > 512) panel_smem_kernel<1024, CT><<<a.njobs, 1024, panel_smem, st>>>(a, jj);
+      else if (pthreads >= 512 && rows > 256) panel_smem_kernel<512, CT><<<a.njobs, 512, panel_smem, st>>>(a, jj);
+      else panel_smem_kernel<256, CT><<<a.njobs, 256, panel_smem, st>>>(a, jj);
     } else {
-      panel_kernel<<<a.njobs, kPanelThreads, 0, st>>>(a, jj);
+      panel_kernel<CT><<<a.njobs, kPanelThreads, 0, st>>>(a, jj);
     }
     symhss::count_launches(1);
     return cudaGetLastError();
@@ -513,13 +522,13 @@ cudaError_t launch_getrf(const LuLaunch& a, cudaStream_t s) {
   for (int j = 0; j < a.max_n; j += kNb) {
     const int rest = a.max_n - j - kNb;
     if (rest <= 0) continue;
-    swap_trsm_warp_kernel<<<dim3(a.njobs, ncolblk), 256, 0, s>>>(a, j);
+    swap_trsm_warp_kernel<CT><<<dim3(a.njobs, ncolblk), 256, 0, s>>>(a, j);
     symhss::count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int rtiles = (rest + kTs - 1) / kTs;
     const bool split = la != nullptr && rest > kTs;
     // first trailing tile column (all of it when not splitting)
-    update_kernel<<<dim3(a.njobs, rtiles, split ? 1 : rtiles), 256, 0, s>>>(a, j, 0, split ? kTs : -1);
+    update_kernel<CT><<<dim3(a.njobs, rtiles, split ? 1 : rtiles), 256, 0, s>>>(a, j, 0, split ? kTs : -1);
     symhss::count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (!split) {
@@ -531,16 +540,20 @@ cudaError_t launch_getrf(const LuLaunch& a, cudaStream_t s) {
     if ((e = panel(j + kNb, la->side)) != cudaSuccess) return e;
     if ((e = cudaEventRecord(la->done, la->side)) != cudaSuccess) return e;
     const int ctiles = (rest - kTs + kTs - 1) / kTs;
-    update_kernel<<<dim3(a.njobs, rtiles, ctiles), 256, 0, s>>>(a, j, kTs, -1);
+    update_kernel<CT><<<dim3(a.njobs, rtiles, ctiles), 256, 0, s>>>(a, j, kTs, -1);
     symhss::count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(s, la->done, 0)) != cudaSuccess) return e;
   }
   // the last panel's interchanges still have to reach the columns left of it
   const int jlast = ((a.max_n - 1) / kNb) * kNb;
-  swap_trsm_warp_kernel<<<dim3(a.njobs, ncolblk), 256, 0, s>>>(a, jlast);
+  swap_trsm_warp_kernel<CT><<<dim3(a.njobs, ncolblk), 256, 0, s>>>(a, jlast);
   symhss::count_launches(1);
   return cudaGetLastError();
+}
+
+cudaError_t launch_getrf(const LuLaunch& a, cudaStream_t s) {
+  return a.base32 ? getrf_impl<float2>(a, s) : getrf_impl<double2>(a, s);
 }
 
 }  // namespace symhss

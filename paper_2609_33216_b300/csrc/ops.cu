@@ -10,13 +10,67 @@ namespace {
 
 constexpr int kOpsThreads = 256;
 
+template <typename CT> __device__ __forceinline__ CT* bl_out(const BasisLaunch& a);
+template <> __device__ __forceinline__ double2* bl_out<double2>(const BasisLaunch& a) { return a.out; }
+template <> __device__ __forceinline__ float2* bl_out<float2>(const BasisLaunch& a) { return a.out32; }
+template <typename CT> __device__ __forceinline__ const CT* bl_in(const BasisLaunch& a);
+template <> __device__ __forceinline__ const double2* bl_in<double2>(const BasisLaunch& a) { return a.in; }
+template <> __device__ __forceinline__ const float2* bl_in<float2>(const BasisLaunch& a) { return a.in32; }
+
+// out[q[j], c] += in[col0 + j, c] (skeleton rows), out[q[r + i], c] += sum_j T[j, i] in[col0 + j, c]
+// (the other active rows): out += L in with L = R^T in the diagonal-block ordering; every row
+// of the box's block belongs to exactly one part's list, so each is updated by one thread
+__global__ void __launch_bounds__(kOpsThreads) apply_l_kernel(const BasisLaunch a) {
+  const BasisJob jb = a.jobs[blockIdx.x];
+  const double2* in = a.in + jb.in_off;
+  double2* out = a.out + jb.out_off;
+  for (int h = 0; h < 2; ++h) {
+    const BasisPart pt = jb.part[h];
+    const int* q = a.q + pt.q_off;
+    const double2* T = a.T + pt.t_off;
+    const long long cnt = (long long)pt.n * jb.ncols;
+    for (long long e = threadIdx.x + (long long)blockIdx.y * blockDim.x; e < cnt;
+         e += (long long)blockDim.x * gridDim.y) {
+      const int row = (int)(e % pt.n);  // position among the part's pivoted active unknowns
+      const int c = (int)(e / pt.n);
+      const double2* ic = in + (long long)c * jb.ld_in + pt.col0;
+      double2 s;
+      if (row < pt.r) {
+        s = ic[row];
+      } else {
+        const int i = row - pt.r;
+        s = make_double2(0.0, 0.0);
+        for (int j = 0; j < pt.r; ++j) s = cfma(T[j + (long long)i * pt.r], ic[j], s);
+      }
+      double2* o = out + q[row] + (long long)c * jb.ld_out;
+      *o = cadd(*o, s);
+    }
+  }
+}
+
+__global__ void narrow_kernel(const double2* src, float2* dst, long long n) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    dst[e] = make_float2((float)src[e].x, (float)src[e].y);
+}
+
+__global__ void widen_kernel(const float2* src, double2* dst, long long n) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    dst[e] = make_double2((double)src[e].x, (double)src[e].y);
+}
+
+__global__ void axpby_kernel(const double2* x, double2* y, long long n, double a, double b) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    y[e] = make_double2(fma(a, x[e].x, b * y[e].x), fma(a, x[e].y, b * y[e].y));
+}
+
 // dense R^T in the diagonal-block ordering: column col0 + j holds 1 at q[j] and
 // T[j, i] at q[r + i]
+template <typename CT>
 __global__ void __launch_bounds__(kOpsThreads) basis_dense_kernel(const BasisLaunch a) {
   const BasisJob jb = a.jobs[blockIdx.x];
-  double2* out = a.out + jb.out_off;
+  CT* out = bl_out<CT>(a) + jb.out_off;
   const long long total = (long long)jb.size * jb.k;
-  for (long long e = threadIdx.x; e < total; e += blockDim.x) out[e] = make_double2(0.0, 0.0);
+  for (long long e = threadIdx.x; e < total; e += blockDim.x) out[e] = make_c<CT>(0.0, 0.0);
   __syncthreads();
   for (int h = 0; h < 2; ++h) {
     const BasisPart pt = jb.part[h];
@@ -28,17 +82,18 @@ __global__ void __launch_bounds__(kOpsThreads) basis_dense_kernel(const BasisLau
       const int j = (int)(e % pt.r);
       const int i = (int)(e / pt.r);  // 0: skeleton entry, 1..nr: T row
       const int col = pt.col0 + j;
-      if (i == 0) out[q[j] + (long long)col * jb.size] = make_double2(1.0, 0.0);
-      else out[q[pt.r + i - 1] + (long long)col * jb.size] = T[j + (long long)(i - 1) * pt.r];
+      if (i == 0) out[q[j] + (long long)col * jb.size] = make_c<CT>(1.0, 0.0);
+      else out[q[pt.r + i - 1] + (long long)col * jb.size] = to_c<CT>(T[j + (long long)(i - 1) * pt.r]);
     }
   }
 }
 
 // out[col0 + j, c] = in[q[j], c] + sum_i T[j, i] in[q[r + i], c]
+template <typename CT>
 __global__ void __launch_bounds__(kOpsThreads) apply_r_kernel(const BasisLaunch a) {
   const BasisJob jb = a.jobs[blockIdx.x];
-  const double2* in = a.in + jb.in_off;
-  double2* out = a.out + jb.out_off;
+  const CT* in = bl_in<CT>(a) + jb.in_off;
+  CT* out = bl_out<CT>(a) + jb.out_off;
   for (int h = 0; h < 2; ++h) {
     const BasisPart pt = jb.part[h];
     const int* q = a.q + pt.q_off;
@@ -49,9 +104,9 @@ __global__ void __launch_bounds__(kOpsThreads) apply_r_kernel(const BasisLaunch 
          e += (long long)blockDim.x * gridDim.y) {
       const int j = (int)(e % pt.r);
       const int c = (int)(e / pt.r);
-      const double2* ic = in + (long long)c * jb.ld_in;
-      double2 s = ic[q[j]];
-      for (int i = 0; i < nr; ++i) s = cfma(T[j + (long long)i * pt.r], ic[q[pt.r + i]], s);
+      const CT* ic = in + (long long)c * jb.ld_in;
+      CT s = ic[q[j]];
+      for (int i = 0; i < nr; ++i) s = cfma(to_c<CT>(T[j + (long long)i * pt.r]), ic[q[pt.r + i]], s);
       out[pt.col0 + j + (long long)c * jb.ld_out] = s;
     }
   }
@@ -90,16 +145,17 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmLaunch a) {
   }
 }
 
-__global__ void __launch_bounds__(kOpsThreads) copy_kernel(const double2* src, double2* dst,
+template <typename CT>
+__global__ void __launch_bounds__(kOpsThreads) copy_kernel(const CT* src, CT* dst,
                                                            const CopyJob* jobs) {
   const CopyJob jb = jobs[blockIdx.x];
   const long long total = (long long)jb.rows * jb.cols;
   for (long long e = threadIdx.x + (long long)blockIdx.y * blockDim.x; e < total;
        e += (long long)blockDim.x * gridDim.y) {
     const int i = (int)(e % jb.rows), j = (int)(e / jb.rows);
-    double2 v;
+    CT v;
     if (jb.src_off >= 0) v = src[jb.src_off + i + (long long)j * jb.lds];
-    else v = make_double2(i == j ? 1.0 : 0.0, 0.0);
+    else v = make_c<CT>(i == j ? 1.0 : 0.0, 0.0);
     dst[jb.dst_off + i + (long long)j * jb.ldd] = v;
   }
 }
@@ -149,7 +205,8 @@ __global__ void plane_wave_kernel(const PointTable t, const WaveJob* jobs, doubl
 
 cudaError_t launch_basis_dense(const BasisLaunch& a, cudaStream_t s) {
   if (a.njobs <= 0) return cudaSuccess;
-  basis_dense_kernel<<<a.njobs, kOpsThreads, 0, s>>>(a);
+  if (a.out32) basis_dense_kernel<float2><<<a.njobs, kOpsThreads, 0, s>>>(a);
+  else basis_dense_kernel<double2><<<a.njobs, kOpsThreads, 0, s>>>(a);
   symhss::count_launches(1);
   return cudaGetLastError();
 }
@@ -157,7 +214,8 @@ cudaError_t launch_basis_dense(const BasisLaunch& a, cudaStream_t s) {
 cudaError_t launch_apply_r(const BasisLaunch& a, cudaStream_t s) {
   if (a.njobs <= 0) return cudaSuccess;
   dim3 grid(a.njobs, 4);
-  apply_r_kernel<<<grid, kOpsThreads, 0, s>>>(a);
+  if (a.out32) apply_r_kernel<float2><<<grid, kOpsThreads, 0, s>>>(a);
+  else apply_r_kernel<double2><<<grid, kOpsThreads, 0, s>>>(a);
   symhss::count_launches(1);
   return cudaGetLastError();
 }
@@ -174,7 +232,49 @@ cudaError_t launch_copy_blocks(const double2* src, double2* dst, const CopyJob* 
                                cudaStream_t s) {
   if (njobs <= 0) return cudaSuccess;
   dim3 grid(njobs, 4);
-  copy_kernel<<<grid, kOpsThreads, 0, s>>>(src, dst, jobs);
+  copy_kernel<double2><<<grid, kOpsThreads, 0, s>>>(src, dst, jobs);
+  symhss::count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_blocks32(const float2* src, float2* dst, const CopyJob* jobs, int njobs, cudaStream_t s) {
+  if (njobs <= 0) return cudaSuccess;
+  dim3 grid(njobs, 4);
+  copy_kernel<float2><<<grid, kOpsThreads, 0, s>>>(src, dst, jobs);
+  symhss::count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_l(const BasisLaunch& a, cudaStream_t s) {
+  if (a.njobs <= 0) return cudaSuccess;
+  dim3 grid(a.njobs, 4);
+  apply_l_kernel<<<grid, kOpsThreads, 0, s>>>(a);
+  symhss::count_launches(1);
+  return cudaGetLastError();
+}
+
+static int elementwise_blocks(long long n) {
+  const long long b = (n + 255) / 256;
+  return (int)(b < 148 * 16 ? (b > 0 ? b : 1) : 148 * 16);
+}
+
+cudaError_t launch_narrow(const double2* src, float2* dst, long long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  narrow_kernel<<<elementwise_blocks(n), 256, 0, s>>>(src, dst, n);
+  symhss::count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_widen(const float2* src, double2* dst, long long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  widen_kernel<<<elementwise_blocks(n), 256, 0, s>>>(src, dst, n);
+  symhss::count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpby(const double2* x, double2* y, long long n, double a, double b, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  axpby_kernel<<<elementwise_blocks(n), 256, 0, s>>>(x, y, n, a, b);
   symhss::count_launches(1);
   return cudaGetLastError();
 }

@@ -126,8 +126,12 @@ struct Height {
   DevBuf mr, tbuf, permbuf, rankbuf, refbuf, clists, idjobs, slices, skmeta;
   // factor
   DevBuf D, piv, rxpiv, info, X, RX, At, qbuf, flists, lujobs, cjobs;
+  DevBuf Dop;                    // the assembled diagonal blocks (FP64), kept for the matvec
+  DevBuf D32, X32, RX32, At32;   // complex64 work of the mixed-precision factorisation
   // solve
   DevBuf G, FT, TMP, slists;
+  // matvec
+  DevBuf XV, XS, ZV, YS, YV, mlists;
   std::vector<int> h_rank;
 };
 
@@ -167,6 +171,8 @@ struct symhss_s {
   symhss_mlp_s* mlp = nullptr;                    // attached proposer (not owned)
   double prop_margin = 1.15;
   symhss::DevBuf featjobs, feats, mlpout, chkjobs, chkratio;
+  int refine_steps = 2;                           // SYMHSS_MIXED solves
+  symhss::DevBuf rres, rcor, rtmp;                // refinement vectors
 };
 
 namespace symhss {
@@ -1109,7 +1115,19 @@ int assemble_and_lu(symhss_s* h, int t, cudaStream_t s, long long& pairs) {
   la.lookahead = h->tune.lu_lookahead;
   la.panel_threads = h->tune.lu_panel_threads;
   la.panel_cluster = h->tune.lu_panel_cluster;
-  TIMED(SYMHSS_K_GETRF, lu_work, launch_getrf(la, s));
+  // the assembled blocks are the FP64 operator's (leaf blocks, sibling skeleton blocks)
+  CK(H.Dop.ensure(d_total * sizeof(double2)));
+  CK(cudaMemcpyAsync(H.Dop.p, H.D.p, d_total * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+  if (h->prm.precision == SYMHSS_MIXED) {
+    CK(H.D32.ensure(d_total * sizeof(float2)));
+    TIMED(SYMHSS_K_OTHER, 0.0, launch_narrow(H.D.as<double2>(), H.D32.as<float2>(), d_total, s));
+    la.base32 = H.D32.as<float2>();
+    TIMED(SYMHSS_K_GETRF, lu_work, launch_getrf(la, s));
+    // LU factors in FP64 for the solve phase
+    TIMED(SYMHSS_K_OTHER, 0.0, launch_widen(H.D32.as<float2>(), H.D.as<double2>(), d_total, s));
+  } else {
+    TIMED(SYMHSS_K_GETRF, lu_work, launch_getrf(la, s));
+  }
   return SYMHSS_OK;
 }
 
@@ -1192,12 +1210,19 @@ int factor_height(symhss_s* h, int t, cudaStream_t s, long long& pairs) {
   CK(H.X.ensure(x_total * sizeof(double2)));
   CK(H.RX.ensure(rx_total * sizeof(double2)));
   CK(H.At.ensure(rx_total * sizeof(double2)));
+  const bool mixed = h->prm.precision == SYMHSS_MIXED;
+  if (mixed) {
+    CK(H.X32.ensure(x_total * sizeof(float2)));
+    CK(H.RX32.ensure(rx_total * sizeof(float2)));
+    CK(H.At32.ensure(rx_total * sizeof(float2)));
+  }
   // X = D^{-1} L
   BasisLaunch bl;
   bl.q = reinterpret_cast<const int*>(qb + oq);
   bl.T = H.tbuf.as<double2>();
   bl.in = nullptr;
   bl.out = H.X.as<double2>();
+  if (mixed) bl.out32 = H.X32.as<float2>();
   bl.jobs = reinterpret_cast<const BasisJob*>(qb + ol);
   bl.njobs = (int)lbj.size();
   bl.max_cols = max_k;
@@ -1214,6 +1239,10 @@ int factor_height(symhss_s* h, int t, cudaStream_t s, long long& pairs) {
   ra.abase = H.D.as<double2>();
   ra.piv = H.piv.as<int>();
   ra.bbase = H.X.as<double2>();
+  if (mixed) {
+    ra.abase32 = H.D32.as<float2>();
+    ra.bbase32 = H.X32.as<float2>();
+  }
   ra.jobs = reinterpret_cast<const RsJob*>(qb + ox);
   ra.njobs = (int)xs.size();
   ra.max_rhs = max_k;
@@ -1223,12 +1252,17 @@ int factor_height(symhss_s* h, int t, cudaStream_t s, long long& pairs) {
   BasisLaunch br = bl;
   br.in = H.X.as<double2>();
   br.out = H.RX.as<double2>();
+  if (mixed) {
+    br.in32 = H.X32.as<float2>();
+    br.out32 = H.RX32.as<float2>();
+  }
   br.jobs = reinterpret_cast<const BasisJob*>(qb + orr);
   TIMED(SYMHSS_K_OTHER, w_rx, launch_apply_r(br, s));
   // Atilde = (R X)^{-1}
   CK(H.rxpiv.ensure(rxpiv_total * sizeof(int)));
   LuLaunch la;
   la.base = H.RX.as<double2>();
+  if (mixed) la.base32 = H.RX32.as<float2>();
   la.piv = H.rxpiv.as<int>();
   la.info = H.info.as<int>();
   la.jobs = reinterpret_cast<const LuJob*>(qb + orl);
@@ -1239,17 +1273,29 @@ int factor_height(symhss_s* h, int t, cudaStream_t s, long long& pairs) {
   la.panel_threads = h->tune.lu_panel_threads;
   la.panel_cluster = h->tune.lu_panel_cluster;
   TIMED(SYMHSS_K_GETRF, w_rxlu, launch_getrf(la, s));
-  TIMED(SYMHSS_K_OTHER, 0.0, launch_copy_blocks(nullptr, H.At.as<double2>(),
-                                                reinterpret_cast<const CopyJob*>(qb + oe), (int)eye.size(), s));
+  if (mixed)
+    TIMED(SYMHSS_K_OTHER, 0.0, launch_copy_blocks32(nullptr, H.At32.as<float2>(),
+                                                    reinterpret_cast<const CopyJob*>(qb + oe), (int)eye.size(), s));
+  else
+    TIMED(SYMHSS_K_OTHER, 0.0, launch_copy_blocks(nullptr, H.At.as<double2>(),
+                                                  reinterpret_cast<const CopyJob*>(qb + oe), (int)eye.size(), s));
   RsLaunch rb;
   rb.abase = H.RX.as<double2>();
   rb.piv = H.rxpiv.as<int>();
   rb.bbase = H.At.as<double2>();
+  if (mixed) {
+    rb.abase32 = H.RX32.as<float2>();
+    rb.bbase32 = H.At32.as<float2>();
+  }
   rb.jobs = reinterpret_cast<const RsJob*>(qb + oa);
   rb.njobs = (int)ats.size();
   rb.max_rhs = max_k;
   rb.max_n = max_k;
   TIMED(SYMHSS_K_GETRS, w_at, launch_getrs(rb, s));
+  if (mixed) {  // X and Atilde in FP64 for the parents' blocks and the solve phase
+    TIMED(SYMHSS_K_OTHER, 0.0, launch_widen(H.X32.as<float2>(), H.X.as<double2>(), x_total, s));
+    TIMED(SYMHSS_K_OTHER, 0.0, launch_widen(H.At32.as<float2>(), H.At.as<double2>(), rx_total, s));
+  }
   return SYMHSS_OK;
 }
 
@@ -1274,7 +1320,7 @@ int validate_params(const symhss_params* p) {
   if (p->leaf < 1 || p->nproxy < 8 || !(p->proxy_factor > 1.0) || !std::isfinite(p->proxy_factor))
     return SYMHSS_ERR_INVALID;
   if (p->mode != SYMHSS_SYM && p->mode != SYMHSS_NONSYM) return SYMHSS_ERR_INVALID;
-  if (p->precision != SYMHSS_FP64) return SYMHSS_ERR_INVALID;
+  if (p->precision != SYMHSS_FP64 && p->precision != SYMHSS_MIXED) return SYMHSS_ERR_INVALID;
   if (p->fixed_rank_kL < 0 || (p->fixed_rank_kL > 0 && !(p->rank_scale_a >= 1.0))) return SYMHSS_ERR_INVALID;
   if (p->oversample < 0) return SYMHSS_ERR_INVALID;
   if (p->formulation != SYMHSS_MULLER && p->formulation != SYMHSS_PMCHWT && p->formulation != SYMHSS_BM)
@@ -1563,174 +1609,372 @@ int symhss_rhs_plane_wave(symhss_t h, double angle, void* rhs, void* stream) {
   return SYMHSS_OK;
 }
 
+}  // extern "C"
+
+namespace symhss {
+namespace {
+
+// One application of the factorisation's inverse: x = B^{-1} f (Sec. 4.2 up / down pass).
+int solve_core(symhss_s* h, const double2* f, double2* xo, int nrhs, cudaStream_t s) {
+  const long long ldv = 2LL * h->ntot;
+  (void)ldv;
+    std::vector<BoxRef> refs;
+  // up pass: g = D^{-1} f, f~ = Atilde R g, from the leaves to every root
+  for (int t = 0; t <= h->maxdepth; ++t) {
+    Height& H = h->heights[t];
+    height_boxes(h, t, true, refs);
+    if (refs.empty()) continue;
+    long long g_total = 0, ft_total = 0;
+    for (const BoxRef& rf : refs) {
+      HBox& bx = *rf.bx;
+      const bool root = rf.l == 0;
+      bx.g_off = g_total;
+      g_total += (long long)bx.size * nrhs;
+      bx.ft_off = ft_total;
+      ft_total += (long long)(root ? 0 : bx.k) * nrhs;
+    }
+    CK(H.G.ensure(g_total * sizeof(double2)));
+    CK(H.FT.ensure(ft_total * sizeof(double2)));
+    CK(H.TMP.ensure(ft_total * sizeof(double2)));
+    Packer pk;
+    std::vector<LeafJob> lj;
+    std::vector<CopyJob> cj;
+    std::vector<RsJob> rs;
+    std::vector<BasisJob> bj;
+    std::vector<GemmJob> gj;
+    int max_n = 1;
+    if (t == 0) leaf_jobs(h, lj);
+    for (const BoxRef& rf : refs) {
+      const HBox& bx = *rf.bx;
+      if (t > 0) {
+        const auto& kids = h->probs[rf.p].levels[rf.l + 1];
+        const HBox& c1 = kids[bx.child[0]];
+        const HBox& c2 = kids[bx.child[1]];
+        CopyJob c;
+        c.src_off = c1.ft_off; c.dst_off = bx.g_off; c.rows = c1.k; c.cols = nrhs; c.lds = c1.k; c.ldd = bx.size;
+        cj.push_back(c);
+        c.src_off = c2.ft_off; c.dst_off = bx.g_off + c1.k; c.rows = c2.k; c.lds = c2.k;
+        cj.push_back(c);
+      }
+      RsJob r;
+      r.a_off = bx.d_off; r.n = bx.size; r.lda = bx.size; r.piv_off = bx.piv_off;
+      r.b_off = bx.g_off; r.ldb = bx.size; r.nrhs = nrhs;
+      rs.push_back(r);
+      max_n = std::max(max_n, bx.size);
+      if (rf.l > 0) {
+        BasisJob b{};
+        for (int p = 0; p < 2; ++p) {
+          b.part[p].q_off = bx.q_off[p]; b.part[p].t_off = bx.t_off[p];
+          b.part[p].n = (int)bx.perm[p].size(); b.part[p].r = bx.rank[p];
+          b.part[p].col0 = p == 0 ? 0 : bx.rank[0];
+        }
+        b.size = bx.size; b.k = bx.k;
+        b.in_off = bx.g_off; b.ld_in = bx.size; b.out_off = bx.ft_off; b.ld_out = bx.k; b.ncols = nrhs;
+        bj.push_back(b);
+        GemmJob gmm;
+        gmm.a_off = bx.rx_off; gmm.lda = bx.k;
+        gmm.b_off = bx.ft_off; gmm.ldb = bx.k;
+        gmm.c_off = bx.ft_off; gmm.ldc = bx.k;
+        gmm.m = bx.k; gmm.n = nrhs; gmm.k = bx.k; gmm.alpha = 1.0; gmm.beta = 0.0;
+        gj.push_back(gmm);
+      }
+    }
+    const size_t olj = pk.add(lj), ocj = pk.add(cj), ors = pk.add(rs), obj = pk.add(bj), ogj = pk.add(gj);
+    CK(pk.upload(H.slists, s));
+    char* sb = H.slists.as<char>();
+    if (t == 0)
+      TIMED(SYMHSS_K_OTHER, 0.0, launch_leaf_gather(f, ldv, H.G.as<double2>(),
+                                                    reinterpret_cast<const LeafJob*>(sb + olj), (int)lj.size(),
+                                                    nrhs, s));
+    else
+      TIMED(SYMHSS_K_OTHER, 0.0, launch_copy_blocks(h->heights[t - 1].FT.as<double2>(), H.G.as<double2>(),
+                                                    reinterpret_cast<const CopyJob*>(sb + ocj), (int)cj.size(),
+                                                    s));
+    double w_g = 0, w_up = 0;
+    for (const BoxRef& rf : refs) {
+      const HBox& bx = *rf.bx;
+      w_g += 8.0 * (double)bx.size * bx.size * nrhs;
+      if (rf.l > 0) w_up += 8.0 * (double)bx.k * (double)(bx.perm[0].size() + bx.perm[1].size() + bx.k) * nrhs;
+    }
+    RsLaunch ra;
+    ra.abase = H.D.as<double2>(); ra.piv = H.piv.as<int>(); ra.bbase = H.G.as<double2>();
+    ra.jobs = reinterpret_cast<const RsJob*>(sb + ors); ra.njobs = (int)rs.size();
+    ra.max_rhs = nrhs; ra.max_n = max_n;
+    TIMED(SYMHSS_K_GETRS, w_g, launch_getrs(ra, s));
+    if (!bj.empty()) {
+      // tmp = R g ; f~ = Atilde tmp
+      BasisLaunch ba;
+      ba.q = reinterpret_cast<const int*>(H.qbuf.p);
+      ba.T = H.tbuf.as<double2>();
+      ba.in = H.G.as<double2>();
+      ba.out = H.TMP.as<double2>();
+      ba.jobs = reinterpret_cast<const BasisJob*>(sb + obj);
+      ba.njobs = (int)bj.size();
+      ba.max_cols = nrhs;
+      TIMED(SYMHSS_K_OTHER, w_up, launch_apply_r(ba, s));
+      GemmLaunch ga;
+      ga.A = H.At.as<double2>(); ga.B = H.TMP.as<double2>(); ga.C = H.FT.as<double2>();
+      ga.jobs = reinterpret_cast<const GemmJob*>(sb + ogj); ga.njobs = (int)gj.size();
+      TIMED(SYMHSS_K_OTHER, 0.0, launch_gemm(ga, s));
+    }
+  }
+  // down pass: x_c = g_c - X_c (f~_c - Atilde_c y_c), parents at height t + 1
+  for (int t = h->maxdepth - 1; t >= 0; --t) {
+    Height& H = h->heights[t];
+    Height& HP = h->heights[t + 1];
+    std::vector<GemmJob> g1, g2;
+    for (Problem& P : h->probs) {
+      if (P.depth <= t) continue;
+      const int l = P.depth - t;
+      for (const HBox& par : P.levels[l - 1]) {
+        int row0 = 0;
+        for (int c = 0; c < 2; ++c) {
+          const HBox& bx = P.levels[l][par.child[c]];
+          GemmJob a;
+          a.a_off = bx.rx_off; a.lda = bx.k;
+          a.b_off = par.g_off + row0; a.ldb = par.size;
+          a.c_off = bx.ft_off; a.ldc = bx.k;
+          a.m = bx.k; a.n = nrhs; a.k = bx.k; a.alpha = -1.0; a.beta = 1.0;
+          g1.push_back(a);
+          GemmJob b;
+          b.a_off = bx.x_off; b.lda = bx.size;
+          b.b_off = bx.ft_off; b.ldb = bx.k;
+          b.c_off = bx.g_off; b.ldc = bx.size;
+          b.m = bx.size; b.n = nrhs; b.k = bx.k; b.alpha = -1.0; b.beta = 1.0;
+          g2.push_back(b);
+          row0 += bx.k;
+        }
+      }
+    }
+    if (g1.empty()) continue;
+    Packer pk;
+    const size_t o1 = pk.add(g1), o2 = pk.add(g2);
+    CK(pk.upload(H.slists, s));
+    char* sb = H.slists.as<char>();
+    GemmLaunch ga;
+    ga.A = H.At.as<double2>(); ga.B = HP.G.as<double2>(); ga.C = H.FT.as<double2>();
+    ga.jobs = reinterpret_cast<const GemmJob*>(sb + o1); ga.njobs = (int)g1.size();
+    double w_dn = 0;
+    for (const auto& j : g1) w_dn += 8.0 * (double)j.m * j.n * j.k;
+    for (const auto& j : g2) w_dn += 8.0 * (double)j.m * j.n * j.k;
+    TIMED(SYMHSS_K_OTHER, w_dn, launch_gemm(ga, s));
+    GemmLaunch gb;
+    gb.A = H.X.as<double2>(); gb.B = H.FT.as<double2>(); gb.C = H.G.as<double2>();
+    gb.jobs = reinterpret_cast<const GemmJob*>(sb + o2); gb.njobs = (int)g2.size();
+    TIMED(SYMHSS_K_OTHER, 0.0, launch_gemm(gb, s));
+  }
+  {
+    // the leaf lists of height 0 were overwritten by the down pass: upload them again
+    std::vector<LeafJob> lj;
+    leaf_jobs(h, lj);
+    Packer pk;
+    const size_t o = pk.add(lj);
+    Height& H0 = h->heights[0];
+    DevBuf& lb = h->maxdepth > 0 ? h->heights[h->maxdepth].slists : H0.slists;
+    CK(pk.upload(lb, s));
+    TIMED(SYMHSS_K_OTHER, 0.0, launch_leaf_scatter(H0.G.as<double2>(), xo, ldv,
+                           reinterpret_cast<const LeafJob*>(lb.as<char>() + o), (int)lj.size(), nrhs, s));
+  }
+  return SYMHSS_OK;
+}
+
+// y = A_hss x with the kept FP64 blocks and the ID interpolation operators: an up pass of
+// skeleton values (xs = R xv), the sibling skeleton blocks at every parent (zv = D_off xv),
+// a down pass (yv = zv + L ys_parent; ys_child = rows of yv) and the leaf blocks.
+int matvec_core(symhss_s* h, const double2* xin, double2* yout, int nrhs, cudaStream_t s) {
+  const long long ldv = 2LL * h->ntot;
+  std::vector<BoxRef> refs;
+  // offsets: size-sized and k-sized vectors per box and height
+  for (int t = 0; t <= h->maxdepth; ++t) {
+    Height& H = h->heights[t];
+    height_boxes(h, t, true, refs);
+    long long v_total = 0, k_total = 0;
+    for (const BoxRef& rf : refs) {
+      HBox& bx = *rf.bx;
+      bx.g_off = v_total;
+      v_total += (long long)bx.size * nrhs;
+      bx.ft_off = k_total;
+      k_total += (long long)(rf.l == 0 ? 0 : bx.k) * nrhs;
+    }
+    for (DevBuf* b : {&H.XV, &H.ZV, &H.YV}) CK(b->ensure(v_total * sizeof(double2)));
+    for (DevBuf* b : {&H.XS, &H.YS}) CK(b->ensure(k_total * sizeof(double2)));
+  }
+  // up pass
+  for (int t = 0; t <= h->maxdepth; ++t) {
+    Height& H = h->heights[t];
+    height_boxes(h, t, true, refs);
+    if (refs.empty()) continue;
+    std::vector<LeafJob> lj;
+    std::vector<CopyJob> cj;
+    std::vector<BasisJob> bj;
+    std::vector<GemmJob> gj;
+    if (t == 0) leaf_jobs(h, lj);
+    for (const BoxRef& rf : refs) {
+      const HBox& bx = *rf.bx;
+      if (t > 0) {
+        const auto& kids = h->probs[rf.p].levels[rf.l + 1];
+        const HBox& c1 = kids[bx.child[0]];
+        const HBox& c2 = kids[bx.child[1]];
+        CopyJob c;
+        c.src_off = c1.ft_off; c.dst_off = bx.g_off; c.rows = c1.k; c.cols = nrhs; c.lds = c1.k; c.ldd = bx.size;
+        cj.push_back(c);
+        c.src_off = c2.ft_off; c.dst_off = bx.g_off + c1.k; c.rows = c2.k; c.lds = c2.k;
+        cj.push_back(c);
+        // sibling skeleton blocks of the parent: zv = [0 D12; D21 0] xv
+        GemmJob g;
+        g.a_off = bx.d_off + (long long)c1.k * bx.size; g.lda = bx.size;
+        g.b_off = bx.g_off + c1.k; g.ldb = bx.size;
+        g.c_off = bx.g_off; g.ldc = bx.size;
+        g.m = c1.k; g.n = nrhs; g.k = c2.k; g.alpha = 1.0; g.beta = 0.0;
+        gj.push_back(g);
+        g.a_off = bx.d_off + c1.k; g.b_off = bx.g_off; g.c_off = bx.g_off + c1.k;
+        g.m = c2.k; g.k = c1.k;
+        gj.push_back(g);
+      } else {
+        // leaf block: zv = D xv (the down pass adds L ys)
+        GemmJob g;
+        g.a_off = bx.d_off; g.lda = bx.size; g.b_off = bx.g_off; g.ldb = bx.size;
+        g.c_off = bx.g_off; g.ldc = bx.size; g.m = bx.size; g.n = nrhs; g.k = bx.size;
+        g.alpha = 1.0; g.beta = 0.0;
+        gj.push_back(g);
+      }
+      if (rf.l > 0) {
+        BasisJob b{};
+        for (int p = 0; p < 2; ++p) {
+          b.part[p].q_off = bx.q_off[p]; b.part[p].t_off = bx.t_off[p];
+          b.part[p].n = (int)bx.perm[p].size(); b.part[p].r = bx.rank[p];
+          b.part[p].col0 = p == 0 ? 0 : bx.rank[0];
+        }
+        b.size = bx.size; b.k = bx.k;
+        b.in_off = bx.g_off; b.ld_in = bx.size; b.out_off = bx.ft_off; b.ld_out = bx.k; b.ncols = nrhs;
+        bj.push_back(b);
+      }
+    }
+    Packer pk;
+    const size_t olj = pk.add(lj), ocj = pk.add(cj), obj = pk.add(bj), ogj = pk.add(gj);
+    CK(pk.upload(H.mlists, s));
+    char* sb = H.mlists.as<char>();
+    if (t == 0)
+      CK(launch_leaf_gather(xin, ldv, H.XV.as<double2>(), reinterpret_cast<const LeafJob*>(sb + olj), (int)lj.size(),
+                            nrhs, s));
+    else
+      CK(launch_copy_blocks(h->heights[t - 1].XS.as<double2>(), H.XV.as<double2>(),
+                            reinterpret_cast<const CopyJob*>(sb + ocj), (int)cj.size(), s));
+    GemmLaunch ga;
+    ga.A = H.Dop.as<double2>(); ga.B = H.XV.as<double2>(); ga.C = H.ZV.as<double2>();
+    ga.jobs = reinterpret_cast<const GemmJob*>(sb + ogj); ga.njobs = (int)gj.size();
+    CK(launch_gemm(ga, s));
+    if (!bj.empty()) {
+      BasisLaunch ba;
+      ba.q = reinterpret_cast<const int*>(H.qbuf.p);
+      ba.T = H.tbuf.as<double2>();
+      ba.in = H.XV.as<double2>();
+      ba.out = H.XS.as<double2>();
+      ba.jobs = reinterpret_cast<const BasisJob*>(sb + obj);
+      ba.njobs = (int)bj.size();
+      ba.max_cols = nrhs;
+      CK(launch_apply_r(ba, s));
+    }
+  }
+  // down pass: yv = zv + L ys (non-root), children's ys = their rows of yv
+  for (int t = h->maxdepth; t >= 0; --t) {
+    Height& H = h->heights[t];
+    height_boxes(h, t, true, refs);
+    if (refs.empty()) continue;
+    std::vector<BasisJob> lbj;
+    std::vector<CopyJob> cz, cd;
+    for (const BoxRef& rf : refs) {
+      const HBox& bx = *rf.bx;
+      CopyJob c;
+      c.src_off = bx.g_off; c.dst_off = bx.g_off; c.rows = bx.size; c.cols = nrhs; c.lds = bx.size; c.ldd = bx.size;
+      cz.push_back(c);
+      if (rf.l > 0) {
+        BasisJob b{};
+        for (int p = 0; p < 2; ++p) {
+          b.part[p].q_off = bx.rq_off[p]; b.part[p].t_off = bx.rt_off[p];
+          b.part[p].n = (int)bx.rperm[p].size(); b.part[p].r = bx.rrank[p];
+          b.part[p].col0 = p == 0 ? 0 : bx.rrank[0];
+        }
+        b.size = bx.size; b.k = bx.k;
+        b.in_off = bx.ft_off; b.ld_in = bx.k; b.out_off = bx.g_off; b.ld_out = bx.size; b.ncols = nrhs;
+        lbj.push_back(b);
+      }
+      if (t > 0) {
+        const auto& kids = h->probs[rf.p].levels[rf.l + 1];
+        const HBox& c1 = kids[bx.child[0]];
+        const HBox& c2 = kids[bx.child[1]];
+        c.src_off = bx.g_off; c.dst_off = c1.ft_off; c.rows = c1.k; c.cols = nrhs; c.lds = bx.size; c.ldd = c1.k;
+        cd.push_back(c);
+        c.src_off = bx.g_off + c1.k; c.dst_off = c2.ft_off; c.rows = c2.k; c.lds = bx.size; c.ldd = c2.k;
+        cd.push_back(c);
+      }
+    }
+    Packer pk;
+    const size_t ol = pk.add(lbj), oz = pk.add(cz), od = pk.add(cd);
+    CK(pk.upload(H.mlists, s));
+    char* sb = H.mlists.as<char>();
+    // yv = zv (+ L ys)
+    CK(launch_copy_blocks(H.ZV.as<double2>(), H.YV.as<double2>(), reinterpret_cast<const CopyJob*>(sb + oz),
+                          (int)cz.size(), s));
+    if (!lbj.empty()) {
+      BasisLaunch bl;
+      bl.q = reinterpret_cast<const int*>(H.qbuf.p);
+      bl.T = H.tbuf.as<double2>();
+      bl.in = H.YS.as<double2>();
+      bl.out = H.YV.as<double2>();
+      bl.jobs = reinterpret_cast<const BasisJob*>(sb + ol);
+      bl.njobs = (int)lbj.size();
+      bl.max_cols = nrhs;
+      CK(launch_apply_l(bl, s));  // yv += L ys
+    }
+    if (t > 0)
+      CK(launch_copy_blocks(H.YV.as<double2>(), h->heights[t - 1].YS.as<double2>(),
+                            reinterpret_cast<const CopyJob*>(sb + od), (int)cd.size(), s));
+  }
+  {
+    std::vector<LeafJob> lj;
+    leaf_jobs(h, lj);
+    Packer pk;
+    const size_t o = pk.add(lj);
+    DevBuf& lb = h->maxdepth > 0 ? h->heights[h->maxdepth].mlists : h->heights[0].mlists;
+    CK(pk.upload(lb, s));
+    CK(launch_leaf_scatter(h->heights[0].YV.as<double2>(), yout, ldv,
+                           reinterpret_cast<const LeafJob*>(lb.as<char>() + o), (int)lj.size(), nrhs, s));
+  }
+  return SYMHSS_OK;
+}
+
+}  // namespace
+}  // namespace symhss
+
+extern "C" {
+
 int symhss_solve(symhss_t h, const void* rhs, void* x, int nrhs, void* stream) {
   if (!h || !rhs || !x || nrhs < 1) return SYMHSS_ERR_INVALID;
   if (!h->factored) return SYMHSS_ERR_STATE;
   cudaStream_t s = (cudaStream_t)stream;
-  const long long ldv = 2LL * h->ntot;
   const double2* f = reinterpret_cast<const double2*>(rhs);
   double2* xo = reinterpret_cast<double2*>(x);
   try {
     CK(cudaEventRecord(h->ev[0], s));
-    std::vector<BoxRef> refs;
-    // up pass: g = D^{-1} f, f~ = Atilde R g, from the leaves to every root
-    for (int t = 0; t <= h->maxdepth; ++t) {
-      Height& H = h->heights[t];
-      height_boxes(h, t, true, refs);
-      if (refs.empty()) continue;
-      long long g_total = 0, ft_total = 0;
-      for (const BoxRef& rf : refs) {
-        HBox& bx = *rf.bx;
-        const bool root = rf.l == 0;
-        bx.g_off = g_total;
-        g_total += (long long)bx.size * nrhs;
-        bx.ft_off = ft_total;
-        ft_total += (long long)(root ? 0 : bx.k) * nrhs;
+    int rc = solve_core(h, f, xo, nrhs, s);
+    if (rc) return rc;
+    if (h->prm.precision == SYMHSS_MIXED && h->refine_steps > 0) {
+      // x <- x + B^{-1} (f - A_hss x), A_hss the FP64 compressed operator
+      const long long len = 2LL * h->ntot * nrhs;
+      CK(h->rres.ensure(len * sizeof(double2)));
+      CK(h->rcor.ensure(len * sizeof(double2)));
+      for (int it = 0; it < h->refine_steps; ++it) {
+        rc = matvec_core(h, xo, h->rres.as<double2>(), nrhs, s);
+        if (rc) return rc;
+        TIMED(SYMHSS_K_OTHER, 0.0, launch_axpby(f, h->rres.as<double2>(), len, 1.0, -1.0, s));
+        rc = solve_core(h, h->rres.as<double2>(), h->rcor.as<double2>(), nrhs, s);
+        if (rc) return rc;
+        TIMED(SYMHSS_K_OTHER, 0.0, launch_axpby(h->rcor.as<double2>(), xo, len, 1.0, 1.0, s));
       }
-      CK(H.G.ensure(g_total * sizeof(double2)));
-      CK(H.FT.ensure(ft_total * sizeof(double2)));
-      CK(H.TMP.ensure(ft_total * sizeof(double2)));
-      Packer pk;
-      std::vector<LeafJob> lj;
-      std::vector<CopyJob> cj;
-      std::vector<RsJob> rs;
-      std::vector<BasisJob> bj;
-      std::vector<GemmJob> gj;
-      int max_n = 1;
-      if (t == 0) leaf_jobs(h, lj);
-      for (const BoxRef& rf : refs) {
-        const HBox& bx = *rf.bx;
-        if (t > 0) {
-          const auto& kids = h->probs[rf.p].levels[rf.l + 1];
-          const HBox& c1 = kids[bx.child[0]];
-          const HBox& c2 = kids[bx.child[1]];
-          CopyJob c;
-          c.src_off = c1.ft_off; c.dst_off = bx.g_off; c.rows = c1.k; c.cols = nrhs; c.lds = c1.k; c.ldd = bx.size;
-          cj.push_back(c);
-          c.src_off = c2.ft_off; c.dst_off = bx.g_off + c1.k; c.rows = c2.k; c.lds = c2.k;
-          cj.push_back(c);
-        }
-        RsJob r;
-        r.a_off = bx.d_off; r.n = bx.size; r.lda = bx.size; r.piv_off = bx.piv_off;
-        r.b_off = bx.g_off; r.ldb = bx.size; r.nrhs = nrhs;
-        rs.push_back(r);
-        max_n = std::max(max_n, bx.size);
-        if (rf.l > 0) {
-          BasisJob b{};
-          for (int p = 0; p < 2; ++p) {
-            b.part[p].q_off = bx.q_off[p]; b.part[p].t_off = bx.t_off[p];
-            b.part[p].n = (int)bx.perm[p].size(); b.part[p].r = bx.rank[p];
-            b.part[p].col0 = p == 0 ? 0 : bx.rank[0];
-          }
-          b.size = bx.size; b.k = bx.k;
-          b.in_off = bx.g_off; b.ld_in = bx.size; b.out_off = bx.ft_off; b.ld_out = bx.k; b.ncols = nrhs;
-          bj.push_back(b);
-          GemmJob gmm;
-          gmm.a_off = bx.rx_off; gmm.lda = bx.k;
-          gmm.b_off = bx.ft_off; gmm.ldb = bx.k;
-          gmm.c_off = bx.ft_off; gmm.ldc = bx.k;
-          gmm.m = bx.k; gmm.n = nrhs; gmm.k = bx.k; gmm.alpha = 1.0; gmm.beta = 0.0;
-          gj.push_back(gmm);
-        }
-      }
-      const size_t olj = pk.add(lj), ocj = pk.add(cj), ors = pk.add(rs), obj = pk.add(bj), ogj = pk.add(gj);
-      CK(pk.upload(H.slists, s));
-      char* sb = H.slists.as<char>();
-      if (t == 0)
-        TIMED(SYMHSS_K_OTHER, 0.0, launch_leaf_gather(f, ldv, H.G.as<double2>(),
-                                                      reinterpret_cast<const LeafJob*>(sb + olj), (int)lj.size(),
-                                                      nrhs, s));
-      else
-        TIMED(SYMHSS_K_OTHER, 0.0, launch_copy_blocks(h->heights[t - 1].FT.as<double2>(), H.G.as<double2>(),
-                                                      reinterpret_cast<const CopyJob*>(sb + ocj), (int)cj.size(),
-                                                      s));
-      double w_g = 0, w_up = 0;
-      for (const BoxRef& rf : refs) {
-        const HBox& bx = *rf.bx;
-        w_g += 8.0 * (double)bx.size * bx.size * nrhs;
-        if (rf.l > 0) w_up += 8.0 * (double)bx.k * (double)(bx.perm[0].size() + bx.perm[1].size() + bx.k) * nrhs;
-      }
-      RsLaunch ra;
-      ra.abase = H.D.as<double2>(); ra.piv = H.piv.as<int>(); ra.bbase = H.G.as<double2>();
-      ra.jobs = reinterpret_cast<const RsJob*>(sb + ors); ra.njobs = (int)rs.size();
-      ra.max_rhs = nrhs; ra.max_n = max_n;
-      TIMED(SYMHSS_K_GETRS, w_g, launch_getrs(ra, s));
-      if (!bj.empty()) {
-        // tmp = R g ; f~ = Atilde tmp
-        BasisLaunch ba;
-        ba.q = reinterpret_cast<const int*>(H.qbuf.p);
-        ba.T = H.tbuf.as<double2>();
-        ba.in = H.G.as<double2>();
-        ba.out = H.TMP.as<double2>();
-        ba.jobs = reinterpret_cast<const BasisJob*>(sb + obj);
-        ba.njobs = (int)bj.size();
-        ba.max_cols = nrhs;
-        TIMED(SYMHSS_K_OTHER, w_up, launch_apply_r(ba, s));
-        GemmLaunch ga;
-        ga.A = H.At.as<double2>(); ga.B = H.TMP.as<double2>(); ga.C = H.FT.as<double2>();
-        ga.jobs = reinterpret_cast<const GemmJob*>(sb + ogj); ga.njobs = (int)gj.size();
-        TIMED(SYMHSS_K_OTHER, 0.0, launch_gemm(ga, s));
-      }
-    }
-    // down pass: x_c = g_c - X_c (f~_c - Atilde_c y_c), parents at height t + 1
-    for (int t = h->maxdepth - 1; t >= 0; --t) {
-      Height& H = h->heights[t];
-      Height& HP = h->heights[t + 1];
-      std::vector<GemmJob> g1, g2;
-      for (Problem& P : h->probs) {
-        if (P.depth <= t) continue;
-        const int l = P.depth - t;
-        for (const HBox& par : P.levels[l - 1]) {
-          int row0 = 0;
-          for (int c = 0; c < 2; ++c) {
-            const HBox& bx = P.levels[l][par.child[c]];
-            GemmJob a;
-            a.a_off = bx.rx_off; a.lda = bx.k;
-            a.b_off = par.g_off + row0; a.ldb = par.size;
-            a.c_off = bx.ft_off; a.ldc = bx.k;
-            a.m = bx.k; a.n = nrhs; a.k = bx.k; a.alpha = -1.0; a.beta = 1.0;
-            g1.push_back(a);
-            GemmJob b;
-            b.a_off = bx.x_off; b.lda = bx.size;
-            b.b_off = bx.ft_off; b.ldb = bx.k;
-            b.c_off = bx.g_off; b.ldc = bx.size;
-            b.m = bx.size; b.n = nrhs; b.k = bx.k; b.alpha = -1.0; b.beta = 1.0;
-            g2.push_back(b);
-            row0 += bx.k;
-          }
-        }
-      }
-      if (g1.empty()) continue;
-      Packer pk;
-      const size_t o1 = pk.add(g1), o2 = pk.add(g2);
-      CK(pk.upload(H.slists, s));
-      char* sb = H.slists.as<char>();
-      GemmLaunch ga;
-      ga.A = H.At.as<double2>(); ga.B = HP.G.as<double2>(); ga.C = H.FT.as<double2>();
-      ga.jobs = reinterpret_cast<const GemmJob*>(sb + o1); ga.njobs = (int)g1.size();
-      double w_dn = 0;
-      for (const auto& j : g1) w_dn += 8.0 * (double)j.m * j.n * j.k;
-      for (const auto& j : g2) w_dn += 8.0 * (double)j.m * j.n * j.k;
-      TIMED(SYMHSS_K_OTHER, w_dn, launch_gemm(ga, s));
-      GemmLaunch gb;
-      gb.A = H.X.as<double2>(); gb.B = H.FT.as<double2>(); gb.C = H.G.as<double2>();
-      gb.jobs = reinterpret_cast<const GemmJob*>(sb + o2); gb.njobs = (int)g2.size();
-      TIMED(SYMHSS_K_OTHER, 0.0, launch_gemm(gb, s));
-    }
-    {
-      // the leaf lists of height 0 were overwritten by the down pass: upload them again
-      std::vector<LeafJob> lj;
-      leaf_jobs(h, lj);
-      Packer pk;
-      const size_t o = pk.add(lj);
-      Height& H0 = h->heights[0];
-      DevBuf& lb = h->maxdepth > 0 ? h->heights[h->maxdepth].slists : H0.slists;
-      CK(pk.upload(lb, s));
-      TIMED(SYMHSS_K_OTHER, 0.0, launch_leaf_scatter(H0.G.as<double2>(), xo, ldv,
-                             reinterpret_cast<const LeafJob*>(lb.as<char>() + o), (int)lj.size(), nrhs, s));
     }
     CK(cudaEventRecord(h->ev[1], s));
-    int rc = read_status(h, s);
+    rc = read_status(h, s);
     if (rc) return rc;
     prof_collect(h);
     float ms = 0;
@@ -1739,6 +1983,26 @@ int symhss_solve(symhss_t h, const void* rhs, void* x, int nrhs, void* stream) {
   } catch (const std::bad_alloc&) {
     return SYMHSS_ERR_NOMEM;
   }
+  return SYMHSS_OK;
+}
+
+int symhss_matvec(symhss_t h, const void* x, void* y, int nrhs, void* stream) {
+  if (!h || !x || !y || nrhs < 1) return SYMHSS_ERR_INVALID;
+  if (!h->factored) return SYMHSS_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    int rc = matvec_core(h, reinterpret_cast<const double2*>(x), reinterpret_cast<double2*>(y), nrhs, s);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(s));
+  } catch (const std::bad_alloc&) {
+    return SYMHSS_ERR_NOMEM;
+  }
+  return SYMHSS_OK;
+}
+
+int symhss_set_refinement(symhss_t h, int steps) {
+  if (!h || steps < 0 || steps > 4) return SYMHSS_ERR_INVALID;
+  h->refine_steps = steps;
   return SYMHSS_OK;
 }
 

@@ -22,13 +22,15 @@ class Solver:
     """One scatterer: ``compress()``, ``factor()``, ``solve(rhs)`` on cuda:0."""
 
     def __init__(self, curve, k0: float, k1: float, eps0: float = 1.0, eps1: Optional[float] = None,
-                 mode: str = "sym", curve_on_device: bool = False, formulation: str = "muller", **params):
+                 mode: str = "sym", curve_on_device: bool = False, formulation: str = "muller",
+                 precision: str = "fp64", **params):
         if eps1 is None:
             eps1 = eps0 * (k1 / k0) ** 2
         self.n = int(curve.n)
         self.mode = S.SYMHSS_SYM if mode == "sym" else S.SYMHSS_NONSYM
         form = {"muller": S.SYMHSS_MULLER, "pmchwt": S.SYMHSS_PMCHWT, "bm": S.SYMHSS_BM}[formulation]
-        self.prm = S.params(k0, k1, eps0, eps1, mode=self.mode, formulation=form, **params)
+        prec = S.SYMHSS_MIXED if precision == "mixed" else S.SYMHSS_FP64
+        self.prm = S.params(k0, k1, eps0, eps1, mode=self.mode, formulation=form, precision=prec, **params)
         self._keep = []
         cs = self._curve_struct(curve, curve_on_device)
         self.h = S.symhss_create(cs, self.prm, _stream())
@@ -63,6 +65,18 @@ class Solver:
         x = torch.empty_like(rhs)
         S.symhss_solve(self.h, rhs.data_ptr(), x.data_ptr(), nrhs, _stream())
         return x
+
+    def matvec(self, x: torch.Tensor) -> torch.Tensor:
+        """y = A_hss x (FP64 compressed operator); x like solve's right-hand side."""
+        x = x.contiguous()
+        nrhs = 1 if x.dim() == 1 else x.shape[0]
+        y = torch.empty_like(x)
+        S.check(S.lib.symhss_matvec(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), nrhs,
+                                    C.c_void_p(_stream())), "symhss_matvec")
+        return y
+
+    def set_refinement(self, steps: int) -> None:
+        S.check(S.lib.symhss_set_refinement(self.h, steps), "symhss_set_refinement")
 
     def solve_host(self, rhs: np.ndarray) -> np.ndarray:
         rhs = np.ascontiguousarray(rhs, dtype=np.complex128)
@@ -136,6 +150,17 @@ class BatchSolver:
         x = torch.empty_like(rhs)
         S.symhss_solve(self.h, rhs.data_ptr(), x.data_ptr(), nrhs, _stream())
         return x
+
+    def matvec(self, x: torch.Tensor) -> torch.Tensor:
+        x = x.contiguous()
+        nrhs = 1 if x.dim() == 1 else x.shape[0]
+        y = torch.empty_like(x)
+        S.check(S.lib.symhss_matvec(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), nrhs,
+                                    C.c_void_p(_stream())), "symhss_matvec")
+        return y
+
+    def set_refinement(self, steps: int) -> None:
+        S.check(S.lib.symhss_set_refinement(self.h, steps), "symhss_set_refinement")
 
     def block(self, v: torch.Tensor, c: int) -> torch.Tensor:
         """Problem c's [eq1; eq2] block of a batch vector."""

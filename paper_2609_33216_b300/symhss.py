@@ -27,6 +27,7 @@ SYMHSS_ERR_DEVICE = -8
 SYMHSS_SYM = 0
 SYMHSS_NONSYM = 1
 SYMHSS_FP64 = 0
+SYMHSS_MIXED = 1
 SYMHSS_MULLER = 0
 SYMHSS_PMCHWT = 1
 SYMHSS_BM = 2
@@ -100,6 +101,8 @@ _SIGNATURES = [
     ("symhss_rhs_plane_wave", C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p]),
     ("symhss_solve", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     ("symhss_solve_host", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    ("symhss_matvec", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    ("symhss_set_refinement", C.c_int, [C.c_void_p, C.c_int]),
     ("symhss_stats", C.c_int, [C.c_void_p, C.POINTER(symhss_stats_t)]),
     ("symhss_level_ranks", C.c_int, [C.c_void_p, C.c_int, _ip]),
     ("symhss_problem_ranks", C.c_int, [C.c_void_p, C.c_int, C.c_int, _ip]),
