@@ -35,7 +35,7 @@ def nvcc() -> str:
 
 
 def _headers_mtime() -> float:
-    files = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(ROOT, "include", "*.h"))
+    files = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.inc")) + glob.glob(os.path.join(ROOT, "include", "*.h"))
     return max((os.path.getmtime(f) for f in files), default=0.0)
 
 

@@ -7,11 +7,10 @@
 //                 Y0 = (2/pi) [(ln(x/2) + gamma) J0 + sum (-1)^(k+1) H_k t^k / (k!)^2]
 //                 Y1 = (2/pi)(ln(x/2) + gamma) J1 - 2/(pi x) - (x/(2 pi)) sum (-1)^k (H_k + H_(k+1)) t^k / (k!(k+1)!)
 //                 (H_k the harmonic numbers), 16 terms;
-//   4 < x < 20    Miller's backward recurrence J_(n-1) = (2n/x) J_n - J_(n+1) from
-//                 N = 2 ceil((1.5 x + 22)/2), normalised by J0 + 2 sum J_(2k) = 1, with
-//                 the Neumann series Y0 = (2/pi)[(ln(x/2) + gamma) J0 - 2 sum (-1)^k J_(2k)/k]
-//                 and its derivative Y1 = (2/pi)[-J0/x + (ln(x/2) + gamma) J1
-//                                                 + sum (-1)^k (J_(2k-1) - J_(2k+1))/k];
+//   4 < x < 20    Taylor expansions of J0, Y0, J1, Y1 of degree 15 about the centres
+//                 4.5 + m of the sixteen unit intervals (kHankelMid, hankel_table.inc,
+//                 written by gen_hankel_table.py from mpmath): 64 fused multiply-adds,
+//                 about 2e-16 relative;
 //   x >= 20       Hankel's asymptotic expansion (DLMF 10.17.5)
 //                 H_n(x) = sqrt(2/(pi x)) e^{i(x - n pi/2 - pi/4)} sum_k i^k a_k(n) / x^k,
 //                 a_k(n) = prod_{j<=k} (4n^2 - (2j-1)^2) / (8j), 28 terms; one sincos(x)
@@ -23,6 +22,9 @@
 
 namespace symhss {
 namespace hk {
+
+#include "hankel_table.inc"
+
 
 constexpr double factd(int k) {
   double f = 1.0;
@@ -46,7 +48,6 @@ constexpr double ak(int n, int k) {
 }
 constexpr double pk(int n, int m) { return sgn(m) * ak(n, 2 * m); }
 constexpr double qk(int n, int m) { return sgn(m) * ak(n, 2 * m + 1); }
-constexpr double inv(int k) { return 1.0 / (double)k; }
 
 #define SYMHSS_T16(f) \
   { f(0), f(1), f(2), f(3), f(4), f(5), f(6), f(7), f(8), f(9), f(10), f(11), f(12), f(13), f(14), f(15) }
@@ -56,7 +57,6 @@ constexpr double inv(int k) { return 1.0 / (double)k; }
 #define SYMHSS_Q0(m) qk(0, m)
 #define SYMHSS_P1(m) pk(1, m)
 #define SYMHSS_Q1(m) qk(1, m)
-#define SYMHSS_INV(k) inv((k) + 1)
 
 constexpr int kSeries = 16;
 constexpr int kAsym = 14;
@@ -73,13 +73,6 @@ static __constant__ double cP0[kAsym] = SYMHSS_T14(SYMHSS_P0);
 static __constant__ double cQ0[kAsym] = SYMHSS_T14(SYMHSS_Q0);
 static __constant__ double cP1[kAsym] = SYMHSS_T14(SYMHSS_P1);
 static __constant__ double cQ1[kAsym] = SYMHSS_T14(SYMHSS_Q1);
-static __constant__ double cInv[32] = {
-    SYMHSS_INV(0),  SYMHSS_INV(1),  SYMHSS_INV(2),  SYMHSS_INV(3),  SYMHSS_INV(4),  SYMHSS_INV(5),
-    SYMHSS_INV(6),  SYMHSS_INV(7),  SYMHSS_INV(8),  SYMHSS_INV(9),  SYMHSS_INV(10), SYMHSS_INV(11),
-    SYMHSS_INV(12), SYMHSS_INV(13), SYMHSS_INV(14), SYMHSS_INV(15), SYMHSS_INV(16), SYMHSS_INV(17),
-    SYMHSS_INV(18), SYMHSS_INV(19), SYMHSS_INV(20), SYMHSS_INV(21), SYMHSS_INV(22), SYMHSS_INV(23),
-    SYMHSS_INV(24), SYMHSS_INV(25), SYMHSS_INV(26), SYMHSS_INV(27), SYMHSS_INV(28), SYMHSS_INV(29),
-    SYMHSS_INV(30), SYMHSS_INV(31)};
 
 template <int K>
 __device__ __forceinline__ double horner(const double* c, double t) {
@@ -121,42 +114,19 @@ __device__ __forceinline__ void hankel01(double x, double lh, double ix, double2
     h1 = make_double2(amp * (e1r * p1 - e1i * q1), amp * (e1r * q1 + e1i * p1));
     return;
   }
-  // Miller's backward recurrence
-  const int N = 2 * (int)ceil((1.5 * x + 22.0) * 0.5);
-  const double inv2x = 2.0 * ix;
-  double jp1 = 0.0, jn = 1.0;  // J_(n+1), J_n (unnormalised), n = N
-  double norm = 0.0, s0 = 0.0, s1 = 0.0;
-  // running values at n: after the step below jm1 = J_(n-1)
-  for (int n = N; n >= 1; --n) {
-    const double jm1 = fma((double)n * inv2x, jn, -jp1);
-    const int m = n - 1;  // index of jm1
-    if ((m & 1) == 0) {
-      if (m > 0) {
-        const int k = m >> 1;
-        norm += 2.0 * jm1;
-        const double ik = cInv[k - 1];
-        s0 += (k & 1) ? -jm1 * ik : jm1 * ik;
-      }
-    } else {
-      // m = 2k - 1: term (-1)^k (J_(2k-1) - J_(2k+1)) / k, with J_(2k+1) = jp1
-      const int k = (m + 1) >> 1;
-      const double ik = cInv[k - 1];
-      const double d = (jm1 - jp1) * ik;
-      s1 += (k & 1) ? -d : d;
-    }
-    jp1 = jn;
-    jn = jm1;
-    if (fabs(jn) > 1e250) {
-      jn *= 1e-250; jp1 *= 1e-250; norm *= 1e-250; s0 *= 1e-250; s1 *= 1e-250;
-    }
+  // 4 < x < 20: Horner in t = x - (4.5 + m) with the interval's Taylor coefficients
+  int m = (int)x - 4;
+  m = m < 0 ? 0 : (m > 15 ? 15 : m);
+  const double t = x - (4.5 + (double)m);
+  const double* c = &kHankelMid[m][0][0];
+  double j0v = __ldg(c + 15), y0v = __ldg(c + 31), j1v = __ldg(c + 47), y1v = __ldg(c + 63);
+#pragma unroll
+  for (int n = 14; n >= 0; --n) {
+    j0v = fma(j0v, t, __ldg(c + n));
+    y0v = fma(y0v, t, __ldg(c + 16 + n));
+    j1v = fma(j1v, t, __ldg(c + 32 + n));
+    y1v = fma(y1v, t, __ldg(c + 48 + n));
   }
-  // jn = J_0, jp1 = J_1 (unnormalised)
-  norm += jn;
-  const double rn = 1.0 / norm;
-  const double j0v = jn * rn, j1v = jp1 * rn;
-  const double L = lh + kGamma;
-  const double y0v = (2.0 / kPi) * (L * j0v - 2.0 * s0 * rn);
-  const double y1v = (2.0 / kPi) * (-j0v * (0.5 * inv2x) + L * j1v + s1 * rn);
   h0 = make_double2(j0v, y0v);
   h1 = make_double2(j1v, y1v);
 }
