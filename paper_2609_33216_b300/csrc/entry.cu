@@ -145,8 +145,8 @@ int symhss_column_id(void* A, int m, int n, int lda, long long strideA, int batc
   if (batch == 0) return SYMHSS_OK;
   if (!A || !rank || !perm || !T) return SYMHSS_ERR_INVALID;
   if (strideA < (long long)lda * n || strideT < (long long)(n / 2) * ((n + 1) / 2)) return SYMHSS_ERR_INVALID;
-  const size_t smem = (size_t)m * 16 + (size_t)n * 12;
-  if (smem > 220 * 1024) return SYMHSS_ERR_INVALID;
+  const size_t smem = (size_t)m * 16 + (size_t)n * 16;  // the ID kernel's shared memory
+  if (smem > 200 * 1024) return SYMHSS_ERR_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
   std::vector<IdJob> jobs(batch);
   for (int b = 0; b < batch; ++b) {

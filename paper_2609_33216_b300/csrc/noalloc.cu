@@ -87,7 +87,7 @@ extern "C" int symhss_column_id_noalloc(void* A, int m, int n, int lda, long lon
   if (batch == 0) return SYMHSS_OK;
   if (!A || !rank || !perm || !T) return SYMHSS_ERR_INVALID;
   if (strideA < (long long)lda * n || strideT < (long long)(n / 2) * ((n + 1) / 2)) return SYMHSS_ERR_INVALID;
-  if ((size_t)m * 16 + (size_t)n * 12 > 220 * 1024) return SYMHSS_ERR_INVALID;
+  if ((size_t)m * 16 + (size_t)n * 16 > 200 * 1024) return SYMHSS_ERR_INVALID;  // ID kernel shared memory
   cudaStream_t s = (cudaStream_t)stream;
   unsigned char* base = nullptr;
   cudaError_t e = scratch_address(&base);
