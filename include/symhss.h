@@ -151,6 +151,7 @@ typedef struct {
   long long proposals;            /* ID ranks proposed by the attached network          */
   double proposal_rank_err;       /* mean |proposed - ID rank| / max(1, ID rank)        */
   long long proposal_under;       /* proposals below the ID rank                        */
+  double ms_build;                /* device time of the last symhss_build                */
 } symhss_stats_t;
 
 /* ---- handle lifecycle ------------------------------------------------------ */
@@ -201,6 +202,15 @@ int symhss_compress(symhss_t h, void* stream);
 /* Multilevel factorisation (Sec. 4.2): block LU of every diagonal block,
  * X = D^{-1} L, Atilde = (R X)^{-1}, parent blocks, root LU.  Requires compress. */
 int symhss_factor(symhss_t h, void* stream);
+
+/* symhss_compress followed by symhss_factor, pipelined over tree heights: height t is
+ * factorised on `stream` while height t + 1 is compressed on a high-priority stream the
+ * handle owns (each height's factorisation needs only its own compression and the
+ * factors one height down), so the latency-bound upper-level compression overlaps the
+ * factorisation of the lower levels.  Same results as the two calls; stats().ms_build is
+ * its device time (ms_compress and ms_factor are set to 0; per-kernel-class times are
+ * summed over both streams).  Later work on `stream` is ordered after it. */
+int symhss_build(symhss_t h, void* stream);
 
 /* Right-hand side of the handle's system for the plane wave
  * u_in = exp(i k0 (x cos(angle) + y sin(angle))): [-eps0 W u_in ; W du_in/dnu]

@@ -172,6 +172,7 @@ struct symhss_s {
   double prop_margin = 1.15;
   symhss::DevBuf featjobs, feats, mlpout, chkjobs, chkratio;
   int refine_steps = 2;                           // SYMHSS_MIXED solves
+  cudaStream_t cstream = nullptr;                 // high-priority stream of the pipelined build
   symhss::DevBuf rres, rcor, rtmp;                // refinement vectors
 };
 
@@ -209,15 +210,24 @@ void prof_end(symhss_s* h, cudaStream_t s, int cls, int e0, double work) {
   h->marks.push_back({cls, e0, e1, work});
 }
 // After a stream synchronisation: fold the recorded launches into the statistics.
+// Marks whose end event has not completed yet (work still running on another stream of
+// a pipelined build) are kept, and the event pool is reused only once no mark is pending.
 void prof_collect(symhss_s* h) {
+  std::vector<symhss_s::Mark> pending;
   for (const auto& m : h->marks) {
+    if (cudaEventQuery(h->evpool[m.e1]) == cudaErrorNotReady) {
+      pending.push_back(m);
+      continue;
+    }
+    cudaGetLastError();
     float ms = 0;
     if (cudaEventElapsedTime(&ms, h->evpool[m.e0], h->evpool[m.e1]) == cudaSuccess) h->st.kernel_ms[m.cls] += ms;
+    else cudaGetLastError();
     h->st.kernel_launches[m.cls] += 1;
     h->st.kernel_work[m.cls] += m.work;
   }
-  h->marks.clear();
-  h->evnext = 0;
+  h->marks.swap(pending);
+  if (h->marks.empty()) h->evnext = 0;
 }
 #define TIMED(cls, work, call)                     \
   do {                                             \
@@ -1499,9 +1509,7 @@ int symhss_batch_info(symhss_t h, int* count, int* n, int* depth, long long* row
   return SYMHSS_OK;
 }
 
-int symhss_compress(symhss_t h, void* stream) {
-  if (!h) return SYMHSS_ERR_INVALID;
-  cudaStream_t s = (cudaStream_t)stream;
+static void reset_compress_stats(symhss_s* h) {
   h->compressed = h->factored = false;
   h->st.ms_tiles = h->st.ms_id = 0;
   h->st.pairs_evaluated = 0;
@@ -1520,24 +1528,9 @@ int symhss_compress(symhss_t h, void* stream) {
   }
   h->marks.clear();
   h->evnext = 0;
-  try {
-    CK(cudaMemsetAsync(h->status.p, 0, sizeof(int), s));
-    CK(cudaEventRecord(h->ev[0], s));
-    for (int t = 0; t < h->maxdepth; ++t) {
-      int rc = compress_height(h, t, s);
-      if (rc) return rc;
-      rc = read_status(h, s);
-      if (rc) return rc;
-    }
-    CK(cudaEventRecord(h->ev[1], s));
-    CK(cudaEventSynchronize(h->ev[1]));
-    float ms = 0;
-    cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
-    h->st.ms_compress = ms;
-    if (h->st.proposals > 0) h->st.proposal_rank_err /= (double)h->st.proposals;
-  } catch (const std::bad_alloc&) {
-    return SYMHSS_ERR_NOMEM;
-  }
+}
+
+static void rank_stats(symhss_s* h) {
   // rank statistics by level, over every problem that has the level
   h->st.max_rank[0] = h->st.max_rank[1] = 0;
   for (int l = 0; l < SYMHSS_MAX_LEVELS; ++l) {
@@ -1566,6 +1559,31 @@ int symhss_compress(symhss_t h, void* stream) {
         for (const HBox& b : P.levels[l]) mp = std::max(mp, b.P);
     h->st.level_nproxy[l] = mp;
   }
+}
+
+int symhss_compress(symhss_t h, void* stream) {
+  if (!h) return SYMHSS_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  reset_compress_stats(h);
+  try {
+    CK(cudaMemsetAsync(h->status.p, 0, sizeof(int), s));
+    CK(cudaEventRecord(h->ev[0], s));
+    for (int t = 0; t < h->maxdepth; ++t) {
+      int rc = compress_height(h, t, s);
+      if (rc) return rc;
+      rc = read_status(h, s);
+      if (rc) return rc;
+    }
+    CK(cudaEventRecord(h->ev[1], s));
+    CK(cudaEventSynchronize(h->ev[1]));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
+    h->st.ms_compress = ms;
+    if (h->st.proposals > 0) h->st.proposal_rank_err /= (double)h->st.proposals;
+  } catch (const std::bad_alloc&) {
+    return SYMHSS_ERR_NOMEM;
+  }
+  rank_stats(h);
   h->compressed = true;
   return SYMHSS_OK;
 }
@@ -1599,6 +1617,68 @@ int symhss_factor(symhss_t h, void* stream) {
   }
   h->st.pairs_evaluated += pairs;
   h->factored = true;
+  return SYMHSS_OK;
+}
+
+int symhss_build(symhss_t h, void* stream) {
+  if (!h) return SYMHSS_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!h->cstream) {
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (cudaStreamCreateWithPriority(&h->cstream, cudaStreamNonBlocking, hi) != cudaSuccess) {
+      cudaGetLastError();
+      h->cstream = nullptr;
+    }
+  }
+  if (!h->cstream) {  // no second stream: the two phases one after the other
+    int rc = symhss_compress(h, stream);
+    return rc ? rc : symhss_factor(h, stream);
+  }
+  cudaStream_t cs = h->cstream;
+  reset_compress_stats(h);
+  h->st.flops_lu = 0;
+  h->st.ms_compress = h->st.ms_factor = 0;
+  long long pairs = 0;
+  try {
+    CK(cudaMemsetAsync(h->status.p, 0, sizeof(int), s));
+    CK(cudaEventRecord(h->ev[0], s));
+    CK(cudaStreamWaitEvent(cs, h->ev[0], 0));  // the compression follows earlier work on s
+    int rc = SYMHSS_OK;
+    if (h->maxdepth > 0) {
+      rc = compress_height(h, 0, cs);
+      if (!rc) rc = read_status(h, cs);
+      if (rc) return rc;
+    }
+    for (int t = 0; t <= h->maxdepth; ++t) {
+      // height t is compressed (its stream was synchronised): factor it on s while the
+      // next height is compressed on cs
+      rc = factor_height(h, t, s, pairs);
+      if (rc) return rc;
+      if (t + 1 < h->maxdepth) {
+        rc = compress_height(h, t + 1, cs);
+        if (!rc) rc = read_status(h, cs);
+        if (rc) return rc;
+      }
+    }
+    CK(cudaEventRecord(h->ev[1], s));
+    rc = read_status(h, s);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(cs));
+    prof_collect(h);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
+    h->st.ms_build = ms;
+    if (h->st.proposals > 0) h->st.proposal_rank_err /= (double)h->st.proposals;
+    int rs = 0;
+    for (const Problem& P : h->probs) rs = std::max(rs, P.levels[0][0].size);
+    h->st.root_size = rs;
+  } catch (const std::bad_alloc&) {
+    return SYMHSS_ERR_NOMEM;
+  }
+  rank_stats(h);
+  h->st.pairs_evaluated += pairs;
+  h->compressed = h->factored = true;
   return SYMHSS_OK;
 }
 
@@ -2224,6 +2304,7 @@ int symhss_training_data(symhss_t h, int* count, float* x, float* y_rank, float*
 
 int symhss_destroy(symhss_t h) {
   if (!h) return SYMHSS_OK;
+  if (h->cstream) cudaStreamDestroy(h->cstream);
   for (auto& e : h->ev)
     if (e) cudaEventDestroy(e);
   for (auto& e : h->evpool) cudaEventDestroy(e);

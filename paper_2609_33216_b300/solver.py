@@ -53,6 +53,10 @@ class Solver:
     def factor(self) -> None:
         S.symhss_factor(self.h, _stream())
 
+    def build(self) -> None:
+        """compress() and factor(), pipelined over tree heights on two streams."""
+        S.symhss_build(self.h, _stream())
+
     def rhs(self, angle: float = 0.0) -> torch.Tensor:
         f = torch.empty(2 * self.n, dtype=torch.complex128, device="cuda")
         S.symhss_rhs_plane_wave(self.h, angle, f.data_ptr(), _stream())
@@ -138,6 +142,10 @@ class BatchSolver:
 
     def factor(self) -> None:
         S.symhss_factor(self.h, _stream())
+
+    def build(self) -> None:
+        """compress() and factor(), pipelined over tree heights on two streams."""
+        S.symhss_build(self.h, _stream())
 
     def rhs(self, angle: float = 0.0) -> torch.Tensor:
         f = torch.empty(self.rows, dtype=torch.complex128, device="cuda")

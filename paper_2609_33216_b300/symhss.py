@@ -68,7 +68,7 @@ class symhss_stats_t(C.Structure):
                 ("kernel_ms", C.c_double * 8), ("kernel_launches", C.c_longlong * 8),
                 ("kernel_work", C.c_double * 8), ("sketch_redo", C.c_longlong),
                 ("check_failed", C.c_longlong), ("check_max_ratio", C.c_double), ("proposals", C.c_longlong),
-                ("proposal_rank_err", C.c_double), ("proposal_under", C.c_longlong)]
+                ("proposal_rank_err", C.c_double), ("proposal_under", C.c_longlong), ("ms_build", C.c_double)]
 
 
 class symhss_tuning(C.Structure):
@@ -98,6 +98,7 @@ _SIGNATURES = [
     ("symhss_batch_info", C.c_int, [C.c_void_p, _ip, _ip, _ip, C.POINTER(C.c_longlong)]),
     ("symhss_compress", C.c_int, [C.c_void_p, C.c_void_p]),
     ("symhss_factor", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("symhss_build", C.c_int, [C.c_void_p, C.c_void_p]),
     ("symhss_rhs_plane_wave", C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p]),
     ("symhss_solve", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     ("symhss_solve_host", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
@@ -234,6 +235,10 @@ def symhss_compress(h, stream: int = 0) -> None:
 
 def symhss_factor(h, stream: int = 0) -> None:
     check(lib.symhss_factor(h, C.c_void_p(stream)), "symhss_factor")
+
+
+def symhss_build(h, stream: int = 0) -> None:
+    check(lib.symhss_build(h, C.c_void_p(stream)), "symhss_build")
 
 
 def symhss_rhs_plane_wave(h, angle: float, rhs_ptr: int, stream: int = 0) -> None:

@@ -52,3 +52,50 @@ def test_autotune_returns_valid_setting_and_leaves_handle_factored(mods):
     x = s.solve(s.rhs(0.0))  # factorised by the autotuner
     assert torch.isfinite(torch.view_as_real(x)).all()
     s.close()
+
+
+@pytest.mark.parametrize("mode,precision", [("sym", "fp64"), ("base", "fp64"), ("sym", "mixed")])
+def test_pipelined_build_matches_compress_then_factor(mods, mode, precision):
+    """symhss_build runs the compression of height t + 1 on a second stream while height t is
+    factorised: the same kernels on the same data, so the solution is bit for bit that of
+    symhss_compress followed by symhss_factor, with the same launch count and ranks."""
+    SV, S = mods
+    s = SV.Solver(star(6000), 20.0, 30.0, leaf=128, nproxy=64, tol=1e-10, mode=mode, precision=precision)
+    s.compress()
+    s.factor()
+    ref = s.solve(s.rhs(0.0)).cpu().numpy()
+    st0 = s.stats()
+    r0 = [list(s.ranks(lev)) for lev in range(1, st0.depth + 1)]
+    for _ in range(2):
+        s.build()
+        x = s.solve(s.rhs(0.0)).cpu().numpy()
+        assert np.array_equal(x, ref), np.abs(x - ref).max()
+    st1 = s.stats()
+    assert st1.ms_build > 0
+    assert list(st1.kernel_launches) == list(st0.kernel_launches)
+    assert [list(s.ranks(lev)) for lev in range(1, st1.depth + 1)] == r0
+    s.close()
+
+
+def test_pipelined_build_batch_and_single_leaf(mods):
+    SV, S = mods
+    from synth import random_star_batch
+    probs = random_star_batch(4, seed=17, n_min=40, n_max=5000, k_range=(5.0, 25.0))
+    args = ([p["curve"] for p in probs], [p["k0"] for p in probs], [p["k1"] for p in probs],
+            [p["eps0"] for p in probs], [p["eps1"] for p in probs])
+    b = SV.BatchSolver(*args, leaf=64, nproxy=32, tol=1e-10)
+    b.compress()
+    b.factor()
+    ref = b.solve(b.rhs(0.0)).cpu().numpy()
+    b.build()
+    x = b.solve(b.rhs(0.0)).cpu().numpy()
+    assert np.array_equal(x, ref)
+    b.close()
+    # a handle whose tree is a single leaf: nothing to compress, the build only factorises
+    t = SV.Solver(star(100), 5.0, 8.0, leaf=128, nproxy=32, tol=1e-10)
+    t.compress()
+    t.factor()
+    r1 = t.solve(t.rhs(0.0)).cpu().numpy()
+    t.build()
+    assert np.array_equal(t.solve(t.rhs(0.0)).cpu().numpy(), r1)
+    t.close()
