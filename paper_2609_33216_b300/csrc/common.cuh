@@ -98,6 +98,28 @@ __device__ __forceinline__ void warp_argmax(double& v, int& i) {
   }
 }
 
+// Pivot-search keys: |re| + |im| >= 0 by its IEEE bit pattern, whose integer order is the
+// order of the values for non-negative numbers (NaN maps below every number, so it is never
+// picked).  Comparing keys keeps the pivot search on the integer pipes, which matters where
+// FP64 issues at a small fraction of the FP32 rate.
+__device__ __forceinline__ long long pivot_key(double v) {
+  const long long k = __double_as_longlong(v);
+  return k > 0x7ff0000000000000LL ? -1LL : k;
+}
+__device__ __forceinline__ long long pivot_key(float v) {
+  const int k = __float_as_int(v);
+  return k > 0x7f800000 ? -1LL : (long long)k;
+}
+// argmax over (key, index) with ties to the lowest index
+__device__ __forceinline__ void warp_argmax_key(long long& k, int& i) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long ok = __shfl_xor_sync(0xffffffffu, k, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, i, o);
+    if (ok > k || (ok == k && oi < i)) { k = ok; i = oi; }
+  }
+}
+
 // process-wide count of kernels this library has launched (diagnostics)
 void count_launches(long long n);
 

@@ -33,7 +33,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 
-struct Cand { double v; int i; };
+struct Cand { long long k; int i; };  // pivot key of the norm, column
 
 __device__ __forceinline__ double block_sum(double v, double* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -59,6 +59,7 @@ __global__ void __launch_bounds__(kThreads) cpqr_cluster_kernel(const IdLaunch a
   int* order = reinterpret_cast<int*>(norms + a.max_n);           // max_n
   int* done = order + a.max_n;                                     // max_n: 1 = chosen
   __shared__ double red[kWarps];
+  __shared__ long long redk[kWarps];
   __shared__ int redi[kWarps];
   __shared__ Cand cand[2];
   __shared__ Cand s_pick;
@@ -99,39 +100,39 @@ __global__ void __launch_bounds__(kThreads) cpqr_cluster_kernel(const IdLaunch a
 
   int par = 0;
   while (true) {
-    // 1. local proposal
-    double bv = -1.0;
+    // 1. local proposal (integer keys of the non-negative norms: same order, integer pipes)
+    long long bk = -1;
     int bi = n;
     for (int j = rank + C * tid; j < n; j += C * kThreads) {
       if (done[j]) continue;
-      const double v = norms[j];
-      if (v > bv || (v == bv && j < bi)) { bv = v; bi = j; }
+      const long long kj = pivot_key(norms[j]);
+      if (kj > bk || (kj == bk && j < bi)) { bk = kj; bi = j; }
     }
-    warp_argmax(bv, bi);
-    if (lane == 0) { red[warp] = bv; redi[warp] = bi; }
+    warp_argmax_key(bk, bi);
+    if (lane == 0) { redk[warp] = bk; redi[warp] = bi; }
     __syncthreads();
     if (warp == 0) {
-      bv = lane < kWarps ? red[lane] : -1.0;
+      bk = lane < kWarps ? redk[lane] : -1;
       bi = lane < kWarps ? redi[lane] : n;
-      warp_argmax(bv, bi);
-      if (lane == 0) cand[par] = Cand{bv, bi};
+      warp_argmax_key(bk, bi);
+      if (lane == 0) cand[par] = Cand{bk, bi};
     }
     cl.sync();
     // the C proposals are read in parallel (one lane each) and reduced with shuffles
     if (warp == 0) {
-      double cv = -1.0;
+      long long ck = -1;
       int ci = n;
       if (lane < C) {
         const Cand cd = *cl.map_shared_rank(&cand[par], lane);
-        cv = cd.v;
+        ck = cd.k;
         ci = cd.i;
       }
-      warp_argmax(cv, ci);
-      if (lane == 0) s_pick = Cand{cv, ci};
+      warp_argmax_key(ck, ci);
+      if (lane == 0) s_pick = Cand{ck, ci};
     }
     __syncthreads();
-    double pv = s_pick.v;
-    int p = s_pick.i;
+    const double pv = s_pick.k < 0 ? -1.0 : __longlong_as_double(s_pick.k);
+    const int p = s_pick.i;
     par ^= 1;
     if (ref < 0.0) ref = pv;
     // 2. stop (the same decision in every block of the cluster)

@@ -27,9 +27,9 @@ constexpr int kNb = 16;          // panel width
 constexpr int kPanelThreads = 256;
 constexpr int kPanelWarps = kPanelThreads / 32;
 constexpr int kTs = 32;          // trailing-update tile
-constexpr int kClusterPanelThreads = 256;
+constexpr int kClusterPanelThreads = 128;
 
-struct Cand2 { double v; int i; };
+struct CandK { long long k; int i; };
 
 template <typename CT> __device__ __forceinline__ CT* lu_base(const LuLaunch& a);
 template <> __device__ __forceinline__ double2* lu_base<double2>(const LuLaunch& a) { return a.base; }
@@ -37,11 +37,11 @@ template <> __device__ __forceinline__ float2* lu_base<float2>(const LuLaunch& a
 
 template <typename CT>
 __global__ void __launch_bounds__(kPanelThreads) panel_kernel(const LuLaunch a, int j) {
-  __shared__ double red[kPanelWarps];
+  __shared__ long long redk[kPanelWarps];
   __shared__ int redi[kPanelWarps];
-  __shared__ int s_piv;
-  __shared__ double s_pv;
+  __shared__ int s_piv, s_zero;
   __shared__ CT s_row[kNb];
+  __shared__ CT s_inv;
   const LuJob jb = a.jobs[blockIdx.x];
   const int n = jb.n, ld = jb.ld;
   if (j >= n) return;
@@ -52,32 +52,34 @@ __global__ void __launch_bounds__(kPanelThreads) panel_kernel(const LuLaunch a, 
   for (int c = 0; c < w; ++c) {
     const int jc = j + c;
     const CT* col = A + (long long)jc * ld;
-    double bv = -1.0;
+    long long bk = -1;
     int bi = n;
     for (int i = jc + tid; i < n; i += kPanelThreads) {
-      const double v = cabs1(col[i]);
-      if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
+      const long long k = pivot_key(cabs1(col[i]));
+      if (k > bk || (k == bk && i < bi)) { bk = k; bi = i; }
     }
-    warp_argmax(bv, bi);
-    if (lane == 0) { red[warp] = bv; redi[warp] = bi; }
+    warp_argmax_key(bk, bi);
+    if (lane == 0) { redk[warp] = bk; redi[warp] = bi; }
     __syncthreads();
     if (warp == 0) {
-      bv = lane < kPanelWarps ? red[lane] : -1.0;
+      bk = lane < kPanelWarps ? redk[lane] : -1;
       bi = lane < kPanelWarps ? redi[lane] : n;
-      warp_argmax(bv, bi);
-      if (lane == 0) { s_piv = bi; s_pv = bv; }
+      warp_argmax_key(bk, bi);
+      if (lane == 0) {
+        // an exactly zero (or no finite) pivot skips the step; every barrier stays unconditional
+        const bool zero = bk <= 0 || bi >= n;
+        s_piv = zero ? jc : bi;
+        s_zero = zero;
+        piv[jc] = s_piv;
+        if (zero) {
+          if (a.info[jb.info_idx] == 0) a.info[jb.info_idx] = jc + 1;
+          atomicOr(a.status, ST_SINGULAR);
+        }
+      }
     }
     __syncthreads();
     const int p = s_piv;
-    if (tid == 0) {
-      piv[jc] = p;
-      if (s_pv == 0.0) {
-        if (a.info[jb.info_idx] == 0) a.info[jb.info_idx] = jc + 1;
-        atomicOr(a.status, ST_SINGULAR);
-      }
-    }
-    // an exactly zero pivot column skips the step; every barrier stays unconditional
-    const bool zero = (s_pv == 0.0);
+    const bool zero = s_zero;
     if (!zero && tid < w && p != jc) {
       CT* cc = A + (long long)(j + tid) * ld;
       const CT t = cc[jc];
@@ -85,9 +87,13 @@ __global__ void __launch_bounds__(kPanelThreads) panel_kernel(const LuLaunch a, 
       cc[p] = t;
     }
     __syncthreads();
-    if (tid < w) s_row[tid] = A[jc + (long long)(j + tid) * ld];
+    if (tid < w) {
+      const CT v = A[jc + (long long)(j + tid) * ld];
+      s_row[tid] = v;
+      if (tid == c) s_inv = zero ? make_c<CT>(0.0, 0.0) : cinv(v);
+    }
     __syncthreads();
-    const CT inv = zero ? make_c<CT>(0.0, 0.0) : cinv(s_row[c]);
+    const CT inv = s_inv;
     for (int i = jc + 1 + tid; !zero && i < n; i += kPanelThreads) {
       const CT l = cmul(A[i + (long long)jc * ld], inv);
       A[i + (long long)jc * ld] = l;
@@ -103,15 +109,17 @@ __global__ void __launch_bounds__(kPanelThreads) panel_kernel(const LuLaunch a, 
 // Panel factorisation with the panel (rows [j, n) x w columns) staged in shared
 // memory; the pivot search of column c + 1 is fused into the update of column c.
 // THREADS is chosen per launch so that each thread holds about one or two panel rows.
+// FP64 issues slowly on this GPU, so only the row updates use it: the pivot search
+// compares integer keys and one thread forms the pivot's reciprocal for the block.
 template <int THREADS, typename CT>
 __global__ void __launch_bounds__(THREADS) panel_smem_kernel(const LuLaunch a, int j) {
   constexpr int kWarps = THREADS / 32;
   extern __shared__ __align__(16) unsigned char p_raw[];
   CT* P = reinterpret_cast<CT*>(p_raw);  // column-major: P[q * rows + i]
-  __shared__ double red[kWarps];
+  __shared__ long long redk[kWarps];
   __shared__ int redi[kWarps];
-  __shared__ int s_piv;
-  __shared__ double s_pv;
+  __shared__ int s_piv, s_zero;
+  __shared__ CT s_inv;
   const LuJob jb = a.jobs[blockIdx.x];
   const int n = jb.n, ld = jb.ld;
   if (j >= n) return;  // uniform per block
@@ -124,40 +132,45 @@ __global__ void __launch_bounds__(THREADS) panel_smem_kernel(const LuLaunch a, i
     P[q * rows + i] = A[j + i + (long long)(j + q) * ld];
   }
   __syncthreads();
-  double bv = -1.0;
+  long long bk = -1;
   int bi = rows;
   for (int i = tid; i < rows; i += THREADS) {
-    const double v = cabs1(P[i]);
-    if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
+    const long long k = pivot_key(cabs1(P[i]));
+    if (k > bk || (k == bk && i < bi)) { bk = k; bi = i; }
   }
   for (int c = 0; c < w; ++c) {
-    warp_argmax(bv, bi);
-    if (lane == 0) { red[warp] = bv; redi[warp] = bi; }
+    warp_argmax_key(bk, bi);
+    if (lane == 0) { redk[warp] = bk; redi[warp] = bi; }
     __syncthreads();
     if (warp == 0) {
-      bv = lane < kWarps ? red[lane] : -1.0;
+      bk = lane < kWarps ? redk[lane] : -1;
       bi = lane < kWarps ? redi[lane] : rows;
-      warp_argmax(bv, bi);
-      if (lane == 0) { s_piv = bi; s_pv = bv; }
+      warp_argmax_key(bk, bi);
+      if (lane == 0) {
+        // an exactly zero (or no finite) pivot skips the step; every barrier stays unconditional
+        const bool zero = bk <= 0 || bi >= rows;
+        const int p = zero ? c : bi;
+        s_piv = p;
+        s_zero = zero;
+        s_inv = zero ? make_c<CT>(0.0, 0.0) : cinv(P[c * rows + p]);
+        piv[j + c] = j + p;
+        if (zero) {
+          if (a.info[jb.info_idx] == 0) a.info[jb.info_idx] = j + c + 1;
+          atomicOr(a.status, ST_SINGULAR);
+        }
+      }
     }
     __syncthreads();
     const int p = s_piv;
-    const bool zero = (s_pv == 0.0);
-    if (tid == 0) {
-      piv[j + c] = j + p;
-      if (zero) {
-        if (a.info[jb.info_idx] == 0) a.info[jb.info_idx] = j + c + 1;
-        atomicOr(a.status, ST_SINGULAR);
-      }
-    }
+    const bool zero = s_zero;
     if (!zero && tid < w && p != c) {
       const CT t = P[tid * rows + c];
       P[tid * rows + c] = P[tid * rows + p];
       P[tid * rows + p] = t;
     }
     __syncthreads();
-    const CT inv = zero ? make_c<CT>(0.0, 0.0) : cinv(P[c * rows + c]);
-    bv = -1.0;
+    const CT inv = s_inv;
+    bk = -1;
     bi = rows;
     for (int i = c + 1 + tid; i < rows; i += THREADS) {
       if (!zero) {
@@ -166,8 +179,8 @@ __global__ void __launch_bounds__(THREADS) panel_smem_kernel(const LuLaunch a, i
         for (int q = c + 1; q < w; ++q) P[q * rows + i] = cfms(l, P[q * rows + c], P[q * rows + i]);
       }
       if (c + 1 < w) {
-        const double v = cabs1(P[(c + 1) * rows + i]);
-        if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
+        const long long k = pivot_key(cabs1(P[(c + 1) * rows + i]));
+        if (k > bk || (k == bk && i < bi)) { bk = k; bi = i; }
       }
     }
     __syncthreads();
@@ -182,21 +195,23 @@ __global__ void __launch_bounds__(THREADS) panel_smem_kernel(const LuLaunch a, i
 // Panel factorisation by a thread-block cluster of C blocks (one cluster per matrix), for
 // the few large matrices of the top levels whose panel would otherwise run on one SM.
 // Panel row i (rows [j, n) numbered from 0) lives in block i % C at local index i / C,
-// in shared memory.  Column step c: every block proposes its largest |re| + |im| among its
-// rows >= c; after a cluster barrier every block reads all proposals through distributed
+// in shared memory.  Column step c: every block proposes its largest |re| + |im| key among
+// its rows >= c; after a cluster barrier every block reads all proposals through distributed
 // shared memory and takes the largest (ties to the lowest row: the pivots of the one-block
-// kernel); every block copies the pivot row and the old row c, a second cluster barrier
-// ends those reads, the owners write the swapped rows, and every block updates its own
-// rows below c (fusing the next column's proposal).  The arithmetic of every row is the
-// one-block kernel's, so the factors are identical.
+// kernel); every block copies the pivot row and the old row c (the thread holding the
+// pivot's column forms its reciprocal), a second cluster barrier ends those reads, the
+// owners write the swapped rows, and every block updates its own rows below c (fusing the
+// next column's proposal).  The arithmetic of every row is the one-block kernel's, so the
+// factors are identical.
 __global__ void __launch_bounds__(kClusterPanelThreads) panel_cluster_kernel(const LuLaunch a, int j, int lmax) {
   extern __shared__ __align__(16) double2 P[];  // P[q * lmax + li]
   constexpr int kWarps = kClusterPanelThreads / 32;
-  __shared__ double red[kWarps];
+  __shared__ long long redk[kWarps];
   __shared__ int redi[kWarps];
-  __shared__ Cand2 cand[2];
-  __shared__ Cand2 pick;
+  __shared__ CandK cand[2];
+  __shared__ CandK pick;
   __shared__ double2 prow[kNb], rowc[kNb];
+  __shared__ double2 s_inv;
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
@@ -217,46 +232,46 @@ __global__ void __launch_bounds__(kClusterPanelThreads) panel_cluster_kernel(con
     P[q * lmax + li] = A[j + rank + li * C + (long long)(j + q) * ld];
   }
   __syncthreads();
-  double bv = -1.0;
+  long long bk = -1;
   int bi = rows;
   for (int li = tid; li < lrows; li += kClusterPanelThreads) {
-    const double v = cabs1(P[li]);
+    const long long k = pivot_key(cabs1(P[li]));
     const int i = rank + li * C;
-    if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
+    if (k > bk || (k == bk && i < bi)) { bk = k; bi = i; }
   }
   int par = 0;
   for (int c = 0; c < w; ++c) {
-    warp_argmax(bv, bi);
-    if (lane == 0) { red[warp] = bv; redi[warp] = bi; }
+    warp_argmax_key(bk, bi);
+    if (lane == 0) { redk[warp] = bk; redi[warp] = bi; }
     __syncthreads();
     if (warp == 0) {
-      bv = lane < kWarps ? red[lane] : -1.0;
+      bk = lane < kWarps ? redk[lane] : -1;
       bi = lane < kWarps ? redi[lane] : rows;
-      warp_argmax(bv, bi);
-      if (lane == 0) cand[par] = Cand2{bv, bi};
+      warp_argmax_key(bk, bi);
+      if (lane == 0) cand[par] = CandK{bk, bi};
     }
     cl.sync();
     // the C proposals are read in parallel (one lane each) and reduced with shuffles
     if (warp == 0) {
-      double cv = -1.0;
+      long long ck = -1;
       int ci = rows;
       if (lane < C) {
-        const Cand2 cd = *cl.map_shared_rank(&cand[par], lane);
-        cv = cd.v;
+        const CandK cd = *cl.map_shared_rank(&cand[par], lane);
+        ck = cd.k;
         ci = cd.i;
       }
-      warp_argmax(cv, ci);
-      if (lane == 0) pick = Cand2{cv, ci};
+      warp_argmax_key(ck, ci);
+      if (lane == 0) pick = CandK{ck, ci};
     }
     __syncthreads();
-    double pv = pick.v;
-    int p = pick.i;
+    const bool zero = pick.k <= 0 || pick.i >= rows;
+    const int p = zero ? c : pick.i;
     par ^= 1;
-    const bool zero = !(pv > 0.0) || p >= rows;
-    if (zero) p = c;
     if (tid < w) {
-      prow[tid] = cl.map_shared_rank(P, p % C)[tid * lmax + p / C];
+      const double2 pv = cl.map_shared_rank(P, p % C)[tid * lmax + p / C];
+      prow[tid] = pv;
       rowc[tid] = cl.map_shared_rank(P, c % C)[tid * lmax + c / C];
+      if (tid == c) s_inv = zero ? make_double2(0.0, 0.0) : cinv(pv);
     }
     if (tid == 0 && rank == 0) {
       piv[j + c] = j + p;
@@ -271,8 +286,8 @@ __global__ void __launch_bounds__(kClusterPanelThreads) panel_cluster_kernel(con
       if (p % C == rank) P[tid * lmax + p / C] = rowc[tid];
     }
     __syncthreads();
-    const double2 inv = zero ? make_double2(0.0, 0.0) : cinv(prow[c]);
-    bv = -1.0;
+    const double2 inv = s_inv;
+    bk = -1;
     bi = rows;
     // local rows strictly below c
     for (int li = tid; li < lrows; li += kClusterPanelThreads) {
@@ -284,8 +299,8 @@ __global__ void __launch_bounds__(kClusterPanelThreads) panel_cluster_kernel(con
         for (int q = c + 1; q < w; ++q) P[q * lmax + li] = cfms(l, prow[q], P[q * lmax + li]);
       }
       if (c + 1 < w) {
-        const double v = cabs1(P[(c + 1) * lmax + li]);
-        if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
+        const long long k = pivot_key(cabs1(P[(c + 1) * lmax + li]));
+        if (k > bk || (k == bk && i < bi)) { bk = k; bi = i; }
       }
     }
     __syncthreads();
