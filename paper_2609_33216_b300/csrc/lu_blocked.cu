@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(kClusterPanelThreads) panel_cluster_kernel(con
   }
 }
 
-// Row interchanges of a panel and, right of it, L11 U12 = A12: one warp per column.
+// Row interchanges of a panel and, right of it, L11 U12 = A12: two columns per warp.
 // The panel's w interchanges touch at most 2w rows; their composition is a
 // permutation of that row set, built once per block, so each column is permuted by
 // a single gather (lane l ends with the value of row rows[l]); lanes 0..w-1 hold
@@ -362,20 +362,37 @@ __global__ void __launch_bounds__(256) swap_trsm_warp_kernel(const LuLaunch a, i
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int col = blockIdx.y * 8 + warp;
-  if (col >= n || (col >= j && col < j + w)) return;  // uniform per warp
-  CT* cc = A + (long long)col * ld;
+  const int col0 = (blockIdx.y * 8 + warp) * 2;  // two columns per warp
   const int cnt = nrows_s;
-  CT x = lane < cnt ? cc[src_s[lane]] : make_c<CT>(0.0, 0.0);
-  __syncwarp();
-  if (lane >= w && lane < cnt) cc[rows_s[lane]] = x;
-  if (col >= j + w) {
-    for (int c = 0; c < w; ++c) {
-      const CT xc = make_c<CT>(__shfl_sync(0xffffffffu, x.x, c), __shfl_sync(0xffffffffu, x.y, c));
-      if (lane > c && lane < w) x = cfms(l11[lane][c], xc, x);
-    }
+  const bool v0 = col0 < n && !(col0 >= j && col0 < j + w);
+  const bool v1 = col0 + 1 < n && !(col0 + 1 >= j && col0 + 1 < j + w);
+  if (!v0 && !v1) return;  // uniform per warp
+  // interchanges: the full warp permutes one column at a time
+  CT x[2];
+#pragma unroll
+  for (int hc = 0; hc < 2; ++hc) {
+    x[hc] = make_c<CT>(0.0, 0.0);
+    if (!(hc ? v1 : v0)) continue;  // uniform per warp
+    CT* cc = A + (long long)(col0 + hc) * ld;
+    const CT xv = lane < cnt ? cc[src_s[lane]] : make_c<CT>(0.0, 0.0);
+    __syncwarp();
+    if (lane >= w && lane < cnt) cc[rows_s[lane]] = xv;
+    x[hc] = xv;
   }
-  if (lane < w) cc[j + lane] = x;
+  // L11 U12 = A12 for both columns in one pass: lanes 0-15 hold rows j..j+w-1 of the
+  // first column, lanes 16-31 those of the second (half the FP64 issue of one column a warp)
+  const int half = lane >> 4, r = lane & 15;
+  const CT up = make_c<CT>(__shfl_sync(0xffffffffu, x[1].x, r), __shfl_sync(0xffffffffu, x[1].y, r));
+  CT v = half ? up : x[0];
+  const int col = col0 + half;
+  const bool mine = half ? v1 : v0;
+  const bool trsm = mine && col >= j + w;
+  for (int c = 0; c < w; ++c) {
+    const int src = (lane & 16) | c;
+    const CT vc = make_c<CT>(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+    if (trsm && r > c && r < w) v = cfms(l11[r][c], vc, v);
+  }
+  if (mine && r < w) A[(long long)col * ld + j + r] = v;
 }
 
 // A22 -= L21 U12 for the tile (blockIdx.y, blockIdx.z) of every matrix, over the trailing
@@ -482,7 +499,7 @@ cudaError_t getrf_impl(const LuLaunch& a, cudaStream_t s) {
       e = cudaFuncSetAttribute(panel_smem_kernel<1024, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem);
     if (e != cudaSuccess) return e;
   }
-  const int ncolblk = (a.max_n + 7) / 8;
+  const int ncolblk = (a.max_n + 15) / 16;  // 16 columns per block of the interchange kernel
   // Depth-1 look-ahead: after the interchanges and TRSM of panel j, the first trailing
   // tile column (which holds panel j + kNb) is updated first; panel j + kNb then runs on
   // a high-priority side stream while the rest of the trailing update runs on s.  The two

@@ -1141,9 +1141,11 @@ int assemble_and_lu(symhss_s* h, int t, cudaStream_t s, long long& pairs) {
   return SYMHSS_OK;
 }
 
-int factor_height(symhss_s* h, int t, cudaStream_t s, long long& pairs) {
+// lu_done: the height's diagonal blocks were already assembled and factorised (the
+// leaf blocks of a pipelined build, which need no compression)
+int factor_height(symhss_s* h, int t, cudaStream_t s, long long& pairs, bool lu_done = false) {
   Height& H = h->heights[t];
-  int rc = assemble_and_lu(h, t, s, pairs);
+  int rc = lu_done ? SYMHSS_OK : assemble_and_lu(h, t, s, pairs);
   if (rc) return rc;
   std::vector<BoxRef> refs;
   height_boxes(h, t, false, refs);
@@ -1644,7 +1646,10 @@ int symhss_build(symhss_t h, void* stream) {
     CK(cudaMemsetAsync(h->status.p, 0, sizeof(int), s));
     CK(cudaEventRecord(h->ev[0], s));
     CK(cudaStreamWaitEvent(cs, h->ev[0], 0));  // the compression follows earlier work on s
-    int rc = SYMHSS_OK;
+    // the leaf blocks' assembly and LU need no compression: queued first on s, they run
+    // while height 0 is compressed on cs
+    int rc = assemble_and_lu(h, 0, s, pairs);
+    if (rc) return rc;
     if (h->maxdepth > 0) {
       rc = compress_height(h, 0, cs);
       if (!rc) rc = read_status(h, cs);
@@ -1653,7 +1658,7 @@ int symhss_build(symhss_t h, void* stream) {
     for (int t = 0; t <= h->maxdepth; ++t) {
       // height t is compressed (its stream was synchronised): factor it on s while the
       // next height is compressed on cs
-      rc = factor_height(h, t, s, pairs);
+      rc = factor_height(h, t, s, pairs, t == 0);
       if (rc) return rc;
       if (t + 1 < h->maxdepth) {
         rc = compress_height(h, t + 1, cs);
