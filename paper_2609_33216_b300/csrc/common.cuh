@@ -402,6 +402,8 @@ struct GemmLaunch {
   double2* C;
   const GemmJob* jobs;
   int njobs;
+  int max_m = 0;  // largest m and n over the jobs (0: unknown, the tiled kernel runs)
+  int max_n = 0;
 };
 cudaError_t launch_gemm(const GemmLaunch& a, cudaStream_t s);
 

@@ -80,12 +80,16 @@ __global__ void __launch_bounds__(kCtaThreads) getrs_cta_kernel(const RsLaunch a
   const int c = blockIdx.y;
   if (n > a.max_n || n < 0 || c >= jb.nrhs) return;  // uniform per block
   CT* x = reinterpret_cast<CT*>(smem_raw);
-  int* perm = reinterpret_cast<int*>(x + a.max_n);
+  CT* dinv = x + a.max_n;
+  int* perm = reinterpret_cast<int*>(dinv + a.max_n);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const CT* A = rs_a<CT>(a) + jb.a_off;
   const int lda = jb.lda;
   CT* b = rs_b<CT>(a) + jb.b_off + (long long)c * jb.ldb;
   build_perm(perm, a.piv + jb.piv_off, n);
+  // the reciprocals of U's diagonal, all at once: the serial 32-row solves below then
+  // carry only multiplications on their dependency chain
+  for (int i = tid; i < n; i += kCtaThreads) dinv[i] = cinv(A[i + (long long)i * lda]);
   __syncthreads();
   for (int i = tid; i < n; i += kCtaThreads) x[i] = b[perm[i]];
   __syncthreads();
@@ -101,10 +105,16 @@ __global__ void __launch_bounds__(kCtaThreads) getrs_cta_kernel(const RsLaunch a
       if (lane < w) x[kb + lane] = xr;
     }
     __syncthreads();
+    // rows below: two independent partial sums halve the FP64 dependency chain
     for (int i = kb + w + tid; i < n; i += kCtaThreads) {
-      CT acc = x[i];
-      for (int q = 0; q < w; ++q) acc = cfms(A[i + (long long)(kb + q) * lda], x[kb + q], acc);
-      x[i] = acc;
+      CT acc0 = x[i], acc1 = make_c<CT>(0.0, 0.0);
+      int q = 0;
+      for (; q + 1 < w; q += 2) {
+        acc0 = cfms(A[i + (long long)(kb + q) * lda], x[kb + q], acc0);
+        acc1 = cfms(A[i + (long long)(kb + q + 1) * lda], x[kb + q + 1], acc1);
+      }
+      if (q < w) acc0 = cfms(A[i + (long long)(kb + q) * lda], x[kb + q], acc0);
+      x[i] = cadd(acc0, acc1);
     }
     __syncthreads();
   }
@@ -113,8 +123,9 @@ __global__ void __launch_bounds__(kCtaThreads) getrs_cta_kernel(const RsLaunch a
     const int w = min(32, n - kb);
     if (warp == 0) {
       CT xr = lane < w ? x[kb + lane] : make_c<CT>(0.0, 0.0);
+      const CT dl = lane < w ? dinv[kb + lane] : make_c<CT>(0.0, 0.0);
       for (int q = w - 1; q >= 0; --q) {
-        if (lane == q) xr = cmul(xr, cinv(A[kb + q + (long long)(kb + q) * lda]));
+        if (lane == q) xr = cmul(xr, dl);
         const CT xq = make_c<CT>(__shfl_sync(0xffffffffu, xr.x, q), __shfl_sync(0xffffffffu, xr.y, q));
         if (lane < q) xr = cfms(A[kb + lane + (long long)(kb + q) * lda], xq, xr);
       }
@@ -122,9 +133,14 @@ __global__ void __launch_bounds__(kCtaThreads) getrs_cta_kernel(const RsLaunch a
     }
     __syncthreads();
     for (int i = tid; i < kb; i += kCtaThreads) {
-      CT acc = x[i];
-      for (int q = 0; q < w; ++q) acc = cfms(A[i + (long long)(kb + q) * lda], x[kb + q], acc);
-      x[i] = acc;
+      CT acc0 = x[i], acc1 = make_c<CT>(0.0, 0.0);
+      int q = 0;
+      for (; q + 1 < w; q += 2) {
+        acc0 = cfms(A[i + (long long)(kb + q) * lda], x[kb + q], acc0);
+        acc1 = cfms(A[i + (long long)(kb + q + 1) * lda], x[kb + q + 1], acc1);
+      }
+      if (q < w) acc0 = cfms(A[i + (long long)(kb + q) * lda], x[kb + q], acc0);
+      x[i] = cadd(acc0, acc1);
     }
     __syncthreads();
   }
@@ -139,7 +155,7 @@ cudaError_t getrs_impl(const RsLaunch& a, cudaStream_t s) {
   if (a.njobs <= 0 || a.max_rhs <= 0) return cudaSuccess;
   cudaError_t e;
   if (a.max_rhs <= 4) {
-    const size_t smem = (size_t)max_n * (sizeof(CT) + sizeof(int));
+    const size_t smem = (size_t)max_n * (2 * sizeof(CT) + sizeof(int));
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
     e = cudaFuncSetAttribute(getrs_cta_kernel<CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -145,6 +145,48 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmLaunch a) {
   }
 }
 
+// The same product for narrow B (at most kGemvCols columns: the solve phase and the
+// refinement matvecs carry one or a few right-hand sides): a block takes 32 rows of C, lane =
+// row, and its 8 warps split the inner dimension; the partial sums meet in shared memory.
+// Every FP64 instruction works on 32 useful lanes, where 16 x 16 output tiles would leave
+// all but one tile column idle.
+constexpr int kGemvCols = 4;
+__global__ void __launch_bounds__(256) gemv_kernel(const GemmLaunch a) {
+  __shared__ double2 part[8][kGemvCols][32];
+  const GemmJob jb = a.jobs[blockIdx.x];
+  const int i0 = blockIdx.y * 32;
+  if (i0 >= jb.m || jb.n > kGemvCols) return;  // uniform per block
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i = i0 + lane, nc = jb.n;
+  const int kper = (jb.k + 7) / 8;
+  const int l0 = warp * kper, l1 = min(jb.k, l0 + kper);
+  const double2* A = a.A + jb.a_off;
+  const double2* B = a.B + jb.b_off;
+  double2 acc[kGemvCols];
+#pragma unroll
+  for (int c = 0; c < kGemvCols; ++c) acc[c] = make_double2(0.0, 0.0);
+  if (i < jb.m) {
+    for (int l = l0; l < l1; ++l) {
+      const double2 av = A[i + (long long)l * jb.lda];
+#pragma unroll
+      for (int c = 0; c < kGemvCols; ++c)
+        if (c < nc) acc[c] = cfma(av, B[l + (long long)c * jb.ldb], acc[c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < kGemvCols; ++c) part[warp][c][lane] = acc[c];
+  __syncthreads();
+  if (warp < nc && i < jb.m) {  // warp c sums column c over the 8 slices
+    double2 v = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int w = 0; w < 8; ++w) v = cadd(v, part[w][warp][lane]);
+    double2* c = a.C + jb.c_off + i + (long long)warp * jb.ldc;
+    double2 r = make_double2(jb.alpha * v.x, jb.alpha * v.y);
+    if (jb.beta != 0.0) r = make_double2(r.x + jb.beta * c->x, r.y + jb.beta * c->y);
+    *c = r;
+  }
+}
+
 template <typename CT>
 __global__ void __launch_bounds__(kOpsThreads) copy_kernel(const CT* src, CT* dst,
                                                            const CopyJob* jobs) {
@@ -222,6 +264,11 @@ cudaError_t launch_apply_r(const BasisLaunch& a, cudaStream_t s) {
 
 cudaError_t launch_gemm(const GemmLaunch& a, cudaStream_t s) {
   if (a.njobs <= 0) return cudaSuccess;
+  if (a.max_m > 0 && a.max_n > 0 && a.max_n <= kGemvCols) {
+    gemv_kernel<<<dim3(a.njobs, (a.max_m + 31) / 32), 256, 0, s>>>(a);
+    symhss::count_launches(1);
+    return cudaGetLastError();
+  }
   dim3 grid(a.njobs, 8);
   gemm_kernel<<<grid, 256, 0, s>>>(a);
   symhss::count_launches(1);

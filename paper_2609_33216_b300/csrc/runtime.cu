@@ -1700,6 +1700,12 @@ namespace symhss {
 namespace {
 
 // One application of the factorisation's inverse: x = B^{-1} f (Sec. 4.2 up / down pass).
+int gemm_max_m(const std::vector<GemmJob>& jobs) {
+  int m = 0;
+  for (const GemmJob& j : jobs) m = std::max(m, j.m);
+  return m;
+}
+
 int solve_core(symhss_s* h, const double2* f, double2* xo, int nrhs, cudaStream_t s) {
   const long long ldv = 2LL * h->ntot;
   (void)ldv;
@@ -1800,6 +1806,7 @@ int solve_core(symhss_s* h, const double2* f, double2* xo, int nrhs, cudaStream_
       GemmLaunch ga;
       ga.A = H.At.as<double2>(); ga.B = H.TMP.as<double2>(); ga.C = H.FT.as<double2>();
       ga.jobs = reinterpret_cast<const GemmJob*>(sb + ogj); ga.njobs = (int)gj.size();
+      ga.max_m = gemm_max_m(gj); ga.max_n = nrhs;
       TIMED(SYMHSS_K_OTHER, 0.0, launch_gemm(ga, s));
     }
   }
@@ -1839,6 +1846,7 @@ int solve_core(symhss_s* h, const double2* f, double2* xo, int nrhs, cudaStream_
     GemmLaunch ga;
     ga.A = H.At.as<double2>(); ga.B = HP.G.as<double2>(); ga.C = H.FT.as<double2>();
     ga.jobs = reinterpret_cast<const GemmJob*>(sb + o1); ga.njobs = (int)g1.size();
+    ga.max_m = gemm_max_m(g1); ga.max_n = nrhs;
     double w_dn = 0;
     for (const auto& j : g1) w_dn += 8.0 * (double)j.m * j.n * j.k;
     for (const auto& j : g2) w_dn += 8.0 * (double)j.m * j.n * j.k;
@@ -1846,6 +1854,7 @@ int solve_core(symhss_s* h, const double2* f, double2* xo, int nrhs, cudaStream_
     GemmLaunch gb;
     gb.A = H.X.as<double2>(); gb.B = H.FT.as<double2>(); gb.C = H.G.as<double2>();
     gb.jobs = reinterpret_cast<const GemmJob*>(sb + o2); gb.njobs = (int)g2.size();
+    gb.max_m = gemm_max_m(g2); gb.max_n = nrhs;
     TIMED(SYMHSS_K_OTHER, 0.0, launch_gemm(gb, s));
   }
   {
@@ -1948,6 +1957,7 @@ int matvec_core(symhss_s* h, const double2* xin, double2* yout, int nrhs, cudaSt
     GemmLaunch ga;
     ga.A = H.Dop.as<double2>(); ga.B = H.XV.as<double2>(); ga.C = H.ZV.as<double2>();
     ga.jobs = reinterpret_cast<const GemmJob*>(sb + ogj); ga.njobs = (int)gj.size();
+    ga.max_m = gemm_max_m(gj); ga.max_n = nrhs;
     CK(launch_gemm(ga, s));
     if (!bj.empty()) {
       BasisLaunch ba;
