@@ -72,9 +72,33 @@ __global__ void getrs_kernel(const RsLaunch a, int warps) {
   for (int i = lane; i < n; i += 32) b[i] = sb[i];
 }
 
+// rows [r0, r1) of x (stride kCtaThreads from r0 + tid) -= A[rows, kb .. kb + w) x[kb .. kb + w):
+// for full 32-column blocks the loop is unrolled so that the 32 loads of a row are in
+// flight together, and four partial sums shorten the FP64 dependency chain
+template <typename CT>
+__device__ __forceinline__ void cta_update_rows(const CT* A, int lda, CT* x, int kb, int w, int r0, int r1) {
+  for (int i = r0 + (int)threadIdx.x; i < r1; i += kCtaThreads) {
+    const CT* ai = A + i + (long long)kb * lda;
+    CT acc0 = x[i], acc1 = make_c<CT>(0.0, 0.0), acc2 = acc1, acc3 = acc1;
+    if (w == 32) {
+#pragma unroll
+      for (int q = 0; q < 32; q += 4) {
+        acc0 = cfms(ai[(long long)q * lda], x[kb + q], acc0);
+        acc1 = cfms(ai[(long long)(q + 1) * lda], x[kb + q + 1], acc1);
+        acc2 = cfms(ai[(long long)(q + 2) * lda], x[kb + q + 2], acc2);
+        acc3 = cfms(ai[(long long)(q + 3) * lda], x[kb + q + 3], acc3);
+      }
+    } else {
+      for (int q = 0; q < w; ++q) acc0 = cfms(ai[(long long)q * lda], x[kb + q], acc0);
+    }
+    x[i] = cadd(cadd(acc0, acc1), cadd(acc2, acc3));
+  }
+}
+
 template <typename CT>
 __global__ void __launch_bounds__(kCtaThreads) getrs_cta_kernel(const RsLaunch a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ CT tri[32 * 32];  // the current 32 x 32 diagonal block, column-major
   const RsJob jb = a.jobs[blockIdx.x];
   const int n = jb.n;
   const int c = blockIdx.y;
@@ -92,56 +116,47 @@ __global__ void __launch_bounds__(kCtaThreads) getrs_cta_kernel(const RsLaunch a
   for (int i = tid; i < n; i += kCtaThreads) dinv[i] = cinv(A[i + (long long)i * lda]);
   __syncthreads();
   for (int i = tid; i < n; i += kCtaThreads) x[i] = b[perm[i]];
-  __syncthreads();
-  // forward substitution with the unit lower factor, 32 rows at a time
+  // forward substitution with the unit lower factor, 32 rows at a time; the diagonal
+  // block is staged in shared memory so that warp 0's serial solve waits on no L2 load
   for (int kb = 0; kb < n; kb += 32) {
     const int w = min(32, n - kb);
+    for (int e = tid; e < 32 * w; e += kCtaThreads) {
+      const int r = e & 31, q = e >> 5;
+      tri[e] = r < w ? A[kb + r + (long long)(kb + q) * lda] : make_c<CT>(0.0, 0.0);
+    }
+    __syncthreads();
     if (warp == 0) {
       CT xr = lane < w ? x[kb + lane] : make_c<CT>(0.0, 0.0);
       for (int q = 0; q < w; ++q) {
         const CT xq = make_c<CT>(__shfl_sync(0xffffffffu, xr.x, q), __shfl_sync(0xffffffffu, xr.y, q));
-        if (lane > q && lane < w) xr = cfms(A[kb + lane + (long long)(kb + q) * lda], xq, xr);
+        if (lane > q && lane < w) xr = cfms(tri[q * 32 + lane], xq, xr);
       }
       if (lane < w) x[kb + lane] = xr;
     }
     __syncthreads();
-    // rows below: two independent partial sums halve the FP64 dependency chain
-    for (int i = kb + w + tid; i < n; i += kCtaThreads) {
-      CT acc0 = x[i], acc1 = make_c<CT>(0.0, 0.0);
-      int q = 0;
-      for (; q + 1 < w; q += 2) {
-        acc0 = cfms(A[i + (long long)(kb + q) * lda], x[kb + q], acc0);
-        acc1 = cfms(A[i + (long long)(kb + q + 1) * lda], x[kb + q + 1], acc1);
-      }
-      if (q < w) acc0 = cfms(A[i + (long long)(kb + q) * lda], x[kb + q], acc0);
-      x[i] = cadd(acc0, acc1);
-    }
+    cta_update_rows(A, lda, x, kb, w, kb + w, n);
     __syncthreads();
   }
   // back substitution with the upper factor, 32 rows at a time from the bottom
   for (int kb = ((n - 1) / 32) * 32; n > 0 && kb >= 0; kb -= 32) {
     const int w = min(32, n - kb);
+    for (int e = tid; e < 32 * w; e += kCtaThreads) {
+      const int r = e & 31, q = e >> 5;
+      tri[e] = r < w ? A[kb + r + (long long)(kb + q) * lda] : make_c<CT>(0.0, 0.0);
+    }
+    __syncthreads();
     if (warp == 0) {
       CT xr = lane < w ? x[kb + lane] : make_c<CT>(0.0, 0.0);
       const CT dl = lane < w ? dinv[kb + lane] : make_c<CT>(0.0, 0.0);
       for (int q = w - 1; q >= 0; --q) {
         if (lane == q) xr = cmul(xr, dl);
         const CT xq = make_c<CT>(__shfl_sync(0xffffffffu, xr.x, q), __shfl_sync(0xffffffffu, xr.y, q));
-        if (lane < q) xr = cfms(A[kb + lane + (long long)(kb + q) * lda], xq, xr);
+        if (lane < q) xr = cfms(tri[q * 32 + lane], xq, xr);
       }
       if (lane < w) x[kb + lane] = xr;
     }
     __syncthreads();
-    for (int i = tid; i < kb; i += kCtaThreads) {
-      CT acc0 = x[i], acc1 = make_c<CT>(0.0, 0.0);
-      int q = 0;
-      for (; q + 1 < w; q += 2) {
-        acc0 = cfms(A[i + (long long)(kb + q) * lda], x[kb + q], acc0);
-        acc1 = cfms(A[i + (long long)(kb + q + 1) * lda], x[kb + q + 1], acc1);
-      }
-      if (q < w) acc0 = cfms(A[i + (long long)(kb + q) * lda], x[kb + q], acc0);
-      x[i] = cadd(acc0, acc1);
-    }
+    cta_update_rows(A, lda, x, kb, w, 0, kb);
     __syncthreads();
   }
   for (int i = tid; i < n; i += kCtaThreads) b[i] = x[i];

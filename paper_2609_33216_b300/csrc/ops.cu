@@ -2,6 +2,8 @@
 // interpolation bases, R * X, small GEMMs (Atilde R g, f~ - Atilde y, g - X z),
 // block copies (parent diagonal-block assembly), leaf gather / scatter and the
 // plane-wave right-hand side.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace symhss {
@@ -105,9 +107,14 @@ __global__ void __launch_bounds__(kOpsThreads) apply_r_kernel(const BasisLaunch 
       const int j = (int)(e % pt.r);
       const int c = (int)(e / pt.r);
       const CT* ic = in + (long long)c * jb.ld_in;
-      CT s = ic[q[j]];
-      for (int i = 0; i < nr; ++i) s = cfma(to_c<CT>(T[j + (long long)i * pt.r]), ic[q[pt.r + i]], s);
-      out[pt.col0 + j + (long long)c * jb.ld_out] = s;
+      CT s0 = ic[q[j]], s1 = make_c<CT>(0.0, 0.0);  // two partial sums: half the dependency chain
+      int i = 0;
+      for (; i + 1 < nr; i += 2) {
+        s0 = cfma(to_c<CT>(T[j + (long long)i * pt.r]), ic[q[pt.r + i]], s0);
+        s1 = cfma(to_c<CT>(T[j + (long long)(i + 1) * pt.r]), ic[q[pt.r + i + 1]], s1);
+      }
+      if (i < nr) s0 = cfma(to_c<CT>(T[j + (long long)i * pt.r]), ic[q[pt.r + i]], s0);
+      out[pt.col0 + j + (long long)c * jb.ld_out] = cadd(s0, s1);
     }
   }
 }
@@ -255,7 +262,9 @@ cudaError_t launch_basis_dense(const BasisLaunch& a, cudaStream_t s) {
 
 cudaError_t launch_apply_r(const BasisLaunch& a, cudaStream_t s) {
   if (a.njobs <= 0) return cudaSuccess;
-  dim3 grid(a.njobs, 4);
+  // blocks per job so that even the few boxes of the top levels spread over every SM
+  const int per_job = std::max(4, std::min(64, (4 * 148 + a.njobs - 1) / a.njobs));
+  dim3 grid(a.njobs, per_job);
   if (a.out32) apply_r_kernel<float2><<<grid, kOpsThreads, 0, s>>>(a);
   else apply_r_kernel<double2><<<grid, kOpsThreads, 0, s>>>(a);
   symhss::count_launches(1);
