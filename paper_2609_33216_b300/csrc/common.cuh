@@ -67,6 +67,21 @@ __device__ __forceinline__ float2 cinv(float2 a) {
     return make_float2(r / d, -1.0f / d);
   }
 }
+// Reciprocal of an LU pivot on a serial dependency chain: conj(a) / |a|^2 carries one
+// division where Smith's method carries two; Smith's scaled form is kept for |a|^2 outside
+// the normal range, where the plain form would overflow or underflow.
+__device__ __forceinline__ double2 cinv_pivot(double2 a) {
+  const double s2 = fma(a.x, a.x, a.y * a.y);
+  if (!(s2 > 1e-300 && s2 < 1e300)) return cinv(a);
+  const double r = 1.0 / s2;
+  return make_double2(a.x * r, -a.y * r);
+}
+__device__ __forceinline__ float2 cinv_pivot(float2 a) {
+  const float s2 = fmaf(a.x, a.x, a.y * a.y);
+  if (!(s2 > 1e-36f && s2 < 1e36f)) return cinv(a);
+  const float r = 1.0f / s2;
+  return make_float2(a.x * r, -a.y * r);
+}
 // complex constant / conversion in the element type CT (double2 or float2)
 template <typename CT> __device__ __forceinline__ CT make_c(double re, double im);
 template <> __device__ __forceinline__ double2 make_c<double2>(double re, double im) { return make_double2(re, im); }

@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(kPanelThreads) panel_kernel(const LuLaunch a, 
     if (tid < w) {
       const CT v = A[jc + (long long)(j + tid) * ld];
       s_row[tid] = v;
-      if (tid == c) s_inv = zero ? make_c<CT>(0.0, 0.0) : cinv(v);
+      if (tid == c) s_inv = zero ? make_c<CT>(0.0, 0.0) : cinv_pivot(v);
     }
     __syncthreads();
     const CT inv = s_inv;
@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(THREADS) panel_smem_kernel(const LuLaunch a, i
         const int p = zero ? c : bi;
         s_piv = p;
         s_zero = zero;
-        s_inv = zero ? make_c<CT>(0.0, 0.0) : cinv(P[c * rows + p]);
+        s_inv = zero ? make_c<CT>(0.0, 0.0) : cinv_pivot(P[c * rows + p]);
         piv[j + c] = j + p;
         if (zero) {
           if (a.info[jb.info_idx] == 0) a.info[jb.info_idx] = j + c + 1;
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(kClusterPanelThreads) panel_cluster_kernel(con
       const double2 pv = cl.map_shared_rank(P, p % C)[tid * lmax + p / C];
       prow[tid] = pv;
       rowc[tid] = cl.map_shared_rank(P, c % C)[tid * lmax + c / C];
-      if (tid == c) s_inv = zero ? make_double2(0.0, 0.0) : cinv(pv);
+      if (tid == c) s_inv = zero ? make_double2(0.0, 0.0) : cinv_pivot(pv);
     }
     if (tid == 0 && rank == 0) {
       piv[j + c] = j + p;
@@ -327,16 +327,18 @@ __global__ void __launch_bounds__(256) swap_trsm_warp_kernel(const LuLaunch a, i
   if (j >= n) return;  // uniform per block
   const int w = min(kNb, n - j);
   CT* A = lu_base<CT>(a) + jb.a_off;
-  const int* piv = a.piv + jb.piv_off;
+  __shared__ int piv_s[kNb];
+  if (threadIdx.x < w) piv_s[threadIdx.x] = a.piv[jb.piv_off + j + threadIdx.x];
   for (int e = threadIdx.x; e < w * w; e += 256) {
     const int r = e % w, c = e / w;
     l11[r][c] = A[j + r + (long long)(j + c) * ld];
   }
+  __syncthreads();
   if (threadIdx.x == 0) {
     int cnt = w;
     for (int r = 0; r < w; ++r) rows_s[r] = j + r;
     for (int c = 0; c < w; ++c) {
-      const int p = piv[j + c];
+      const int p = piv_s[c];
       if (p >= j + w) {
         bool seen = false;
         for (int q = w; q < cnt; ++q) seen |= (rows_s[q] == p);
@@ -347,7 +349,7 @@ __global__ void __launch_bounds__(256) swap_trsm_warp_kernel(const LuLaunch a, i
     int content[2 * kNb];
     for (int l = 0; l < cnt; ++l) content[l] = rows_s[l];
     for (int c = 0; c < w; ++c) {
-      const int p = piv[j + c];
+      const int p = piv_s[c];
       if (p == j + c) continue;
       int lp = -1;
       for (int q = 0; q < cnt; ++q)
