@@ -423,7 +423,8 @@ struct GemmLaunch {
 cudaError_t launch_gemm(const GemmLaunch& a, cudaStream_t s);
 
 // dst block (rows x cols, ldd) = src block (lds); identity fill when src_off < 0
-struct CopyJob { long long src_off, dst_off; int rows, cols, lds, ldd; };
+// dst(i, j) = src(i, j) for a rows x cols block; trans != 0: dst(j, i) = src(i, j)
+struct CopyJob { long long src_off, dst_off; int rows, cols, lds, ldd; int trans = 0; int pad_ = 0; };
 cudaError_t launch_copy_blocks(const double2* src, double2* dst, const CopyJob* jobs, int njobs,
                                cudaStream_t s);
 cudaError_t launch_copy_blocks32(const float2* src, float2* dst, const CopyJob* jobs, int njobs, cudaStream_t s);

@@ -205,7 +205,8 @@ __global__ void __launch_bounds__(kOpsThreads) copy_kernel(const CT* src, CT* ds
     CT v;
     if (jb.src_off >= 0) v = src[jb.src_off + i + (long long)j * jb.lds];
     else v = make_c<CT>(i == j ? 1.0 : 0.0, 0.0);
-    dst[jb.dst_off + i + (long long)j * jb.ldd] = v;
+    if (jb.trans) dst[jb.dst_off + j + (long long)i * jb.ldd] = v;
+    else dst[jb.dst_off + i + (long long)j * jb.ldd] = v;
   }
 }
 

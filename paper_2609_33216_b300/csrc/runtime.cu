@@ -1060,7 +1060,7 @@ int assemble_and_lu(symhss_s* h, int t, cudaStream_t s, long long& pairs) {
   CK(H.piv.ensure(piv_total * sizeof(int)));
   CK(H.info.ensure(refs.size() * sizeof(int)));
   TileBuilder tb;
-  std::vector<CopyJob> copies;
+  std::vector<CopyJob> copies, mirrors;
   std::vector<int> t0, t1, u0, u1;
   for (const BoxRef& rf : refs) {
     HBox& bx = *rf.bx;
@@ -1078,9 +1078,23 @@ int assemble_and_lu(symhss_s* h, int t, cudaStream_t s, long long& pairs) {
       skeleton(c1, true, 0, t0); skeleton(c1, true, 1, t1);
       skeleton(c2, false, 0, u0); skeleton(c2, false, 1, u1);
       tb.add(h->mark, t0, 0, t1, c1.rrank[0], u0, a1, u1, a1 + c2.rank[0], bx.d_off, bx.size, flags, rf.p);
-      skeleton(c2, true, 0, t0); skeleton(c2, true, 1, t1);
-      skeleton(c1, false, 0, u0); skeleton(c1, false, 1, u1);
-      tb.add(h->mark, t0, a1, t1, a1 + c2.rrank[0], u0, 0, u1, c1.rank[0], bx.d_off, bx.size, flags, rf.p);
+      if (sym) {
+        // one ID is both bases and the off-diagonal entries are symmetric, so the block of
+        // child 2's rows against child 1's columns is the transpose of the one just tiled
+        CopyJob tj;
+        tj.src_off = bx.d_off + (long long)a1 * bx.size;
+        tj.dst_off = bx.d_off + a1;
+        tj.rows = a1;
+        tj.cols = bx.size - a1;
+        tj.lds = bx.size;
+        tj.ldd = bx.size;
+        tj.trans = 1;
+        mirrors.push_back(tj);
+      } else {
+        skeleton(c2, true, 0, t0); skeleton(c2, true, 1, t1);
+        skeleton(c1, false, 0, u0); skeleton(c1, false, 1, u1);
+        tb.add(h->mark, t0, a1, t1, a1 + c2.rrank[0], u0, 0, u1, c1.rank[0], bx.d_off, bx.size, flags, rf.p);
+      }
       CopyJob cj;
       cj.src_off = c1.rx_off; cj.dst_off = bx.d_off; cj.rows = a1; cj.cols = a1; cj.lds = a1; cj.ldd = bx.size;
       copies.push_back(cj);
@@ -1095,7 +1109,12 @@ int assemble_and_lu(symhss_s* h, int t, cudaStream_t s, long long& pairs) {
   if (!copies.empty()) {
     Packer pk;
     pk.add(copies);
+    const size_t om = pk.add(mirrors);
     CK(pk.upload(H.cjobs, s));
+    if (!mirrors.empty())
+      TIMED(SYMHSS_K_OTHER, 0.0, launch_copy_blocks(H.D.as<double2>(), H.D.as<double2>(),
+                                                    reinterpret_cast<const CopyJob*>(H.cjobs.as<char>() + om),
+                                                    (int)mirrors.size(), s));
     // the children's Atilde live in the At buffer one height down
     TIMED(SYMHSS_K_OTHER, 0.0, launch_copy_blocks(h->heights[t - 1].At.as<double2>(), H.D.as<double2>(),
                                                   H.cjobs.as<CopyJob>(), (int)copies.size(), s));
