@@ -169,22 +169,37 @@ __global__ void __launch_bounds__(kThreads) cpqr_cluster_kernel(const IdLaunch a
     if (tid == 0) { done[p] = 1; order[k] = p; }
     __syncthreads();
     const double tau = s_tau;
-    // 4. apply to owned remaining columns, recompute their remaining norms
-    for (int j = rank + C * warp; j < n; j += C * kWarps) {
-      if (done[j]) continue;
-      double2* col = M + (long long)j * ld;
-      double2 w = make_double2(0.0, 0.0);
-      for (int i = k + lane; i < m; i += 32) w = cadd(w, cconjmul(vbuf[i - k], col[i]));
-      w = warp_csum(w);
-      w = make_double2(w.x * tau, w.y * tau);
-      double ns = 0.0;
-      for (int i = k + lane; i < m; i += 32) {
-        const double2 c = cfms(vbuf[i - k], w, col[i]);
-        col[i] = c;
-        if (i > k) ns += cabs2(c);
+    // 4. apply to owned remaining columns, recompute their remaining norms: 8 lanes per
+    //    column, 4 columns per warp (each column segment is one 128-byte line; the lane sums
+    //    take 3 shuffle levels instead of 5, and fewer lanes idle at the column's end)
+    {
+      const int grp = lane >> 3, gl = lane & 7;
+      const int nown = (n - rank + C - 1) / C;  // owned columns: j = rank + C * t, t < nown
+      for (int t0 = 4 * warp; t0 < nown; t0 += 4 * kWarps) {  // uniform per warp
+        const int t = t0 + grp;
+        const int j = rank + C * t;
+        const bool act = t < nown && j < n && !done[j];
+        double2* col = M + (long long)(act ? j : 0) * ld;
+        double2 w = make_double2(0.0, 0.0);
+        if (act)
+          for (int i = k + gl; i < m; i += 8) w = cadd(w, cconjmul(vbuf[i - k], col[i]));
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) {
+          w.x += __shfl_xor_sync(0xffffffffu, w.x, o);
+          w.y += __shfl_xor_sync(0xffffffffu, w.y, o);
+        }
+        w = make_double2(w.x * tau, w.y * tau);
+        double ns = 0.0;
+        if (act)
+          for (int i = k + gl; i < m; i += 8) {
+            const double2 c = cfms(vbuf[i - k], w, col[i]);
+            col[i] = c;
+            if (i > k) ns += cabs2(c);
+          }
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) ns += __shfl_xor_sync(0xffffffffu, ns, o);
+        if (act && gl == 0) norms[j] = sqrt(ns);
       }
-      ns = warp_sum(ns);
-      if (lane == 0) norms[j] = sqrt(ns);
     }
     if (rank == owner && tid == 0) M[k + (long long)p * ld] = s_alpha;
     // the owner rewrites vbuf only after the next step's first cluster barrier,
