@@ -542,7 +542,7 @@ def main():
                     help="compress and factor through the pipelined build call (two streams)")
     ap.add_argument("--autotune", type=int, default=1, help="run the library's launch autotuner before timing")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
-                    help="mixed: complex64 factorisation + one refinement step against the FP64 operator")
+                    help="mixed: complex64 factorisation + iterative refinement (two steps) against the FP64 operator")
     args = ap.parse_args()
     if args.profile:
         run_profile(args)
