@@ -153,7 +153,7 @@ def test_attached_proposer_keeps_solution_and_reports_id_time(mods, trained):
 
 
 def test_proposer_gain_on_high_frequency_star(mods):
-    """Config-5 workload (262144-node star, k 100 / 150, tol 1e-8): the default rank estimate
+    """The high-frequency star workload (262144 nodes, k 100 / 150, tol 1e-8): the default rank estimate
     (1.7x the rank one level down) is too thin where ranks grow faster, so IDs are continued
     or redone; the trained network sizes the sketches and the ID-side time drops."""
     P, SV, S = mods
