@@ -18,10 +18,13 @@ hss       Proxy-method compression with column IDs (Sec. 4.1), the symmetric
 
 Parity status
 -------------
-Every function is pinned by tests under ``tests/test_oracle_*.py``.  The one
-unpinned quantity is the exact value of the paper's one-point correction
-constants beyond what third-order convergence fixes: the paper does not print
-them (Sec. 3.1), so the diagonal entries follow the reading derived in
-``kernels.py`` and are pinned only through the O(h^3) convergence of the disk
-solution and the transparent-obstacle identity ("parity unpinned" beyond that).
+Every function is pinned by tests under ``tests/test_oracle_*.py``.  The paper does not
+print its one-point correction terms (Sec. 3.1); the diagonal entries follow the readings
+derived in ``kernels.py`` and ``pmchwt.py`` and are pinned by mathematics rather than by
+printed values: the O(h^3) convergence of the disk solution and of nested node sets on a
+non-convex star, the transparent-obstacle identity, and the limits of the off-diagonal
+kernels along the curve (D~ = D*~ = -kappa / 4 pi; the constant term of the hypersingular
+kernel, kappa^2 / 24 pi plus the parametrisation-speed term).  What stays unpinned is only
+whether the paper's own correction weights differ from these beyond what the convergence
+orders fix ("parity unpinned" for those constants, which the paper does not give).
 """

@@ -42,14 +42,14 @@ def bm_blocks(obs: Points, src: Points, prm: Params, scaled: bool = False):
     g1, d1, ds1, n1 = _layer_kernels(prm.k1, r, a, b, nn)
     if same.any():
         oi, si = np.nonzero(same)
-        wi, ki = obs.w[oi], obs.kappa[oi]
+        wi, ki, hi = obs.w[oi], obs.kappa[oi], obs.hs[oi]
         g0[oi, si] = diag_S(prm.k0, wi)
         g1[oi, si] = diag_S(prm.k1, wi)
         dd = diag_D(ki)
         d0[oi, si] = dd
         ds0[oi, si] = dd
         d1[oi, si] = dd
-        n0[oi, si] = diag_N(prm.k0, wi, ki)
+        n0[oi, si] = diag_N(prm.k0, wi, ki, hi)
     wgt = obs.w[:, None] * src.w[None, :] if scaled else np.broadcast_to(src.w[None, :], dx.shape)
     a11 = wgt * (-e0 * g0 - alpha * e0 * ds0)
     a12 = wgt * (d0 + alpha * n0)

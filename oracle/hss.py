@@ -195,8 +195,7 @@ def _rows_points(pts: Points, ids_by_eq) -> Tuple[Points, np.ndarray]:
 
 
 def _stack(a: Points, b: Points) -> Points:
-    return Points(*(np.concatenate([u, v]) for u, v in zip(
-        (a.x, a.y, a.nx, a.ny, a.w, a.kappa, a.gid), (b.x, b.y, b.nx, b.ny, b.w, b.kappa, b.gid))))
+    return Points(*(np.concatenate([u, v]) for u, v in zip(a.fields(), b.fields())))
 
 
 class HSS:

@@ -50,6 +50,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
+from fractions import Fraction
 from typing import Optional, Sequence, Tuple
 
 import numpy as np
@@ -73,9 +74,63 @@ class Params:
         return Params(k0, k1, eps0, eps0 * (k1 / k0) ** 2)
 
 
+def central_weights(m: int, order: int):
+    """Weights c_{-m..m} of the central difference of the given derivative order with
+    2m + 1 equispaced points (unit spacing), as exact rationals: the unique weights that
+    reproduce every polynomial of degree <= 2m, i.e. sum_j c_j j^p = order! [p = order]
+    for p = 0..2m (solved by Gaussian elimination over the rationals)."""
+    js = list(range(-m, m + 1))
+    size = 2 * m + 1
+    rows = [[Fraction(j) ** p for j in js] + [Fraction(math.factorial(order) if p == order else 0)]
+            for p in range(size)]
+    for c in range(size):
+        piv = next(r for r in range(c, size) if rows[r][c] != 0)
+        rows[c], rows[piv] = rows[piv], rows[c]
+        for r in range(size):
+            if r != c and rows[r][c] != 0:
+                f = rows[r][c] / rows[c][c]
+                rows[r] = [a - f * b for a, b in zip(rows[r], rows[c])]
+    return [rows[i][size] / rows[i][i] for i in range(size)]
+
+
+def hypersingular_speed_term(w, m: int = 8) -> np.ndarray:
+    """Speed-dependent part of the constant term of the hypersingular diagonal, per node.
+
+    With the parametrisation speed v = |gamma'| sampled as the trapezoidal weights
+    w_j = v(theta_j) h, the Laplace hypersingular kernel times the source's weight has the
+    expansion A / tau^2 + C + O(tau) in the parameter offset tau, with A = 1 / (2 pi v) and
+    C / v = kappa^2 / (24 pi) + (v''/6 - v'^2 / (4 v)) / (2 pi v^3) (a change of variables
+    from arclength, where the constant is kappa^2 / (24 pi)).  In index units (derivatives
+    with respect to j, so h drops out) the second part is s_j / w_j^2 with
+        s_j = (l2_j / 6 - l1_j^2 / 4) / (2 pi),   l1 = (dw/dj) / w,   l2 = (d^2 w/dj^2) / w,
+    and this function returns s (dimensionless; zero on a circle).  The derivatives of the
+    periodic sequence w are central differences of order 2m (m = 8, fewer on very short
+    curves), which are exact to rounding for the smooth curves used here.
+    """
+    w = np.asarray(w, dtype=np.float64)
+    n = w.shape[0]
+    m = max(0, min(m, (n - 1) // 2))
+    if m == 0:
+        return np.zeros(n)
+    c1 = [float(c) for c in central_weights(m, 1)]
+    c2 = [float(c) for c in central_weights(m, 2)]
+    d1 = np.zeros(n)
+    d2 = np.zeros(n)
+    for k, j in enumerate(range(-m, m + 1)):
+        sh = np.roll(w, -j)  # sh[i] = w[i + j] (periodic)
+        d1 += c1[k] * sh
+        d2 += c2[k] * sh
+    l1, l2 = d1 / w, d2 / w
+    return (l2 / 6.0 - l1 * l1 / 4.0) / (2.0 * math.pi)
+
+
 @dataclasses.dataclass
 class Points:
-    """A set of points: curve nodes (gid >= 0 is the node index) or proxy points (gid = -1)."""
+    """A set of points: curve nodes (gid >= 0 is the node index) or proxy points (gid = -1).
+
+    hs is the per-node speed term of the hypersingular diagonal (hypersingular_speed_term);
+    zero for proxy points and where not given.
+    """
 
     x: np.ndarray
     y: np.ndarray
@@ -84,17 +139,24 @@ class Points:
     w: np.ndarray
     kappa: np.ndarray
     gid: np.ndarray
+    hs: Optional[np.ndarray] = None
+
+    def __post_init__(self):
+        if self.hs is None:
+            self.hs = np.zeros(self.x.shape[0])
 
     @staticmethod
     def from_curve(curve) -> "Points":
         n = curve.x.shape[0]
         return Points(curve.x, curve.y, curve.nx, curve.ny, curve.w, curve.kappa,
-                      np.arange(n, dtype=np.int64))
+                      np.arange(n, dtype=np.int64), hypersingular_speed_term(curve.w))
+
+    def fields(self):
+        return (self.x, self.y, self.nx, self.ny, self.w, self.kappa, self.gid, self.hs)
 
     def take(self, idx) -> "Points":
         idx = np.asarray(idx, dtype=np.int64)
-        return Points(self.x[idx], self.y[idx], self.nx[idx], self.ny[idx], self.w[idx],
-                      self.kappa[idx], self.gid[idx])
+        return Points(*(v[idx] for v in self.fields()))
 
     @staticmethod
     def circle(cx: float, cy: float, radius: float, count: int) -> "Points":
@@ -224,7 +286,7 @@ def dense_matrix(curve, prm: Params, scaled: bool = True) -> np.ndarray:
     """The full 2N x 2N matrix with unknowns ordered [q_1..q_N, u_1..u_N] (Eq. 15 / Sec. 6)."""
     pts = Points.from_curve(curve)
     n = len(pts)
-    both = Points(*(np.concatenate([v, v]) for v in (pts.x, pts.y, pts.nx, pts.ny, pts.w, pts.kappa, pts.gid)))
+    both = Points(*(np.concatenate([v, v]) for v in pts.fields()))
     lab = np.concatenate([np.zeros(n, np.int64), np.ones(n, np.int64)])
     return entries(both, lab, both, lab, prm, scaled)
 
@@ -257,7 +319,7 @@ def matvec_rows(curve, prm: Params, x: np.ndarray, rows: Optional[Sequence[int]]
     pts = Points.from_curve(curve)
     n = len(pts)
     rows = np.arange(2 * n) if rows is None else np.asarray(rows, dtype=np.int64)
-    both = Points(*(np.concatenate([v, v]) for v in (pts.x, pts.y, pts.nx, pts.ny, pts.w, pts.kappa, pts.gid)))
+    both = Points(*(np.concatenate([v, v]) for v in pts.fields()))
     lab = np.concatenate([np.zeros(n, np.int64), np.ones(n, np.int64)])
     out = np.empty(rows.shape[0], dtype=np.complex128)
     step = max(1, (1 << 21) // (2 * n))

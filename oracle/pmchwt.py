@@ -11,14 +11,17 @@ derivatives: the free terms cancel, and the hypersingular parts of N_k0, N_k1 ad
 
 One-point corrected diagonal of the hypersingular kernel (the paper does not print it;
 reading): near the diagonal the Laplace part of N_k is 1/(2 pi sigma^2) + kappa^2/(24 pi)
-+ O(sigma^2) in arclength sigma (exact constant on a circle), i.e. 1/(2 pi |gamma'| tau^2)
-in the parameter tau.  The zeta-corrected trapezoidal rule for FP int g(tau)/tau^2 adds
--2 zeta(2) g(0) / h = -pi^2 g(0) / (3h) at the node, so the diagonal entry (per weight
-w_i = |gamma'_i| h) is -pi / (6 w_i^2), plus the constant kappa^2/(24 pi), plus the
++ O(sigma^2) in arclength sigma (exact constant on a circle).  In the parameter tau of the
+equispaced rule, the kernel times the source's speed v = |gamma'| is A/tau^2 + C + O(tau)
+with A = 1/(2 pi v) and C/v = kappa^2/(24 pi) + (v''/6 - v'^2/(4v))/(2 pi v^3) (the odd
+1/tau term vanishes).  The zeta-corrected trapezoidal rule for FP int f(tau) dtau adds
+-2 zeta(2) A / h = -pi^2 A / (3h) at the node plus the constant C, so the diagonal entry
+(per weight w_i = v_i h) is -pi / (6 w_i^2) + kappa^2/(24 pi) + s_i / w_i^2, where s_i is
+the speed term of kernels.hypersingular_speed_term (zero on a circle), plus the
 log-singular and constant terms of N_k - N_0 (those of the Muller-like N difference for
 one wavenumber):
-    N~_k(i,i) = -pi/(6 w_i^2) + kappa_i^2/(24 pi) + (i/8) k^2 - k^2 (log(k/2) + gamma_E)/(4 pi)
-                + k^2/(8 pi) - (k^2/(4 pi)) log(w_i / 2 pi).
+    N~_k(i,i) = (s_i - pi/6) / w_i^2 + kappa_i^2/(24 pi) + (i/8) k^2
+                - k^2 (log(k/2) + gamma_E)/(4 pi) + k^2/(8 pi) - (k^2/(4 pi)) log(w_i / 2 pi).
 The rule is first order (the error of the corrected 1/tau^2 rule is O(h)), which is the
 O(h) convergence the paper reports for PMCHWT.  S~, D~, D*~ as in kernels.py.
 """
@@ -32,10 +35,11 @@ import numpy as np
 from .kernels import EULER_GAMMA, Params, Points, _layer_kernels, diag_D, diag_S, incident_plane_wave
 
 
-def diag_N(k: float, w, kappa):
-    """One-point corrected N~_k(i,i) (reading in the module docstring)."""
+def diag_N(k: float, w, kappa, hs=0.0):
+    """One-point corrected N~_k(i,i) (reading in the module docstring); hs is the node's
+    speed term (kernels.hypersingular_speed_term)."""
     c = (0.125j * k * k - (k * k / (4.0 * math.pi)) * (math.log(k / 2.0) + EULER_GAMMA) + k * k / (8.0 * math.pi))
-    return (-math.pi / (6.0 * w * w) + kappa * kappa / (24.0 * math.pi) + c
+    return ((hs - math.pi / 6.0) / (w * w) + kappa * kappa / (24.0 * math.pi) + c
             - (k * k / (4.0 * math.pi)) * np.log(w / (2.0 * math.pi)))
 
 
@@ -58,12 +62,12 @@ def pmchwt_blocks(obs: Points, src: Points, prm: Params, scaled: bool = True):
     kn = n0 / e0 + n1 / e1
     if same.any():
         oi, si = np.nonzero(same)
-        wi, ki = obs.w[oi], obs.kappa[oi]
+        wi, ki, hi = obs.w[oi], obs.kappa[oi], obs.hs[oi]
         ks[oi, si] = e0 * diag_S(prm.k0, wi) + e1 * diag_S(prm.k1, wi)
         dd = diag_D(ki)
         kd[oi, si] = 2.0 * dd
         kds[oi, si] = 2.0 * dd
-        kn[oi, si] = diag_N(prm.k0, wi, ki) / e0 + diag_N(prm.k1, wi, ki) / e1
+        kn[oi, si] = diag_N(prm.k0, wi, ki, hi) / e0 + diag_N(prm.k1, wi, ki, hi) / e1
     if scaled:
         wgt = obs.w[:, None] * src.w[None, :]
     else:

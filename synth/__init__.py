@@ -11,6 +11,7 @@ from .curves import (  # noqa: F401
     disk,
     star,
     fourier_star,
+    fourier_star_at,
     random_star_batch,
     workload,
     WORKLOADS,

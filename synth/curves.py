@@ -43,30 +43,48 @@ class Curve:
         return (self.x, self.y, self.nx, self.ny, self.w, self.kappa)
 
 
+def fourier_star_at(theta, modes: Sequence[Tuple[int, float, float]] = ()) -> Dict[str, np.ndarray]:
+    """Closed-form geometry of r(theta) = 1 + sum a*cos(m*theta + phi) at arbitrary parameters.
+
+    Returns the point (x, y), the outward unit normal (nx, ny), the parametrisation speed
+    v = |gamma'|, its first two derivatives dv, ddv with respect to theta, and the signed
+    curvature kappa, all as float64 arrays shaped like ``theta``.
+    """
+    theta = np.asarray(theta, dtype=np.float64)
+    r = np.ones_like(theta)
+    d1 = np.zeros_like(theta)
+    d2 = np.zeros_like(theta)
+    d3 = np.zeros_like(theta)
+    for m, a, phi in modes:
+        arg = m * theta + phi
+        r = r + a * np.cos(arg)
+        d1 = d1 - a * m * np.sin(arg)
+        d2 = d2 - a * m * m * np.cos(arg)
+        d3 = d3 + a * m * m * m * np.sin(arg)
+    c, s = np.cos(theta), np.sin(theta)
+    # derivatives of gamma = r (cos, sin) up to third order
+    x, y = r * c, r * s
+    dx, dy = d1 * c - r * s, d1 * s + r * c
+    ddx = d2 * c - 2.0 * d1 * s - r * c
+    ddy = d2 * s + 2.0 * d1 * c - r * s
+    dddx = d3 * c - 3.0 * d2 * s - 3.0 * d1 * c + r * s
+    dddy = d3 * s + 3.0 * d2 * c - 3.0 * d1 * s - r * c
+    v = np.sqrt(dx * dx + dy * dy)
+    g12 = dx * ddx + dy * ddy
+    dv = g12 / v
+    ddv = (ddx * ddx + ddy * ddy + dx * dddx + dy * dddy) / v - g12 * g12 / v**3
+    return {"x": x, "y": y, "nx": dy / v, "ny": -dx / v, "v": v, "dv": dv, "ddv": ddv,
+            "kappa": (dx * ddy - dy * ddx) / v**3}
+
+
 def fourier_star(n: int, modes: Sequence[Tuple[int, float, float]] = (), name: str = "star") -> Curve:
     """Sample r(theta) = 1 + sum a*cos(m*theta + phi) over (m, a, phi) in ``modes``."""
     if n <= 0:
         raise ValueError("n must be positive")
     theta = 2.0 * np.pi * np.arange(n, dtype=np.float64) / n
-    r = np.ones(n)
-    dr = np.zeros(n)
-    ddr = np.zeros(n)
-    for m, a, phi in modes:
-        arg = m * theta + phi
-        r += a * np.cos(arg)
-        dr -= a * m * np.sin(arg)
-        ddr -= a * m * m * np.cos(arg)
-    c, s = np.cos(theta), np.sin(theta)
-    x, y = r * c, r * s
-    dx = dr * c - r * s
-    dy = dr * s + r * c
-    ddx = ddr * c - 2.0 * dr * s - r * c
-    ddy = ddr * s + 2.0 * dr * c - r * s
-    speed = np.sqrt(dx * dx + dy * dy)
-    nx, ny = dy / speed, -dx / speed
-    w = speed * (2.0 * np.pi / n)
-    kappa = (dx * ddy - dy * ddx) / speed**3
-    return Curve(x, y, nx, ny, w, kappa, name)
+    g = fourier_star_at(theta, modes)
+    w = g["v"] * (2.0 * np.pi / n)
+    return Curve(g["x"], g["y"], g["nx"], g["ny"], w, g["kappa"], name)
 
 
 def disk(n: int) -> Curve:

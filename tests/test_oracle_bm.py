@@ -51,7 +51,7 @@ def _variant(kind):
             _, _, _, n0 = OK._layer_kernels(p.k0, *_geom(pts))
             i = np.arange(n)
             from oracle.pmchwt import diag_N
-            n0[i, i] = diag_N(p.k0, c.w, c.kappa)
+            n0[i, i] = diag_N(p.k0, c.w, c.kappa, pts.hs)
             A[:n, n:] -= alpha * n0 * c.w[None, :]
         else:  # no free term in the interior trace row
             i = np.arange(n)

@@ -7,7 +7,11 @@
   1/eps0 right-hand side) breaks that convergence;
 * the transparent obstacle (k1 = k0, eps1 = eps0) has the exact solution u = u_in;
 * the row-scaled matrix is symmetric bit for bit off the diagonal (Eq. syms) and the
-  free terms are its only asymmetry (Eq. 15); Table 1 magnitudes bound the asymmetry.
+  free terms are its only asymmetry (Eq. 15); Table 1 magnitudes bound the asymmetry;
+* the curvature-dependent diagonal D~ = D*~ = -kappa / 4 pi is the limit of the
+  off-diagonal D and D* kernels along a non-convex star, and the solution on that star
+  converges at O(h^3) against nested finer node sets; planted curvature mistakes (the
+  disk's constant, |kappa|, a flipped sign) fail the limit and break the convergence.
 """
 
 import json
@@ -20,7 +24,7 @@ from scipy import special
 
 from oracle import kernels as K
 from oracle.exact import disk_solution
-from synth import disk, fourier_star, star
+from synth import disk, fourier_star, fourier_star_at, star
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -173,3 +177,100 @@ def test_table1_magnitudes():
     # the paper's star is a different curve: only the order of magnitude is compared
     assert np.linalg.norm(s - s.T) > 1e-2 * ref["table2_unscaled_smooth_star"]["S"]
     assert np.linalg.norm(d - ds.T) > 1e-2 * ref["table2_unscaled_smooth_star"]["D_vs_Dstar"]
+
+
+# ---- the curvature-dependent diagonal (D~ = D*~ = -kappa / 4 pi), pinned by mathematics ----
+#
+# The paper defers the corrected diagonal entries (Sec. 3.1).  The D and D* kernels are
+# continuous on a smooth curve, so their one-point diagonal value must be the limit of the
+# off-diagonal kernel (pinned above by finite differences of G) as the source approaches the
+# target along the curve.  The points at parameter offsets come from the closed-form curve,
+# not from the sampled arrays, so the pin also checks the sampled curvature.
+
+STAR_MODES = {"star3": ((3, 0.2, 0.0),), "star5": ((5, 0.3, 0.0),)}  # both non-convex
+
+
+def _sampled(modes, n):
+    th = 2 * np.pi * np.arange(n) / n
+    return th, fourier_star(n, modes)
+
+
+def _kernel_limit_error(modes, delta, k=8.0, which="d", sides=(1, -1)):
+    """max_i |mean_s K(gamma(t_i), gamma(t_i + s delta)) - diag_D(kappa_i)| over nodes of a star."""
+    th, c = _sampled(modes, 97)
+    p = fourier_star_at(th, modes)
+    vals = []
+    for s in sides:
+        q = fourier_star_at(th + s * delta, modes)
+        dx, dy = p["x"] - q["x"], p["y"] - q["y"]
+        r = np.hypot(dx, dy)
+        a = dx * p["nx"] + dy * p["ny"]
+        b = dx * q["nx"] + dy * q["ny"]
+        nn = p["nx"] * q["nx"] + p["ny"] * q["ny"]
+        _, d, ds, _ = K._layer_kernels(k, r, a, b, nn)
+        vals.append(d if which == "d" else ds)
+    lim = np.mean(vals, axis=0)
+    return np.max(np.abs(lim - K.diag_D(c.kappa)) / (1.0 + np.abs(c.kappa)))
+
+
+@pytest.mark.parametrize("name", sorted(STAR_MODES))
+@pytest.mark.parametrize("which", ["d", "dstar"])
+def test_diag_D_is_the_limit_of_the_kernel_on_a_star(name, which):
+    modes = STAR_MODES[name]
+    # two-sided mean: error O(delta^2); one-sided: O(delta)
+    e3, e4 = (_kernel_limit_error(modes, d, which=which) for d in (1e-3, 1e-4))
+    assert e4 < 2e-6 and e3 / e4 > 30, (e3, e4)
+    o3, o4 = (_kernel_limit_error(modes, d, which=which, sides=(1,)) for d in (1e-3, 1e-4))
+    assert o4 < 2e-3 and 5 < o3 / o4 < 20, (o3, o4)
+
+
+_PLANTED_D = {
+    "constant": lambda kap: -np.ones_like(kap) / (4 * math.pi),   # the unit-disk value everywhere
+    "abs_kappa": lambda kap: -np.abs(kap) / (4 * math.pi),        # curvature sign lost
+    "sign": lambda kap: kap / (4 * math.pi),                      # flipped sign
+}
+
+
+@pytest.mark.parametrize("mistake", sorted(_PLANTED_D))
+def test_planted_diag_D_mistakes_fail_the_limit(mistake, monkeypatch):
+    monkeypatch.setattr(K, "diag_D", _PLANTED_D[mistake])
+    assert _kernel_limit_error(STAR_MODES["star3"], 1e-4) > 1e-2
+
+
+def _nested(x, n, nref):
+    """Entries of a [q; u] solution on nref nodes at the n nodes theta_j = 2 pi j / n."""
+    s = nref // n
+    return np.concatenate([x[:nref][::s], x[nref:][::s]])
+
+
+@pytest.fixture(scope="module")
+def star3_reference():
+    prm = K.Params.from_wavenumbers(5.0, 8.0)
+    return prm, K.dense_solve(fourier_star(2048, STAR_MODES["star3"]), prm)
+
+
+def _self_errors(prm, ref, sizes=(128, 256, 512)):
+    out = []
+    for n in sizes:
+        x = K.dense_solve(fourier_star(n, STAR_MODES["star3"]), prm)
+        r = _nested(ref, n, 2048)
+        out.append(np.linalg.norm(x - r) / np.linalg.norm(r))
+    return np.array(out)
+
+
+def test_star_self_convergence_is_third_order(star3_reference):
+    """O(h^3) on a non-circular, non-convex curve, where kappa varies and changes sign
+    (the disk tests have kappa = 1): nested node sets against 2048 nodes."""
+    prm, ref = star3_reference
+    errs = _self_errors(prm, ref)
+    orders = _orders(errs)
+    assert np.all(orders > 2.85) and np.all(orders < 3.4), (errs, orders)
+
+
+@pytest.mark.parametrize("mistake", ["constant", "abs_kappa"])
+def test_planted_diag_D_mistakes_break_self_convergence(mistake, star3_reference, monkeypatch):
+    prm, ref = star3_reference
+    good = _self_errors(prm, ref)
+    monkeypatch.setattr(K, "diag_D", _PLANTED_D[mistake])
+    bad = _self_errors(prm, ref)
+    assert np.all(_orders(bad) < 2.0) and bad[-1] > 20 * good[-1], (good, bad)
