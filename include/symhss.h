@@ -348,12 +348,27 @@ int symhss_hankel01(const double* x, int n, void* out, void* stream);
 /* A set of points for symhss_kernel_block: coordinates, unit normals, weights,
  * curvature and an id; two points with the same id >= 0 are the same curve
  * node and receive the corrected diagonal (Sec. 3.1) and the free terms (Eq. 15).
- * All arrays are device arrays of n entries. */
+ * hs: each node's speed term of the hypersingular diagonal (symhss_speed_terms of
+ * its curve's weights), used only by the PMCHWT and Burton-Miller diagonals; NULL
+ * reads as zero (a circle).  All arrays are device arrays of n entries. */
 typedef struct {
   int n;
   const double *x, *y, *nx, *ny, *w, *kappa;
   const int* id;
+  const double* hs;
 } symhss_points;
+
+/* Speed term of the one-point corrected hypersingular diagonal (Sec. 3.1, used by the
+ * PMCHWT and Burton-Miller comparators) for one closed curve given by its n trapezoidal
+ * weights w_j = |gamma'(theta_j)| 2 pi / n (host arrays; w > 0 and finite, else
+ * SYMHSS_ERR_INVALID).  The hypersingular kernel times the source's speed v = |gamma'| has
+ * the constant term v [kappa^2 / (24 pi) + (v''/6 - v'^2/(4 v)) / (2 pi v^3)] about a node;
+ * the second part equals s_j / w_j^2 with
+ *   s_j = ((d2w_j / w_j) / 6 - (d1w_j / w_j)^2 / 4) / (2 pi),
+ * d1w, d2w the first and second derivatives of the periodic sequence w with respect to the
+ * index j, taken by central differences of order 16 (fewer points for n < 17).  Writes s
+ * (host double[n]; zero on a circle).  Handles compute it from their curves at create. */
+int symhss_speed_terms(const double* w, int n, double* s);
 
 /* Tile generator: out[i + j*ld] = A[(obs_i, obs_eq[i]), (src_j, src_comp[j])]
  * with eq/comp in {0, 1} (0: first equation / flux unknown q, 1: second
@@ -400,9 +415,20 @@ int symhss_column_id_noalloc(void* A, int m, int n, int lda, long long strideA, 
  * splitmix64(seed ^ b*0xD1B54A32D192ED03 ^ i*0x8CB92BA72F3D8DD7 ^ k) is set and +1
  * otherwise (i: row of Y, k: row of M; 64-bit wrapping arithmetic).  Y_b = Y +
  * b*strideY: s x n complex128, leading dimension ldy.  m <= 65536, s <= 1024.
- * Returns SYMHSS_ERR_TIMEOUT if a bounded device wait expired. */
+ * Returns SYMHSS_ERR_TIMEOUT if a bounded device wait expired (see
+ * symhss_set_wait_limit_ns); Y is then undefined but the device stays usable. */
 int symhss_sketch(const void* A, int m, int n, int lda, long long strideA, int batch, int s,
                   unsigned long long seed, void* Y, int ldy, long long strideY, void* stream);
+
+/* Time limit, in nanoseconds, of each bounded wait inside the tensor-core sketch kernel
+ * (the waits for its bulk copies and for its tensor-core MMAs) for launches made after this
+ * call, process-wide; ns <= 0 restores the default of 200 ms.  When a wait expires the
+ * kernel records the timeout, waits once more (bounded by the default) for the copy or MMAs
+ * it may still have in flight, frees its tensor memory and exits; the call (symhss_sketch,
+ * or symhss_compress / symhss_build of a handle that sketches) returns
+ * SYMHSS_ERR_TIMEOUT and the CUDA context stays usable.  Intended for exercising that path
+ * in tests; a very short limit makes every sketch time out. */
+int symhss_set_wait_limit_ns(long long ns);
 
 /* Batched LU with partial pivoting of n x n complex128 matrices A + b*strideA
  * (leading dimension lda; overwritten by L\U), pivots ipiv + b*n (0-based row

@@ -138,6 +138,10 @@ __device__ __forceinline__ void warp_argmax_key(long long& k, int& i) {
 // process-wide count of kernels this library has launched (diagnostics)
 void count_launches(long long n);
 
+// Streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount, cached per
+// device; 148 on a B300 if the query fails).  Used to size grids in multiples of the SM count.
+int device_sm_count();
+
 // device status bits (OR-ed into a device word the host reads at sync points)
 enum : int {
   ST_BAD_INDEX = 1,
@@ -149,11 +153,17 @@ enum : int {
 
 // ---- tile generator ---------------------------------------------------------
 
-// Point table (structure of arrays).  id >= 0 marks a curve node.
+// Point table (structure of arrays).  id >= 0 marks a curve node.  hs: the node's
+// parametrisation-speed term of the hypersingular diagonal (speed_terms; NULL reads as 0).
 struct PointTable {
   const double *x, *y, *nx, *ny, *w, *kappa;
   const int* id;
+  const double* hs;
 };
+
+// Speed term of the one-point corrected hypersingular diagonal for one closed curve with
+// trapezoidal weights w[0..n) (see symhss_speed_terms in symhss.h): host code.
+void speed_terms(const double* w, int n, double* out);
 
 // Physical constants of one system.
 // Per-problem constants of the tile generator.  The blocks are combinations of the layer
@@ -319,8 +329,12 @@ struct SketchLaunch {
   int ntiles;
   uint64_t seed;
   int* status;
+  long long wait_ns;   // time limit of each pipeline wait (the drain after a timeout keeps the default)
 };
 cudaError_t launch_sketch(const SketchLaunch& a, cudaStream_t s);
+// Time limit of the sketch kernel's pipeline waits for launches made from now on (ns; <= 0
+// restores the default): a test hook for the timeout path.
+void set_sketch_wait_ns(long long ns);
 size_t sketch_slice_bytes(int mpad, int n2pad);
 int sketch_mpad(int m);
 int sketch_n2pad(int n);

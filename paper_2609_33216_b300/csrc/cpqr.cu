@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(kThreads) cpqr_cluster_kernel(const IdLaunch a
 // over the SMs, at most 16, and at least 8 columns per block.
 int cpqr_cluster_size(int njobs, int max_n) {
   int c = 1;
-  while (c < 16 && njobs * c * 2 <= 296 && max_n >= 16 * c) c *= 2;
+  while (c < 16 && njobs * c <= device_sm_count() && max_n >= 16 * c) c *= 2;
   return c;
 }
 

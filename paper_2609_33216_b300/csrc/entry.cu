@@ -3,6 +3,7 @@
 // batched LU / solve.  They validate their arguments, allocate the small job
 // arrays they need, launch the same kernels the solver uses, and synchronise
 // the stream before returning.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -17,6 +18,20 @@ std::atomic<long long> g_launches{0};
 }  // namespace
 
 void symhss::count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+int symhss::device_sm_count() {
+  static std::atomic<int> cache[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 148;
+  if (dev < 64) {
+    const int c = cache[dev].load(std::memory_order_relaxed);
+    if (c > 0) return c;
+  }
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 148;
+  if (dev < 64) cache[dev].store(sms, std::memory_order_relaxed);
+  return sms;
+}
 
 namespace {
 
@@ -37,9 +52,46 @@ int cerr(cudaError_t e) { return e == cudaErrorMemoryAllocation ? SYMHSS_ERR_NOM
 int status_code(int st) {
   if (st & ST_BAD_INDEX) return SYMHSS_ERR_DEVICE;
   if (st & ST_SINGULAR) return SYMHSS_ERR_SINGULAR;
+  if (st & ST_TIMEOUT) return SYMHSS_ERR_TIMEOUT;
   if (st) return SYMHSS_ERR_DEVICE;
   return SYMHSS_OK;
 }
+
+}  // namespace
+
+// Central differences of order 2m on a periodic sequence, unit spacing, with the closed-form
+// weights  a_j = (-1)^(j+1) c_j / j  (first derivative, on f[i+j] - f[i-j]) and
+// b_j = 2 (-1)^(j+1) c_j / j^2  (second derivative, on f[i+j] + f[i-j]; centre -2 sum b_j),
+// c_j = (m!)^2 / ((m-j)! (m+j)!) = prod_{t=1..j} (m-j+t) / (m+t).
+void symhss::speed_terms(const double* w, int n, double* out) {
+  const int m = std::max(0, std::min(8, (n - 1) / 2));
+  if (m == 0) {
+    for (int i = 0; i < n; ++i) out[i] = 0.0;
+    return;
+  }
+  double a[9] = {0}, b[9] = {0}, b0 = 0.0;
+  for (int j = 1; j <= m; ++j) {
+    double c = 1.0;
+    for (int t = 1; t <= j; ++t) c *= (double)(m - j + t) / (double)(m + t);
+    const double sg = (j % 2 == 1) ? 1.0 : -1.0;
+    a[j] = sg * c / j;
+    b[j] = 2.0 * sg * c / ((double)j * j);
+    b0 -= 2.0 * b[j];
+  }
+  const double inv2pi = 1.0 / (2.0 * 3.141592653589793238462643383279502884);
+  for (int i = 0; i < n; ++i) {
+    double d1 = 0.0, d2 = b0 * w[i];
+    for (int j = 1; j <= m; ++j) {
+      const double fp = w[(i + j) % n], fm = w[((i - j) % n + n) % n];
+      d1 += a[j] * (fp - fm);
+      d2 += b[j] * (fp + fm);
+    }
+    const double l1 = d1 / w[i], l2 = d2 / w[i];
+    out[i] = (l2 / 6.0 - 0.25 * l1 * l1) * inv2pi;
+  }
+}
+
+namespace {
 
 bool points_ok(const symhss_points* p) {
   return p && p->n >= 0 && (p->n == 0 || (p->x && p->y && p->nx && p->ny && p->w && p->kappa && p->id));
@@ -50,6 +102,19 @@ bool points_ok(const symhss_points* p) {
 extern "C" {
 
 long long symhss_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int symhss_set_wait_limit_ns(long long ns) {
+  symhss::set_sketch_wait_ns(ns);
+  return SYMHSS_OK;
+}
+
+int symhss_speed_terms(const double* w, int n, double* s) {
+  if (n < 1 || !w || !s) return SYMHSS_ERR_INVALID;
+  for (int i = 0; i < n; ++i)
+    if (!(w[i] > 0) || !std::isfinite(w[i])) return SYMHSS_ERR_INVALID;
+  symhss::speed_terms(w, n, s);
+  return SYMHSS_OK;
+}
 
 int symhss_hankel01(const double* x, int n, void* out, void* stream) {
   if (n < 0 || (n > 0 && (!x || !out))) return SYMHSS_ERR_INVALID;
@@ -117,8 +182,8 @@ int symhss_kernel_block(const symhss_params* prm, const symhss_points* obs, cons
   CKE(cudaMemcpyAsync(buf.p, hp, bytes, cudaMemcpyHostToDevice, s));
   char* d = reinterpret_cast<char*>(buf.p);
   TileLaunch a;
-  a.tpts = PointTable{obs->x, obs->y, obs->nx, obs->ny, obs->w, obs->kappa, obs->id};
-  a.lpts = PointTable{src->x, src->y, src->nx, src->ny, src->w, src->kappa, src->id};
+  a.tpts = PointTable{obs->x, obs->y, obs->nx, obs->ny, obs->w, obs->kappa, obs->id, obs->hs};
+  a.lpts = PointTable{src->x, src->y, src->nx, src->ny, src->w, src->kappa, src->id, src->hs};
   a.tp_pt = reinterpret_cast<const int*>(d + o1);
   a.tp_s0 = reinterpret_cast<const int*>(d + o2);
   a.tp_s1 = reinterpret_cast<const int*>(d + o3);

@@ -181,7 +181,7 @@ cudaError_t getrs_impl(const RsLaunch& a, cudaStream_t s) {
   // fewer warps per block when the batch is small (top levels: few boxes, many right-hand
   // sides), so that the grid covers every SM twice: each SM's FP64 pipe bounds its warps
   int warps = kRsMaxWarps;
-  while (warps > 2 && (long long)a.njobs * ((a.max_rhs + warps - 1) / warps) < 2 * 148) warps /= 2;
+  while (warps > 2 && (long long)a.njobs * ((a.max_rhs + warps - 1) / warps) < 2 * device_sm_count()) warps /= 2;
   size_t smem = 0;
   for (;; warps /= 2) {
     smem = (size_t)max_n * sizeof(CT) * (1 + warps) + (size_t)max_n * sizeof(int);

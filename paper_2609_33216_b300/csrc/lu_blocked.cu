@@ -510,7 +510,7 @@ cudaError_t getrf_impl(const LuLaunch& a, cudaStream_t s) {
   // cluster panels for few large matrices: C blocks per matrix while the batch still leaves
   // SMs free and every block keeps at least 32 panel rows
   int pc = 1;
-  while (sizeof(CT) == sizeof(double2) && pc < 16 && 2 * pc <= a.panel_cluster && a.njobs * 2 * pc <= 148 && a.max_n / (2 * pc) >= 32) pc *= 2;
+  while (sizeof(CT) == sizeof(double2) && pc < 16 && 2 * pc <= a.panel_cluster && a.njobs * 2 * pc <= device_sm_count() && a.max_n / (2 * pc) >= 32) pc *= 2;
   const int lmax = (a.max_n + pc - 1) / pc;
   if (pc > 1) {
     e = cudaFuncSetAttribute(panel_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

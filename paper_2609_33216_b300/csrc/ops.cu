@@ -264,7 +264,7 @@ cudaError_t launch_basis_dense(const BasisLaunch& a, cudaStream_t s) {
 cudaError_t launch_apply_r(const BasisLaunch& a, cudaStream_t s) {
   if (a.njobs <= 0) return cudaSuccess;
   // blocks per job so that even the few boxes of the top levels spread over every SM
-  const int per_job = std::max(4, std::min(64, (4 * 148 + a.njobs - 1) / a.njobs));
+  const int per_job = std::max(4, std::min(64, (4 * device_sm_count() + a.njobs - 1) / a.njobs));
   dim3 grid(a.njobs, per_job);
   if (a.out32) apply_r_kernel<float2><<<grid, kOpsThreads, 0, s>>>(a);
   else apply_r_kernel<double2><<<grid, kOpsThreads, 0, s>>>(a);
@@ -312,7 +312,8 @@ cudaError_t launch_apply_l(const BasisLaunch& a, cudaStream_t s) {
 
 static int elementwise_blocks(long long n) {
   const long long b = (n + 255) / 256;
-  return (int)(b < 148 * 16 ? (b > 0 ? b : 1) : 148 * 16);
+  const long long cap = 16LL * device_sm_count();
+  return (int)(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
 cudaError_t launch_narrow(const double2* src, float2* dst, long long n, cudaStream_t s) {

@@ -259,7 +259,8 @@ PointTable table_of(const symhss_s* h) {
   t.ny = base + 3 * np;
   t.w = base + 4 * np;
   t.kappa = base + 5 * np;
-  t.id = reinterpret_cast<const int*>(base + 6 * np);
+  t.hs = base + 6 * np;
+  t.id = reinterpret_cast<const int*>(base + 7 * np);
   return t;
 }
 
@@ -283,6 +284,7 @@ int read_status(symhss_s* h, cudaStream_t s) {
   if (st & ST_BAD_INDEX) return SYMHSS_ERR_DEVICE;
   if (st & ST_RANK_OVERFLOW) return SYMHSS_ERR_RANK_OVERFLOW;
   if (st & ST_SINGULAR) return SYMHSS_ERR_SINGULAR;
+  if (st & ST_TIMEOUT) return SYMHSS_ERR_TIMEOUT;
   if (st) return SYMHSS_ERR_DEVICE;
   return SYMHSS_OK;
 }
@@ -361,13 +363,15 @@ int build_geometry(symhss_s* h, cudaStream_t s) {
   }
   h->npts = npts;
   const size_t np = (size_t)npts;
-  std::vector<double> tab(7 * np, 0.0);
-  double *X = tab.data(), *Y = X + np, *NX = Y + np, *NY = NX + np, *W = NY + np, *K = W + np;
-  int* ID = reinterpret_cast<int*>(K + np);
+  std::vector<double> tab(8 * np, 0.0);
+  double *X = tab.data(), *Y = X + np, *NX = Y + np, *NY = NX + np, *W = NY + np, *K = W + np, *HS = K + np;
+  int* ID = reinterpret_cast<int*>(HS + np);
   for (int i = 0; i < h->ntot; ++i) {
     X[i] = h->hx[i]; Y[i] = h->hy[i]; NX[i] = h->hnx[i]; NY[i] = h->hny[i]; W[i] = h->hw[i]; K[i] = h->hk[i];
     ID[i] = i;
   }
+  // speed term of the hypersingular diagonal, per closed curve (problem); zero at proxies
+  for (const Problem& P : h->probs) speed_terms(h->hw.data() + P.node0, P.n, HS + P.node0);
   for (Problem& P : h->probs) {
     for (int l = 1; l <= P.depth; ++l) {
       for (auto& bx : P.levels[l]) {
@@ -465,7 +469,8 @@ struct TileBuilder {
     long long base = 0;
     for (const TileJob& jb : jobs)
       base += (long long)((jb.n_tp + TILE_T - 1) / TILE_T) * ((jb.n_lp + TILE_L - 1) / TILE_L);
-    int ln = base >= 4 * 148 ? TILE_L : (base >= 2 * 148 ? TILE_L / 2 : TILE_L / 4);
+    const int sms = device_sm_count();
+    int ln = base >= 4 * sms ? TILE_L : (base >= 2 * sms ? TILE_L / 2 : TILE_L / 4);
     if (fixed_ln > 0) ln = std::min(fixed_ln, TILE_L);
     chunks.clear();
     for (int j = 0; j < (int)jobs.size(); ++j)
@@ -700,7 +705,8 @@ int compress_height(symhss_s* h, int t, cudaStream_t s) {
       const int mtiles = (stot + 127) / 128;
       for (int cb = 0; cb < sj.n2pad / 32; ++cb)
         for (int mt = 0; mt < mtiles; ++mt) sktiles.push_back(SketchTile{sji, cb, mt});
-      sketch_work += 2.0 * 128.0 * mtiles * sj.mpad * 224.0 * (sj.n2pad / 32);
+      // algorithmic work of Y = Omega M: an s x m by m x n complex product, 8 s m n real flops
+      sketch_work += 8.0 * (double)stot * (double)j.m * (double)j.n;
       y_total += (long long)stot * j.n;
       slice_total += (long long)sketch_slice_bytes(sj.mpad, sj.n2pad);
       exp_total += 2LL * j.n;

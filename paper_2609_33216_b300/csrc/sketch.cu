@@ -20,7 +20,16 @@
 // the block writes its Omega chunk into shared memory and one bulk asynchronous copy
 // brings the 28 KB of slices (stored in global memory already in the core-matrix
 // order the MMA reads), then one elected thread issues 4 MMAs and commits them to an
-// mbarrier.  All waits are bounded; on timeout the block records an error and leaves.
+// mbarrier.  Every wait is bounded in time (%globaltimer, kWaitNs by default).  On a
+// timeout the block records ST_TIMEOUT, then waits once more (bounded by kWaitNs) for the
+// work it may still have in flight -- the bulk copy into shared memory or the MMAs writing
+// tensor memory -- and only then frees its tensor memory and exits, so no late write can
+// land in shared or tensor memory that another block owns by then.
+//
+// Recombination.  Each slice product v_t = (Omega S_t)(i, c) is an integer below 2^24 held
+// exactly in FP32.  The epilogue converts the seven to int32 and forms two exact int64
+// partial sums, hi = v0 2^16 + v1 2^8 + v2 (< 2^41) and lo = v3 2^24 + v4 2^16 + v5 2^8 + v6
+// (< 2^49), so Y(i, c) = hi 2^(e_c - 24) + lo 2^(e_c - 56) with one FP64 rounding.
 #include <stdint.h>
 
 #include "common.cuh"
@@ -38,7 +47,9 @@ constexpr int kTmemCols = 256;     // power of two >= kN
 constexpr int kBlockBytes = kSlices * kNCols * kKChunk * 2;  // 28672: one (column block, K-chunk) of slices
 constexpr int kABytes = kMTile * kKChunk * 2;                // 16384: Omega chunk
 constexpr int kThreads = 128;
-constexpr long long kSpinLimit = 1ll << 26;
+constexpr long long kWaitNs = 200ll * 1000 * 1000;  // 200 ms per wait
+
+long long g_wait_ns = kWaitNs;
 
 __host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
   x += 0x9E3779B97F4A7C15ull;
@@ -73,15 +84,23 @@ __host__ __device__ constexpr uint32_t make_idesc(int m, int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (long long it = 0; it < kSpinLimit; ++it) {
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// wait for phase `parity` of an mbarrier for at most limit_ns nanoseconds (at least one try)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit_ns) {
+  const unsigned long long t0 = global_ns();
+  while (true) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done) : "r"(bar), "r"(parity) : "memory");
     if (done) return true;
+    if ((long long)(global_ns() - t0) > limit_ns) return false;
   }
-  return false;
 }
 
 // ---- slicing: B = [Re M | Im M] -> 7 bf16 slices in the MMA core-matrix order ----------
@@ -189,6 +208,8 @@ __global__ void __launch_bounds__(kThreads) sketch_mma_kernel(const SketchLaunch
   const uint32_t idesc = make_idesc(kMTile, kN);
   const uint64_t stream = (uint64_t)jb.stream_id;
 
+  // s_fail: 0 = fine; 1 + 2 kc: the wait for chunk kc's copy expired (copy maybe in flight);
+  // 2 + 2 kc: the wait for chunk kc's MMAs expired (MMAs maybe in flight)
   for (int kc = 0; kc < nk; ++kc) {
     const uint32_t parity = (uint32_t)(kc & 1);
     // slices of this K-chunk: one bulk copy
@@ -217,11 +238,12 @@ __global__ void __launch_bounds__(kThreads) sketch_mma_kernel(const SketchLaunch
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
-    bool ok = mbar_wait(smem_u32(&bar_tx), parity);
-    if (!ok) s_fail = 1;
-    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (tid == 0 && !mbar_wait(smem_u32(&bar_tx), parity, a.wait_ns)) s_fail = 1 + 2 * kc;
     __syncthreads();
     if (s_fail) break;  // uniform: read after the barrier
+    // every thread observes the completed copy before the MMAs read it
+    mbar_wait(smem_u32(&bar_tx), parity, kWaitNs);
+    asm volatile("tcgen05.fence::after_thread_sync;");
     if (tid == 0) {
 #pragma unroll
       for (int kk = 0; kk < kKChunk / 16; ++kk) {
@@ -235,57 +257,68 @@ __global__ void __launch_bounds__(kThreads) sketch_mma_kernel(const SketchLaunch
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                    :: "r"(smem_u32(&bar_mma)) : "memory");
+      if (!mbar_wait(smem_u32(&bar_mma), parity, a.wait_ns)) s_fail = 2 + 2 * kc;
     }
-    ok = mbar_wait(smem_u32(&bar_mma), parity);
-    if (!ok) s_fail = 1;
-    asm volatile("tcgen05.fence::after_thread_sync;");
     __syncthreads();
     if (s_fail) break;
+    // every thread observes the completed MMAs before shared memory is rewritten or TMEM read
+    mbar_wait(smem_u32(&bar_mma), parity, kWaitNs);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+  }
+
+  if (s_fail) {
+    // drain: wait (bounded, default limit) for the copy or the MMAs that may be in flight
+    if (tid == 0) {
+      const int f = s_fail - 1;
+      const uint32_t par = (uint32_t)((f >> 1) & 1);
+      mbar_wait(smem_u32((f & 1) ? &bar_mma : &bar_tx), par, kWaitNs);
+      atomicOr(a.status, ST_TIMEOUT);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
   }
 
   if (!s_fail) {
-    // epilogue: warp w reads rows 32w..32w+31 (TMEM lanes), 32 columns per slice
+    // epilogue: warp w reads rows 32w..32w+31 (TMEM lanes); two halves of 16 columns
     const int row = row0 + warp * 32 + lane;
-    double acc[kNCols];
+    double* y = reinterpret_cast<double*>(a.y + jb.y_off);
 #pragma unroll
-    for (int c = 0; c < kNCols; ++c) acc[c] = 0.0;
-    int ecol[kNCols];
+    for (int half = 0; half < 2; ++half) {
+      long long hi[16], lo[16];
 #pragma unroll
-    for (int c = 0; c < kNCols; ++c) {
-      const int bc = tl.cb * kNCols + c;
-      ecol[c] = bc < 2 * jb.n ? a.exps[jb.exp_off + bc] : 0;
-    }
-    for (int t = kSlices - 1; t >= 0; --t) {
-      uint32_t v[32];
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * kNCols);
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-            "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-            "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-            "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      for (int c = 0; c < 16; ++c) { hi[c] = 0; lo[c] = 0; }
 #pragma unroll
-      for (int c = 0; c < kNCols; ++c) {
-        // slice t of column c carries weight 2^(e_c - 8(t+1)), e_c = emax - 1022
-        const double w = ldexp(1.0, ecol[c] - 1022 - 8 * (t + 1));
-        acc[c] = fma((double)__uint_as_float(v[c]), ecol[c] ? w : 0.0, acc[c]);
+      for (int t = 0; t < kSlices; ++t) {
+        uint32_t v[16];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * kNCols + half * 16);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15},"
+            " [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+              "=r"(v[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          // exact: the FP32 accumulator holds an integer below 2^24
+          const long long d = (long long)__float2int_rn(__uint_as_float(v[c]));
+          if (t < 3) hi[c] = hi[c] * 256 + d;
+          else lo[c] = lo[c] * 256 + d;
+        }
+      }
+      if (row < jb.s) {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const int bc = tl.cb * kNCols + half * 16 + c;
+          if (bc >= 2 * jb.n) continue;
+          const int ec = a.exps[jb.exp_off + bc];  // biased exponent of the column's largest entry
+          // slice t carries weight 2^(ec - 1022 - 8(t+1)): hi at 2^(ec - 1046), lo at 2^(ec - 1078)
+          const double val = ec ? fma((double)hi[c], ldexp(1.0, ec - 1046), ldexp((double)lo[c], ec - 1078)) : 0.0;
+          if (bc < jb.n) y[2 * (row + (long long)bc * jb.ldy)] = val;
+          else y[2 * (row + (long long)(bc - jb.n) * jb.ldy) + 1] = val;
+        }
       }
     }
-    if (row < jb.s) {
-      double* y = reinterpret_cast<double*>(a.y + jb.y_off);
-#pragma unroll
-      for (int c = 0; c < kNCols; ++c) {
-        const int bc = tl.cb * kNCols + c;
-        if (bc < jb.n) y[2 * (row + (long long)bc * jb.ldy)] = acc[c];
-        else if (bc < 2 * jb.n) y[2 * (row + (long long)(bc - jb.n) * jb.ldy) + 1] = acc[c];
-      }
-    }
-  } else if (tid == 0) {
-    atomicOr(a.status, ST_TIMEOUT);
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -302,8 +335,12 @@ size_t sketch_slice_bytes(int mpad, int n2pad) {
 int sketch_mpad(int m) { return ((m + kKChunk - 1) / kKChunk) * kKChunk; }
 int sketch_n2pad(int n) { return ((2 * n + kNCols - 1) / kNCols) * kNCols; }
 
-cudaError_t launch_sketch(const SketchLaunch& a, cudaStream_t s) {
-  if (a.ncolwork <= 0 || a.ntiles <= 0) return cudaSuccess;
+void set_sketch_wait_ns(long long ns) { g_wait_ns = ns > 0 ? ns : kWaitNs; }
+
+cudaError_t launch_sketch(const SketchLaunch& a_in, cudaStream_t s) {
+  if (a_in.ncolwork <= 0 || a_in.ntiles <= 0) return cudaSuccess;
+  SketchLaunch a = a_in;
+  a.wait_ns = g_wait_ns;
   slice_kernel<<<(a.ncolwork + 7) / 8, 256, 0, s>>>(a);
   symhss::count_launches(1);
   cudaError_t e = cudaGetLastError();

@@ -24,9 +24,11 @@
 //   D~ = D*~ = -kappa / (4 pi)
 //   (N_k0 - N_k1)~ = (i/8)(k0^2 - k1^2) - [k0^2 (log(k0/2) + gamma_E) - k1^2 (log(k1/2) + gamma_E)] / (4 pi)
 //                    + (k0^2 - k1^2) / (8 pi) - (k0^2 - k1^2) log(w / 2 pi) / (4 pi)
-//   PMCHWT: N~_k = -pi / (6 w^2) + kappa^2 / (24 pi) + (the k-dependent terms above for one k):
+//   PMCHWT: N~_k = (hs - pi/6) / w^2 + kappa^2 / (24 pi) + (the k-dependent terms above for one k):
 //   the zeta-corrected trapezoidal weight of the 1/tau^2 singularity, -2 zeta(2)/h, on the
-//   Laplace part 1/(2 pi |gamma'| tau^2) in the parameter tau, plus its constant on a circle.
+//   Laplace part 1/(2 pi |gamma'| tau^2) in the parameter tau, plus the constant term of the
+//   kernel times the source speed: kappa^2/(24 pi) and the speed term hs / w^2 (zero on a
+//   circle; hs from the node weights, see speed_terms).
 // H_0 and H_1 come from hankel01() (hankel.cuh), accurate to about 1e-15 at every
 // argument.
 #include "common.cuh"
@@ -72,7 +74,7 @@ __device__ __forceinline__ double2 rscale(double s, double2 u) {
   return make_double2(__dmul_rn(s, u.x), __dmul_rn(s, u.y));
 }
 
-struct P7 { double x, y, nx, ny, w, kappa; int id; };
+struct P7 { double x, y, nx, ny, w, kappa, hs; int id; };
 
 // 2x2 block [A11 A12; A21 A22] for observation o, source s.
 __device__ __forceinline__ void pair_block(const P7& o, const P7& s, const KernelParams& kp,
@@ -87,7 +89,7 @@ __device__ __forceinline__ void pair_block(const P7& o, const P7& s, const Kerne
     const double dd = -o.kappa / (4.0 * kPi);
     const double lw = log(w / (2.0 * kPi));
     const double k0s = kp.k0 * kp.k0;
-    const double hyp = -kPi / (6.0 * w * w) + o.kappa * o.kappa / (24.0 * kPi);
+    const double hyp = (o.hs - kPi / 6.0) / (w * w) + o.kappa * o.kappa / (24.0 * kPi);
     const double2 n0 = make_double2(hyp - k0s * (kp.lhk0 + kEulerGamma) / (4.0 * kPi) + k0s / (8.0 * kPi) -
                                         k0s / (4.0 * kPi) * lw,
                                     0.125 * k0s);
@@ -117,8 +119,8 @@ __device__ __forceinline__ void pair_block(const P7& o, const P7& s, const Kerne
     const double f1 = -k1s * (kp.lhk1 + kEulerGamma) / (4.0 * kPi) + k1s / (8.0 * kPi) - k1s / (4.0 * kPi) * lw;
     double2 kn;
     if (kp.form == SYMHSS_PMCHWT) {
-      // hypersingular part: -pi / (6 w^2) (zeta-corrected 1/tau^2) + kappa^2 / (24 pi)
-      const double hyp = -kPi / (6.0 * w * w) + o.kappa * o.kappa / (24.0 * kPi);
+      // hypersingular part: -pi / (6 w^2) (zeta-corrected 1/tau^2) + kappa^2 / (24 pi) + hs / w^2
+      const double hyp = (o.hs - kPi / 6.0) / (w * w) + o.kappa * o.kappa / (24.0 * kPi);
       kn = make_double2(kp.cn0 * (hyp + f0) - kp.cn1 * (hyp + f1), 0.125 * (kp.cn0 * k0s - kp.cn1 * k1s));
     } else {
       // the hypersingular parts cancel in N_k0 - N_k1
@@ -169,7 +171,7 @@ __device__ __forceinline__ void pair_block(const P7& o, const P7& s, const Kerne
 }
 
 __global__ void __launch_bounds__(TILE_T) tile_kernel(const TileLaunch a) {
-  __shared__ double sx[TILE_L], sy[TILE_L], snx[TILE_L], sny[TILE_L], sw[TILE_L], sk[TILE_L];
+  __shared__ double sx[TILE_L], sy[TILE_L], snx[TILE_L], sny[TILE_L], sw[TILE_L], sk[TILE_L], shs[TILE_L];
   __shared__ int sid[TILE_L], ss0[TILE_L], ss1[TILE_L];
   const TileChunk ch = a.chunks[blockIdx.x];
   const TileJob jb = a.jobs[ch.job];
@@ -180,6 +182,7 @@ __global__ void __launch_bounds__(TILE_T) tile_kernel(const TileLaunch a) {
     const int p = a.lp_pt[li];
     sx[t] = a.lpts.x[p]; sy[t] = a.lpts.y[p]; snx[t] = a.lpts.nx[p]; sny[t] = a.lpts.ny[p];
     sw[t] = a.lpts.w[p]; sk[t] = a.lpts.kappa[p]; sid[t] = a.lpts.id[p];
+    shs[t] = a.lpts.hs ? a.lpts.hs[p] : 0.0;
     ss0[t] = a.lp_s0[li]; ss1[t] = a.lp_s1[li];
   }
   __syncthreads();
@@ -190,6 +193,7 @@ __global__ void __launch_bounds__(TILE_T) tile_kernel(const TileLaunch a) {
   P7 tp;
   tp.x = a.tpts.x[p]; tp.y = a.tpts.y[p]; tp.nx = a.tpts.nx[p]; tp.ny = a.tpts.ny[p];
   tp.w = a.tpts.w[p]; tp.kappa = a.tpts.kappa[p]; tp.id = a.tpts.id[p];
+  tp.hs = a.tpts.hs ? a.tpts.hs[p] : 0.0;
   const int ts0 = a.tp_s0[tidx], ts1 = a.tp_s1[tidx];
   const bool src_thread = (jb.flags & TILE_SRC_IS_THREAD) != 0;
   const bool unscaled = (jb.flags & TILE_UNSCALED) != 0;
@@ -198,7 +202,7 @@ __global__ void __launch_bounds__(TILE_T) tile_kernel(const TileLaunch a) {
   double2* out = a.out + jb.out_off;
   for (int l = 0; l < nl; ++l) {
     P7 lp;
-    lp.x = sx[l]; lp.y = sy[l]; lp.nx = snx[l]; lp.ny = sny[l]; lp.w = sw[l]; lp.kappa = sk[l];
+    lp.x = sx[l]; lp.y = sy[l]; lp.nx = snx[l]; lp.ny = sny[l]; lp.w = sw[l]; lp.kappa = sk[l]; lp.hs = shs[l];
     lp.id = sid[l];
     const int ls0 = ss0[l], ls1 = ss1[l];
     if ((ts0 < 0 && ts1 < 0) || (ls0 < 0 && ls1 < 0)) continue;

@@ -82,7 +82,8 @@ class symhss_tuning(C.Structure):
 
 class symhss_points(C.Structure):
     _fields_ = [("n", C.c_int), ("x", C.c_void_p), ("y", C.c_void_p), ("nx", C.c_void_p),
-                ("ny", C.c_void_p), ("w", C.c_void_p), ("kappa", C.c_void_p), ("id", C.c_void_p)]
+                ("ny", C.c_void_p), ("w", C.c_void_p), ("kappa", C.c_void_p), ("id", C.c_void_p),
+                ("hs", C.c_void_p)]
 
 
 # (name, restype, argtypes) of every exported symbol
@@ -125,6 +126,8 @@ _SIGNATURES = [
                                        C.c_void_p, C.c_void_p]),
     ("symhss_launch_count", C.c_longlong, []),
     ("symhss_hankel01", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    ("symhss_speed_terms", C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    ("symhss_set_wait_limit_ns", C.c_int, [C.c_longlong]),
     ("symhss_kernel_block", C.c_int, [C.POINTER(symhss_params), C.POINTER(symhss_points), C.c_void_p,
                                       C.POINTER(symhss_points), C.c_void_p, C.c_int, C.c_void_p, C.c_int,
                                       C.c_void_p]),
@@ -274,8 +277,20 @@ def symhss_hankel01(x_ptr: int, n: int, out_ptr: int, stream: int = 0) -> None:
     check(lib.symhss_hankel01(C.c_void_p(x_ptr), n, C.c_void_p(out_ptr), C.c_void_p(stream)), "symhss_hankel01")
 
 
-def points_struct(n: int, ptrs, id_ptr: int) -> symhss_points:
-    return symhss_points(n, *[C.c_void_p(int(p)) for p in ptrs], C.c_void_p(int(id_ptr)))
+def points_struct(n: int, ptrs, id_ptr: int, hs_ptr: int = 0) -> symhss_points:
+    """ptrs: six device pointers (x, y, nx, ny, w, kappa); hs_ptr: speed terms or 0 (none)."""
+    return symhss_points(n, *[C.c_void_p(int(p)) for p in ptrs], C.c_void_p(int(id_ptr)),
+                         C.c_void_p(int(hs_ptr)) if hs_ptr else None)
+
+
+def symhss_speed_terms(w) -> "np.ndarray":
+    """Speed terms of the hypersingular diagonal for one curve's weights (host arrays)."""
+    import numpy as np
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    out = np.empty_like(w)
+    check(lib.symhss_speed_terms(w.ctypes.data_as(C.c_void_p), int(w.shape[0]), out.ctypes.data_as(C.c_void_p)),
+          "symhss_speed_terms")
+    return out
 
 
 def symhss_kernel_block(prm: symhss_params, obs: symhss_points, obs_eq: int, src: symhss_points, src_comp: int,
@@ -302,6 +317,10 @@ def symhss_sketch(a: int, m: int, n: int, lda: int, stride_a: int, batch: int, s
                   stride_y: int, stream: int = 0) -> None:
     check(lib.symhss_sketch(C.c_void_p(a), m, n, lda, stride_a, batch, s, seed, C.c_void_p(y), ldy, stride_y,
                             C.c_void_p(stream)), "symhss_sketch")
+
+
+def symhss_set_wait_limit_ns(ns: int) -> None:
+    check(lib.symhss_set_wait_limit_ns(int(ns)), "symhss_set_wait_limit_ns")
 
 
 def symhss_lu_batched(a: int, n: int, lda: int, stride_a: int, batch: int, ipiv: int, info: int,

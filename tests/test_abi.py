@@ -83,3 +83,21 @@ def test_tuning_calls_validate_on_host():
     assert S.lib.symhss_get_tuning(None, C.byref(t)) == S.SYMHSS_ERR_INVALID
     assert S.lib.symhss_set_tuning(None, C.byref(t)) == S.SYMHSS_ERR_INVALID
     assert S.lib.symhss_autotune(None, 1, None, None) == S.SYMHSS_ERR_INVALID
+
+
+def test_speed_terms_match_oracle_on_host():
+    """symhss_speed_terms (host code: closed-form difference weights) against the oracle's
+    speed term (difference weights solved over the rationals) on sampled curves."""
+    from paper_2609_33216_b300 import symhss as S
+    import numpy as np
+    from oracle import kernels as OK
+    from synth import fourier_star, random_star_batch, star
+    curves = [star(300), star(16384), fourier_star(97, ((3, 0.2, 0.0),)), fourier_star(5, ((2, 0.1, 0.0),))]
+    curves += [p["curve"] for p in random_star_batch(2, 11, 2048, 4096)]
+    for c in curves:
+        got = S.symhss_speed_terms(c.w)
+        ref = OK.hypersingular_speed_term(c.w)
+        # s enters the diagonal as (s - pi/6) / w^2: summation-order rounding of ~1e-16
+        assert np.max(np.abs(got - ref)) <= 1e-15, c.name
+    with pytest.raises(RuntimeError):
+        S.symhss_speed_terms(np.array([1.0, -1.0, 1.0]))

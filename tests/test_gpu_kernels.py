@@ -31,6 +31,7 @@ def _dev(a, dtype=torch.float64):
 
 
 def _points(S, pts: OK.Points):
+    # the Muller-like entries do not use the hypersingular speed term: none is passed
     arrs = [_dev(v) for v in (pts.x, pts.y, pts.nx, pts.ny, pts.w, pts.kappa)]
     ids = _dev(pts.gid.astype(np.int32), torch.int32)
     st = S.points_struct(len(pts), [a.data_ptr() for a in arrs], ids.data_ptr())
@@ -241,6 +242,35 @@ def test_tensor_core_sketch_matches_fp64_product(S, m, n, s, batch):
     seed = 987654321
     S.symhss_sketch(da.data_ptr(), m, n, m, m * n, batch, s, seed, y.data_ptr(), s, s * n,
                     torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    yg = np.transpose(y.cpu().numpy(), (0, 2, 1))
+    for b in range(batch):
+        ref = _omega(seed, b, s, m) @ mats[b]
+        err = np.abs(yg[b] - ref).max(axis=0) / np.abs(ref).max(axis=0)
+        assert err.max() <= 4e-15, (b, err.max())
+
+
+def test_sketch_wait_timeout_returns_status_and_device_stays_usable(S):
+    """Every wait of the sketch kernel is bounded in time.  With a 1 ns limit the waits for the
+    bulk copies and MMAs expire: the kernel drains what it has in flight, frees its tensor
+    memory and reports SYMHSS_ERR_TIMEOUT.  With the default limit restored, the same call on
+    the same (still usable) device gives the FP64 product again."""
+    m, n, s, batch = 300, 70, 48, 3
+    rng = np.random.default_rng(42)
+    mats = rng.normal(size=(batch, m, n)) + 1j * rng.normal(size=(batch, m, n))
+    da = torch.as_tensor(np.ascontiguousarray(np.transpose(mats, (0, 2, 1)))).to("cuda")
+    y = torch.zeros((batch, n, s), dtype=torch.complex128, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    seed = 5
+    try:
+        S.symhss_set_wait_limit_ns(1)
+        with pytest.raises(S.SymhssError) as exc:
+            S.symhss_sketch(da.data_ptr(), m, n, m, m * n, batch, s, seed, y.data_ptr(), s, s * n, stream)
+        assert exc.value.code == S.SYMHSS_ERR_TIMEOUT
+    finally:
+        S.symhss_set_wait_limit_ns(0)
+    torch.cuda.synchronize()
+    S.symhss_sketch(da.data_ptr(), m, n, m, m * n, batch, s, seed, y.data_ptr(), s, s * n, stream)
     torch.cuda.synchronize()
     yg = np.transpose(y.cpu().numpy(), (0, 2, 1))
     for b in range(batch):

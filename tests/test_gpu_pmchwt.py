@@ -37,14 +37,19 @@ def _dev(a, dtype=torch.float64):
     return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
 
 
-def _block(S, prm, obs, obs_eq, src, src_comp, scaled, form=None):
+def _block(S, prm, obs, obs_eq, src, src_comp, scaled, form=None, curve=None):
+    """GPU tile of the given points; the nodes' hypersingular speed terms come from the
+    library's own symhss_speed_terms of `curve`'s weights (zero at proxy points)."""
     keep = []
+    lib_hs = S.symhss_speed_terms(curve.w) if curve is not None else None
 
     def pts(p):
         arrs = [_dev(v) for v in (p.x, p.y, p.nx, p.ny, p.w, p.kappa)]
         ids = _dev(p.gid.astype(np.int32), torch.int32)
-        keep.extend(arrs + [ids])
-        return S.points_struct(len(p), [a.data_ptr() for a in arrs], ids.data_ptr())
+        hs = np.zeros(len(p)) if lib_hs is None else np.where(p.gid >= 0, lib_hs[np.maximum(p.gid, 0)], 0.0)
+        hs = _dev(hs)
+        keep.extend(arrs + [ids, hs])
+        return S.points_struct(len(p), [a.data_ptr() for a in arrs], ids.data_ptr(), hs.data_ptr())
 
     ost, sst = pts(obs), pts(src)
     eq = _dev(np.asarray(obs_eq, np.int32), torch.int32)
@@ -73,7 +78,7 @@ def test_pmchwt_tiles_match_oracle(S, scaled):
     src = pts.take(cols)
     comp = rng.integers(0, 2, 170)
     ref = PM.pmchwt_entries(obs, eq, src, comp, prm, scaled)
-    got = _block(S, prm, obs, eq, src, comp, scaled)
+    got = _block(S, prm, obs, eq, src, comp, scaled, curve=c)
     scale = np.abs(ref).max()
     err = np.abs(got - ref)
     assert np.all(err <= 2e-13 * np.abs(ref) + 1e-14 * scale), (err.max(), scale)
@@ -85,7 +90,7 @@ def test_pmchwt_gpu_matrix_symmetric_bit_exact(S):
     pts = OK.Points.from_curve(c)
     both = OH._stack(pts, pts)
     lab = np.concatenate([np.zeros(333, int), np.ones(333, int)])
-    a = _block(S, prm, both, lab, both, lab, True)
+    a = _block(S, prm, both, lab, both, lab, True, curve=c)
     assert np.array_equal(a, a.T)
 
 
@@ -137,7 +142,7 @@ def test_bm_tiles_match_oracle(S, scaled):
     src = pts.take(cols)
     comp = rng.integers(0, 2, 170)
     ref = BM.bm_entries(obs, eq, src, comp, prm, scaled)
-    got = _block(S, prm, obs, eq, src, comp, scaled, form=S.SYMHSS_BM)
+    got = _block(S, prm, obs, eq, src, comp, scaled, form=S.SYMHSS_BM, curve=c)
     scale = np.abs(ref).max()
     err = np.abs(got - ref)
     assert np.all(err <= 2e-13 * np.abs(ref) + 1e-14 * scale), (err.max(), scale)
