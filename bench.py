@@ -17,8 +17,15 @@ a step is the whole batch.
 Metric: seconds per scatterer (compress + factor + solve); for N GPUs every rank solves its own
 copy of the workload (replicas, weak scaling) and value = max-over-ranks seconds per step / N.
 L2: flushed between timed steps by writing a 512 MiB buffer outside the timed events.
+The timed steps use the pipelined build (compression of height t + 1 on a second stream while
+height t is factorised), so per-kernel-class events overlap there; per_kernel and the roofline come
+from up to 5 further serialised steps (compress, factor, solve on one stream) of the same handle.
+At one GPU the default run also times the other configurations (extra_workloads): the 65536-node
+star in mixed precision, the 64-scatterer batch and the 262144-node star with the learned proposer.
 
---impl reference times the FP64 CPU oracle on this host (bounded sample, see cpu_baseline).
+cpu_baseline: the FP64 oracle's whole job on the workload, run once on this host's cores.
+--impl reference: the same oracle job as the reference arm, one whole job per step, as many steps
+as fit in --ref-budget-s (the JSON line reports the steps actually run).
 """
 
 from __future__ import annotations
@@ -38,7 +45,6 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "HSS compress+factor+solve sec, sym vs non-sym, rel err ≤1e-8; % roofline"
-FP64_PEAK_TFLOPS = 1.25   # nominal dense FP64 of a B300 (148 SMs at up to 2032 MHz)
 
 
 def _env_rank():
@@ -142,45 +148,75 @@ def _config(w, mode):
 
 # ----------------------------------------------------------------------------------- ours
 
-def run_ours(args):
-    import numpy as np
+def fp64_peak_tflops(sm_mhz):
+    """FP64 peak of this device: SMs x 4 FP64 flops per clock (two DFMA per SM per cycle, the
+    rate ncu reports for this part) x the SM clock sampled while the timed steps ran."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = sm_mhz or 2032.0
+    return sms * 4.0 * mhz * 1e6 / 1e12, sms, mhz
+
+
+# DRAM bytes per launch of the dominant kernel class, from one ncu capture each (dram__bytes_read.sum
+# + dram__bytes_write.sum); keyed by kernel class, with the capture it came from.  A class whose
+# kernels changed after the capture has no entry (traffic is then reported as null).
+NCU_TRAFFIC = {}
+
+
+class _Timer:
+    def __init__(self, stream):
+        import torch
+        self.stream = stream
+        self.e0 = torch.cuda.Event(enable_timing=True)
+        self.e1 = torch.cuda.Event(enable_timing=True)
+
+    def __enter__(self):
+        self.e0.record(self.stream)
+        return self
+
+    def __exit__(self, *exc):
+        self.e1.record(self.stream)
+        self.e1.synchronize()
+        self.ms = self.e0.elapsed_time(self.e1)
+
+
+def _class_accumulate(acc, st):
+    for k in range(8):
+        acc["ms"][k] += st.kernel_ms[k]
+        acc["work"][k] += st.kernel_work[k]
+        acc["launch"][k] += st.kernel_launches[k]
+
+
+def _new_acc():
+    return {"ms": [0.0] * 8, "work": [0.0] * 8, "launch": [0] * 8}
+
+
+def bench_workload(w, args, steps, warmup, precision="fp64", net=None, autotune=True, sample_clocks=False,
+                   serial_pass=0, world=1):
+    """Time the symmetric and the two-ID solver on workload `w`: `warmup` untimed and `steps` timed
+    steps each (CUDA events on the caller's stream, L2 flushed between steps).  Returns per mode the
+    total ms, the solution, stats, launches and per-class device time of the timed (pipelined) steps,
+    and, if serial_pass > 0, per-class device time of that many serialised steps of the symmetric
+    solver (compress then factor on one stream, so class events do not overlap)."""
     import torch
     import torch.distributed as dist
 
     from paper_2609_33216_b300 import symhss as S
     from paper_2609_33216_b300.solver import BatchSolver, Solver
 
-    rank, world, local = _env_rank()
-    torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl")
-    w = _workload(args.workload)
     batch = "problems" in w
     curves = [p["curve"] for p in w["problems"]] if batch else [w["curve"]]
-    n_total = sum(cv.n for cv in curves)
     kw = dict(leaf=w["leaf"], nproxy=w["nproxy"], tol=w["tol"])
-    if args.precision == "mixed":
-        kw["precision"] = S.SYMHSS_MIXED
-
-    net, prop_info = None, None
-    if args.proposer:  # train the rank proposer first (outside every timed region)
-        from paper_2609_33216_b300.proposer import train_default
-        t_train = time.perf_counter()
-        net = train_default(seed=0, steps=3000)
-        prop_info = {"train_s": time.perf_counter() - t_train, "samples": int(net.data_size), "margin": 1.3,
-                     "training_data": "plain IDs of disk512, star16k, star64k (k 40/60 and 80/120) and 6 random "
-                                      "stars (k 5..60) at tol 1e-10 and 1e-8"}
 
     def make(mode):
         if batch:
             P = w["problems"]
             sv = BatchSolver(curves, [p["k0"] for p in P], [p["k1"] for p in P], [p["eps0"] for p in P],
-                             [p["eps1"] for p in P], mode=mode, **kw)
+                             [p["eps1"] for p in P], mode=mode, precision=S.SYMHSS_MIXED if precision == "mixed"
+                             else S.SYMHSS_FP64, **kw)
         else:
-            kws = dict(kw)
-            if "precision" in kws:
-                kws["precision"] = "mixed"
-            sv = Solver(w["curve"], w["k0"], w["k1"], w["eps0"], w["eps1"], mode=mode, curve_on_device=True, **kws)
+            sv = Solver(w["curve"], w["k0"], w["k1"], w["eps0"], w["eps1"], mode=mode, curve_on_device=True,
+                        precision=precision, **kw)
         if net is not None:
             net.attach(sv, margin=1.3)
         return sv
@@ -188,8 +224,8 @@ def run_ours(args):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def step(s):
-        if args.pipeline:  # compression of height t + 1 overlaps factorisation of height t
+    def step(s, pipelined=True):
+        if pipelined:  # compression of height t + 1 overlaps factorisation of height t
             s.build()
         else:
             s.compress()
@@ -202,126 +238,138 @@ def run_ours(args):
             dist.barrier()
             torch.cuda.synchronize()
 
-    results = {}
-    solvers = {}
-    tunings = {}
-    for mode in ("base", "sym"):  # the symmetric handle stays alive for the end-to-end leg
+    out = {"solvers": {}, "tuning": {}}
+    for mode in ("base", "sym"):
         s = make(mode)
-        solvers[mode] = s
-        if args.autotune:  # launch shapes chosen by the library's autotuner, outside the timed region
+        if autotune:  # launch shapes chosen by the library's autotuner, outside the timed region
             t_at = time.perf_counter()
             tn = S.symhss_autotune(s.h, reps=2, stream=stream.cuda_stream)
-            tunings[mode] = dict(tn.as_dict(), seconds=time.perf_counter() - t_at)
-        for _ in range(args.warmup):
+            out["tuning"][mode] = dict(tn.as_dict(), seconds=time.perf_counter() - t_at)
+        for _ in range(warmup):
             x = step(s)
         barrier()
-        sampler = ClockSampler(local) if (mode == "sym" and rank == 0) else None
+        sampler = ClockSampler(torch.cuda.current_device()) if (mode == "sym" and sample_clocks) else None
         if sampler:
             sampler.start()
         times = []
         launches0 = S.lib.symhss_launch_count()
-        kms = [0.0] * 8
-        kwork = [0.0] * 8
-        klaunch = [0] * 8
-        for _ in range(args.steps):
+        acc = _new_acc()
+        for _ in range(steps):
             flush.fill_(1.0)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            x = step(s)
-            e1.record(stream)
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1))
-            st = s.stats()
-            for k in range(8):
-                kms[k] += st.kernel_ms[k]
-                kwork[k] += st.kernel_work[k]
-                klaunch[k] += st.kernel_launches[k]
+            with _Timer(stream) as tm:
+                x = step(s)
+            times.append(tm.ms)
+            _class_accumulate(acc, s.stats())
         barrier()
         launches = S.lib.symhss_launch_count() - launches0
         clocks = sampler.stop() if sampler else None
         tot = torch.tensor([sum(times)], device="cuda", dtype=torch.float64)
         if world > 1:
             dist.all_reduce(tot, op=dist.ReduceOp.MAX)
-        st = s.stats()
-        results[mode] = dict(ms_total=float(tot.item()), times=times, x=x.cpu().numpy(), stats=st, clocks=clocks,
-                             launches=launches, kms=kms, kwork=kwork, klaunch=klaunch)
+        r = dict(ms_total=float(tot.item()), times=times, x=x.cpu().numpy(), stats=s.stats(), clocks=clocks,
+                 launches=launches, acc=acc)
         del x
+        if mode == "sym" and serial_pass > 0:
+            ser = _new_acc()
+            ser_ms = []
+            for _ in range(serial_pass):
+                flush.fill_(1.0)
+                with _Timer(stream) as tm:
+                    step(s, pipelined=False)
+                ser_ms.append(tm.ms)
+                _class_accumulate(ser, s.stats())
+            r["serial"] = dict(acc=ser, steps=serial_pass, ms=ser_ms)
+        out[mode] = r
         if mode == "base":
             s.close()
             torch.cuda.empty_cache()
+        else:
+            out["solvers"]["sym"] = s
+    del flush
+    xs, xb = out["sym"]["x"], out["base"]["x"]
+    import numpy as np
+    if batch:  # largest per-scatterer relative difference
+        sv = out["solvers"]["sym"]
+        out["rel_diff"] = max(float(np.linalg.norm(xs[r:r + 2 * n] - xb[r:r + 2 * n]) / np.linalg.norm(xb[r:r + 2 * n]))
+                              for r, n in zip(sv.row0, sv.ns))
+    else:
+        out["rel_diff"] = float(np.linalg.norm(xs - xb) / np.linalg.norm(xb))
+    out["step"] = step
+    return out
 
-    # comparator: the symmetric PMCHWT system (first-order accurate) on the same solver
+
+def _per_kernel(acc, steps, names):
+    return {names[k]: {"ms_per_step": acc["ms"][k] / steps, "launches_per_step": acc["launch"][k] / steps,
+                       "work_per_step": acc["work"][k] / steps} for k in range(len(names))}
+
+
+def _roofline(acc, steps, names, sm_mhz, K_SKETCH):
+    """Roofline of the dominant kernel class (largest serialised device time) with algorithmic work."""
+    nk = len(names)
+    cand = [k for k in range(nk) if acc["ms"][k] > 0 and acc["work"][k] > 0 and names[k] != "tiles"]
+    if not cand:
+        return None
+    dom = max(cand, key=lambda k: acc["ms"][k])
+    ms_launch = acc["ms"][dom] / max(1, acc["launch"][dom])
+    work_launch = acc["work"][dom] / max(1, acc["launch"][dom])
+    achieved = acc["work"][dom] / (acc["ms"][dom] * 1e-3) / 1e12
+    tr = NCU_TRAFFIC.get(names[dom])
+    if dom == K_SKETCH:
+        pk = _measured_peaks().get("bf16_tflops")
+        roof = {"kernel": names[dom], "bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
+                "frac": achieved / pk if pk else None, "peak_source": "measured bf16 (MEASURED_PEAKS.json)"}
+    else:
+        pk, sms, mhz = fp64_peak_tflops(sm_mhz)
+        roof = {"kernel": names[dom], "bound": "alu", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
+                "frac": achieved / pk,
+                "peak_source": f"derived FP64: {sms} SMs x 4 flop/clk x {mhz:.0f} MHz (median sampled SM clock)"}
+    roof["traffic"] = tr["bytes_per_launch"] if tr else None
+    roof["timing"] = ("serialised steps (compress then factor on one stream): CUDA events around every launch "
+                      "of the class on the stream it runs on")
+    roof["avg_launch_ms"] = ms_launch
+    roof["work_per_launch"] = work_launch
+    return roof
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2609_33216_b300 import symhss as S
+
+    rank, world, local = _env_rank()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    w = _workload(args.workload)
+    batch = "problems" in w
+    curves = [p["curve"] for p in w["problems"]] if batch else [w["curve"]]
+    n_total = sum(cv.n for cv in curves)
+    stream = torch.cuda.current_stream()
+
+    net, prop_info = None, None
+    if args.proposer:  # train the rank proposer first (outside every timed region)
+        net, prop_info = _train_proposer()
+
+    res = bench_workload(w, args, args.steps, args.warmup, precision=args.precision, net=net,
+                         autotune=bool(args.autotune), sample_clocks=(rank == 0),
+                         serial_pass=min(args.steps, 5), world=world)
+    step = res["step"]
+    r = res["sym"]
+    names = S.K_NAMES
+
+    # comparators: the symmetric PMCHWT and the Burton-Miller systems on the same solver
     comparators = {}
     if not batch and args.comparators:
-        pm = Solver(w["curve"], w["k0"], w["k1"], w["eps0"], w["eps1"], mode="sym", curve_on_device=True,
-                    formulation="pmchwt", **kw)
-        if "sym" in tunings:  # the symmetric solver's launch tuning
-            S.symhss_set_tuning(pm.h, **{k: v for k, v in tunings["sym"].items() if k != "seconds"})
-        for _ in range(args.warmup):
-            step(pm)
-        barrier()
-        tms = []
-        for _ in range(args.steps):
-            flush.fill_(1.0)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            step(pm)
-            e1.record(stream)
-            e1.synchronize()
-            tms.append(e0.elapsed_time(e1))
-        stp = pm.stats()
-        comparators["pmchwt_sym"] = {"ms_per_step": sum(tms) / len(tms), "max_rank": list(stp.max_rank),
-                                     "root_size": stp.root_size,
-                                     "accuracy": "first order in h (O(h^3) for the Muller-like system)"}
-        pm.close()
-        bm = Solver(w["curve"], w["k0"], w["k1"], w["eps0"], w["eps1"], mode="base", curve_on_device=True,
-                    formulation="bm", **kw)
-        if "base" in tunings:
-            S.symhss_set_tuning(bm.h, **{k: v for k, v in tunings["base"].items() if k != "seconds"})
-        for _ in range(args.warmup):
-            step(bm)
-        barrier()
-        tms = []
-        for _ in range(args.steps):
-            flush.fill_(1.0)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            step(bm)
-            e1.record(stream)
-            e1.synchronize()
-            tms.append(e0.elapsed_time(e1))
-        stb = bm.stats()
-        comparators["burton_miller_nonsym"] = {"ms_per_step": sum(tms) / len(tms), "max_rank": list(stb.max_rank),
-                                               "root_size": stb.root_size,
-                                               "accuracy": "first order in h (hypersingular N_k0)"}
-        bm.close()
+        comparators = _comparators(w, args, res["tuning"], step, world)
 
     mixed_diff = None
     if args.precision == "mixed" and not batch:
-        ref = Solver(w["curve"], w["k0"], w["k1"], w["eps0"], w["eps1"], mode="sym", curve_on_device=True,
-                     leaf=w["leaf"], nproxy=w["nproxy"], tol=w["tol"])
-        xr = step(ref).cpu().numpy()
-        ref.close()
-        for md in ("sym", "base"):
-            xm = results[md]["x"]
-            results[md]["vs_fp64"] = float(np.linalg.norm(xm - xr) / np.linalg.norm(xr))
-        mixed_diff = {"sym_vs_fp64_sym": results["sym"]["vs_fp64"], "base_vs_fp64_sym": results["base"]["vs_fp64"],
-                      "refinement_steps": 2}
-
-    xs = results["sym"]["x"]
-    xb = results["base"]["x"]
-    if batch:  # largest per-scatterer relative difference
-        e2e_tmp = solvers["sym"]
-        rel_diff = max(float(np.linalg.norm(xs[r:r + 2 * n] - xb[r:r + 2 * n]) / np.linalg.norm(xb[r:r + 2 * n]))
-                       for r, n in zip(e2e_tmp.row0, e2e_tmp.ns))
-    else:
-        rel_diff = float(np.linalg.norm(xs - xb) / np.linalg.norm(xb))
+        mixed_diff = _mixed_vs_fp64(w, res, step)
 
     # end to end through the C ABI: host curves in, host solution out, every step
-    e2e_s = solvers["sym"]
+    e2e_s = res["solvers"]["sym"]
     host = [[torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in cv.arrays()] for cv in curves]
     xh = torch.empty(2 * n_total, dtype=torch.complex128).pin_memory()
     curve_structs = [S.curve_struct(cv.n, [t.data_ptr() for t in hs], S.SYMHSS_HOST) for cv, hs in zip(curves, host)]
@@ -334,44 +382,34 @@ def run_ours(args):
 
     for _ in range(max(1, args.warmup)):
         e2e_step()
-    barrier()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         e2e_step()
-    barrier()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     e2e_sec = (time.perf_counter() - t0) / args.steps
     e2e_t = torch.tensor([e2e_sec], device="cuda", dtype=torch.float64)
     if world > 1:
         dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
     e2e_sec = float(e2e_t.item())
+    e2e_s.close()
+    del res["solvers"]
+    torch.cuda.empty_cache()
+
+    extras = None
+    if world == 1 and args.extras and args.workload == "star16k":
+        extras = _extra_workloads(args)
 
     if rank == 0:
-        r = results["sym"]
         sec_sym = r["ms_total"] / args.steps / 1000.0
-        sec_base = results["base"]["ms_total"] / args.steps / 1000.0
-        names = S.K_NAMES
-        nk = len(names)
-        per_kernel = {names[k]: {"ms_per_step": r["kms"][k] / args.steps, "launches_per_step": r["klaunch"][k] / args.steps,
-                                 "work_per_step": r["kwork"][k] / args.steps} for k in range(nk)}
-        # dominant kernel class by device time
-        dom = max(range(nk), key=lambda k: r["kms"][k])
-        roof = None
-        if dom == S.K_SKETCH and r["kms"][dom] > 0:
-            peaks = _measured_peaks()
-            achieved = r["kwork"][dom] / (r["kms"][dom] * 1e-3) / 1e12
-            pk = peaks.get("bf16_tflops")
-            roof = {"kernel": names[dom], "bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
-                    "frac": achieved / pk if pk else None, "traffic": None, "peak_source": "measured bf16"}
-        elif r["kms"][dom] > 0 and r["kwork"][dom] > 0 and dom != 0:
-            achieved = r["kwork"][dom] / (r["kms"][dom] * 1e-3) / 1e12
-            roof = {"kernel": names[dom], "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                    "peak_source": "nominal FP64 of the B300 (derived: not in the measured-peaks file)",
-                    "avg_launch_ms": r["kms"][dom] / max(1, r["klaunch"][dom])}
-        elif r["kms"][dom] > 0:
-            roof = {"kernel": names[dom], "bound": "alu", "achieved": r["kwork"][dom] / (r["kms"][dom] * 1e-3),
-                    "peak": None, "unit": "pairs/s", "frac": None, "traffic": None}
+        sec_base = res["base"]["ms_total"] / args.steps / 1000.0
         st = r["stats"]
+        clocks = r["clocks"] or {}
+        ser = r["serial"]
         out = {
             "metric": METRIC, "value": sec_sym / world, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": sec_sym * 1000.0, "higher_is_better": False, "scaling": "weak",
@@ -381,33 +419,131 @@ def run_ours(args):
             "config": _config(w, "sym"),
             "nonsym": {"value": sec_base / world, "unit": "s", "ms_per_step": sec_base * 1000.0},
             "speedup_sym_vs_nonsym": sec_base / sec_sym,
-            "rel_diff_sym_vs_nonsym": rel_diff,
-            "phases_ms": ({"build": st.ms_build, "solve": st.ms_solve} if args.pipeline else
-                          {"compress": st.ms_compress, "factor": st.ms_factor, "solve": st.ms_solve}),
-            "per_kernel": per_kernel,
+            "rel_diff_sym_vs_nonsym": res["rel_diff"],
+            "phases_ms": {"build": st.ms_build, "solve": st.ms_solve},
+            "per_kernel": _per_kernel(ser["acc"], ser["steps"], names),
+            "per_kernel_timing": ("serialised steps (compress, then factor, then solve, one stream), CUDA events "
+                                  f"around every launch; {ser['steps']} steps of "
+                                  f"{statistics.median(ser['ms']):.1f} ms (median) against "
+                                  f"{sec_sym * 1000.0:.1f} ms for the pipelined timed step"),
             "proposer": prop_info,
             "comparators": comparators or None,
             "mixed_precision": mixed_diff,
-            "tuning": tunings or None,
+            "tuning": res["tuning"] or None,
             "id_checks": {"failed_then_continued": int(st.check_failed), "max_accepted_ratio": st.check_max_ratio,
                           "proposals": int(st.proposals), "proposal_rank_err": st.proposal_rank_err},
-            "sketch": {"redone_ids": int(st.sketch_redo),
-                       "tensor_tflops": (r["kwork"][S.K_SKETCH] / (r["kms"][S.K_SKETCH] * 1e-3) / 1e12
-                                         if r["kms"][S.K_SKETCH] > 0 else None)},
+            "sketch": {"redone_ids": int(st.sketch_redo)},
             "ranks": {"max_flux": st.max_rank[0], "max_trace": st.max_rank[1], "root_size": st.root_size,
                       "leaf_mean": [st.level_mean_rank[st.depth][0], st.level_mean_rank[st.depth][1]]},
-            "roofline": roof,
+            "roofline": _roofline(ser["acc"], ser["steps"], names, clocks.get("sm_mhz"), S.K_SKETCH),
             "e2e": {"value": e2e_sec / world, "unit": "s", "h2d_bytes_per_step": 6 * 8 * n_total,
                     "d2h_bytes_per_step": 16 * 2 * n_total},
             "gpu_launches": int(r["launches"]),
             "clocks": r["clocks"],
         }
-        if not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline(w, args.cpu_sample_boxes)
+        if extras:
+            out["extra_workloads"] = extras
+        if not args.no_cpu_baseline and world == 1:
+            out["cpu_baseline"] = cpu_baseline(w, args.cpu_budget_s)
         print(json.dumps(out), flush=True)
-    solvers["sym"].close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def _train_proposer():
+    from paper_2609_33216_b300.proposer import train_default
+    t_train = time.perf_counter()
+    net = train_default(seed=0, steps=3000)
+    info = {"train_s": time.perf_counter() - t_train, "samples": int(net.data_size), "margin": 1.3,
+            "training_data": "plain IDs of disk512, star16k, star64k (k 40/60 and 80/120) and 6 random "
+                             "stars (k 5..60) at tol 1e-10 and 1e-8"}
+    return net, info
+
+
+def _comparators(w, args, tunings, step, world):
+    import torch
+
+    from paper_2609_33216_b300 import symhss as S
+    from paper_2609_33216_b300.solver import Solver
+
+    kw = dict(leaf=w["leaf"], nproxy=w["nproxy"], tol=w["tol"])
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    out = {}
+    for key, form, mode, acc in (("pmchwt_sym", "pmchwt", "sym", "first order in h (O(h^3) for the Muller-like system)"),
+                                 ("burton_miller_nonsym", "bm", "base", "first order in h (hypersingular N_k0)")):
+        sv = Solver(w["curve"], w["k0"], w["k1"], w["eps0"], w["eps1"], mode=mode, curve_on_device=True,
+                    formulation=form, **kw)
+        if mode in tunings:
+            S.symhss_set_tuning(sv.h, **{k: v for k, v in tunings[mode].items() if k != "seconds"})
+        for _ in range(args.warmup):
+            step(sv)
+        torch.cuda.synchronize()
+        tms = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            with _Timer(stream) as tm:
+                step(sv)
+            tms.append(tm.ms)
+        st = sv.stats()
+        out[key] = {"ms_per_step": sum(tms) / len(tms), "max_rank": list(st.max_rank), "root_size": st.root_size,
+                    "accuracy": acc}
+        sv.close()
+    return out
+
+
+def _mixed_vs_fp64(w, res, step):
+    import numpy as np
+
+    from paper_2609_33216_b300.solver import Solver
+    ref = Solver(w["curve"], w["k0"], w["k1"], w["eps0"], w["eps1"], mode="sym", curve_on_device=True,
+                 leaf=w["leaf"], nproxy=w["nproxy"], tol=w["tol"])
+    xr = step(ref).cpu().numpy()
+    ref.close()
+    out = {}
+    for md in ("sym", "base"):
+        out[f"{md}_vs_fp64_sym"] = float(np.linalg.norm(res[md]["x"] - xr) / np.linalg.norm(xr))
+    out["refinement_steps"] = 2
+    return out
+
+
+def _extra_workloads(args):
+    """The other benchmark configurations, each timed with `args.extra_steps` steps after 3 warm-up
+    steps (default launch tuning; no autotuner): the 65536-node star in mixed precision, the batch of
+    64 random scatterers, and the 262144-node star with the learned rank proposer."""
+    import torch
+
+    from paper_2609_33216_b300 import symhss as S
+
+    out = {}
+    specs = [("star64k", "mixed", False), ("batch64", "fp64", False), ("star262k", "fp64", True)]
+    for name, prec, proposer in specs:
+        w = _workload(name)
+        net, pinfo = (None, None)
+        if proposer:
+            net, pinfo = _train_proposer()
+        res = bench_workload(w, args, args.extra_steps, 3, precision=prec, net=net, autotune=False,
+                             sample_clocks=True, serial_pass=0)
+        st = res["sym"]["stats"]
+        sec_sym = res["sym"]["ms_total"] / args.extra_steps / 1000.0
+        sec_base = res["base"]["ms_total"] / args.extra_steps / 1000.0
+        d = {"config": _config(w, "sym"), "precision": prec, "value": sec_sym, "unit": "s",
+             "steps": args.extra_steps, "warmup": 3, "nonsym": sec_base, "speedup_sym_vs_nonsym": sec_base / sec_sym,
+             "rel_diff_sym_vs_nonsym": res["rel_diff"], "phases_ms": {"build": st.ms_build, "solve": st.ms_solve},
+             "per_kernel_pipelined": _per_kernel(res["sym"]["acc"], args.extra_steps, S.K_NAMES),
+             "ranks": {"max_flux": st.max_rank[0], "max_trace": st.max_rank[1], "root_size": st.root_size},
+             "clocks": res["sym"]["clocks"]}
+        if prec == "mixed":
+            d["mixed_precision"] = _mixed_vs_fp64(w, res, res["step"])
+        if proposer:
+            d["proposer"] = pinfo
+            d["id_checks"] = {"failed_then_continued": int(st.check_failed), "redone_ids": int(st.sketch_redo),
+                              "proposals": int(st.proposals), "proposal_rank_err": st.proposal_rank_err}
+        out[name] = d
+        res["solvers"]["sym"].close()
+        del res
+        torch.cuda.empty_cache()
+    return out
 
 
 def run_profile(args):
@@ -433,95 +569,84 @@ def run_profile(args):
 
 # ----------------------------------------------------------------------------- CPU oracle
 
-def _oracle_leaf_sample(curve, k0, k1, eps0, eps1, w, sample_boxes: int):
-    """Oracle leaf-level compress + factor of `sample_boxes` leaf boxes of one scatterer:
-    (seconds, boxes sampled, leaf boxes of the scatterer)."""
-    import numpy as np
-    import scipy.linalg as sla
-
-    from oracle.hss import HSS, Options, cpqr_id
-    from oracle.kernels import Params
+def _oracle_job(curve, k0, k1, eps0, eps1, w):
+    """The FP64 oracle's whole job for one scatterer: compress (proxy tiles and column IDs of every
+    level), factor, right-hand side and solve.  Returns the seconds of each phase."""
+    from oracle.hss import HSS, Options
+    from oracle.kernels import Params, rhs
 
     prm = Params(k0, k1, eps0, eps1)
-    solver = HSS(curve, prm, Options(leaf=w["leaf"], nproxy=w["nproxy"], tol=w["tol"]))
-    lev = solver.levels[-1]
-    for b in lev:
-        ids = np.arange(b.begin, b.end)
-        b.act = [ids, ids]
-        b.actrow = [ids, ids]
-    idx = np.linspace(0, len(lev) - 1, min(sample_boxes, len(lev))).astype(int)
     t0 = time.perf_counter()
-    for i in idx:
-        b = lev[i]
-        mr = solver.m_r(b, lev)
-        n0 = len(b.act[0])
-        b.rank, b.perm, b.T = [], [], []
-        for half in (mr[:, :n0], mr[:, n0:]):
-            r, p, t = cpqr_id(half, w["tol"])
-            b.rank.append(r)
-            b.perm.append(p)
-            b.T.append(t)
-        b.rrank, b.rperm, b.rT = b.rank, b.perm, b.T
-        d = solver._diag_block(b, solver.depth)
-        lu = sla.lu_factor(d)
-        rt = solver._basis(b, solver.depth, row=False)
-        x = sla.lu_solve(lu, rt)
-        np.linalg.inv(rt.T @ x)
-    return time.perf_counter() - t0, len(idx), len(lev)
+    solver = HSS(curve, prm, Options(leaf=w["leaf"], nproxy=w["nproxy"], tol=w["tol"]))
+    solver.compress()
+    t1 = time.perf_counter()
+    solver.factor()
+    t2 = time.perf_counter()
+    solver.solve(rhs(curve, prm))
+    t3 = time.perf_counter()
+    return {"compress": t1 - t0, "factor": t2 - t1, "solve": t3 - t2, "total": t3 - t0}
 
 
-def cpu_baseline(w, sample_boxes: int):
-    """Time the FP64 oracle on a bounded sample of the workload and scale it to the whole job.
+def _cores():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
 
-    Sample: the leaf level of the oracle's compression and factorisation (M_R tiles, two column
-    IDs, diagonal-block LU, X = D^-1 R^T and Atilde) for `sample_boxes` of the leaf boxes; the
-    per-box time is multiplied by the number of leaf boxes (of every scatterer of a batch: the
-    sampled boxes are then spread over up to 4 scatterers).  Upper levels are not included, so
-    the value is a lower bound of the oracle's whole-job time.
-    """
-    import math as _m
 
+def cpu_baseline(w, budget_s: float):
+    """The FP64 oracle (numpy/scipy, BLAS threads = host cores) timed on this host.
+
+    One scatterer: the whole compress + factor + solve of the workload, run once (no sampling,
+    no extrapolation).  A batch: whole oracle jobs of its scatterers in a fixed order until
+    `budget_s` is spent (at least one); the per-node time of those jobs is scaled to the batch's
+    node count, which the value says."""
     if "problems" in w:
         P = w["problems"]
-        total_leaves = sum(2 ** max(0, _m.ceil(_m.log2(p["curve"].n / w["leaf"]))) if p["curve"].n > w["leaf"] else 1
-                           for p in P)
-        picks = sorted(set(int(round(v)) for v in
-                           [i * (len(P) - 1) / max(1, min(4, len(P)) - 1) for i in range(min(4, len(P)))]))
-        per = max(1, sample_boxes // len(picks))
-        dt, cnt = 0.0, 0
-        for i in picks:
+        order = sorted(range(len(P)), key=lambda i: P[i]["curve"].n)
+        done, nodes, t = 0, 0, 0.0
+        for i in order:
             p = P[i]
-            d, c, _ = _oracle_leaf_sample(p["curve"], p["k0"], p["k1"], p["eps0"], p["eps1"], w, per)
-            dt += d
-            cnt += c
-        nlev, what = total_leaves, f"{cnt} leaf boxes of {len(picks)} of the {len(P)} scatterers"
-    else:
-        dt, cnt, nlev = _oracle_leaf_sample(w["curve"], w["k0"], w["k1"], w["eps0"], w["eps1"], w, sample_boxes)
-        what = f"{cnt} of {nlev} leaf boxes"
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    return {"value": dt / cnt * nlev, "unit": "s", "cores": cores, "kind": "oracle",
-            "sample": f"leaf level only: compress+factor of {what} ({dt:.1f} s), scaled to all {nlev} leaf boxes; "
-                      f"numpy/scipy FP64, BLAS threads = host cores"}
+            ph = _oracle_job(p["curve"], p["k0"], p["k1"], p["eps0"], p["eps1"], w)
+            t += ph["total"]
+            nodes += p["curve"].n
+            done += 1
+            if t >= budget_s:
+                break
+        total_nodes = sum(p["curve"].n for p in P)
+        return {"value": t / nodes * total_nodes, "unit": "s", "cores": _cores(), "kind": "oracle",
+                "sample": f"whole oracle jobs of the {done} smallest of {len(P)} scatterers ({nodes} nodes, "
+                          f"{t:.1f} s), scaled by node count to all {total_nodes} nodes (an extrapolation)"}
+    ph = _oracle_job(w["curve"], w["k0"], w["k1"], w["eps0"], w["eps1"], w)
+    return {"value": ph["total"], "unit": "s", "cores": _cores(), "kind": "oracle",
+            "phases_s": {k: ph[k] for k in ("compress", "factor", "solve")},
+            "sample": "the whole job, run once: oracle compress (proxy tiles and column IDs of every level), "
+                      "factor and solve of the workload; numpy/scipy FP64, BLAS threads = host cores"}
 
 
 def run_reference(args):
+    """The oracle as the reference arm: whole jobs of the workload, one per step, for at most
+    `args.steps` steps and until `args.ref_budget_s` of timed work is spent (at least one step).
+    The oracle holds no device or compiled state, so no warm-up step is run; the JSON line reports
+    the steps and warm-up actually run."""
     rank, world, _ = _env_rank()
     if rank != 0:
         return
     w = _workload(args.workload)
-    for _ in range(args.warmup):
-        cpu_baseline(w, args.ref_sample_boxes)
     vals = []
     last = None
-    for _ in range(args.steps):
-        last = cpu_baseline(w, args.ref_sample_boxes)
+    t_start = time.perf_counter()
+    while len(vals) < max(1, args.steps):
+        last = cpu_baseline(w, args.cpu_budget_s)
         vals.append(last["value"])
+        spent = time.perf_counter() - t_start
+        if spent + spent / len(vals) > args.ref_budget_s:
+            break
     v = sum(vals) / len(vals)
-    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": v * 1000.0, "higher_is_better": False, "scaling": "weak",
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": world, "steps": len(vals),
+           "warmup": 0, "ms_per_step": v * 1000.0, "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "complex128 (f64)", "data": "synthetic", "config": _config(w, "sym"),
            "cpu_baseline": dict(last, value=v),
            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    if len(vals) < args.steps:
+        out["steps_requested"] = args.steps
     print(json.dumps(out), flush=True)
 
 
@@ -533,13 +658,17 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="star16k")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-boxes", type=int, default=16)
-    ap.add_argument("--ref-sample-boxes", type=int, default=4)
+    ap.add_argument("--cpu-budget-s", type=float, default=60.0,
+                    help="batch workloads: oracle seconds to spend on whole scatterer jobs")
+    ap.add_argument("--ref-budget-s", type=float, default=150.0,
+                    help="reference arm: stop adding whole-job steps once this many seconds are spent")
+    ap.add_argument("--extras", type=int, default=1,
+                    help="with the default workload at one GPU, also time the 65536-node mixed-precision star, "
+                         "the 64-scatterer batch and the 262144-node star with the proposer")
+    ap.add_argument("--extra-steps", type=int, default=3)
     ap.add_argument("--profile", action="store_true", help="one warm-up + one symmetric step only")
     ap.add_argument("--proposer", action="store_true", help="train the learned rank proposer and attach it")
     ap.add_argument("--comparators", type=int, default=1, help="also time the symmetric PMCHWT comparator")
-    ap.add_argument("--pipeline", type=int, default=1,
-                    help="compress and factor through the pipelined build call (two streams)")
     ap.add_argument("--autotune", type=int, default=1, help="run the library's launch autotuner before timing")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="mixed: complex64 factorisation + iterative refinement (two steps) against the FP64 operator")
