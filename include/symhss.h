@@ -420,15 +420,38 @@ int symhss_column_id_noalloc(void* A, int m, int n, int lda, long long strideA, 
 int symhss_sketch(const void* A, int m, int n, int lda, long long strideA, int batch, int s,
                   unsigned long long seed, void* Y, int ldy, long long strideY, void* stream);
 
-/* Time limit, in nanoseconds, of each bounded wait inside the tensor-core sketch kernel
- * (the waits for its bulk copies and for its tensor-core MMAs) for launches made after this
- * call, process-wide; ns <= 0 restores the default of 200 ms.  When a wait expires the
- * kernel records the timeout, waits once more (bounded by the default) for the copy or MMAs
- * it may still have in flight, frees its tensor memory and exits; the call (symhss_sketch,
- * or symhss_compress / symhss_build of a handle that sketches) returns
+/* Time limit, in nanoseconds, of each bounded wait inside the tensor-core kernels (the
+ * sketch's waits for its bulk copies and MMAs, the matrix product's waits for its MMAs) for
+ * launches made after this call, process-wide; ns <= 0 restores the default of 200 ms.  When
+ * a wait expires the kernel records the timeout, waits once more (bounded by the default)
+ * for the copies or MMAs it may still have in flight, frees its tensor memory and exits; the
+ * call (symhss_sketch, symhss_zgemm, or a solver call that runs them) returns
  * SYMHSS_ERR_TIMEOUT and the CUDA context stays usable.  Intended for exercising that path
- * in tests; a very short limit makes every sketch time out. */
+ * in tests; a very short limit makes every such kernel time out. */
 int symhss_set_wait_limit_ns(long long ns);
+
+/* Test hook for the timeout path of the tensor-core matrix product (symhss_zgemm and the
+ * factorisation's blocked LU and solves, which use it): while on (on != 0), the last wait
+ * of every product launch waits for an mbarrier phase that no commit completes, so it
+ * expires after the wait limit (symhss_set_wait_limit_ns); the kernel then waits for its
+ * MMAs in flight, frees its tensor memory and the call returns SYMHSS_ERR_TIMEOUT with the
+ * CUDA context usable.  Off after load; process-wide. */
+int symhss_set_timeout_probe(int on);
+
+/* Batched complex FP64 matrix product on the tensor cores: for b < batch,
+ *   mode 0: C_b = A_b B_b,   mode 1: C_b -= A_b B_b,   mode 2: C_b += A_b B_b,
+ * A_b = A + b*strideA (m x k, leading dimension lda), B_b = B + b*strideB (k x n, ldb),
+ * C_b = C + b*strideC (m x n, ldc); complex128, column-major, device pointers; C must not
+ * overlap A or B.  This is the product the factorisation (Sec. 4.2) applies to its
+ * diagonal blocks: each row of A and each column of B is scaled by its largest power of two
+ * and cut into eight 7-bit slices that are exact in bf16; the 36 slice products of weight
+ * at least 2^-49 are summed exactly in FP32 on the tcgen05 tensor cores and recombined in
+ * integers, so every entry is within about 2^-52 k max_l |A(i,l)| max_l |B(l,j)| of the
+ * exact product (the usual FP64 bound with row and column maxima).  k > 64 is split into
+ * chunks of 64 accumulated in FP64.  Returns SYMHSS_ERR_TIMEOUT if a bounded device wait
+ * expired (symhss_set_wait_limit_ns). */
+int symhss_zgemm(const void* A, int lda, long long strideA, const void* B, int ldb, long long strideB, void* C,
+                 int ldc, long long strideC, int m, int n, int k, int batch, int mode, void* stream);
 
 /* Batched LU with partial pivoting of n x n complex128 matrices A + b*strideA
  * (leading dimension lda; overwritten by L\U), pivots ipiv + b*n (0-based row

@@ -360,6 +360,7 @@ struct LuLaunch {
   int lookahead = 1;       // depth-1 look-ahead on a side stream
   int panel_threads = 1024;  // largest panel block
   int panel_cluster = 1;     // largest cluster for the panels of few large matrices (1: one block)
+  int tc = 1;                // FP64: trailing updates of 64-column blocks on the tensor cores
 };
 cudaError_t launch_getrf(const LuLaunch& a, cudaStream_t s);
 
@@ -377,8 +378,53 @@ struct RsLaunch {
   int njobs;
   int max_rhs;
   int max_n;
+  int* status = nullptr;  // device status word; needed (with tc) by the tensor-core path
+  int tc = 1;             // FP64, > 4 right-hand sides, n > 64: blocked solve with tensor-core updates
 };
 cudaError_t launch_getrs(const RsLaunch& a, cudaStream_t s);
+
+// ---- complex FP64 GEMM on the tensor cores (zgemm_tc.cu) ---------------------------
+
+enum : int { ZGEMM_SET = 0, ZGEMM_SUB = 1, ZGEMM_ADD = 2 };  // C = AB, C -= AB, C += AB
+struct ZgemmJob {
+  long long a_off, b_off, c_off;  // complex offsets of A (m x k), B (k x n), C (m x n)
+  int m, n, k;                    // k <= zgemm_tc_max_k()
+  int lda, ldb, ldc;
+};
+struct ZgemmTile { int job, mt, nt; };  // row tile mt (128 rows), column tile nt (32 columns)
+// Jobs derived on the device from the factorisation's job arrays (block J = 64-aligned row):
+enum : int {
+  ZGEMM_JOBS = 0,      // explicit ZgemmJob / ZgemmTile arrays
+  ZGEMM_LU_UPDATE = 1,  // LuJob: A[J+64:n, J+64:n] -= A[J+64:n, J:J+64] A[J:J+64, J+64:n]
+  ZGEMM_RS_FWD = 2,     // RsJob: X[J+64:n, :] -= L[J+64:n, J:J+64] X[J:J+64, :]
+  ZGEMM_RS_BWD = 3,     // RsJob: X[0:J, :] -= U[0:J, J:J+64] X[J:J+64, :]
+};
+struct ZgemmLaunch {
+  const double2* A;
+  const double2* B;
+  double2* C;
+  const ZgemmJob* jobs;
+  const ZgemmTile* tiles;
+  int ntiles;          // grid size (derived jobs: njobs x mtiles x ntiles, idle tiles exit)
+  int mode;            // ZGEMM_SET / ZGEMM_SUB / ZGEMM_ADD
+  int* status;         // ST_TIMEOUT is OR-ed in when a bounded wait expires
+  long long wait_ns;   // set by launch_zgemm_tc
+  int derive = ZGEMM_JOBS;
+  const LuJob* lu_jobs = nullptr;
+  const RsJob* rs_jobs = nullptr;
+  int block_j = 0;     // J of the derived jobs
+  int mtiles = 0, ntiles_c = 0;  // tiles per derived job
+  int probe_timeout = 0;           // set by launch_zgemm_tc (test hook, see set_zgemm_timeout_probe)
+};
+cudaError_t launch_zgemm_tc(const ZgemmLaunch& a, cudaStream_t s);
+void set_zgemm_wait_ns(long long ns);
+// test hook: while on, the last MMA wait of every product launch targets a phase that no
+// commit completes, so it expires after the wait limit (the kernel then drains its MMAs)
+void set_zgemm_timeout_probe(int on);
+int zgemm_tc_tile_rows();
+int zgemm_tc_tile_cols();
+int zgemm_tc_max_k();
+
 
 // ---- factor / solve helpers ------------------------------------------------------
 

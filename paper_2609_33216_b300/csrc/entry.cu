@@ -105,7 +105,77 @@ long long symhss_launch_count(void) { return g_launches.load(std::memory_order_r
 
 int symhss_set_wait_limit_ns(long long ns) {
   symhss::set_sketch_wait_ns(ns);
+  symhss::set_zgemm_wait_ns(ns);
   return SYMHSS_OK;
+}
+
+int symhss_set_timeout_probe(int on) {
+  symhss::set_zgemm_timeout_probe(on);
+  return SYMHSS_OK;
+}
+
+int symhss_zgemm(const void* A, int lda, long long strideA, const void* B, int ldb, long long strideB, void* C,
+                 int ldc, long long strideC, int m, int n, int k, int batch, int mode, void* stream) {
+  if (m < 0 || n < 0 || k < 0 || batch < 0 || mode < 0 || mode > 2) return SYMHSS_ERR_INVALID;
+  if (m == 0 || n == 0 || batch == 0) return SYMHSS_OK;
+  if (!C || ldc < m || strideC < (long long)ldc * n) return SYMHSS_ERR_INVALID;
+  if (k > 0 && (!A || !B || lda < m || ldb < k || strideA < (long long)lda * k || strideB < (long long)ldb * n))
+    return SYMHSS_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (k == 0) {
+    if (mode != ZGEMM_SET) return SYMHSS_OK;
+    for (int b = 0; b < batch; ++b)
+      CKE(cudaMemset2DAsync(reinterpret_cast<double2*>(C) + strideC * b, (size_t)ldc * sizeof(double2), 0,
+                            (size_t)m * sizeof(double2), n, s));
+    CKE(cudaStreamSynchronize(s));
+    return SYMHSS_OK;
+  }
+  const int TM = zgemm_tc_tile_rows(), TN = zgemm_tc_tile_cols(), KM = zgemm_tc_max_k();
+  const int mt = (m + TM - 1) / TM, nt = (n + TN - 1) / TN;
+  std::vector<ZgemmTile> tiles;
+  for (int b = 0; b < batch; ++b)
+    for (int i = 0; i < mt; ++i)
+      for (int j = 0; j < nt; ++j) tiles.push_back(ZgemmTile{b, i, j});
+  const int nchunk = (k + KM - 1) / KM;
+  const size_t o_jobs = 0;
+  const size_t o_tiles = ((size_t)batch * nchunk * sizeof(ZgemmJob) + 255) & ~size_t(255);
+  const size_t o_status = o_tiles + ((tiles.size() * sizeof(ZgemmTile) + 255) & ~size_t(255));
+  const size_t total = o_status + 256;
+  std::vector<char> host(total, 0);
+  ZgemmJob* jobs = reinterpret_cast<ZgemmJob*>(host.data() + o_jobs);
+  for (int c = 0; c < nchunk; ++c)
+    for (int b = 0; b < batch; ++b) {
+      ZgemmJob& j = jobs[(size_t)c * batch + b];
+      const int k0 = c * KM;
+      j.a_off = strideA * b + (long long)k0 * lda;
+      j.b_off = strideB * b + k0;
+      j.c_off = strideC * b;
+      j.m = m; j.n = n; j.k = std::min(KM, k - k0);
+      j.lda = lda; j.ldb = ldb; j.ldc = ldc;
+    }
+  std::memcpy(host.data() + o_tiles, tiles.data(), tiles.size() * sizeof(ZgemmTile));
+  TmpBuf meta;
+  CKE(meta.alloc(total));
+  CKE(cudaMemcpyAsync(meta.p, host.data(), total, cudaMemcpyHostToDevice, s));
+  char* d = reinterpret_cast<char*>(meta.p);
+  ZgemmLaunch a;
+  a.A = reinterpret_cast<const double2*>(A);
+  a.B = reinterpret_cast<const double2*>(B);
+  a.C = reinterpret_cast<double2*>(C);
+  a.tiles = reinterpret_cast<const ZgemmTile*>(d + o_tiles);
+  a.ntiles = (int)tiles.size();
+  a.status = reinterpret_cast<int*>(d + o_status);
+  a.wait_ns = 0;
+  // chunks of k in order on the stream: the first sets (or updates) C, the rest accumulate
+  for (int c = 0; c < nchunk; ++c) {
+    a.jobs = reinterpret_cast<const ZgemmJob*>(d + o_jobs) + (size_t)c * batch;
+    a.mode = (c == 0) ? mode : (mode == ZGEMM_SUB ? ZGEMM_SUB : ZGEMM_ADD);
+    CKE(launch_zgemm_tc(a, s));
+  }
+  int st = 0;
+  CKE(cudaMemcpyAsync(&st, a.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CKE(cudaStreamSynchronize(s));
+  return status_code(st);
 }
 
 int symhss_speed_terms(const double* w, int n, double* s) {
@@ -331,7 +401,9 @@ int symhss_lu_batched(void* A, int n, int lda, long long strideA, int batch, int
   int st = 0;
   CKE(cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, s));
   CKE(cudaStreamSynchronize(s));
-  return (st & ST_BAD_INDEX) ? SYMHSS_ERR_DEVICE : SYMHSS_OK;  // singular blocks are reported in info
+  if (st & ST_BAD_INDEX) return SYMHSS_ERR_DEVICE;
+  if (st & ST_TIMEOUT) return SYMHSS_ERR_TIMEOUT;
+  return SYMHSS_OK;  // singular blocks are reported in info
 }
 
 int symhss_lu_solve_batched(const void* LU, int n, int lda, long long strideA, const int* ipiv, void* B, int nrhs,
@@ -348,8 +420,11 @@ int symhss_lu_solve_batched(const void* LU, int n, int lda, long long strideA, c
     jobs[b].b_off = strideB * b; jobs[b].ldb = ldb; jobs[b].nrhs = nrhs;
   }
   TmpBuf buf;
-  CKE(buf.alloc(jobs.size() * sizeof(RsJob)));
+  const size_t o_status = (jobs.size() * sizeof(RsJob) + 15) & ~size_t(15);
+  CKE(buf.alloc(o_status + 16));
   CKE(cudaMemcpyAsync(buf.p, jobs.data(), jobs.size() * sizeof(RsJob), cudaMemcpyHostToDevice, s));
+  int* status = reinterpret_cast<int*>(reinterpret_cast<char*>(buf.p) + o_status);
+  CKE(cudaMemsetAsync(status, 0, sizeof(int), s));
   RsLaunch a;
   a.abase = reinterpret_cast<const double2*>(LU);
   a.piv = ipiv;
@@ -358,9 +433,12 @@ int symhss_lu_solve_batched(const void* LU, int n, int lda, long long strideA, c
   a.njobs = batch;
   a.max_rhs = nrhs;
   a.max_n = n;
+  a.status = status;
   CKE(launch_getrs(a, s));
+  int st = 0;
+  CKE(cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, s));
   CKE(cudaStreamSynchronize(s));
-  return SYMHSS_OK;
+  return status_code(st);
 }
 
 }  // extern "C"

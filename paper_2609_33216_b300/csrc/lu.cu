@@ -6,6 +6,10 @@
 // Few right-hand sides (solve phase): one block per right-hand side; the column is
 // processed in 32-row blocks -- one warp solves the 32 x 32 triangle with register
 // shuffles, then every thread of the block updates the rows below (above, for U).
+// FP64 with many right-hand sides and n > 64 (the factorisation's X = D^{-1} L and Atilde):
+// blocked by 64 rows -- an FP64 solve with each diagonal block (one warp per right-hand
+// side) and the update of the other rows, X[rows] -= (block column of L or U) X[block], on
+// the tensor cores (zgemm_tc.cu).
 #include "common.cuh"
 
 namespace symhss {
@@ -162,6 +166,133 @@ __global__ void __launch_bounds__(kCtaThreads) getrs_cta_kernel(const RsLaunch a
   for (int i = tid; i < n; i += kCtaThreads) b[i] = x[i];
 }
 
+// ---- blocked solve with tensor-core updates (FP64, many right-hand sides) ----------------
+constexpr int kBlk = 64;  // diagonal block of the blocked solve
+
+// b <- P b for every right-hand side (one warp per column, the column staged in shared memory)
+__global__ void permute_kernel(const RsLaunch a, int warps) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const RsJob jb = a.jobs[blockIdx.x];
+  const int n = jb.n;
+  if (n > a.max_n || n < 0) return;  // uniform per block
+  double2* cols = reinterpret_cast<double2*>(smem_raw);
+  int* perm = reinterpret_cast<int*>(cols + (size_t)warps * a.max_n);
+  build_perm(perm, a.piv + jb.piv_off, n);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = blockIdx.y * warps + warp;
+  if (c >= jb.nrhs) return;
+  double2* b = a.bbase + jb.b_off + (long long)c * jb.ldb;
+  double2* sb = cols + (long long)warp * a.max_n;
+  for (int i = lane; i < n; i += 32) sb[i] = b[perm[i]];
+  __syncwarp();
+  for (int i = lane; i < n; i += 32) b[i] = sb[i];
+}
+
+// rows [J, J + w) of every right-hand side: solve with the unit-lower (LOWER) or the upper
+// diagonal block of the factors, staged in shared memory; one warp per right-hand side
+template <bool LOWER>
+__global__ void trsv_block_kernel(const RsLaunch a, int J, int warps) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* tri = reinterpret_cast<double2*>(smem_raw);  // kBlk x kBlk, column-major
+  double2* dinv = tri + kBlk * kBlk;
+  double2* cols = dinv + kBlk;
+  const RsJob jb = a.jobs[blockIdx.x];
+  const int n = jb.n;
+  if (n > a.max_n || J >= n) return;  // uniform per block
+  const int w = min(kBlk, n - J);
+  const double2* A = a.abase + jb.a_off + J + (long long)J * jb.lda;
+  for (int e = threadIdx.x; e < kBlk * w; e += blockDim.x) {
+    const int r = e % kBlk, q = e / kBlk;
+    tri[e] = r < w ? A[r + (long long)q * jb.lda] : make_double2(0.0, 0.0);
+  }
+  if (!LOWER)
+    for (int i = threadIdx.x; i < w; i += blockDim.x) dinv[i] = cinv(A[i + (long long)i * jb.lda]);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = blockIdx.y * warps + warp;
+  if (c >= jb.nrhs) return;
+  double2* b = a.bbase + jb.b_off + (long long)c * jb.ldb + J;
+  double2* sb = cols + warp * kBlk;
+  for (int i = lane; i < w; i += 32) sb[i] = b[i];
+  __syncwarp();
+  if (LOWER) {
+    for (int k = 0; k < w; ++k) {
+      const double2 bk = sb[k];
+      for (int i = k + 1 + lane; i < w; i += 32) sb[i] = cfms(tri[i + k * kBlk], bk, sb[i]);
+      __syncwarp();
+    }
+  } else {
+    for (int k = w - 1; k >= 0; --k) {
+      const double2 bk = cmul(sb[k], dinv[k]);
+      __syncwarp();
+      if (lane == 0) sb[k] = bk;
+      for (int i = lane; i < k; i += 32) sb[i] = cfms(tri[i + k * kBlk], bk, sb[i]);
+      __syncwarp();
+    }
+  }
+  for (int i = lane; i < w; i += 32) b[i] = sb[i];
+}
+
+cudaError_t getrs_blocked_tc(const RsLaunch& a, cudaStream_t s) {
+  const int max_n = a.max_n;
+  int warps = kRsMaxWarps;
+  while (warps > 2 && (long long)a.njobs * ((a.max_rhs + warps - 1) / warps) < 2 * device_sm_count()) warps /= 2;
+  size_t psmem = 0;
+  for (;; warps /= 2) {
+    psmem = (size_t)max_n * sizeof(double2) * warps + (size_t)max_n * sizeof(int);
+    if (psmem <= 200 * 1024 || warps == 1) break;
+  }
+  if (psmem > 200 * 1024) return cudaErrorInvalidValue;
+  const size_t tsmem = (size_t)(kBlk * kBlk + kBlk + warps * kBlk) * sizeof(double2);
+  cudaError_t e = cudaFuncSetAttribute(permute_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(trsv_block_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(trsv_block_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem);
+  if (e != cudaSuccess) return e;
+  const dim3 grid(a.njobs, (a.max_rhs + warps - 1) / warps);
+  permute_kernel<<<grid, warps * 32, psmem, s>>>(a, warps);
+  symhss::count_launches(1);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  ZgemmLaunch g;
+  g.A = a.abase; g.B = a.bbase; g.C = a.bbase;
+  g.jobs = nullptr; g.tiles = nullptr;
+  g.mode = ZGEMM_SUB;
+  g.status = a.status;
+  g.wait_ns = 0;
+  g.rs_jobs = a.jobs;
+  g.ntiles_c = (a.max_rhs + zgemm_tc_tile_cols() - 1) / zgemm_tc_tile_cols();
+  // forward: L y = P b, block by block; the rows below a block are updated on the tensor cores
+  for (int J = 0; J < max_n; J += kBlk) {
+    trsv_block_kernel<true><<<grid, warps * 32, tsmem, s>>>(a, J, warps);
+    symhss::count_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int below = max_n - J - kBlk;
+    if (below > 0) {
+      g.derive = ZGEMM_RS_FWD;
+      g.block_j = J;
+      g.mtiles = (below + zgemm_tc_tile_rows() - 1) / zgemm_tc_tile_rows();
+      g.ntiles = a.njobs * g.mtiles * g.ntiles_c;
+      if ((e = launch_zgemm_tc(g, s)) != cudaSuccess) return e;
+    }
+  }
+  // backward: U x = y from the last block; the rows above a block are updated on the tensor cores
+  for (int J = ((max_n - 1) / kBlk) * kBlk; J >= 0; J -= kBlk) {
+    trsv_block_kernel<false><<<grid, warps * 32, tsmem, s>>>(a, J, warps);
+    symhss::count_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (J > 0) {
+      g.derive = ZGEMM_RS_BWD;
+      g.block_j = J;
+      g.mtiles = (J + zgemm_tc_tile_rows() - 1) / zgemm_tc_tile_rows();
+      g.ntiles = a.njobs * g.mtiles * g.ntiles_c;
+      if ((e = launch_zgemm_tc(g, s)) != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
 }  // namespace
 
 template <typename CT>
@@ -169,6 +300,10 @@ cudaError_t getrs_impl(const RsLaunch& a, cudaStream_t s) {
   const int max_n = a.max_n;
   if (a.njobs <= 0 || a.max_rhs <= 0) return cudaSuccess;
   cudaError_t e;
+  // FP64 with many right-hand sides and blocks larger than one diagonal block: blocked solve
+  // whose off-diagonal updates run on the tensor cores
+  if (sizeof(CT) == sizeof(double2) && a.tc && a.status && a.max_rhs > 4 && max_n > kBlk)
+    return getrs_blocked_tc(a, s);
   if (a.max_rhs <= 4) {
     const size_t smem = (size_t)max_n * (2 * sizeof(CT) + sizeof(int));
     if (smem > 200 * 1024) return cudaErrorInvalidValue;

@@ -24,6 +24,7 @@ namespace symhss {
 namespace {
 
 constexpr int kNb = 16;          // panel width
+constexpr int kOuter = 64;       // column block of the tensor-core trailing update (FP64)
 constexpr int kPanelThreads = 256;
 constexpr int kPanelWarps = kPanelThreads / 32;
 constexpr int kTs = 32;          // trailing-update tile
@@ -316,8 +317,11 @@ __global__ void __launch_bounds__(kClusterPanelThreads) panel_cluster_kernel(con
 // permutation of that row set, built once per block, so each column is permuted by
 // a single gather (lane l ends with the value of row rows[l]); lanes 0..w-1 hold
 // rows j..j+w-1 and then solve the unit-lower 16 x 16 system with shuffles.
+// tlo, thi: the solve covers only columns in [max(j + w, tlo), thi); swaps = 0: no
+// interchanges (the columns are already permuted); cbase: first column of blockIdx.y = 0.
 template <typename CT>
-__global__ void __launch_bounds__(256) swap_trsm_warp_kernel(const LuLaunch a, int j) {
+__global__ void __launch_bounds__(256) swap_trsm_warp_kernel(const LuLaunch a, int j, int tlo, int thi, int swaps,
+                                                              int cbase) {
   __shared__ CT l11[kNb][kNb];
   __shared__ int rows_s[2 * kNb];   // row set: j..j+w-1, then the outside pivot rows
   __shared__ int src_s[2 * kNb];    // lane l takes its new value from row src_s[l]
@@ -348,7 +352,7 @@ __global__ void __launch_bounds__(256) swap_trsm_warp_kernel(const LuLaunch a, i
     // content[l] = original row currently stored at rows_s[l]; apply the swaps in order
     int content[2 * kNb];
     for (int l = 0; l < cnt; ++l) content[l] = rows_s[l];
-    for (int c = 0; c < w; ++c) {
+    for (int c = 0; swaps && c < w; ++c) {
       const int p = piv_s[c];
       if (p == j + c) continue;
       int lp = -1;
@@ -364,10 +368,12 @@ __global__ void __launch_bounds__(256) swap_trsm_warp_kernel(const LuLaunch a, i
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int col0 = (blockIdx.y * 8 + warp) * 2;  // two columns per warp
+  const int col0 = cbase + (blockIdx.y * 8 + warp) * 2;  // two columns per warp
   const int cnt = nrows_s;
-  const bool v0 = col0 < n && !(col0 >= j && col0 < j + w);
-  const bool v1 = col0 + 1 < n && !(col0 + 1 >= j && col0 + 1 < j + w);
+  const int tl = max(j + w, tlo), th = min(thi, n);
+  // a column takes part if it is interchanged, or (without interchanges) if it is solved
+  const bool v0 = col0 < n && !(col0 >= j && col0 < j + w) && (swaps || (col0 >= tl && col0 < th));
+  const bool v1 = col0 + 1 < n && !(col0 + 1 >= j && col0 + 1 < j + w) && (swaps || (col0 + 1 >= tl && col0 + 1 < th));
   if (!v0 && !v1) return;  // uniform per warp
   // interchanges: the full warp permutes one column at a time
   CT x[2];
@@ -378,7 +384,7 @@ __global__ void __launch_bounds__(256) swap_trsm_warp_kernel(const LuLaunch a, i
     CT* cc = A + (long long)(col0 + hc) * ld;
     const CT xv = lane < cnt ? cc[src_s[lane]] : make_c<CT>(0.0, 0.0);
     __syncwarp();
-    if (lane >= w && lane < cnt) cc[rows_s[lane]] = xv;
+    if (swaps && lane >= w && lane < cnt) cc[rows_s[lane]] = xv;
     x[hc] = xv;
   }
   // L11 U12 = A12 for both columns in one pass: lanes 0-15 hold rows j..j+w-1 of the
@@ -388,7 +394,7 @@ __global__ void __launch_bounds__(256) swap_trsm_warp_kernel(const LuLaunch a, i
   CT v = half ? up : x[0];
   const int col = col0 + half;
   const bool mine = half ? v1 : v0;
-  const bool trsm = mine && col >= j + w;
+  const bool trsm = mine && col >= tl && col < th;
   for (int c = 0; c < w; ++c) {
     const int src = (lane & 16) | c;
     const CT vc = make_c<CT>(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
@@ -398,18 +404,20 @@ __global__ void __launch_bounds__(256) swap_trsm_warp_kernel(const LuLaunch a, i
 }
 
 // A22 -= L21 U12 for the tile (blockIdx.y, blockIdx.z) of every matrix, over the trailing
-// columns [j + w + cskip, j + w + cskip + clen) (clen < 0: to the last column)
+// columns [j + w + cskip, j + w + cskip + clen) (clen < 0: to the last column) and the
+// trailing rows [j + w, j + w + rlen) (rlen < 0: to the last row)
 template <typename CT>
-__global__ void __launch_bounds__(256) update_kernel(const LuLaunch a, int j, int cskip, int clen) {
+__global__ void __launch_bounds__(256) update_kernel(const LuLaunch a, int j, int cskip, int clen, int rlen) {
   __shared__ CT at[kNb][kTs];      // L21 tile, transposed: at[c][r]
   __shared__ CT bt[kNb][kTs];      // U12 tile: bt[c][col]
   const LuJob jb = a.jobs[blockIdx.x];
-  const int n = jb.n, ld = jb.ld;
-  const int w = min(kNb, n - j);
+  const int n0 = jb.n, ld = jb.ld;
+  const int w = min(kNb, n0 - j);
   const int s = j + w;                   // first trailing row / column
+  const int n = rlen < 0 ? n0 : min(n0, s + rlen);  // rows end here; columns at cend
   const int r0 = s + blockIdx.y * kTs, c0 = s + cskip + blockIdx.z * kTs;
-  const int cend = clen < 0 ? n : min(n, s + cskip + clen);
-  if (j >= n || r0 >= n || c0 >= cend) return;
+  const int cend = clen < 0 ? n0 : min(n0, s + cskip + clen);
+  if (j >= n0 || r0 >= n || c0 >= cend) return;
   CT* A = lu_base<CT>(a) + jb.a_off;
   const int tid = threadIdx.x;
   for (int e = tid; e < kNb * kTs; e += 256) {
@@ -553,16 +561,74 @@ cudaError_t getrf_impl(const LuLaunch& a, cudaStream_t s) {
     return cudaGetLastError();
   };
   if ((e = panel(0, s)) != cudaSuccess) return e;
+  if (sizeof(CT) == sizeof(double2) && a.tc && a.max_n > kOuter + kNb) {
+    // FP64: blocked by 64 columns (the order of a blocked right-looking LU).  Inside a block
+    // the 16-column panels run as above with their interchanges applied to every column, but
+    // their U-row solves and FP64 updates cover only the block's own columns.  At the block's
+    // end its U rows for the columns right of it are solved (16 rows at a time), and
+    // A22 -= L21 U12 (k = 64) runs on the tensor cores (zgemm_tc.cu).
+    for (int j = 0; j < a.max_n; j += kNb) {
+      const int J = (j / kOuter) * kOuter;
+      const int rest = a.max_n - j - kNb;
+      if (rest > 0) {
+        // interchanges in every column; U rows only in the block's own columns
+        swap_trsm_warp_kernel<CT><<<dim3(a.njobs, ncolblk), 256, 0, s>>>(a, j, 0, J + kOuter, 1, 0);
+        symhss::count_launches(1);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        const int pc = J + kOuter - (j + kNb);  // columns of the block right of this panel
+        if (pc > 0) {
+          update_kernel<CT><<<dim3(a.njobs, (rest + kTs - 1) / kTs, (pc + kTs - 1) / kTs), 256, 0, s>>>(a, j, 0, pc, -1);
+          symhss::count_launches(1);
+          if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+      }
+      const int right = a.max_n - (J + kOuter);
+      if (j + kNb == J + kOuter && right > 0) {
+        // the block's U rows for the columns right of it, now that all its interchanges are
+        // applied: 16-row solves, each followed by the update of the block rows below it
+        const int rblk = (right + 15) / 16;  // blocks of 16 columns starting at J + 64
+        for (int jj = J; jj < J + kOuter; jj += kNb) {
+          swap_trsm_warp_kernel<CT><<<dim3(a.njobs, rblk), 256, 0, s>>>(a, jj, J + kOuter, a.max_n, 0, J + kOuter);
+          symhss::count_launches(1);
+          if ((e = cudaGetLastError()) != cudaSuccess) return e;
+          const int r = J + kOuter - (jj + kNb);
+          if (r > 0) {
+            update_kernel<CT><<<dim3(a.njobs, (r + kTs - 1) / kTs, (right + kTs - 1) / kTs), 256, 0, s>>>(a, jj, r, -1, r);
+            symhss::count_launches(1);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+          }
+        }
+        ZgemmLaunch g;
+        g.A = a.base; g.B = a.base; g.C = a.base;
+        g.jobs = nullptr; g.tiles = nullptr;
+        g.mode = ZGEMM_SUB;
+        g.status = a.status;
+        g.wait_ns = 0;
+        g.derive = ZGEMM_LU_UPDATE;
+        g.lu_jobs = a.jobs;
+        g.block_j = J;
+        g.mtiles = (right + zgemm_tc_tile_rows() - 1) / zgemm_tc_tile_rows();
+        g.ntiles_c = (right + zgemm_tc_tile_cols() - 1) / zgemm_tc_tile_cols();
+        g.ntiles = a.njobs * g.mtiles * g.ntiles_c;
+        if ((e = launch_zgemm_tc(g, s)) != cudaSuccess) return e;
+      }
+      if (j + kNb < a.max_n && (e = panel(j + kNb, s)) != cudaSuccess) return e;
+    }
+    const int jlast = ((a.max_n - 1) / kNb) * kNb;
+    swap_trsm_warp_kernel<CT><<<dim3(a.njobs, ncolblk), 256, 0, s>>>(a, jlast, 0, a.max_n, 1, 0);
+    symhss::count_launches(1);
+    return cudaGetLastError();
+  }
   for (int j = 0; j < a.max_n; j += kNb) {
     const int rest = a.max_n - j - kNb;
     if (rest <= 0) continue;
-    swap_trsm_warp_kernel<CT><<<dim3(a.njobs, ncolblk), 256, 0, s>>>(a, j);
+    swap_trsm_warp_kernel<CT><<<dim3(a.njobs, ncolblk), 256, 0, s>>>(a, j, 0, a.max_n, 1, 0);
     symhss::count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int rtiles = (rest + kTs - 1) / kTs;
     const bool split = la != nullptr && rest > kTs;
     // first trailing tile column (all of it when not splitting)
-    update_kernel<CT><<<dim3(a.njobs, rtiles, split ? 1 : rtiles), 256, 0, s>>>(a, j, 0, split ? kTs : -1);
+    update_kernel<CT><<<dim3(a.njobs, rtiles, split ? 1 : rtiles), 256, 0, s>>>(a, j, 0, split ? kTs : -1, -1);
     symhss::count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (!split) {
@@ -574,14 +640,14 @@ cudaError_t getrf_impl(const LuLaunch& a, cudaStream_t s) {
     if ((e = panel(j + kNb, la->side)) != cudaSuccess) return e;
     if ((e = cudaEventRecord(la->done, la->side)) != cudaSuccess) return e;
     const int ctiles = (rest - kTs + kTs - 1) / kTs;
-    update_kernel<CT><<<dim3(a.njobs, rtiles, ctiles), 256, 0, s>>>(a, j, kTs, -1);
+    update_kernel<CT><<<dim3(a.njobs, rtiles, ctiles), 256, 0, s>>>(a, j, kTs, -1, -1);
     symhss::count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(s, la->done, 0)) != cudaSuccess) return e;
   }
   // the last panel's interchanges still have to reach the columns left of it
   const int jlast = ((a.max_n - 1) / kNb) * kNb;
-  swap_trsm_warp_kernel<CT><<<dim3(a.njobs, ncolblk), 256, 0, s>>>(a, jlast);
+  swap_trsm_warp_kernel<CT><<<dim3(a.njobs, ncolblk), 256, 0, s>>>(a, jlast, 0, a.max_n, 1, 0);
   symhss::count_launches(1);
   return cudaGetLastError();
 }

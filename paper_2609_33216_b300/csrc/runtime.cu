@@ -1284,6 +1284,7 @@ int factor_height(symhss_s* h, int t, cudaStream_t s, long long& pairs, bool lu_
   ra.njobs = (int)xs.size();
   ra.max_rhs = max_k;
   ra.max_n = max_n;
+  ra.status = h->status.as<int>();
   TIMED(SYMHSS_K_GETRS, w_x, launch_getrs(ra, s));
   // R X
   BasisLaunch br = bl;
@@ -1328,6 +1329,7 @@ int factor_height(symhss_s* h, int t, cudaStream_t s, long long& pairs, bool lu_
   rb.njobs = (int)ats.size();
   rb.max_rhs = max_k;
   rb.max_n = max_k;
+  rb.status = h->status.as<int>();
   TIMED(SYMHSS_K_GETRS, w_at, launch_getrs(rb, s));
   if (mixed) {  // X and Atilde in FP64 for the parents' blocks and the solve phase
     TIMED(SYMHSS_K_OTHER, 0.0, launch_widen(H.X32.as<float2>(), H.X.as<double2>(), x_total, s));

@@ -92,14 +92,17 @@ __device__ __forceinline__ unsigned long long global_ns() {
 
 // wait for phase `parity` of an mbarrier for at most limit_ns nanoseconds (at least one try)
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit_ns) {
+  // non-blocking tests with a short back-off: the elapsed time is checked between tests, so
+  // the limit holds however short it is (a blocking try may sleep until the phase completes)
   const unsigned long long t0 = global_ns();
   while (true) {
     uint32_t done;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done) : "r"(bar), "r"(parity) : "memory");
     if (done) return true;
     if ((long long)(global_ns() - t0) > limit_ns) return false;
+    __nanosleep(32);
   }
 }
 

@@ -128,6 +128,9 @@ _SIGNATURES = [
     ("symhss_hankel01", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     ("symhss_speed_terms", C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     ("symhss_set_wait_limit_ns", C.c_int, [C.c_longlong]),
+    ("symhss_set_timeout_probe", C.c_int, [C.c_int]),
+    ("symhss_zgemm", C.c_int, [C.c_void_p, C.c_int, C.c_longlong, C.c_void_p, C.c_int, C.c_longlong, C.c_void_p,
+                               C.c_int, C.c_longlong, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p]),
     ("symhss_kernel_block", C.c_int, [C.POINTER(symhss_params), C.POINTER(symhss_points), C.c_void_p,
                                       C.POINTER(symhss_points), C.c_void_p, C.c_int, C.c_void_p, C.c_int,
                                       C.c_void_p]),
@@ -317,6 +320,17 @@ def symhss_sketch(a: int, m: int, n: int, lda: int, stride_a: int, batch: int, s
                   stride_y: int, stream: int = 0) -> None:
     check(lib.symhss_sketch(C.c_void_p(a), m, n, lda, stride_a, batch, s, seed, C.c_void_p(y), ldy, stride_y,
                             C.c_void_p(stream)), "symhss_sketch")
+
+
+def symhss_zgemm(a: int, lda: int, stride_a: int, b: int, ldb: int, stride_b: int, c: int, ldc: int, stride_c: int,
+                 m: int, n: int, k: int, batch: int, mode: int, stream: int = 0) -> None:
+    """mode 0: C = A B, 1: C -= A B, 2: C += A B (batched, column-major complex128, device pointers)."""
+    check(lib.symhss_zgemm(C.c_void_p(a), lda, stride_a, C.c_void_p(b), ldb, stride_b, C.c_void_p(c), ldc, stride_c,
+                           m, n, k, batch, mode, C.c_void_p(stream)), "symhss_zgemm")
+
+
+def symhss_set_timeout_probe(on: bool) -> None:
+    check(lib.symhss_set_timeout_probe(int(bool(on))), "symhss_set_timeout_probe")
 
 
 def symhss_set_wait_limit_ns(ns: int) -> None:

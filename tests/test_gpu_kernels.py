@@ -277,3 +277,70 @@ def test_sketch_wait_timeout_returns_status_and_device_stays_usable(S):
         ref = _omega(seed, b, s, m) @ mats[b]
         err = np.abs(yg[b] - ref).max(axis=0) / np.abs(ref).max(axis=0)
         assert err.max() <= 4e-15, (b, err.max())
+
+
+def _zgemm_case(rng, m, n, k, batch, spread):
+    a = (rng.normal(size=(batch, m, k)) + 1j * rng.normal(size=(batch, m, k)))
+    b = (rng.normal(size=(batch, k, n)) + 1j * rng.normal(size=(batch, k, n)))
+    a *= np.exp(spread * rng.normal(size=(batch, m, 1)))  # rows and columns of very different scale
+    b *= np.exp(spread * rng.normal(size=(batch, 1, n)))
+    if m > 3 and k > 2:
+        a[:, 1, :] = 0.0  # an all-zero row
+        a[:, 2, 1] *= 1e-40  # an entry far below its row's maximum
+    c = rng.normal(size=(batch, m, n)) + 1j * rng.normal(size=(batch, m, n))
+    return a, b, c
+
+
+def _colmajor(x):
+    """(batch, rows, cols) -> device tensor laid out column-major per matrix."""
+    return torch.as_tensor(np.ascontiguousarray(np.transpose(x, (0, 2, 1)))).to("cuda")
+
+
+@pytest.mark.parametrize("m,n,k,batch", [(1, 1, 1, 1), (37, 5, 3, 2), (128, 32, 64, 1), (300, 70, 64, 3),
+                                         (192, 192, 64, 2), (257, 33, 100, 2), (64, 61, 17, 4)])
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_tensor_core_zgemm_matches_fp64_product(S, m, n, k, batch, mode):
+    """C = A B, C -= A B, C += A B on the tensor cores (exact 7-bit slices, FP32 accumulation of
+    integers below 2^24, int64 recombination) against numpy's FP64 product: every entry within
+    8 k 2^-52 max_l|A(i,l)| max_l|B(l,j)| (the FP64 bound with row and column maxima)."""
+    rng = np.random.default_rng(1000 * m + 10 * n + k + mode)
+    a, b, c = _zgemm_case(rng, m, n, k, batch, spread=3.0)
+    da, db, dc = _colmajor(a), _colmajor(b), _colmajor(c)
+    S.symhss_zgemm(da.data_ptr(), m, m * k, db.data_ptr(), k, k * n, dc.data_ptr(), m, m * n, m, n, k, batch, mode,
+                   torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    got = np.transpose(dc.cpu().numpy(), (0, 2, 1))
+    prod = a @ b
+    ref = {0: prod, 1: c - prod, 2: c + prod}[mode]
+    amax = np.maximum(np.abs(a.real), np.abs(a.imag)).max(axis=2)   # (batch, m)
+    bmax = np.maximum(np.abs(b.real), np.abs(b.imag)).max(axis=1)   # (batch, n)
+    bound = 8 * k * 2.0 ** -52 * amax[:, :, None] * bmax[:, None, :] + 4 * 2.0 ** -52 * np.abs(ref)
+    err = np.abs(got - ref)
+    assert np.all(err <= bound), float((err / bound).max())
+
+
+def test_tensor_core_zgemm_timeout_and_recovery(S):
+    """With the timeout probe on, the product's last MMA wait targets a phase that nothing
+    completes and expires after the 1 ms limit: SYMHSS_ERR_TIMEOUT after the kernel drained its
+    MMAs; with the probe off and the default limit the same call then gives the product."""
+    rng = np.random.default_rng(9)
+    m, n, k, batch = 200, 40, 64, 2
+    a, b, c = _zgemm_case(rng, m, n, k, batch, spread=1.0)
+    da, db = _colmajor(a), _colmajor(b)
+    dc = torch.zeros((batch, n, m), dtype=torch.complex128, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    try:
+        S.symhss_set_wait_limit_ns(1_000_000)
+        S.symhss_set_timeout_probe(True)
+        with pytest.raises(S.SymhssError) as exc:
+            S.symhss_zgemm(da.data_ptr(), m, m * k, db.data_ptr(), k, k * n, dc.data_ptr(), m, m * n, m, n, k,
+                           batch, 0, stream)
+        assert exc.value.code == S.SYMHSS_ERR_TIMEOUT
+    finally:
+        S.symhss_set_timeout_probe(False)
+        S.symhss_set_wait_limit_ns(0)
+    S.symhss_zgemm(da.data_ptr(), m, m * k, db.data_ptr(), k, k * n, dc.data_ptr(), m, m * n, m, n, k, batch, 0,
+                   stream)
+    torch.cuda.synchronize()
+    got = np.transpose(dc.cpu().numpy(), (0, 2, 1))
+    assert np.abs(got - a @ b).max() <= 1e-12 * np.abs(a @ b).max()
