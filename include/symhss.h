@@ -260,25 +260,31 @@ long long symhss_launch_count(void);
 const char* symhss_strerror(int status);
 
 /* ---- launch tuning and the autotuner -------------------------------------------------
- * Launch-shape choices that do not change any result bit (except tile_loop_chunk and
- * id_cluster_max, which change nothing either: the same arithmetic runs in other blocks). */
+ * Launch-shape choices that do not change any result bit (tile_loop_chunk and id_cluster_max
+ * change nothing either: the same arithmetic runs in other blocks), and lu_tc, which selects
+ * the factorisation's arithmetic path. */
 typedef struct {
   int lu_lookahead;       /* 1: next LU panel on a high-priority stream during the trailing update */
   int lu_panel_threads;   /* 256, 512 or 1024: largest thread block of the LU panel kernel      */
   int tile_loop_chunk;    /* 0: adaptive (8..32 by launch size); else 8, 16 or 32 loop points per block */
   int id_cluster_max;     /* 1, 2, 4, 8 or 16: largest thread-block cluster of one column ID      */
   int lu_panel_cluster;   /* 1, 2, 4, 8 or 16: largest cluster factoring one LU panel (1: one block) */
-  int reserved[3];
+  int lu_tc;              /* 1 (default): FP64 block LUs blocked by 64 columns and multi-RHS solves
+                           * blocked by 64 rows, their updates on the tensor cores (symhss_zgemm);
+                           * 0: 16-column LU and unblocked solves on the FP64 pipe.  Both give the
+                           * factorisation to FP64 rounding, not the same bits. */
+  int reserved[2];
 } symhss_tuning;
 
 int symhss_get_tuning(symhss_t h, symhss_tuning* out);
 /* Set the handle's launch tuning (values outside the lists above: SYMHSS_ERR_INVALID). */
 int symhss_set_tuning(symhss_t h, const symhss_tuning* t);
 /* Autotuner: time the handle's own compress / factor with each value of each tunable
- * (coordinate search: tile_loop_chunk and id_cluster_max on compress, then
- * lu_panel_threads x lu_lookahead and lu_panel_cluster on factor), `reps` runs per value, the minimum device
- * time of the affected kernel class deciding; leaves the best tuning set (and in *out,
- * if not NULL) and the handle compressed and factorised.  Synchronises `stream`. */
+ * (coordinate search: tile_loop_chunk and id_cluster_max on compress, then lu_tc (block LU +
+ * solve time), lu_panel_threads x lu_lookahead and lu_panel_cluster on factor), `reps` runs
+ * per value, the minimum device time of the affected kernel classes deciding; leaves the best
+ * tuning set (and in *out, if not NULL) and the handle compressed and factorised.
+ * Synchronises `stream`. */
 int symhss_autotune(symhss_t h, int reps, symhss_tuning* out, void* stream);
 
 /* ---- learned rank / skeleton proposer (an addition to the paper's method) --------------

@@ -167,7 +167,7 @@ struct symhss_s {
   symhss_stats_t st{};
   cudaError_t last_cuda = cudaSuccess;
   std::vector<int> mark;                          // host scratch (size npts)
-  symhss_tuning tune = {0, 256, 0, 16, 1, {0, 0, 0}};  // launch tuning (symhss_set_tuning)
+  symhss_tuning tune = {0, 256, 0, 16, 1, 1, {0, 0}};  // launch tuning (symhss_set_tuning)
   symhss_mlp_s* mlp = nullptr;                    // attached proposer (not owned)
   double prop_margin = 1.15;
   symhss::DevBuf featjobs, feats, mlpout, chkjobs, chkratio;
@@ -1150,6 +1150,7 @@ int assemble_and_lu(symhss_s* h, int t, cudaStream_t s, long long& pairs) {
   la.lookahead = h->tune.lu_lookahead;
   la.panel_threads = h->tune.lu_panel_threads;
   la.panel_cluster = h->tune.lu_panel_cluster;
+  la.tc = h->tune.lu_tc;
   // the assembled blocks are the FP64 operator's (leaf blocks, sibling skeleton blocks)
   CK(H.Dop.ensure(d_total * sizeof(double2)));
   CK(cudaMemcpyAsync(H.Dop.p, H.D.p, d_total * sizeof(double2), cudaMemcpyDeviceToDevice, s));
@@ -1285,6 +1286,7 @@ int factor_height(symhss_s* h, int t, cudaStream_t s, long long& pairs, bool lu_
   ra.max_rhs = max_k;
   ra.max_n = max_n;
   ra.status = h->status.as<int>();
+  ra.tc = h->tune.lu_tc;
   TIMED(SYMHSS_K_GETRS, w_x, launch_getrs(ra, s));
   // R X
   BasisLaunch br = bl;
@@ -1310,6 +1312,7 @@ int factor_height(symhss_s* h, int t, cudaStream_t s, long long& pairs, bool lu_
   la.lookahead = h->tune.lu_lookahead;
   la.panel_threads = h->tune.lu_panel_threads;
   la.panel_cluster = h->tune.lu_panel_cluster;
+  la.tc = h->tune.lu_tc;
   TIMED(SYMHSS_K_GETRF, w_rxlu, launch_getrf(la, s));
   if (mixed)
     TIMED(SYMHSS_K_OTHER, 0.0, launch_copy_blocks32(nullptr, H.At32.as<float2>(),
@@ -1330,6 +1333,7 @@ int factor_height(symhss_s* h, int t, cudaStream_t s, long long& pairs, bool lu_
   rb.max_rhs = max_k;
   rb.max_n = max_k;
   rb.status = h->status.as<int>();
+  rb.tc = h->tune.lu_tc;
   TIMED(SYMHSS_K_GETRS, w_at, launch_getrs(rb, s));
   if (mixed) {  // X and Atilde in FP64 for the parents' blocks and the solve phase
     TIMED(SYMHSS_K_OTHER, 0.0, launch_widen(H.X32.as<float2>(), H.X.as<double2>(), x_total, s));
@@ -2182,7 +2186,7 @@ static bool tuning_ok(const symhss_tuning* t) {
   };
   return in(t->lu_lookahead, {0, 1}) && in(t->lu_panel_threads, {256, 512, 1024}) &&
          in(t->tile_loop_chunk, {0, 8, 16, 32}) && in(t->id_cluster_max, {1, 2, 4, 8, 16}) &&
-         in(t->lu_panel_cluster, {1, 2, 4, 8, 16});
+         in(t->lu_panel_cluster, {1, 2, 4, 8, 16}) && in(t->lu_tc, {0, 1});
 }
 
 int symhss_get_tuning(symhss_t h, symhss_tuning* out) {
@@ -2230,6 +2234,20 @@ int symhss_autotune(symhss_t h, int reps, symhss_tuning* out, void* stream) {
   h->tune = best;
   int rc = symhss_compress(h, stream);
   if (rc) return rc;
+  // the factorisation's arithmetic path: block LU and solve classes together
+  bms = 1e300;
+  for (int v : {1, 0}) {
+    h->tune = best;
+    h->tune.lu_tc = v;
+    double m = 1e300;
+    for (int r = 0; r < reps; ++r) {
+      const double b0 = h->st.kernel_ms[SYMHSS_K_GETRF] + h->st.kernel_ms[SYMHSS_K_GETRS];
+      rc = symhss_factor(h, stream);
+      if (rc) return rc;
+      m = std::min(m, h->st.kernel_ms[SYMHSS_K_GETRF] + h->st.kernel_ms[SYMHSS_K_GETRS] - b0);
+    }
+    if (m < bms) { bms = m; best.lu_tc = v; }
+  }
   bms = 1e300;
   for (int pt : {256, 512, 1024})
     for (int la : {0, 1}) {
