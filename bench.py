@@ -493,6 +493,8 @@ def _comparators(w, args, tunings, step, world):
 
 
 def _mixed_vs_fp64(w, res, step):
+    """Relative differences of the mixed-precision solutions (after the default two refinement
+    steps, and with none) from the FP64 symmetric solution of the same workload."""
     import numpy as np
 
     from paper_2609_33216_b300.solver import Solver
@@ -503,8 +505,45 @@ def _mixed_vs_fp64(w, res, step):
     out = {}
     for md in ("sym", "base"):
         out[f"{md}_vs_fp64_sym"] = float(np.linalg.norm(res[md]["x"] - xr) / np.linalg.norm(xr))
+    sv = res["solvers"]["sym"]
+    sv.set_refinement(0)
+    x0 = sv.solve(sv.rhs(0.0)).cpu().numpy()
+    sv.set_refinement(2)
+    out["sym_vs_fp64_sym_before_refinement"] = float(np.linalg.norm(x0 - xr) / np.linalg.norm(xr))
     out["refinement_steps"] = 2
     return out
+
+
+def _fixed_rank_sweep(sizes=(4096, 8192, 16384, 32768, 65536, 131072, 262144), steps=3, warmup=2):
+    """The fixed-rank schedule k_l = ceil(1.15^(L - l) 30) (Sec. 4.3) on the star r = 1 + 0.3 cos 5t
+    with k 20/30, leaf 128, for N = 4096 .. 262144: device ms of build + solve per step (CUDA
+    events, median of `steps`), and ms per 1000 nodes (flat for the linear complexity of
+    Theorem `order`, which holds for a < 2^(1/3))."""
+    import torch
+
+    from paper_2609_33216_b300.solver import Solver
+    from synth import star
+
+    stream = torch.cuda.current_stream()
+    rows = []
+    for n in sizes:
+        sv = Solver(star(n), 20.0, 30.0, mode="sym", curve_on_device=True, leaf=128, nproxy=64, tol=1e-10,
+                    fixed_rank_kL=30, rank_scale_a=1.15)
+        for _ in range(warmup):
+            sv.build()
+            sv.solve(sv.rhs(0.0))
+        ms = []
+        for _ in range(steps):
+            with _Timer(stream) as tm:
+                sv.build()
+                sv.solve(sv.rhs(0.0))
+            ms.append(tm.ms)
+        st = sv.stats()
+        rows.append({"n": n, "ms": statistics.median(ms), "ms_per_1000_nodes": statistics.median(ms) / (n / 1000.0),
+                     "root_size": st.root_size, "depth": st.depth})
+        sv.close()
+    return {"schedule": "k_l = ceil(1.15^(L-l) 30), symmetric, FP64, star r = 1 + 0.3 cos 5t, k 20/30, leaf 128",
+            "rows": rows}
 
 
 def _extra_workloads(args):
@@ -515,7 +554,7 @@ def _extra_workloads(args):
 
     from paper_2609_33216_b300 import symhss as S
 
-    out = {}
+    out = {"fixed_rank_sweep": _fixed_rank_sweep()}
     specs = [("star64k", "mixed", False), ("batch64", "fp64", False), ("star262k", "fp64", True)]
     for name, prec, proposer in specs:
         w = _workload(name)

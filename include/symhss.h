@@ -249,6 +249,21 @@ int symhss_level_ranks(symhss_t h, int level, int* out);
 /* As symhss_level_ranks for problem `problem` of a batch (level 1..depth[problem]). */
 int symhss_problem_ranks(symhss_t h, int problem, int level, int* out);
 
+/* Largest ID rank the caller accepts (<= 0: no limit, the default).  A compression whose
+ * column (or, with SYMHSS_NONSYM, row) ID of any box exceeds it stops with
+ * SYMHSS_ERR_RANK_OVERFLOW and leaves the handle uncompressed; the handle stays usable (raise
+ * the limit and compress again).  For callers that size later storage -- skeleton sets,
+ * factors, transfers to other processes -- from a rank bound fixed in advance. */
+int symhss_set_rank_limit(symhss_t h, int max_rank);
+
+/* Device-memory budget, in bytes, for the buffers the handle allocates or grows in its later
+ * calls (<= 0: none, the default).  An allocation that would take the handle's total beyond
+ * it fails before cudaMalloc is called, and the call returns SYMHSS_ERR_NOMEM as on a full
+ * device; the handle stays usable and a later call succeeds once the budget allows.  For
+ * callers that share one GPU between several solvers under a fixed memory plan.  Buffers
+ * allocated by symhss_create are not counted. */
+int symhss_set_memory_limit(symhss_t h, long long bytes);
+
 /* Release everything the handle owns.  NULL is accepted. */
 int symhss_destroy(symhss_t h);
 
@@ -324,12 +339,14 @@ int symhss_mlp_destroy(symhss_mlp_t net);
 /* Attach a trained network to a solver handle (NULL detaches; the network must outlive
  * its use).  During symhss_compress the network proposes each box's two ID ranks r~ and
  * the randomized sketch of that ID gets s = 16 ceil((ceil(margin r~) + 2 + oversample) / 16)
- * rows for the ID (at least 32) instead of the default estimate.  Every sketched ID --
- * proposed or not -- also gets 16 held-out sketch rows; it is accepted only if its
- * interpolation residual on those rows (an a-posteriori estimate of the residual on the
- * proxy matrix) is at most tol times their largest column norm, and is otherwise redone
- * as a plain ID of the proxy matrix.  margin >= 1.  Has no effect with oversample = 0 or
- * fixed ranks. */
+ * rows for the ID (at least 32) instead of the default estimate.  While a network is
+ * attached, every sketched ID is accepted only if its interpolation residual on the proxy
+ * matrix itself, max_c ||m_c - M_J t_c||, is at most tol times the largest column norm of M
+ * (the bound the plain ID meets by construction); an ID that fails continues its pivoted QR
+ * on the sketch at tol / 16 and is checked again, and is otherwise redone as a plain ID of
+ * the proxy matrix.  (Without a network the check uses 16 held-out sketch rows, an
+ * a-posteriori estimate of that residual.)  margin >= 1.  Has no effect with oversample = 0
+ * or fixed ranks. */
 int symhss_set_proposer(symhss_t h, symhss_mlp_t net, double margin);
 
 /* Training data of the last compression: one sample per compressed (non-root) box of

@@ -273,6 +273,20 @@ int cpqr_cluster_size(int njobs, int max_n);
 // run on held-out sketch rows): ratio[out] = max over non-skeleton columns c of
 // ||M[:, c] - M[:, J] T[:, c]|| divided by the largest column norm of M (J = perm[0 .. rank),
 // T = R11^{-1} R12 with leading dimension rank).
+// One ID checked on its proxy matrix M (m x n at m_off, leading dimension ld): its skeleton
+// columns go to g + g1_off (m x r), the others to g + g2_off (m x (n - r)), both with leading
+// dimension m (idcheck.cu).
+struct GatherJob {
+  long long m_off;
+  int m, n, ld, r;
+  long long perm_off;
+  long long g1_off, g2_off;
+};
+cudaError_t launch_gather_cols(const double2* mats, const int* perm, const GatherJob* jobs, const int2* work,
+                               int nwork, double2* g, cudaStream_t s);
+cudaError_t launch_residual_ratio(const double2* mats, const double2* g, const GatherJob* jobs, const int* outs,
+                                  int njobs, double* ratio, cudaStream_t s);
+
 struct CheckJob {
   long long m_off;   // M at mats + m_off (column-major, leading dim ld)
   int m, n, ld;

@@ -69,3 +69,71 @@ cudaError_t launch_id_check(const double2* mats, const double2* tbuf, const int*
 }
 
 }  // namespace symhss
+
+// ---- exact residual on the proxy matrix, with the product on the tensor cores ----------
+// For each checked ID of M (m x n): G1 = M[:, perm[0:r]] and G2 = M[:, perm[r:n]] are
+// gathered, G2 -= G1 T runs on the tensor cores (zgemm_tc.cu), and the ratio of G2's largest
+// column norm to M's is taken.
+
+namespace symhss {
+
+namespace {
+
+__global__ void __launch_bounds__(256) gather_cols_kernel(const double2* mats, const int* perm,
+                                                           const GatherJob* jobs, const int2* work, double2* g) {
+  const int2 w = work[blockIdx.x];
+  const GatherJob jb = jobs[w.x];
+  const int c = w.y;
+  const int src = perm[jb.perm_off + c];
+  if (src < 0 || src >= jb.n) return;  // a permutation entry out of range: leave the column unset
+  const double2* col = mats + jb.m_off + (long long)src * jb.ld;
+  double2* dst = g + (c < jb.r ? jb.g1_off + (long long)c * jb.m : jb.g2_off + (long long)(c - jb.r) * jb.m);
+  for (int i = threadIdx.x; i < jb.m; i += blockDim.x) dst[i] = col[i];
+}
+
+__global__ void __launch_bounds__(256) ratio_kernel(const double2* mats, const double2* g, const GatherJob* jobs,
+                                                    const int* outs, double* ratio) {
+  __shared__ double s_max[2][8];
+  const GatherJob jb = jobs[blockIdx.x];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double ref = 0.0, res = 0.0;
+  for (int c = warp; c < jb.n; c += 8) {
+    const double2* col = mats + jb.m_off + (long long)c * jb.ld;
+    double ss = 0.0;
+    for (int i = lane; i < jb.m; i += 32) ss = fma(col[i].x, col[i].x, fma(col[i].y, col[i].y, ss));
+    ref = fmax(ref, warp_sum(ss));
+  }
+  for (int c = warp; c < jb.n - jb.r; c += 8) {
+    const double2* col = g + jb.g2_off + (long long)c * jb.m;
+    double ss = 0.0;
+    for (int i = lane; i < jb.m; i += 32) ss = fma(col[i].x, col[i].x, fma(col[i].y, col[i].y, ss));
+    res = fmax(res, warp_sum(ss));
+  }
+  if (lane == 0) { s_max[0][warp] = ref; s_max[1][warp] = res; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int q = 0; q < 8; ++q) { a = fmax(a, s_max[0][q]); b = fmax(b, s_max[1][q]); }
+    ratio[outs[blockIdx.x]] = a > 0.0 ? sqrt(b / a) : 0.0;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_gather_cols(const double2* mats, const int* perm, const GatherJob* jobs, const int2* work,
+                               int nwork, double2* g, cudaStream_t s) {
+  if (nwork <= 0) return cudaSuccess;
+  gather_cols_kernel<<<nwork, 256, 0, s>>>(mats, perm, jobs, work, g);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual_ratio(const double2* mats, const double2* g, const GatherJob* jobs, const int* outs,
+                                  int njobs, double* ratio, cudaStream_t s) {
+  if (njobs <= 0) return cudaSuccess;
+  ratio_kernel<<<njobs, 256, 0, s>>>(mats, g, jobs, outs, ratio);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace symhss

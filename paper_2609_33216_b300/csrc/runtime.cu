@@ -40,31 +40,60 @@
 namespace symhss {
 
 // ---- growable device buffer -------------------------------------------------------
+// A handle's device-memory budget (symhss_set_memory_limit): the bytes its growable buffers
+// hold.  While one of the handle's calls runs, g_budget points at it; a buffer remembers
+// the budget it was allocated under and returns its bytes on release.
+struct Budget {
+  long long limit = 0;  // <= 0: none
+  long long used = 0;
+};
+thread_local Budget* g_budget = nullptr;
+
+struct BudgetScope {
+  Budget* saved;
+  explicit BudgetScope(Budget* b) : saved(g_budget) { g_budget = b; }
+  ~BudgetScope() { g_budget = saved; }
+};
+
 struct DevBuf {
   void* p = nullptr;
   size_t cap = 0;
+  Budget* bud = nullptr;
   DevBuf() = default;
   DevBuf(const DevBuf&) = delete;
   DevBuf& operator=(const DevBuf&) = delete;
-  DevBuf(DevBuf&& o) noexcept : p(o.p), cap(o.cap) { o.p = nullptr; o.cap = 0; }
+  DevBuf(DevBuf&& o) noexcept : p(o.p), cap(o.cap), bud(o.bud) { o.p = nullptr; o.cap = 0; o.bud = nullptr; }
   DevBuf& operator=(DevBuf&& o) noexcept {
-    if (this != &o) { release(); p = o.p; cap = o.cap; o.p = nullptr; o.cap = 0; }
+    if (this != &o) {
+      release();
+      p = o.p; cap = o.cap; bud = o.bud;
+      o.p = nullptr; o.cap = 0; o.bud = nullptr;
+    }
     return *this;
   }
   ~DevBuf() { release(); }
   void release() {
-    if (p) cudaFree(p);
+    if (p) {
+      cudaFree(p);
+      if (bud) bud->used -= (long long)cap;
+    }
     p = nullptr;
     cap = 0;
+    bud = nullptr;
   }
-  // grow to at least `bytes` (contents are not preserved on growth)
+  // grow to at least `bytes` (contents are not preserved on growth); beyond the current
+  // call's budget this fails as an out-of-memory allocation, without calling cudaMalloc
   cudaError_t ensure(size_t bytes) {
     if (bytes == 0) bytes = 16;
     if (bytes <= cap) return cudaSuccess;
     release();
+    Budget* b = g_budget;
+    if (b && b->limit > 0 && b->used + (long long)bytes > b->limit) return cudaErrorMemoryAllocation;
     cudaError_t e = cudaMalloc(&p, bytes);
     if (e != cudaSuccess) { p = nullptr; return e; }
     cap = bytes;
+    bud = b;
+    if (bud) bud->used += (long long)bytes;
     return cudaSuccess;
   }
   template <class T> T* as() const { return reinterpret_cast<T*>(p); }
@@ -130,6 +159,7 @@ struct Height {
   DevBuf D32, X32, RX32, At32;   // complex64 work of the mixed-precision factorisation
   // solve
   DevBuf G, FT, TMP, slists;
+  DevBuf chkmeta, chkg;          // exact residual checks of sketched IDs (proposer mode)
   // matvec
   DevBuf XV, XS, ZV, YS, YV, mlists;
   std::vector<int> h_rank;
@@ -174,6 +204,8 @@ struct symhss_s {
   int refine_steps = 2;                           // SYMHSS_MIXED solves
   cudaStream_t cstream = nullptr;                 // high-priority stream of the pipelined build
   symhss::DevBuf rres, rcor, rtmp;                // refinement vectors
+  int rank_limit = 0;                             // symhss_set_rank_limit (<= 0: none)
+  symhss::Budget budget;                          // symhss_set_memory_limit
 };
 
 namespace symhss {
@@ -772,17 +804,29 @@ int compress_height(symhss_s* h, int t, cudaStream_t s) {
   TIMED(SYMHSS_K_ID, 0.0, launch_cpqr(ia, s));
   ia.tol = h->prm.tol;
   const size_t id_mark = h->marks.size() > id_before ? id_before : (size_t)-1;
-  // a-posteriori residual estimate of every sketched ID: its interpolation of the
+  // residual check of every sketched ID.  Without a proposer: its interpolation of the
   // held-out sketch rows Omega_h M (Halko-Martinsson-Tropp, Sec. 4.3 of their survey:
-  // ||Omega_h e|| / sqrt(q) estimates ||e|| for Rademacher Omega_h with q rows)
+  // ||Omega_h e|| / sqrt(q) estimates ||e|| for Rademacher Omega_h with q rows).  With a
+  // proposer attached, the ID of a proposed sketch is accepted on its residual on the proxy
+  // matrix itself, max_c ||m_c - M_J t_c|| <= tol max_c ||m_c|| (the bound a plain ID meets by
+  // construction: its stopping pivot is the largest remaining column norm).
+  const bool proxy_check = h->mlp != nullptr;
+  auto check_rows = [&](int i) {
+    CheckJob c;
+    if (proxy_check) {
+      c.m_off = full[i].m_off; c.m = full[i].m; c.n = full[i].n; c.ld = full[i].ld;
+    } else {
+      c.m_off = jobs[i].m_off + sk_rows[i]; c.m = kHoldRows; c.n = jobs[i].n; c.ld = jobs[i].ld;
+    }
+    return c;
+  };
   std::vector<int> chk_of(njobs, -1);
   std::vector<double> ratio;
-  if (!sketch_jobs.empty()) {
+  if (!sketch_jobs.empty() && !proxy_check) {
     std::vector<CheckJob> cj;
     for (int i = 0; i < njobs; ++i) {
       if (sk_rows[i] == 0) continue;
-      CheckJob c;
-      c.m_off = jobs[i].m_off + sk_rows[i]; c.m = kHoldRows; c.n = jobs[i].n; c.ld = jobs[i].ld;
+      CheckJob c = check_rows(i);
       c.rank_idx = jobs[i].out_idx; c.t_off = jobs[i].t_off; c.perm_off = jobs[i].perm_off;
       c.out = (int)cj.size(); c.pad_ = 0;
       chk_of[i] = c.out;
@@ -802,6 +846,90 @@ int compress_height(symhss_s* h, int t, cudaStream_t s) {
   CK(cudaMemcpyAsync(hr.data(), H.rankbuf.p, njobs * sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(hp.data(), H.permbuf.p, perm_total * sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  // exact residual of the given sketched IDs on their proxy matrices (ranks and permutations
+  // read back above): gather M_J and M_rest, M_rest -= M_J T on the tensor cores, ratio of the
+  // largest residual column norm to the largest column norm of M
+  auto proxy_ratios = [&](const std::vector<int>& ids, std::vector<double>& out) -> int {
+    out.assign(ids.size(), 0.0);
+    if (ids.empty()) return SYMHSS_OK;
+    std::vector<GatherJob> gj;
+    std::vector<int2> work;
+    std::vector<int> outs;
+    long long gtot = 0;
+    int maxr = 0;
+    for (size_t k = 0; k < ids.size(); ++k) {
+      const int i = ids[k];
+      GatherJob g;
+      g.m_off = full[i].m_off; g.m = full[i].m; g.n = full[i].n; g.ld = full[i].ld;
+      g.r = std::min(std::max(hr[jobs[i].out_idx], 0), g.n);
+      g.perm_off = jobs[i].perm_off;
+      g.g1_off = gtot;
+      g.g2_off = gtot + (long long)g.m * g.r;
+      gtot += (long long)g.m * g.n;
+      maxr = std::max(maxr, g.r);
+      for (int c = 0; c < g.n; ++c) work.push_back(make_int2((int)gj.size(), c));
+      outs.push_back((int)k);
+      gj.push_back(g);
+    }
+    const int TM = zgemm_tc_tile_rows(), TN = zgemm_tc_tile_cols(), KM = zgemm_tc_max_k();
+    const int nchunk = (maxr + KM - 1) / KM;
+    std::vector<std::vector<ZgemmJob>> zj(nchunk);
+    std::vector<std::vector<ZgemmTile>> zt(nchunk);
+    for (size_t k = 0; k < ids.size(); ++k) {
+      const GatherJob& g = gj[k];
+      const int rest = g.n - g.r;
+      if (g.r == 0 || rest == 0) continue;
+      for (int c = 0; c * KM < g.r; ++c) {
+        ZgemmJob z;
+        z.a_off = g.g1_off + (long long)c * KM * g.m; z.lda = g.m;
+        z.b_off = jobs[ids[k]].t_off + (long long)c * KM; z.ldb = g.r;
+        z.c_off = g.g2_off; z.ldc = g.m;
+        z.m = g.m; z.n = rest; z.k = std::min(KM, g.r - c * KM);
+        const int jid = (int)zj[c].size();
+        zj[c].push_back(z);
+        for (int a = 0; a < (g.m + TM - 1) / TM; ++a)
+          for (int b = 0; b < (rest + TN - 1) / TN; ++b) zt[c].push_back(ZgemmTile{jid, a, b});
+      }
+    }
+    Packer pg;
+    const size_t og = pg.add(gj), ow = pg.add(work), oo = pg.add(outs);
+    std::vector<size_t> ozj(nchunk), ozt(nchunk);
+    for (int c = 0; c < nchunk; ++c) { ozj[c] = pg.add(zj[c]); ozt[c] = pg.add(zt[c]); }
+    CK(pg.upload(H.chkmeta, s));
+    CK(H.chkg.ensure((size_t)gtot * sizeof(double2)));
+    CK(h->chkratio.ensure(ids.size() * sizeof(double)));
+    const char* mb = H.chkmeta.as<char>();
+    double w = 0;
+    for (const GatherJob& g : gj) w += 8.0 * (double)g.m * g.r * (g.n - g.r);
+    const int e0 = prof_begin(h, s);
+    CK(launch_gather_cols(H.mr.as<double2>(), H.permbuf.as<int>(), reinterpret_cast<const GatherJob*>(mb + og),
+                          reinterpret_cast<const int2*>(mb + ow), (int)work.size(), H.chkg.as<double2>(), s));
+    for (int c = 0; c < nchunk; ++c) {
+      if (zt[c].empty()) continue;
+      ZgemmLaunch za;
+      za.A = H.chkg.as<double2>(); za.B = H.tbuf.as<double2>(); za.C = H.chkg.as<double2>();
+      za.jobs = reinterpret_cast<const ZgemmJob*>(mb + ozj[c]);
+      za.tiles = reinterpret_cast<const ZgemmTile*>(mb + ozt[c]);
+      za.ntiles = (int)zt[c].size();
+      za.mode = ZGEMM_SUB;
+      za.status = h->status.as<int>();
+      za.wait_ns = 0;
+      CK(launch_zgemm_tc(za, s));
+    }
+    CK(launch_residual_ratio(H.mr.as<double2>(), H.chkg.as<double2>(), reinterpret_cast<const GatherJob*>(mb + og),
+                             reinterpret_cast<const int*>(mb + oo), (int)gj.size(), h->chkratio.as<double>(), s));
+    prof_end(h, s, SYMHSS_K_CHECK, e0, w);
+    CK(cudaMemcpyAsync(out.data(), h->chkratio.p, ids.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return read_status(h, s);
+  };
+  if (!sketch_jobs.empty() && proxy_check) {
+    std::vector<int> ids;
+    for (int i = 0; i < njobs; ++i)
+      if (sk_rows[i] != 0) { chk_of[i] = (int)ids.size(); ids.push_back(i); }
+    const int rc = proxy_ratios(ids, ratio);
+    if (rc) return rc;
+  }
   if (!prop.empty()) {
     for (int i = 0; i < njobs; ++i) {
       if (jobs[i].n == 0 || jobs[i].out_idx >= 2 * nb) continue;
@@ -849,8 +977,7 @@ int compress_height(symhss_s* h, int t, cudaStream_t s) {
         j.start = hr[i];
         cjobs.push_back(j);
         mm = std::max(mm, j.m);
-        CheckJob c;
-        c.m_off = jobs[i].m_off + sk_rows[i]; c.m = kHoldRows; c.n = jobs[i].n; c.ld = jobs[i].ld;
+        CheckJob c = check_rows(i);
         c.rank_idx = jobs[i].out_idx; c.t_off = jobs[i].t_off; c.perm_off = jobs[i].perm_off;
         c.out = (int)chk.size(); c.pad_ = 0;
         chk.push_back(c);
@@ -866,18 +993,24 @@ int compress_height(symhss_s* h, int t, cudaStream_t s) {
       TIMED(SYMHSS_K_ID, 0.0, launch_cpqr(ia, s));
       ia.tol = h->prm.tol;
       ia.max_m = max_m;
-      CK(h->chkratio.ensure(chk.size() * sizeof(double)));
-      TIMED(SYMHSS_K_CHECK, 0.0, launch_id_check(H.mr.as<double2>(), H.tbuf.as<double2>(), H.permbuf.as<int>(),
-                                                 H.rankbuf.as<int>(),
-                                                 reinterpret_cast<const CheckJob*>(H.idjobs.as<char>() + oc),
-                                                 (int)chk.size(), h->chkratio.as<double>(), s));
       std::vector<double> r2(chk.size());
+      if (!proxy_check) {
+        CK(h->chkratio.ensure(chk.size() * sizeof(double)));
+        TIMED(SYMHSS_K_CHECK, 0.0, launch_id_check(H.mr.as<double2>(), H.tbuf.as<double2>(), H.permbuf.as<int>(),
+                                                   H.rankbuf.as<int>(),
+                                                   reinterpret_cast<const CheckJob*>(H.idjobs.as<char>() + oc),
+                                                   (int)chk.size(), h->chkratio.as<double>(), s));
+        CK(cudaMemcpyAsync(r2.data(), h->chkratio.p, chk.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+      }
       std::vector<int> before(cont.size());
       for (size_t k = 0; k < cont.size(); ++k) before[k] = hr[cont[k]];
-      CK(cudaMemcpyAsync(r2.data(), h->chkratio.p, chk.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
       CK(cudaMemcpyAsync(hr.data(), H.rankbuf.p, njobs * sizeof(int), cudaMemcpyDeviceToHost, s));
       CK(cudaMemcpyAsync(hp.data(), H.permbuf.p, perm_total * sizeof(int), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
+      if (proxy_check) {
+        const int rc = proxy_ratios(cont, r2);
+        if (rc) return rc;
+      }
       if (h->marks.size() > cb) {
         double w = 0;
         for (size_t k = 0; k < cont.size(); ++k) {
@@ -975,6 +1108,7 @@ int compress_height(symhss_s* h, int t, cudaStream_t s) {
     for (int p = 0; p < 2; ++p) {
       const IdJob& j = jobs[2 * i + p];
       bx.rank[p] = hr[2 * i + p];
+      if (h->rank_limit > 0 && bx.rank[p] > h->rank_limit) return SYMHSS_ERR_RANK_OVERFLOW;
       bx.perm[p].assign(hp.begin() + j.perm_off, hp.begin() + j.perm_off + j.n);
       if (sym) {
         bx.rrank[p] = bx.rank[p];
@@ -983,6 +1117,7 @@ int compress_height(symhss_s* h, int t, cudaStream_t s) {
       } else {
         const IdJob& jr = jobs[2 * nb + 2 * i + p];
         bx.rrank[p] = hr[jr.out_idx];
+        if (h->rank_limit > 0 && bx.rrank[p] > h->rank_limit) return SYMHSS_ERR_RANK_OVERFLOW;
         bx.rperm[p].assign(hp.begin() + jr.perm_off, hp.begin() + jr.perm_off + jr.n);
         if (bx.rrank[p] != bx.rank[p]) return SYMHSS_ERR_DEVICE;
       }
@@ -1511,6 +1646,7 @@ int symhss_create(const symhss_curve* curve, const symhss_params* prm, void* str
 }
 
 int symhss_set_curves(symhss_t h, const symhss_curve* curves, int count, void* stream) {
+  BudgetScope budget_scope(h ? &h->budget : nullptr);
   if (!h || !curves || count != (int)h->probs.size()) return SYMHSS_ERR_INVALID;
   for (int c = 0; c < count; ++c)
     if (curves[c].n != h->probs[c].n) return SYMHSS_ERR_INVALID;
@@ -1595,6 +1731,7 @@ static void rank_stats(symhss_s* h) {
 }
 
 int symhss_compress(symhss_t h, void* stream) {
+  BudgetScope budget_scope(h ? &h->budget : nullptr);
   if (!h) return SYMHSS_ERR_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
   reset_compress_stats(h);
@@ -1622,6 +1759,7 @@ int symhss_compress(symhss_t h, void* stream) {
 }
 
 int symhss_factor(symhss_t h, void* stream) {
+  BudgetScope budget_scope(h ? &h->budget : nullptr);
   if (!h) return SYMHSS_ERR_INVALID;
   if (!h->compressed && h->maxdepth > 0) return SYMHSS_ERR_STATE;
   cudaStream_t s = (cudaStream_t)stream;
@@ -1654,6 +1792,7 @@ int symhss_factor(symhss_t h, void* stream) {
 }
 
 int symhss_build(symhss_t h, void* stream) {
+  BudgetScope budget_scope(h ? &h->budget : nullptr);
   if (!h) return SYMHSS_ERR_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
   if (!h->cstream) {
@@ -1719,6 +1858,7 @@ int symhss_build(symhss_t h, void* stream) {
 }
 
 int symhss_rhs_plane_wave(symhss_t h, double angle, void* rhs, void* stream) {
+  BudgetScope budget_scope(h ? &h->budget : nullptr);
   if (!h || !rhs || !std::isfinite(angle)) return SYMHSS_ERR_INVALID;
   CK(launch_plane_wave(table_of(h), h->waves.as<WaveJob>(), (int)h->probs.size(), h->max_n, angle,
                        h->prm.mode == SYMHSS_SYM ? 1 : 0, reinterpret_cast<double2*>(rhs), (cudaStream_t)stream));
@@ -2076,6 +2216,7 @@ int matvec_core(symhss_s* h, const double2* xin, double2* yout, int nrhs, cudaSt
 extern "C" {
 
 int symhss_solve(symhss_t h, const void* rhs, void* x, int nrhs, void* stream) {
+  BudgetScope budget_scope(h ? &h->budget : nullptr);
   if (!h || !rhs || !x || nrhs < 1) return SYMHSS_ERR_INVALID;
   if (!h->factored) return SYMHSS_ERR_STATE;
   cudaStream_t s = (cudaStream_t)stream;
@@ -2113,6 +2254,7 @@ int symhss_solve(symhss_t h, const void* rhs, void* x, int nrhs, void* stream) {
 }
 
 int symhss_matvec(symhss_t h, const void* x, void* y, int nrhs, void* stream) {
+  BudgetScope budget_scope(h ? &h->budget : nullptr);
   if (!h || !x || !y || nrhs < 1) return SYMHSS_ERR_INVALID;
   if (!h->factored) return SYMHSS_ERR_STATE;
   cudaStream_t s = (cudaStream_t)stream;
@@ -2133,6 +2275,7 @@ int symhss_set_refinement(symhss_t h, int steps) {
 }
 
 int symhss_solve_host(symhss_t h, const void* rhs_host, void* x_host, int nrhs, void* stream) {
+  BudgetScope budget_scope(h ? &h->budget : nullptr);
   if (!h || !rhs_host || !x_host || nrhs < 1) return SYMHSS_ERR_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
   const size_t bytes = (size_t)2 * h->ntot * nrhs * sizeof(double2);
@@ -2202,6 +2345,7 @@ int symhss_set_tuning(symhss_t h, const symhss_tuning* t) {
 }
 
 int symhss_autotune(symhss_t h, int reps, symhss_tuning* out, void* stream) {
+  BudgetScope budget_scope(h ? &h->budget : nullptr);
   if (!h || reps < 1 || reps > 100) return SYMHSS_ERR_INVALID;
   symhss_tuning best = h->tune;
   // min over reps of one kernel class's device time in compress
@@ -2280,6 +2424,18 @@ int symhss_autotune(symhss_t h, int reps, symhss_tuning* out, void* stream) {
   rc = symhss_factor(h, stream);
   if (rc) return rc;
   if (out) *out = best;
+  return SYMHSS_OK;
+}
+
+int symhss_set_rank_limit(symhss_t h, int max_rank) {
+  if (!h) return SYMHSS_ERR_INVALID;
+  h->rank_limit = max_rank > 0 ? max_rank : 0;
+  return SYMHSS_OK;
+}
+
+int symhss_set_memory_limit(symhss_t h, long long bytes) {
+  if (!h) return SYMHSS_ERR_INVALID;
+  h->budget.limit = bytes > 0 ? bytes : 0;
   return SYMHSS_OK;
 }
 

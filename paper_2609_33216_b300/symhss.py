@@ -130,6 +130,8 @@ _SIGNATURES = [
     ("symhss_speed_terms", C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     ("symhss_set_wait_limit_ns", C.c_int, [C.c_longlong]),
     ("symhss_set_timeout_probe", C.c_int, [C.c_int]),
+    ("symhss_set_rank_limit", C.c_int, [C.c_void_p, C.c_int]),
+    ("symhss_set_memory_limit", C.c_int, [C.c_void_p, C.c_longlong]),
     ("symhss_zgemm", C.c_int, [C.c_void_p, C.c_int, C.c_longlong, C.c_void_p, C.c_int, C.c_longlong, C.c_void_p,
                                C.c_int, C.c_longlong, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p]),
     ("symhss_kernel_block", C.c_int, [C.POINTER(symhss_params), C.POINTER(symhss_points), C.c_void_p,
@@ -328,6 +330,14 @@ def symhss_zgemm(a: int, lda: int, stride_a: int, b: int, ldb: int, stride_b: in
     """mode 0: C = A B, 1: C -= A B, 2: C += A B (batched, column-major complex128, device pointers)."""
     check(lib.symhss_zgemm(C.c_void_p(a), lda, stride_a, C.c_void_p(b), ldb, stride_b, C.c_void_p(c), ldc, stride_c,
                            m, n, k, batch, mode, C.c_void_p(stream)), "symhss_zgemm")
+
+
+def symhss_set_rank_limit(h, max_rank: int) -> None:
+    check(lib.symhss_set_rank_limit(h, int(max_rank)), "symhss_set_rank_limit")
+
+
+def symhss_set_memory_limit(h, nbytes: int) -> None:
+    check(lib.symhss_set_memory_limit(h, int(nbytes)), "symhss_set_memory_limit")
 
 
 def symhss_set_timeout_probe(on: bool) -> None:

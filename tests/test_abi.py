@@ -101,3 +101,9 @@ def test_speed_terms_match_oracle_on_host():
         assert np.max(np.abs(got - ref)) <= 1e-15, c.name
     with pytest.raises(RuntimeError):
         S.symhss_speed_terms(np.array([1.0, -1.0, 1.0]))
+
+
+def test_limits_reject_null_handles():
+    from paper_2609_33216_b300 import symhss as S
+    assert S.lib.symhss_set_rank_limit(None, 10) == S.SYMHSS_ERR_INVALID
+    assert S.lib.symhss_set_memory_limit(None, 1 << 20) == S.SYMHSS_ERR_INVALID

@@ -3,11 +3,13 @@ FP64 oracle:
 
 * A_hss x matches the oracle's dense A x to the compression tolerance, in both modes, and
   A_hss (B^{-1} f) = f to rounding (the factorisation inverts the same operator);
-* with precision = SYMHSS_MIXED (complex64 block LUs and solves, FP64 compression) the
-  unrefined solution is within 1e-6 of the dense LU solution and one refinement step against
-  A_hss brings it within 1e-8 (the target after refinement; before it the complex64 factors
-  leave about 2.5e-5 at 2048 nodes), in both modes; a batch of small scatterers, whose
-  unrefined error is larger, takes two steps.
+* with precision = SYMHSS_MIXED (complex64 block LUs and solves, FP64 compression) one
+  refinement step against A_hss brings the solution within 1e-8 of the dense LU solution (the
+  target after refinement), in both modes; a batch of small scatterers takes two steps.
+  Before refinement the complex64 factors leave about 2.5e-5 at 2048 nodes (k 20/30): the
+  test bounds it by 1e-4.  This misses the 1e-6 that the benchmark's mixed-precision
+  configuration asks of the unrefined solution; complex64 factorisation errors of about
+  n eps32 cond(D) set that floor, and refinement, not the unrefined solve, delivers the 1e-8.
 """
 
 import numpy as np
@@ -70,7 +72,7 @@ def test_mixed_precision_before_and_after_refinement(SV, mode):
     e0, e1, e2 = _rel(x0, xd), _rel(x1, xd), _rel(x2, xd)
     print(f"\nmixed precision ({mode}): error before refinement {e0:.2e}, after one step {e1:.2e}, two {e2:.2e}")
     assert e1 <= 1e-8, (e0, e1, e2)
-    assert e0 <= 1e-4
+    assert e0 <= 1e-4  # measured ~2.5e-5: above the 1e-6 asked before refinement (docstring)
     s.close()
 
 
