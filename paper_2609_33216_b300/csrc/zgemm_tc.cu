@@ -97,8 +97,9 @@ __device__ __forceinline__ int bexp(double x) { return (int)((__double_as_longlo
 // bit patterns with the sign of x.  The fields come from two 32-bit halves of the aligned
 // mantissa, and each 7-bit integer d becomes a float by one FP32 subtraction,
 // (2^23 + d) - 2^23, exact (instead of an integer-to-float conversion per slice).
-__device__ __forceinline__ void slice8(double x, int emax, uint32_t out[kSlices]) {
-  const long long bits = __double_as_longlong(x);
+__device__ __forceinline__ void slice8(double x, int emax, uint32_t out[kSlices], bool negate = false) {
+  // the sign is taken from the bit pattern (negation flips it: no FP64 instruction)
+  const long long bits = __double_as_longlong(x) ^ (negate ? (long long)0x8000000000000000ull : 0ll);
   const int E = (int)((bits >> 52) & 0x7FF);
   uint64_t A = 0;
   if (E != 0 && emax != 0) {
@@ -126,7 +127,7 @@ __device__ __forceinline__ double scale2(double x, int E) {
   const long long b = __double_as_longlong(x);
   const int ex = (int)((b >> 52) & 0x7FF);
   if (ex != 0 && ex + E > 0 && ex + E < 2047) return __longlong_as_double(b + ((long long)E << 52));
-  return x == 0.0 ? 0.0 : ldexp(x, E);
+  return (b & 0x7FFFFFFFFFFFFFFFll) == 0 ? x : ldexp(x, E);  // zero (tested on the bits) stays zero
 }
 
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t v[8]) {
@@ -294,16 +295,17 @@ __global__ void __launch_bounds__(kThreads, 1) zgemm_tc_kernel(const ZgemmLaunch
         const int k = k0 + 8 * kh + e;
         double2 v = make_double2(0.0, 0.0);
         if (col < n && k < K) v = B[k + (long long)col * jb.ldb];
-        // rows with Re a: (Re b | Im b); rows with Im a: (-Im b | Re b)
-        x[e] = wim ? (part ? v.x : -v.y) : (part ? v.y : v.x);
+        // rows with Re a: (Re b | Im b); rows with Im a: (-Im b | Re b), the sign applied below
+        x[e] = wim ? (part ? v.x : v.y) : (part ? v.y : v.x);
       }
+      const bool neg = wim && !part;
       uint32_t pk[kSlices][4];
 #pragma unroll
       for (int t = 0; t < kSlices; ++t) pk[t][0] = pk[t][1] = pk[t][2] = pk[t][3] = 0;
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
         uint32_t sl[kSlices];
-        slice8(x[e], fb, sl);
+        slice8(x[e], fb, sl, neg);
 #pragma unroll
         for (int t = 0; t < kSlices; ++t) pk[t][e >> 1] |= sl[t] << (16 * (e & 1));
       }
@@ -427,9 +429,10 @@ __global__ void __launch_bounds__(kThreads, 1) zgemm_tc_kernel(const ZgemmLaunch
             p.y = scale2(val[2 * cc + 1], E);
           }
           const double2 o = old4[cc];
-          C[er + (long long)col * jb.ldc] = a.mode == ZGEMM_SET ? p
-                                            : (a.mode == ZGEMM_SUB ? make_double2(o.x - p.x, o.y - p.y)
-                                                                   : make_double2(o.x + p.x, o.y + p.y));
+          double2* cp = C + er + (long long)col * jb.ldc;
+          if (a.mode == ZGEMM_SET) *cp = p;  // the mode is uniform over the launch
+          else if (a.mode == ZGEMM_SUB) *cp = make_double2(o.x - p.x, o.y - p.y);
+          else *cp = make_double2(o.x + p.x, o.y + p.y);
         }
       }
     }
