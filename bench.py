@@ -157,10 +157,19 @@ def fp64_peak_tflops(sm_mhz):
     return sms * 4.0 * mhz * 1e6 / 1e12, sms, mhz
 
 
-# DRAM bytes per launch of the dominant kernel class, from one ncu capture each (dram__bytes_read.sum
-# + dram__bytes_write.sum); keyed by kernel class, with the capture it came from.  A class whose
-# kernels changed after the capture has no entry (traffic is then reported as null).
-NCU_TRAFFIC = {}
+# DRAM bytes of a kernel class on the star16k workload, from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum over every launch of the class in the second step of `bench.py --profile`,
+# cold cache per launch, so upper bounds); per class call ("launch" of the library's class timing)
+# and per step.  A class whose kernels change after the capture must lose its entry (its traffic is
+# then reported as null).
+NCU_TRAFFIC = {
+    "getrf": {"bytes_per_launch": 1411.4e6 / 15, "bytes_per_step": 1411.4e6,
+              "capture": "profiles/star16k_launch_list.md (DRAM table)"},
+    "getrs": {"bytes_per_launch": 934.5e6 / 22, "bytes_per_step": 934.5e6,
+              "capture": "profiles/star16k_launch_list.md (DRAM table)"},
+    "id": {"bytes_per_launch": 79.6e6 / 8, "bytes_per_step": 79.6e6,
+           "capture": "profiles/star16k_launch_list.md (DRAM table)"},
+}
 
 
 class _Timer:
@@ -324,11 +333,29 @@ def _roofline(acc, steps, names, sm_mhz, K_SKETCH):
                 "frac": achieved / pk,
                 "peak_source": f"derived FP64: {sms} SMs x 4 flop/clk x {mhz:.0f} MHz (median sampled SM clock)"}
     roof["traffic"] = tr["bytes_per_launch"] if tr else None
+    if tr:
+        roof["traffic_source"] = tr["capture"]
     roof["timing"] = ("serialised steps (compress then factor on one stream): CUDA events around every launch "
                       "of the class on the stream it runs on")
     roof["avg_launch_ms"] = ms_launch
     roof["work_per_launch"] = work_launch
     return roof
+
+
+def _hbm(acc, steps, names):
+    """Achieved HBM bandwidth of the column ID (c) and the block LU and solves (d): DRAM bytes per step
+    from the ncu capture in NCU_TRAFFIC over the class's serialised device time per step."""
+    peak = _measured_peaks().get("hbm_gbs")
+    out = {}
+    for cls in ("id", "getrf", "getrs"):
+        k = names.index(cls)
+        tr = NCU_TRAFFIC.get(cls)
+        if not tr or acc["ms"][k] <= 0:
+            continue
+        gbs = tr["bytes_per_step"] / (acc["ms"][k] / steps * 1e-3) / 1e9
+        out[cls] = {"GB_per_s": gbs, "frac_of_measured_hbm": gbs / peak if peak else None,
+                    "dram_bytes_per_step": tr["bytes_per_step"]}
+    return out
 
 
 def run_ours(args):
@@ -435,7 +462,9 @@ def run_ours(args):
             "sketch": {"redone_ids": int(st.sketch_redo)},
             "ranks": {"max_flux": st.max_rank[0], "max_trace": st.max_rank[1], "root_size": st.root_size,
                       "leaf_mean": [st.level_mean_rank[st.depth][0], st.level_mean_rank[st.depth][1]]},
-            "roofline": _roofline(ser["acc"], ser["steps"], names, clocks.get("sm_mhz"), S.K_SKETCH),
+            "roofline": _roofline(ser["acc"], ser["steps"], names, clocks.get("sm_mhz"), S.K_SKETCH)
+            if args.workload == "star16k" else None,
+            "hbm": _hbm(ser["acc"], ser["steps"], names) if args.workload == "star16k" else None,
             "e2e": {"value": e2e_sec / world, "unit": "s", "h2d_bytes_per_step": 6 * 8 * n_total,
                     "d2h_bytes_per_step": 16 * 2 * n_total},
             "gpu_launches": int(r["launches"]),

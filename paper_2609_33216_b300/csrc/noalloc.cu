@@ -13,7 +13,9 @@
 // device it asks the runtime for the array's device address (with that device
 // current) and caches it; later calls on the same device reuse the cached
 // address.  Because that first call talks to the runtime, it should be made
-// before any stream capture begins.  All calls share the one array, and each
+// before any stream capture begins.  The cached address belongs to the device's
+// current context: a cudaDeviceReset while the library is in use would leave it
+// stale, so devices the library has used must not be reset.  All calls share the one array, and each
 // call leaves its job descriptors and status word behind: the status word is
 // cleared at the start of every call, and calls whose work overlaps on the GPU
 // (different streams or host threads without ordering between them) race on the
