@@ -624,6 +624,11 @@ def run_profile(args):
     w = _workload(args.workload)
     s = Solver(w["curve"], w["k0"], w["k1"], w["eps0"], w["eps1"], mode="sym", curve_on_device=True,
                leaf=w["leaf"], nproxy=w["nproxy"], tol=w["tol"])
+    from paper_2609_33216_b300 import symhss as S
+    if args.lu_tc is not None:
+        S.symhss_set_tuning(s.h, lu_tc=args.lu_tc)
+    if args.panel_cluster is not None:
+        S.symhss_set_tuning(s.h, lu_panel_cluster=args.panel_cluster)
     for _ in range(2):
         s.compress()
         s.factor()
@@ -735,6 +740,10 @@ def main():
                          "the 64-scatterer batch and the 262144-node star with the proposer")
     ap.add_argument("--extra-steps", type=int, default=3)
     ap.add_argument("--profile", action="store_true", help="one warm-up + one symmetric step only")
+    ap.add_argument("--lu-tc", type=int, default=None, choices=[0, 1, 2],
+                    help="with --profile: factorisation path (1: tensor-core updates, 0: FP64 pipe, 2: by launch size)")
+    ap.add_argument("--panel-cluster", type=int, default=None, choices=[1, 2, 4, 8, 16],
+                    help="with --profile: largest thread-block cluster of an LU panel")
     ap.add_argument("--proposer", action="store_true", help="train the learned rank proposer and attach it")
     ap.add_argument("--comparators", type=int, default=1, help="also time the symmetric PMCHWT comparator")
     ap.add_argument("--autotune", type=int, default=1, help="run the library's launch autotuner before timing")

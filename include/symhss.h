@@ -284,10 +284,12 @@ typedef struct {
   int tile_loop_chunk;    /* 0: adaptive (8..32 by launch size); else 8, 16 or 32 loop points per block */
   int id_cluster_max;     /* 1, 2, 4, 8 or 16: largest thread-block cluster of one column ID      */
   int lu_panel_cluster;   /* 1, 2, 4, 8 or 16: largest cluster factoring one LU panel (1: one block) */
-  int lu_tc;              /* 1 (default): FP64 block LUs blocked by 64 columns and multi-RHS solves
-                           * blocked by 64 rows, their updates on the tensor cores (symhss_zgemm);
-                           * 0: 16-column LU and unblocked solves on the FP64 pipe.  Both give the
-                           * factorisation to FP64 rounding, not the same bits. */
+  int lu_tc;              /* 1: FP64 block LUs blocked by 64 columns and multi-RHS solves blocked
+                           * by 64 rows, their updates on the tensor cores (symhss_zgemm);
+                           * 0: 16-column LU and unblocked solves on the FP64 pipe; 2 (default):
+                           * the first for launches of at least 32 blocks (the lower tree levels),
+                           * the second above.  All give the factorisation to FP64 rounding, not
+                           * the same bits. */
   int reserved[2];
 } symhss_tuning;
 

@@ -134,6 +134,16 @@ __device__ __forceinline__ void warp_argmax_key(long long& k, int& i) {
     if (ok > k || (ok == k && oi < i)) { k = ok; i = oi; }
   }
 }
+// the same, carrying a payload x with the winning (k, i); every lane ends with the result
+__device__ __forceinline__ void warp_argmax_key(long long& k, int& i, int& x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long ok = __shfl_xor_sync(0xffffffffu, k, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, i, o);
+    const int ox = __shfl_xor_sync(0xffffffffu, x, o);
+    if (ok > k || (ok == k && oi < i)) { k = ok; i = oi; x = ox; }
+  }
+}
 
 // process-wide count of kernels this library has launched (diagnostics)
 void count_launches(long long n);
@@ -374,7 +384,8 @@ struct LuLaunch {
   int lookahead = 1;       // depth-1 look-ahead on a side stream
   int panel_threads = 1024;  // largest panel block
   int panel_cluster = 1;     // largest cluster for the panels of few large matrices (1: one block)
-  int tc = 1;                // FP64: trailing updates of 64-column blocks on the tensor cores
+  int tc = 2;                // FP64: 64-column blocks with tensor-core updates (1: always, 2: for
+                             // launches of at least 32 matrices, 0: never)
 };
 cudaError_t launch_getrf(const LuLaunch& a, cudaStream_t s);
 
@@ -393,7 +404,8 @@ struct RsLaunch {
   int max_rhs;
   int max_n;
   int* status = nullptr;  // device status word; needed (with tc) by the tensor-core path
-  int tc = 1;             // FP64, > 4 right-hand sides, n > 64: blocked solve with tensor-core updates
+  int tc = 2;             // FP64, > 4 right-hand sides, n > 64: blocked solve with tensor-core updates
+                          // (1: always, 2: for launches of at least 32 matrices, 0: never)
 };
 cudaError_t launch_getrs(const RsLaunch& a, cudaStream_t s);
 

@@ -302,7 +302,8 @@ cudaError_t getrs_impl(const RsLaunch& a, cudaStream_t s) {
   cudaError_t e;
   // FP64 with many right-hand sides and blocks larger than one diagonal block: blocked solve
   // whose off-diagonal updates run on the tensor cores
-  if (sizeof(CT) == sizeof(double2) && a.tc && a.status && a.max_rhs > 4 && max_n > kBlk)
+  const bool use_tc = a.tc == 1 || (a.tc == 2 && a.njobs >= 32);  // as the block LU's lu_tc rule
+  if (sizeof(CT) == sizeof(double2) && use_tc && a.status && a.max_rhs > 4 && max_n > kBlk)
     return getrs_blocked_tc(a, s);
   if (a.max_rhs <= 4) {
     const size_t smem = (size_t)max_n * (2 * sizeof(CT) + sizeof(int));

@@ -25,6 +25,7 @@ namespace {
 
 constexpr int kNb = 16;          // panel width
 constexpr int kOuter = 64;       // column block of the tensor-core trailing update (FP64)
+constexpr int kTcMinJobs = 32;   // lu_tc = 2: the tensor-core path for launches of this many matrices
 constexpr int kPanelThreads = 256;
 constexpr int kPanelWarps = kPanelThreads / 32;
 constexpr int kTs = 32;          // trailing-update tile
@@ -195,24 +196,32 @@ __global__ void __launch_bounds__(THREADS) panel_smem_kernel(const LuLaunch a, i
 
 // Panel factorisation by a thread-block cluster of C blocks (one cluster per matrix), for
 // the few large matrices of the top levels whose panel would otherwise run on one SM.
-// Panel row i (rows [j, n) numbered from 0) lives in block i % C at local index i / C,
-// in shared memory.  Column step c: every block proposes its largest |re| + |im| key among
-// its rows >= c; after a cluster barrier every block reads all proposals through distributed
-// shared memory and takes the largest (ties to the lowest row: the pivots of the one-block
-// kernel); every block copies the pivot row and the old row c (the thread holding the
-// pivot's column forms its reciprocal), a second cluster barrier ends those reads, the
-// owners write the swapped rows, and every block updates its own rows below c (fusing the
-// next column's proposal).  The arithmetic of every row is the one-block kernel's, so the
-// factors are identical.
+// Panel row i (rows [j, n) numbered from 0) lives in block i % C at local index i / C, in
+// shared memory, and never moves: the interchanges are kept as a permutation (pos2phys /
+// phys2pos, the same in every block) and applied when the panel is written back.  Column
+// step c: every block publishes its candidate -- the largest |re| + |im| key among its rows
+// not yet pivoted, ties to the lowest current position (the one-block kernel's pivots) --
+// together with that row's w entries; after ONE cluster barrier every block reads the C keys
+// through distributed shared memory, takes the largest, copies the winner's row from the
+// winner's candidate slot, updates the permutation, and updates its own unpivoted rows
+// (fusing the next column's candidate).  A pivot row is no longer written once chosen, and a
+// candidate slot is double-buffered, so no second barrier is needed.  The arithmetic of every
+// row is the one-block kernel's, so the factors are identical.
+struct CandRow {
+  long long k;
+  int pos, phys;
+  double2 row[kNb];
+};
+
 __global__ void __launch_bounds__(kClusterPanelThreads) panel_cluster_kernel(const LuLaunch a, int j, int lmax) {
-  extern __shared__ __align__(16) double2 P[];  // P[q * lmax + li]
+  extern __shared__ __align__(16) double2 P[];  // P[q * lmax + li]; then pos2phys, phys2pos
   constexpr int kWarps = kClusterPanelThreads / 32;
   __shared__ long long redk[kWarps];
-  __shared__ int redi[kWarps];
-  __shared__ CandK cand[2];
-  __shared__ CandK pick;
-  __shared__ double2 prow[kNb], rowc[kNb];
-  __shared__ double2 s_inv;
+  __shared__ int redi[kWarps], redr[kWarps];
+  __shared__ CandRow cand[2];
+  __shared__ long long s_k;
+  __shared__ int s_pos, s_blk;
+  __shared__ double2 prow[kNb];
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
@@ -221,10 +230,12 @@ __global__ void __launch_bounds__(kClusterPanelThreads) panel_cluster_kernel(con
   if (j >= n) return;  // uniform over the cluster (one matrix per cluster)
   const int w = min(kNb, n - j), rows = n - j;
   const int lrows = rank < rows ? (rows - rank + C - 1) / C : 0;
-  if ((rows + C - 1) / C > lmax) {  // uniform over the cluster (block 0's row count)
+  if ((rows + C - 1) / C > lmax || rows > a.max_n) {  // uniform over the cluster
     if (threadIdx.x == 0 && rank == 0) atomicOr(a.status, ST_BAD_INDEX);
     return;
   }
+  int* pos2phys = reinterpret_cast<int*>(P + (size_t)kNb * lmax);
+  int* phys2pos = pos2phys + a.max_n;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   double2* A = a.base + jb.a_off;
   int* piv = a.piv + jb.piv_off;
@@ -232,68 +243,74 @@ __global__ void __launch_bounds__(kClusterPanelThreads) panel_cluster_kernel(con
     const int li = e % lrows, q = e / lrows;
     P[q * lmax + li] = A[j + rank + li * C + (long long)(j + q) * ld];
   }
+  for (int i = tid; i < rows; i += kClusterPanelThreads) { pos2phys[i] = i; phys2pos[i] = i; }
   __syncthreads();
+  // candidate for column 0: (key, current position, physical row)
   long long bk = -1;
-  int bi = rows;
+  int bi = rows, br = -1;
   for (int li = tid; li < lrows; li += kClusterPanelThreads) {
+    const int r = rank + li * C;
     const long long k = pivot_key(cabs1(P[li]));
-    const int i = rank + li * C;
-    if (k > bk || (k == bk && i < bi)) { bk = k; bi = i; }
+    if (k > bk || (k == bk && r < bi)) { bk = k; bi = r; br = r; }
   }
   int par = 0;
   for (int c = 0; c < w; ++c) {
-    warp_argmax_key(bk, bi);
-    if (lane == 0) { redk[warp] = bk; redi[warp] = bi; }
+    // block's best (ties: lowest position), then publish it with its row
+    warp_argmax_key(bk, bi, br);
+    if (lane == 0) { redk[warp] = bk; redi[warp] = bi; redr[warp] = br; }
     __syncthreads();
     if (warp == 0) {
       bk = lane < kWarps ? redk[lane] : -1;
       bi = lane < kWarps ? redi[lane] : rows;
-      warp_argmax_key(bk, bi);
-      if (lane == 0) cand[par] = CandK{bk, bi};
+      br = lane < kWarps ? redr[lane] : -1;
+      warp_argmax_key(bk, bi, br);
+      if (lane == 0) { cand[par].k = bk; cand[par].pos = bi; cand[par].phys = br; }
+      const int li = br >= 0 ? (br - rank) / C : 0;
+      if (lane < w) cand[par].row[lane] = br >= 0 ? P[lane * lmax + li] : make_double2(0.0, 0.0);
     }
     cl.sync();
-    // the C proposals are read in parallel (one lane each) and reduced with shuffles
+    // the C proposals (one lane each), reduced with shuffles; then the winner's row
     if (warp == 0) {
       long long ck = -1;
-      int ci = rows;
+      int cp = rows, cb = -1;
       if (lane < C) {
-        const CandK cd = *cl.map_shared_rank(&cand[par], lane);
-        ck = cd.k;
-        ci = cd.i;
+        const CandRow* cd = cl.map_shared_rank(&cand[par], lane);
+        ck = cd->k;
+        cp = cd->pos;
+        cb = lane;
       }
-      warp_argmax_key(ck, ci);
-      if (lane == 0) pick = CandK{ck, ci};
+      warp_argmax_key(ck, cp, cb);
+      if (lane == 0) { s_k = ck; s_pos = cp; s_blk = cb; }
+      __syncwarp();
+      const int wb = __shfl_sync(0xffffffffu, cb, 0);
+      if (lane < w && wb >= 0) prow[lane] = cl.map_shared_rank(&cand[par], wb)->row[lane];
     }
     __syncthreads();
-    const bool zero = pick.k <= 0 || pick.i >= rows;
-    const int p = zero ? c : pick.i;
+    const bool zero = s_k <= 0 || s_pos >= rows;
+    const int p = zero ? c : s_pos;  // current position of the pivot row
     par ^= 1;
-    if (tid < w) {
-      const double2 pv = cl.map_shared_rank(P, p % C)[tid * lmax + p / C];
-      prow[tid] = pv;
-      rowc[tid] = cl.map_shared_rank(P, c % C)[tid * lmax + c / C];
-      if (tid == c) s_inv = zero ? make_double2(0.0, 0.0) : cinv_pivot(pv);
-    }
-    if (tid == 0 && rank == 0) {
-      piv[j + c] = j + p;
-      if (zero) {
-        if (a.info[jb.info_idx] == 0) a.info[jb.info_idx] = j + c + 1;
-        atomicOr(a.status, ST_SINGULAR);
+    if (tid == 0) {  // the interchange of positions c and p, in every block
+      const int rc = pos2phys[c], rp = pos2phys[p];
+      pos2phys[c] = rp; pos2phys[p] = rc;
+      phys2pos[rp] = c; phys2pos[rc] = p;
+      if (rank == 0) {
+        piv[j + c] = j + p;
+        if (zero) {
+          if (a.info[jb.info_idx] == 0) a.info[jb.info_idx] = j + c + 1;
+          atomicOr(a.status, ST_SINGULAR);
+        }
       }
     }
-    cl.sync();  // every block has read rows p and c
-    if (!zero && p != c && tid < w) {
-      if (c % C == rank) P[tid * lmax + c / C] = prow[tid];
-      if (p % C == rank) P[tid * lmax + p / C] = rowc[tid];
-    }
     __syncthreads();
-    const double2 inv = s_inv;
+    const double2 inv = zero ? make_double2(0.0, 0.0) : cinv_pivot(prow[c]);
     bk = -1;
     bi = rows;
-    // local rows strictly below c
+    br = -1;
+    // own rows not yet pivoted (current position > c)
     for (int li = tid; li < lrows; li += kClusterPanelThreads) {
-      const int i = rank + li * C;
-      if (i <= c) continue;
+      const int r = rank + li * C;
+      const int pos = phys2pos[r];
+      if (pos <= c) continue;
       if (!zero) {
         const double2 l = cmul(P[c * lmax + li], inv);
         P[c * lmax + li] = l;
@@ -301,14 +318,16 @@ __global__ void __launch_bounds__(kClusterPanelThreads) panel_cluster_kernel(con
       }
       if (c + 1 < w) {
         const long long k = pivot_key(cabs1(P[(c + 1) * lmax + li]));
-        if (k > bk || (k == bk && i < bi)) { bk = k; bi = i; }
+        if (k > bk || (k == bk && pos < bi)) { bk = k; bi = pos; br = r; }
       }
     }
     __syncthreads();
   }
+  cl.sync();  // no block reads another's candidate slots after this point
   for (int e = tid; e < lrows * w; e += kClusterPanelThreads) {
     const int li = e % lrows, q = e / lrows;
-    A[j + rank + li * C + (long long)(j + q) * ld] = P[q * lmax + li];
+    const int r = rank + li * C;
+    A[j + phys2pos[r] + (long long)(j + q) * ld] = P[q * lmax + li];
   }
 }
 
@@ -522,7 +541,7 @@ cudaError_t getrf_impl(const LuLaunch& a, cudaStream_t s) {
   const int lmax = (a.max_n + pc - 1) / pc;
   if (pc > 1) {
     e = cudaFuncSetAttribute(panel_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)((size_t)lmax * kNb * sizeof(double2)));
+                             (int)((size_t)lmax * kNb * sizeof(double2) + 2 * (size_t)a.max_n * sizeof(int)));
     if (e == cudaSuccess && pc > 8)
       e = cudaFuncSetAttribute(panel_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) {
@@ -535,7 +554,7 @@ cudaError_t getrf_impl(const LuLaunch& a, cudaStream_t s) {
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(a.njobs * pc, 1, 1);
       cfg.blockDim = dim3(kClusterPanelThreads, 1, 1);
-      cfg.dynamicSmemBytes = (size_t)lmax * kNb * sizeof(double2);
+      cfg.dynamicSmemBytes = (size_t)lmax * kNb * sizeof(double2) + 2 * (size_t)a.max_n * sizeof(int);
       cfg.stream = st;
       cudaLaunchAttribute attr[1];
       attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -561,7 +580,11 @@ cudaError_t getrf_impl(const LuLaunch& a, cudaStream_t s) {
     return cudaGetLastError();
   };
   if ((e = panel(0, s)) != cudaSuccess) return e;
-  if (sizeof(CT) == sizeof(double2) && a.tc && a.max_n > kOuter + kNb) {
+  // lu_tc = 1: always; 2: launches of at least kTcMinJobs matrices (the lower tree levels, whose
+  // many blocks fill the tensor-core product; at the top levels its per-launch latency and the
+  // extra launches cost more than the FP64 updates they replace)
+  const bool use_tc = a.tc == 1 || (a.tc == 2 && a.njobs >= kTcMinJobs);
+  if (sizeof(CT) == sizeof(double2) && use_tc && a.max_n > kOuter + kNb) {
     // FP64: blocked by 64 columns (the order of a blocked right-looking LU).  Inside a block
     // the 16-column panels run as above with their interchanges applied to every column, but
     // their U-row solves and FP64 updates cover only the block's own columns.  At the block's

@@ -197,7 +197,7 @@ struct symhss_s {
   symhss_stats_t st{};
   cudaError_t last_cuda = cudaSuccess;
   std::vector<int> mark;                          // host scratch (size npts)
-  symhss_tuning tune = {0, 256, 0, 16, 1, 1, {0, 0}};  // launch tuning (symhss_set_tuning)
+  symhss_tuning tune = {0, 256, 0, 16, 1, 2, {0, 0}};  // launch tuning (symhss_set_tuning)
   symhss_mlp_s* mlp = nullptr;                    // attached proposer (not owned)
   double prop_margin = 1.15;
   symhss::DevBuf featjobs, feats, mlpout, chkjobs, chkratio;
@@ -2329,7 +2329,7 @@ static bool tuning_ok(const symhss_tuning* t) {
   };
   return in(t->lu_lookahead, {0, 1}) && in(t->lu_panel_threads, {256, 512, 1024}) &&
          in(t->tile_loop_chunk, {0, 8, 16, 32}) && in(t->id_cluster_max, {1, 2, 4, 8, 16}) &&
-         in(t->lu_panel_cluster, {1, 2, 4, 8, 16}) && in(t->lu_tc, {0, 1});
+         in(t->lu_panel_cluster, {1, 2, 4, 8, 16}) && in(t->lu_tc, {0, 1, 2});
 }
 
 int symhss_get_tuning(symhss_t h, symhss_tuning* out) {
@@ -2380,7 +2380,7 @@ int symhss_autotune(symhss_t h, int reps, symhss_tuning* out, void* stream) {
   if (rc) return rc;
   // the factorisation's arithmetic path: block LU and solve classes together
   bms = 1e300;
-  for (int v : {1, 0}) {
+  for (int v : {2, 1, 0}) {
     h->tune = best;
     h->tune.lu_tc = v;
     double m = 1e300;
