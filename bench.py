@@ -629,6 +629,8 @@ def run_profile(args):
         S.symhss_set_tuning(s.h, lu_tc=args.lu_tc)
     if args.panel_cluster is not None:
         S.symhss_set_tuning(s.h, lu_panel_cluster=args.panel_cluster)
+    if args.lookahead is not None:
+        S.symhss_set_tuning(s.h, lu_lookahead=args.lookahead)
     for _ in range(2):
         s.compress()
         s.factor()
@@ -744,6 +746,8 @@ def main():
                     help="with --profile: factorisation path (1: tensor-core updates, 0: FP64 pipe, 2: by launch size)")
     ap.add_argument("--panel-cluster", type=int, default=None, choices=[1, 2, 4, 8, 16],
                     help="with --profile: largest thread-block cluster of an LU panel")
+    ap.add_argument("--lookahead", type=int, default=None, choices=[0, 1],
+                    help="with --profile: depth-1 look-ahead of the FP64-pipe LU (panel on a side stream)")
     ap.add_argument("--proposer", action="store_true", help="train the learned rank proposer and attach it")
     ap.add_argument("--comparators", type=int, default=1, help="also time the symmetric PMCHWT comparator")
     ap.add_argument("--autotune", type=int, default=1, help="run the library's launch autotuner before timing")

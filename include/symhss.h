@@ -283,13 +283,15 @@ typedef struct {
   int lu_panel_threads;   /* 256, 512 or 1024: largest thread block of the LU panel kernel      */
   int tile_loop_chunk;    /* 0: adaptive (8..32 by launch size); else 8, 16 or 32 loop points per block */
   int id_cluster_max;     /* 1, 2, 4, 8 or 16: largest thread-block cluster of one column ID      */
-  int lu_panel_cluster;   /* 1, 2, 4, 8 or 16: largest cluster factoring one LU panel (1: one block) */
+  int lu_panel_cluster;   /* 1, 2, 4, 8 or 16 (default 16): largest thread-block cluster factoring
+                           * one LU panel, used while blocks x cluster <= the SM count and every
+                           * member keeps >= 32 panel rows (the top tree levels); 1: one block */
   int lu_tc;              /* 1: FP64 block LUs blocked by 64 columns and multi-RHS solves blocked
                            * by 64 rows, their updates on the tensor cores (symhss_zgemm);
                            * 0: 16-column LU and unblocked solves on the FP64 pipe; 2 (default):
-                           * the first for launches of at least 32 blocks (the lower tree levels),
-                           * the second above.  All give the factorisation to FP64 rounding, not
-                           * the same bits. */
+                           * the first for launches of at least 32 blocks (the lower tree levels;
+                           * solves also when blocks x right-hand sides >= 512), the second above.
+                           * All give the factorisation to FP64 rounding, not the same bits. */
   int reserved[2];
 } symhss_tuning;
 
@@ -298,7 +300,8 @@ int symhss_get_tuning(symhss_t h, symhss_tuning* out);
 int symhss_set_tuning(symhss_t h, const symhss_tuning* t);
 /* Autotuner: time the handle's own compress / factor with each value of each tunable
  * (coordinate search: tile_loop_chunk and id_cluster_max on compress, then lu_tc (block LU +
- * solve time), lu_panel_threads x lu_lookahead and lu_panel_cluster on factor), `reps` runs
+ * solve time), lu_panel_threads x lu_lookahead, then lu_panel_cluster x lu_lookahead on
+ * factor), `reps` runs
  * per value, the minimum device time of the affected kernel classes deciding; leaves the best
  * tuning set (and in *out, if not NULL) and the handle compressed and factorised.
  * Synchronises `stream`. */

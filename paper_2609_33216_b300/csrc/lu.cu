@@ -302,7 +302,9 @@ cudaError_t getrs_impl(const RsLaunch& a, cudaStream_t s) {
   cudaError_t e;
   // FP64 with many right-hand sides and blocks larger than one diagonal block: blocked solve
   // whose off-diagonal updates run on the tensor cores
-  const bool use_tc = a.tc == 1 || (a.tc == 2 && a.njobs >= 32);  // as the block LU's lu_tc rule
+  // lu_tc = 2: the blocked tensor-core solve for many blocks or many right-hand sides in total
+  // (its block updates then fill the product's tiles), the unblocked FP64 solve otherwise
+  const bool use_tc = a.tc == 1 || (a.tc == 2 && (a.njobs >= 32 || (long long)a.njobs * a.max_rhs >= 512));
   if (sizeof(CT) == sizeof(double2) && use_tc && a.status && a.max_rhs > 4 && max_n > kBlk)
     return getrs_blocked_tc(a, s);
   if (a.max_rhs <= 4) {

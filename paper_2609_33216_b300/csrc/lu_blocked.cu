@@ -29,7 +29,7 @@ constexpr int kTcMinJobs = 32;   // lu_tc = 2: the tensor-core path for launches
 constexpr int kPanelThreads = 256;
 constexpr int kPanelWarps = kPanelThreads / 32;
 constexpr int kTs = 32;          // trailing-update tile
-constexpr int kClusterPanelThreads = 128;
+constexpr int kClusterPanelThreads = 256;
 
 struct CandK { long long k; int i; };
 
@@ -219,9 +219,9 @@ __global__ void __launch_bounds__(kClusterPanelThreads) panel_cluster_kernel(con
   __shared__ long long redk[kWarps];
   __shared__ int redi[kWarps], redr[kWarps];
   __shared__ CandRow cand[2];
-  __shared__ long long s_k;
-  __shared__ int s_pos, s_blk;
+  __shared__ int s_pos, s_zero;
   __shared__ double2 prow[kNb];
+  __shared__ double2 s_inv;
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
@@ -269,7 +269,9 @@ __global__ void __launch_bounds__(kClusterPanelThreads) panel_cluster_kernel(con
       if (lane < w) cand[par].row[lane] = br >= 0 ? P[lane * lmax + li] : make_double2(0.0, 0.0);
     }
     cl.sync();
-    // the C proposals (one lane each), reduced with shuffles; then the winner's row
+    // warp 0: the C proposals (one lane each), reduced with shuffles; the winner's row; the
+    // pivot's reciprocal (one lane: FP64 issues slowly on this GPU); the interchange of
+    // positions c and p in the permutation
     if (warp == 0) {
       long long ck = -1;
       int cp = rows, cb = -1;
@@ -280,48 +282,59 @@ __global__ void __launch_bounds__(kClusterPanelThreads) panel_cluster_kernel(con
         cb = lane;
       }
       warp_argmax_key(ck, cp, cb);
-      if (lane == 0) { s_k = ck; s_pos = cp; s_blk = cb; }
-      __syncwarp();
-      const int wb = __shfl_sync(0xffffffffu, cb, 0);
-      if (lane < w && wb >= 0) prow[lane] = cl.map_shared_rank(&cand[par], wb)->row[lane];
-    }
-    __syncthreads();
-    const bool zero = s_k <= 0 || s_pos >= rows;
-    const int p = zero ? c : s_pos;  // current position of the pivot row
-    par ^= 1;
-    if (tid == 0) {  // the interchange of positions c and p, in every block
-      const int rc = pos2phys[c], rp = pos2phys[p];
-      pos2phys[c] = rp; pos2phys[p] = rc;
-      phys2pos[rp] = c; phys2pos[rc] = p;
-      if (rank == 0) {
-        piv[j + c] = j + p;
-        if (zero) {
-          if (a.info[jb.info_idx] == 0) a.info[jb.info_idx] = j + c + 1;
-          atomicOr(a.status, ST_SINGULAR);
+      const bool zero = ck <= 0 || cp >= rows || cb < 0;
+      const int p = zero ? c : cp;  // current position of the pivot row
+      if (lane < w) {
+        const double2 v = zero ? make_double2(0.0, 0.0) : cl.map_shared_rank(&cand[par], cb)->row[lane];
+        prow[lane] = v;
+        if (lane == c) s_inv = zero ? make_double2(0.0, 0.0) : cinv_pivot(v);
+      }
+      if (lane == 0) {
+        s_zero = zero;
+        s_pos = p;
+        const int rc = pos2phys[c], rp = pos2phys[p];
+        pos2phys[c] = rp; pos2phys[p] = rc;
+        phys2pos[rp] = c; phys2pos[rc] = p;
+        if (rank == 0) {
+          piv[j + c] = j + p;
+          if (zero) {
+            if (a.info[jb.info_idx] == 0) a.info[jb.info_idx] = j + c + 1;
+            atomicOr(a.status, ST_SINGULAR);
+          }
         }
       }
     }
+    par ^= 1;
     __syncthreads();
-    const double2 inv = zero ? make_double2(0.0, 0.0) : cinv_pivot(prow[c]);
+    const bool zero = s_zero;
+    // the multipliers of the own rows not yet pivoted (current position > c)
+    if (!zero) {
+      const double2 inv = s_inv;
+      for (int li = tid; li < lrows; li += kClusterPanelThreads)
+        if (phys2pos[rank + li * C] > c) P[c * lmax + li] = cmul(P[c * lmax + li], inv);
+    }
+    __syncthreads();
+    // rank-1 update, one element per thread (all lanes busy), fused with the next column's
+    // candidate; the arithmetic of each element is the one-block kernel's
     bk = -1;
     bi = rows;
     br = -1;
-    // own rows not yet pivoted (current position > c)
-    for (int li = tid; li < lrows; li += kClusterPanelThreads) {
+    const int nq = w - c - 1;
+    for (int e = tid; e < lrows * nq; e += kClusterPanelThreads) {
+      const int li = e % lrows, q = c + 1 + e / lrows;
       const int r = rank + li * C;
       const int pos = phys2pos[r];
       if (pos <= c) continue;
+      double2 v = P[q * lmax + li];
       if (!zero) {
-        const double2 l = cmul(P[c * lmax + li], inv);
-        P[c * lmax + li] = l;
-        for (int q = c + 1; q < w; ++q) P[q * lmax + li] = cfms(l, prow[q], P[q * lmax + li]);
+        v = cfms(P[c * lmax + li], prow[q], v);
+        P[q * lmax + li] = v;
       }
-      if (c + 1 < w) {
-        const long long k = pivot_key(cabs1(P[(c + 1) * lmax + li]));
+      if (q == c + 1) {
+        const long long k = pivot_key(cabs1(v));
         if (k > bk || (k == bk && pos < bi)) { bk = k; bi = pos; br = r; }
       }
     }
-    __syncthreads();
   }
   cl.sync();  // no block reads another's candidate slots after this point
   for (int e = tid; e < lrows * w; e += kClusterPanelThreads) {
@@ -537,7 +550,9 @@ cudaError_t getrf_impl(const LuLaunch& a, cudaStream_t s) {
   // cluster panels for few large matrices: C blocks per matrix while the batch still leaves
   // SMs free and every block keeps at least 32 panel rows
   int pc = 1;
-  while (sizeof(CT) == sizeof(double2) && pc < 16 && 2 * pc <= a.panel_cluster && a.njobs * 2 * pc <= device_sm_count() && a.max_n / (2 * pc) >= 32) pc *= 2;
+  while (sizeof(CT) == sizeof(double2) && pc < 16 && 2 * pc <= a.panel_cluster &&
+         a.njobs * 2 * pc <= device_sm_count() && a.max_n / (2 * pc) >= 32)
+    pc *= 2;
   const int lmax = (a.max_n + pc - 1) / pc;
   if (pc > 1) {
     e = cudaFuncSetAttribute(panel_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

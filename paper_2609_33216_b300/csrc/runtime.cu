@@ -197,7 +197,7 @@ struct symhss_s {
   symhss_stats_t st{};
   cudaError_t last_cuda = cudaSuccess;
   std::vector<int> mark;                          // host scratch (size npts)
-  symhss_tuning tune = {0, 256, 0, 16, 1, 2, {0, 0}};  // launch tuning (symhss_set_tuning)
+  symhss_tuning tune = {0, 256, 0, 16, 16, 2, {0, 0}};  // launch tuning (symhss_set_tuning)
   symhss_mlp_s* mlp = nullptr;                    // attached proposer (not owned)
   double prop_margin = 1.15;
   symhss::DevBuf featjobs, feats, mlpout, chkjobs, chkratio;
@@ -2407,19 +2407,23 @@ int symhss_autotune(symhss_t h, int reps, symhss_tuning* out, void* stream) {
       }
       if (m < bms) { bms = m; best.lu_panel_threads = pt; best.lu_lookahead = la; }
     }
+  // panel cluster and look-ahead together: a cluster panel is short enough to hide behind the
+  // trailing update on the side stream, a one-block panel is not
   bms = 1e300;
-  for (int pcv : {1, 2, 4, 8, 16}) {
-    h->tune = best;
-    h->tune.lu_panel_cluster = pcv;
-    double m = 1e300;
-    for (int r = 0; r < reps; ++r) {
-      const double before = h->st.kernel_ms[SYMHSS_K_GETRF];
-      rc = symhss_factor(h, stream);
-      if (rc) return rc;
-      m = std::min(m, h->st.kernel_ms[SYMHSS_K_GETRF] - before);
+  for (int pcv : {1, 2, 4, 8, 16})
+    for (int la : {0, 1}) {
+      h->tune = best;
+      h->tune.lu_panel_cluster = pcv;
+      h->tune.lu_lookahead = la;
+      double m = 1e300;
+      for (int r = 0; r < reps; ++r) {
+        const double before = h->st.kernel_ms[SYMHSS_K_GETRF];
+        rc = symhss_factor(h, stream);
+        if (rc) return rc;
+        m = std::min(m, h->st.kernel_ms[SYMHSS_K_GETRF] - before);
+      }
+      if (m < bms) { bms = m; best.lu_panel_cluster = pcv; best.lu_lookahead = la; }
     }
-    if (m < bms) { bms = m; best.lu_panel_cluster = pcv; }
-  }
   h->tune = best;
   rc = symhss_factor(h, stream);
   if (rc) return rc;
