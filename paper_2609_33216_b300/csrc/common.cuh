@@ -386,6 +386,8 @@ struct LuLaunch {
   int panel_cluster = 1;     // largest cluster for the panels of few large matrices (1: one block)
   int tc = 2;                // FP64: 64-column blocks with tensor-core updates (1: always, 2: for
                              // launches of at least 32 matrices, 0: never)
+  unsigned char* zimg = nullptr;  // tensor-core product scratch, zgemm_lu_img_bytes(njobs, max_n)
+  long long zimg_bytes = 0;       // bytes (too few: the FP64-pipe path)
 };
 cudaError_t launch_getrf(const LuLaunch& a, cudaStream_t s);
 
@@ -406,8 +408,13 @@ struct RsLaunch {
   int* status = nullptr;  // device status word; needed (with tc) by the tensor-core path
   int tc = 2;             // FP64, > 4 right-hand sides, n > 64: blocked solve with tensor-core updates
                           // (1: always, 2: for launches of at least 32 matrices, 0: never)
+  unsigned char* zimg = nullptr;  // tensor-core product scratch, zgemm_rs_img_bytes(njobs, max_n, max_rhs)
+  long long zimg_bytes = 0;       // bytes (too few: the unblocked FP64 solve)
 };
 cudaError_t launch_getrs(const RsLaunch& a, cudaStream_t s);
+// scratch of the tensor-core products of a blocked LU / blocked solve launch
+long long zgemm_lu_img_bytes(int njobs, int max_n);
+long long zgemm_rs_img_bytes(int njobs, int max_n, int max_rhs);
 
 // ---- complex FP64 GEMM on the tensor cores (zgemm_tc.cu) ---------------------------
 
@@ -439,7 +446,10 @@ struct ZgemmLaunch {
   const LuJob* lu_jobs = nullptr;
   const RsJob* rs_jobs = nullptr;
   int block_j = 0;     // J of the derived jobs
-  int mtiles = 0, ntiles_c = 0;  // tiles per derived job
+  int mtiles = 0, ntiles_c = 0;  // row / column blocks per job (explicit jobs: the largest)
+  int njobs = 0;                   // jobs of the launch
+  unsigned char* img = nullptr;    // scratch for the slice images (16-byte aligned),
+  long long img_bytes = 0;         // at least zgemm_img_bytes(njobs, mtiles, ntiles_c)
   int probe_timeout = 0;           // set by launch_zgemm_tc (test hook, see set_zgemm_timeout_probe)
 };
 cudaError_t launch_zgemm_tc(const ZgemmLaunch& a, cudaStream_t s);
@@ -450,6 +460,9 @@ void set_zgemm_timeout_probe(int on);
 int zgemm_tc_tile_rows();
 int zgemm_tc_tile_cols();
 int zgemm_tc_max_k();
+// scratch bytes of a launch of njobs jobs with mtiles x ntiles blocks each (or of m x n jobs)
+long long zgemm_img_bytes(int njobs, int mtiles, int ntiles);
+long long zgemm_img_bytes_for(int njobs, int max_m, int max_n);
 
 
 // ---- factor / solve helpers ------------------------------------------------------

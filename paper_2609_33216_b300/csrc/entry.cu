@@ -166,6 +166,13 @@ int symhss_zgemm(const void* A, int lda, long long strideA, const void* B, int l
   a.ntiles = (int)tiles.size();
   a.status = reinterpret_cast<int*>(d + o_status);
   a.wait_ns = 0;
+  a.njobs = batch;
+  a.mtiles = mt;
+  a.ntiles_c = nt;
+  TmpBuf img;  // slice images, reused by the chunks of k one after another on the stream
+  a.img_bytes = zgemm_img_bytes(batch, mt, nt);
+  CKE(img.alloc((size_t)a.img_bytes));
+  a.img = reinterpret_cast<unsigned char*>(img.p);
   // chunks of k in order on the stream: the first sets (or updates) C, the rest accumulate
   for (int c = 0; c < nchunk; ++c) {
     a.jobs = reinterpret_cast<const ZgemmJob*>(d + o_jobs) + (size_t)c * batch;
@@ -397,6 +404,12 @@ int symhss_lu_batched(void* A, int n, int lda, long long strideA, int batch, int
   a.njobs = batch;
   a.max_n = n;
   a.status = status;
+  TmpBuf zimg;  // tensor-core product scratch of the blocked LU
+  a.zimg_bytes = zgemm_lu_img_bytes(batch, n);
+  if (a.zimg_bytes > 0) {
+    CKE(zimg.alloc((size_t)a.zimg_bytes));
+    a.zimg = reinterpret_cast<unsigned char*>(zimg.p);
+  }
   CKE(launch_getrf(a, s));
   int st = 0;
   CKE(cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -434,6 +447,12 @@ int symhss_lu_solve_batched(const void* LU, int n, int lda, long long strideA, c
   a.max_rhs = nrhs;
   a.max_n = n;
   a.status = status;
+  TmpBuf zimg;  // tensor-core product scratch of the blocked solve
+  a.zimg_bytes = zgemm_rs_img_bytes(batch, n, nrhs);
+  if (a.zimg_bytes > 0) {
+    CKE(zimg.alloc((size_t)a.zimg_bytes));
+    a.zimg = reinterpret_cast<unsigned char*>(zimg.p);
+  }
   CKE(launch_getrs(a, s));
   int st = 0;
   CKE(cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, s));

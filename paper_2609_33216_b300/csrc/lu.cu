@@ -262,6 +262,9 @@ cudaError_t getrs_blocked_tc(const RsLaunch& a, cudaStream_t s) {
   g.status = a.status;
   g.wait_ns = 0;
   g.rs_jobs = a.jobs;
+  g.njobs = a.njobs;
+  g.img = a.zimg;
+  g.img_bytes = a.zimg_bytes;
   g.ntiles_c = (a.max_rhs + zgemm_tc_tile_cols() - 1) / zgemm_tc_tile_cols();
   // forward: L y = P b, block by block; the rows below a block are updated on the tensor cores
   for (int J = 0; J < max_n; J += kBlk) {
@@ -304,7 +307,8 @@ cudaError_t getrs_impl(const RsLaunch& a, cudaStream_t s) {
   // whose off-diagonal updates run on the tensor cores
   // lu_tc = 2: the blocked tensor-core solve for many blocks or many right-hand sides in total
   // (its block updates then fill the product's tiles), the unblocked FP64 solve otherwise
-  const bool use_tc = a.tc == 1 || (a.tc == 2 && (a.njobs >= 32 || (long long)a.njobs * a.max_rhs >= 512));
+  const bool use_tc = (a.tc == 1 || (a.tc == 2 && (a.njobs >= 32 || (long long)a.njobs * a.max_rhs >= 512))) &&
+                      a.zimg && a.zimg_bytes >= zgemm_rs_img_bytes(a.njobs, a.max_n, a.max_rhs);
   if (sizeof(CT) == sizeof(double2) && use_tc && a.status && a.max_rhs > 4 && max_n > kBlk)
     return getrs_blocked_tc(a, s);
   if (a.max_rhs <= 4) {

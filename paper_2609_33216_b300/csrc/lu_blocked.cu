@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(kClusterPanelThreads) panel_cluster_kernel(con
   __shared__ long long redk[kWarps];
   __shared__ int redi[kWarps], redr[kWarps];
   __shared__ CandRow cand[2];
-  __shared__ int s_pos, s_zero;
+  __shared__ int s_zero;
   __shared__ double2 prow[kNb];
   __shared__ double2 s_inv;
   cg::cluster_group cl = cg::this_cluster();
@@ -291,7 +291,6 @@ __global__ void __launch_bounds__(kClusterPanelThreads) panel_cluster_kernel(con
       }
       if (lane == 0) {
         s_zero = zero;
-        s_pos = p;
         const int rc = pos2phys[c], rp = pos2phys[p];
         pos2phys[c] = rp; pos2phys[p] = rc;
         phys2pos[rp] = c; phys2pos[rc] = p;
@@ -598,7 +597,8 @@ cudaError_t getrf_impl(const LuLaunch& a, cudaStream_t s) {
   // lu_tc = 1: always; 2: launches of at least kTcMinJobs matrices (the lower tree levels, whose
   // many blocks fill the tensor-core product; at the top levels its per-launch latency and the
   // extra launches cost more than the FP64 updates they replace)
-  const bool use_tc = a.tc == 1 || (a.tc == 2 && a.njobs >= kTcMinJobs);
+  const bool use_tc = (a.tc == 1 || (a.tc == 2 && a.njobs >= kTcMinJobs)) && a.zimg &&
+                      a.zimg_bytes >= zgemm_lu_img_bytes(a.njobs, a.max_n);
   if (sizeof(CT) == sizeof(double2) && use_tc && a.max_n > kOuter + kNb) {
     // FP64: blocked by 64 columns (the order of a blocked right-looking LU).  Inside a block
     // the 16-column panels run as above with their interchanges applied to every column, but
@@ -644,6 +644,9 @@ cudaError_t getrf_impl(const LuLaunch& a, cudaStream_t s) {
         g.wait_ns = 0;
         g.derive = ZGEMM_LU_UPDATE;
         g.lu_jobs = a.jobs;
+        g.njobs = a.njobs;
+        g.img = a.zimg;
+        g.img_bytes = a.zimg_bytes;
         g.block_j = J;
         g.mtiles = (right + zgemm_tc_tile_rows() - 1) / zgemm_tc_tile_rows();
         g.ntiles_c = (right + zgemm_tc_tile_cols() - 1) / zgemm_tc_tile_cols();

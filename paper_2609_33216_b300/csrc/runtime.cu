@@ -160,6 +160,8 @@ struct Height {
   // solve
   DevBuf G, FT, TMP, slists;
   DevBuf chkmeta, chkg;          // exact residual checks of sketched IDs (proposer mode)
+  DevBuf chkimg;                 // their tensor-core product scratch (compression stream)
+  DevBuf zimg;                   // tensor-core product scratch of the factorisation stream
   // matvec
   DevBuf XV, XS, ZV, YS, YV, mlists;
   std::vector<int> h_rank;
@@ -875,6 +877,7 @@ int compress_height(symhss_s* h, int t, cudaStream_t s) {
     const int nchunk = (maxr + KM - 1) / KM;
     std::vector<std::vector<ZgemmJob>> zj(nchunk);
     std::vector<std::vector<ZgemmTile>> zt(nchunk);
+    int zmt = 1, znt = 1;  // the largest row / column block counts of the products
     for (size_t k = 0; k < ids.size(); ++k) {
       const GatherJob& g = gj[k];
       const int rest = g.n - g.r;
@@ -887,6 +890,8 @@ int compress_height(symhss_s* h, int t, cudaStream_t s) {
         z.m = g.m; z.n = rest; z.k = std::min(KM, g.r - c * KM);
         const int jid = (int)zj[c].size();
         zj[c].push_back(z);
+        zmt = std::max(zmt, (g.m + TM - 1) / TM);
+        znt = std::max(znt, (rest + TN - 1) / TN);
         for (int a = 0; a < (g.m + TM - 1) / TM; ++a)
           for (int b = 0; b < (rest + TN - 1) / TN; ++b) zt[c].push_back(ZgemmTile{jid, a, b});
       }
@@ -897,6 +902,9 @@ int compress_height(symhss_s* h, int t, cudaStream_t s) {
     for (int c = 0; c < nchunk; ++c) { ozj[c] = pg.add(zj[c]); ozt[c] = pg.add(zt[c]); }
     CK(pg.upload(H.chkmeta, s));
     CK(H.chkg.ensure((size_t)gtot * sizeof(double2)));
+    size_t zmax = 0;
+    for (int c = 0; c < nchunk; ++c) zmax = std::max(zmax, zj[c].size());
+    CK(H.chkimg.ensure((size_t)zgemm_img_bytes((int)zmax, zmt, znt)));
     CK(h->chkratio.ensure(ids.size() * sizeof(double)));
     const char* mb = H.chkmeta.as<char>();
     double w = 0;
@@ -914,6 +922,11 @@ int compress_height(symhss_s* h, int t, cudaStream_t s) {
       za.mode = ZGEMM_SUB;
       za.status = h->status.as<int>();
       za.wait_ns = 0;
+      za.njobs = (int)zj[c].size();
+      za.mtiles = zmt;
+      za.ntiles_c = znt;
+      za.img = H.chkimg.as<unsigned char>();
+      za.img_bytes = (long long)H.chkimg.cap;
       CK(launch_zgemm_tc(za, s));
     }
     CK(launch_residual_ratio(H.mr.as<double2>(), H.chkg.as<double2>(), reinterpret_cast<const GatherJob*>(mb + og),
@@ -1286,6 +1299,9 @@ int assemble_and_lu(symhss_s* h, int t, cudaStream_t s, long long& pairs) {
   la.panel_threads = h->tune.lu_panel_threads;
   la.panel_cluster = h->tune.lu_panel_cluster;
   la.tc = h->tune.lu_tc;
+  CK(H.zimg.ensure((size_t)zgemm_lu_img_bytes(la.njobs, max_n)));
+  la.zimg = H.zimg.as<unsigned char>();
+  la.zimg_bytes = (long long)H.zimg.cap;
   // the assembled blocks are the FP64 operator's (leaf blocks, sibling skeleton blocks)
   CK(H.Dop.ensure(d_total * sizeof(double2)));
   CK(cudaMemcpyAsync(H.Dop.p, H.D.p, d_total * sizeof(double2), cudaMemcpyDeviceToDevice, s));
@@ -1422,6 +1438,15 @@ int factor_height(symhss_s* h, int t, cudaStream_t s, long long& pairs, bool lu_
   ra.max_n = max_n;
   ra.status = h->status.as<int>();
   ra.tc = h->tune.lu_tc;
+  {
+    // one scratch for the height's tensor-core products (one stream): the largest of them
+    const int nb = (int)refs.size();
+    const long long need = std::max({zgemm_lu_img_bytes(nb, max_n), zgemm_rs_img_bytes(nb, max_n, max_k),
+                                     zgemm_lu_img_bytes(nb, max_k), zgemm_rs_img_bytes(nb, max_k, max_k)});
+    CK(H.zimg.ensure((size_t)need));
+  }
+  ra.zimg = H.zimg.as<unsigned char>();
+  ra.zimg_bytes = (long long)H.zimg.cap;
   TIMED(SYMHSS_K_GETRS, w_x, launch_getrs(ra, s));
   // R X
   BasisLaunch br = bl;
@@ -1448,6 +1473,8 @@ int factor_height(symhss_s* h, int t, cudaStream_t s, long long& pairs, bool lu_
   la.panel_threads = h->tune.lu_panel_threads;
   la.panel_cluster = h->tune.lu_panel_cluster;
   la.tc = h->tune.lu_tc;
+  la.zimg = H.zimg.as<unsigned char>();
+  la.zimg_bytes = (long long)H.zimg.cap;
   TIMED(SYMHSS_K_GETRF, w_rxlu, launch_getrf(la, s));
   if (mixed)
     TIMED(SYMHSS_K_OTHER, 0.0, launch_copy_blocks32(nullptr, H.At32.as<float2>(),
@@ -1469,6 +1496,8 @@ int factor_height(symhss_s* h, int t, cudaStream_t s, long long& pairs, bool lu_
   rb.max_n = max_k;
   rb.status = h->status.as<int>();
   rb.tc = h->tune.lu_tc;
+  rb.zimg = H.zimg.as<unsigned char>();
+  rb.zimg_bytes = (long long)H.zimg.cap;
   TIMED(SYMHSS_K_GETRS, w_at, launch_getrs(rb, s));
   if (mixed) {  // X and Atilde in FP64 for the parents' blocks and the solve phase
     TIMED(SYMHSS_K_OTHER, 0.0, launch_widen(H.X32.as<float2>(), H.X.as<double2>(), x_total, s));

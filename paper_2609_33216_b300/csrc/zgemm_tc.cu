@@ -20,17 +20,21 @@
 // recombined exactly in two int64 partial sums hi, lo (T = hi 2^28 + lo), rounded once to
 // FP64 and scaled by a power of two: a few FP64 operations per real output instead of 4k FMAs.
 //
-// Kernel.  One thread block of 256 threads computes a 128 x 32 complex tile of C.  For each
-// chunk of 16 complex columns of A (32 columns of A'), two threads per row slice the row's
-// halves of the chunk and every thread one core row of the tile's B chunk into shared memory
-// (two stages, 96 KB each, in the core-matrix order the MMA reads); one thread issues the
-// 36 slice-pair MMAs per K-step
-// (M = 128, N = 64, K = 16, bf16 x bf16 -> FP32) into the eight groups of a 512-column
-// tensor-memory accumulator and commits them to the stage's mbarrier; slicing of the next
-// chunk overlaps those MMAs.  Every wait is bounded by %globaltimer; after a timeout the block
-// waits once more (bounded) for its MMAs in flight, records ST_TIMEOUT, frees its tensor
-// memory and exits.  A test hook (set_zgemm_timeout_probe) makes the last wait target a
-// phase that no commit completes, so that this path can be exercised on purpose.
+// Kernels.  A launch is two kernels.  The slicing kernel cuts every 128-row block of A' and
+// every 32-column block of B' once, in 16-column chunks of k, into the core-matrix order the MMA
+// reads (eight slices per chunk, 64 KB for A', 32 KB for B'), in a scratch buffer the caller
+// provides, together with the row and column exponents.  The product kernel then computes one
+// 128 x 32 complex tile of C per thread block of 512 threads: one thread streams the tile's
+// chunk images into two 96 KB shared-memory stages by bulk copies (cp.async.bulk, completing on
+// an mbarrier) and issues the 36 slice-pair products per K-step as 12 MMAs (M = 128, K = 16,
+// N = 64 per B slice, up to four B slices per MMA; bf16 x bf16 -> FP32) into the eight groups
+// of a 512-column tensor-memory accumulator; the copy of
+// chunk c + 1 overlaps the MMAs of chunk c.  The epilogue rounds T 2^(e_i + f_c - 2107) to FP64
+// by integer operations (one FP64 addition per real output for C -= AB and C += AB, none for
+// C = AB).  Every wait is bounded by %globaltimer; after a timeout the block waits once more
+// (bounded) for its copies and MMAs in flight, records ST_TIMEOUT, frees its tensor memory and
+// exits.  A test hook (set_zgemm_timeout_probe) makes the last wait target a phase that no
+// commit completes, so that this path can be exercised on purpose.
 #include <stdint.h>
 
 #include "common.cuh"
@@ -39,7 +43,7 @@ namespace symhss {
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kMmaThreads = 512;  // product kernel (16 warps share the epilogue)
 constexpr int kTileM = 128;       // rows of C per block
 constexpr int kTileNc = 32;       // complex columns of C per block
 constexpr int kNr = 2 * kTileNc;  // real columns of B' (MMA N)
@@ -48,7 +52,10 @@ constexpr int kGroups = 8;
 constexpr int kChunkK = 16;                        // complex k per chunk (32 columns of A')
 constexpr int kASliceBytes = kTileM * 32 * 2;      // 8192: one slice of the A' chunk
 constexpr int kBSliceBytes = kNr * 32 * 2;         // 4096: one slice of the B' chunk
-constexpr int kStageBytes = kSlices * (kASliceBytes + kBSliceBytes);  // 98304
+constexpr int kAChunkBytes = kSlices * kASliceBytes;               // 65536: A' chunk image
+constexpr int kBChunkBytes = kSlices * kBSliceBytes;               // 32768: B' chunk image
+constexpr int kStageBytes = kAChunkBytes + kBChunkBytes;           // 98304
+constexpr int kMaxChunks = 4;                                      // k <= 64
 constexpr int kTmemCols = kGroups * kNr;           // 512
 constexpr long long kWaitNs = 200ll * 1000 * 1000;
 
@@ -136,94 +143,258 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t v[8]) {
                : "r"(taddr));
 }
 
-__global__ void __launch_bounds__(kThreads, 1) zgemm_tc_kernel(const ZgemmLaunch a) {
+// T 2^E rounded once to FP64 (to nearest, ties to even), for T = hi 2^28 + lo with |hi|,
+// |lo| < 2^46, by integer operations on the bits: |T| = H 2^28 + L (0 <= L < 2^28) is cut to
+// its leading 53 bits and the exponent field set to msb + E.  A result outside the normal
+// range (never for the products of this solver) is formed by FP64 operations instead.
+__device__ __forceinline__ double recombine(long long hi, long long lo, int E) {
+  const long long h2 = hi + (lo >> 28);  // T = h2 2^28 + l2, 0 <= l2 < 2^28
+  const long long l2 = lo & 0xFFFFFFFll;
+  const bool neg = h2 < 0;
+  const uint64_t H = neg ? (uint64_t)(l2 ? -h2 - 1 : -h2) : (uint64_t)h2;
+  const uint64_t L = neg ? (uint64_t)(l2 ? (1ll << 28) - l2 : 0) : (uint64_t)l2;
+  if ((H | L) == 0) return 0.0;
+  int msb;
+  uint64_t q;
+  if (H != 0) {
+    const int mH = 63 - __clzll((long long)H);  // H < 2^47
+    msb = mH + 28;
+    if (msb <= 52) {
+      q = ((H << 28) | L) << (52 - msb);
+    } else {
+      const int sh = msb - 52;  // 1 .. 22 bits below the kept 53, all inside L
+      q = (H << (28 - sh)) | (L >> sh);
+      const uint64_t rem = L & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+      if (rem > half || (rem == half && (q & 1))) {
+        ++q;
+        if (q >> 53) { q >>= 1; ++msb; }
+      }
+    }
+  } else {
+    msb = 63 - __clzll((long long)L);
+    q = L << (52 - msb);
+  }
+  const int be = msb + E + 1023;
+  if (be <= 0 || be >= 2047) return scale2(fma((double)hi, 268435456.0, (double)lo), E);
+  return __longlong_as_double((long long)((neg ? 0x8000000000000000ull : 0ull) | ((uint64_t)be << 52) |
+                                          (q & 0xFFFFFFFFFFFFFull)));
+}
+
+// the job of index jidx of a launch: explicit, or derived from the factorisation's job arrays
+// (the block-J product of one matrix of the blocked LU or of the blocked triangular solves)
+__device__ __forceinline__ ZgemmJob decode_job(const ZgemmLaunch& a, int jidx) {
+  ZgemmJob jb;
+  if (a.derive == ZGEMM_JOBS) return a.jobs[jidx];
+  const int J = a.block_j;
+  if (a.derive == ZGEMM_LU_UPDATE) {
+    const LuJob lj = a.lu_jobs[jidx];
+    jb.m = lj.n - J - 64; jb.n = jb.m; jb.k = min(64, lj.n - J);
+    jb.lda = jb.ldb = jb.ldc = lj.ld;
+    jb.a_off = lj.a_off + (J + 64) + (long long)J * lj.ld;
+    jb.b_off = lj.a_off + J + (long long)(J + 64) * lj.ld;
+    jb.c_off = lj.a_off + (J + 64) + (long long)(J + 64) * lj.ld;
+  } else {
+    const RsJob rj = a.rs_jobs[jidx];
+    jb.k = min(64, rj.n - J); jb.n = rj.nrhs;
+    jb.lda = rj.lda; jb.ldb = jb.ldc = rj.ldb;
+    jb.b_off = rj.b_off + J;
+    if (a.derive == ZGEMM_RS_FWD) {
+      jb.m = rj.n - J - 64;
+      jb.a_off = rj.a_off + (J + 64) + (long long)J * rj.lda;
+      jb.c_off = rj.b_off + J + 64;
+    } else {
+      jb.m = J;
+      jb.a_off = rj.a_off + (long long)J * rj.lda;
+      jb.c_off = rj.b_off;
+    }
+  }
+  return jb;
+}
+
+// scratch layout: A' chunk images of every (job, row block), then B' chunk images of every
+// (job, column block), then the row exponents (128 per row block), then the column exponents
+// (32 per column block)
+struct ImgLayout {
+  unsigned char* a;
+  unsigned char* b;
+  int* ea;
+  int* fb;
+};
+__host__ __device__ __forceinline__ ImgLayout img_layout(unsigned char* img, int njobs, int mtiles, int ntiles) {
+  ImgLayout L;
+  L.a = img;
+  L.b = L.a + (size_t)njobs * mtiles * kMaxChunks * kAChunkBytes;
+  L.ea = reinterpret_cast<int*>(L.b + (size_t)njobs * ntiles * kMaxChunks * kBChunkBytes);
+  L.fb = L.ea + (size_t)njobs * mtiles * kTileM;
+  return L;
+}
+
+// Slicing kernel (512 threads): blocks [0, njobs mtiles) cut row blocks of A', the rest column
+// blocks of B'.  Every thread loads its share of the block once (all loads in flight together),
+// takes the exponents from registers and writes its slices.
+constexpr int kSliceThreads = 512;
+
+// the eight slices of eight values (relative to biased exponent emax) packed as bf16 pairs
+__device__ __forceinline__ void slice_pack8(const double x[8], int emax, uint32_t pk[kSlices][4]) {
+#pragma unroll
+  for (int t = 0; t < kSlices; ++t) pk[t][0] = pk[t][1] = pk[t][2] = pk[t][3] = 0;
+#pragma unroll
+  for (int e8 = 0; e8 < 8; ++e8) {
+    uint32_t sl[kSlices];
+    slice8(x[e8], emax, sl);
+#pragma unroll
+    for (int t = 0; t < kSlices; ++t) pk[t][e8 >> 1] |= sl[t] << (16 * (e8 & 1));
+  }
+}
+
+__global__ void __launch_bounds__(kSliceThreads) zslice_kernel(const ZgemmLaunch a) {
+  __shared__ int s_e[kMaxChunks][kTileM];
+  const ImgLayout L = img_layout(a.img, a.njobs, a.mtiles, a.ntiles_c);
+  const int nA = a.njobs * a.mtiles;
+  const int tid = threadIdx.x;
+  if ((int)blockIdx.x < nA) {
+    const int jidx = blockIdx.x / a.mtiles, mt = blockIdx.x - jidx * a.mtiles;
+    const ZgemmJob jb = decode_job(a, jidx);
+    const int r0 = mt * kTileM;
+    if (jb.m <= 0 || jb.n <= 0 || jb.k <= 0 || r0 >= jb.m) return;  // uniform per block
+    const int m = jb.m, K = jb.k;
+    const double2* A = a.A + jb.a_off;
+    // thread (rt, ch): row r0 + rt, the 16 values of k chunk ch
+    const int rt = tid & (kTileM - 1), ch = tid >> 7;
+    const int row = r0 + rt;
+    double2 v[kChunkK];
+    int e = 0;
+#pragma unroll
+    for (int q = 0; q < kChunkK; ++q) {
+      const int k = ch * kChunkK + q;
+      v[q] = (row < m && k < K) ? A[row + (long long)k * jb.lda] : make_double2(0.0, 0.0);
+      e = max(e, max(bexp(v[q].x), bexp(v[q].y)));
+    }
+    s_e[ch][rt] = e;
+    __syncthreads();
+    const int ea = max(max(s_e[0][rt], s_e[1][rt]), max(s_e[2][rt], s_e[3][rt]));  // the row's largest
+    const size_t blk = (size_t)jidx * a.mtiles + mt;
+    if (ch == 0) L.ea[blk * kTileM + rt] = ea;
+    if (ch * kChunkK >= K) return;  // no such chunk
+    unsigned char* img = L.a + (blk * kMaxChunks + ch) * kAChunkBytes;
+    // core rows q = 0, 1 hold Re a(row, k0 + 8q + e), q = 2, 3 hold Im of the same k
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int h = q & 1, part = q >> 1;
+      double x[8];
+#pragma unroll
+      for (int e8 = 0; e8 < 8; ++e8) x[e8] = part ? v[8 * h + e8].y : v[8 * h + e8].x;
+      uint32_t pk[kSlices][4];
+      slice_pack8(x, ea, pk);
+#pragma unroll
+      for (int t = 0; t < kSlices; ++t)
+        *reinterpret_cast<uint4*>(img + t * kASliceBytes + (rt >> 3) * 512 + q * 128 + (rt & 7) * 16) =
+            make_uint4(pk[t][0], pk[t][1], pk[t][2], pk[t][3]);
+    }
+    return;
+  }
+  const int bidx = blockIdx.x - nA;
+  const int jidx = bidx / a.ntiles_c, nt = bidx - jidx * a.ntiles_c;
+  const ZgemmJob jb = decode_job(a, jidx);
+  const int c0 = nt * kTileNc;
+  if (jb.m <= 0 || jb.n <= 0 || jb.k <= 0 || c0 >= jb.n) return;  // uniform per block
+  const int n = jb.n, K = jb.k;
+  const double2* B = a.B + jb.b_off;
+  // thread (c, ch, comp, kh): component comp (Re / Im) of b(16 ch + 8 kh .. + 7, c0 + c); the
+  // 16 threads of a column are 16 consecutive lanes
+  const int c = tid >> 4, ch = (tid >> 2) & 3, comp = (tid >> 1) & 1, kh = tid & 1;
+  const int col = c0 + c;
+  double x[8];
+  int fb = 0;
+#pragma unroll
+  for (int e8 = 0; e8 < 8; ++e8) {
+    const int k = ch * kChunkK + 8 * kh + e8;
+    const double2 v = (col < n && k < K) ? B[k + (long long)col * jb.ldb] : make_double2(0.0, 0.0);
+    x[e8] = comp ? v.y : v.x;
+    fb = max(fb, bexp(x[e8]));
+  }
+#pragma unroll
+  for (int o = 1; o < 16; o <<= 1) fb = max(fb, __shfl_xor_sync(0xffffffffu, fb, o));  // the column's largest
+  const size_t blk = (size_t)jidx * a.ntiles_c + nt;
+  if ((tid & 15) == 0) L.fb[blk * kTileNc + c] = fb;
+  if (ch * kChunkK >= K) return;  // no such chunk
+  unsigned char* img = L.b + (blk * kMaxChunks + ch) * kBChunkBytes;
+  // B' columns of complex column c: n' = 2c holds [Re b; -Im b], n' = 2c + 1 holds [Im b; Re b]
+  // (core rows q = 0, 1: the k halves paired with Re a; q = 2, 3: with Im a).  Re b goes to
+  // (2c, kh) and (2c + 1, kh + 2); Im b to (2c + 1, kh) and, sign bits flipped, (2c, kh + 2)
+  const int np1 = 2 * c + comp, q1 = kh;
+  const int np2 = 2 * c + 1 - comp, q2 = kh + 2;
+  const uint32_t flip2 = comp ? 0x80008000u : 0u;
+  uint32_t pk[kSlices][4];
+  slice_pack8(x, fb, pk);
+#pragma unroll
+  for (int t = 0; t < kSlices; ++t) {
+    unsigned char* sl = img + t * kBSliceBytes;
+    *reinterpret_cast<uint4*>(sl + (np1 >> 3) * 512 + q1 * 128 + (np1 & 7) * 16) =
+        make_uint4(pk[t][0], pk[t][1], pk[t][2], pk[t][3]);
+    // a flipped zero slice is -0: its products add nothing to the sums
+    *reinterpret_cast<uint4*>(sl + (np2 >> 3) * 512 + q2 * 128 + (np2 & 7) * 16) =
+        make_uint4(pk[t][0] ^ flip2, pk[t][1] ^ flip2, pk[t][2] ^ flip2, pk[t][3] ^ flip2);
+  }
+}
+
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               :: "r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+
+__global__ void __launch_bounds__(kMmaThreads, 1) zgemm_tc_kernel(const ZgemmLaunch a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar_mma[2];
+  __shared__ __align__(8) uint64_t bar_load[2];
   __shared__ uint32_t tmem_base_s;
   __shared__ int s_fail, s_last;
   __shared__ int s_fexp[kTileNc];
-  __shared__ int s_eh[2][kTileM];
-  ZgemmJob jb;
-  int mt, nt;
+  __shared__ int s_e[kTileM];
+  int jidx, mt, nt;
   if (a.derive == ZGEMM_JOBS) {
     const ZgemmTile tl = a.tiles[blockIdx.x];
-    jb = a.jobs[tl.job];
+    jidx = tl.job;
     mt = tl.mt;
     nt = tl.nt;
   } else {
-    // the block-J product of one factorisation job (64-column blocks of the blocked LU and
-    // of the blocked triangular solves)
     const int per = a.mtiles * a.ntiles_c;
-    const int jidx = blockIdx.x / per, rem = blockIdx.x - jidx * per;
+    jidx = blockIdx.x / per;
+    const int rem = blockIdx.x - jidx * per;
     mt = rem / a.ntiles_c;
     nt = rem - mt * a.ntiles_c;
-    const int J = a.block_j;
-    if (a.derive == ZGEMM_LU_UPDATE) {
-      const LuJob lj = a.lu_jobs[jidx];
-      jb.m = lj.n - J - 64; jb.n = jb.m; jb.k = min(64, lj.n - J);
-      jb.lda = jb.ldb = jb.ldc = lj.ld;
-      jb.a_off = lj.a_off + (J + 64) + (long long)J * lj.ld;
-      jb.b_off = lj.a_off + J + (long long)(J + 64) * lj.ld;
-      jb.c_off = lj.a_off + (J + 64) + (long long)(J + 64) * lj.ld;
-    } else {
-      const RsJob rj = a.rs_jobs[jidx];
-      jb.k = min(64, rj.n - J); jb.n = rj.nrhs;
-      jb.lda = rj.lda; jb.ldb = jb.ldc = rj.ldb;
-      jb.b_off = rj.b_off + J;
-      if (a.derive == ZGEMM_RS_FWD) {
-        jb.m = rj.n - J - 64;
-        jb.a_off = rj.a_off + (J + 64) + (long long)J * rj.lda;
-        jb.c_off = rj.b_off + J + 64;
-      } else {
-        jb.m = J;
-        jb.a_off = rj.a_off + (long long)J * rj.lda;
-        jb.c_off = rj.b_off;
-      }
-    }
   }
+  const ZgemmJob jb = decode_job(a, jidx);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int r0 = mt * kTileM, c0 = nt * kTileNc;
-  // idle tile of a derived job (smaller than the launch's largest): leave before any barrier
-  if (jb.m <= 0 || jb.n <= 0 || jb.k <= 0 || r0 >= jb.m || c0 >= jb.n) return;
+  // idle tile (a derived job smaller than the launch's largest, or a tile outside the
+  // image blocks): leave before any barrier
+  if (jb.m <= 0 || jb.n <= 0 || jb.k <= 0 || r0 >= jb.m || c0 >= jb.n || mt >= a.mtiles || nt >= a.ntiles_c ||
+      jidx >= a.njobs)
+    return;
   const int m = jb.m, n = jb.n, K = jb.k;
-  const double2* A = a.A + jb.a_off;
-  const double2* B = a.B + jb.b_off;
   double2* C = a.C + jb.c_off;
-  // slicing roles: thread (rt, half) slices row r0 + rt of A, k-half `half` of every chunk
-  const int rt = tid & (kTileM - 1), half = tid >> 7;
-  const int row = r0 + rt;
-
-  // exponents: rows of A (two threads per row, halves of k), columns of B (8 threads each);
-  // the loads of a thread are independent and unrolled so that many are in flight
-  {
-    int e = 0;
-    if (row < m) {
-#pragma unroll 8
-      for (int k = half; k < K; k += 2) {
-        const double2 v = A[row + (long long)k * jb.lda];
-        e = max(e, max(bexp(v.x), bexp(v.y)));
-      }
-    }
-    s_eh[half][rt] = e;
-    const int c = tid >> 3, q = tid & 7;
-    int fb = 0;
-    if (c0 + c < n) {
-#pragma unroll 8
-      for (int k = q; k < K; k += 8) {
-        const double2 v = B[k + (long long)(c0 + c) * jb.ldb];
-        fb = max(fb, max(bexp(v.x), bexp(v.y)));
-      }
-    }
-    fb = max(fb, __shfl_xor_sync(0xffffffffu, fb, 1));
-    fb = max(fb, __shfl_xor_sync(0xffffffffu, fb, 2));
-    fb = max(fb, __shfl_xor_sync(0xffffffffu, fb, 4));
-    if (q == 0) s_fexp[c] = fb;
+  const ImgLayout L = img_layout(a.img, a.njobs, a.mtiles, a.ntiles_c);
+  const size_t ablk = (size_t)jidx * a.mtiles + mt, bblk = (size_t)jidx * a.ntiles_c + nt;
+  const unsigned char* gA = L.a + ablk * kMaxChunks * kAChunkBytes;
+  const unsigned char* gB = L.b + bblk * kMaxChunks * kBChunkBytes;
+  if (tid < kTileM) s_e[tid] = L.ea[ablk * kTileM + tid];
+  if (tid < kTileNc) s_fexp[tid] = L.fb[bblk * kTileNc + tid];
+  if (a.mode != ZGEMM_SET && warp == 1) {
+    // the old values of the tile's columns into L2 while the MMAs run (one column per lane)
+    const int col = c0 + lane, rows = min(kTileM, m - r0);
+    if (col < n && rows > 0)
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;"
+                   :: "l"(C + r0 + (long long)col * jb.ldc), "r"((uint32_t)(rows * sizeof(double2))) : "memory");
   }
   if (tid == 0) {
     s_fail = 0;
     s_last = -1;
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&bar_mma[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&bar_mma[1])));
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&bar_mma[i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&bar_load[i])));
+    }
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   if (warp == 0) {
@@ -235,110 +406,70 @@ __global__ void __launch_bounds__(kThreads, 1) zgemm_tc_kernel(const ZgemmLaunch
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base_s;
-  const int ea = max(s_eh[0][rt], s_eh[1][rt]);  // this row's largest biased exponent
-  const uint32_t idesc = make_idesc(kTileM, kNr);
   const int nch = (K + kChunkK - 1) / kChunkK;
 
-  for (int ch = 0; ch < nch; ++ch) {
-    const int st = ch & 1;
-    unsigned char* sA = smem + st * kStageBytes;
-    unsigned char* sB = sA + kSlices * kASliceBytes;
-    if (ch >= 2) {  // the MMAs of chunk ch - 2 read this stage: wait for them
-      if (tid == 0 && !mbar_wait(smem_u32(&bar_mma[st]), (uint32_t)(((ch - 2) >> 1) & 1), a.wait_ns)) s_fail = 1;
-      __syncthreads();
-      if (s_fail) break;
+  if (tid == 0) {
+    // one thread streams the chunk images and issues the MMAs: chunk c lives in stage c % 2;
+    // the copy of chunk c + 1 (c >= 1) is issued once the MMAs of chunk c - 1 have released
+    // its stage, so that it overlaps the MMAs of chunk c
+    const uint32_t sbase = smem_u32(smem);
+    int issued = 0, waited = 0, fail = 0;
+    auto issue = [&](int ch) {
+      const int st = ch & 1;
+      const uint32_t bar = smem_u32(&bar_load[st]);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(kStageBytes) : "memory");
+      bulk_load(sbase + st * kStageBytes, gA + (size_t)ch * kAChunkBytes, kAChunkBytes, bar);
+      bulk_load(sbase + st * kStageBytes + kAChunkBytes, gB + (size_t)ch * kBChunkBytes, kBChunkBytes, bar);
+      issued = ch + 1;
+    };
+    issue(0);
+    if (nch > 1) issue(1);
+    for (int ch = 0; ch < nch; ++ch) {
+      const int st = ch & 1;
+      if (!mbar_wait(smem_u32(&bar_load[st]), (uint32_t)((ch >> 1) & 1), a.wait_ns)) { fail = 1; break; }
+      waited = ch + 1;
       asm volatile("tcgen05.fence::after_thread_sync;");
-    }
-    const int k0 = ch * kChunkK;
-    // A' chunk: core rows q = 0, 1 hold Re a(row, k0 + 8q + e), q = 2, 3 hold Im of the same
-    // k; thread (rt, half) writes the rows q = half and q = half + 2 of its row
-    {
-      const int h = half;
-      double re[8], im[8];
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int k = k0 + 8 * h + e;
-        double2 v = make_double2(0.0, 0.0);
-        if (row < m && k < K) v = A[row + (long long)k * jb.lda];
-        re[e] = v.x;
-        im[e] = v.y;
-      }
-#pragma unroll
-      for (int part = 0; part < 2; ++part) {
-        uint32_t pk[kSlices][4];
-#pragma unroll
-        for (int t = 0; t < kSlices; ++t) pk[t][0] = pk[t][1] = pk[t][2] = pk[t][3] = 0;
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          uint32_t sl[kSlices];
-          slice8(part ? im[e] : re[e], ea, sl);
-#pragma unroll
-          for (int t = 0; t < kSlices; ++t) pk[t][e >> 1] |= sl[t] << (16 * (e & 1));
-        }
-        const int q = h + 2 * part;
-#pragma unroll
-        for (int t = 0; t < kSlices; ++t)
-          *reinterpret_cast<uint4*>(sA + t * kASliceBytes + (rt >> 3) * 512 + q * 128 + (rt & 7) * 16) =
-              make_uint4(pk[t][0], pk[t][1], pk[t][2], pk[t][3]);
-      }
-    }
-    // B' chunk: thread -> real column n' = tid / 4 (complex column c = n' / 2, part = n' % 2)
-    // and core row q = tid % 4 (k half kh = q % 2; q < 2: rows paired with Re a, else Im a)
-    {
-      const int np = tid >> 2, q = tid & 3;
-      const int c = np >> 1, part = np & 1, kh = q & 1, wim = q >> 1;
-      const int col = c0 + c;
-      const int fb = s_fexp[c];
-      double x[8];
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int k = k0 + 8 * kh + e;
-        double2 v = make_double2(0.0, 0.0);
-        if (col < n && k < K) v = B[k + (long long)col * jb.ldb];
-        // rows with Re a: (Re b | Im b); rows with Im a: (-Im b | Re b), the sign applied below
-        x[e] = wim ? (part ? v.x : v.y) : (part ? v.y : v.x);
-      }
-      const bool neg = wim && !part;
-      uint32_t pk[kSlices][4];
-#pragma unroll
-      for (int t = 0; t < kSlices; ++t) pk[t][0] = pk[t][1] = pk[t][2] = pk[t][3] = 0;
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        uint32_t sl[kSlices];
-        slice8(x[e], fb, sl, neg);
-#pragma unroll
-        for (int t = 0; t < kSlices; ++t) pk[t][e >> 1] |= sl[t] << (16 * (e & 1));
-      }
-#pragma unroll
-      for (int t = 0; t < kSlices; ++t)
-        *reinterpret_cast<uint4*>(sB + t * kBSliceBytes + (np >> 3) * 512 + q * 128 + (np & 7) * 16) =
-            make_uint4(pk[t][0], pk[t][1], pk[t][2], pk[t][3]);
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t sA = sbase + st * kStageBytes, sB = sA + kAChunkBytes;
       // descriptors differ only in their address field (address / 16 < 2^14 in shared memory)
-      const uint64_t ad0 = make_desc(smem_u32(sA), 128, 512), bd0 = make_desc(smem_u32(sB), 128, 512);
+      const uint64_t ad0 = make_desc(sA, 128, 512), bd0 = make_desc(sB, 128, 512);
 #pragma unroll
       for (int kk = 0; kk < 2; ++kk) {
+        // A slice i times B slices j0 .. j0 + nb - 1 in one MMA of N = 64 nb: the B slices lie
+        // next to each other along N (same 512-byte stride between 8-row groups), and so do the
+        // accumulator groups i + j0 .. i + j0 + nb - 1 in tensor memory; slice pairs with
+        // i + j >= 8 are never formed
 #pragma unroll
-        for (int s = 0; s < kGroups; ++s) {
+        for (int i = 0; i < kSlices; ++i) {
 #pragma unroll
-          for (int i = 0; i <= s; ++i) {
+          for (int j0 = 0; j0 < kSlices - i; j0 += 4) {
+            const int nb = (kSlices - i - j0) < 4 ? (kSlices - i - j0) : 4;
             const uint64_t ad = ad0 + (uint64_t)((i * kASliceBytes + kk * 256) >> 4);
-            const uint64_t bd = bd0 + (uint64_t)(((s - i) * kBSliceBytes + kk * 256) >> 4);
-            const uint32_t acc = (ch > 0 || kk > 0 || i > 0) ? 1u : 0u;
+            const uint64_t bd = bd0 + (uint64_t)((j0 * kBSliceBytes + kk * 256) >> 4);
+            const uint32_t acc = (ch > 0 || kk > 0 || i > 0) ? 1u : 0u;  // i = 0 opens every group
             asm volatile(
                 "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                :: "r"(tmem + (uint32_t)(s * kNr)), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                :: "r"(tmem + (uint32_t)((i + j0) * kNr)), "l"(ad), "l"(bd), "r"(make_idesc(kTileM, kNr * nb)),
+                   "r"(acc));
           }
         }
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                    :: "r"(smem_u32(&bar_mma[st])) : "memory");
       s_last = ch;
+      if (ch >= 1 && ch + 1 < nch) {
+        // stage (ch + 1) % 2 held chunk ch - 1: wait for its MMAs, then copy chunk ch + 1
+        if (!mbar_wait(smem_u32(&bar_mma[(ch - 1) & 1]), (uint32_t)(((ch - 1) >> 1) & 1), a.wait_ns)) {
+          fail = 1;
+          break;
+        }
+        issue(ch + 1);
+      }
+    }
+    if (fail) {
+      // drain: every copy still in flight (bounded), before the stages are given up
+      for (int c = waited; c < issued; ++c) mbar_wait(smem_u32(&bar_load[c & 1]), (uint32_t)((c >> 1) & 1), kWaitNs);
+      s_fail = 1;
     }
   }
   __syncthreads();
@@ -357,20 +488,20 @@ __global__ void __launch_bounds__(kThreads, 1) zgemm_tc_kernel(const ZgemmLaunch
       s_fail = 1;
       mbar_wait(bar, par, kWaitNs);  // drain
     }
-    if (s_fail) atomicOr(a.status, ST_TIMEOUT);
   }
+  if (tid == 0 && s_fail) atomicOr(a.status, ST_TIMEOUT);
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
 
   if (!s_fail) {
     // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows r0 + 32 (w % 4) + lane) and
-    // the complex columns 16 (w / 4) .. + 15 of the tile
+    // the complex columns 8 (w / 4) .. + 7 of the tile
     const int er = r0 + 32 * (warp & 3) + lane;
-    const int eea = max(s_eh[0][er - r0], s_eh[1][er - r0]);
+    const int eea = s_e[er - r0];
     const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
 #pragma unroll 1
-    for (int cq = 0; cq < 4; ++cq) {
-      const int cb = 4 * (warp >> 2) + cq;  // 4 complex (8 real) columns
+    for (int cq = 0; cq < 2; ++cq) {
+      const int cb = 2 * (warp >> 2) + cq;  // 4 complex (8 real) columns
       if (c0 + cb * 4 >= n) break;           // uniform per warp
       // the old values first, so that their loads overlap the tensor-memory reads
       double2 old4[4];
@@ -402,37 +533,27 @@ __global__ void __launch_bounds__(kThreads, 1) zgemm_tc_kernel(const ZgemmLaunch
 #pragma unroll
           for (int q = 0; q < 8; ++q) gi[s][q] = __float2int_rn(__uint_as_float(v[s][q]));
       }
-      double val[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const long long hi = ((((long long)gi[0][q] * 128 + gi[1][q]) * 128 + gi[2][q]) * 128) + gi[3][q];
-        const long long lo = ((((long long)gi[4][q] * 128 + gi[5][q]) * 128 + gi[6][q]) * 128) + gi[7][q];
-        // T = hi 2^28 + lo (|hi|, |lo| < 2^45.01): exact in int64 and rounded once when
-        // |hi| < 2^34, else two exact conversions joined by one rounded fma
-        val[q] = (hi > -(1ll << 34) && hi < (1ll << 34)) ? (double)(hi * (1ll << 28) + lo)
-                                                          : fma((double)hi, 268435456.0, (double)lo);
-      }
       if (er < m) {
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) {
           const int c = cb * 4 + cc, col = c0 + c;
           if (col >= n) continue;
           const int fb = s_fexp[c];
-          // times 2^(e_i + f_c - 2107): an integer addition to the exponent field while the
-          // result stays normal, else a multiplication
+          // times 2^(e_i + f_c - 2107), folded into the rounding
           const int E = eea + fb - 2107;
-          double2 p;
-          if (eea == 0 || fb == 0) {
-            p = make_double2(0.0, 0.0);
-          } else {
-            p.x = scale2(val[2 * cc], E);
-            p.y = scale2(val[2 * cc + 1], E);
+          double pr[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int q = 2 * cc + h;
+            const long long hi = ((((long long)gi[0][q] * 128 + gi[1][q]) * 128 + gi[2][q]) * 128) + gi[3][q];
+            const long long lo = ((((long long)gi[4][q] * 128 + gi[5][q]) * 128 + gi[6][q]) * 128) + gi[7][q];
+            pr[h] = (eea == 0 || fb == 0) ? 0.0 : recombine(hi, lo, E);
           }
           const double2 o = old4[cc];
           double2* cp = C + er + (long long)col * jb.ldc;
-          if (a.mode == ZGEMM_SET) *cp = p;  // the mode is uniform over the launch
-          else if (a.mode == ZGEMM_SUB) *cp = make_double2(o.x - p.x, o.y - p.y);
-          else *cp = make_double2(o.x + p.x, o.y + p.y);
+          if (a.mode == ZGEMM_SET) *cp = make_double2(pr[0], pr[1]);  // the mode is uniform over the launch
+          else if (a.mode == ZGEMM_SUB) *cp = make_double2(o.x - pr[0], o.y - pr[1]);
+          else *cp = make_double2(o.x + pr[0], o.y + pr[1]);
         }
       }
     }
@@ -452,17 +573,38 @@ void set_zgemm_timeout_probe(int on) { g_zgemm_probe = on ? 1 : 0; }
 
 int zgemm_tc_tile_rows() { return kTileM; }
 int zgemm_tc_tile_cols() { return kTileNc; }
-int zgemm_tc_max_k() { return 4 * kChunkK; }
+int zgemm_tc_max_k() { return kMaxChunks * kChunkK; }
+
+long long zgemm_img_bytes(int njobs, int mtiles, int ntiles) {
+  if (njobs <= 0 || mtiles <= 0 || ntiles <= 0) return 0;
+  return (long long)njobs * ((long long)mtiles * (kMaxChunks * (long long)kAChunkBytes + kTileM * 4) +
+                             (long long)ntiles * (kMaxChunks * (long long)kBChunkBytes + kTileNc * 4));
+}
+
+long long zgemm_img_bytes_for(int njobs, int max_m, int max_n) {
+  if (max_m <= 0 || max_n <= 0) return 0;
+  return zgemm_img_bytes(njobs, (max_m + kTileM - 1) / kTileM, (max_n + kTileNc - 1) / kTileNc);
+}
+
+long long zgemm_lu_img_bytes(int njobs, int max_n) { return zgemm_img_bytes_for(njobs, max_n - 64, max_n - 64); }
+long long zgemm_rs_img_bytes(int njobs, int max_n, int max_rhs) { return zgemm_img_bytes_for(njobs, max_n, max_rhs); }
 
 cudaError_t launch_zgemm_tc(const ZgemmLaunch& a_in, cudaStream_t s) {
   if (a_in.ntiles <= 0) return cudaSuccess;
   ZgemmLaunch a = a_in;
+  if (a.njobs <= 0 || a.mtiles <= 0 || a.ntiles_c <= 0 || !a.img ||
+      a.img_bytes < zgemm_img_bytes(a.njobs, a.mtiles, a.ntiles_c) || (reinterpret_cast<uintptr_t>(a.img) & 15))
+    return cudaErrorInvalidValue;
   a.wait_ns = g_zgemm_wait_ns;
   a.probe_timeout = g_zgemm_probe;
-  const int smem = 2 * kStageBytes;
-  cudaError_t e = cudaFuncSetAttribute(zgemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  zslice_kernel<<<a.njobs * (a.mtiles + a.ntiles_c), kSliceThreads, 0, s>>>(a);
+  symhss::count_launches(1);
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  zgemm_tc_kernel<<<a.ntiles, kThreads, smem, s>>>(a);
+  const int smem = 2 * kStageBytes;
+  e = cudaFuncSetAttribute(zgemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  zgemm_tc_kernel<<<a.ntiles, kMmaThreads, smem, s>>>(a);
   symhss::count_launches(1);
   return cudaGetLastError();
 }
