@@ -388,6 +388,8 @@ struct LuLaunch {
                              // launches of at least 32 matrices, 0: never)
   unsigned char* zimg = nullptr;  // tensor-core product scratch, zgemm_lu_img_bytes(njobs, max_n)
   long long zimg_bytes = 0;       // bytes (too few: the FP64-pipe path)
+  int* perm = nullptr;            // optional: the row permutation of every matrix (at piv_off),
+                                  // kept current by the interchange kernel (x = P b: x[i] = b[perm[i]])
 };
 cudaError_t launch_getrf(const LuLaunch& a, cudaStream_t s);
 
@@ -410,6 +412,8 @@ struct RsLaunch {
                           // (1: always, 2: for launches of at least 32 matrices, 0: never)
   unsigned char* zimg = nullptr;  // tensor-core product scratch, zgemm_rs_img_bytes(njobs, max_n, max_rhs)
   long long zimg_bytes = 0;       // bytes (too few: the unblocked FP64 solve)
+  const int* perm = nullptr;      // optional: the LU's row permutations (LuLaunch::perm); else
+                                  // every solve composes them from piv
 };
 cudaError_t launch_getrs(const RsLaunch& a, cudaStream_t s);
 // scratch of the tensor-core products of a blocked LU / blocked solve launch

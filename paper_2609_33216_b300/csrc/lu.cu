@@ -10,7 +10,11 @@
 // blocked by 64 rows -- an FP64 solve with each diagonal block (one warp per right-hand
 // side) and the update of the other rows, X[rows] -= (block column of L or U) X[block], on
 // the tensor cores (zgemm_tc.cu).
+#include <cooperative_groups.h>
+
 #include "common.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace symhss {
 
@@ -37,6 +41,102 @@ __device__ __forceinline__ void build_perm(int* perm, const int* piv, int n) {
   }
 }
 
+// the solve's row permutation into shared memory: copied from the one the LU kept, else
+// composed from piv by thread 0; the caller synchronises the block before using it
+__device__ __forceinline__ void load_perm(int* perm, const RsLaunch& a, const RsJob& jb, int n) {
+  if (a.perm) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) perm[i] = a.perm[jb.piv_off + i];
+  } else {
+    build_perm(perm, a.piv + jb.piv_off, n);
+  }
+}
+
+// ---- 32-row diagonal blocks solved through the inverses of their 8 x 8 diagonal sub-blocks
+// (the serial chain of a 32-step substitution becomes four short matrix-vector steps)
+
+// Column j of the inverse of sub-block s (rows and columns 8 s .. 8 s + 7) of a 32 x 32 diagonal
+// block (column-major `tri`, w valid rows): unit lower part (LOWER) or upper part with the
+// diagonal reciprocals dinv (indexed by block row); written to inv[s * 64 + j * 8 + i].
+template <bool LOWER>
+__device__ __forceinline__ void inv8_column(const double2* tri, const double2* dinv, double2* inv, int w, int s,
+                                            int j) {
+  const int o = 8 * s;
+  double2 y[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) y[i] = make_double2(0.0, 0.0);
+  if (o + j < w) {
+    if (LOWER) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        if (i == j) y[i] = make_double2(1.0, 0.0);
+        if (i > j && o + i < w) {
+          double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+          for (int k = 0; k < i; ++k)
+            if (k >= j) acc = cfms(tri[(o + k) * 32 + o + i], y[k], acc);
+          y[i] = acc;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int i = 7; i >= 0; --i) {
+        if (i == j) y[i] = dinv[o + i];
+        if (i < j) {
+          double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+          for (int k = 1; k < 8; ++k)
+            if (k > i && k <= j) acc = cfms(tri[(o + k) * 32 + o + i], y[k], acc);
+          y[i] = cmul(acc, dinv[o + i]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) inv[s * 64 + j * 8 + i] = y[i];
+}
+
+// sum of v over the 8 lanes of each aligned group of 8 (every lane of the warp takes part)
+__device__ __forceinline__ double2 sum8(double2 v) {
+#pragma unroll
+  for (int o = 1; o < 8; o <<= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+
+// xb[0 .. w) <- T^{-1} xb for the 32 x 32 diagonal block T (unit lower: LOWER; else upper), by
+// all threads of the block (at least 256): per 8-row sub-block (top-down for L, bottom-up for
+// U), y = inv_s x_s, then the rows of the sub-blocks still to come are updated with y.
+template <bool LOWER>
+__device__ __forceinline__ void block_solve32(double2* xb, const double2* tri, const double2* inv, int w) {
+  const int tid = threadIdx.x;
+#pragma unroll 1
+  for (int ss = 0; ss < 4; ++ss) {
+    const int s = LOWER ? ss : 3 - ss;
+    const int o = 8 * s;
+    if (o >= w) continue;  // uniform
+    double2 p = make_double2(0.0, 0.0);
+    if (tid < 64) {
+      const int i = tid >> 3, k = tid & 7;
+      if ((LOWER ? k <= i : k >= i) && o + k < w && o + i < w) p = cmul(inv[s * 64 + k * 8 + i], xb[o + k]);
+    }
+    const double2 y = sum8(p);
+    __syncthreads();  // every read of the sub-block's x before its new values
+    if (tid < 64 && (tid & 7) == 0 && o + (tid >> 3) < w) xb[o + (tid >> 3)] = y;
+    __syncthreads();
+    const int rlo = LOWER ? o + 8 : 0, rhi = LOWER ? w : o;
+    if (rhi > rlo) {  // uniform
+      const int r = rlo + (tid >> 3), k = tid & 7;
+      double2 q = make_double2(0.0, 0.0);
+      if (r < rhi && o + k < w) q = cmul(tri[(o + k) * 32 + r], xb[o + k]);
+      const double2 u = sum8(q);
+      if (r < rhi && k == 0) xb[r] = make_double2(xb[r].x - u.x, xb[r].y - u.y);
+    }
+    __syncthreads();
+  }
+}
+
 template <typename CT>
 __global__ void getrs_kernel(const RsLaunch a, int warps) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -47,10 +147,9 @@ __global__ void getrs_kernel(const RsLaunch a, int warps) {
   CT* cols = dinv + a.max_n;
   int* perm = reinterpret_cast<int*>(cols + (size_t)warps * a.max_n);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int* piv = a.piv + jb.piv_off;
   const CT* A = rs_a<CT>(a) + jb.a_off;
   const int lda = jb.lda;
-  build_perm(perm, piv, n);
+  load_perm(perm, a, jb, n);
   for (int i = threadIdx.x; i < n; i += blockDim.x) dinv[i] = cinv(A[i + (long long)i * lda]);
   __syncthreads();
   const int c = blockIdx.y * warps + warp;
@@ -114,7 +213,7 @@ __global__ void __launch_bounds__(kCtaThreads) getrs_cta_kernel(const RsLaunch a
   const CT* A = rs_a<CT>(a) + jb.a_off;
   const int lda = jb.lda;
   CT* b = rs_b<CT>(a) + jb.b_off + (long long)c * jb.ldb;
-  build_perm(perm, a.piv + jb.piv_off, n);
+  load_perm(perm, a, jb, n);
   // the reciprocals of U's diagonal, all at once: the serial 32-row solves below then
   // carry only multiplications on their dependency chain
   for (int i = tid; i < n; i += kCtaThreads) dinv[i] = cinv(A[i + (long long)i * lda]);
@@ -166,6 +265,155 @@ __global__ void __launch_bounds__(kCtaThreads) getrs_cta_kernel(const RsLaunch a
   for (int i = tid; i < n; i += kCtaThreads) b[i] = x[i];
 }
 
+// Few right-hand sides and few large blocks (the top tree levels of the solve phase): one
+// thread-block cluster of C blocks per (matrix, right-hand side), so that the FP64 updates of a
+// block's rows spread over C SMs.  The 32-row blocks of the matrix belong to the cluster's
+// members in turn (block b to member b % C), which preload their diagonal 32 x 32 blocks
+// (unit L below the diagonal, U on and above it) and the inverses of their 8 x 8 diagonal
+// sub-blocks.  Forward: the owner of block b solves its triangle with all its threads
+// (block_solve32), one cluster barrier publishes the 32 values, and
+// every member reads them through distributed shared memory and updates its own rows below;
+// backward likewise with U, from the last block.  The arithmetic of every row is that of the
+// one-block kernel up to the order of the partial sums.
+constexpr int kClThreads = 256;
+
+__global__ void __launch_bounds__(kClThreads) getrs_cluster_kernel(const RsLaunch a, int nbown) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double2 xk[32];
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+  const int grp = blockIdx.x / C;
+  const int jidx = grp / a.max_rhs, c = grp - jidx * a.max_rhs;
+  const RsJob jb = a.jobs[jidx];
+  const int n = jb.n;
+  const int nb = (n + 31) / 32;
+  // uniform over the cluster (every member has the same job and right-hand side)
+  if (n > a.max_n || n <= 0 || c >= jb.nrhs || (nb + C - 1) / C > nbown) return;
+  double2* x = reinterpret_cast<double2*>(smem_raw);          // max_n: the own rows are current
+  double2* tri = x + a.max_n;                                  // nbown x 32 x 32, column-major
+  double2* dinv = tri + (size_t)nbown * 1024;                  // nbown x 32
+  double2* inv = dinv + (size_t)nbown * 32;                    // nbown x (L, U) x 4 x 8 x 8
+  int* perm = reinterpret_cast<int*>(inv + (size_t)nbown * 512);  // max_n
+  const int tid = threadIdx.x;
+  const double2* A = a.abase + jb.a_off;
+  const int lda = jb.lda;
+  double2* b = a.bbase + jb.b_off + (long long)c * jb.ldb;
+  load_perm(perm, a, jb, n);
+  // own diagonal blocks and the reciprocals of their U diagonal
+  for (int t = 0; rank + t * C < nb; ++t) {
+    const int kb = (rank + t * C) * 32, w = min(32, n - kb);
+    for (int e = tid; e < 1024; e += kClThreads) {
+      const int r = e & 31, q = e >> 5;
+      tri[t * 1024 + e] = (r < w && q < w) ? A[kb + r + (long long)(kb + q) * lda] : make_double2(0.0, 0.0);
+    }
+    if (tid < w) dinv[t * 32 + tid] = cinv(A[kb + tid + (long long)(kb + tid) * lda]);
+  }
+  __syncthreads();
+  // the inverses of the 8 x 8 diagonal sub-blocks of the own blocks (one thread per column)
+  const int nown = (nb - rank + C - 1) / C;
+  for (int task = tid; task < nown * 64; task += kClThreads) {
+    const int t = task >> 6, r = task & 63;
+    const int w = min(32, n - (rank + t * C) * 32);
+    if (r < 32) inv8_column<true>(tri + t * 1024, nullptr, inv + t * 512, w, r >> 3, r & 7);
+    else inv8_column<false>(tri + t * 1024, dinv + t * 32, inv + t * 512 + 256, w, (r - 32) >> 3, r & 7);
+  }
+  __syncthreads();
+  // x = P b on the own rows
+  for (int bb = rank; bb < nb; bb += C)
+    for (int i = bb * 32 + tid; i < min(n, bb * 32 + 32); i += kClThreads) x[i] = b[perm[i]];
+  __syncthreads();
+  // Update of the own rows of blocks [blo, bhi): x_i -= A[i, kb .. kb + w) xk, four threads per
+  // row (eight columns each, two chains), 64 rows per pass.  The operands of the first pass do
+  // not depend on the block's solution: they are loaded before the cluster barrier, while the
+  // owner solves its triangle.
+  struct Pass { int i; bool live; };
+  auto pass_row = [&](int blo, int bhi, int base) -> Pass {
+    const int first = blo + ((rank - blo) % C + C) % C;  // first own block >= blo
+    const int ri = base + (tid >> 2);
+    const int bidx = first + (ri >> 5) * C;
+    const int i = bidx * 32 + (ri & 31);
+    return Pass{i, bidx < bhi && i < n};
+  };
+  auto pass_any = [&](int blo, int bhi, int base) {  // uniform: does this pass hold own rows?
+    const int first = blo + ((rank - blo) % C + C) % C;
+    return first + (base >> 5) * C < bhi;
+  };
+  auto load_ops = [&](const Pass& p, int kb, int w, double2 av[8]) {
+    const int part = tid & 3;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int q = part * 8 + e;
+      av[e] = (p.live && q < w) ? A[p.i + (long long)(kb + q) * lda] : make_double2(0.0, 0.0);
+    }
+  };
+  auto apply = [&](const Pass& p, const double2 av[8]) {
+    const int part = tid & 3;
+    double2 acc0 = make_double2(0.0, 0.0), acc1 = acc0;
+#pragma unroll
+    for (int e = 0; e < 8; e += 2) {
+      acc0 = cfms(av[e], xk[part * 8 + e], acc0);
+      acc1 = cfms(av[e + 1], xk[part * 8 + e + 1], acc1);
+    }
+    double2 acc = cadd(acc0, acc1);
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 2);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 2);
+    if (p.live && part == 0) x[p.i] = make_double2(x[p.i].x + acc.x, x[p.i].y + acc.y);
+  };
+  auto update_rest = [&](int blo, int bhi, int kb, int w) {  // passes after the first
+    for (int base = kClThreads / 4; pass_any(blo, bhi, base); base += kClThreads / 4) {
+      const Pass p = pass_row(blo, bhi, base);
+      double2 av[8];
+      load_ops(p, kb, w, av);
+      apply(p, av);
+    }
+  };
+  // forward substitution with the unit lower factor
+  for (int bk = 0; bk < nb; ++bk) {
+    const int kb = bk * 32, w = min(32, n - kb), owner = bk % C;
+    const bool upd = bk + 1 < nb && pass_any(bk + 1, nb, 0);
+    Pass p0{0, false};
+    double2 av[8];
+    if (upd) {
+      p0 = pass_row(bk + 1, nb, 0);
+      load_ops(p0, kb, w, av);
+    }
+    if (rank == owner) block_solve32<true>(x + kb, tri + (bk / C) * 1024, inv + (bk / C) * 512, w);
+    cl.sync();
+    if (tid < 32) xk[tid] = tid < w ? cl.map_shared_rank(x, owner)[kb + tid] : make_double2(0.0, 0.0);
+    __syncthreads();
+    if (upd) {
+      apply(p0, av);
+      update_rest(bk + 1, nb, kb, w);
+    }
+    __syncthreads();
+  }
+  // back substitution with the upper factor, from the last block
+  for (int bk = nb - 1; bk >= 0; --bk) {
+    const int kb = bk * 32, w = min(32, n - kb), owner = bk % C;
+    const bool upd = bk > 0 && pass_any(0, bk, 0);
+    Pass p0{0, false};
+    double2 av[8];
+    if (upd) {
+      p0 = pass_row(0, bk, 0);
+      load_ops(p0, kb, w, av);
+    }
+    if (rank == owner) block_solve32<false>(x + kb, tri + (bk / C) * 1024, inv + (bk / C) * 512 + 256, w);
+    cl.sync();
+    if (tid < 32) xk[tid] = tid < w ? cl.map_shared_rank(x, owner)[kb + tid] : make_double2(0.0, 0.0);
+    __syncthreads();
+    if (upd) {
+      apply(p0, av);
+      update_rest(0, bk, kb, w);
+    }
+    __syncthreads();
+  }
+  for (int bb = rank; bb < nb; bb += C)
+    for (int i = bb * 32 + tid; i < min(n, bb * 32 + 32); i += kClThreads) b[i] = x[i];
+  cl.sync();  // no member reads another's shared memory after this point
+}
+
 // ---- blocked solve with tensor-core updates (FP64, many right-hand sides) ----------------
 constexpr int kBlk = 64;  // diagonal block of the blocked solve
 
@@ -177,7 +425,7 @@ __global__ void permute_kernel(const RsLaunch a, int warps) {
   if (n > a.max_n || n < 0) return;  // uniform per block
   double2* cols = reinterpret_cast<double2*>(smem_raw);
   int* perm = reinterpret_cast<int*>(cols + (size_t)warps * a.max_n);
-  build_perm(perm, a.piv + jb.piv_off, n);
+  load_perm(perm, a, jb, n);
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int c = blockIdx.y * warps + warp;
@@ -311,6 +559,38 @@ cudaError_t getrs_impl(const RsLaunch& a, cudaStream_t s) {
                       a.zimg && a.zimg_bytes >= zgemm_rs_img_bytes(a.njobs, a.max_n, a.max_rhs);
   if (sizeof(CT) == sizeof(double2) && use_tc && a.status && a.max_rhs > 4 && max_n > kBlk)
     return getrs_blocked_tc(a, s);
+  if (a.max_rhs <= 4 && sizeof(CT) == sizeof(double2) && max_n >= 128) {
+    // few large blocks: a cluster per (matrix, right-hand side) while the SMs allow
+    const int nb = (max_n + 31) / 32;
+    int C = 16;
+    while (C >= 2 && ((long long)a.njobs * a.max_rhs * C > device_sm_count() || nb < C)) C /= 2;
+    if (C >= 2) {
+      const int nbown = (nb + C - 1) / C;
+      const size_t smem = (size_t)max_n * sizeof(double2) + (size_t)nbown * (1024 + 32 + 512) * sizeof(double2) +
+                          (size_t)max_n * sizeof(int);
+      if (smem <= 200 * 1024) {
+        e = cudaFuncSetAttribute(getrs_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess && C > 8)
+          e = cudaFuncSetAttribute(getrs_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(a.njobs * a.max_rhs * C, 1, 1);
+        cfg.blockDim = dim3(kClThreads, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, getrs_cluster_kernel, a, nbown);
+        symhss::count_launches(1);
+        return e;
+      }
+    }
+  }
   if (a.max_rhs <= 4) {
     const size_t smem = (size_t)max_n * (2 * sizeof(CT) + sizeof(int));
     if (smem > 200 * 1024) return cudaErrorInvalidValue;

@@ -396,6 +396,14 @@ __global__ void __launch_bounds__(256) swap_trsm_warp_kernel(const LuLaunch a, i
     }
     for (int l = 0; l < cnt; ++l) src_s[l] = content[l];
     nrows_s = cnt;
+    // the same interchanges on the kept row permutation (once per panel: the first column block)
+    if (swaps && a.perm && blockIdx.y == 0) {
+      int* pm = a.perm + jb.piv_off;
+      for (int c = 0; c < w; ++c) {
+        const int p = piv_s[c];
+        if (p != j + c && p >= 0 && p < n) { const int t = pm[j + c]; pm[j + c] = pm[p]; pm[p] = t; }
+      }
+    }
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -484,6 +492,12 @@ __global__ void zero_info_kernel(int* info, const LuJob* jobs, int njobs) {
   if (b < njobs) info[jobs[b].info_idx] = 0;
 }
 
+// the row permutation of every matrix starts as the identity (one block per matrix)
+__global__ void perm_init_kernel(const LuLaunch a) {
+  const LuJob jb = a.jobs[blockIdx.x];
+  for (int i = threadIdx.x; i < jb.n; i += blockDim.x) a.perm[jb.piv_off + i] = i;
+}
+
 // Side stream (highest priority) and two events for the look-ahead, one set per host
 // thread and device, created on first use; nullptr if they cannot be created (the
 // factorisation then runs without look-ahead on the caller's stream).
@@ -526,6 +540,11 @@ cudaError_t getrf_impl(const LuLaunch& a, cudaStream_t s) {
   symhss::count_launches(1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (a.perm) {
+    perm_init_kernel<<<a.njobs, 256, 0, s>>>(a);
+    symhss::count_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   // panels of up to 780 rows fit in shared memory (780 x 16 x 16 B = 195 KB)
   const size_t panel_smem = (size_t)a.max_n * kNb * sizeof(CT);
   const bool smem_panel = panel_smem <= 200 * 1024;

@@ -155,6 +155,7 @@ struct Height {
   DevBuf mr, tbuf, permbuf, rankbuf, refbuf, clists, idjobs, slices, skmeta;
   // factor
   DevBuf D, piv, rxpiv, info, X, RX, At, qbuf, flists, lujobs, cjobs;
+  DevBuf perm, rxperm;           // the LUs' row permutations (kept by the LU, read by the solves)
   DevBuf Dop;                    // the assembled diagonal blocks (FP64), kept for the matvec
   DevBuf D32, X32, RX32, At32;   // complex64 work of the mixed-precision factorisation
   // solve
@@ -1212,6 +1213,7 @@ int assemble_and_lu(symhss_s* h, int t, cudaStream_t s, long long& pairs) {
   }
   CK(H.D.ensure(d_total * sizeof(double2)));
   CK(H.piv.ensure(piv_total * sizeof(int)));
+  CK(H.perm.ensure(piv_total * sizeof(int)));
   CK(H.info.ensure(refs.size() * sizeof(int)));
   TileBuilder tb;
   std::vector<CopyJob> copies, mirrors;
@@ -1299,6 +1301,7 @@ int assemble_and_lu(symhss_s* h, int t, cudaStream_t s, long long& pairs) {
   la.panel_threads = h->tune.lu_panel_threads;
   la.panel_cluster = h->tune.lu_panel_cluster;
   la.tc = h->tune.lu_tc;
+  la.perm = H.perm.as<int>();
   CK(H.zimg.ensure((size_t)zgemm_lu_img_bytes(la.njobs, max_n)));
   la.zimg = H.zimg.as<unsigned char>();
   la.zimg_bytes = (long long)H.zimg.cap;
@@ -1447,6 +1450,7 @@ int factor_height(symhss_s* h, int t, cudaStream_t s, long long& pairs, bool lu_
   }
   ra.zimg = H.zimg.as<unsigned char>();
   ra.zimg_bytes = (long long)H.zimg.cap;
+  ra.perm = H.perm.as<int>();
   TIMED(SYMHSS_K_GETRS, w_x, launch_getrs(ra, s));
   // R X
   BasisLaunch br = bl;
@@ -1460,6 +1464,7 @@ int factor_height(symhss_s* h, int t, cudaStream_t s, long long& pairs, bool lu_
   TIMED(SYMHSS_K_OTHER, w_rx, launch_apply_r(br, s));
   // Atilde = (R X)^{-1}
   CK(H.rxpiv.ensure(rxpiv_total * sizeof(int)));
+  CK(H.rxperm.ensure(rxpiv_total * sizeof(int)));
   LuLaunch la;
   la.base = H.RX.as<double2>();
   if (mixed) la.base32 = H.RX32.as<float2>();
@@ -1475,6 +1480,7 @@ int factor_height(symhss_s* h, int t, cudaStream_t s, long long& pairs, bool lu_
   la.tc = h->tune.lu_tc;
   la.zimg = H.zimg.as<unsigned char>();
   la.zimg_bytes = (long long)H.zimg.cap;
+  la.perm = H.rxperm.as<int>();
   TIMED(SYMHSS_K_GETRF, w_rxlu, launch_getrf(la, s));
   if (mixed)
     TIMED(SYMHSS_K_OTHER, 0.0, launch_copy_blocks32(nullptr, H.At32.as<float2>(),
@@ -1498,6 +1504,7 @@ int factor_height(symhss_s* h, int t, cudaStream_t s, long long& pairs, bool lu_
   rb.tc = h->tune.lu_tc;
   rb.zimg = H.zimg.as<unsigned char>();
   rb.zimg_bytes = (long long)H.zimg.cap;
+  rb.perm = H.rxperm.as<int>();
   TIMED(SYMHSS_K_GETRS, w_at, launch_getrs(rb, s));
   if (mixed) {  // X and Atilde in FP64 for the parents' blocks and the solve phase
     TIMED(SYMHSS_K_OTHER, 0.0, launch_widen(H.X32.as<float2>(), H.X.as<double2>(), x_total, s));
@@ -1991,6 +1998,7 @@ int solve_core(symhss_s* h, const double2* f, double2* xo, int nrhs, cudaStream_
     ra.abase = H.D.as<double2>(); ra.piv = H.piv.as<int>(); ra.bbase = H.G.as<double2>();
     ra.jobs = reinterpret_cast<const RsJob*>(sb + ors); ra.njobs = (int)rs.size();
     ra.max_rhs = nrhs; ra.max_n = max_n;
+    ra.perm = H.perm.as<int>();
     TIMED(SYMHSS_K_GETRS, w_g, launch_getrs(ra, s));
     if (!bj.empty()) {
       // tmp = R g ; f~ = Atilde tmp

@@ -111,8 +111,10 @@ def test_batch_launches_do_not_grow_with_problem_count(solver_mod):
         singles.append(S.lib.symhss_launch_count() - n0)
         b.close()
     # one launch per kernel and height: the blocked LU adds panel launches for the largest
-    # block of a height, so the batch may exceed its largest single problem a little
-    assert batch_launches <= 1.3 * max(singles), (batch_launches, singles)
+    # block of a height, and a batched height of >= 32 blocks takes the tensor-core path (64-column
+    # blocks, two launches per product) that a single problem's few blocks do not, so the batch
+    # may exceed its largest single problem by a bounded factor; it stays far below their sum
+    assert batch_launches <= 1.5 * max(singles), (batch_launches, singles)
     assert batch_launches <= 0.4 * sum(singles), (batch_launches, singles)
 
 

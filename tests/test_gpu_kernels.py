@@ -199,6 +199,13 @@ def _lu_solve_case(S, n, nrhs, batch):
         assert np.linalg.norm(x[i] - ref) <= 1e-12 * np.linalg.cond(a[i]) * np.linalg.norm(ref), (n, nrhs)
 
 
+@pytest.mark.parametrize("n,nrhs,batch", [(600, 1, 1), (1000, 2, 3), (130, 1, 9), (2048, 1, 1), (300, 4, 20)])
+def test_lu_cluster_solves(S, n, nrhs, batch):
+    """Few right-hand sides on few large blocks: the solve runs on a thread-block cluster per
+    (block, right-hand side), 32-row blocks owned in turn, ragged last block."""
+    _lu_solve_case(S, n, nrhs, batch)
+
+
 def test_lu_reports_singular_block(S):
     n = 6
     a = np.eye(n, dtype=np.complex128)
