@@ -627,6 +627,8 @@ def run_profile(args):
     from paper_2609_33216_b300 import symhss as S
     if args.lu_tc is not None:
         S.symhss_set_tuning(s.h, lu_tc=args.lu_tc)
+    if args.lu_outer is not None:
+        S.symhss_set_tuning(s.h, lu_outer=args.lu_outer)
     if args.panel_cluster is not None:
         S.symhss_set_tuning(s.h, lu_panel_cluster=args.panel_cluster)
     if args.lookahead is not None:
@@ -744,6 +746,8 @@ def main():
     ap.add_argument("--profile", action="store_true", help="one warm-up + one symmetric step only")
     ap.add_argument("--lu-tc", type=int, default=None, choices=[0, 1, 2],
                     help="with --profile: factorisation path (1: tensor-core updates, 0: FP64 pipe, 2: by launch size)")
+    ap.add_argument("--lu-outer", type=int, default=None, choices=[16, 32, 64],
+                    help="with --profile: column block of the tensor-core LU updates")
     ap.add_argument("--panel-cluster", type=int, default=None, choices=[1, 2, 4, 8, 16],
                     help="with --profile: largest thread-block cluster of an LU panel")
     ap.add_argument("--lookahead", type=int, default=None, choices=[0, 1],

@@ -286,22 +286,26 @@ typedef struct {
   int lu_panel_cluster;   /* 1, 2, 4, 8 or 16 (default 16): largest thread-block cluster factoring
                            * one LU panel, used while blocks x cluster <= the SM count and every
                            * member keeps >= 32 panel rows (the top tree levels); 1: one block */
-  int lu_tc;              /* 1: FP64 block LUs blocked by 64 columns and multi-RHS solves blocked
+  int lu_tc;              /* 1: FP64 block LUs blocked by lu_outer columns and multi-RHS solves blocked
                            * by 64 rows, their updates on the tensor cores (symhss_zgemm);
                            * 0: 16-column LU and unblocked solves on the FP64 pipe; 2 (default):
                            * the first for launches of at least 32 blocks (the lower tree levels;
                            * solves also when blocks x right-hand sides >= 512), the second above.
                            * All give the factorisation to FP64 rounding, not the same bits. */
-  int reserved[2];
+  int lu_outer;           /* column block of the LU's tensor-core updates: 16 (default), 32 or 64
+                           * (0 = 64); 16: a rank-16 update on the tensor cores after every
+                           * 16-column panel, no FP64 updates inside a block.  The blocked
+                           * solves keep 64-row blocks (measured faster than 16 or 32). */
+  int reserved[1];
 } symhss_tuning;
 
 int symhss_get_tuning(symhss_t h, symhss_tuning* out);
 /* Set the handle's launch tuning (values outside the lists above: SYMHSS_ERR_INVALID). */
 int symhss_set_tuning(symhss_t h, const symhss_tuning* t);
 /* Autotuner: time the handle's own compress / factor with each value of each tunable
- * (coordinate search: tile_loop_chunk and id_cluster_max on compress, then lu_tc (block LU +
- * solve time), lu_panel_threads x lu_lookahead, then lu_panel_cluster x lu_lookahead on
- * factor), `reps` runs
+ * (coordinate search: tile_loop_chunk and id_cluster_max on compress, then lu_tc x lu_outer
+ * (block LU + solve time), lu_panel_threads x lu_lookahead, then lu_panel_cluster x
+ * lu_lookahead on factor), `reps` runs
  * per value, the minimum device time of the affected kernel classes deciding; leaves the best
  * tuning set (and in *out, if not NULL) and the handle compressed and factorised.
  * Synchronises `stream`. */

@@ -384,8 +384,9 @@ struct LuLaunch {
   int lookahead = 1;       // depth-1 look-ahead on a side stream
   int panel_threads = 1024;  // largest panel block
   int panel_cluster = 1;     // largest cluster for the panels of few large matrices (1: one block)
-  int tc = 2;                // FP64: 64-column blocks with tensor-core updates (1: always, 2: for
+  int tc = 2;                // FP64: column blocks with tensor-core updates (1: always, 2: for
                              // launches of at least 32 matrices, 0: never)
+  int outer = 64;            // their width: 16 (a tensor-core update after every panel), 32 or 64
   unsigned char* zimg = nullptr;  // tensor-core product scratch, zgemm_lu_img_bytes(njobs, max_n)
   long long zimg_bytes = 0;       // bytes (too few: the FP64-pipe path)
   int* perm = nullptr;            // optional: the row permutation of every matrix (at piv_off),
@@ -414,6 +415,7 @@ struct RsLaunch {
   long long zimg_bytes = 0;       // bytes (too few: the unblocked FP64 solve)
   const int* perm = nullptr;      // optional: the LU's row permutations (LuLaunch::perm); else
                                   // every solve composes them from piv
+  int blk = 64;                   // row block of the blocked tensor-core solve: 16, 32 or 64
 };
 cudaError_t launch_getrs(const RsLaunch& a, cudaStream_t s);
 // scratch of the tensor-core products of a blocked LU / blocked solve launch
@@ -432,9 +434,9 @@ struct ZgemmTile { int job, mt, nt; };  // row tile mt (128 rows), column tile n
 // Jobs derived on the device from the factorisation's job arrays (block J = 64-aligned row):
 enum : int {
   ZGEMM_JOBS = 0,      // explicit ZgemmJob / ZgemmTile arrays
-  ZGEMM_LU_UPDATE = 1,  // LuJob: A[J+64:n, J+64:n] -= A[J+64:n, J:J+64] A[J:J+64, J+64:n]
-  ZGEMM_RS_FWD = 2,     // RsJob: X[J+64:n, :] -= L[J+64:n, J:J+64] X[J:J+64, :]
-  ZGEMM_RS_BWD = 3,     // RsJob: X[0:J, :] -= U[0:J, J:J+64] X[J:J+64, :]
+  ZGEMM_LU_UPDATE = 1,  // LuJob: A[J+W:n, J+W:n] -= A[J+W:n, J:J+W] A[J:J+W, J+W:n], W = block_w
+  ZGEMM_RS_FWD = 2,     // RsJob: X[J+W:n, :] -= L[J+W:n, J:J+W] X[J:J+W, :]
+  ZGEMM_RS_BWD = 3,     // RsJob: X[0:J, :] -= U[0:J, J:J+W] X[J:J+W, :]
 };
 struct ZgemmLaunch {
   const double2* A;
@@ -450,6 +452,7 @@ struct ZgemmLaunch {
   const LuJob* lu_jobs = nullptr;
   const RsJob* rs_jobs = nullptr;
   int block_j = 0;     // J of the derived jobs
+  int block_w = 64;    // W: width of the column block J .. J + W of the derived jobs
   int mtiles = 0, ntiles_c = 0;  // row / column blocks per job (explicit jobs: the largest)
   int njobs = 0;                   // jobs of the launch
   unsigned char* img = nullptr;    // scratch for the slice images (16-byte aligned),

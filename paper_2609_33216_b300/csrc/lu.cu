@@ -415,7 +415,7 @@ __global__ void __launch_bounds__(kClThreads) getrs_cluster_kernel(const RsLaunc
 }
 
 // ---- blocked solve with tensor-core updates (FP64, many right-hand sides) ----------------
-constexpr int kBlk = 64;  // diagonal block of the blocked solve
+constexpr int kBlk = 64;  // largest diagonal block of the blocked solve (shared-memory stride)
 
 // b <- P b for every right-hand side (one warp per column, the column staged in shared memory)
 __global__ void permute_kernel(const RsLaunch a, int warps) {
@@ -440,7 +440,7 @@ __global__ void permute_kernel(const RsLaunch a, int warps) {
 // rows [J, J + w) of every right-hand side: solve with the unit-lower (LOWER) or the upper
 // diagonal block of the factors, staged in shared memory; one warp per right-hand side
 template <bool LOWER>
-__global__ void trsv_block_kernel(const RsLaunch a, int J, int warps) {
+__global__ void trsv_block_kernel(const RsLaunch a, int J, int warps, int W) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* tri = reinterpret_cast<double2*>(smem_raw);  // kBlk x kBlk, column-major
   double2* dinv = tri + kBlk * kBlk;
@@ -448,7 +448,7 @@ __global__ void trsv_block_kernel(const RsLaunch a, int J, int warps) {
   const RsJob jb = a.jobs[blockIdx.x];
   const int n = jb.n;
   if (n > a.max_n || J >= n) return;  // uniform per block
-  const int w = min(kBlk, n - J);
+  const int w = min(W, n - J);
   const double2* A = a.abase + jb.a_off + J + (long long)J * jb.lda;
   for (int e = threadIdx.x; e < kBlk * w; e += blockDim.x) {
     const int r = e % kBlk, q = e / kBlk;
@@ -515,11 +515,13 @@ cudaError_t getrs_blocked_tc(const RsLaunch& a, cudaStream_t s) {
   g.img_bytes = a.zimg_bytes;
   g.ntiles_c = (a.max_rhs + zgemm_tc_tile_cols() - 1) / zgemm_tc_tile_cols();
   // forward: L y = P b, block by block; the rows below a block are updated on the tensor cores
-  for (int J = 0; J < max_n; J += kBlk) {
-    trsv_block_kernel<true><<<grid, warps * 32, tsmem, s>>>(a, J, warps);
+  const int W = (a.blk == 16 || a.blk == 32) ? a.blk : kBlk;
+  g.block_w = W;
+  for (int J = 0; J < max_n; J += W) {
+    trsv_block_kernel<true><<<grid, warps * 32, tsmem, s>>>(a, J, warps, W);
     symhss::count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const int below = max_n - J - kBlk;
+    const int below = max_n - J - W;
     if (below > 0) {
       g.derive = ZGEMM_RS_FWD;
       g.block_j = J;
@@ -529,8 +531,8 @@ cudaError_t getrs_blocked_tc(const RsLaunch& a, cudaStream_t s) {
     }
   }
   // backward: U x = y from the last block; the rows above a block are updated on the tensor cores
-  for (int J = ((max_n - 1) / kBlk) * kBlk; J >= 0; J -= kBlk) {
-    trsv_block_kernel<false><<<grid, warps * 32, tsmem, s>>>(a, J, warps);
+  for (int J = ((max_n - 1) / W) * W; J >= 0; J -= W) {
+    trsv_block_kernel<false><<<grid, warps * 32, tsmem, s>>>(a, J, warps, W);
     symhss::count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (J > 0) {
@@ -557,7 +559,8 @@ cudaError_t getrs_impl(const RsLaunch& a, cudaStream_t s) {
   // (its block updates then fill the product's tiles), the unblocked FP64 solve otherwise
   const bool use_tc = (a.tc == 1 || (a.tc == 2 && (a.njobs >= 32 || (long long)a.njobs * a.max_rhs >= 512))) &&
                       a.zimg && a.zimg_bytes >= zgemm_rs_img_bytes(a.njobs, a.max_n, a.max_rhs);
-  if (sizeof(CT) == sizeof(double2) && use_tc && a.status && a.max_rhs > 4 && max_n > kBlk)
+  if (sizeof(CT) == sizeof(double2) && use_tc && a.status && a.max_rhs > 4 &&
+      max_n > ((a.blk == 16 || a.blk == 32) ? a.blk : kBlk))
     return getrs_blocked_tc(a, s);
   if (a.max_rhs <= 4 && sizeof(CT) == sizeof(double2) && max_n >= 128) {
     // few large blocks: a cluster per (matrix, right-hand side) while the SMs allow

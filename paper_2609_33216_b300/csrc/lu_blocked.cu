@@ -24,7 +24,7 @@ namespace symhss {
 namespace {
 
 constexpr int kNb = 16;          // panel width
-constexpr int kOuter = 64;       // column block of the tensor-core trailing update (FP64)
+constexpr int kOuterMax = 64;    // largest column block of the tensor-core trailing update (FP64)
 constexpr int kTcMinJobs = 32;   // lu_tc = 2: the tensor-core path for launches of this many matrices
 constexpr int kPanelThreads = 256;
 constexpr int kPanelWarps = kPanelThreads / 32;
@@ -618,6 +618,7 @@ cudaError_t getrf_impl(const LuLaunch& a, cudaStream_t s) {
   // extra launches cost more than the FP64 updates they replace)
   const bool use_tc = (a.tc == 1 || (a.tc == 2 && a.njobs >= kTcMinJobs)) && a.zimg &&
                       a.zimg_bytes >= zgemm_lu_img_bytes(a.njobs, a.max_n);
+  const int kOuter = (a.outer == 16 || a.outer == 32) ? a.outer : kOuterMax;
   if (sizeof(CT) == sizeof(double2) && use_tc && a.max_n > kOuter + kNb) {
     // FP64: blocked by 64 columns (the order of a blocked right-looking LU).  Inside a block
     // the 16-column panels run as above with their interchanges applied to every column, but
@@ -628,8 +629,10 @@ cudaError_t getrf_impl(const LuLaunch& a, cudaStream_t s) {
       const int J = (j / kOuter) * kOuter;
       const int rest = a.max_n - j - kNb;
       if (rest > 0) {
-        // interchanges in every column; U rows only in the block's own columns
-        swap_trsm_warp_kernel<CT><<<dim3(a.njobs, ncolblk), 256, 0, s>>>(a, j, 0, J + kOuter, 1, 0);
+        // interchanges in every column; U rows only in the block's own columns (a block of
+        // one panel: in every column right of it, so that no second pass is needed)
+        swap_trsm_warp_kernel<CT><<<dim3(a.njobs, ncolblk), 256, 0, s>>>(a, j, 0, kOuter == kNb ? a.max_n : J + kOuter,
+                                                                          1, 0);
         symhss::count_launches(1);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         const int pc = J + kOuter - (j + kNb);  // columns of the block right of this panel
@@ -643,8 +646,8 @@ cudaError_t getrf_impl(const LuLaunch& a, cudaStream_t s) {
       if (j + kNb == J + kOuter && right > 0) {
         // the block's U rows for the columns right of it, now that all its interchanges are
         // applied: 16-row solves, each followed by the update of the block rows below it
-        const int rblk = (right + 15) / 16;  // blocks of 16 columns starting at J + 64
-        for (int jj = J; jj < J + kOuter; jj += kNb) {
+        const int rblk = (right + 15) / 16;  // blocks of 16 columns starting at J + kOuter
+        for (int jj = J; kOuter > kNb && jj < J + kOuter; jj += kNb) {
           swap_trsm_warp_kernel<CT><<<dim3(a.njobs, rblk), 256, 0, s>>>(a, jj, J + kOuter, a.max_n, 0, J + kOuter);
           symhss::count_launches(1);
           if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -662,6 +665,7 @@ cudaError_t getrf_impl(const LuLaunch& a, cudaStream_t s) {
         g.status = a.status;
         g.wait_ns = 0;
         g.derive = ZGEMM_LU_UPDATE;
+        g.block_w = kOuter;
         g.lu_jobs = a.jobs;
         g.njobs = a.njobs;
         g.img = a.zimg;

@@ -200,7 +200,7 @@ struct symhss_s {
   symhss_stats_t st{};
   cudaError_t last_cuda = cudaSuccess;
   std::vector<int> mark;                          // host scratch (size npts)
-  symhss_tuning tune = {0, 256, 0, 16, 16, 2, {0, 0}};  // launch tuning (symhss_set_tuning)
+  symhss_tuning tune = {0, 256, 0, 16, 16, 2, 16, {0}};  // launch tuning (symhss_set_tuning)
   symhss_mlp_s* mlp = nullptr;                    // attached proposer (not owned)
   double prop_margin = 1.15;
   symhss::DevBuf featjobs, feats, mlpout, chkjobs, chkratio;
@@ -1301,6 +1301,7 @@ int assemble_and_lu(symhss_s* h, int t, cudaStream_t s, long long& pairs) {
   la.panel_threads = h->tune.lu_panel_threads;
   la.panel_cluster = h->tune.lu_panel_cluster;
   la.tc = h->tune.lu_tc;
+  la.outer = h->tune.lu_outer > 0 ? h->tune.lu_outer : 64;
   la.perm = H.perm.as<int>();
   CK(H.zimg.ensure((size_t)zgemm_lu_img_bytes(la.njobs, max_n)));
   la.zimg = H.zimg.as<unsigned char>();
@@ -1478,6 +1479,7 @@ int factor_height(symhss_s* h, int t, cudaStream_t s, long long& pairs, bool lu_
   la.panel_threads = h->tune.lu_panel_threads;
   la.panel_cluster = h->tune.lu_panel_cluster;
   la.tc = h->tune.lu_tc;
+  la.outer = h->tune.lu_outer > 0 ? h->tune.lu_outer : 64;
   la.zimg = H.zimg.as<unsigned char>();
   la.zimg_bytes = (long long)H.zimg.cap;
   la.perm = H.rxperm.as<int>();
@@ -2366,7 +2368,7 @@ static bool tuning_ok(const symhss_tuning* t) {
   };
   return in(t->lu_lookahead, {0, 1}) && in(t->lu_panel_threads, {256, 512, 1024}) &&
          in(t->tile_loop_chunk, {0, 8, 16, 32}) && in(t->id_cluster_max, {1, 2, 4, 8, 16}) &&
-         in(t->lu_panel_cluster, {1, 2, 4, 8, 16}) && in(t->lu_tc, {0, 1, 2});
+         in(t->lu_panel_cluster, {1, 2, 4, 8, 16}) && in(t->lu_tc, {0, 1, 2}) && in(t->lu_outer, {0, 16, 32, 64});
 }
 
 int symhss_get_tuning(symhss_t h, symhss_tuning* out) {
@@ -2415,11 +2417,13 @@ int symhss_autotune(symhss_t h, int reps, symhss_tuning* out, void* stream) {
   h->tune = best;
   int rc = symhss_compress(h, stream);
   if (rc) return rc;
-  // the factorisation's arithmetic path: block LU and solve classes together
+  // the factorisation's arithmetic path and its block width: block LU and solve classes together
   bms = 1e300;
-  for (int v : {2, 1, 0}) {
+  const int paths[7][2] = {{2, 64}, {2, 32}, {2, 16}, {1, 64}, {1, 32}, {1, 16}, {0, 64}};
+  for (const auto& pv : paths) {
     h->tune = best;
-    h->tune.lu_tc = v;
+    h->tune.lu_tc = pv[0];
+    h->tune.lu_outer = pv[1];
     double m = 1e300;
     for (int r = 0; r < reps; ++r) {
       const double b0 = h->st.kernel_ms[SYMHSS_K_GETRF] + h->st.kernel_ms[SYMHSS_K_GETRS];
@@ -2427,7 +2431,7 @@ int symhss_autotune(symhss_t h, int reps, symhss_tuning* out, void* stream) {
       if (rc) return rc;
       m = std::min(m, h->st.kernel_ms[SYMHSS_K_GETRF] + h->st.kernel_ms[SYMHSS_K_GETRS] - b0);
     }
-    if (m < bms) { bms = m; best.lu_tc = v; }
+    if (m < bms) { bms = m; best.lu_tc = pv[0]; best.lu_outer = pv[1]; }
   }
   bms = 1e300;
   for (int pt : {256, 512, 1024})

@@ -188,20 +188,22 @@ __device__ __forceinline__ ZgemmJob decode_job(const ZgemmLaunch& a, int jidx) {
   const int J = a.block_j;
   if (a.derive == ZGEMM_LU_UPDATE) {
     const LuJob lj = a.lu_jobs[jidx];
-    jb.m = lj.n - J - 64; jb.n = jb.m; jb.k = min(64, lj.n - J);
+    const int W = a.block_w;
+    jb.m = lj.n - J - W; jb.n = jb.m; jb.k = min(W, lj.n - J);
     jb.lda = jb.ldb = jb.ldc = lj.ld;
-    jb.a_off = lj.a_off + (J + 64) + (long long)J * lj.ld;
-    jb.b_off = lj.a_off + J + (long long)(J + 64) * lj.ld;
-    jb.c_off = lj.a_off + (J + 64) + (long long)(J + 64) * lj.ld;
+    jb.a_off = lj.a_off + (J + W) + (long long)J * lj.ld;
+    jb.b_off = lj.a_off + J + (long long)(J + W) * lj.ld;
+    jb.c_off = lj.a_off + (J + W) + (long long)(J + W) * lj.ld;
   } else {
     const RsJob rj = a.rs_jobs[jidx];
-    jb.k = min(64, rj.n - J); jb.n = rj.nrhs;
+    const int W = a.block_w;
+    jb.k = min(W, rj.n - J); jb.n = rj.nrhs;
     jb.lda = rj.lda; jb.ldb = jb.ldc = rj.ldb;
     jb.b_off = rj.b_off + J;
     if (a.derive == ZGEMM_RS_FWD) {
-      jb.m = rj.n - J - 64;
-      jb.a_off = rj.a_off + (J + 64) + (long long)J * rj.lda;
-      jb.c_off = rj.b_off + J + 64;
+      jb.m = rj.n - J - W;
+      jb.a_off = rj.a_off + (J + W) + (long long)J * rj.lda;
+      jb.c_off = rj.b_off + J + W;
     } else {
       jb.m = J;
       jb.a_off = rj.a_off + (long long)J * rj.lda;
@@ -586,7 +588,7 @@ long long zgemm_img_bytes_for(int njobs, int max_m, int max_n) {
   return zgemm_img_bytes(njobs, (max_m + kTileM - 1) / kTileM, (max_n + kTileNc - 1) / kTileNc);
 }
 
-long long zgemm_lu_img_bytes(int njobs, int max_n) { return zgemm_img_bytes_for(njobs, max_n - 64, max_n - 64); }
+long long zgemm_lu_img_bytes(int njobs, int max_n) { return zgemm_img_bytes_for(njobs, max_n - 16, max_n - 16); }
 long long zgemm_rs_img_bytes(int njobs, int max_n, int max_rhs) { return zgemm_img_bytes_for(njobs, max_n, max_rhs); }
 
 cudaError_t launch_zgemm_tc(const ZgemmLaunch& a_in, cudaStream_t s) {

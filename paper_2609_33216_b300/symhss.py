@@ -74,11 +74,11 @@ class symhss_stats_t(C.Structure):
 class symhss_tuning(C.Structure):
     _fields_ = [("lu_lookahead", C.c_int), ("lu_panel_threads", C.c_int), ("tile_loop_chunk", C.c_int),
                 ("id_cluster_max", C.c_int), ("lu_panel_cluster", C.c_int), ("lu_tc", C.c_int),
-                ("reserved", C.c_int * 2)]
+                ("lu_outer", C.c_int), ("reserved", C.c_int * 1)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k in ("lu_lookahead", "lu_panel_threads", "tile_loop_chunk", "id_cluster_max",
-                                              "lu_panel_cluster", "lu_tc")}
+                                              "lu_panel_cluster", "lu_tc", "lu_outer")}
 
 
 class symhss_points(C.Structure):

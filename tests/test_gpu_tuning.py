@@ -47,7 +47,7 @@ def test_autotune_returns_valid_setting_and_leaves_handle_factored(mods):
     t = S.symhss_autotune(s.h, reps=1)
     assert t.lu_lookahead in (0, 1) and t.lu_panel_threads in (256, 512, 1024)
     assert t.tile_loop_chunk in (0, 8, 16, 32) and t.id_cluster_max in (1, 2, 4, 8, 16)
-    assert t.lu_panel_cluster in (1, 2, 4, 8, 16) and t.lu_tc in (0, 1, 2)
+    assert t.lu_panel_cluster in (1, 2, 4, 8, 16) and t.lu_tc in (0, 1, 2) and t.lu_outer in (16, 32, 64)
     assert S.symhss_get_tuning(s.h).as_dict() == t.as_dict()
     x = s.solve(s.rhs(0.0))  # factorised by the autotuner
     assert torch.isfinite(torch.view_as_real(x)).all()
@@ -55,20 +55,20 @@ def test_autotune_returns_valid_setting_and_leaves_handle_factored(mods):
 
 
 def test_tensor_core_and_fp64_factorisations_agree(mods):
-    """lu_tc = 1 (64-blocked LU and solves with tensor-core updates), lu_tc = 0 (16-column LU and
-    unblocked solves on the FP64 pipe) and lu_tc = 2 (the first at levels of >= 32 blocks) factorise
-    the same compressed system: the solutions agree to FP64 rounding amplified by the blocks'
-    conditioning (<= 1e-11 relative)."""
+    """lu_tc = 1 (blocked LU and solves with tensor-core updates, column blocks of lu_outer = 64, 32
+    or 16), lu_tc = 0 (16-column LU and unblocked solves on the FP64 pipe) and lu_tc = 2 (the first
+    at levels of >= 32 blocks) factorise the same compressed system: the solutions agree to FP64
+    rounding amplified by the blocks' conditioning (<= 1e-11 relative)."""
     SV, S = mods
     s = SV.Solver(star(6000), 20.0, 30.0, leaf=128, nproxy=64, tol=1e-10)
     xs = []
-    for tc in (1, 0, 2):
-        S.symhss_set_tuning(s.h, lu_tc=tc)
+    for tc, outer in ((1, 64), (0, 64), (2, 64), (1, 16), (1, 32), (2, 16)):
+        S.symhss_set_tuning(s.h, lu_tc=tc, lu_outer=outer)
         s.compress()
         s.factor()
         xs.append(s.solve(s.rhs(0.0)).cpu().numpy())
-    assert np.linalg.norm(xs[0] - xs[1]) / np.linalg.norm(xs[1]) <= 1e-11
-    assert np.linalg.norm(xs[2] - xs[1]) / np.linalg.norm(xs[1]) <= 1e-11
+    for i in (0, 2, 3, 4, 5):
+        assert np.linalg.norm(xs[i] - xs[1]) / np.linalg.norm(xs[1]) <= 1e-11, i
     s.close()
 
 
