@@ -482,6 +482,64 @@ __global__ void trsv_block_kernel(const RsLaunch a, int J, int warps, int W) {
   for (int i = lane; i < w; i += 32) b[i] = sb[i];
 }
 
+// The same diagonal-block solve with the right-hand sides on the lanes (many blocks, the lower
+// levels): an FP64 instruction costs this GPU the same issue time however many of its lanes
+// are active, and here every lane works in every step, where the row-per-lane kernel above
+// leaves the lanes past the triangle idle.  One block of four warps per (matrix, 32 right-hand
+// sides); step k updates the rows below (above) k, split over the warps by row mod 4.
+constexpr int kRhsWarps = 4;
+
+template <bool LOWER>
+__global__ void __launch_bounds__(kRhsWarps * 32) trsv_rhs_kernel(const RsLaunch a, int J, int W) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* tri = reinterpret_cast<double2*>(smem_raw);  // kBlk x kBlk, column-major
+  double2* xs = tri + kBlk * kBlk;                       // kBlk x 32: row i, lane l at i * 32 + l
+  double2* dinv = xs + kBlk * 32;                        // kBlk
+  const RsJob jb = a.jobs[blockIdx.x];
+  const int n = jb.n;
+  if (n > a.max_n || J >= n) return;  // uniform per block
+  const int w = min(W, n - J);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int c0 = blockIdx.y * 32;
+  if (c0 >= jb.nrhs) return;  // uniform per block
+  const double2* A = a.abase + jb.a_off + J + (long long)J * jb.lda;
+  double2* B = a.bbase + jb.b_off + J;
+  for (int e = tid; e < kBlk * w; e += kRhsWarps * 32) {
+    const int r = e % kBlk, q = e / kBlk;
+    tri[e] = r < w ? A[r + (long long)q * jb.lda] : make_double2(0.0, 0.0);
+  }
+  if (!LOWER)
+    for (int i = tid; i < w; i += kRhsWarps * 32) dinv[i] = cinv(A[i + (long long)i * jb.lda]);
+  // the 32 right-hand sides' rows of the block (reads along columns)
+  for (int e = tid; e < w * 32; e += kRhsWarps * 32) {
+    const int i = e % w, cl = e / w, col = c0 + cl;
+    xs[i * 32 + cl] = col < jb.nrhs ? B[i + (long long)col * jb.ldb] : make_double2(0.0, 0.0);
+  }
+  if (LOWER) {
+    for (int k = 0; k < w; ++k) {
+      __syncthreads();  // row k is final
+      const double2 xk = xs[k * 32 + lane];
+      for (int i = k + 1 + ((warp - (k + 1)) & (kRhsWarps - 1)); i < w; i += kRhsWarps)
+        xs[i * 32 + lane] = cfms(tri[i + k * kBlk], xk, xs[i * 32 + lane]);
+    }
+  } else {
+    for (int k = w - 1; k >= 0; --k) {
+      __syncthreads();  // row k is final up to its diagonal
+      const double2 xk = cmul(xs[k * 32 + lane], dinv[k]);
+      __syncthreads();  // every warp has read row k before its owner rewrites it
+      if ((k & (kRhsWarps - 1)) == warp) xs[k * 32 + lane] = xk;
+      const int d = (k - warp) & (kRhsWarps - 1);  // the own rows below k: k - d, k - d - 4, ...
+      for (int i = k - (d ? d : kRhsWarps); i >= 0; i -= kRhsWarps)
+        xs[i * 32 + lane] = cfms(tri[i + k * kBlk], xk, xs[i * 32 + lane]);
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < w * 32; e += kRhsWarps * 32) {
+    const int i = e % w, cl = e / w, col = c0 + cl;
+    if (col < jb.nrhs) B[i + (long long)col * jb.ldb] = xs[i * 32 + cl];
+  }
+}
+
 cudaError_t getrs_blocked_tc(const RsLaunch& a, cudaStream_t s) {
   const int max_n = a.max_n;
   int warps = kRsMaxWarps;
@@ -493,11 +551,19 @@ cudaError_t getrs_blocked_tc(const RsLaunch& a, cudaStream_t s) {
   }
   if (psmem > 200 * 1024) return cudaErrorInvalidValue;
   const size_t tsmem = (size_t)(kBlk * kBlk + kBlk + warps * kBlk) * sizeof(double2);
+  // many blocks: the diagonal solves with the right-hand sides on the lanes
+  const bool rhs_lanes = a.njobs >= 32;
+  const size_t rsmem = (size_t)(kBlk * kBlk + kBlk * 32 + kBlk) * sizeof(double2);
+  const dim3 rgrid(a.njobs, (a.max_rhs + 31) / 32);
   cudaError_t e = cudaFuncSetAttribute(permute_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(trsv_block_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(trsv_block_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem);
+  if (e == cudaSuccess && rhs_lanes)
+    e = cudaFuncSetAttribute(trsv_rhs_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem);
+  if (e == cudaSuccess && rhs_lanes)
+    e = cudaFuncSetAttribute(trsv_rhs_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem);
   if (e != cudaSuccess) return e;
   const dim3 grid(a.njobs, (a.max_rhs + warps - 1) / warps);
   permute_kernel<<<grid, warps * 32, psmem, s>>>(a, warps);
@@ -518,7 +584,8 @@ cudaError_t getrs_blocked_tc(const RsLaunch& a, cudaStream_t s) {
   const int W = (a.blk == 16 || a.blk == 32) ? a.blk : kBlk;
   g.block_w = W;
   for (int J = 0; J < max_n; J += W) {
-    trsv_block_kernel<true><<<grid, warps * 32, tsmem, s>>>(a, J, warps, W);
+    if (rhs_lanes) trsv_rhs_kernel<true><<<rgrid, kRhsWarps * 32, rsmem, s>>>(a, J, W);
+    else trsv_block_kernel<true><<<grid, warps * 32, tsmem, s>>>(a, J, warps, W);
     symhss::count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int below = max_n - J - W;
@@ -532,7 +599,8 @@ cudaError_t getrs_blocked_tc(const RsLaunch& a, cudaStream_t s) {
   }
   // backward: U x = y from the last block; the rows above a block are updated on the tensor cores
   for (int J = ((max_n - 1) / W) * W; J >= 0; J -= W) {
-    trsv_block_kernel<false><<<grid, warps * 32, tsmem, s>>>(a, J, warps, W);
+    if (rhs_lanes) trsv_rhs_kernel<false><<<rgrid, kRhsWarps * 32, rsmem, s>>>(a, J, W);
+    else trsv_block_kernel<false><<<grid, warps * 32, tsmem, s>>>(a, J, warps, W);
     symhss::count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (J > 0) {
