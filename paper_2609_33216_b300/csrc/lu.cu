@@ -540,6 +540,55 @@ __global__ void __launch_bounds__(kRhsWarps * 32) trsv_rhs_kernel(const RsLaunch
   }
 }
 
+// The whole solve of a block of at most kBlk rows with the right-hand sides on the lanes
+// (the many small k x k blocks of Atilde at the lower levels): x = P b, then the unit lower
+// and the upper solve, in shared memory, four warps splitting the rows of each step.
+__global__ void __launch_bounds__(kRhsWarps * 32) getrs_rhs_small_kernel(const RsLaunch a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* tri = reinterpret_cast<double2*>(smem_raw);  // kBlk x kBlk, column-major (the LU factors)
+  double2* xs = tri + kBlk * kBlk;                       // kBlk x 32
+  double2* dinv = xs + kBlk * 32;                        // kBlk
+  int* perm = reinterpret_cast<int*>(dinv + kBlk);       // kBlk
+  const RsJob jb = a.jobs[blockIdx.x];
+  const int n = jb.n;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int c0 = blockIdx.y * 32;
+  if (n > kBlk || n > a.max_n || n <= 0 || c0 >= jb.nrhs) return;  // uniform per block
+  const double2* A = a.abase + jb.a_off;
+  double2* B = a.bbase + jb.b_off;
+  load_perm(perm, a, jb, n);
+  for (int e = tid; e < kBlk * n; e += kRhsWarps * 32) {
+    const int r = e % kBlk, q = e / kBlk;
+    tri[e] = r < n ? A[r + (long long)q * jb.lda] : make_double2(0.0, 0.0);
+  }
+  for (int i = tid; i < n; i += kRhsWarps * 32) dinv[i] = cinv(A[i + (long long)i * jb.lda]);
+  __syncthreads();
+  for (int e = tid; e < n * 32; e += kRhsWarps * 32) {
+    const int i = e % n, cl = e / n, col = c0 + cl;
+    xs[i * 32 + cl] = col < jb.nrhs ? B[perm[i] + (long long)col * jb.ldb] : make_double2(0.0, 0.0);
+  }
+  for (int k = 0; k < n; ++k) {  // unit lower
+    __syncthreads();
+    const double2 xk = xs[k * 32 + lane];
+    for (int i = k + 1 + ((warp - (k + 1)) & (kRhsWarps - 1)); i < n; i += kRhsWarps)
+      xs[i * 32 + lane] = cfms(tri[i + k * kBlk], xk, xs[i * 32 + lane]);
+  }
+  for (int k = n - 1; k >= 0; --k) {  // upper
+    __syncthreads();
+    const double2 xk = cmul(xs[k * 32 + lane], dinv[k]);
+    __syncthreads();
+    if ((k & (kRhsWarps - 1)) == warp) xs[k * 32 + lane] = xk;
+    const int d = (k - warp) & (kRhsWarps - 1);
+    for (int i = k - (d ? d : kRhsWarps); i >= 0; i -= kRhsWarps)
+      xs[i * 32 + lane] = cfms(tri[i + k * kBlk], xk, xs[i * 32 + lane]);
+  }
+  __syncthreads();
+  for (int e = tid; e < n * 32; e += kRhsWarps * 32) {
+    const int i = e % n, cl = e / n, col = c0 + cl;
+    if (col < jb.nrhs) B[i + (long long)col * jb.ldb] = xs[i * 32 + cl];
+  }
+}
+
 cudaError_t getrs_blocked_tc(const RsLaunch& a, cudaStream_t s) {
   const int max_n = a.max_n;
   int warps = kRsMaxWarps;
@@ -630,6 +679,15 @@ cudaError_t getrs_impl(const RsLaunch& a, cudaStream_t s) {
   if (sizeof(CT) == sizeof(double2) && use_tc && a.status && a.max_rhs > 4 &&
       max_n > ((a.blk == 16 || a.blk == 32) ? a.blk : kBlk))
     return getrs_blocked_tc(a, s);
+  if (sizeof(CT) == sizeof(double2) && a.max_rhs > 4 && max_n <= kBlk && a.njobs >= 32) {
+    // many small blocks: the whole solve with the right-hand sides on the lanes
+    const size_t smem = (size_t)(kBlk * kBlk + kBlk * 32 + kBlk) * sizeof(double2) + kBlk * sizeof(int);
+    e = cudaFuncSetAttribute(getrs_rhs_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    getrs_rhs_small_kernel<<<dim3(a.njobs, (a.max_rhs + 31) / 32), kRhsWarps * 32, smem, s>>>(a);
+    symhss::count_launches(1);
+    return cudaGetLastError();
+  }
   if (a.max_rhs <= 4 && sizeof(CT) == sizeof(double2) && max_n >= 128) {
     // few large blocks: a cluster per (matrix, right-hand side) while the SMs allow
     const int nb = (max_n + 31) / 32;
