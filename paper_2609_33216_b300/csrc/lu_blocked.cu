@@ -343,11 +343,12 @@ __global__ void __launch_bounds__(kClusterPanelThreads) panel_cluster_kernel(con
   }
 }
 
-// Row interchanges of a panel and, right of it, L11 U12 = A12: two columns per warp.
+// Row interchanges of a panel and, right of it, L11 U12 = A12, for 32 columns per block.
 // The panel's w interchanges touch at most 2w rows; their composition is a
 // permutation of that row set, built once per block, so each column is permuted by
-// a single gather (lane l ends with the value of row rows[l]); lanes 0..w-1 hold
-// rows j..j+w-1 and then solve the unit-lower 16 x 16 system with shuffles.
+// a single gather (lane l ends with the value of row rows[l]); rows j..j+w-1 of the 32
+// columns then go through shared memory to the unit-lower 16 x 16 solve, which runs with
+// one column per lane.
 // tlo, thi: the solve covers only columns in [max(j + w, tlo), thi); swaps = 0: no
 // interchanges (the columns are already permuted); cbase: first column of blockIdx.y = 0.
 template <typename CT>
@@ -406,40 +407,41 @@ __global__ void __launch_bounds__(256) swap_trsm_warp_kernel(const LuLaunch a, i
     }
   }
   __syncthreads();
+  __shared__ CT xs[kNb][32];  // rows j .. j + w - 1 of the block's 32 columns, after the interchanges
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int col0 = cbase + (blockIdx.y * 8 + warp) * 2;  // two columns per warp
   const int cnt = nrows_s;
   const int tl = max(j + w, tlo), th = min(thi, n);
+  const int cfirst = cbase + blockIdx.y * 32;
   // a column takes part if it is interchanged, or (without interchanges) if it is solved
-  const bool v0 = col0 < n && !(col0 >= j && col0 < j + w) && (swaps || (col0 >= tl && col0 < th));
-  const bool v1 = col0 + 1 < n && !(col0 + 1 >= j && col0 + 1 < j + w) && (swaps || (col0 + 1 >= tl && col0 + 1 < th));
-  if (!v0 && !v1) return;  // uniform per warp
-  // interchanges: the full warp permutes one column at a time
-  CT x[2];
-#pragma unroll
-  for (int hc = 0; hc < 2; ++hc) {
-    x[hc] = make_c<CT>(0.0, 0.0);
-    if (!(hc ? v1 : v0)) continue;  // uniform per warp
-    CT* cc = A + (long long)(col0 + hc) * ld;
+  auto part = [&](int col) {
+    return col < n && !(col >= j && col < j + w) && (swaps || (col >= tl && col < th));
+  };
+  // interchanges: one column per warp at a time, the lanes over the row set
+  for (int cl = warp; cl < 32; cl += 8) {
+    const int col = cfirst + cl;
+    if (!part(col)) continue;  // uniform per warp
+    CT* cc = A + (long long)col * ld;
     const CT xv = lane < cnt ? cc[src_s[lane]] : make_c<CT>(0.0, 0.0);
     __syncwarp();
     if (swaps && lane >= w && lane < cnt) cc[rows_s[lane]] = xv;
-    x[hc] = xv;
+    if (lane < w) xs[lane][cl] = xv;
   }
-  // L11 U12 = A12 for both columns in one pass: lanes 0-15 hold rows j..j+w-1 of the
-  // first column, lanes 16-31 those of the second (half the FP64 issue of one column a warp)
-  const int half = lane >> 4, r = lane & 15;
-  const CT up = make_c<CT>(__shfl_sync(0xffffffffu, x[1].x, r), __shfl_sync(0xffffffffu, x[1].y, r));
-  CT v = half ? up : x[0];
-  const int col = col0 + half;
-  const bool mine = half ? v1 : v0;
-  const bool trsm = mine && col >= tl && col < th;
+  // L11 U12 = A12 with the 32 columns on the lanes (every lane of an FP64 instruction works),
+  // rows split over warps 0..3 by row mod 4
+  const int col = cfirst + lane;
+  const bool solve = col >= tl && col < th;
   for (int c = 0; c < w; ++c) {
-    const int src = (lane & 16) | c;
-    const CT vc = make_c<CT>(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
-    if (trsm && r > c && r < w) v = cfms(l11[r][c], vc, v);
+    __syncthreads();  // row c is final
+    if (warp < 4 && solve) {
+      const CT xc = xs[c][lane];
+      for (int r = c + 1 + ((warp - (c + 1)) & 3); r < w; r += 4) xs[r][lane] = cfms(l11[r][c], xc, xs[r][lane]);
+    }
   }
-  if (mine && r < w) A[(long long)col * ld + j + r] = v;
+  __syncthreads();
+  for (int e = threadIdx.x; e < 32 * w; e += 256) {
+    const int r = e % w, cl = e / w;
+    if (part(cfirst + cl)) A[(long long)(cfirst + cl) * ld + j + r] = xs[r][cl];
+  }
 }
 
 // A22 -= L21 U12 for the tile (blockIdx.y, blockIdx.z) of every matrix, over the trailing
@@ -559,7 +561,7 @@ cudaError_t getrf_impl(const LuLaunch& a, cudaStream_t s) {
       e = cudaFuncSetAttribute(panel_smem_kernel<1024, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem);
     if (e != cudaSuccess) return e;
   }
-  const int ncolblk = (a.max_n + 15) / 16;  // 16 columns per block of the interchange kernel
+  const int ncolblk = (a.max_n + 31) / 32;  // 32 columns per block of the interchange kernel
   // Depth-1 look-ahead: after the interchanges and TRSM of panel j, the first trailing
   // tile column (which holds panel j + kNb) is updated first; panel j + kNb then runs on
   // a high-priority side stream while the rest of the trailing update runs on s.  The two
@@ -646,7 +648,7 @@ cudaError_t getrf_impl(const LuLaunch& a, cudaStream_t s) {
       if (j + kNb == J + kOuter && right > 0) {
         // the block's U rows for the columns right of it, now that all its interchanges are
         // applied: 16-row solves, each followed by the update of the block rows below it
-        const int rblk = (right + 15) / 16;  // blocks of 16 columns starting at J + kOuter
+        const int rblk = (right + 31) / 32;  // blocks of 32 columns starting at J + kOuter
         for (int jj = J; kOuter > kNb && jj < J + kOuter; jj += kNb) {
           swap_trsm_warp_kernel<CT><<<dim3(a.njobs, rblk), 256, 0, s>>>(a, jj, J + kOuter, a.max_n, 0, J + kOuter);
           symhss::count_launches(1);
