@@ -229,7 +229,10 @@ struct TileJob {
   int prm;                 // index of this job's physical constants in TileLaunch::kps
   int pad_;
 };
-enum : int { TILE_SRC_IS_THREAD = 1, TILE_UNSCALED = 2 };
+// TILE_SYM_DIAG: a symmetric diagonal block whose thread points are its loop points (same
+// list): only pairs j >= i are evaluated and each j > i is written twice, once transposed
+// (the symmetric system's matrix is exactly symmetric off the node diagonal)
+enum : int { TILE_SRC_IS_THREAD = 1, TILE_UNSCALED = 2, TILE_SYM_DIAG = 4 };
 
 struct TileChunk { int job, t0, l0, ln; };  // ln: loop points of this chunk (<= TILE_L)
 

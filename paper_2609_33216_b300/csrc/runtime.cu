@@ -496,7 +496,7 @@ struct TileBuilder {
     jb.pad_ = 0;
     if (jb.n_tp == 0 || jb.n_lp == 0) return;
     jobs.push_back(jb);
-    pairs += (long long)jb.n_tp * jb.n_lp;
+    pairs += (flags & TILE_SYM_DIAG) ? (long long)jb.n_tp * (jb.n_tp + 1) / 2 : (long long)jb.n_tp * jb.n_lp;
   }
   // chunks of TILE_T thread points x ln loop points; a launch that would leave most SMs
   // idle uses shorter loop chunks (more blocks, each with less work)
@@ -510,7 +510,11 @@ struct TileBuilder {
     chunks.clear();
     for (int j = 0; j < (int)jobs.size(); ++j)
       for (int a = 0; a < jobs[j].n_tp; a += TILE_T)
-        for (int b = 0; b < jobs[j].n_lp; b += ln) chunks.push_back(TileChunk{j, a, b, ln});
+        for (int b = 0; b < jobs[j].n_lp; b += ln) {
+          // a symmetric diagonal block: no chunk whose loop points all precede its thread points
+          if ((jobs[j].flags & TILE_SYM_DIAG) && b + ln <= a) continue;
+          chunks.push_back(TileChunk{j, a, b, ln});
+        }
   }
   cudaError_t launch(symhss_s* h, DevBuf& buf, double2* out, cudaStream_t s) {
     if (jobs.empty()) return cudaSuccess;
@@ -1224,7 +1228,8 @@ int assemble_and_lu(symhss_s* h, int t, cudaStream_t s, long long& pairs) {
       std::vector<int> ids(bx.end - bx.begin);
       for (int i = 0; i < (int)ids.size(); ++i) ids[i] = bx.begin + i;
       const int nb = (int)ids.size();
-      tb.add(h->mark, ids, 0, ids, nb, ids, 0, ids, nb, bx.d_off, bx.size, flags, rf.p);
+      // the leaf block is symmetric off its node diagonal in the symmetric system: one triangle
+      tb.add(h->mark, ids, 0, ids, nb, ids, 0, ids, nb, bx.d_off, bx.size, sym ? flags | TILE_SYM_DIAG : flags, rf.p);
     } else {
       const auto& kids = h->probs[rf.p].levels[rf.l + 1];
       const HBox& c1 = kids[bx.child[0]];

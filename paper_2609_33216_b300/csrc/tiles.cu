@@ -200,7 +200,9 @@ __global__ void __launch_bounds__(TILE_T) tile_kernel(const TileLaunch a) {
   const KernelParams kp = a.kps[jb.prm];
   if (ts0 >= jb.ld || ts1 >= jb.ld) { atomicOr(a.status, ST_BAD_INDEX); return; }
   double2* out = a.out + jb.out_off;
+  const bool symd = (jb.flags & TILE_SYM_DIAG) != 0 && !src_thread;
   for (int l = 0; l < nl; ++l) {
+    if (symd && ch.l0 + l < ti) continue;  // the pair (j, i) of j < i is written by thread j
     P7 lp;
     lp.x = sx[l]; lp.y = sy[l]; lp.nx = snx[l]; lp.ny = sny[l]; lp.w = sw[l]; lp.kappa = sk[l]; lp.hs = shs[l];
     lp.id = sid[l];
@@ -220,6 +222,14 @@ __global__ void __launch_bounds__(TILE_T) tile_kernel(const TileLaunch a) {
         const int col = src_thread ? lsl[e] : lsl[c];
         if (row >= 0 && col >= 0) out[row + (long long)col * jb.ld] = blk[e * 2 + c];
       }
+    }
+    if (symd && ch.l0 + l != ti) {
+      // the transposed position of every entry (the pair (j, i))
+#pragma unroll
+      for (int e = 0; e < 2; ++e)
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+          if (tsl[e] >= 0 && lsl[c] >= 0) out[lsl[c] + (long long)tsl[e] * jb.ld] = blk[e * 2 + c];
     }
   }
 }
