@@ -21,20 +21,21 @@
 // FP64 and scaled by a power of two: a few FP64 operations per real output instead of 4k FMAs.
 //
 // Kernels.  A launch is two kernels.  The slicing kernel cuts every 128-row block of A' and
-// every 32-column block of B' once, in 16-column chunks of k, into the core-matrix order the MMA
-// reads (eight slices per chunk, 64 KB for A', 32 KB for B'), in a scratch buffer the caller
-// provides, together with the row and column exponents.  The product kernel then computes one
-// 128 x 32 complex tile of C per thread block of 512 threads: one thread streams the tile's
-// chunk images into two 96 KB shared-memory stages by bulk copies (cp.async.bulk, completing on
-// an mbarrier) and issues the 36 slice-pair products per K-step as 12 MMAs (M = 128, K = 16,
-// N = 64 per B slice, up to four B slices per MMA; bf16 x bf16 -> FP32) into the eight groups
-// of a 512-column tensor-memory accumulator; the copy of
-// chunk c + 1 overlaps the MMAs of chunk c.  The epilogue rounds T 2^(e_i + f_c - 2107) to FP64
-// by integer operations (one FP64 addition per real output for C -= AB and C += AB, none for
-// C = AB).  Every wait is bounded by %globaltimer; after a timeout the block waits once more
-// (bounded) for its copies and MMAs in flight, records ST_TIMEOUT, frees its tensor memory and
-// exits.  A test hook (set_zgemm_timeout_probe) makes the last wait target a phase that no
-// commit completes, so that this path can be exercised on purpose.
+// every 16-column block of B' once, in 16-column chunks of k, into the core-matrix order the
+// MMA reads (eight slices per chunk, 64 KB for A', 16 KB for B'), in a scratch buffer the
+// caller provides, together with the row and column exponents.  The product kernel then
+// computes one 128 x 16 complex tile of C per thread block of 256 threads, two blocks per SM
+// (256 tensor-memory columns, one 80 KB stage and 32K registers each), so that one block's
+// epilogue overlaps the other's copies and MMAs.  One thread streams the tile's chunk images
+// into the stage by bulk copies (cp.async.bulk, completing on an mbarrier) and issues the 36
+// slice-pair products per K-step as 8 MMAs (M = 128, K = 16, N = 32 per B slice, the B slices
+// j = 0 .. 7 - i of A slice i in one MMA; bf16 x bf16 -> FP32) into the eight groups of the
+// accumulator.  The epilogue rounds T 2^(e_i + f_c - 2107) to FP64 by integer operations
+// (one FP64 addition per real output for C -= AB and C += AB, none for C = AB).  Every wait is
+// bounded by %globaltimer; after a timeout the block waits once more (bounded) for its copies
+// and MMAs in flight, records ST_TIMEOUT, frees its tensor memory and exits.  A test hook
+// (set_zgemm_timeout_probe) makes the last wait target a phase that no commit completes, so
+// that this path can be exercised on purpose.
 #include <stdint.h>
 
 #include "common.cuh"
@@ -43,20 +44,20 @@ namespace symhss {
 
 namespace {
 
-constexpr int kMmaThreads = 512;  // product kernel (16 warps share the epilogue)
+constexpr int kMmaThreads = 256;  // product kernel (8 warps share the epilogue; two blocks per SM)
 constexpr int kTileM = 128;       // rows of C per block
-constexpr int kTileNc = 32;       // complex columns of C per block
+constexpr int kTileNc = 16;       // complex columns of C per block
 constexpr int kNr = 2 * kTileNc;  // real columns of B' (MMA N)
 constexpr int kSlices = 8;
 constexpr int kGroups = 8;
 constexpr int kChunkK = 16;                        // complex k per chunk (32 columns of A')
 constexpr int kASliceBytes = kTileM * 32 * 2;      // 8192: one slice of the A' chunk
-constexpr int kBSliceBytes = kNr * 32 * 2;         // 4096: one slice of the B' chunk
+constexpr int kBSliceBytes = kNr * 32 * 2;         // 2048: one slice of the B' chunk
 constexpr int kAChunkBytes = kSlices * kASliceBytes;               // 65536: A' chunk image
-constexpr int kBChunkBytes = kSlices * kBSliceBytes;               // 32768: B' chunk image
-constexpr int kStageBytes = kAChunkBytes + kBChunkBytes;           // 98304
+constexpr int kBChunkBytes = kSlices * kBSliceBytes;               // 16384: B' chunk image
+constexpr int kStageBytes = kAChunkBytes + kBChunkBytes;           // 81920
 constexpr int kMaxChunks = 4;                                      // k <= 64
-constexpr int kTmemCols = kGroups * kNr;           // 512
+constexpr int kTmemCols = kGroups * kNr;           // 256: two blocks per SM share the 512 columns
 constexpr long long kWaitNs = 200ll * 1000 * 1000;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -303,8 +304,9 @@ __global__ void __launch_bounds__(kSliceThreads) zslice_kernel(const ZgemmLaunch
   const int n = jb.n, K = jb.k;
   const double2* B = a.B + jb.b_off;
   // thread (c, ch, comp, kh): component comp (Re / Im) of b(16 ch + 8 kh .. + 7, c0 + c); the
-  // 16 threads of a column are 16 consecutive lanes
+  // 16 threads of a column are 16 consecutive lanes (whole warps beyond the block's columns)
   const int c = tid >> 4, ch = (tid >> 2) & 3, comp = (tid >> 1) & 1, kh = tid & 1;
+  if (c >= kTileNc) return;
   const int col = c0 + c;
   double x[8];
   int fb = 0;
@@ -345,7 +347,7 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
                :: "r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
 }
 
-__global__ void __launch_bounds__(kMmaThreads, 1) zgemm_tc_kernel(const ZgemmLaunch a) {
+__global__ void __launch_bounds__(kMmaThreads, 2) zgemm_tc_kernel(const ZgemmLaunch a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar_mma[2];
   __shared__ __align__(8) uint64_t bar_load[2];
@@ -385,7 +387,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) zgemm_tc_kernel(const ZgemmLau
   if (a.mode != ZGEMM_SET && warp == 1) {
     // the old values of the tile's columns into L2 while the MMAs run (one column per lane)
     const int col = c0 + lane, rows = min(kTileM, m - r0);
-    if (col < n && rows > 0)
+    if (lane < kTileNc && col < n && rows > 0)
       asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;"
                    :: "l"(C + r0 + (long long)col * jb.ldc), "r"((uint32_t)(rows * sizeof(double2))) : "memory");
   }
@@ -417,51 +419,44 @@ __global__ void __launch_bounds__(kMmaThreads, 1) zgemm_tc_kernel(const ZgemmLau
     const uint32_t sbase = smem_u32(smem);
     int issued = 0, waited = 0, fail = 0;
     auto issue = [&](int ch) {
-      const int st = ch & 1;
-      const uint32_t bar = smem_u32(&bar_load[st]);
+      const uint32_t bar = smem_u32(&bar_load[0]);
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(kStageBytes) : "memory");
-      bulk_load(sbase + st * kStageBytes, gA + (size_t)ch * kAChunkBytes, kAChunkBytes, bar);
-      bulk_load(sbase + st * kStageBytes + kAChunkBytes, gB + (size_t)ch * kBChunkBytes, kBChunkBytes, bar);
+      bulk_load(sbase, gA + (size_t)ch * kAChunkBytes, kAChunkBytes, bar);
+      bulk_load(sbase + kAChunkBytes, gB + (size_t)ch * kBChunkBytes, kBChunkBytes, bar);
       issued = ch + 1;
     };
     issue(0);
-    if (nch > 1) issue(1);
     for (int ch = 0; ch < nch; ++ch) {
-      const int st = ch & 1;
-      if (!mbar_wait(smem_u32(&bar_load[st]), (uint32_t)((ch >> 1) & 1), a.wait_ns)) { fail = 1; break; }
+      if (!mbar_wait(smem_u32(&bar_load[0]), (uint32_t)(ch & 1), a.wait_ns)) { fail = 1; break; }
       waited = ch + 1;
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t sA = sbase + st * kStageBytes, sB = sA + kAChunkBytes;
+      const uint32_t sA = sbase, sB = sA + kAChunkBytes;
       // descriptors differ only in their address field (address / 16 < 2^14 in shared memory)
       const uint64_t ad0 = make_desc(sA, 128, 512), bd0 = make_desc(sB, 128, 512);
 #pragma unroll
       for (int kk = 0; kk < 2; ++kk) {
-        // A slice i times B slices j0 .. j0 + nb - 1 in one MMA of N = 64 nb: the B slices lie
+        // A slice i times B slices 0 .. 7 - i in one MMA of N = 32 (8 - i): the B slices lie
         // next to each other along N (same 512-byte stride between 8-row groups), and so do the
-        // accumulator groups i + j0 .. i + j0 + nb - 1 in tensor memory; slice pairs with
-        // i + j >= 8 are never formed
+        // accumulator groups i .. 7 in tensor memory; slice pairs with i + j >= 8 are never formed
 #pragma unroll
         for (int i = 0; i < kSlices; ++i) {
-#pragma unroll
-          for (int j0 = 0; j0 < kSlices - i; j0 += 4) {
-            const int nb = (kSlices - i - j0) < 4 ? (kSlices - i - j0) : 4;
-            const uint64_t ad = ad0 + (uint64_t)((i * kASliceBytes + kk * 256) >> 4);
-            const uint64_t bd = bd0 + (uint64_t)((j0 * kBSliceBytes + kk * 256) >> 4);
-            const uint32_t acc = (ch > 0 || kk > 0 || i > 0) ? 1u : 0u;  // i = 0 opens every group
-            asm volatile(
-                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                :: "r"(tmem + (uint32_t)((i + j0) * kNr)), "l"(ad), "l"(bd), "r"(make_idesc(kTileM, kNr * nb)),
-                   "r"(acc));
-          }
+          const int nb = kSlices - i;
+          const uint64_t ad = ad0 + (uint64_t)((i * kASliceBytes + kk * 256) >> 4);
+          const uint64_t bd = bd0 + (uint64_t)((kk * 256) >> 4);
+          const uint32_t acc = (ch > 0 || kk > 0 || i > 0) ? 1u : 0u;  // i = 0 opens every group
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+              :: "r"(tmem + (uint32_t)(i * kNr)), "l"(ad), "l"(bd), "r"(make_idesc(kTileM, kNr * nb)), "r"(acc));
         }
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                   :: "r"(smem_u32(&bar_mma[st])) : "memory");
+                   :: "r"(smem_u32(&bar_mma[0])) : "memory");
       s_last = ch;
-      if (ch >= 1 && ch + 1 < nch) {
-        // stage (ch + 1) % 2 held chunk ch - 1: wait for its MMAs, then copy chunk ch + 1
-        if (!mbar_wait(smem_u32(&bar_mma[(ch - 1) & 1]), (uint32_t)(((ch - 1) >> 1) & 1), a.wait_ns)) {
+      if (ch + 1 < nch) {
+        // one stage: the MMAs of chunk ch release it for chunk ch + 1 (the other block on this
+        // SM keeps the tensor pipe busy meanwhile)
+        if (!mbar_wait(smem_u32(&bar_mma[0]), (uint32_t)(ch & 1), a.wait_ns)) {
           fail = 1;
           break;
         }
@@ -470,7 +465,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) zgemm_tc_kernel(const ZgemmLau
     }
     if (fail) {
       // drain: every copy still in flight (bounded), before the stages are given up
-      for (int c = waited; c < issued; ++c) mbar_wait(smem_u32(&bar_load[c & 1]), (uint32_t)((c >> 1) & 1), kWaitNs);
+      for (int c = waited; c < issued; ++c) mbar_wait(smem_u32(&bar_load[0]), (uint32_t)(c & 1), kWaitNs);
       s_fail = 1;
     }
   }
@@ -478,8 +473,8 @@ __global__ void __launch_bounds__(kMmaThreads, 1) zgemm_tc_kernel(const ZgemmLau
   // wait for the last committed chunk (its commit covers every earlier MMA of the block)
   if (tid == 0 && s_last >= 0) {
     const int lc = s_last;
-    const uint32_t bar = smem_u32(&bar_mma[lc & 1]);
-    const uint32_t par = (uint32_t)((lc >> 1) & 1);
+    const uint32_t bar = smem_u32(&bar_mma[0]);
+    const uint32_t par = (uint32_t)(lc & 1);
     if (s_fail) {
       mbar_wait(bar, par, kWaitNs);  // drain the MMAs still in flight
     } else if (a.probe_timeout) {
@@ -603,7 +598,7 @@ cudaError_t launch_zgemm_tc(const ZgemmLaunch& a_in, cudaStream_t s) {
   symhss::count_launches(1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int smem = 2 * kStageBytes;
+  const int smem = kStageBytes;
   e = cudaFuncSetAttribute(zgemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   zgemm_tc_kernel<<<a.ntiles, kMmaThreads, smem, s>>>(a);
