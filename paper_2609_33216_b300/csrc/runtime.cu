@@ -707,8 +707,9 @@ int compress_height(symhss_s* h, int t, cudaStream_t s) {
   // Randomized sketch (Halko-Martinsson-Tropp): an ID job whose rank estimate plus
   // oversampling is well below its row count is taken of Y = Omega M instead of M.
   // Y blocks live after all proxy matrices in the same buffer.  Rank estimate: the
-  // network's proposal times the margin when a network is attached; else half the
-  // smaller dimension at the leaves, 1.7x the problem's largest rank one level down above.
+  // network's proposal times the margin when a network is attached; else, at the leaves,
+  // 3 log10(1/tol) + 2 k rho + 12 (at most half the smaller dimension), and above, 1.7x the
+  // problem's largest rank one level down.
   const std::vector<IdJob> full = jobs;  // the same IDs on the full proxy matrices
   std::vector<int> sk_rows(njobs, 0);
   std::vector<SketchJob> sk;
@@ -728,8 +729,15 @@ int compress_height(symhss_s* h, int t, cudaStream_t s) {
       else if (!prop.empty()) {
         const double r = std::exp2(8.0 * (double)prop[2 * bi + part]) - 1.0;
         est = (int)std::ceil(h->prop_margin * std::max(0.0, std::min(r, 1e6))) + 2;
-      } else if (t == 0) est = (std::min(j.m, j.n) + 1) / 2;
-      else est = (int)std::ceil(1.7 * std::max(8, h->probs[rf.p].lvl_max_rank[rf.l + 1][part]));
+      } else if (t == 0) {
+        // leaves: a box of radius rho sees about 2 k rho oscillations plus a few terms per
+        // decade of the tolerance (the proxy expansion's length); never above half the smaller
+        // dimension.  The held-out check and the redo path stay the judges of every ID.
+        const symhss_params& pp = h->probs[rf.p].prm;
+        const double kr = std::max(pp.k0, pp.k1) * rf.bx->rho;
+        const double dec = std::log10(1.0 / std::max(1e-300, h->prm.tol));
+        est = std::min((std::min(j.m, j.n) + 1) / 2, (int)std::ceil(3.0 * dec + 2.0 * kr) + 12);
+      } else est = (int)std::ceil(1.7 * std::max(8, h->probs[rf.p].lvl_max_rank[rf.l + 1][part]));
       const int sr = std::max(32, ((est + p_over + 15) / 16) * 16);
       const int stot = sr + kHoldRows;  // rows for the ID, then held-out rows for its check
       if (stot > 1024 || 5 * stot >= 4 * j.m) continue;
