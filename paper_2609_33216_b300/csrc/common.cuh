@@ -458,6 +458,8 @@ struct ZgemmLaunch {
   int block_w = 64;    // W: width of the column block J .. J + W of the derived jobs
   int mtiles = 0, ntiles_c = 0;  // row / column blocks per job (explicit jobs: the largest)
   int njobs = 0;                   // jobs of the launch
+  int inline_slice = 0;            // every job has k <= 16: each tile slices its own operands
+                                   // (no slicing launch, no images; img may be null)
   unsigned char* img = nullptr;    // scratch for the slice images (16-byte aligned),
   long long img_bytes = 0;         // at least zgemm_img_bytes(njobs, mtiles, ntiles_c)
   int probe_timeout = 0;           // set by launch_zgemm_tc (test hook, see set_zgemm_timeout_probe)

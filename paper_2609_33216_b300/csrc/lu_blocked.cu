@@ -668,6 +668,7 @@ cudaError_t getrf_impl(const LuLaunch& a, cudaStream_t s) {
         g.wait_ns = 0;
         g.derive = ZGEMM_LU_UPDATE;
         g.block_w = kOuter;
+        g.inline_slice = kOuter <= 16;  // one 16-column chunk: sliced by the product's tiles
         g.lu_jobs = a.jobs;
         g.njobs = a.njobs;
         g.img = a.zimg;

@@ -382,8 +382,10 @@ __global__ void __launch_bounds__(kMmaThreads, 2) zgemm_tc_kernel(const ZgemmLau
   const size_t ablk = (size_t)jidx * a.mtiles + mt, bblk = (size_t)jidx * a.ntiles_c + nt;
   const unsigned char* gA = L.a + ablk * kMaxChunks * kAChunkBytes;
   const unsigned char* gB = L.b + bblk * kMaxChunks * kBChunkBytes;
-  if (tid < kTileM) s_e[tid] = L.ea[ablk * kTileM + tid];
-  if (tid < kTileNc) s_fexp[tid] = L.fb[bblk * kTileNc + tid];
+  if (!a.inline_slice) {
+    if (tid < kTileM) s_e[tid] = L.ea[ablk * kTileM + tid];
+    if (tid < kTileNc) s_fexp[tid] = L.fb[bblk * kTileNc + tid];
+  }
   if (a.mode != ZGEMM_SET && warp == 1) {
     // the old values of the tile's columns into L2 while the MMAs run (one column per lane)
     const int col = c0 + lane, rows = min(kTileM, m - r0);
@@ -412,7 +414,97 @@ __global__ void __launch_bounds__(kMmaThreads, 2) zgemm_tc_kernel(const ZgemmLau
   const uint32_t tmem = tmem_base_s;
   const int nch = (K + kChunkK - 1) / kChunkK;
 
-  if (tid == 0) {
+  if (a.inline_slice) {
+    // one chunk (k <= 16): the block slices its own operands into the stage (row / column
+    // exponents over this chunk, which is all of k), no images and no slicing launch
+    __shared__ int s_eh[2][kTileM];
+    const int rt = tid & (kTileM - 1), half = tid >> 7;
+    const int row = r0 + rt;
+    const double2* A = a.A + jb.a_off;
+    const double2* B = a.B + jb.b_off;
+    double re[8], im[8];
+    int e = 0;
+#pragma unroll
+    for (int e8 = 0; e8 < 8; ++e8) {
+      const int k = 8 * half + e8;
+      const double2 v = (row < m && k < K) ? A[row + (long long)k * jb.lda] : make_double2(0.0, 0.0);
+      re[e8] = v.x;
+      im[e8] = v.y;
+      e = max(e, max(bexp(v.x), bexp(v.y)));
+    }
+    s_eh[half][rt] = e;
+    // B: thread (c, comp, kh) for tid < 64: component comp of b(8 kh .. + 7, c0 + c)
+    double xb[8];
+    const int cb = tid >> 2, comp = (tid >> 1) & 1, kh = tid & 1;
+    int fb = 0;
+    if (tid < 4 * kTileNc) {
+#pragma unroll
+      for (int e8 = 0; e8 < 8; ++e8) {
+        const int k = 8 * kh + e8;
+        const double2 v = (c0 + cb < n && k < K) ? B[k + (long long)(c0 + cb) * jb.ldb] : make_double2(0.0, 0.0);
+        xb[e8] = comp ? v.y : v.x;
+        fb = max(fb, bexp(xb[e8]));
+      }
+    }
+    if (warp < 2) {  // the column's largest over its four threads (lanes 4c .. 4c + 3)
+      fb = max(fb, __shfl_xor_sync(0xffffffffu, fb, 1));
+      fb = max(fb, __shfl_xor_sync(0xffffffffu, fb, 2));
+      if (tid < 4 * kTileNc && (tid & 3) == 0) s_fexp[cb] = fb;
+    }
+    __syncthreads();
+    const int ea = max(s_eh[0][rt], s_eh[1][rt]);
+    if (half == 0) s_e[rt] = ea;
+    unsigned char* sA = smem;
+#pragma unroll
+    for (int part = 0; part < 2; ++part) {
+      uint32_t pk[kSlices][4];
+      slice_pack8(part ? im : re, ea, pk);
+      const int q = half + 2 * part;
+#pragma unroll
+      for (int t = 0; t < kSlices; ++t)
+        *reinterpret_cast<uint4*>(sA + t * kASliceBytes + (rt >> 3) * 512 + q * 128 + (rt & 7) * 16) =
+            make_uint4(pk[t][0], pk[t][1], pk[t][2], pk[t][3]);
+    }
+    if (tid < 4 * kTileNc) {
+      unsigned char* sB = smem + kAChunkBytes;
+      const int np1 = 2 * cb + comp, q1 = kh, np2 = 2 * cb + 1 - comp, q2 = kh + 2;
+      const uint32_t flip2 = comp ? 0x80008000u : 0u;
+      uint32_t pk[kSlices][4];
+      slice_pack8(xb, s_fexp[cb], pk);
+#pragma unroll
+      for (int t = 0; t < kSlices; ++t) {
+        unsigned char* sl = sB + t * kBSliceBytes;
+        *reinterpret_cast<uint4*>(sl + (np1 >> 3) * 512 + q1 * 128 + (np1 & 7) * 16) =
+            make_uint4(pk[t][0], pk[t][1], pk[t][2], pk[t][3]);
+        *reinterpret_cast<uint4*>(sl + (np2 >> 3) * 512 + q2 * 128 + (np2 & 7) * 16) =
+            make_uint4(pk[t][0] ^ flip2, pk[t][1] ^ flip2, pk[t][2] ^ flip2, pk[t][3] ^ flip2);
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t sa = smem_u32(smem), sb = sa + kAChunkBytes;
+      const uint64_t ad0 = make_desc(sa, 128, 512), bd0 = make_desc(sb, 128, 512);
+#pragma unroll
+      for (int kk = 0; kk < 2; ++kk) {
+#pragma unroll
+        for (int i = 0; i < kSlices; ++i) {
+          const uint64_t ad = ad0 + (uint64_t)((i * kASliceBytes + kk * 256) >> 4);
+          const uint64_t bd = bd0 + (uint64_t)((kk * 256) >> 4);
+          const uint32_t acc = (kk > 0 || i > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+              :: "r"(tmem + (uint32_t)(i * kNr)), "l"(ad), "l"(bd), "r"(make_idesc(kTileM, kNr * (kSlices - i))),
+                 "r"(acc));
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                   :: "r"(smem_u32(&bar_mma[0])) : "memory");
+      s_last = 0;
+    }
+  } else if (tid == 0) {
     // one thread streams the chunk images and issues the MMAs: chunk c lives in stage c % 2;
     // the copy of chunk c + 1 (c >= 1) is issued once the MMAs of chunk c - 1 have released
     // its stage, so that it overlaps the MMAs of chunk c
@@ -589,15 +681,22 @@ long long zgemm_rs_img_bytes(int njobs, int max_n, int max_rhs) { return zgemm_i
 cudaError_t launch_zgemm_tc(const ZgemmLaunch& a_in, cudaStream_t s) {
   if (a_in.ntiles <= 0) return cudaSuccess;
   ZgemmLaunch a = a_in;
-  if (a.njobs <= 0 || a.mtiles <= 0 || a.ntiles_c <= 0 || !a.img ||
-      a.img_bytes < zgemm_img_bytes(a.njobs, a.mtiles, a.ntiles_c) || (reinterpret_cast<uintptr_t>(a.img) & 15))
+  if (a.njobs <= 0 || a.mtiles <= 0 || a.ntiles_c <= 0) return cudaErrorInvalidValue;
+  // tiles slice their own operands only where every k is one chunk: the LU update of a
+  // block of at most 16 columns (the kernel takes chunk 0 alone on that path)
+  if (a.inline_slice && !(a.derive == ZGEMM_LU_UPDATE && a.block_w > 0 && a.block_w <= kChunkK))
+    return cudaErrorInvalidValue;
+  if (!a.inline_slice && (!a.img || a.img_bytes < zgemm_img_bytes(a.njobs, a.mtiles, a.ntiles_c) ||
+                          (reinterpret_cast<uintptr_t>(a.img) & 15)))
     return cudaErrorInvalidValue;
   a.wait_ns = g_zgemm_wait_ns;
   a.probe_timeout = g_zgemm_probe;
-  zslice_kernel<<<a.njobs * (a.mtiles + a.ntiles_c), kSliceThreads, 0, s>>>(a);
-  symhss::count_launches(1);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
+  if (!a.inline_slice) {
+    zslice_kernel<<<a.njobs * (a.mtiles + a.ntiles_c), kSliceThreads, 0, s>>>(a);
+    symhss::count_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   const int smem = kStageBytes;
   e = cudaFuncSetAttribute(zgemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
