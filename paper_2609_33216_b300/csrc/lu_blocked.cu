@@ -370,40 +370,42 @@ __global__ void __launch_bounds__(256) swap_trsm_warp_kernel(const LuLaunch a, i
     l11[r][c] = A[j + r + (long long)(j + c) * ld];
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    int cnt = w;
-    for (int r = 0; r < w; ++r) rows_s[r] = j + r;
-    for (int c = 0; c < w; ++c) {
-      const int p = piv_s[c];
-      if (p >= j + w) {
-        bool seen = false;
-        for (int q = w; q < cnt; ++q) seen |= (rows_s[q] == p);
-        if (!seen && cnt < 2 * kNb) rows_s[cnt++] = p;
-      }
-    }
-    // content[l] = original row currently stored at rows_s[l]; apply the swaps in order
-    int content[2 * kNb];
-    for (int l = 0; l < cnt; ++l) content[l] = rows_s[l];
+  if (threadIdx.x < 32) {
+    // warp 0, lane c for column c of the panel (a serial thread here cost more than the rest
+    // of the kernel): the row set is rows j .. j + w - 1, then each pivot row outside them
+    // once, in column order
+    const unsigned full = 0xffffffffu;
+    const int l = threadIdx.x;
+    const int p = l < w ? piv_s[l] : -1;
+    const unsigned same = __match_any_sync(full, p);
+    const int lead = __ffs(same) - 1;  // lowest lane with the same pivot row
+    const bool outside = l < w && p >= j + w;
+    const unsigned fm = __ballot_sync(full, outside && lead == l);
+    const int cnt = w + __popc(fm);
+    if (outside && lead == l) rows_s[w + __popc(fm & ((1u << l) - 1))] = p;
+    if (l < w) rows_s[l] = j + l;
+    // position of column l's pivot row in the set (-1: none, which a valid pivot never gives)
+    int lp = -1;
+    if (l < w && p >= j) lp = p < j + w ? p - j : w + __popc(fm & ((1u << lead) - 1));
+    __syncwarp();
+    // content (lane l): the original row whose values end at rows_s[l]; the interchanges in order
+    int content = l < cnt ? rows_s[l] : 0;
     for (int c = 0; swaps && c < w; ++c) {
-      const int p = piv_s[c];
-      if (p == j + c) continue;
-      int lp = -1;
-      for (int q = 0; q < cnt; ++q)
-        if (rows_s[q] == p) lp = q;
-      if (lp < 0) continue;  // cannot happen: every pivot row is in the set
-      const int t = content[c];
-      content[c] = content[lp];
-      content[lp] = t;
+      const int lpc = __shfl_sync(full, lp, c);
+      if (lpc < 0 || lpc == c) continue;  // uniform
+      const int vc = __shfl_sync(full, content, c);
+      const int vp = __shfl_sync(full, content, lpc);
+      if (l == c) content = vp;
+      else if (l == lpc) content = vc;
     }
-    for (int l = 0; l < cnt; ++l) src_s[l] = content[l];
-    nrows_s = cnt;
+    if (l < cnt) src_s[l] = content;
+    if (l == 0) nrows_s = cnt;
     // the same interchanges on the kept row permutation (once per panel: the first column block)
     if (swaps && a.perm && blockIdx.y == 0) {
       int* pm = a.perm + jb.piv_off;
-      for (int c = 0; c < w; ++c) {
-        const int p = piv_s[c];
-        if (p != j + c && p >= 0 && p < n) { const int t = pm[j + c]; pm[j + c] = pm[p]; pm[p] = t; }
-      }
+      const int v = l < cnt ? pm[content] : 0;
+      __syncwarp();
+      if (l < cnt) pm[rows_s[l]] = v;
     }
   }
   __syncthreads();
