@@ -144,6 +144,23 @@ __device__ __forceinline__ void warp_argmax_key(long long& k, int& i, int& x) {
     if (ok > k || (ok == k && oi < i)) { k = ok; i = oi; x = ox; }
   }
 }
+// the same result (all lanes) through warp reductions instead of five shuffle rounds: the
+// largest key as two 32-bit maxima (high word, then the low word among the lanes holding it;
+// key + 1 so that "no candidate" = -1 maps to 0), then the lowest index among the lanes
+// holding that key, then the payload of the lane holding both
+__device__ __forceinline__ void warp_argmax_key_redux(long long& k, int& i, int& x) {
+  const unsigned full = 0xffffffffu;
+  const unsigned long long u = (unsigned long long)(k + 1);
+  const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
+  const unsigned mh = __reduce_max_sync(full, hi);
+  const unsigned ml = __reduce_max_sync(full, hi == mh ? lo : 0u);
+  const bool top = hi == mh && lo == ml;
+  const int mi = __reduce_min_sync(full, top ? i : 0x7fffffff);
+  const unsigned win = __ballot_sync(full, top && i == mi);
+  x = __shfl_sync(full, x, __ffs(win) - 1);
+  k = (long long)(((unsigned long long)mh << 32) | ml) - 1;
+  i = mi;
+}
 
 // process-wide count of kernels this library has launched (diagnostics)
 void count_launches(long long n);

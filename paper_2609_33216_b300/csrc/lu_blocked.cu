@@ -219,8 +219,8 @@ __global__ void __launch_bounds__(kClusterPanelThreads) panel_cluster_kernel(con
   __shared__ long long redk[kWarps];
   __shared__ int redi[kWarps], redr[kWarps];
   __shared__ CandRow cand[2];
-  __shared__ int s_zero;
-  __shared__ double2 prow[kNb];
+  __shared__ int s_zero[2];
+  __shared__ double2 prow[2][kNb];  // pivot rows of the last two columns (by column parity)
   __shared__ double2 s_inv;
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
@@ -253,44 +253,61 @@ __global__ void __launch_bounds__(kClusterPanelThreads) panel_cluster_kernel(con
     const long long k = pivot_key(cabs1(P[li]));
     if (k > bk || (k == bk && r < bi)) { bk = k; bi = r; br = r; }
   }
+  // Column c: the block's candidate row and the cluster's choice need column c updated for
+  // every earlier pivot, but the other columns of the rank-1 update of pivot c - 1 (c + 1 ..
+  // w - 1) wait: warps 1 .. 7 apply them between their arrival at the cluster barrier of
+  // column c and their wait, while warp 0 waits and picks the pivot, so the update is off the
+  // serial path.  The one row that cannot wait, the block's candidate (its entries go to every
+  // block of the cluster), warp 0 updates on its own before publishing it.
   int par = 0;
   for (int c = 0; c < w; ++c) {
+    const bool lag = c >= 1 && !s_zero[(c - 1) & 1];  // pivot c - 1's update of columns > c is pending
     // block's best (ties: lowest position), then publish it with its row
-    warp_argmax_key(bk, bi, br);
+    warp_argmax_key_redux(bk, bi, br);
     if (lane == 0) { redk[warp] = bk; redi[warp] = bi; redr[warp] = br; }
     __syncthreads();
     if (warp == 0) {
       bk = lane < kWarps ? redk[lane] : -1;
       bi = lane < kWarps ? redi[lane] : rows;
       br = lane < kWarps ? redr[lane] : -1;
-      warp_argmax_key(bk, bi, br);
+      warp_argmax_key_redux(bk, bi, br);
       if (lane == 0) { cand[par].k = bk; cand[par].pos = bi; cand[par].phys = br; }
       const int li = br >= 0 ? (br - rank) / C : 0;
-      if (lane < w) cand[par].row[lane] = br >= 0 ? P[lane * lmax + li] : make_double2(0.0, 0.0);
+      if (lane < w) {
+        double2 v = br >= 0 ? P[lane * lmax + li] : make_double2(0.0, 0.0);
+        // the pending update of pivot c - 1 on this row (the same arithmetic the deferred
+        // update below applies to it)
+        if (br >= 0 && lag && lane > c) v = cfms(P[(c - 1) * lmax + li], prow[(c - 1) & 1][lane], v);
+        cand[par].row[lane] = v;
+      }
     }
-    cl.sync();
-    // warp 0: the C proposals (one lane each), reduced with shuffles; the winner's row; the
-    // pivot's reciprocal (one lane: FP64 issues slowly on this GPU); the interchange of
-    // positions c and p in the permutation
+    __syncthreads();  // the candidate row is read before the deferred update writes it
+    asm volatile("barrier.cluster.arrive.release;" ::: "memory");
     if (warp == 0) {
+      asm volatile("barrier.cluster.wait.acquire;" ::: "memory");
+      // the C proposals (one lane each) with their pivot entries, whose reciprocals are
+      // formed while the shuffles pick the winner; the winner's row; the interchange of
+      // positions c and p in the permutation
       long long ck = -1;
       int cp = rows, cb = -1;
+      double2 pv = make_double2(0.0, 0.0);
       if (lane < C) {
         const CandRow* cd = cl.map_shared_rank(&cand[par], lane);
         ck = cd->k;
         cp = cd->pos;
+        pv = cd->row[c];
         cb = lane;
       }
-      warp_argmax_key(ck, cp, cb);
+      const double2 pinv = lane < C ? cinv_pivot(pv) : make_double2(0.0, 0.0);
+      warp_argmax_key_redux(ck, cp, cb);
       const bool zero = ck <= 0 || cp >= rows || cb < 0;
       const int p = zero ? c : cp;  // current position of the pivot row
-      if (lane < w) {
-        const double2 v = zero ? make_double2(0.0, 0.0) : cl.map_shared_rank(&cand[par], cb)->row[lane];
-        prow[lane] = v;
-        if (lane == c) s_inv = zero ? make_double2(0.0, 0.0) : cinv_pivot(v);
-      }
+      const double ix = __shfl_sync(0xffffffffu, pinv.x, cb < 0 ? 0 : cb);
+      const double iy = __shfl_sync(0xffffffffu, pinv.y, cb < 0 ? 0 : cb);
+      if (lane < w) prow[c & 1][lane] = zero ? make_double2(0.0, 0.0) : cl.map_shared_rank(&cand[par], cb)->row[lane];
       if (lane == 0) {
-        s_zero = zero;
+        s_inv = zero ? make_double2(0.0, 0.0) : make_double2(ix, iy);
+        s_zero[c & 1] = zero;
         const int rc = pos2phys[c], rp = pos2phys[p];
         pos2phys[c] = rp; pos2phys[p] = rc;
         phys2pos[rp] = c; phys2pos[rc] = p;
@@ -302,34 +319,46 @@ __global__ void __launch_bounds__(kClusterPanelThreads) panel_cluster_kernel(con
           }
         }
       }
+    } else {
+      if (lag) {
+        // the deferred update of pivot c - 1, columns c + 1 .. w - 1 of the rows below it.
+        // Warp 0 meanwhile swaps two positions >= c in phys2pos: either value of such a row
+        // passes the test below, so the read needs no ordering.
+        const int nq = w - c - 1;
+        const double2* pr = prow[(c - 1) & 1];
+        for (int e = tid - 32; e < lrows * nq; e += kClusterPanelThreads - 32) {
+          const int li = e % lrows, q = c + 1 + e / lrows;
+          if (phys2pos[rank + li * C] <= c - 1) continue;
+          P[q * lmax + li] = cfms(P[(c - 1) * lmax + li], pr[q], P[q * lmax + li]);
+        }
+      }
+      asm volatile("barrier.cluster.wait.acquire;" ::: "memory");
     }
     par ^= 1;
     __syncthreads();
-    const bool zero = s_zero;
-    // the multipliers of the own rows not yet pivoted (current position > c)
-    if (!zero) {
-      const double2 inv = s_inv;
-      for (int li = tid; li < lrows; li += kClusterPanelThreads)
-        if (phys2pos[rank + li * C] > c) P[c * lmax + li] = cmul(P[c * lmax + li], inv);
-    }
-    __syncthreads();
-    // rank-1 update, one element per thread (all lanes busy), fused with the next column's
-    // candidate; the arithmetic of each element is the one-block kernel's
+    const bool zero = s_zero[c & 1];
+    const double2 inv = s_inv;
+    // per own row not yet pivoted (current position > c), one thread: its multiplier, then the
+    // rank-1 update of its column c + 1 alone (the next candidate; the rest waits, see above);
+    // the arithmetic of each element is the one-block kernel's
     bk = -1;
     bi = rows;
     br = -1;
-    const int nq = w - c - 1;
-    for (int e = tid; e < lrows * nq; e += kClusterPanelThreads) {
-      const int li = e % lrows, q = c + 1 + e / lrows;
+    for (int li = tid; li < lrows; li += kClusterPanelThreads) {
       const int r = rank + li * C;
       const int pos = phys2pos[r];
       if (pos <= c) continue;
-      double2 v = P[q * lmax + li];
+      double2 l = P[c * lmax + li];
       if (!zero) {
-        v = cfms(P[c * lmax + li], prow[q], v);
-        P[q * lmax + li] = v;
+        l = cmul(l, inv);
+        P[c * lmax + li] = l;
       }
-      if (q == c + 1) {
+      if (c + 1 < w) {
+        double2 v = P[(c + 1) * lmax + li];
+        if (!zero) {
+          v = cfms(l, prow[c & 1][c + 1], v);
+          P[(c + 1) * lmax + li] = v;
+        }
         const long long k = pivot_key(cabs1(v));
         if (k > bk || (k == bk && pos < bi)) { bk = k; bi = pos; br = r; }
       }
@@ -419,14 +448,22 @@ __global__ void __launch_bounds__(256) swap_trsm_warp_kernel(const LuLaunch a, i
     return col < n && !(col >= j && col < j + w) && (swaps || (col >= tl && col < th));
   };
   // interchanges: one column per warp at a time, the lanes over the row set
-  for (int cl = warp; cl < 32; cl += 8) {
-    const int col = cfirst + cl;
+  // (the four columns of a warp are loaded before any of them is written: each column's
+  // stores touch only that column, so the loads need not wait for them)
+  CT xv[4];
+  const int src = lane < cnt ? src_s[lane] : 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int col = cfirst + warp + 8 * i;
+    xv[i] = (part(col) && lane < cnt) ? A[(long long)col * ld + src] : make_c<CT>(0.0, 0.0);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int cl = warp + 8 * i, col = cfirst + cl;
     if (!part(col)) continue;  // uniform per warp
-    CT* cc = A + (long long)col * ld;
-    const CT xv = lane < cnt ? cc[src_s[lane]] : make_c<CT>(0.0, 0.0);
-    __syncwarp();
-    if (swaps && lane >= w && lane < cnt) cc[rows_s[lane]] = xv;
-    if (lane < w) xs[lane][cl] = xv;
+    if (swaps && lane >= w && lane < cnt) A[(long long)col * ld + rows_s[lane]] = xv[i];
+    if (lane < w) xs[lane][cl] = xv[i];
   }
   // L11 U12 = A12 with the 32 columns on the lanes (every lane of an FP64 instruction works),
   // rows split over warps 0..3 by row mod 4
