@@ -162,6 +162,15 @@ __device__ __forceinline__ void warp_argmax_key_redux(long long& k, int& i, int&
   i = mi;
 }
 
+// Programmatic dependent launch: a kernel launched with it may be scheduled while the kernel
+// before it in the stream is still running.  Every thread waits here for that kernel (its
+// completion and its memory) before the first global-memory access and before any exit, and
+// then lets the next such kernel be scheduled.  Without a programmatic launch both are no-ops.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // process-wide count of kernels this library has launched (diagnostics)
 void count_launches(long long n);
 
@@ -477,6 +486,8 @@ struct ZgemmLaunch {
   int njobs = 0;                   // jobs of the launch
   int inline_slice = 0;            // every job has k <= 16: each tile slices its own operands
                                    // (no slicing launch, no images; img may be null)
+  int chained = 0;                 // with inline_slice: a programmatic dependent launch of the
+                                   // kernel before it in the stream
   unsigned char* img = nullptr;    // scratch for the slice images (16-byte aligned),
   long long img_bytes = 0;         // at least zgemm_img_bytes(njobs, mtiles, ntiles_c)
   int probe_timeout = 0;           // set by launch_zgemm_tc (test hook, see set_zgemm_timeout_probe)

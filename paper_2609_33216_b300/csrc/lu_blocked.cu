@@ -214,6 +214,7 @@ struct CandRow {
 };
 
 __global__ void __launch_bounds__(kClusterPanelThreads) panel_cluster_kernel(const LuLaunch a, int j, int lmax) {
+  pdl_enter();
   extern __shared__ __align__(16) double2 P[];  // P[q * lmax + li]; then pos2phys, phys2pos
   constexpr int kWarps = kClusterPanelThreads / 32;
   __shared__ long long redk[kWarps];
@@ -383,6 +384,7 @@ __global__ void __launch_bounds__(kClusterPanelThreads) panel_cluster_kernel(con
 template <typename CT>
 __global__ void __launch_bounds__(256) swap_trsm_warp_kernel(const LuLaunch a, int j, int tlo, int thi, int swaps,
                                                               int cbase) {
+  pdl_enter();
   __shared__ CT l11[kNb][kNb];
   __shared__ int rows_s[2 * kNb];   // row set: j..j+w-1, then the outside pivot rows
   __shared__ int src_s[2 * kNb];    // lane l takes its new value from row src_s[l]
@@ -623,20 +625,24 @@ cudaError_t getrf_impl(const LuLaunch& a, cudaStream_t s) {
       pc = 1;
     }
   }
-  auto panel = [&](int jj, cudaStream_t st) {
+  // chained: a programmatic dependent launch of the kernel before it on the same stream (the
+  // kernels of the tensor-core path's serial chain; each waits for its predecessor first)
+  auto panel = [&](int jj, cudaStream_t st, bool chained) {
     if (pc > 1) {
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(a.njobs * pc, 1, 1);
       cfg.blockDim = dim3(kClusterPanelThreads, 1, 1);
       cfg.dynamicSmemBytes = (size_t)lmax * kNb * sizeof(double2) + 2 * (size_t)a.max_n * sizeof(int);
       cfg.stream = st;
-      cudaLaunchAttribute attr[1];
+      cudaLaunchAttribute attr[2];
       attr[0].id = cudaLaunchAttributeClusterDimension;
       attr[0].val.clusterDim.x = pc;
       attr[0].val.clusterDim.y = 1;
       attr[0].val.clusterDim.z = 1;
+      attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      attr[1].val.programmaticStreamSerializationAllowed = 1;
       cfg.attrs = attr;
-      cfg.numAttrs = 1;
+      cfg.numAttrs = chained ? 2 : 1;
       cudaError_t le = cudaLaunchKernelEx(&cfg, panel_cluster_kernel, a, jj, lmax);
       symhss::count_launches(1);
       return le;
@@ -653,14 +659,17 @@ cudaError_t getrf_impl(const LuLaunch& a, cudaStream_t s) {
     symhss::count_launches(1);
     return cudaGetLastError();
   };
-  if ((e = panel(0, s)) != cudaSuccess) return e;
   // lu_tc = 1: always; 2: launches of at least kTcMinJobs matrices (the lower tree levels, whose
   // many blocks fill the tensor-core product; at the top levels its per-launch latency and the
   // extra launches cost more than the FP64 updates they replace)
   const bool use_tc = (a.tc == 1 || (a.tc == 2 && a.njobs >= kTcMinJobs)) && a.zimg &&
                       a.zimg_bytes >= zgemm_lu_img_bytes(a.njobs, a.max_n);
   const int kOuter = (a.outer == 16 || a.outer == 32) ? a.outer : kOuterMax;
-  if (sizeof(CT) == sizeof(double2) && use_tc && a.max_n > kOuter + kNb) {
+  const bool tc_path = sizeof(CT) == sizeof(double2) && use_tc && a.max_n > kOuter + kNb;
+  // with rank-16 updates the chain is panel -> interchanges -> update -> panel, one stream
+  const bool chain = tc_path && kOuter == kNb;
+  if ((e = panel(0, s, chain)) != cudaSuccess) return e;
+  if (tc_path) {
     // FP64: blocked by 64 columns (the order of a blocked right-looking LU).  Inside a block
     // the 16-column panels run as above with their interchanges applied to every column, but
     // their U-row solves and FP64 updates cover only the block's own columns.  At the block's
@@ -672,10 +681,23 @@ cudaError_t getrf_impl(const LuLaunch& a, cudaStream_t s) {
       if (rest > 0) {
         // interchanges in every column; U rows only in the block's own columns (a block of
         // one panel: in every column right of it, so that no second pass is needed)
-        swap_trsm_warp_kernel<CT><<<dim3(a.njobs, ncolblk), 256, 0, s>>>(a, j, 0, kOuter == kNb ? a.max_n : J + kOuter,
-                                                                          1, 0);
+        if (chain) {
+          cudaLaunchConfig_t cfg = {};
+          cfg.gridDim = dim3(a.njobs, ncolblk);
+          cfg.blockDim = dim3(256);
+          cfg.stream = s;
+          cudaLaunchAttribute attr[1];
+          attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+          attr[0].val.programmaticStreamSerializationAllowed = 1;
+          cfg.attrs = attr;
+          cfg.numAttrs = 1;
+          e = cudaLaunchKernelEx(&cfg, swap_trsm_warp_kernel<CT>, a, j, 0, a.max_n, 1, 0);
+        } else {
+          swap_trsm_warp_kernel<CT><<<dim3(a.njobs, ncolblk), 256, 0, s>>>(a, j, 0, J + kOuter, 1, 0);
+          e = cudaGetLastError();
+        }
         symhss::count_launches(1);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (e != cudaSuccess) return e;
         const int pc = J + kOuter - (j + kNb);  // columns of the block right of this panel
         if (pc > 0) {
           update_kernel<CT><<<dim3(a.njobs, (rest + kTs - 1) / kTs, (pc + kTs - 1) / kTs), 256, 0, s>>>(a, j, 0, pc, -1);
@@ -708,6 +730,7 @@ cudaError_t getrf_impl(const LuLaunch& a, cudaStream_t s) {
         g.derive = ZGEMM_LU_UPDATE;
         g.block_w = kOuter;
         g.inline_slice = kOuter <= 16;  // one 16-column chunk: sliced by the product's tiles
+        g.chained = chain;
         g.lu_jobs = a.jobs;
         g.njobs = a.njobs;
         g.img = a.zimg;
@@ -718,7 +741,7 @@ cudaError_t getrf_impl(const LuLaunch& a, cudaStream_t s) {
         g.ntiles = a.njobs * g.mtiles * g.ntiles_c;
         if ((e = launch_zgemm_tc(g, s)) != cudaSuccess) return e;
       }
-      if (j + kNb < a.max_n && (e = panel(j + kNb, s)) != cudaSuccess) return e;
+      if (j + kNb < a.max_n && (e = panel(j + kNb, s, chain)) != cudaSuccess) return e;
     }
     const int jlast = ((a.max_n - 1) / kNb) * kNb;
     swap_trsm_warp_kernel<CT><<<dim3(a.njobs, ncolblk), 256, 0, s>>>(a, jlast, 0, a.max_n, 1, 0);
@@ -738,12 +761,12 @@ cudaError_t getrf_impl(const LuLaunch& a, cudaStream_t s) {
     symhss::count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (!split) {
-      if ((e = panel(j + kNb, s)) != cudaSuccess) return e;
+      if ((e = panel(j + kNb, s, false)) != cudaSuccess) return e;
       continue;
     }
     if ((e = cudaEventRecord(la->ready, s)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(la->side, la->ready, 0)) != cudaSuccess) return e;
-    if ((e = panel(j + kNb, la->side)) != cudaSuccess) return e;
+    if ((e = panel(j + kNb, la->side, false)) != cudaSuccess) return e;
     if ((e = cudaEventRecord(la->done, la->side)) != cudaSuccess) return e;
     const int ctiles = (rest - kTs + kTs - 1) / kTs;
     update_kernel<CT><<<dim3(a.njobs, rtiles, ctiles), 256, 0, s>>>(a, j, kTs, -1, -1);

@@ -349,6 +349,7 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
 
 __global__ void __launch_bounds__(kMmaThreads, 2) zgemm_tc_kernel(const ZgemmLaunch a) {
   extern __shared__ __align__(1024) unsigned char smem[];
+  pdl_enter();
   __shared__ __align__(8) uint64_t bar_mma[2];
   __shared__ __align__(8) uint64_t bar_load[2];
   __shared__ uint32_t tmem_base_s;
@@ -700,9 +701,24 @@ cudaError_t launch_zgemm_tc(const ZgemmLaunch& a_in, cudaStream_t s) {
   const int smem = kStageBytes;
   e = cudaFuncSetAttribute(zgemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  zgemm_tc_kernel<<<a.ntiles, kMmaThreads, smem, s>>>(a);
+  if (a.inline_slice && a.chained) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(a.ntiles);
+    cfg.blockDim = dim3(kMmaThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, zgemm_tc_kernel, a);
+  } else {
+    zgemm_tc_kernel<<<a.ntiles, kMmaThreads, smem, s>>>(a);
+    e = cudaGetLastError();
+  }
   symhss::count_launches(1);
-  return cudaGetLastError();
+  return e;
 }
 
 }  // namespace symhss
