@@ -171,6 +171,24 @@ __device__ __forceinline__ void pdl_enter() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// A kernel launch, as a programmatic dependent of the kernel before it on the stream when
+// `chained` (then the kernel must begin with pdl_enter), else a plain launch.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_chained(bool chained, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                  cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = chained ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 // process-wide count of kernels this library has launched (diagnostics)
 void count_launches(long long n);
 
@@ -486,8 +504,9 @@ struct ZgemmLaunch {
   int njobs = 0;                   // jobs of the launch
   int inline_slice = 0;            // every job has k <= 16: each tile slices its own operands
                                    // (no slicing launch, no images; img may be null)
-  int chained = 0;                 // with inline_slice: a programmatic dependent launch of the
-                                   // kernel before it in the stream
+  int chained = 0;                 // the first kernel of the product (the slicing kernel, or
+                                   // with inline_slice the product kernel) is a programmatic
+                                   // dependent launch of the kernel before it in the stream
   unsigned char* img = nullptr;    // scratch for the slice images (16-byte aligned),
   long long img_bytes = 0;         // at least zgemm_img_bytes(njobs, mtiles, ntiles_c)
   int probe_timeout = 0;           // set by launch_zgemm_tc (test hook, see set_zgemm_timeout_probe)

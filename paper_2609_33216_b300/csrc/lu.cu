@@ -441,6 +441,7 @@ __global__ void permute_kernel(const RsLaunch a, int warps) {
 // diagonal block of the factors, staged in shared memory; one warp per right-hand side
 template <bool LOWER>
 __global__ void trsv_block_kernel(const RsLaunch a, int J, int warps, int W) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* tri = reinterpret_cast<double2*>(smem_raw);  // kBlk x kBlk, column-major
   double2* dinv = tri + kBlk * kBlk;
@@ -491,6 +492,7 @@ constexpr int kRhsWarps = 4;
 
 template <bool LOWER>
 __global__ void __launch_bounds__(kRhsWarps * 32) trsv_rhs_kernel(const RsLaunch a, int J, int W) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* tri = reinterpret_cast<double2*>(smem_raw);  // kBlk x kBlk, column-major
   double2* xs = tri + kBlk * kBlk;                       // kBlk x 32: row i, lane l at i * 32 + l
@@ -632,11 +634,14 @@ cudaError_t getrs_blocked_tc(const RsLaunch& a, cudaStream_t s) {
   // forward: L y = P b, block by block; the rows below a block are updated on the tensor cores
   const int W = (a.blk == 16 || a.blk == 32) ? a.blk : kBlk;
   g.block_w = W;
+  // one serial chain on s: every kernel after the permutation is a programmatic dependent of
+  // the one before it
+  g.chained = 1;
   for (int J = 0; J < max_n; J += W) {
-    if (rhs_lanes) trsv_rhs_kernel<true><<<rgrid, kRhsWarps * 32, rsmem, s>>>(a, J, W);
-    else trsv_block_kernel<true><<<grid, warps * 32, tsmem, s>>>(a, J, warps, W);
+    if (rhs_lanes) e = launch_chained(true, trsv_rhs_kernel<true>, rgrid, dim3(kRhsWarps * 32), rsmem, s, a, J, W);
+    else e = launch_chained(true, trsv_block_kernel<true>, grid, dim3(warps * 32), tsmem, s, a, J, warps, W);
     symhss::count_launches(1);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (e != cudaSuccess) return e;
     const int below = max_n - J - W;
     if (below > 0) {
       g.derive = ZGEMM_RS_FWD;
@@ -648,10 +653,10 @@ cudaError_t getrs_blocked_tc(const RsLaunch& a, cudaStream_t s) {
   }
   // backward: U x = y from the last block; the rows above a block are updated on the tensor cores
   for (int J = ((max_n - 1) / W) * W; J >= 0; J -= W) {
-    if (rhs_lanes) trsv_rhs_kernel<false><<<rgrid, kRhsWarps * 32, rsmem, s>>>(a, J, W);
-    else trsv_block_kernel<false><<<grid, warps * 32, tsmem, s>>>(a, J, warps, W);
+    if (rhs_lanes) e = launch_chained(true, trsv_rhs_kernel<false>, rgrid, dim3(kRhsWarps * 32), rsmem, s, a, J, W);
+    else e = launch_chained(true, trsv_block_kernel<false>, grid, dim3(warps * 32), tsmem, s, a, J, warps, W);
     symhss::count_launches(1);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (e != cudaSuccess) return e;
     if (J > 0) {
       g.derive = ZGEMM_RS_BWD;
       g.block_j = J;

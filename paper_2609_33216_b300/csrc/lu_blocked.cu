@@ -681,21 +681,8 @@ cudaError_t getrf_impl(const LuLaunch& a, cudaStream_t s) {
       if (rest > 0) {
         // interchanges in every column; U rows only in the block's own columns (a block of
         // one panel: in every column right of it, so that no second pass is needed)
-        if (chain) {
-          cudaLaunchConfig_t cfg = {};
-          cfg.gridDim = dim3(a.njobs, ncolblk);
-          cfg.blockDim = dim3(256);
-          cfg.stream = s;
-          cudaLaunchAttribute attr[1];
-          attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-          attr[0].val.programmaticStreamSerializationAllowed = 1;
-          cfg.attrs = attr;
-          cfg.numAttrs = 1;
-          e = cudaLaunchKernelEx(&cfg, swap_trsm_warp_kernel<CT>, a, j, 0, a.max_n, 1, 0);
-        } else {
-          swap_trsm_warp_kernel<CT><<<dim3(a.njobs, ncolblk), 256, 0, s>>>(a, j, 0, J + kOuter, 1, 0);
-          e = cudaGetLastError();
-        }
+        e = launch_chained(chain, swap_trsm_warp_kernel<CT>, dim3(a.njobs, ncolblk), dim3(256), 0, s, a, j, 0,
+                           chain ? a.max_n : J + kOuter, 1, 0);
         symhss::count_launches(1);
         if (e != cudaSuccess) return e;
         const int pc = J + kOuter - (j + kNb);  // columns of the block right of this panel
@@ -744,9 +731,10 @@ cudaError_t getrf_impl(const LuLaunch& a, cudaStream_t s) {
       if (j + kNb < a.max_n && (e = panel(j + kNb, s, chain)) != cudaSuccess) return e;
     }
     const int jlast = ((a.max_n - 1) / kNb) * kNb;
-    swap_trsm_warp_kernel<CT><<<dim3(a.njobs, ncolblk), 256, 0, s>>>(a, jlast, 0, a.max_n, 1, 0);
+    e = launch_chained(chain, swap_trsm_warp_kernel<CT>, dim3(a.njobs, ncolblk), dim3(256), 0, s, a, jlast, 0,
+                       a.max_n, 1, 0);
     symhss::count_launches(1);
-    return cudaGetLastError();
+    return e;
   }
   for (int j = 0; j < a.max_n; j += kNb) {
     const int rest = a.max_n - j - kNb;

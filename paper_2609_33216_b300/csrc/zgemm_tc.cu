@@ -251,6 +251,7 @@ __device__ __forceinline__ void slice_pack8(const double x[8], int emax, uint32_
 }
 
 __global__ void __launch_bounds__(kSliceThreads) zslice_kernel(const ZgemmLaunch a) {
+  pdl_enter();
   __shared__ int s_e[kMaxChunks][kTileM];
   const ImgLayout L = img_layout(a.img, a.njobs, a.mtiles, a.ntiles_c);
   const int nA = a.njobs * a.mtiles;
@@ -694,29 +695,16 @@ cudaError_t launch_zgemm_tc(const ZgemmLaunch& a_in, cudaStream_t s) {
   a.probe_timeout = g_zgemm_probe;
   cudaError_t e;
   if (!a.inline_slice) {
-    zslice_kernel<<<a.njobs * (a.mtiles + a.ntiles_c), kSliceThreads, 0, s>>>(a);
+    e = launch_chained(a.chained, zslice_kernel, dim3(a.njobs * (a.mtiles + a.ntiles_c)), dim3(kSliceThreads), 0, s,
+                       a);
     symhss::count_launches(1);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (e != cudaSuccess) return e;
   }
   const int smem = kStageBytes;
   e = cudaFuncSetAttribute(zgemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  if (a.inline_slice && a.chained) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(a.ntiles);
-    cfg.blockDim = dim3(kMmaThreads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, zgemm_tc_kernel, a);
-  } else {
-    zgemm_tc_kernel<<<a.ntiles, kMmaThreads, smem, s>>>(a);
-    e = cudaGetLastError();
-  }
+  // after the slicing kernel: always its programmatic dependent
+  e = launch_chained(a.chained || !a.inline_slice, zgemm_tc_kernel, dim3(a.ntiles), dim3(kMmaThreads), smem, s, a);
   symhss::count_launches(1);
   return e;
 }
