@@ -286,12 +286,12 @@ typedef struct {
   int lu_panel_cluster;   /* 1, 2, 4, 8 or 16 (default 16): largest thread-block cluster factoring
                            * one LU panel, used while blocks x cluster <= the SM count and every
                            * member keeps >= 32 panel rows (the top tree levels); 1: one block */
-  int lu_tc;              /* 1: FP64 block LUs blocked by lu_outer columns and multi-RHS solves blocked
-                           * by 64 rows, their updates on the tensor cores (symhss_zgemm);
-                           * 0: 16-column LU and unblocked solves on the FP64 pipe; 2 (default):
-                           * the first for launches of at least 32 blocks (the lower tree levels;
-                           * solves also when blocks x right-hand sides >= 512), the second above.
-                           * All give the factorisation to FP64 rounding, not the same bits. */
+  int lu_tc;              /* 1 (default): FP64 block LUs blocked by lu_outer columns and multi-RHS
+                           * solves blocked by 64 rows, their updates on the tensor cores
+                           * (symhss_zgemm); 0: 16-column LU and unblocked solves on the FP64
+                           * pipe; 2: the first for launches of at least 32 blocks (the lower tree
+                           * levels; solves also when blocks x right-hand sides >= 512), the second
+                           * above.  All give the factorisation to FP64 rounding, not the same bits. */
   int lu_outer;           /* column block of the LU's tensor-core updates: 16 (default), 32 or 64
                            * (0 = 64); 16: a rank-16 update on the tensor cores after every
                            * 16-column panel, no FP64 updates inside a block.  The blocked

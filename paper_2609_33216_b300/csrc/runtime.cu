@@ -200,7 +200,7 @@ struct symhss_s {
   symhss_stats_t st{};
   cudaError_t last_cuda = cudaSuccess;
   std::vector<int> mark;                          // host scratch (size npts)
-  symhss_tuning tune = {0, 256, 0, 16, 16, 2, 16, {0}};  // launch tuning (symhss_set_tuning)
+  symhss_tuning tune = {0, 256, 0, 16, 16, 1, 16, {0}};  // launch tuning (symhss_set_tuning)
   symhss_mlp_s* mlp = nullptr;                    // attached proposer (not owned)
   double prop_margin = 1.15;
   symhss::DevBuf featjobs, feats, mlpout, chkjobs, chkratio;
