@@ -145,40 +145,30 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t v[8]) {
 }
 
 // T 2^E rounded once to FP64 (to nearest, ties to even), for T = hi 2^28 + lo with |hi|,
-// |lo| < 2^46, by integer operations on the bits: |T| = H 2^28 + L (0 <= L < 2^28) is cut to
-// its leading 53 bits and the exponent field set to msb + E.  A result outside the normal
-// range (never for the products of this solver) is formed by FP64 operations instead.
+// |lo| < 2^46.  T = h2 2^28 + l2 (0 <= l2 < 2^28) is cut to Ts = floor(T / 2^s) with s chosen
+// so that Ts fits 64 bits (and, for s > 0, has at least 62 significant bits); the dropped bits
+// of l2 become a sticky bit in the last place, which cannot move the rounding of a value of
+// that length.  One correctly rounded integer-to-FP64 conversion then rounds T / 2^s, and the
+// exponent field takes s + E.  (The conversion replaces about sixty integer instructions of an
+// explicit cut and round, the larger part of the epilogue's issue time.)  A result outside the
+// normal range (never for the products of this solver) is formed by FP64 operations instead.
+// the FP64 path for results outside the normal range, as a call, so that its instructions are
+// not if-converted into the common path (this GPU issues FP64 instructions slowly)
+__device__ __noinline__ double recombine_slow(long long hi, long long lo, int E) {
+  return scale2(fma((double)hi, 268435456.0, (double)lo), E);
+}
 __device__ __forceinline__ double recombine(long long hi, long long lo, int E) {
-  const long long h2 = hi + (lo >> 28);  // T = h2 2^28 + l2, 0 <= l2 < 2^28
+  const long long h2 = hi + (lo >> 28);
   const long long l2 = lo & 0xFFFFFFFll;
-  const bool neg = h2 < 0;
-  const uint64_t H = neg ? (uint64_t)(l2 ? -h2 - 1 : -h2) : (uint64_t)h2;
-  const uint64_t L = neg ? (uint64_t)(l2 ? (1ll << 28) - l2 : 0) : (uint64_t)l2;
-  if ((H | L) == 0) return 0.0;
-  int msb;
-  uint64_t q;
-  if (H != 0) {
-    const int mH = 63 - __clzll((long long)H);  // H < 2^47
-    msb = mH + 28;
-    if (msb <= 52) {
-      q = ((H << 28) | L) << (52 - msb);
-    } else {
-      const int sh = msb - 52;  // 1 .. 22 bits below the kept 53, all inside L
-      q = (H << (28 - sh)) | (L >> sh);
-      const uint64_t rem = L & ((1ull << sh) - 1), half = 1ull << (sh - 1);
-      if (rem > half || (rem == half && (q & 1))) {
-        ++q;
-        if (q >> 53) { q >>= 1; ++msb; }
-      }
-    }
-  } else {
-    msb = 63 - __clzll((long long)L);
-    q = L << (52 - msb);
-  }
-  const int be = msb + E + 1023;
-  if (be <= 0 || be >= 2047) return scale2(fma((double)hi, 268435456.0, (double)lo), E);
-  return __longlong_as_double((long long)((neg ? 0x8000000000000000ull : 0ull) | ((uint64_t)be << 52) |
-                                          (q & 0xFFFFFFFFFFFFFull)));
+  const int mh = 63 - __clzll(h2 ^ (h2 >> 63));  // highest bit of |h2| (of |h2| - 1 if h2 < 0)
+  const int s = mh > 34 ? mh - 34 : 0;           // |h2| 2^(28 - s) <= 2^63
+  const long long Ts = ((long long)((unsigned long long)h2 << (28 - s)) + (l2 >> s)) |
+                       ((l2 & ((1ll << s) - 1)) != 0 ? 1ll : 0ll);
+  const long long db = __double_as_longlong(__ll2double_rn(Ts));
+  const int be = (int)((db >> 52) & 0x7FF) + s + E;
+  if (Ts == 0) return 0.0;
+  if (be <= 0 || be >= 2047) return recombine_slow(hi, lo, E);
+  return __longlong_as_double(db + ((long long)(s + E) << 52));
 }
 
 // the job of index jidx of a launch: explicit, or derived from the factorisation's job arrays
@@ -636,9 +626,13 @@ __global__ void __launch_bounds__(kMmaThreads, 2) zgemm_tc_kernel(const ZgemmLau
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const int q = 2 * cc + h;
-            const long long hi = ((((long long)gi[0][q] * 128 + gi[1][q]) * 128 + gi[2][q]) * 128) + gi[3][q];
-            const long long lo = ((((long long)gi[4][q] * 128 + gi[5][q]) * 128 + gi[6][q]) * 128) + gi[7][q];
-            pr[h] = (eea == 0 || fb == 0) ? 0.0 : recombine(hi, lo, E);
+            // below 2^22 the pairs g0 2^7 + g1 fit 32 bits
+            const long long hi = small ? (long long)(gi[0][q] * 128 + gi[1][q]) * 16384 + (gi[2][q] * 128 + gi[3][q])
+                                       : ((((long long)gi[0][q] * 128 + gi[1][q]) * 128 + gi[2][q]) * 128) + gi[3][q];
+            const long long lo = small ? (long long)(gi[4][q] * 128 + gi[5][q]) * 16384 + (gi[6][q] * 128 + gi[7][q])
+                                       : ((((long long)gi[4][q] * 128 + gi[5][q]) * 128 + gi[6][q]) * 128) + gi[7][q];
+            const double rv = recombine(hi, lo, E);
+            pr[h] = (eea == 0 || fb == 0) ? 0.0 : rv;
           }
           const double2 o = old4[cc];
           double2* cp = C + er + (long long)col * jb.ldc;
