@@ -101,13 +101,13 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long lo
 
 __device__ __forceinline__ int bexp(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7FF); }
 
-// the eight 7-bit slices of x relative to the biased exponent emax (>= that of x), as bf16
-// bit patterns with the sign of x.  The fields come from two 32-bit halves of the aligned
-// mantissa, and each 7-bit integer d becomes a float by one FP32 subtraction,
-// (2^23 + d) - 2^23, exact (instead of an integer-to-float conversion per slice).
-__device__ __forceinline__ void slice8(double x, int emax, uint32_t out[kSlices], bool negate = false) {
-  // the sign is taken from the bit pattern (negation flips it: no FP64 instruction)
-  const long long bits = __double_as_longlong(x) ^ (negate ? (long long)0x8000000000000000ull : 0ll);
+// the eight 7-bit slices of |x| relative to the biased exponent emax (>= that of x), each as an
+// FP32 number whose upper half is its bf16 bit pattern, and the sign bit (0x8000) of x.  The
+// fields come from two 32-bit halves of the aligned mantissa, and each 7-bit integer d becomes
+// a float by one FP32 subtraction, (2^23 + d) - 2^23, exact (instead of an integer-to-float
+// conversion per slice).
+__device__ __forceinline__ void slice8(double x, int emax, uint32_t f[kSlices], uint32_t& sgn) {
+  const long long bits = __double_as_longlong(x);
   const int E = (int)((bits >> 52) & 0x7FF);
   uint64_t A = 0;
   if (E != 0 && emax != 0) {
@@ -116,12 +116,11 @@ __device__ __forceinline__ void slice8(double x, int emax, uint32_t out[kSlices]
     A = sh >= 0 ? (mant << sh) : (sh > -64 ? (mant >> (-sh)) : 0ull);
   }
   const uint32_t ahi = (uint32_t)(A >> 28), alo = (uint32_t)A & 0xFFFFFFFu;  // bits 55..28, 27..0
-  const uint32_t sgn = bits < 0 ? 0x8000u : 0u;
+  sgn = bits < 0 ? 0x8000u : 0u;
 #pragma unroll
   for (int t = 0; t < kSlices; ++t) {
     const uint32_t d = ((t < 4 ? ahi : alo) >> (21 - 7 * (t & 3))) & 0x7Fu;
-    const float f = __int_as_float(0x4B000000 | (int)d) - 8388608.0f;
-    out[t] = d ? ((__float_as_uint(f) >> 16) | sgn) : 0u;
+    f[t] = __float_as_uint(__int_as_float(0x4B000000 | (int)d) - 8388608.0f);
   }
 }
 
@@ -222,23 +221,25 @@ __host__ __device__ __forceinline__ ImgLayout img_layout(unsigned char* img, int
   return L;
 }
 
+// the eight slices of eight values (relative to biased exponent emax) packed as bf16 pairs:
+// one byte permutation joins slice t of two neighbouring values.  A zero slice of a negative
+// value is -0, whose products add nothing to the sums.
+__device__ __forceinline__ void slice_pack8(const double x[8], int emax, uint32_t pk[kSlices][4]) {
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    uint32_t fa[kSlices], fb[kSlices], sa, sb;
+    slice8(x[2 * m], emax, fa, sa);
+    slice8(x[2 * m + 1], emax, fb, sb);
+    const uint32_t sg = sa | (sb << 16);
+#pragma unroll
+    for (int t = 0; t < kSlices; ++t) pk[t][m] = __byte_perm(fa[t], fb[t], 0x7632) | sg;
+  }
+}
+
 // Slicing kernel (512 threads): blocks [0, njobs mtiles) cut row blocks of A', the rest column
 // blocks of B'.  Every thread loads its share of the block once (all loads in flight together),
 // takes the exponents from registers and writes its slices.
 constexpr int kSliceThreads = 512;
-
-// the eight slices of eight values (relative to biased exponent emax) packed as bf16 pairs
-__device__ __forceinline__ void slice_pack8(const double x[8], int emax, uint32_t pk[kSlices][4]) {
-#pragma unroll
-  for (int t = 0; t < kSlices; ++t) pk[t][0] = pk[t][1] = pk[t][2] = pk[t][3] = 0;
-#pragma unroll
-  for (int e8 = 0; e8 < 8; ++e8) {
-    uint32_t sl[kSlices];
-    slice8(x[e8], emax, sl);
-#pragma unroll
-    for (int t = 0; t < kSlices; ++t) pk[t][e8 >> 1] |= sl[t] << (16 * (e8 & 1));
-  }
-}
 
 __global__ void __launch_bounds__(kSliceThreads) zslice_kernel(const ZgemmLaunch a) {
   pdl_enter();
