@@ -448,6 +448,7 @@ def run_ours(args):
             "speedup_sym_vs_nonsym": sec_base / sec_sym,
             "rel_diff_sym_vs_nonsym": res["rel_diff"],
             "phases_ms": {"build": st.ms_build, "solve": st.ms_solve},
+            "step_ms": {"median": statistics.median(r["times"]), "min": min(r["times"]), "max": max(r["times"])},
             "per_kernel": _per_kernel(ser["acc"], ser["steps"], names),
             "per_kernel_timing": ("serialised steps (compress, then factor, then solve, one stream), CUDA events "
                                   f"around every launch; {ser['steps']} steps of "

@@ -377,6 +377,13 @@ int symhss_training_data(symhss_t h, int* count, float* x, float* y_rank, float*
  * Hankel's expansion; about 1e-15 relative accuracy). */
 int symhss_hankel01(const double* x, int n, void* out, void* stream);
 
+/* The reciprocal the LU panels (Sec. 4.2 factorisation) take of each pivot: out_i ~ 1 / a_i
+ * for n device complex128 values a (out: device complex128[n]), as conj(a) / |a|^2 with
+ * 1 / |a|^2 from Newton's iteration for the reciprocal (two steps from the hardware's
+ * approximation), or by Smith's scaled division when |a|^2 is outside [2^-996, 2^997).
+ * Within a few units in the last place of 1 / a; zero gives non-finite values. */
+int symhss_pivot_reciprocal(const void* a, int n, void* out, void* stream);
+
 /* A set of points for symhss_kernel_block: coordinates, unit normals, weights,
  * curvature and an id; two points with the same id >= 0 are the same curve
  * node and receive the corrected diagonal (Sec. 3.1) and the free terms (Eq. 15).

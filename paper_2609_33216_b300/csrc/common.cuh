@@ -67,13 +67,28 @@ __device__ __forceinline__ float2 cinv(float2 a) {
     return make_float2(r / d, -1.0f / d);
   }
 }
-// Reciprocal of an LU pivot on a serial dependency chain: conj(a) / |a|^2 carries one
-// division where Smith's method carries two; Smith's scaled form is kept for |a|^2 outside
-// the normal range, where the plain form would overflow or underflow.
+// 1 / d for d > 0 with a biased exponent in [27, 2019]: Newton's iteration for the reciprocal,
+// r <- r + r (1 - d r), whose relative error squares at each step, taken twice from the
+// hardware's approximate reciprocal (rcp.approx.ftz.f64); the result is within about one unit
+// in the last place of the rounded quotient 1.0 / d.  Four fused multiply-adds on the FP64
+// pipe, against the longer sequence of a full division (this GPU issues FP64 instructions
+// slowly, and the pivot's reciprocal is on the LU panel's serial chain).
+__device__ __forceinline__ double recip_newton(double d) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+  double e = fma(-d, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-d, r, 1.0);
+  return fma(r, e, r);
+}
+// Reciprocal of an LU pivot on a serial dependency chain: conj(a) / |a|^2 with the reciprocal
+// of |a|^2 by recip_newton; Smith's scaled form is kept for |a|^2 outside [2^-996, 2^997)
+// (tested on the exponent bits), where the plain form would overflow or underflow.
 __device__ __forceinline__ double2 cinv_pivot(double2 a) {
   const double s2 = fma(a.x, a.x, a.y * a.y);
-  if (!(s2 > 1e-300 && s2 < 1e300)) return cinv(a);
-  const double r = 1.0 / s2;
+  const int ex = (int)((__double_as_longlong(s2) >> 52) & 0x7FF);
+  if (ex < 27 || ex > 2019) return cinv(a);
+  const double r = recip_newton(s2);
   return make_double2(a.x * r, -a.y * r);
 }
 __device__ __forceinline__ float2 cinv_pivot(float2 a) {
@@ -297,6 +312,8 @@ constexpr int TILE_L = 32;    // loop points per chunk
 
 cudaError_t launch_tiles(const TileLaunch& a, cudaStream_t s);
 cudaError_t launch_hankel(const double* x, int n, double2* out, cudaStream_t s);
+// out[i] = the LU panels' pivot reciprocal (cinv_pivot) of a[i], n complex128 values
+cudaError_t launch_pivot_reciprocal(const double2* a, int n, double2* out, cudaStream_t s);
 
 // ---- column ID (pivoted QR) ---------------------------------------------------
 

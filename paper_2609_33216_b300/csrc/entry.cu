@@ -202,6 +202,15 @@ int symhss_hankel01(const double* x, int n, void* out, void* stream) {
   return SYMHSS_OK;
 }
 
+int symhss_pivot_reciprocal(const void* a, int n, void* out, void* stream) {
+  if (n < 0 || (n > 0 && (!a || !out))) return SYMHSS_ERR_INVALID;
+  if (n == 0) return SYMHSS_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  CKE(launch_pivot_reciprocal(reinterpret_cast<const double2*>(a), n, reinterpret_cast<double2*>(out), s));
+  CKE(cudaStreamSynchronize(s));
+  return SYMHSS_OK;
+}
+
 int symhss_kernel_block(const symhss_params* prm, const symhss_points* obs, const int* obs_eq,
                         const symhss_points* src, const int* src_comp, int scaled, void* out, int ld,
                         void* stream) {

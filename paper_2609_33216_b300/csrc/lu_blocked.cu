@@ -225,6 +225,7 @@ __global__ void __launch_bounds__(kClusterPanelThreads) panel_cluster_kernel(con
   __shared__ double2 s_inv;
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
+  const int lgC = __ffs(C) - 1;  // C is a power of two
   const int rank = (int)cl.block_rank();
   const LuJob jb = a.jobs[blockIdx.x / C];
   const int n = jb.n, ld = jb.ld;
@@ -273,7 +274,7 @@ __global__ void __launch_bounds__(kClusterPanelThreads) panel_cluster_kernel(con
       br = lane < kWarps ? redr[lane] : -1;
       warp_argmax_key_redux(bk, bi, br);
       if (lane == 0) { cand[par].k = bk; cand[par].pos = bi; cand[par].phys = br; }
-      const int li = br >= 0 ? (br - rank) / C : 0;
+      const int li = br >= 0 ? (br - rank) >> lgC : 0;
       if (lane < w) {
         double2 v = br >= 0 ? P[lane * lmax + li] : make_double2(0.0, 0.0);
         // the pending update of pivot c - 1 on this row (the same arithmetic the deferred
@@ -765,6 +766,18 @@ cudaError_t getrf_impl(const LuLaunch& a, cudaStream_t s) {
   // the last panel's interchanges still have to reach the columns left of it
   const int jlast = ((a.max_n - 1) / kNb) * kNb;
   swap_trsm_warp_kernel<CT><<<dim3(a.njobs, ncolblk), 256, 0, s>>>(a, jlast, 0, a.max_n, 1, 0);
+  symhss::count_launches(1);
+  return cudaGetLastError();
+}
+
+__global__ void pivot_reciprocal_kernel(const double2* a, int n, double2* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = cinv_pivot(a[i]);
+}
+
+cudaError_t launch_pivot_reciprocal(const double2* a, int n, double2* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  pivot_reciprocal_kernel<<<(n + 255) / 256, 256, 0, s>>>(a, n, out);
   symhss::count_launches(1);
   return cudaGetLastError();
 }

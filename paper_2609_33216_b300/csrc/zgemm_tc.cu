@@ -379,6 +379,32 @@ __global__ void __launch_bounds__(kMmaThreads, 2) zgemm_tc_kernel(const ZgemmLau
     if (tid < kTileM) s_e[tid] = L.ea[ablk * kTileM + tid];
     if (tid < kTileNc) s_fexp[tid] = L.fb[bblk * kTileNc + tid];
   }
+  // inline slicing: the operand loads are issued before the setup below, which their latency
+  // then overlaps.  A: thread (rt, half) holds a(r0 + rt, 8 half .. + 7); B: thread (bc, comp,
+  // kh), tid < 64, component comp of b(8 kh .. + 7, c0 + bc)
+  double re[8], im[8], xb[8];
+  const int rt = tid & (kTileM - 1), half = tid >> 7;
+  const int bc = tid >> 2, comp = (tid >> 1) & 1, kh = tid & 1;
+  if (a.inline_slice) {
+    const double2* A = a.A + jb.a_off;
+    const int row = r0 + rt;
+#pragma unroll
+    for (int e8 = 0; e8 < 8; ++e8) {
+      const int k = 8 * half + e8;
+      const double2 v = (row < m && k < K) ? A[row + (long long)k * jb.lda] : make_double2(0.0, 0.0);
+      re[e8] = v.x;
+      im[e8] = v.y;
+    }
+    if (tid < 4 * kTileNc) {
+      const double2* B = a.B + jb.b_off;
+#pragma unroll
+      for (int e8 = 0; e8 < 8; ++e8) {
+        const int k = 8 * kh + e8;
+        const double2 v = (c0 + bc < n && k < K) ? B[k + (long long)(c0 + bc) * jb.ldb] : make_double2(0.0, 0.0);
+        xb[e8] = comp ? v.y : v.x;
+      }
+    }
+  }
   if (a.mode != ZGEMM_SET && warp == 1) {
     // the old values of the tile's columns into L2 while the MMAs run (one column per lane)
     const int col = c0 + lane, rows = min(kTileM, m - r0);
@@ -411,38 +437,19 @@ __global__ void __launch_bounds__(kMmaThreads, 2) zgemm_tc_kernel(const ZgemmLau
     // one chunk (k <= 16): the block slices its own operands into the stage (row / column
     // exponents over this chunk, which is all of k), no images and no slicing launch
     __shared__ int s_eh[2][kTileM];
-    const int rt = tid & (kTileM - 1), half = tid >> 7;
-    const int row = r0 + rt;
-    const double2* A = a.A + jb.a_off;
-    const double2* B = a.B + jb.b_off;
-    double re[8], im[8];
     int e = 0;
 #pragma unroll
-    for (int e8 = 0; e8 < 8; ++e8) {
-      const int k = 8 * half + e8;
-      const double2 v = (row < m && k < K) ? A[row + (long long)k * jb.lda] : make_double2(0.0, 0.0);
-      re[e8] = v.x;
-      im[e8] = v.y;
-      e = max(e, max(bexp(v.x), bexp(v.y)));
-    }
+    for (int e8 = 0; e8 < 8; ++e8) e = max(e, max(bexp(re[e8]), bexp(im[e8])));
     s_eh[half][rt] = e;
-    // B: thread (c, comp, kh) for tid < 64: component comp of b(8 kh .. + 7, c0 + c)
-    double xb[8];
-    const int cb = tid >> 2, comp = (tid >> 1) & 1, kh = tid & 1;
     int fb = 0;
     if (tid < 4 * kTileNc) {
 #pragma unroll
-      for (int e8 = 0; e8 < 8; ++e8) {
-        const int k = 8 * kh + e8;
-        const double2 v = (c0 + cb < n && k < K) ? B[k + (long long)(c0 + cb) * jb.ldb] : make_double2(0.0, 0.0);
-        xb[e8] = comp ? v.y : v.x;
-        fb = max(fb, bexp(xb[e8]));
-      }
+      for (int e8 = 0; e8 < 8; ++e8) fb = max(fb, bexp(xb[e8]));
     }
     if (warp < 2) {  // the column's largest over its four threads (lanes 4c .. 4c + 3)
       fb = max(fb, __shfl_xor_sync(0xffffffffu, fb, 1));
       fb = max(fb, __shfl_xor_sync(0xffffffffu, fb, 2));
-      if (tid < 4 * kTileNc && (tid & 3) == 0) s_fexp[cb] = fb;
+      if (tid < 4 * kTileNc && (tid & 3) == 0) s_fexp[bc] = fb;
     }
     __syncthreads();
     const int ea = max(s_eh[0][rt], s_eh[1][rt]);
@@ -460,10 +467,10 @@ __global__ void __launch_bounds__(kMmaThreads, 2) zgemm_tc_kernel(const ZgemmLau
     }
     if (tid < 4 * kTileNc) {
       unsigned char* sB = smem + kAChunkBytes;
-      const int np1 = 2 * cb + comp, q1 = kh, np2 = 2 * cb + 1 - comp, q2 = kh + 2;
+      const int np1 = 2 * bc + comp, q1 = kh, np2 = 2 * bc + 1 - comp, q2 = kh + 2;
       const uint32_t flip2 = comp ? 0x80008000u : 0u;
       uint32_t pk[kSlices][4];
-      slice_pack8(xb, s_fexp[cb], pk);
+      slice_pack8(xb, s_fexp[bc], pk);
 #pragma unroll
       for (int t = 0; t < kSlices; ++t) {
         unsigned char* sl = sB + t * kBSliceBytes;

@@ -127,6 +127,7 @@ _SIGNATURES = [
                                        C.c_void_p, C.c_void_p]),
     ("symhss_launch_count", C.c_longlong, []),
     ("symhss_hankel01", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    ("symhss_pivot_reciprocal", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     ("symhss_speed_terms", C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     ("symhss_set_wait_limit_ns", C.c_int, [C.c_longlong]),
     ("symhss_set_timeout_probe", C.c_int, [C.c_int]),
@@ -277,6 +278,11 @@ def symhss_level_ranks(h, level: int):
 
 def symhss_destroy(h) -> None:
     check(lib.symhss_destroy(h), "symhss_destroy")
+
+
+def symhss_pivot_reciprocal(a_ptr: int, n: int, out_ptr: int, stream: int = 0) -> None:
+    check(lib.symhss_pivot_reciprocal(C.c_void_p(a_ptr), n, C.c_void_p(out_ptr), C.c_void_p(stream)),
+          "symhss_pivot_reciprocal")
 
 
 def symhss_hankel01(x_ptr: int, n: int, out_ptr: int, stream: int = 0) -> None:

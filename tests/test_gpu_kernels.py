@@ -76,6 +76,38 @@ def test_hankel_matches_mpmath(S):
         assert rel.max() <= 5e-15, (n, rel.max(), x[np.argmax(rel)])
 
 
+def test_pivot_reciprocal_within_ulps_of_exact(S):
+    """The LU panels' pivot reciprocal (conj(a) / |a|^2, 1 / |a|^2 by two Newton steps from the
+    hardware's approximate reciprocal; Smith's division outside [2^-996, 2^997)) against the
+    exact 1 / a in rational arithmetic: each component within 4 units of 2^-53 |1 / a| (the
+    rounding of |a|^2, of the reciprocal and of the final products), and zero gives no finite
+    value."""
+    from fractions import Fraction
+    rng = np.random.default_rng(5)
+    mag = 10.0 ** rng.uniform(-290, 290, 3000)
+    ph = rng.uniform(0, 2 * np.pi, 3000)
+    a = mag * np.exp(1j * ph)
+    edge = np.array([1.0, -1.0, 1j, -1j, 2.0 ** -500 + 0j, 2.0 ** 498, 3.0 - 4.0j, 1e-160 + 1e-161j,
+                     1e155 - 1e154j, 2.0 ** -510 * (1 + 1j), 2.0 ** 511 * (1 - 1j)])
+    a = np.concatenate([a, edge])
+    dev = torch.as_tensor(a).to("cuda")
+    out = torch.empty_like(dev)
+    S.symhss_pivot_reciprocal(dev.data_ptr(), len(a), out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    for v, g in zip(a, got):
+        x, y = Fraction(float(v.real)), Fraction(float(v.imag))
+        s2 = x * x + y * y
+        ex, ey = x / s2, -y / s2
+        scale = abs(complex(float(ex), float(ey)))
+        tol = 4 * 2.0 ** -53 * scale
+        assert abs(float(Fraction(float(g.real)) - ex)) <= tol and abs(float(Fraction(float(g.imag)) - ey)) <= tol, (v, g)
+    z = torch.zeros(1, dtype=torch.complex128, device="cuda")
+    S.symhss_pivot_reciprocal(z.data_ptr(), 1, out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert not np.isfinite(out[:1].cpu().numpy()).all()
+
+
 @pytest.mark.parametrize("scaled", [True, False], ids=["scaled", "unscaled"])
 def test_tiles_match_oracle_on_nodes_and_proxies(S, scaled):
     c = fourier_star(300, ((3, 0.2, 0.1), (5, 0.05, 0.7)))
