@@ -480,8 +480,14 @@ struct RsLaunch {
   const int* perm = nullptr;      // optional: the LU's row permutations (LuLaunch::perm); else
                                   // every solve composes them from piv
   int blk = 64;                   // row block of the blocked tensor-core solve: 16, 32 or 64
+  double2* dinv = nullptr;        // optional scratch, getrs_dinv_bytes(njobs, max_n): the blocked
+  long long dinv_bytes = 0;       // solve with 64-row blocks and few matrices (< 32) then solves its
+                                  // diagonal blocks through their inverses on the tensor cores
 };
 cudaError_t launch_getrs(const RsLaunch& a, cudaStream_t s);
+// bytes of RsLaunch::dinv: two 64 x 64 complex128 blocks (the inverses of L's unit-lower and U's
+// upper diagonal block) per 64-row block of every matrix
+long long getrs_dinv_bytes(int njobs, int max_n);
 // scratch of the tensor-core products of a blocked LU / blocked solve launch
 long long zgemm_lu_img_bytes(int njobs, int max_n);
 long long zgemm_rs_img_bytes(int njobs, int max_n, int max_rhs);
@@ -501,6 +507,8 @@ enum : int {
   ZGEMM_LU_UPDATE = 1,  // LuJob: A[J+W:n, J+W:n] -= A[J+W:n, J:J+W] A[J:J+W, J+W:n], W = block_w
   ZGEMM_RS_FWD = 2,     // RsJob: X[J+W:n, :] -= L[J+W:n, J:J+W] X[J:J+W, :]
   ZGEMM_RS_BWD = 3,     // RsJob: X[0:J, :] -= U[0:J, J:J+W] X[J:J+W, :]
+  ZGEMM_RS_FWD_DIAG = 4,  // RsJob: X[J:J+W, :] = inv(L[J:J+W, J:J+W]) X[J:J+W, :] (A: the inverse scratch)
+  ZGEMM_RS_BWD_DIAG = 5,  // RsJob: X[J:J+W, :] = inv(U[J:J+W, J:J+W]) X[J:J+W, :] (A: the inverse scratch)
 };
 struct ZgemmLaunch {
   const double2* A;
@@ -517,6 +525,7 @@ struct ZgemmLaunch {
   const RsJob* rs_jobs = nullptr;
   int block_j = 0;     // J of the derived jobs
   int block_w = 64;    // W: width of the column block J .. J + W of the derived jobs
+  int inv_nb = 0;      // RS_*_DIAG: 64-row blocks per matrix in the inverse scratch (A)
   int mtiles = 0, ntiles_c = 0;  // row / column blocks per job (explicit jobs: the largest)
   int njobs = 0;                   // jobs of the launch
   int inline_slice = 0;            // every job has k <= 16: each tile slices its own operands

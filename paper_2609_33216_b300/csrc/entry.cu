@@ -462,6 +462,12 @@ int symhss_lu_solve_batched(const void* LU, int n, int lda, long long strideA, c
     CKE(zimg.alloc((size_t)a.zimg_bytes));
     a.zimg = reinterpret_cast<unsigned char*>(zimg.p);
   }
+  TmpBuf dinv;  // inverses of the diagonal blocks (blocked solve of few matrices)
+  if (batch < 32 && nrhs > 4) {
+    a.dinv_bytes = getrs_dinv_bytes(batch, n);
+    CKE(dinv.alloc((size_t)a.dinv_bytes));
+    a.dinv = reinterpret_cast<double2*>(dinv.p);
+  }
   CKE(launch_getrs(a, s));
   int st = 0;
   CKE(cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -591,6 +591,91 @@ __global__ void __launch_bounds__(kRhsWarps * 32) getrs_rhs_small_kernel(const R
   }
 }
 
+// Inverses of the 64-row diagonal blocks of the factors, for the blocked solve that applies
+// them on the tensor cores: block (matrix blockIdx.x, row block blockIdx.y), side blockIdx.z / 8
+// (0: L's unit-lower block, 1: U's upper block), columns 8 (blockIdx.z % 8) .. + 7 of the
+// inverse.  Column c of the inverse solves the block against e_c by substitution, the eight
+// columns on lanes (lane % 8) and the rows on 16 slots (warp, lane / 8), four rows each; one
+// block barrier per step publishes the step's value of each column.  Written to dinv: per
+// (matrix, row block) the inverse of L's block then of U's block, 64 x 64 column-major (entries
+// outside the block's w x w are zero).
+constexpr int kInvThreads = 128;
+__global__ void __launch_bounds__(kInvThreads) trinv_kernel(const RsLaunch a, int nbmax) {
+  pdl_enter();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* tri = reinterpret_cast<double2*>(smem_raw);  // 64 x 64, column-major: tri[k * 64 + i]
+  double2* dinv_u = tri + 64 * 64;                      // 1 / U_kk
+  double2* xs = dinv_u + 64;                             // [2][8]: the step's values, by parity
+  const RsJob jb = a.jobs[blockIdx.x];
+  const int J = blockIdx.y * 64;
+  const int n = jb.n;
+  if (n > a.max_n || J >= n) return;  // uniform per block
+  const int w = min(64, n - J);
+  const int upper = blockIdx.z >> 3, g = blockIdx.z & 7;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int cl = lane & 7, slot = warp * 4 + (lane >> 3);
+  const int col = 8 * g + cl;
+  const double2* A = a.abase + jb.a_off + J + (long long)J * jb.lda;
+  for (int e = tid; e < 64 * 64; e += kInvThreads) {
+    const int i = e & 63, k = e >> 6;
+    tri[e] = (i < w && k < w) ? A[i + (long long)k * jb.lda] : make_double2(0.0, 0.0);
+  }
+  if (upper)
+    for (int k = tid; k < w; k += kInvThreads) dinv_u[k] = cinv(A[k + (long long)k * jb.lda]);
+  double2 x[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) x[m] = make_double2(slot + 16 * m == col && col < w ? 1.0 : 0.0, 0.0);
+  __syncthreads();
+  int par = 0;
+  if (!upper) {
+    // L y = e_col: for k = 8g .. w - 2, rows i > k take -L_ik y_k (y_k = 0 for k < col)
+#pragma unroll
+    for (int mk = 0; mk < 4; ++mk) {
+      for (int kk = 0; kk < 16; ++kk) {
+        const int k = 16 * mk + kk;
+        if (k < 8 * g || k >= w - 1) continue;  // uniform
+        if (slot == kk) xs[par * 8 + cl] = x[mk];
+        __syncthreads();
+        const double2 xk = xs[par * 8 + cl];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const int i = slot + 16 * m;
+          if (i > k && i < w) x[m] = cfms(tri[k * 64 + i], xk, x[m]);
+        }
+        par ^= 1;
+      }
+    }
+  } else {
+    // U y = e_col: for k = min(8g + 7, w - 1) .. 0, y_k /= U_kk, rows i < k take -U_ik y_k
+    const int kmax = min(8 * g + 7, w - 1);
+#pragma unroll
+    for (int mk = 3; mk >= 0; --mk) {
+      for (int kk = 15; kk >= 0; --kk) {
+        const int k = 16 * mk + kk;
+        if (k > kmax) continue;  // uniform
+        if (slot == kk) {
+          x[mk] = cmul(x[mk], dinv_u[k]);
+          xs[par * 8 + cl] = x[mk];
+        }
+        __syncthreads();
+        const double2 xk = xs[par * 8 + cl];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const int i = slot + 16 * m;
+          if (i < k) x[m] = cfms(tri[k * 64 + i], xk, x[m]);
+        }
+        par ^= 1;
+      }
+    }
+  }
+  double2* out = a.dinv + (((long long)blockIdx.x * nbmax + blockIdx.y) * 2 + upper) * 4096 + (long long)col * 64;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const int i = slot + 16 * m;
+    out[i] = (i < w && col < w) ? x[m] : make_double2(0.0, 0.0);
+  }
+}
+
 cudaError_t getrs_blocked_tc(const RsLaunch& a, cudaStream_t s) {
   const int max_n = a.max_n;
   int warps = kRsMaxWarps;
@@ -637,6 +722,51 @@ cudaError_t getrs_blocked_tc(const RsLaunch& a, cudaStream_t s) {
   // one serial chain on s: every kernel after the permutation is a programmatic dependent of
   // the one before it
   g.chained = 1;
+  // few matrices (the upper tree levels): the diagonal blocks through their inverses, formed
+  // once (trinv_kernel) and applied as tensor-core products, instead of substitutions on the
+  // FP64 pipe, which there run one right-hand side per warp
+  const int nbmax = (max_n + 63) / 64;
+  if (W == kBlk && !rhs_lanes && a.dinv && a.dinv_bytes >= getrs_dinv_bytes(a.njobs, max_n)) {
+    const size_t ismem = (size_t)(64 * 64 + 64 + 16) * sizeof(double2);
+    if ((e = cudaFuncSetAttribute(trinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ismem)) !=
+        cudaSuccess)
+      return e;
+    e = launch_chained(true, trinv_kernel, dim3(a.njobs, nbmax, 16), dim3(kInvThreads), ismem, s, a, nbmax);
+    symhss::count_launches(1);
+    if (e != cudaSuccess) return e;
+    ZgemmLaunch gd = g;
+    gd.A = a.dinv;
+    gd.mode = ZGEMM_SET;
+    gd.inv_nb = nbmax;
+    gd.mtiles = 1;  // a 64-row block
+    gd.ntiles = a.njobs * gd.ntiles_c;
+    for (int J = 0; J < max_n; J += W) {
+      gd.derive = ZGEMM_RS_FWD_DIAG;
+      gd.block_j = J;
+      if ((e = launch_zgemm_tc(gd, s)) != cudaSuccess) return e;
+      const int below = max_n - J - W;
+      if (below > 0) {
+        g.derive = ZGEMM_RS_FWD;
+        g.block_j = J;
+        g.mtiles = (below + zgemm_tc_tile_rows() - 1) / zgemm_tc_tile_rows();
+        g.ntiles = a.njobs * g.mtiles * g.ntiles_c;
+        if ((e = launch_zgemm_tc(g, s)) != cudaSuccess) return e;
+      }
+    }
+    for (int J = ((max_n - 1) / W) * W; J >= 0; J -= W) {
+      gd.derive = ZGEMM_RS_BWD_DIAG;
+      gd.block_j = J;
+      if ((e = launch_zgemm_tc(gd, s)) != cudaSuccess) return e;
+      if (J > 0) {
+        g.derive = ZGEMM_RS_BWD;
+        g.block_j = J;
+        g.mtiles = (J + zgemm_tc_tile_rows() - 1) / zgemm_tc_tile_rows();
+        g.ntiles = a.njobs * g.mtiles * g.ntiles_c;
+        if ((e = launch_zgemm_tc(g, s)) != cudaSuccess) return e;
+      }
+    }
+    return cudaSuccess;
+  }
   for (int J = 0; J < max_n; J += W) {
     if (rhs_lanes) e = launch_chained(true, trsv_rhs_kernel<true>, rgrid, dim3(kRhsWarps * 32), rsmem, s, a, J, W);
     else e = launch_chained(true, trsv_block_kernel<true>, grid, dim3(warps * 32), tsmem, s, a, J, warps, W);
@@ -750,6 +880,10 @@ cudaError_t getrs_impl(const RsLaunch& a, cudaStream_t s) {
   getrs_kernel<CT><<<grid, warps * 32, smem, s>>>(a, warps);
   symhss::count_launches(1);
   return cudaGetLastError();
+}
+
+long long getrs_dinv_bytes(int njobs, int max_n) {
+  return (long long)njobs * ((max_n + 63) / 64) * 2 * 4096 * (long long)sizeof(double2);
 }
 
 cudaError_t launch_getrs(const RsLaunch& a, cudaStream_t s) {

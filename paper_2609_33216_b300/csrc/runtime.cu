@@ -163,6 +163,7 @@ struct Height {
   DevBuf chkmeta, chkg;          // exact residual checks of sketched IDs (proposer mode)
   DevBuf chkimg;                 // their tensor-core product scratch (compression stream)
   DevBuf zimg;                   // tensor-core product scratch of the factorisation stream
+  DevBuf dinv;                   // inverses of the diagonal blocks of the blocked solves (< 32 blocks)
   // matvec
   DevBuf XV, XS, ZV, YS, YV, mlists;
   std::vector<int> h_rank;
@@ -1464,6 +1465,13 @@ int factor_height(symhss_s* h, int t, cudaStream_t s, long long& pairs, bool lu_
   }
   ra.zimg = H.zimg.as<unsigned char>();
   ra.zimg_bytes = (long long)H.zimg.cap;
+  if ((int)refs.size() < 32) {
+    // the blocked solves of few blocks apply their diagonal blocks' inverses on the tensor cores
+    CK(H.dinv.ensure((size_t)std::max(getrs_dinv_bytes((int)refs.size(), max_n),
+                                       getrs_dinv_bytes((int)refs.size(), max_k))));
+    ra.dinv = H.dinv.as<double2>();
+    ra.dinv_bytes = (long long)H.dinv.cap;
+  }
   ra.perm = H.perm.as<int>();
   TIMED(SYMHSS_K_GETRS, w_x, launch_getrs(ra, s));
   // R X
@@ -1519,6 +1527,8 @@ int factor_height(symhss_s* h, int t, cudaStream_t s, long long& pairs, bool lu_
   rb.tc = h->tune.lu_tc;
   rb.zimg = H.zimg.as<unsigned char>();
   rb.zimg_bytes = (long long)H.zimg.cap;
+  rb.dinv = ra.dinv;
+  rb.dinv_bytes = ra.dinv_bytes;
   rb.perm = H.rxperm.as<int>();
   TIMED(SYMHSS_K_GETRS, w_at, launch_getrs(rb, s));
   if (mixed) {  // X and Atilde in FP64 for the parents' blocks and the solve phase

@@ -184,6 +184,15 @@ __device__ __forceinline__ ZgemmJob decode_job(const ZgemmLaunch& a, int jidx) {
     jb.a_off = lj.a_off + (J + W) + (long long)J * lj.ld;
     jb.b_off = lj.a_off + J + (long long)(J + W) * lj.ld;
     jb.c_off = lj.a_off + (J + W) + (long long)(J + W) * lj.ld;
+  } else if (a.derive == ZGEMM_RS_FWD_DIAG || a.derive == ZGEMM_RS_BWD_DIAG) {
+    // the diagonal block's inverse (64 x 64, column-major, L's then U's per block) times the
+    // block's rows of X, written over them (the slicing launch has read them first)
+    const RsJob rj = a.rs_jobs[jidx];
+    const int W = a.block_w;
+    jb.m = jb.k = min(W, rj.n - J); jb.n = rj.nrhs;
+    jb.lda = 64; jb.ldb = jb.ldc = rj.ldb;
+    jb.a_off = (((long long)jidx * a.inv_nb + J / 64) * 2 + (a.derive == ZGEMM_RS_BWD_DIAG ? 1 : 0)) * 4096;
+    jb.b_off = jb.c_off = rj.b_off + J;
   } else {
     const RsJob rj = a.rs_jobs[jidx];
     const int W = a.block_w;

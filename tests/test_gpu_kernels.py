@@ -231,6 +231,14 @@ def _lu_solve_case(S, n, nrhs, batch):
         assert np.linalg.norm(x[i] - ref) <= 1e-12 * np.linalg.cond(a[i]) * np.linalg.norm(ref), (n, nrhs)
 
 
+@pytest.mark.parametrize("n,nrhs,batch", [(500, 280, 2), (257, 130, 4), (130, 600, 1), (64 * 5, 17, 31)])
+def test_lu_inverse_blocked_solves(S, n, nrhs, batch):
+    """Many right-hand sides on few blocks (< 32): the blocked solve forms the inverses of its
+    64-row diagonal blocks (unit-lower and upper) and applies them as tensor-core products, the
+    off-diagonal blocks as before; ragged last block, one and several matrices."""
+    _lu_solve_case(S, n, nrhs, batch)
+
+
 @pytest.mark.parametrize("n,nrhs,batch", [(600, 1, 1), (1000, 2, 3), (130, 1, 9), (2048, 1, 1), (300, 4, 20)])
 def test_lu_cluster_solves(S, n, nrhs, batch):
     """Few right-hand sides on few large blocks: the solve runs on a thread-block cluster per
