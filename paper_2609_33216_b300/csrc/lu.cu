@@ -726,7 +726,7 @@ cudaError_t getrs_blocked_tc(const RsLaunch& a, cudaStream_t s) {
   // once (trinv_kernel) and applied as tensor-core products, instead of substitutions on the
   // FP64 pipe, which there run one right-hand side per warp
   const int nbmax = (max_n + 63) / 64;
-  if (W == kBlk && !rhs_lanes && a.dinv && a.dinv_bytes >= getrs_dinv_bytes(a.njobs, max_n)) {
+  if (W == kBlk && a.dinv && a.dinv_bytes >= getrs_dinv_bytes(a.njobs, max_n)) {
     const size_t ismem = (size_t)(64 * 64 + 64 + 16) * sizeof(double2);
     if ((e = cudaFuncSetAttribute(trinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ismem)) !=
         cudaSuccess)

@@ -1465,8 +1465,8 @@ int factor_height(symhss_s* h, int t, cudaStream_t s, long long& pairs, bool lu_
   }
   ra.zimg = H.zimg.as<unsigned char>();
   ra.zimg_bytes = (long long)H.zimg.cap;
-  if ((int)refs.size() < 32) {
-    // the blocked solves of few blocks apply their diagonal blocks' inverses on the tensor cores
+  {
+    // the blocked solves apply their diagonal blocks' inverses on the tensor cores
     CK(H.dinv.ensure((size_t)std::max(getrs_dinv_bytes((int)refs.size(), max_n),
                                        getrs_dinv_bytes((int)refs.size(), max_k))));
     ra.dinv = H.dinv.as<double2>();
