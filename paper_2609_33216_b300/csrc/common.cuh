@@ -25,6 +25,12 @@ __device__ __forceinline__ double2 cmulc(double2 a, double2 b) {
 __device__ __forceinline__ double2 cconjmul(double2 a, double2 b) {
   return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.x, b.y, -a.y * b.x));
 }
+// acc += conj(a) * b, four fused multiply-adds
+__device__ __forceinline__ double2 cconjfma(double2 a, double2 b, double2 acc) {
+  return make_double2(fma(a.x, b.x, fma(a.y, b.y, acc.x)), fma(a.x, b.y, fma(-a.y, b.x, acc.y)));
+}
+// acc + |a|^2, two fused multiply-adds
+__device__ __forceinline__ double cabs2_acc(double2 a, double acc) { return fma(a.x, a.x, fma(a.y, a.y, acc)); }
 // acc += a * b
 __device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 acc) {
   return make_double2(fma(a.x, b.x, fma(-a.y, b.y, acc.x)), fma(a.x, b.y, fma(a.y, b.x, acc.y)));

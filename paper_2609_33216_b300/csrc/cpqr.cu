@@ -171,7 +171,10 @@ __global__ void __launch_bounds__(kThreads) cpqr_cluster_kernel(const IdLaunch a
     const double tau = s_tau;
     // 4. apply to owned remaining columns, recompute their remaining norms: 8 lanes per
     //    column, 4 columns per warp (each column segment is one 128-byte line; the lane sums
-    //    take 3 shuffle levels instead of 5, and fewer lanes idle at the column's end)
+    //    take 3 shuffle levels instead of 5, and fewer lanes idle at the column's end).
+    //    Every sum is a chain of fused multiply-adds (4 per element for v^H c, 2 for |c|^2):
+    //    the FP64 pipe bounds this loop on this GPU, and separate products and additions
+    //    would issue 13 FP64 instructions per element instead of 10.
     {
       const int grp = lane >> 3, gl = lane & 7;
       const int nown = (n - rank + C - 1) / C;  // owned columns: j = rank + C * t, t < nown
@@ -182,7 +185,7 @@ __global__ void __launch_bounds__(kThreads) cpqr_cluster_kernel(const IdLaunch a
         double2* col = M + (long long)(act ? j : 0) * ld;
         double2 w = make_double2(0.0, 0.0);
         if (act)
-          for (int i = k + gl; i < m; i += 8) w = cadd(w, cconjmul(vbuf[i - k], col[i]));
+          for (int i = k + gl; i < m; i += 8) w = cconjfma(vbuf[i - k], col[i], w);
 #pragma unroll
         for (int o = 4; o > 0; o >>= 1) {
           w.x += __shfl_xor_sync(0xffffffffu, w.x, o);
@@ -194,7 +197,7 @@ __global__ void __launch_bounds__(kThreads) cpqr_cluster_kernel(const IdLaunch a
           for (int i = k + gl; i < m; i += 8) {
             const double2 c = cfms(vbuf[i - k], w, col[i]);
             col[i] = c;
-            if (i > k) ns += cabs2(c);
+            if (i > k) ns = cabs2_acc(c, ns);
           }
 #pragma unroll
         for (int o = 4; o > 0; o >>= 1) ns += __shfl_xor_sync(0xffffffffu, ns, o);
