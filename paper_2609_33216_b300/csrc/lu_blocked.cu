@@ -382,9 +382,14 @@ __global__ void __launch_bounds__(kClusterPanelThreads) panel_cluster_kernel(con
 // one column per lane.
 // tlo, thi: the solve covers only columns in [max(j + w, tlo), thi); swaps = 0: no
 // interchanges (the columns are already permuted); cbase: first column of blockIdx.y = 0.
-template <typename CT>
-__global__ void __launch_bounds__(256) swap_trsm_warp_kernel(const LuLaunch a, int j, int tlo, int thi, int swaps,
-                                                              int cbase) {
+// CB columns per block: 32 (256 threads; the solve with the columns on the lanes and the rows
+// over warps 0..3) or 8 (128 threads; the solve with lane = column + 8 x row group, each of the
+// 16 rows on one thread: four times the blocks for the same FP64 work, for launches whose
+// 32-column blocks would leave most SMs idle).
+template <typename CT, int CB>
+__global__ void __launch_bounds__(CB == 32 ? 256 : 128) swap_trsm_warp_kernel(const LuLaunch a, int j, int tlo,
+                                                                               int thi, int swaps, int cbase) {
+  constexpr int NT = CB == 32 ? 256 : 128, NW = NT / 32, CPW = CB / NW;
   pdl_enter();
   __shared__ CT l11[kNb][kNb];
   __shared__ int rows_s[2 * kNb];   // row set: j..j+w-1, then the outside pivot rows
@@ -397,7 +402,7 @@ __global__ void __launch_bounds__(256) swap_trsm_warp_kernel(const LuLaunch a, i
   CT* A = lu_base<CT>(a) + jb.a_off;
   __shared__ int piv_s[kNb];
   if (threadIdx.x < w) piv_s[threadIdx.x] = a.piv[jb.piv_off + j + threadIdx.x];
-  for (int e = threadIdx.x; e < w * w; e += 256) {
+  for (int e = threadIdx.x; e < w * w; e += NT) {
     const int r = e % w, c = e / w;
     l11[r][c] = A[j + r + (long long)(j + c) * ld];
   }
@@ -441,46 +446,59 @@ __global__ void __launch_bounds__(256) swap_trsm_warp_kernel(const LuLaunch a, i
     }
   }
   __syncthreads();
-  __shared__ CT xs[kNb][32];  // rows j .. j + w - 1 of the block's 32 columns, after the interchanges
+  __shared__ CT xs[kNb][CB];  // rows j .. j + w - 1 of the block's CB columns, after the interchanges
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int cnt = nrows_s;
   const int tl = max(j + w, tlo), th = min(thi, n);
-  const int cfirst = cbase + blockIdx.y * 32;
+  const int cfirst = cbase + blockIdx.y * CB;
   // a column takes part if it is interchanged, or (without interchanges) if it is solved
   auto part = [&](int col) {
     return col < n && !(col >= j && col < j + w) && (swaps || (col >= tl && col < th));
   };
   // interchanges: one column per warp at a time, the lanes over the row set
-  // (the four columns of a warp are loaded before any of them is written: each column's
-  // stores touch only that column, so the loads need not wait for them)
-  CT xv[4];
+  // (the columns of a warp are loaded before any of them is written: each column's stores
+  // touch only that column, so the loads need not wait for them)
+  CT xv[CPW];
   const int src = lane < cnt ? src_s[lane] : 0;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int col = cfirst + warp + 8 * i;
+  for (int i = 0; i < CPW; ++i) {
+    const int col = cfirst + warp + NW * i;
     xv[i] = (part(col) && lane < cnt) ? A[(long long)col * ld + src] : make_c<CT>(0.0, 0.0);
   }
   __syncwarp();
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int cl = warp + 8 * i, col = cfirst + cl;
+  for (int i = 0; i < CPW; ++i) {
+    const int cl = warp + NW * i, col = cfirst + cl;
     if (!part(col)) continue;  // uniform per warp
     if (swaps && lane >= w && lane < cnt) A[(long long)col * ld + rows_s[lane]] = xv[i];
     if (lane < w) xs[lane][cl] = xv[i];
   }
-  // L11 U12 = A12 with the 32 columns on the lanes (every lane of an FP64 instruction works),
-  // rows split over warps 0..3 by row mod 4
-  const int col = cfirst + lane;
-  const bool solve = col >= tl && col < th;
-  for (int c = 0; c < w; ++c) {
-    __syncthreads();  // row c is final
-    if (warp < 4 && solve) {
-      const CT xc = xs[c][lane];
-      for (int r = c + 1 + ((warp - (c + 1)) & 3); r < w; r += 4) xs[r][lane] = cfms(l11[r][c], xc, xs[r][lane]);
+  if (CB == 32) {
+    // L11 U12 = A12 with the 32 columns on the lanes (every lane of an FP64 instruction works),
+    // rows split over warps 0..3 by row mod 4
+    const int col = cfirst + lane;
+    const bool solve = col >= tl && col < th;
+    for (int c = 0; c < w; ++c) {
+      __syncthreads();  // row c is final
+      if (warp < 4 && solve) {
+        const CT xc = xs[c][lane % CB];
+        for (int r = c + 1 + ((warp - (c + 1)) & 3); r < w; r += 4)
+          xs[r][lane % CB] = cfms(l11[r][c], xc, xs[r][lane % CB]);
+      }
+    }
+  } else {
+    // column lane % 8, row warp + 4 (lane / 8): one row per thread, the four rows of a warp
+    // in one instruction
+    const int cl = lane & 7, r = warp + 4 * (lane >> 3);
+    const int col = cfirst + cl;
+    const bool solve = col >= tl && col < th && r < w;
+    for (int c = 0; c < w; ++c) {
+      __syncthreads();  // row c is final
+      if (solve && r > c) xs[r][cl] = cfms(l11[r][c], xs[c][cl], xs[r][cl]);
     }
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < 32 * w; e += 256) {
+  for (int e = threadIdx.x; e < CB * w; e += NT) {
     const int r = e % w, cl = e / w;
     if (part(cfirst + cl)) A[(long long)(cfirst + cl) * ld + j + r] = xs[r][cl];
   }
@@ -604,6 +622,9 @@ cudaError_t getrf_impl(const LuLaunch& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
   }
   const int ncolblk = (a.max_n + 31) / 32;  // 32 columns per block of the interchange kernel
+  // 8 columns per block where 32-column blocks would leave most SMs idle (the upper levels)
+  const int ncolblk8 = (a.max_n + 7) / 8;
+  const bool narrow = (long long)a.njobs * ncolblk < device_sm_count();
   // Depth-1 look-ahead: after the interchanges and TRSM of panel j, the first trailing
   // tile column (which holds panel j + kNb) is updated first; panel j + kNb then runs on
   // a high-priority side stream while the rest of the trailing update runs on s.  The two
@@ -682,8 +703,10 @@ cudaError_t getrf_impl(const LuLaunch& a, cudaStream_t s) {
       if (rest > 0) {
         // interchanges in every column; U rows only in the block's own columns (a block of
         // one panel: in every column right of it, so that no second pass is needed)
-        e = launch_chained(chain, swap_trsm_warp_kernel<CT>, dim3(a.njobs, ncolblk), dim3(256), 0, s, a, j, 0,
-                           chain ? a.max_n : J + kOuter, 1, 0);
+        e = narrow ? launch_chained(chain, swap_trsm_warp_kernel<CT, 8>, dim3(a.njobs, ncolblk8), dim3(128), 0, s, a,
+                                    j, 0, chain ? a.max_n : J + kOuter, 1, 0)
+                   : launch_chained(chain, swap_trsm_warp_kernel<CT, 32>, dim3(a.njobs, ncolblk), dim3(256), 0, s, a,
+                                    j, 0, chain ? a.max_n : J + kOuter, 1, 0);
         symhss::count_launches(1);
         if (e != cudaSuccess) return e;
         const int pc = J + kOuter - (j + kNb);  // columns of the block right of this panel
@@ -699,7 +722,7 @@ cudaError_t getrf_impl(const LuLaunch& a, cudaStream_t s) {
         // applied: 16-row solves, each followed by the update of the block rows below it
         const int rblk = (right + 31) / 32;  // blocks of 32 columns starting at J + kOuter
         for (int jj = J; kOuter > kNb && jj < J + kOuter; jj += kNb) {
-          swap_trsm_warp_kernel<CT><<<dim3(a.njobs, rblk), 256, 0, s>>>(a, jj, J + kOuter, a.max_n, 0, J + kOuter);
+          swap_trsm_warp_kernel<CT, 32><<<dim3(a.njobs, rblk), 256, 0, s>>>(a, jj, J + kOuter, a.max_n, 0, J + kOuter);
           symhss::count_launches(1);
           if ((e = cudaGetLastError()) != cudaSuccess) return e;
           const int r = J + kOuter - (jj + kNb);
@@ -732,15 +755,17 @@ cudaError_t getrf_impl(const LuLaunch& a, cudaStream_t s) {
       if (j + kNb < a.max_n && (e = panel(j + kNb, s, chain)) != cudaSuccess) return e;
     }
     const int jlast = ((a.max_n - 1) / kNb) * kNb;
-    e = launch_chained(chain, swap_trsm_warp_kernel<CT>, dim3(a.njobs, ncolblk), dim3(256), 0, s, a, jlast, 0,
-                       a.max_n, 1, 0);
+    e = narrow ? launch_chained(chain, swap_trsm_warp_kernel<CT, 8>, dim3(a.njobs, ncolblk8), dim3(128), 0, s, a,
+                                jlast, 0, a.max_n, 1, 0)
+               : launch_chained(chain, swap_trsm_warp_kernel<CT, 32>, dim3(a.njobs, ncolblk), dim3(256), 0, s, a,
+                                jlast, 0, a.max_n, 1, 0);
     symhss::count_launches(1);
     return e;
   }
   for (int j = 0; j < a.max_n; j += kNb) {
     const int rest = a.max_n - j - kNb;
     if (rest <= 0) continue;
-    swap_trsm_warp_kernel<CT><<<dim3(a.njobs, ncolblk), 256, 0, s>>>(a, j, 0, a.max_n, 1, 0);
+    swap_trsm_warp_kernel<CT, 32><<<dim3(a.njobs, ncolblk), 256, 0, s>>>(a, j, 0, a.max_n, 1, 0);
     symhss::count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int rtiles = (rest + kTs - 1) / kTs;
@@ -765,7 +790,7 @@ cudaError_t getrf_impl(const LuLaunch& a, cudaStream_t s) {
   }
   // the last panel's interchanges still have to reach the columns left of it
   const int jlast = ((a.max_n - 1) / kNb) * kNb;
-  swap_trsm_warp_kernel<CT><<<dim3(a.njobs, ncolblk), 256, 0, s>>>(a, jlast, 0, a.max_n, 1, 0);
+  swap_trsm_warp_kernel<CT, 32><<<dim3(a.njobs, ncolblk), 256, 0, s>>>(a, jlast, 0, a.max_n, 1, 0);
   symhss::count_launches(1);
   return cudaGetLastError();
 }
