@@ -7,8 +7,12 @@
 // the bound the plain ID meets by construction -- and is otherwise redone as a plain ID
 // of M.  The kernel itself computes the ratio for whatever rows it is given.
 //
-// One block per ID: warps own columns; a lane walks the rows of its warp's column, so
-// reads of M are coalesced; per-column sums of squares are reduced with shuffles.
+// kCheckSplit blocks per ID, each taking every kCheckSplit-th group of columns: warps own
+// columns; a lane walks the rows of its warp's column, so reads of M are coalesced;
+// per-column sums of squares are reduced with shuffles.  The blocks' largest sums meet in
+// two 64-bit maxima per ID (the bit patterns of non-negative doubles order like the values),
+// and a second launch forms the ratio.  (One block per ID left the top levels' few IDs, whose
+// columns each take an r-step dependent chain, on a few SMs.)
 #include "common.cuh"
 
 namespace symhss {
@@ -16,10 +20,12 @@ namespace symhss {
 namespace {
 
 constexpr int kCheckThreads = 256;
+constexpr int kCheckSplit = 8;
 
 __global__ void __launch_bounds__(kCheckThreads) id_check_kernel(const double2* mats, const double2* tbuf,
                                                                  const int* perm, const int* rank,
-                                                                 const CheckJob* jobs, double* ratio) {
+                                                                 const CheckJob* jobs,
+                                                                 unsigned long long* acc) {
   __shared__ double s_max[2][kCheckThreads / 32];
   const CheckJob jb = jobs[blockIdx.x];
   const double2* M = mats + jb.m_off;
@@ -27,9 +33,10 @@ __global__ void __launch_bounds__(kCheckThreads) id_check_kernel(const double2* 
   const int* pm = perm + jb.perm_off;
   const int r = min(max(rank[jb.rank_idx], 0), jb.n);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kCheckThreads / 32;
+  const int c0 = warp + nw * blockIdx.y, cs = nw * kCheckSplit;
   double ref = 0.0, res = 0.0;
   // largest column norm of M
-  for (int c = warp; c < jb.n; c += nw) {
+  for (int c = c0; c < jb.n; c += cs) {
     const double2* col = M + (long long)c * jb.ld;
     double ss = 0.0;
     for (int i = lane; i < jb.m; i += 32) ss = fma(col[i].x, col[i].x, fma(col[i].y, col[i].y, ss));
@@ -37,7 +44,7 @@ __global__ void __launch_bounds__(kCheckThreads) id_check_kernel(const double2* 
     ref = fmax(ref, ss);
   }
   // residual of every non-skeleton column
-  for (int c = r + warp; c < jb.n; c += nw) {
+  for (int c = r + c0; c < jb.n; c += cs) {
     const double2* col = M + (long long)pm[c] * jb.ld;
     const double2* tc = T + (long long)(c - r) * r;
     double ss = 0.0;
@@ -54,8 +61,16 @@ __global__ void __launch_bounds__(kCheckThreads) id_check_kernel(const double2* 
   if (threadIdx.x == 0) {
     double a = 0.0, b = 0.0;
     for (int w = 0; w < nw; ++w) { a = fmax(a, s_max[0][w]); b = fmax(b, s_max[1][w]); }
-    ratio[jb.out] = a > 0.0 ? sqrt(b / a) : 0.0;
+    atomicMax(&acc[2 * jb.out], (unsigned long long)__double_as_longlong(a));
+    atomicMax(&acc[2 * jb.out + 1], (unsigned long long)__double_as_longlong(b));
   }
+}
+
+__global__ void id_check_ratio_kernel(const unsigned long long* acc, int n, double* ratio) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double a = __longlong_as_double((long long)acc[2 * i]), b = __longlong_as_double((long long)acc[2 * i + 1]);
+  ratio[i] = a > 0.0 ? sqrt(b / a) : 0.0;
 }
 
 }  // namespace
@@ -63,7 +78,14 @@ __global__ void __launch_bounds__(kCheckThreads) id_check_kernel(const double2* 
 cudaError_t launch_id_check(const double2* mats, const double2* tbuf, const int* perm, const int* rank,
                             const CheckJob* jobs, int njobs, double* ratio, cudaStream_t s) {
   if (njobs <= 0) return cudaSuccess;
-  id_check_kernel<<<njobs, kCheckThreads, 0, s>>>(mats, tbuf, perm, rank, jobs, ratio);
+  // the maxima after the njobs ratios (the caller's buffer holds 3 njobs doubles)
+  unsigned long long* acc = reinterpret_cast<unsigned long long*>(ratio + njobs);
+  cudaError_t e = cudaMemsetAsync(acc, 0, 2 * (size_t)njobs * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  id_check_kernel<<<dim3(njobs, kCheckSplit), kCheckThreads, 0, s>>>(mats, tbuf, perm, rank, jobs, acc);
+  count_launches(1);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  id_check_ratio_kernel<<<(njobs + 127) / 128, 128, 0, s>>>(acc, njobs, ratio);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -851,7 +851,7 @@ int compress_height(symhss_s* h, int t, cudaStream_t s) {
     Packer cp;
     cp.add(cj);
     CK(cp.upload(h->chkjobs, s));
-    CK(h->chkratio.ensure(cj.size() * sizeof(double)));
+    CK(h->chkratio.ensure(cj.size() * 3 * sizeof(double)));  // ratios, then the check's maxima
     TIMED(SYMHSS_K_CHECK, 0.0, launch_id_check(H.mr.as<double2>(), H.tbuf.as<double2>(), H.permbuf.as<int>(),
                                                H.rankbuf.as<int>(), h->chkjobs.as<CheckJob>(), (int)cj.size(),
                                                h->chkratio.as<double>(), s));
@@ -1022,7 +1022,7 @@ int compress_height(symhss_s* h, int t, cudaStream_t s) {
       ia.max_m = max_m;
       std::vector<double> r2(chk.size());
       if (!proxy_check) {
-        CK(h->chkratio.ensure(chk.size() * sizeof(double)));
+        CK(h->chkratio.ensure(chk.size() * 3 * sizeof(double)));  // ratios, then the check's maxima
         TIMED(SYMHSS_K_CHECK, 0.0, launch_id_check(H.mr.as<double2>(), H.tbuf.as<double2>(), H.permbuf.as<int>(),
                                                    H.rankbuf.as<int>(),
                                                    reinterpret_cast<const CheckJob*>(H.idjobs.as<char>() + oc),
