@@ -616,9 +616,11 @@ __global__ void __launch_bounds__(kInvThreads) trinv_kernel(const RsLaunch a, in
   const int cl = lane & 7, slot = warp * 4 + (lane >> 3);
   const int col = 8 * g + cl;
   const double2* A = a.abase + jb.a_off + J + (long long)J * jb.lda;
-  for (int e = tid; e < 64 * 64; e += kInvThreads) {
+  // the columns the steps below read: k >= 8g (L side), k <= 8g + 7 (U side)
+  const int klo = upper ? 0 : 8 * g, khi = upper ? min(8 * g + 8, w) : w;
+  for (int e = tid + klo * 64; e < khi * 64; e += kInvThreads) {
     const int i = e & 63, k = e >> 6;
-    tri[e] = (i < w && k < w) ? A[i + (long long)k * jb.lda] : make_double2(0.0, 0.0);
+    tri[e] = i < w ? A[i + (long long)k * jb.lda] : make_double2(0.0, 0.0);
   }
   if (upper)
     for (int k = tid; k < w; k += kInvThreads) dinv_u[k] = cinv(A[k + (long long)k * jb.lda]);
@@ -639,6 +641,7 @@ __global__ void __launch_bounds__(kInvThreads) trinv_kernel(const RsLaunch a, in
         const double2 xk = xs[par * 8 + cl];
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
+          if (16 * m + 15 <= k) continue;  // uniform: no row of this layer below k
           const int i = slot + 16 * m;
           if (i > k && i < w) x[m] = cfms(tri[k * 64 + i], xk, x[m]);
         }
@@ -661,6 +664,7 @@ __global__ void __launch_bounds__(kInvThreads) trinv_kernel(const RsLaunch a, in
         const double2 xk = xs[par * 8 + cl];
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
+          if (16 * m >= k) continue;  // uniform: no row of this layer above k
           const int i = slot + 16 * m;
           if (i < k) x[m] = cfms(tri[k * 64 + i], xk, x[m]);
         }
