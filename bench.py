@@ -254,12 +254,15 @@ def bench_workload(w, args, steps, warmup, precision="fp64", net=None, autotune=
             t_at = time.perf_counter()
             tn = S.symhss_autotune(s.h, reps=2, stream=stream.cuda_stream)
             out["tuning"][mode] = dict(tn.as_dict(), seconds=time.perf_counter() - t_at)
-        for _ in range(warmup):
-            x = step(s)
-        barrier()
+        # the clock sampler (an nvidia-smi process polling every 200 ms) starts before the warm-up
+        # steps: its start-up competes for the host cores that enqueue the pipelined build, and
+        # inside the timed region it stalled the first timed step by about 20 ms
         sampler = ClockSampler(torch.cuda.current_device()) if (mode == "sym" and sample_clocks) else None
         if sampler:
             sampler.start()
+        for _ in range(warmup):
+            x = step(s)
+        barrier()
         times = []
         launches0 = S.lib.symhss_launch_count()
         acc = _new_acc()
