@@ -439,10 +439,11 @@ int symhss_column_id(void* A, int m, int n, int lda, long long strideA, int batc
  * a status word) lives in one library-owned __device__ array sized for at most
  * 4096 matrices per call, which every GPU that loads the library keeps until the
  * process exits; batch > 4096 returns SYMHSS_ERR_INVALID.  The first call on a
- * device looks up that array's device address with the device current, so make
- * it before any stream capture begins; the address is kept for the process, so
- * the device must not be reset (cudaDeviceReset) while the library is in use.
- * Every call synchronises `stream` to read its status word back.  Every call reuses the same array: calls
+ * device looks up that array's device address with the device current; the
+ * address is kept for the process, so the device must not be reset
+ * (cudaDeviceReset) while the library is in use.  Every call synchronises
+ * `stream` to read its status word back, so no call can be made while the stream
+ * is being captured into a graph.  Every call reuses the same array: calls
  * whose GPU work overlaps (unordered streams or host threads) race and must not
  * be issued.  This entry point is an engineering addition with no counterpart in
  * the paper. */
