@@ -733,7 +733,7 @@ int compress_height(symhss_s* h, int t, cudaStream_t s) {
       } else if (t == 0) {
         // leaves: a box of radius rho sees about 2 k rho oscillations plus a few terms per
         // decade of the tolerance (the proxy expansion's length); never above half the smaller
-        // dimension.  The held-out check and the redo path stay the judges of every ID.
+        // dimension.  The held-out check and the redo path still decide every ID.
         const symhss_params& pp = h->probs[rf.p].prm;
         const double kr = std::max(pp.k0, pp.k1) * rf.bx->rho;
         const double dec = std::log10(1.0 / std::max(1e-300, h->prm.tol));
