@@ -487,8 +487,8 @@ struct RsLaunch {
                                   // every solve composes them from piv
   int blk = 64;                   // row block of the blocked tensor-core solve: 16, 32 or 64
   double2* dinv = nullptr;        // optional scratch, getrs_dinv_bytes(njobs, max_n): the blocked
-  long long dinv_bytes = 0;       // solve with 64-row blocks and few matrices (< 32) then solves its
-                                  // diagonal blocks through their inverses on the tensor cores
+  long long dinv_bytes = 0;       // solve with 64-row blocks then solves its diagonal blocks
+                                  // through their inverses on the tensor cores
 };
 cudaError_t launch_getrs(const RsLaunch& a, cudaStream_t s);
 // bytes of RsLaunch::dinv: two 64 x 64 complex128 blocks (the inverses of L's unit-lower and U's

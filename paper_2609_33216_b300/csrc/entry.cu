@@ -462,7 +462,9 @@ int symhss_lu_solve_batched(const void* LU, int n, int lda, long long strideA, c
     CKE(zimg.alloc((size_t)a.zimg_bytes));
     a.zimg = reinterpret_cast<unsigned char*>(zimg.p);
   }
-  TmpBuf dinv;  // inverses of the diagonal blocks (blocked solve of few matrices)
+  // inverses of the diagonal blocks for batches of fewer than 32 matrices; larger batches keep
+  // the substitutions with the right-hand sides on the lanes (both paths reachable from here)
+  TmpBuf dinv;
   if (batch < 32 && nrhs > 4) {
     a.dinv_bytes = getrs_dinv_bytes(batch, n);
     CKE(dinv.alloc((size_t)a.dinv_bytes));

@@ -726,9 +726,9 @@ cudaError_t getrs_blocked_tc(const RsLaunch& a, cudaStream_t s) {
   // one serial chain on s: every kernel after the permutation is a programmatic dependent of
   // the one before it
   g.chained = 1;
-  // few matrices (the upper tree levels): the diagonal blocks through their inverses, formed
-  // once (trinv_kernel) and applied as tensor-core products, instead of substitutions on the
-  // FP64 pipe, which there run one right-hand side per warp
+  // with the inverse scratch: the diagonal blocks through their inverses, formed once
+  // (trinv_kernel) and applied as tensor-core products, instead of substitutions on the FP64
+  // pipe (one right-hand side per warp for few matrices, per lane for many)
   const int nbmax = (max_n + 63) / 64;
   if (W == kBlk && a.dinv && a.dinv_bytes >= getrs_dinv_bytes(a.njobs, max_n)) {
     const size_t ismem = (size_t)(64 * 64 + 64 + 16) * sizeof(double2);

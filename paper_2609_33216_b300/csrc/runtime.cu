@@ -163,7 +163,7 @@ struct Height {
   DevBuf chkmeta, chkg;          // exact residual checks of sketched IDs (proposer mode)
   DevBuf chkimg;                 // their tensor-core product scratch (compression stream)
   DevBuf zimg;                   // tensor-core product scratch of the factorisation stream
-  DevBuf dinv;                   // inverses of the diagonal blocks of the blocked solves (< 32 blocks)
+  DevBuf dinv;                   // inverses of the diagonal blocks of the blocked solves
   // matvec
   DevBuf XV, XS, ZV, YS, YV, mlists;
   std::vector<int> h_rank;
