@@ -22,6 +22,8 @@
 // a factorisation left by an earlier launch (used to raise a rank).
 #include <cooperative_groups.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace cg = cooperative_groups;
@@ -169,41 +171,47 @@ __global__ void __launch_bounds__(kThreads) cpqr_cluster_kernel(const IdLaunch a
     if (tid == 0) { done[p] = 1; order[k] = p; }
     __syncthreads();
     const double tau = s_tau;
-    // 4. apply to owned remaining columns, recompute their remaining norms: 8 lanes per
-    //    column, 4 columns per warp (each column segment is one 128-byte line; the lane sums
-    //    take 3 shuffle levels instead of 5, and fewer lanes idle at the column's end).
+    // 4. apply to owned remaining columns, recompute their remaining norms: LPC lanes per
+    //    column, 32 / LPC columns per warp (LPC = 8: each column segment is one 128-byte line,
+    //    the lane sums take 3 shuffle levels instead of 5; LPC = 16 for tall matrices, m >= 128,
+    //    where a block owns few columns: twice the warps share them, so the busiest
+    //    sub-partition's FP64 pipe carries less of the step).  The choice depends on the
+    //    launch's largest m only, so every cluster size gives the same sums.
     //    Every sum is a chain of fused multiply-adds (4 per element for v^H c, 2 for |c|^2):
     //    the FP64 pipe bounds this loop on this GPU, and separate products and additions
     //    would issue 13 FP64 instructions per element instead of 10.
-    {
-      const int grp = lane >> 3, gl = lane & 7;
+    auto apply_cols = [&](auto lpc) {
+      constexpr int LPC = decltype(lpc)::value, CPW = 32 / LPC;
+      const int grp = lane / LPC, gl = lane % LPC;
       const int nown = (n - rank + C - 1) / C;  // owned columns: j = rank + C * t, t < nown
-      for (int t0 = 4 * warp; t0 < nown; t0 += 4 * kWarps) {  // uniform per warp
+      for (int t0 = CPW * warp; t0 < nown; t0 += CPW * kWarps) {  // uniform per warp
         const int t = t0 + grp;
         const int j = rank + C * t;
         const bool act = t < nown && j < n && !done[j];
         double2* col = M + (long long)(act ? j : 0) * ld;
         double2 w = make_double2(0.0, 0.0);
         if (act)
-          for (int i = k + gl; i < m; i += 8) w = cconjfma(vbuf[i - k], col[i], w);
+          for (int i = k + gl; i < m; i += LPC) w = cconjfma(vbuf[i - k], col[i], w);
 #pragma unroll
-        for (int o = 4; o > 0; o >>= 1) {
+        for (int o = LPC / 2; o > 0; o >>= 1) {
           w.x += __shfl_xor_sync(0xffffffffu, w.x, o);
           w.y += __shfl_xor_sync(0xffffffffu, w.y, o);
         }
         w = make_double2(w.x * tau, w.y * tau);
         double ns = 0.0;
         if (act)
-          for (int i = k + gl; i < m; i += 8) {
+          for (int i = k + gl; i < m; i += LPC) {
             const double2 c = cfms(vbuf[i - k], w, col[i]);
             col[i] = c;
             if (i > k) ns = cabs2_acc(c, ns);
           }
 #pragma unroll
-        for (int o = 4; o > 0; o >>= 1) ns += __shfl_xor_sync(0xffffffffu, ns, o);
+        for (int o = LPC / 2; o > 0; o >>= 1) ns += __shfl_xor_sync(0xffffffffu, ns, o);
         if (act && gl == 0) norms[j] = sqrt(ns);
       }
-    }
+    };
+    if (a.max_m >= 128) apply_cols(std::integral_constant<int, 16>{});
+    else apply_cols(std::integral_constant<int, 8>{});
     if (rank == owner && tid == 0) M[k + (long long)p * ld] = s_alpha;
     // the owner rewrites vbuf only after the next step's first cluster barrier,
     // which every reader of this step's v passes after finishing with it
