@@ -163,11 +163,11 @@ def fp64_peak_tflops(sm_mhz):
 # and per step.  A class whose kernels change after the capture must lose its entry (its traffic is
 # then reported as null).
 NCU_TRAFFIC = {
-    "getrf": {"bytes_per_launch": 1728.4e6 / 15, "bytes_per_step": 1728.4e6,
+    "getrf": {"bytes_per_launch": 1728.7e6 / 15, "bytes_per_step": 1728.7e6,
               "capture": "profiles/star16k_launch_list.md (DRAM table)"},
-    "getrs": {"bytes_per_launch": 3214.1e6 / 22, "bytes_per_step": 3214.1e6,
+    "getrs": {"bytes_per_launch": 3215.5e6 / 22, "bytes_per_step": 3215.5e6,
               "capture": "profiles/star16k_launch_list.md (DRAM table)"},
-    "id": {"bytes_per_launch": 68.6e6 / 8, "bytes_per_step": 68.6e6,
+    "id": {"bytes_per_launch": 68.8e6 / 8, "bytes_per_step": 68.8e6,
            "capture": "profiles/star16k_launch_list.md (DRAM table)"},
 }
 
